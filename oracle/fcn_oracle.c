@@ -1,0 +1,598 @@
+/*
+ * fcn_oracle.c -- plain FP64 CPU oracle of the FCN z-step (Ma & Lin,
+ * arXiv:1507.05988, Sec. 3).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests, the smoke check and the CPU-baseline
+ * leg of the benchmark may load this code; the CUDA library never does.  It is
+ * written to be read against the paper: every loop follows the order in which
+ * Sec. 3 states the method, with no blocking, fusion or reordering.
+ *
+ * Readings of the paper taken here (the paper is ambiguous or garbled at
+ * these places):
+ *   R1  c_j and f_j (Sec. 3, coefficients of Eq. (matrix1)) carry the factor
+ *       (1 + 1/(2j)), which is what Eqs. (diff2)-(diff3) give for the
+ *       A_{j+1} entries; the printed (1 - 1/(2j)) is kept behind
+ *       ORC_PRINTED_CJ only so the tests can show that it is rejected.
+ *   R2  The plasma term of Eq. (nonlinearpart) uses omega_pe^2/omega0^2
+ *       = rho/rho_c (the printed omega_pe^2/omega0 is not dimensionless):
+ *       N_plasma = -i k0/(2 n0^2) rho/rho_c.
+ *   R3  rho follows Eq. (ionization) with beta_K/(K hbar omega0) written as
+ *       sigma_K rho_nt and rho_at := rho_nt, i.e.
+ *       d rho/d tau = sigma_K I^K (rho_nt - rho).
+ *   R4  Within one nonlinear half step (Eq. (Anhalf)) N is frozen at the
+ *       field entering that half step; rho is integrated by RK4 (Sec. 3.2)
+ *       from rho(tau_min) = 0 using the intensity of the pre-update row, with
+ *       the RK4 midpoint intensity taken as the mean of the two neighbours.
+ *   R5  Grid: dr = R/(Nr-1) with the Dirichlet node at m = Nr-1 (Eq. (bound));
+ *       dtau = T/Nt, tau_p = -T/2 + p dtau, periodic in tau; omega_q = 2 pi q
+ *       /(Nt dtau) for q < Nt/2 and 2 pi (q - Nt)/(Nt dtau) otherwise.
+ *   R6  The forward transform is exp(-2 pi i p q / Nt), unnormalised; the
+ *       inverse carries 1/Nt (Eq. (antifourier)).
+ */
+#include "fcn_oracle.h"
+
+#include <complex.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* CODATA 2018 values (SI). */
+#define ORC_C_LIGHT 299792458.0
+#define ORC_HBAR    1.054571817e-34
+#define ORC_EPS0    8.8541878128e-12
+#define ORC_M_E     9.1093837015e-31
+#define ORC_Q_E     1.602176634e-19
+#define ORC_PI      3.14159265358979323846
+
+typedef double complex cplx;
+
+/* ------------------------------------------------------------------ */
+/* Derived constants                                                   */
+/* ------------------------------------------------------------------ */
+
+/* Carrier wave number k0 = 2 pi n0 / lambda0 (Sec. 2). */
+double orc_k0(const orc_problem *pb) { return 2.0 * ORC_PI * pb->n0 / pb->lambda0; }
+
+/* Carrier angular frequency omega0 = 2 pi c / lambda0 (Sec. 2). */
+double orc_omega0(const orc_problem *pb) { return 2.0 * ORC_PI * ORC_C_LIGHT / pb->lambda0; }
+
+/* Critical plasma density rho_c = eps0 m_e omega0^2 / q_e^2, the density at
+ * which omega_pe (Sec. 2, below Eq. (plasmasource)) equals omega0 (reading R2). */
+double orc_rho_c(const orc_problem *pb)
+{
+    double w0 = orc_omega0(pb);
+    return ORC_EPS0 * ORC_M_E * w0 * w0 / (ORC_Q_E * ORC_Q_E);
+}
+
+/* MPI loss coefficient beta_K = K hbar omega0 sigma_K rho_nt, so that the
+ * rate of Eq. (ionization) is sigma_K I^K (rho_nt - rho) (reading R3). */
+double orc_beta_k(const orc_problem *pb)
+{
+    return (double)pb->K * ORC_HBAR * orc_omega0(pb) * pb->sigma_k * pb->rho_nt;
+}
+
+/* Angular frequency of FFT bin q (reading R5). */
+double orc_omega(const orc_problem *pb, int q)
+{
+    double dtau = pb->t_window / pb->nt;
+    int qq = (q < pb->nt / 2) ? q : q - pb->nt;
+    return 2.0 * ORC_PI * (double)qq / (pb->nt * dtau);
+}
+
+static double ipow(double x, int k)
+{
+    double r = 1.0;
+    for (int i = 0; i < k; ++i) r *= x;
+    return r;
+}
+
+/* ------------------------------------------------------------------ */
+/* FFT along tau (Sec. 3.1, first and third loop)                     */
+/* ------------------------------------------------------------------ */
+
+/* In-place iterative radix-2 Cooley-Tukey transform of n interleaved complex
+ * values.  inverse = 0: X_q = sum_p x_p exp(-2 pi i p q / n).
+ * inverse = 1: x_p = (1/n) sum_q X_q exp(+2 pi i p q / n).
+ * Returns -1 if n is not a power of two. */
+int orc_fft(double *xd, int n, int inverse)
+{
+    if (n < 1 || (n & (n - 1)) != 0) return -1;
+    cplx *x = (cplx *)xd;
+    /* bit-reversal permutation */
+    for (int i = 1, j = 0; i < n; ++i) {
+        int bit = n >> 1;
+        for (; j & bit; bit >>= 1) j ^= bit;
+        j ^= bit;
+        if (i < j) { cplx t = x[i]; x[i] = x[j]; x[j] = t; }
+    }
+    double sgn = inverse ? 1.0 : -1.0;
+    for (int len = 2; len <= n; len <<= 1) {
+        int half = len / 2;
+        for (int k = 0; k < half; ++k) {
+            double ang = sgn * 2.0 * ORC_PI * (double)k / (double)len;
+            cplx w = cos(ang) + I * sin(ang);
+            for (int s = 0; s < n; s += len) {
+                cplx u = x[s + k];
+                cplx v = x[s + k + half] * w;
+                x[s + k] = u + v;
+                x[s + k + half] = u - v;
+            }
+        }
+    }
+    if (inverse) {
+        double inv = 1.0 / (double)n;
+        for (int i = 0; i < n; ++i) x[i] *= inv;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Tridiagonal "chasing" solve (Sec. 3.1, remark after the loops)     */
+/* ------------------------------------------------------------------ */
+
+/* Thomas algorithm without pivoting for
+ *   a_j x_{j-1} + b_j x_j + c_j x_{j+1} = d_j,  j = 0..n-1
+ * (a_0 and c_{n-1} are ignored).  All arrays interleaved complex.
+ * Returns -1 on a zero pivot. */
+int orc_thomas(int n, const double *ad, const double *bd, const double *cd,
+               const double *dd, double *xd)
+{
+    const cplx *a = (const cplx *)ad, *b = (const cplx *)bd, *c = (const cplx *)cd;
+    const cplx *d = (const cplx *)dd;
+    cplx *x = (cplx *)xd;
+    cplx *cp = (cplx *)malloc(sizeof(cplx) * (size_t)n);
+    cplx *dp = (cplx *)malloc(sizeof(cplx) * (size_t)n);
+    if (!cp || !dp) { free(cp); free(dp); return -2; }
+    cplx piv = b[0];
+    if (piv == 0) { free(cp); free(dp); return -1; }
+    cp[0] = c[0] / piv;
+    dp[0] = d[0] / piv;
+    for (int j = 1; j < n; ++j) {
+        piv = b[j] - a[j] * cp[j - 1];
+        if (piv == 0) { free(cp); free(dp); return -1; }
+        cp[j] = (j < n - 1) ? c[j] / piv : 0;
+        dp[j] = (d[j] - a[j] * dp[j - 1]) / piv;
+    }
+    x[n - 1] = dp[n - 1];
+    for (int j = n - 2; j >= 0; --j) x[j] = dp[j] - cp[j] * x[j + 1];
+    free(cp);
+    free(dp);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Crank-Nicolson matrices (Eqs. (diff1)-(diff3), (bound), (matrix))  */
+/* ------------------------------------------------------------------ */
+
+/* Fills the six diagonals of M_abc^q (a, b, c) and M_def^q (d, e, f) for
+ * frequency bin q, each nr interleaved complex values.
+ * With s = dz/(4 k0 dr^2) and delta_q = k'' omega_q^2 dz / 4:
+ *   row 0      : b = 1 + 4is - i delta, c = -4is, e = 1 - 4is + i delta, f = 4is
+ *   1<=j<=nr-2 : a = -is(1 - 1/2j), b = 1 + 2is - i delta, c = -is(1 + 1/2j)
+ *                d =  is(1 - 1/2j), e = 1 - 2is + i delta, f =  is(1 + 1/2j)
+ *   row nr-1   : b = 1, a = c = d = e = f = 0       (A = 0 at r = R)
+ * The row-0 entries come from the r -> 0 limit Delta_perp -> 2 d^2/dr^2 with
+ * the mirror point A_{-1} = A_1 (dA/dr = 0 at r = 0, Eq. (bound)). */
+void orc_cn_coeffs(const orc_problem *pb, double dz, int q,
+                   double *ad, double *bd, double *cd,
+                   double *dd, double *ed, double *fd)
+{
+    int nr = pb->nr;
+    cplx *a = (cplx *)ad, *b = (cplx *)bd, *c = (cplx *)cd;
+    cplx *d = (cplx *)dd, *e = (cplx *)ed, *f = (cplx *)fd;
+    double dr = pb->r_max / (double)(nr - 1);
+    double k0 = orc_k0(pb);
+    double s = (pb->flags & ORC_DIFFRACTION) ? dz / (4.0 * k0 * dr * dr) : 0.0;
+    double w = orc_omega(pb, q);
+    double delta = (pb->flags & ORC_DISPERSION) ? pb->k2 * w * w * dz / 4.0 : 0.0;
+
+    a[0] = 0;
+    b[0] = 1.0 + I * (4.0 * s) - I * delta;
+    c[0] = -I * (4.0 * s);
+    d[0] = 0;
+    e[0] = 1.0 - I * (4.0 * s) + I * delta;
+    f[0] = I * (4.0 * s);
+    for (int j = 1; j <= nr - 2; ++j) {
+        double lo = 1.0 - 1.0 / (2.0 * j);
+        double hi = (pb->flags & ORC_PRINTED_CJ) ? lo : 1.0 + 1.0 / (2.0 * j);
+        a[j] = -I * s * lo;
+        b[j] = 1.0 + I * (2.0 * s) - I * delta;
+        c[j] = -I * s * hi;
+        d[j] = I * s * lo;
+        e[j] = 1.0 - I * (2.0 * s) + I * delta;
+        f[j] = I * s * hi;
+    }
+    a[nr - 1] = 0;
+    b[nr - 1] = 1.0;
+    c[nr - 1] = 0;
+    d[nr - 1] = 0;
+    e[nr - 1] = 0;
+    f[nr - 1] = 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Plasma density along tau (Eq. (ionization), RK4 of Sec. 3.2)       */
+/* ------------------------------------------------------------------ */
+
+/* d rho / d tau = sigma_K I^K (rho_nt - rho)   (reading R3) */
+static double rho_rate(const orc_problem *pb, double intensity, double rho)
+{
+    return pb->sigma_k * ipow(intensity, pb->K) * (pb->rho_nt - rho);
+}
+
+/* Integrates rho along one row with classic RK4, step dtau, from
+ * rho(tau_min) = 0.  intensity[p] = |A_{m,p}|^2 of the row entering the half
+ * step; the midpoint intensity is the mean of its neighbours (reading R4). */
+void orc_rho_row(const orc_problem *pb, const double *intensity, double *rho)
+{
+    double h = pb->t_window / pb->nt;
+    rho[0] = 0.0;
+    for (int p = 0; p + 1 < pb->nt; ++p) {
+        double ia = intensity[p];
+        double ib = intensity[p + 1];
+        double im = 0.5 * (ia + ib);
+        double r = rho[p];
+        double k1 = rho_rate(pb, ia, r);
+        double k2 = rho_rate(pb, im, r + 0.5 * h * k1);
+        double k3 = rho_rate(pb, im, r + 0.5 * h * k2);
+        double k4 = rho_rate(pb, ib, r + h * k3);
+        rho[p + 1] = r + h / 6.0 * (k1 + 2.0 * k2 + 2.0 * k3 + k4);
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Nonlinear half step (Eqs. (nonlinearpart), (Anhalf), (Anhalf1))     */
+/* ------------------------------------------------------------------ */
+
+/* The operator N of Eq. (nonlinearpart) at intensity I and density rho:
+ *   N = i (k0/n0) sum_j n_2j I^j - i k0/(2 n0^2) rho/rho_c - (beta_K/2) I^(K-1)
+ * (readings R2, R3; the optional ORC_MPI_SAT factor multiplies the loss by
+ * (1 - rho/rho_nt)). */
+static cplx nl_operator(const orc_problem *pb, double intensity, double rho)
+{
+    double k0 = orc_k0(pb);
+    double phase = 0.0, loss = 0.0;
+    if (pb->flags & ORC_KERR) {
+        double ij = 1.0;
+        for (int j = 0; j < 4; ++j) {
+            ij *= intensity;
+            phase += (k0 / pb->n0) * pb->n2j[j] * ij;
+        }
+    }
+    if (pb->flags & ORC_PLASMA)
+        phase -= k0 / (2.0 * pb->n0 * pb->n0) * rho / orc_rho_c(pb);
+    if (pb->flags & ORC_MPI) {
+        loss = 0.5 * orc_beta_k(pb) * ipow(intensity, pb->K - 1);
+        if (pb->flags & ORC_MPI_SAT) loss *= (1.0 - rho / pb->rho_nt);
+    }
+    return -loss + I * phase;
+}
+
+/* One nonlinear half step on one row: rho from the row as it enters
+ * (orc_rho_row), then A_p <- A_p exp(h N(I_p, rho_p)) for p = 0..nt-1, with
+ * h = dz/2.  rho (nt values) receives the density used. */
+void orc_nl_half(const orc_problem *pb, double h, double *rowd, double *rho)
+{
+    int nt = pb->nt;
+    cplx *row = (cplx *)rowd;
+    double *inten = (double *)malloc(sizeof(double) * (size_t)nt);
+    for (int p = 0; p < nt; ++p) {
+        double re = creal(row[p]), im = cimag(row[p]);
+        inten[p] = re * re + im * im;
+    }
+    orc_rho_row(pb, inten, rho);
+    for (int p = 0; p < nt; ++p) row[p] *= cexp(h * nl_operator(pb, inten[p], rho[p]));
+    free(inten);
+}
+
+/* ------------------------------------------------------------------ */
+/* Linear step (Sec. 3.1: three loops)                                 */
+/* ------------------------------------------------------------------ */
+
+/* A <- F^{-1}( (M_abc^q)^{-1} M_def^q F(A) ) for the whole nr x nt field. */
+int orc_linear_step(const orc_problem *pb, double dz, double *Ad)
+{
+    int nr = pb->nr, nt = pb->nt;
+    cplx *A = (cplx *)Ad;
+    /* first loop: forward transform of every row */
+    for (int m = 0; m < nr; ++m)
+        if (orc_fft((double *)(A + (size_t)m * nt), nt, 0)) return -1;
+    /* second loop: one tridiagonal system per frequency */
+    cplx *co = (cplx *)malloc(sizeof(cplx) * (size_t)nr * 8);
+    cplx *a = co, *b = co + nr, *c = co + 2 * nr, *d = co + 3 * nr;
+    cplx *e = co + 4 * nr, *f = co + 5 * nr, *col = co + 6 * nr, *rhs = co + 7 * nr;
+    int rc = 0;
+    for (int q = 0; q < nt && rc == 0; ++q) {
+        orc_cn_coeffs(pb, dz, q, (double *)a, (double *)b, (double *)c,
+                      (double *)d, (double *)e, (double *)f);
+        for (int j = 0; j < nr; ++j) col[j] = A[(size_t)j * nt + q];
+        /* rhs = M_def^q * A~_{.,q} */
+        for (int j = 0; j < nr; ++j) {
+            cplx v = e[j] * col[j];
+            if (j > 0) v += d[j] * col[j - 1];
+            if (j < nr - 1) v += f[j] * col[j + 1];
+            rhs[j] = v;
+        }
+        rc = orc_thomas(nr, (double *)a, (double *)b, (double *)c,
+                        (double *)rhs, (double *)col);
+        for (int j = 0; j < nr; ++j) A[(size_t)j * nt + q] = col[j];
+    }
+    free(co);
+    if (rc) return -2;
+    /* third loop: inverse transform of every row */
+    for (int m = 0; m < nr; ++m)
+        if (orc_fft((double *)(A + (size_t)m * nt), nt, 1)) return -1;
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* One Strang step (Eq. (nlseq)) and the serial driver (Sec. 3 end)    */
+/* ------------------------------------------------------------------ */
+
+/* A^{n+1} = exp(N dz/2) exp(D dz) exp(N dz/2) A^n.  rho (nr*nt, nullable)
+ * receives the density of the second half step. */
+int orc_step(const orc_problem *pb, double dz, double *Ad, double *rho)
+{
+    int nr = pb->nr, nt = pb->nt;
+    double *tmp = (double *)malloc(sizeof(double) * (size_t)nt);
+    for (int m = 0; m < nr; ++m)
+        orc_nl_half(pb, 0.5 * dz, Ad + (size_t)2 * m * nt, tmp);
+    int rc = orc_linear_step(pb, dz, Ad);
+    for (int m = 0; m < nr && rc == 0; ++m)
+        orc_nl_half(pb, 0.5 * dz, Ad + (size_t)2 * m * nt,
+                    rho ? rho + (size_t)m * nt : tmp);
+    free(tmp);
+    return rc;
+}
+
+int orc_run(const orc_problem *pb, double dz, long nsteps, double *A, double *rho)
+{
+    for (long n = 0; n < nsteps; ++n) {
+        int rc = orc_step(pb, dz, A, rho);
+        if (rc) return rc;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Diagnostics (quantities of Fig. 4 plus energy, peaks, spectrum)     */
+/* ------------------------------------------------------------------ */
+
+/* Radial weight of row m in the area integral 2 pi int r dr:
+ * 2 pi dr^2 W_m with W_0 = 1/8 (disc of radius dr/2) and W_m = m.  These are
+ * also the weights in which the Crank-Nicolson operator is self-adjoint. */
+static double radial_weight(int m) { return m == 0 ? 0.125 : (double)m; }
+
+/* energy = 2 pi dr^2 dtau sum_m W_m sum_p |A_mp|^2;
+ * power[p] = 2 pi dr^2 sum_m W_m |A_mp|^2 (nt values, nullable);
+ * fluence[m] = dtau sum_p |A_mp|^2 (nr values, nullable);
+ * spectral_rms from S_q = sum_m W_m |FFT(A_m.)_q|^2. */
+void orc_diag_compute(const orc_problem *pb, const double *Ad, const double *rho,
+                      orc_diag *out, double *power, double *fluence)
+{
+    int nr = pb->nr, nt = pb->nt;
+    const cplx *A = (const cplx *)Ad;
+    double dr = pb->r_max / (double)(nr - 1);
+    double dtau = pb->t_window / nt;
+    double area = 2.0 * ORC_PI * dr * dr;
+    memset(out, 0, sizeof(*out));
+    if (power) for (int p = 0; p < nt; ++p) power[p] = 0.0;
+    double esum = 0.0;
+    for (int m = 0; m < nr; ++m) {
+        double rowsum = 0.0;
+        for (int p = 0; p < nt; ++p) {
+            cplx v = A[(size_t)m * nt + p];
+            double re = creal(v), im = cimag(v);
+            if (!isfinite(re) || !isfinite(im)) out->nonfinite = 1;
+            double i2 = re * re + im * im;
+            rowsum += i2;
+            if (i2 > out->peak_intensity) out->peak_intensity = i2;
+            if (m == 0 && i2 > out->onaxis_peak) out->onaxis_peak = i2;
+            if (power) power[p] += area * radial_weight(m) * i2;
+        }
+        esum += radial_weight(m) * rowsum;
+        if (fluence) fluence[m] = dtau * rowsum;
+    }
+    out->energy = area * dtau * esum;
+    if (rho) {
+        for (size_t i = 0; i < (size_t)nr * nt; ++i)
+            if (rho[i] > out->peak_rho) out->peak_rho = rho[i];
+    }
+    /* spectral rms width */
+    double *row = (double *)malloc(sizeof(double) * 2 * (size_t)nt);
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int m = 0; m < nr; ++m) {
+        memcpy(row, A + (size_t)m * nt, sizeof(double) * 2 * (size_t)nt);
+        orc_fft(row, nt, 0);
+        for (int q = 0; q < nt; ++q) {
+            double sq = radial_weight(m) * (row[2 * q] * row[2 * q] + row[2 * q + 1] * row[2 * q + 1]);
+            double w = orc_omega(pb, q);
+            s0 += sq;
+            s1 += sq * w;
+            s2 += sq * w * w;
+        }
+    }
+    free(row);
+    if (s0 > 0) {
+        double mean = s1 / s0;
+        double var = s2 / s0 - mean * mean;
+        out->spectral_rms = var > 0 ? sqrt(var) : 0.0;
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Step-doubling dz controller (not in the paper: it uses a fixed dz)  */
+/* ------------------------------------------------------------------ */
+
+static double rel_l2(size_t n2, const double *x, const double *ref)
+{
+    double num = 0.0, den = 0.0;
+    for (size_t i = 0; i < n2; ++i) {
+        double d = x[i] - ref[i];
+        num += d * d;
+        den += ref[i] * ref[i];
+    }
+    return den > 0 ? sqrt(num / den) : sqrt(num);
+}
+
+/* From state A at z0, one step of dz gives A1 and two steps of dz/2 give A2;
+ * err = ||A2 - A1|| / ||A2||.  err <= rtol accepts A2.  Either way the next
+ * dz is dz * clamp(0.9 (rtol/err)^(1/3), 0.2, 2) (the Strang local error is
+ * O(dz^3)); err = 0 gives the factor 2.  The last step is clipped to land on
+ * z_end exactly.  Fails (status -1) if dz falls below dz_min or max_reject
+ * consecutive rejections occur. */
+int orc_propagate_adaptive(const orc_problem *pb, double *A, double *rho,
+                           double z0, double z_end, double dz0, double rtol,
+                           double dz_min, int max_reject,
+                           orc_adaptive_result *res)
+{
+    size_t n2 = (size_t)2 * pb->nr * pb->nt;
+    size_t n1 = (size_t)pb->nr * pb->nt;
+    double *a1 = (double *)malloc(sizeof(double) * n2);
+    double *a2 = (double *)malloc(sizeof(double) * n2);
+    double *r2 = (double *)malloc(sizeof(double) * n1);
+    memset(res, 0, sizeof(*res));
+    double z = z0, dz = dz0;
+    int consecutive = 0;
+    int status = 0;
+    while (z < z_end) {
+        double h = dz;
+        int last = 0;
+        if (z + h >= z_end) { h = z_end - z; last = 1; }
+        memcpy(a1, A, sizeof(double) * n2);
+        memcpy(a2, A, sizeof(double) * n2);
+        orc_step(pb, h, a1, NULL);
+        orc_step(pb, 0.5 * h, a2, NULL);
+        orc_step(pb, 0.5 * h, a2, r2);
+        double err = rel_l2(n2, a1, a2);
+        res->last_err = err;
+        double fac = (err > 0) ? 0.9 * cbrt(rtol / err) : 2.0;
+        if (fac < 0.2) fac = 0.2;
+        if (fac > 2.0) fac = 2.0;
+        if (err <= rtol) {
+            memcpy(A, a2, sizeof(double) * n2);
+            if (rho) memcpy(rho, r2, sizeof(double) * n1);
+            z = last ? z_end : z + h;
+            res->accepted++;
+            consecutive = 0;
+            /* a clipped last step does not shrink the proposal */
+            dz = last ? dz : h * fac;
+        } else {
+            res->rejected++;
+            consecutive++;
+            dz = h * fac;
+        }
+        if (dz < dz_min || consecutive > max_reject) { status = -1; break; }
+    }
+    res->z = z;
+    res->dz_next = dz;
+    res->status = status;
+    free(a1);
+    free(a2);
+    free(r2);
+    return status;
+}
+
+/* ------------------------------------------------------------------ */
+/* Learned-dz MLP, FP64 (not in the paper)                             */
+/* ------------------------------------------------------------------ */
+/* Parameter layout (flat): W1[nh][nin], b1[nh], W2[nh][nh], b2[nh],
+ * W3[nh], b3.  Hidden layers use tanh, the output is linear.  Loss is the
+ * mean over the batch of (y - target)^2. */
+
+static void mlp_offsets(int nin, int nh, size_t off[6])
+{
+    off[0] = 0;
+    off[1] = off[0] + (size_t)nh * nin;
+    off[2] = off[1] + (size_t)nh;
+    off[3] = off[2] + (size_t)nh * nh;
+    off[4] = off[3] + (size_t)nh;
+    off[5] = off[4] + (size_t)nh;
+}
+
+int orc_mlp_forward(int batch, int nin, int nh, const double *pr,
+                    const double *x, double *y)
+{
+    size_t o[6];
+    mlp_offsets(nin, nh, o);
+    double *h1 = (double *)malloc(sizeof(double) * (size_t)nh);
+    double *h2 = (double *)malloc(sizeof(double) * (size_t)nh);
+    for (int b = 0; b < batch; ++b) {
+        const double *xb = x + (size_t)b * nin;
+        for (int i = 0; i < nh; ++i) {
+            double s = pr[o[1] + i];
+            for (int k = 0; k < nin; ++k) s += pr[o[0] + (size_t)i * nin + k] * xb[k];
+            h1[i] = tanh(s);
+        }
+        for (int i = 0; i < nh; ++i) {
+            double s = pr[o[3] + i];
+            for (int k = 0; k < nh; ++k) s += pr[o[2] + (size_t)i * nh + k] * h1[k];
+            h2[i] = tanh(s);
+        }
+        double s = pr[o[5]];
+        for (int k = 0; k < nh; ++k) s += pr[o[4] + k] * h2[k];
+        y[b] = s;
+    }
+    free(h1);
+    free(h2);
+    return 0;
+}
+
+/* Loss and its gradient by reverse-mode differentiation of the forward pass
+ * above (chain rule layer by layer; tanh' = 1 - tanh^2). */
+int orc_mlp_loss_grad(int batch, int nin, int nh, const double *pr,
+                      const double *x, const double *target,
+                      double *loss, double *grad)
+{
+    size_t o[6];
+    mlp_offsets(nin, nh, o);
+    size_t np = o[5] + 1;
+    for (size_t i = 0; i < np; ++i) grad[i] = 0.0;
+    double *h1 = (double *)malloc(sizeof(double) * (size_t)nh);
+    double *h2 = (double *)malloc(sizeof(double) * (size_t)nh);
+    double *g1 = (double *)malloc(sizeof(double) * (size_t)nh);
+    double *g2 = (double *)malloc(sizeof(double) * (size_t)nh);
+    double total = 0.0;
+    for (int b = 0; b < batch; ++b) {
+        const double *xb = x + (size_t)b * nin;
+        for (int i = 0; i < nh; ++i) {
+            double s = pr[o[1] + i];
+            for (int k = 0; k < nin; ++k) s += pr[o[0] + (size_t)i * nin + k] * xb[k];
+            h1[i] = tanh(s);
+        }
+        for (int i = 0; i < nh; ++i) {
+            double s = pr[o[3] + i];
+            for (int k = 0; k < nh; ++k) s += pr[o[2] + (size_t)i * nh + k] * h1[k];
+            h2[i] = tanh(s);
+        }
+        double y = pr[o[5]];
+        for (int k = 0; k < nh; ++k) y += pr[o[4] + k] * h2[k];
+        double r = y - target[b];
+        total += r * r;
+        double gy = 2.0 * r / batch;            /* d loss / d y */
+        grad[o[5]] += gy;
+        for (int k = 0; k < nh; ++k) {
+            grad[o[4] + k] += gy * h2[k];
+            g2[k] = gy * pr[o[4] + k] * (1.0 - h2[k] * h2[k]);   /* d/d pre2 */
+        }
+        for (int i = 0; i < nh; ++i) {
+            grad[o[3] + i] += g2[i];
+            for (int k = 0; k < nh; ++k) grad[o[2] + (size_t)i * nh + k] += g2[i] * h1[k];
+        }
+        for (int k = 0; k < nh; ++k) {
+            double s = 0.0;
+            for (int i = 0; i < nh; ++i) s += pr[o[2] + (size_t)i * nh + k] * g2[i];
+            g1[k] = s * (1.0 - h1[k] * h1[k]);                   /* d/d pre1 */
+        }
+        for (int i = 0; i < nh; ++i) {
+            grad[o[1] + i] += g1[i];
+            for (int k = 0; k < nin; ++k) grad[o[0] + (size_t)i * nin + k] += g1[i] * xb[k];
+        }
+    }
+    *loss = total / batch;
+    free(h1);
+    free(h2);
+    free(g1);
+    free(g2);
+    return 0;
+}

@@ -1,0 +1,145 @@
+"""Pins of the oracle's nonlinear half step and plasma-density integration
+(Sec. 3.2, Eqs. (nonlinearpart), (ionization), (Anhalf)) against closed
+forms and physical conservation laws."""
+import math
+
+import numpy as np
+import pytest
+import scipy.constants as sc
+
+import oracle
+from tests.conftest import rel_l2
+
+
+def _problem(nr=4, nt=64, flags=0, **kw):
+    base = dict(nr=nr, nt=nt, r_max=5e-3, t_window=1.6e-12, lambda0=800e-9, n0=1.0,
+                n2j=(3.2e-23, -2.5e-37, 0, 0), k2=2e-29, sigma_k=2.88e-131, rho_nt=5.4e24,
+                K=8, flags=flags)
+    base.update(kw)
+    return oracle.Problem(**base)
+
+
+def test_derived_constants_match_textbook_values():
+    pb = _problem()
+    assert pb.k0() == pytest.approx(2 * np.pi / 800e-9, rel=1e-15)
+    assert pb.omega0() == pytest.approx(2 * np.pi * sc.c / 800e-9, rel=1e-12)
+    # critical density at 800 nm: eps0 m_e omega0^2 / e^2 ~ 1.742e21 cm^-3
+    rc = sc.epsilon_0 * sc.m_e * (2 * np.pi * sc.c / 800e-9) ** 2 / sc.e ** 2
+    assert pb.rho_c() == pytest.approx(rc, rel=1e-8)     # CODATA 2018 vs 2022: ~2e-9
+    assert pb.rho_c() == pytest.approx(1.742e27, rel=1e-3)
+
+
+def _rk4_constant(pb, x):
+    """rho_nt (1 - R^p), R - 1 = sum_{k=1..4} (-x)^k/k!, evaluated without
+    cancellation."""
+    rm1 = sum((-x) ** k / math.factorial(k) for k in range(1, 5))
+    return -pb.rho_nt * np.expm1(np.arange(pb.nt) * np.log1p(rm1))
+
+
+def test_rho_constant_intensity_matches_discrete_rk4_closed_form():
+    """For constant I the ODE rho' = w (rho_nt - rho) is linear with constant
+    coefficients; RK4 multiplies (rho_nt - rho) by R = sum_{k<=4} (-x)^k/k!
+    per step, x = dtau sigma_K I^K."""
+    pb = _problem(nt=256)
+    for I in (1e16, 3e17, 1e18):
+        rho = oracle.rho_row(pb, np.full(pb.nt, I))
+        x = pb.dtau * pb.sigma_k * I ** pb.K
+        ref = _rk4_constant(pb, x)
+        assert rel_l2(rho, ref) < 1e-13
+        # and the continuous solution to O(x^5) per step
+        cont = pb.rho_nt * -np.expm1(-pb.sigma_k * I ** pb.K * pb.dtau * np.arange(pb.nt))
+        assert rel_l2(rho, cont) < max(1e-12, 10 * pb.nt * x ** 5)
+
+
+def test_rho_is_fourth_order_for_a_gaussian_pulse():
+    """Exact solution for piecewise-linear I (the midpoint rule of reading R4):
+    rho = rho_nt (1 - exp(-sigma int I^K)); int over a cell of a linear I is
+    h (Ib^(K+1) - Ia^(K+1)) / ((K+1)(Ib - Ia)).  RK4 error falls as h^4."""
+    errs = []
+    for nt in (512, 1024, 2048):
+        pb = _problem(nt=nt)
+        tau = -pb.t_window / 2 + np.arange(nt) * pb.dtau
+        I = 6e16 * np.exp(-2 * tau ** 2 / (100e-15) ** 2)
+        rho = oracle.rho_row(pb, I)
+        K = pb.K
+        Ia, Ib = I[:-1], I[1:]
+        with np.errstate(invalid="ignore", divide="ignore"):
+            cell = np.where(np.abs(Ib - Ia) > 1e-12 * np.maximum(Ia, Ib),
+                            (Ib ** (K + 1) - Ia ** (K + 1)) / ((K + 1) * (Ib - Ia)),
+                            Ia ** K)
+        integral = np.r_[0.0, np.cumsum(cell * pb.dtau)]
+        exact = pb.rho_nt * -np.expm1(-pb.sigma_k * integral)
+        errs.append(np.max(np.abs(rho - exact)) / np.max(exact))
+    assert errs[-1] < 1e-6
+    assert errs[0] / errs[1] > 12 and errs[1] / errs[2] > 12
+
+
+def test_kerr_half_step_is_a_pure_phase_of_the_kerr_index():
+    pb = _problem(flags=oracle.KERR, n2j=(3.2e-23, -2.5e-37, 1e-52, -1e-67))
+    rng = np.random.default_rng(1)
+    row = 1e8 * (rng.standard_normal(pb.nt) + 1j * rng.standard_normal(pb.nt))
+    out, _ = oracle.nl_half(pb, 5e-3, row)
+    assert np.allclose(np.abs(out), np.abs(row), rtol=1e-14)
+    I = np.abs(row) ** 2
+    dn = sum(pb.n2j[j] * I ** (j + 1) for j in range(4))        # Kerr index change
+    phase = np.angle(out / row)
+    total = pb.k0() * dn / pb.n0 * 5e-3
+    ref = np.angle(np.exp(1j * total))
+    # round-off of a phase of size |total| is ~ eps |total|
+    tol = 1e-14 + 4e-15 * np.abs(total)
+    assert np.all(np.abs(np.angle(np.exp(1j * (phase - ref)))) < tol)
+    assert np.max(np.abs(total)) > 10.0
+
+
+def test_plasma_half_step_phase_follows_the_plasma_index():
+    """Plasma only, flat-top row: the phase is k0 h (n_pl - 1) with the
+    plasma index n_pl = sqrt(1 - rho/rho_c) ~ 1 - rho/(2 rho_c), and rho from
+    the constant-I closed form."""
+    pb = _problem(nt=128, flags=oracle.PLASMA)
+    I = 3e17
+    row = np.full(pb.nt, np.sqrt(I), dtype=complex)
+    h = 5e-2
+    out, rho = oracle.nl_half(pb, h, row)
+    assert np.allclose(np.abs(out), np.sqrt(I), rtol=1e-14)
+    x = pb.dtau * pb.sigma_k * I ** pb.K
+    rho_ref = _rk4_constant(pb, x)
+    assert rel_l2(rho, rho_ref) < 1e-13
+    phase = np.unwrap(np.angle(out))
+    ref = -pb.k0() * h * rho_ref / (2 * pb.rho_c())
+    assert np.max(np.abs(phase - ref)) < 1e-12 * max(1.0, np.max(np.abs(ref)))
+    assert np.max(np.abs(ref)) > 0.5           # the check is not vacuous
+
+
+def test_mpi_loss_energy_equals_ionisation_energy():
+    """Energy conservation between the loss term of Eq. (nlse) and Eq.
+    (ionization): the field loses K hbar omega0 per electron created
+    (rho << rho_nt), which fixes beta_K = K hbar omega0 sigma_K rho_nt.
+    Constant intensity: loss rate per unit length and time, (I - I_out)/h,
+    equals K hbar omega0 d rho/d tau = K hbar omega0 rho_1 / dtau."""
+    pb = _problem(nr=3, nt=16, flags=oracle.MPI)
+    I0 = 3e16
+    row = np.full(pb.nt, np.sqrt(I0), dtype=complex)
+    h = 1e2      # any length: x = h beta I^(K-1) ~ 1e-6 keeps the loss linear in h
+    out, rho = oracle.nl_half(pb, h, row)
+    loss_rate = (I0 - abs(out[0]) ** 2) / h                # W/m^3
+    photon = sc.hbar * 2 * np.pi * sc.c / 800e-9
+    assert 1e-8 < (I0 - abs(out[0]) ** 2) / I0 < 1e-5
+    assert rho[1] / pb.rho_nt < 1e-9
+    assert loss_rate == pytest.approx(pb.K * photon * rho[1] / pb.dtau, rel=1e-5)
+
+
+def test_mpi_only_converges_to_the_loss_ode_at_first_order():
+    """Only MPI on: dI/dz = -beta_K I^K has I(z) = I0 [1 + (K-1) beta I0^(K-1) z]^(-1/(K-1)).
+    The frozen-intensity half steps converge at first order in dz."""
+    I0 = 5e17
+    z = 0.5
+    errs = []
+    for n in (10, 20, 40):
+        pb = _problem(nr=3, nt=4, flags=oracle.MPI)
+        A = np.full((3, 4), np.sqrt(I0), dtype=complex)
+        out, _ = oracle.run(pb, z / n, n, A)
+        K, b = pb.K, pb.beta_k()
+        exact = I0 * (1 + (K - 1) * b * I0 ** (K - 1) * z) ** (-1 / (K - 1))
+        errs.append(abs(abs(out[0, 0]) ** 2 - exact) / exact)
+    assert errs[0] > 1e-6                      # the loss is not negligible
+    assert 1.7 < errs[0] / errs[1] < 2.3 and 1.7 < errs[1] / errs[2] < 2.3
