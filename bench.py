@@ -1,0 +1,348 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the GB300 FCN z-step (Nr*Nt*z-steps per second).
+
+Workload (ours): the filamentation-regime grid Nr = 1024, Nt = 4096 (w0 = 2 mm,
+tp = 50 fs, 5 P_cr, n2 + n4, 1 % seeded amplitude noise, dz = 2 mm), run in the
+FP32-mixed precision form.  Each GPU advances a batch of independent pulses
+of that grid (noise seeds rank*B .. rank*B+B-1), so that the field (B x 33.5 MB)
+is larger than the 129 MB L2 between timed steps.  One bench step is one
+z-step of the whole batch: Strang step = nonlinear half step, FFT along tau,
+Crank-Nicolson column solve, inverse FFT, nonlinear half step.
+
+Also reported on the same line: the kernel roofline of the dominant kernel
+(CUDA-event durations of a profiled replay of the timed steps), the
+end-to-end figure through the C-ABI with host buffers, the plain FP64 path on
+the same batch, the FP32-vs-FP64 field difference after the full 1000-step
+run of one pulse, SM clocks sampled during the timed region, and the FP64
+CPU oracle timed on a bounded sample (rank 0, N = 1).
+
+--impl reference times that oracle (the deliberately slow CPU program the
+CUDA path is checked against) on the same metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Nr*Nt*z-steps/sec on 1 GB300, chosen form vs plain FP64 FCN at <=1e-4 rel-L2"
+UNIT = "point-steps/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--pulses", type=int, default=8, help="pulses per GPU")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "MEASURED_PEAKS.json hbm_gbs (copy, burst)"
+    return 6800.0, "fallback 6.8 TB/s"
+
+
+class ClockSampler:
+    """nvidia-smi clocks sampled every 200 ms while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["clock sampling unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax = float(parts[2])
+                except ValueError:
+                    continue
+                for n, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def rel_l2(a, b):
+    import numpy as np
+    return float(np.sqrt(np.sum(np.abs(a - b) ** 2) / np.sum(np.abs(b) ** 2)))
+
+
+def cpu_oracle_sample(wl, budget_s=15.0):
+    """Times the FP64 CPU oracle (single-threaded) on one pulse of the bench
+    grid for as many whole z-steps as fit in ~budget_s."""
+    import oracle
+    pb = oracle.Problem(**wl.physics())
+    a = wl.field()
+    t0 = time.perf_counter()
+    a, _ = oracle.run(pb, wl.dz, 1, a)
+    t1 = time.perf_counter() - t0
+    n = max(1, int(budget_s / max(t1, 1e-3)) - 1)
+    t0 = time.perf_counter()
+    oracle.run(pb, wl.dz, n, a)
+    dt = time.perf_counter() - t0
+    return {"value": wl.points * n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n} z-steps of one {wl.nr}x{wl.nt} pulse (after 1 untimed), FP64 C oracle, "
+                      f"1 thread, {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_1507_05988_gb300 import workloads as W
+    import oracle
+    wl = W.config2(seed=0)
+    pb = oracle.Problem(**wl.physics())
+    a = wl.field()
+    for _ in range(args.warmup):
+        a, _ = oracle.run(pb, wl.dz, 1, a)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        a, _ = oracle.run(pb, wl.dz, 1, a)
+    dt = time.perf_counter() - t0
+    v = wl.points * args.steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"cfg2 {wl.nr}x{wl.nt} one pulse (seed 0), dz=2 mm, FP64 CPU oracle"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} z-steps of one {wl.nr}x{wl.nt} pulse"},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+        pg = dist
+
+    from paper_1507_05988_gb300 import build
+    build.build()
+    from paper_1507_05988_gb300 import fcn, workloads as W
+
+    B = args.pulses
+    wls = [W.config2(seed=rank * B + i) for i in range(B)]
+    wl0 = wls[0]
+    pts = wl0.points
+    dz = wl0.dz
+    solver = fcn.Solver([w.physics() for w in wls], precision=fcn.FCN_FP32_MIXED)
+    fields = [w.field() for w in wls]
+    for i, f in enumerate(fields):
+        solver.set_field(f, pulse=i)
+    solver.step(dz, args.warmup)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if pg:
+            pg.barrier()
+
+    # ---- timed region: K z-steps of the whole batch, device-resident ----
+    clocks = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    solver.step(dz, args.steps)
+    e1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    barrier()
+    t_ms = e0.elapsed_time(e1)
+    if pg:
+        t = torch.tensor([t_ms], device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        t_ms = float(t.item())
+    value = world * B * pts * args.steps / (t_ms * 1e-3)
+
+    # ---- kernel roofline: replay the same steps with per-launch events ----
+    solver.profile(True)
+    solver.step(dz, args.steps)
+    prof = solver.profile_read(reset=True)
+    solver.profile(False)
+    launches = int(sum(n for _, n in prof.values()))
+    dom = max(prof.items(), key=lambda kv: kv[1][0])
+    dom_name, (dom_ms, dom_n) = dom
+    bytes_per_launch = 2 * pts * 8          # one field read + one write (complex64)
+    peak, peak_src = measured_peaks()
+    achieved = bytes_per_launch / (dom_ms / dom_n * 1e-3) / 1e9
+    kernels = {k: {"launches": n, "avg_us": (ms / n * 1e3 if n else None),
+                   "alg_GBps": (bytes_per_launch / (ms / n * 1e-3) / 1e9 if n else None)}
+               for k, (ms, n) in prof.items()}
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tpath):
+        with open(tpath) as f:
+            traffic = json.load(f).get(dom_name)
+
+    # ---- end to end through the C-ABI with pinned host buffers ----
+    host_in = [torch.from_numpy(f).pin_memory() for f in fields]
+    host_out = [torch.empty_like(h).pin_memory() for h in host_in]
+    K2 = max(1, min(args.steps, 10))
+    import ctypes as C
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(K2):
+        for i in range(B):
+            fcn.check(fcn.fcn_set_field(solver.ctx, i, C.cast(host_in[i].data_ptr(), fcn._D)),
+                      solver.ctx)
+        solver.step(dz, 1)
+        for i in range(B):
+            fcn.check(fcn.fcn_get_field(solver.ctx, i, C.cast(host_out[i].data_ptr(), fcn._D)),
+                      solver.ctx)
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - t0
+    if pg:
+        t = torch.tensor([t_e2e], device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        t_e2e = float(t.item())
+    e2e = {"value": world * B * pts * K2 / t_e2e, "unit": UNIT,
+           "h2d_bytes_per_step": B * pts * 16, "d2h_bytes_per_step": B * pts * 16,
+           "steps": K2, "note": "set_field (host complex128) + fcn_step(dz,1) + get_field per step"}
+    solver.close()
+
+    # ---- plain FP64 FCN on the same batch ----
+    K64 = max(2, min(args.steps, 6))
+    s64 = fcn.Solver([w.physics() for w in wls], precision=fcn.FCN_FP64)
+    for i, f in enumerate(fields):
+        s64.set_field(f, pulse=i)
+    s64.step(dz, 1)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    s64.step(dz, K64)
+    b.record()
+    torch.cuda.synchronize()
+    v64 = world * B * pts * K64 / (a.elapsed_time(b) * 1e-3)
+    s64.close()
+
+    # ---- accuracy of the chosen form against the FP64 path, full 1000-step run ----
+    acc = None
+    if rank == 0 and not args.no_accuracy:
+        out = {}
+        for prec in (fcn.FCN_FP32_MIXED, fcn.FCN_FP64):
+            s = fcn.Solver(wl0.physics(), precision=prec)
+            s.set_field(fields[0])
+            s.step(dz, wl0.nsteps)
+            out[prec] = (s.get_field(), s.diag()["energy"])
+            s.close()
+        acc = {"field_rel_l2": rel_l2(out[fcn.FCN_FP32_MIXED][0], out[fcn.FCN_FP64][0]),
+               "energy_rel": abs(out[fcn.FCN_FP32_MIXED][1] / out[fcn.FCN_FP64][1] - 1),
+               "run": f"{wl0.nsteps} steps of dz = {dz} m, pulse seed 0, FP32-mixed vs FP64 GPU path"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_oracle_sample(wl0)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {
+                "workload": f"cfg2 {wl0.nr}x{wl0.nt} (w0=2 mm, tp=50 fs, 5 Pcr, n2+n4, 1% noise), "
+                            f"dz=2 mm, FP32-mixed, {B} pulses per GPU",
+                "nr": wl0.nr, "nt": wl0.nt, "pulses_per_gpu": B, "dz_m": dz,
+                "l2": f"inputs larger than L2: {B} x {pts * 8 / 1e6:.1f} MB complex64 field "
+                      f"per GPU vs 129 MB L2",
+                "timed": f"one fcn_step(dz, {args.steps}) call (CUDA graphs), CUDA events on "
+                         "the launch stream",
+            },
+            "ms_per_z_step_per_pulse": t_ms / args.steps / B,
+            "gpu_launches": launches,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": dom_name, "peak_source": peak_src,
+                         "algorithmic_bytes_per_launch": bytes_per_launch,
+                         "note": "achieved = algorithmic bytes / mean CUDA-event launch time"},
+            "kernels": kernels,
+            "fp64_gpu": {"value": v64, "unit": UNIT, "steps": K64,
+                         "speedup_of_chosen_form": value / v64},
+            "accuracy_vs_fp64": acc,
+            "clocks": clk,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

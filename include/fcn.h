@@ -1,0 +1,268 @@
+/*
+ * fcn.h -- C-ABI of the GB300 (sm_103a) split-step Fourier / Crank-Nicolson
+ * z-step library for the 2D+1 NLSE of ultra-short pulses in air
+ * (Ma & Lin, arXiv:1507.05988).
+ *
+ * The library advances A(r, tau) along z by Strang steps (Sec. 3, Eq. (nlseq)):
+ *     A^{n+1} = exp(N dz/2) exp(D dz) exp(N dz/2) A^n
+ * with D (Eq. (linearpart)) solved per frequency by the Crank-Nicolson system
+ * of Eq. (matrix) and N (Eq. (nonlinearpart)) applied pointwise in time, the
+ * plasma density coming from Eq. (ionization) integrated along tau by RK4.
+ *
+ * Conventions shared by every entry point
+ *   - Units are SI.  A is in sqrt(W/m^2), |A|^2 is intensity in W/m^2.
+ *   - A field is Nr x Nt complex values, row-major A[m][p]: m = radial index
+ *     (m = 0 on axis, dr = r_max/(Nr-1), A = 0 at m = Nr-1), p = time index
+ *     (contiguous; dtau = t_window/Nt, tau_p = -t_window/2 + p dtau).
+ *     Host buffers are interleaved (re, im) doubles: 2*Nr*Nt doubles.
+ *     Device buffers are interleaved in the working precision: float
+ *     (FCN_FP32_MIXED) or double (FCN_FP64).
+ *   - Nt must be a power of two in [2, 8192]; Nr must be in [3, 2048].
+ *   - Every function returns FCN_OK (0) or a negative FCN_ERR_* code; no C++
+ *     exception crosses the ABI.  fcn_last_error() gives a message.
+ *   - Streams: every launch goes to the stream given at creation (or the
+ *     stream set by fcn_set_stream); NULL means the legacy default stream.
+ *     Functions that return host data synchronise that stream.
+ *   - Ownership: the caller owns every host buffer and every device buffer it
+ *     passes; the library never frees them.  A context owns its own device
+ *     buffers and frees them in fcn_destroy.
+ */
+#ifndef FCN_H
+#define FCN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define FCN_OK                   0
+#define FCN_ERR_ARG             -1   /* invalid argument (size, pointer, dz ...)    */
+#define FCN_ERR_CUDA            -2   /* a CUDA runtime call or launch failed          */
+#define FCN_ERR_NONFINITE       -3   /* the field contains NaN or Inf                 */
+#define FCN_ERR_STEP_UNDERFLOW  -4   /* adaptive dz fell below dz_min / too many rejections */
+#define FCN_ERR_UNSUPPORTED     -5   /* valid request outside the supported sizes     */
+#define FCN_ERR_NOMEM           -6   /* device or host allocation failed              */
+#define FCN_ERR_STATE           -7   /* call out of order (e.g. no field set)         */
+
+/* ---- physics switches (fcn_params.flags) ---- */
+#define FCN_DIFFRACTION   1u   /* (i/2k0) Delta_perp of Eq. (linearpart)                */
+#define FCN_DISPERSION    2u   /* -(i k''/2) d^2/dtau^2 of Eq. (linearpart)             */
+#define FCN_KERR          4u   /* i (k0/n0) sum_j n_2j |A|^2j of Eq. (nonlinearpart)    */
+#define FCN_PLASMA        8u   /* -i k0/(2 n0^2) rho/rho_c of Eq. (nonlinearpart)       */
+#define FCN_MPI          16u   /* -(beta_K/2)|A|^(2K-2) of Eq. (nonlinearpart)          */
+#define FCN_MPI_SAT      32u   /* optional extra factor (1 - rho/rho_nt) on the loss    */
+#define FCN_ALL_PHYSICS  31u
+
+/* ---- working precision ---- */
+#define FCN_FP64        0      /* complex128 everywhere                                   */
+#define FCN_FP32_MIXED  1      /* complex64 field and arithmetic; FP64 reductions and the
+                                  cross-warp carry of the rho(tau) scan                   */
+
+/* Grid (Sec. 3: lattice A(m dr, n dz, p dtau + tau_min)). */
+typedef struct {
+    int32_t nr;          /* radial points                                  */
+    int32_t nt;          /* time points (power of two)                     */
+    double  r_max;       /* R [m]: dr = R/(Nr-1), Dirichlet node at r = R  */
+    double  t_window;    /* T [s]: dtau = T/Nt, tau_min = -T/2             */
+} fcn_grid;
+
+/* Physics (Sec. 2, Eqs. (nlse) and (ionization)).
+ * The rate of Eq. (ionization) is taken as sigma_K I^K (rho_nt - rho), i.e.
+ * beta_K = K hbar omega0 sigma_K rho_nt and rho_at = rho_nt. */
+typedef struct {
+    double   lambda0;    /* carrier wavelength [m]                             */
+    double   n0;         /* linear refractive index                            */
+    double   n2j[4];     /* n2 [m^2/W], n4 [m^4/W^2], n6 [m^6/W^3], n8 [m^8/W^4] */
+    double   k2;         /* GVD k'' [s^2/m]                                    */
+    double   sigma_k;    /* MPI cross section sigma_K [s^-1 m^(2K) W^-K]       */
+    double   rho_nt;     /* neutral density [m^-3]                             */
+    int32_t  K;          /* photon number (1..16)                              */
+    uint32_t flags;      /* FCN_* physics switches                             */
+} fcn_params;
+
+/* Diagnostics, FP64 reductions over the current field (Fig. 4 quantities and
+ * energy).  energy = 2 pi dr^2 dtau sum_m W_m sum_p |A|^2 with W_0 = 1/8,
+ * W_m = m; spectral_rms is the rms width of omega weighted by
+ * sum_m W_m |FFT_tau(A)|^2. */
+typedef struct {
+    double  z;               /* propagated distance [m]                     */
+    double  energy;          /* [J]                                         */
+    double  peak_intensity;  /* max |A|^2 [W/m^2]                           */
+    double  peak_rho;        /* max rho of the last nonlinear half step [m^-3] */
+    double  onaxis_peak;     /* max_p |A_{0,p}|^2 [W/m^2]                   */
+    double  spectral_rms;    /* [rad/s]                                     */
+    int64_t steps;           /* accepted z-steps so far                     */
+    int64_t rejected;        /* rejected adaptive attempts so far           */
+    int32_t nonfinite;       /* 1 if the field holds NaN/Inf                */
+    int32_t pad_;
+} fcn_diag;
+
+/* Result of an adaptive propagation (step doubling; not in the paper, which
+ * uses a fixed dz). */
+typedef struct {
+    double  z;               /* position reached                            */
+    double  dz_next;         /* proposal for the next step                  */
+    double  last_err;        /* last relative L2 step-doubling error        */
+    int64_t accepted;
+    int64_t rejected;
+    int64_t substeps;        /* Strang steps run, including rejected attempts */
+    int64_t mlp_proposals;   /* steps whose dz came from the MLP            */
+} fcn_stats;
+
+typedef struct fcn_ctx fcn_ctx;
+
+/* ========================= context API ========================= */
+
+/* Creates a context for one pulse on the current CUDA device.
+ * grid/params: validated as stated above.  precision: FCN_FP64 or
+ * FCN_FP32_MIXED.  stream: a cudaStream_t (may be NULL).  On success *out
+ * receives the context; the field is zero until fcn_set_field.
+ * Errors: FCN_ERR_ARG, FCN_ERR_UNSUPPORTED, FCN_ERR_NOMEM, FCN_ERR_CUDA. */
+int fcn_create(const fcn_grid *grid, const fcn_params *params, int32_t precision,
+               void *stream, fcn_ctx **out);
+
+/* Creates a context for n independent pulses, each with its own grid and
+ * params (arrays of n).  All pulses advance together in every call; row and
+ * column stages of all pulses run in one launch each (uneven grids are
+ * packed into one work list). */
+int fcn_create_batch(int32_t n, const fcn_grid *grids, const fcn_params *params,
+                     int32_t precision, void *stream, fcn_ctx **out);
+
+/* Frees every device buffer and graph of the context.  NULL is ignored. */
+void fcn_destroy(fcn_ctx *ctx);
+
+/* Message of the last failed call on this context (or of the last failed
+ * creation if ctx is NULL).  Never NULL. */
+const char *fcn_last_error(const fcn_ctx *ctx);
+
+/* Routes all later launches of ctx to stream (cudaStream_t, may be NULL). */
+int fcn_set_stream(fcn_ctx *ctx, void *stream);
+
+/* Copies pulse `pulse`'s field from host memory (2*Nr*Nt doubles, layout
+ * above) to the device, converting to the working precision on the device.
+ * Resets z, the step counters and the diagnostics of that pulse. */
+int fcn_set_field(fcn_ctx *ctx, int32_t pulse, const double *host_field);
+
+/* As fcn_set_field but from a device buffer already in the working
+ * precision (float or double interleaved, Nr*Nt complex).  Device-to-device
+ * copy on the context stream. */
+int fcn_set_field_device(fcn_ctx *ctx, int32_t pulse, const void *dev_field);
+
+/* Copies pulse `pulse`'s field to a caller-owned host buffer of 2*Nr*Nt
+ * doubles (widened on the device in FCN_FP32_MIXED).  Synchronises. */
+int fcn_get_field(fcn_ctx *ctx, int32_t pulse, double *host_out);
+
+/* Copies the field to a caller-owned device buffer in the working precision. */
+int fcn_get_field_device(fcn_ctx *ctx, int32_t pulse, void *dev_out);
+
+/* rho (Nr*Nt doubles, [m^-3]) of the last nonlinear half step of the last
+ * fcn_step/fcn_propagate call (zeros before the first step).  Synchronises. */
+int fcn_get_rho(fcn_ctx *ctx, int32_t pulse, double *host_out);
+
+/* Runs n fixed Strang steps of length dz on every pulse (Sec. 3, the serial
+ * driver's z-loop).  dz > 0 and finite; n >= 0.  Asynchronous: launches only
+ * (a CUDA graph per (dz, n-block) is captured on first use and replayed). */
+int fcn_step(fcn_ctx *ctx, double dz, int64_t n);
+
+/* Same as fcn_step but launches every kernel directly, without CUDA graphs
+ * (for profiling and for checking that graph replay is identical). */
+int fcn_step_nograph(fcn_ctx *ctx, double dz, int64_t n);
+
+/* Adaptive propagation of a single-pulse context to z_end by step doubling:
+ * one step of dz and two of dz/2 from the same state; err = ||A2-A1||/||A2||
+ * (FP64 reduction); err <= rtol accepts A2; next dz = dz*clamp(0.9
+ * (rtol/err)^(1/3), 0.2, 2); the last step lands on z_end exactly.
+ * controller 0: proposals from that formula; controller 1: proposals from
+ * the learned MLP (fcn_mlp_set) with the formula as fallback after a
+ * rejection.  dz0 > 0 is the first proposal.  Fails with
+ * FCN_ERR_STEP_UNDERFLOW if dz < dz_min or after max_reject consecutive
+ * rejections.  out may be NULL. */
+int fcn_propagate(fcn_ctx *ctx, double z_end, double dz0, double rtol, double dz_min,
+                  int32_t max_reject, int32_t controller, fcn_stats *out);
+
+/* FP64 diagnostics of pulse `pulse` (reduction kernels; synchronises).
+ * Returns FCN_ERR_NONFINITE (with *out filled) if the field holds NaN/Inf. */
+int fcn_get_diag(fcn_ctx *ctx, int32_t pulse, fcn_diag *out);
+
+/* On-axis-weighted power P(tau_p) = 2 pi dr^2 sum_m W_m |A_mp|^2 [W]
+ * (Nt doubles) and fluence F(r_m) = dtau sum_p |A_mp|^2 [J/m^2] (Nr doubles)
+ * of pulse `pulse`; either pointer may be NULL.  Synchronises. */
+int fcn_get_profiles(fcn_ctx *ctx, int32_t pulse, double *power, double *fluence);
+
+/* Checkpoint: z, accepted/rejected counters and the last dz proposal
+ * (4 doubles: z, steps, rejected, dz_next).  The field itself is saved with
+ * fcn_get_field and restored with fcn_set_field followed by fcn_set_state. */
+int fcn_get_state(fcn_ctx *ctx, int32_t pulse, double state[4]);
+int fcn_set_state(fcn_ctx *ctx, int32_t pulse, const double state[4]);
+
+/* ========================= kernel timing ========================= */
+/* Kernel kinds reported by fcn_profile_read. */
+#define FCN_PROF_ROW_HEAD  0   /* nonlinear half step + forward FFT               */
+#define FCN_PROF_ROW_MID   1   /* inverse FFT + two half steps + forward FFT      */
+#define FCN_PROF_ROW_TAIL  2   /* inverse FFT + half step + rho + row statistics  */
+#define FCN_PROF_COLUMN    3   /* Crank-Nicolson column solve                      */
+#define FCN_PROF_KINDS     4
+
+/* on != 0: later fcn_step calls launch kernels directly (no graphs) with a
+ * CUDA event pair around each launch on the context stream; on = 0 stops. */
+int fcn_profile_enable(fcn_ctx *ctx, int32_t on);
+
+/* Total device milliseconds and launch counts per kind (FCN_PROF_KINDS
+ * entries each) since the last reset; reset != 0 clears them.  Synchronises. */
+int fcn_profile_read(fcn_ctx *ctx, double *ms, int64_t *count, int32_t reset);
+
+/* ===================== learned dz (MLP) ===================== */
+/* Network 6 -> 64 -> 64 -> 1, tanh hidden layers, linear output; BF16
+ * weights in the forward pass, FP32 accumulation and FP32 master weights.
+ * Flat parameter layout (floats): W1[64][6], b1[64], W2[64][64], b2[64],
+ * W3[64], b3 -- 4673 values. */
+#define FCN_MLP_NIN     6
+#define FCN_MLP_NH      64
+#define FCN_MLP_NPARAM  4673
+
+/* Loads FP32 master weights (host, FCN_MLP_NPARAM floats) into ctx. */
+int fcn_mlp_set(fcn_ctx *ctx, const float *host_params);
+int fcn_mlp_get(fcn_ctx *ctx, float *host_params);
+
+/* ====================== stateless device operations ======================
+ * These run one stage on caller-owned device buffers (e.g. torch tensors)
+ * and exist so each kernel can be checked on its own.  `field`, `rho`,
+ * `table` are device pointers in the working precision; `stream` is a
+ * cudaStream_t.  They allocate nothing. */
+
+#define FCN_OP_IFFT    1   /* inverse FFT along tau (Eq. (antifourier)), 1/Nt applied */
+#define FCN_OP_NL      2   /* one nonlinear half step of length dz_half (Eq. (Anhalf)) */
+#define FCN_OP_NL2     4   /* a second nonlinear half step right after the first        */
+#define FCN_OP_FFT     8   /* forward FFT along tau (Sec. 3.1, first loop)             */
+#define FCN_OP_RHO    16   /* write rho (working precision, Nr*Nt) of the last half step */
+
+/* Row stage: for every row, in order: [IFFT] [NL] [NL2] [FFT].  rho may be
+ * NULL unless FCN_OP_RHO is set.  Errors: FCN_ERR_ARG, FCN_ERR_CUDA. */
+int fcn_op_rows(const fcn_grid *grid, const fcn_params *params, int32_t precision,
+                int32_t ops, double dz_half, void *field, void *rho, void *stream);
+
+/* Number of complex entries of the Crank-Nicolson factorisation table:
+ * Nr * (Nt/2 + 1). */
+int64_t fcn_cn_table_entries(const fcn_grid *grid);
+
+/* Fills `table` (fcn_cn_table_entries complex values, working precision)
+ * with 1/pivot_j of the Thomas factorisation of M_abc^q (Eq. (matrix)) for
+ * every radial index j and every |frequency| bin q = 0..Nt/2. */
+int fcn_op_cn_table(const fcn_grid *grid, const fcn_params *params, int32_t precision,
+                    double dz, void *table, void *stream);
+
+/* Column stage on a frequency-domain field (Sec. 3.1, second loop): for
+ * every q, A~_{.,q} <- (M_abc^q)^{-1} M_def^q A~_{.,q}, in place, using the
+ * table from fcn_op_cn_table for the same dz. */
+int fcn_op_cn(const fcn_grid *grid, const fcn_params *params, int32_t precision,
+              double dz, const void *table, void *field, void *stream);
+
+/* Library version string. */
+const char *fcn_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FCN_H */

@@ -1,0 +1,290 @@
+// col_kernel.cu -- the column stage of the FCN z-step: for every frequency
+// bin q the Crank-Nicolson system M_abc^q A~^{n+1} = M_def^q A~^n of Eq. (matrix)
+// (Ma & Lin, arXiv:1507.05988, Sec. 3.1, Eqs. (diff1)-(diff3), (bound),
+// (matrix1) and the coefficients after it; reading: c_j and f_j carry
+// (1 + 1/(2j)), the value Eqs. (diff2)-(diff3) give).
+//
+// With s = dz/(4 k0 dr^2) and delta_q = k'' omega_q^2 dz/4:
+//   row 0      : b = 1 + i(4s - delta), c = -4is ; e = 1 - i(4s - delta), f = 4is
+//   1..Nr-2    : a = -is lo_j, b = 1 + i(2s - delta), c = -is hi_j
+//                d =  is lo_j, e = 1 - i(2s - delta), f =  is hi_j
+//   row Nr-1   : b = 1, everything else 0 (A = 0 at r = R)
+// with lo_j = 1 - 1/(2j), hi_j = 1 + 1/(2j).
+//
+// The matrix depends on (j, |q|, dz) only, never on the field, so its Thomas
+// factorisation (the pivots) is computed once per dz by cn_table_kernel and
+// kept in HBM as 1/pivot_j for q = 0..Nt/2 (bins q and Nt-q share omega^2).
+// Given the pivots, the two Thomas sweeps are first-order linear recurrences
+//   y_j = alpha_j y_{j-1} + beta_j        (alpha = -a/piv, beta = rhs/piv)
+//   x_j = gamma_j x_{j+1} + y_j           (gamma = -c/piv)
+// i.e. compositions of affine maps, which the column kernel evaluates as a
+// chunked parallel scan: a thread owns L consecutive rows of one column
+// (values in registers), composes its chunk's map, the chunk maps of a
+// column are scanned with warp shuffles (one short pass over the warp
+// totals in shared memory), and each thread then replays its recurrence
+// from the exact carry.  The result equals the sequential Thomas
+// sweep up to rounding.
+//
+// Layout: the field is [Nr][Nt] with Nt contiguous.  A CTA takes C adjacent
+// columns (C complex = 32 B, one DRAM sector, at least) and all Nr rows, so
+// each row access of a warp covers whole sectors.  CTAs for the bins q and
+// Nt-q are launched next to each other so that the second reads the shared
+// pivot rows from L2.
+#include "fcn_device.cuh"
+
+namespace fcn {
+namespace {
+
+template <typename T>
+__device__ __forceinline__ cx<T> czero() { return mk(T(0), T(0)); }
+
+// 1/z in FP64
+__device__ __forceinline__ cx<double> crecip(cx<double> z) {
+    const double d = z.x * z.x + z.y * z.y;
+    return mk(z.x / d, -z.y / d);
+}
+
+// One thread per |q| = 0..Nt/2 runs the Thomas pivot recurrence down the
+// radial index in FP64: piv_j = b_j - a_j c_{j-1}/piv_{j-1}.
+template <typename T>
+__global__ void cn_table_kernel(TableArgs a, cx<T> *table) {
+    const int nq = a.nt / 2 + 1;
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nq) return;
+    const double delta = a.dk * double(q) * double(q);
+    const double s = a.s;
+    cx<double> cp = mk(0.0, 0.0);
+    for (int j = 0; j < a.nr; ++j) {
+        cx<double> b, aa, c;
+        if (j == 0) {
+            aa = mk(0.0, 0.0);
+            b = mk(1.0, 4.0 * s - delta);
+            c = mk(0.0, -4.0 * s);
+        } else if (j < a.nr - 1) {
+            aa = mk(0.0, -s * a.lo[j]);
+            b = mk(1.0, 2.0 * s - delta);
+            c = mk(0.0, -s * a.hi[j]);
+        } else {
+            aa = mk(0.0, 0.0);
+            b = mk(1.0, 0.0);
+            c = mk(0.0, 0.0);
+        }
+        const cx<double> den = b - cmul(aa, cp);
+        const cx<double> inv = crecip(den);
+        cp = cmul(c, inv);
+        table[(size_t)j * nq + q] = mk(T(inv.x), T(inv.y));
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ cx<T> shfl_up_cx(cx<T> v, int d) {
+    return mk(__shfl_up_sync(0xffffffffu, v.x, d), __shfl_up_sync(0xffffffffu, v.y, d));
+}
+template <typename T>
+__device__ __forceinline__ cx<T> shfl_down_cx(cx<T> v, int d) {
+    return mk(__shfl_down_sync(0xffffffffu, v.x, d), __shfl_down_sync(0xffffffffu, v.y, d));
+}
+
+// Value entering this thread's chunk when the chunk maps x -> A x + B of one
+// column are composed in chunk order (REV = false: from chunk 0, value 0
+// entering it) or in reverse chunk order (REV = true: from the last chunk).
+// Lanes of one column sit C apart in a warp, so the in-warp part is a
+// shuffle scan; warp totals are combined by one thread per column.
+template <typename T, bool REV>
+__device__ __forceinline__ cx<T> chunk_scan(cx<T> A, cx<T> B, int C, int col, cx<T> *smA,
+                                            cx<T> *smB, cx<T> *smC) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int cpw = 32 / C;
+    const int ciw = lane / C;
+    for (int d = 1; d < cpw; d <<= 1) {
+        const cx<T> Ao = REV ? shfl_down_cx(A, d * C) : shfl_up_cx(A, d * C);
+        const cx<T> Bo = REV ? shfl_down_cx(B, d * C) : shfl_up_cx(B, d * C);
+        const bool take = REV ? (ciw + d < cpw) : (ciw >= d);
+        if (take) {
+            B = cmul(A, Bo) + B;
+            A = cmul(A, Ao);
+        }
+    }
+    cx<T> Ae = REV ? shfl_down_cx(A, C) : shfl_up_cx(A, C);
+    cx<T> Be = REV ? shfl_down_cx(B, C) : shfl_up_cx(B, C);
+    if (REV ? (ciw == cpw - 1) : (ciw == 0)) {
+        Ae = mk(T(1), T(0));
+        Be = czero<T>();
+    }
+    const int nw = blockDim.x >> 5;
+    cx<T> wc = czero<T>();
+    if (nw > 1) {
+        if (REV ? (ciw == 0) : (ciw == cpw - 1)) {
+            smA[w * C + col] = A;
+            smB[w * C + col] = B;
+        }
+        __syncthreads();
+        if ((int)threadIdx.x < C) {
+            const int c0 = threadIdx.x;
+            cx<T> c = czero<T>();
+            if (!REV) {
+                for (int k = 0; k < nw; ++k) {
+                    smC[k * C + c0] = c;
+                    c = cmul(smA[k * C + c0], c) + smB[k * C + c0];
+                }
+            } else {
+                for (int k = nw - 1; k >= 0; --k) {
+                    smC[k * C + c0] = c;
+                    c = cmul(smA[k * C + c0], c) + smB[k * C + c0];
+                }
+            }
+        }
+        __syncthreads();
+        wc = smC[w * C + col];
+    }
+    return cmul(Ae, wc) + Be;
+}
+
+template <typename T, int L>
+__global__ void __launch_bounds__(512)
+cn_kernel(ColArgs<T> a, int C) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nwarp = blockDim.x >> 5;
+    cx<T> *smA = reinterpret_cast<cx<T> *>(smem_raw);
+    cx<T> *smB = smA + nwarp * C;
+    cx<T> *smC = smB + nwarp * C;
+
+    const int tid = threadIdx.x;
+    const int col = tid % C;
+    const int chunk = tid / C;
+    const int ngroups = a.nt / C;
+    const int b = blockIdx.x;
+    const int g = (b & 1) ? (ngroups - 1 - (b >> 1)) : (b >> 1);
+    const int q = g * C + col;
+    const int nt = a.nt, nr = a.nr;
+    const int nq = nt / 2 + 1;
+    const int qq = (q <= nt / 2) ? q : nt - q;
+    const T delta = a.dk * T(qq) * T(qq);
+    const T s = a.s;
+    const T g0 = T(4) * s - delta;   // row 0: e = 1 - i g0
+    const T g1 = T(2) * s - delta;   // rows 1..Nr-2
+    const int j0 = chunk * L;
+    cx<T> *colp = a.field + q;
+
+    cx<T> x[L + 2];
+#pragma unroll
+    for (int k = 0; k < L + 2; ++k) {
+        const int j = j0 - 1 + k;
+        x[k] = (j >= 0 && j < nr) ? colp[(size_t)j * nt] : czero<T>();
+    }
+    cx<T> inv[L];
+#pragma unroll
+    for (int k = 0; k < L; ++k) {
+        const int j = j0 + k;
+        inv[k] = (j < nr) ? ldg_cx(&a.invden[(size_t)j * nq + qq]) : czero<T>();
+    }
+
+    // forward sweep, pass 1: beta_j and the chunk map y_end = PA y_in + PB
+    cx<T> y[L];
+    cx<T> PA = mk(T(1), T(0)), PB = czero<T>();
+#pragma unroll
+    for (int k = 0; k < L; ++k) {
+        const int j = j0 + k;
+        if (j < nr) {
+            cx<T> rhs, alpha;
+            if (j == 0) {
+                const cx<T> w = mk(T(4) * s * x[k + 2].x - g0 * x[k + 1].x,
+                                   T(4) * s * x[k + 2].y - g0 * x[k + 1].y);
+                rhs = mk(x[k + 1].x - w.y, x[k + 1].y + w.x);
+                alpha = czero<T>();
+            } else if (j < nr - 1) {
+                const T sl = s * a.lo[j], sh = s * a.hi[j];
+                const cx<T> w = mk(sl * x[k].x + sh * x[k + 2].x - g1 * x[k + 1].x,
+                                   sl * x[k].y + sh * x[k + 2].y - g1 * x[k + 1].y);
+                rhs = mk(x[k + 1].x - w.y, x[k + 1].y + w.x);
+                alpha = cmul_i(inv[k], sl);
+            } else {
+                rhs = czero<T>();
+                alpha = czero<T>();
+            }
+            y[k] = cmul(rhs, inv[k]);
+            PB = cmul(alpha, PB) + y[k];
+            PA = cmul(alpha, PA);
+        } else {
+            y[k] = czero<T>();
+        }
+    }
+    // forward sweep, pass 2: exact y from the carry entering the chunk
+    {
+        cx<T> yp = chunk_scan<T, false>(PA, PB, C, col, smA, smB, smC);
+#pragma unroll
+        for (int k = 0; k < L; ++k) {
+            const int j = j0 + k;
+            if (j < nr) {
+                const cx<T> alpha = (j >= 1 && j < nr - 1) ? cmul_i(inv[k], s * a.lo[j]) : czero<T>();
+                y[k] = cmul(alpha, yp) + y[k];
+                yp = y[k];
+            }
+        }
+    }
+    // backward sweep, pass 1: chunk map x_first = QA x_next + QB
+    cx<T> QA = mk(T(1), T(0)), QB = czero<T>();
+#pragma unroll
+    for (int k = L - 1; k >= 0; --k) {
+        const int j = j0 + k;
+        if (j < nr) {
+            const cx<T> gamma = (j == 0) ? cmul_i(inv[k], T(4) * s)
+                              : (j < nr - 1) ? cmul_i(inv[k], s * a.hi[j]) : czero<T>();
+            QB = cmul(gamma, QB) + y[k];
+            QA = cmul(gamma, QA);
+        }
+    }
+    // backward sweep, pass 2 and store
+    {
+        cx<T> xn = chunk_scan<T, true>(QA, QB, C, col, smA, smB, smC);
+#pragma unroll
+        for (int k = L - 1; k >= 0; --k) {
+            const int j = j0 + k;
+            if (j < nr) {
+                const cx<T> gamma = (j == 0) ? cmul_i(inv[k], T(4) * s)
+                                  : (j < nr - 1) ? cmul_i(inv[k], s * a.hi[j]) : czero<T>();
+                xn = cmul(gamma, xn) + y[k];
+                colp[(size_t)j * nt] = xn;
+            }
+        }
+    }
+}
+
+template <typename T, int L>
+cudaError_t launch_cn_l(const ColArgs<T> &a, cudaStream_t st) {
+    constexpr int CMIN = 32 / int(sizeof(cx<T>));   // one 32-byte sector of columns
+    const int P = (a.nr + L - 1) / L;
+    int C = CMIN;
+    while (C * 2 * P <= 256 && C * 2 <= 32) C *= 2;
+    if (C > a.nt) C = a.nt;
+    // whole warps: chunks beyond P are empty (identity maps)
+    const int threads = ((C * P + 31) / 32) * 32;
+    if (threads > 512) return cudaErrorInvalidConfiguration;
+    const size_t smem = sizeof(cx<T>) * 3 * (size_t)(threads / 32) * C;
+    const int grid = a.nt / C;
+    cn_kernel<T, L><<<grid, threads, smem, st>>>(a, C);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_cn(const ColArgs<T> &a, cudaStream_t st) {
+    if constexpr (sizeof(T) == 4) return launch_cn_l<T, 16>(a, st);
+    else return launch_cn_l<T, 8>(a, st);
+}
+
+template <typename T>
+cudaError_t launch_cn_table(const TableArgs &a, cx<T> *table, cudaStream_t st) {
+    const int nq = a.nt / 2 + 1;
+    const int threads = 64;
+    cn_table_kernel<T><<<(nq + threads - 1) / threads, threads, 0, st>>>(a, table);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_cn<float>(const ColArgs<float> &, cudaStream_t);
+template cudaError_t launch_cn<double>(const ColArgs<double> &, cudaStream_t);
+template cudaError_t launch_cn_table<float>(const TableArgs &, cx<float> *, cudaStream_t);
+template cudaError_t launch_cn_table<double>(const TableArgs &, cx<double> *, cudaStream_t);
+
+}  // namespace fcn

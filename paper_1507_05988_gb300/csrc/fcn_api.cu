@@ -1,0 +1,936 @@
+// fcn_api.cu -- C-ABI of the GB300 FCN z-step library (declared in
+// include/fcn.h).  Host-side orchestration only: argument checks, physical
+// constants, device buffers, the pivot-table cache, CUDA-graph capture of
+// the z-loop and the step-doubling controller.  Every arithmetic step of
+// the z-step runs in the kernels of row_kernel.cu, col_kernel.cu and
+// reduce.cu.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/fcn.h"
+#include "fcn_device.cuh"
+
+using namespace fcn;
+
+namespace {
+
+// CODATA 2018 (SI)
+constexpr double kC = 299792458.0;
+constexpr double kHbar = 1.054571817e-34;
+constexpr double kEps0 = 8.8541878128e-12;
+constexpr double kMe = 9.1093837015e-31;
+constexpr double kQe = 1.602176634e-19;
+constexpr double kPi = 3.14159265358979323846;
+// Intensity scale of the nonlinear stage: a power of two, so Ihat = I/I_s is
+// exact; 2^53 W/m^2 ~ 9e15 keeps Ihat^K inside FP32 range for I up to ~5e20.
+constexpr double kIs = 9007199254740992.0;
+
+std::string g_create_error = "no error";
+std::mutex g_mu;
+
+bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+int check_grid_params(int prec, const fcn_grid *g, const fcn_params *p, std::string *why) {
+    if (!g || !p) { *why = "null grid or params"; return FCN_ERR_ARG; }
+    if (prec != FCN_FP64 && prec != FCN_FP32_MIXED) { *why = "unknown precision"; return FCN_ERR_ARG; }
+    if (!is_pow2(g->nt) || g->nt < 2) { *why = "nt must be a power of two >= 2"; return FCN_ERR_ARG; }
+    if (g->nt > 8192) { *why = "nt > 8192 is not supported"; return FCN_ERR_UNSUPPORTED; }
+    if (g->nr < 3) { *why = "nr must be >= 3"; return FCN_ERR_ARG; }
+    if (g->nr > 2048) { *why = "nr > 2048 is not supported"; return FCN_ERR_UNSUPPORTED; }
+    if (!(g->r_max > 0) || !std::isfinite(g->r_max)) { *why = "r_max must be > 0"; return FCN_ERR_ARG; }
+    if (!(g->t_window > 0) || !std::isfinite(g->t_window)) { *why = "t_window must be > 0"; return FCN_ERR_ARG; }
+    if (!(p->lambda0 > 0) || !(p->n0 > 0)) { *why = "lambda0 and n0 must be > 0"; return FCN_ERR_ARG; }
+    if (p->K < 1 || p->K > 16) { *why = "K must be in 1..16"; return FCN_ERR_ARG; }
+    if (p->flags & ~63u) { *why = "unknown physics flag"; return FCN_ERR_ARG; }
+    if (!(p->sigma_k >= 0) || !(p->rho_nt >= 0) || !std::isfinite(p->k2)) {
+        *why = "sigma_k, rho_nt must be >= 0 and k2 finite"; return FCN_ERR_ARG;
+    }
+    for (int j = 0; j < 4; ++j)
+        if (!std::isfinite(p->n2j[j])) { *why = "n2j must be finite"; return FCN_ERR_ARG; }
+    return FCN_OK;
+}
+
+// Derived constants of one pulse (host, FP64).
+struct Consts {
+    double k0, omega0, rho_c, beta_k, dr, dtau, domega;
+};
+
+Consts derive(const fcn_grid &g, const fcn_params &p) {
+    Consts c;
+    c.k0 = 2.0 * kPi * p.n0 / p.lambda0;
+    c.omega0 = 2.0 * kPi * kC / p.lambda0;
+    c.rho_c = kEps0 * kMe * c.omega0 * c.omega0 / (kQe * kQe);
+    c.beta_k = double(p.K) * kHbar * c.omega0 * p.sigma_k * p.rho_nt;
+    c.dr = g.r_max / double(g.nr - 1);
+    c.dtau = g.t_window / double(g.nt);
+    c.domega = 2.0 * kPi / (double(g.nt) * c.dtau);
+    return c;
+}
+
+template <typename T>
+NLCoef<T> nl_coef(const fcn_grid &g, const fcn_params &p, double h) {
+    const Consts c = derive(g, p);
+    NLCoef<T> n;
+    n.h = T(h);
+    double isj = kIs;
+    for (int j = 0; j < 4; ++j) {
+        n.kerr[j] = T((c.k0 / p.n0) * p.n2j[j] * isj);
+        isj *= kIs;
+    }
+    n.plasma = T(c.k0 / (2.0 * p.n0 * p.n0 * c.rho_c) * p.rho_nt);
+    n.loss = T(0.5 * c.beta_k * std::pow(kIs, p.K - 1));
+    n.sdt = T(p.sigma_k * c.dtau * std::pow(kIs, p.K));
+    n.inv_is = T(1.0 / kIs);
+    n.inv_nt = T(1.0 / double(g.nt));
+    n.rho_nt = T(p.rho_nt);
+    n.K = p.K;
+    n.flags = p.flags;
+    return n;
+}
+
+void cn_coefs(const fcn_grid &g, const fcn_params &p, double dz, double *s, double *dk) {
+    const Consts c = derive(g, p);
+    *s = (p.flags & FCN_DIFFRACTION) ? dz / (4.0 * c.k0 * c.dr * c.dr) : 0.0;
+    *dk = (p.flags & FCN_DISPERSION) ? p.k2 * dz / 4.0 * c.domega * c.domega : 0.0;
+}
+
+// ---- process-wide constant tables (twiddles, radial ratios) ----
+struct ConstTables {
+    std::map<std::pair<int, int>, void *> tw;      // (prec, nt) -> cx<T>[nt]
+    std::map<std::pair<int, int>, void *> lohi;    // (prec, nr) -> T[2*nr]
+    std::map<int, double *> lohi64;                // nr -> double[2*nr]
+};
+ConstTables g_tables;
+
+template <typename T>
+cudaError_t get_twiddles(int nt, const cx<T> **out) {
+    const int prec = sizeof(T) == 8 ? FCN_FP64 : FCN_FP32_MIXED;
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto key = std::make_pair(prec, nt);
+    auto it = g_tables.tw.find(key);
+    if (it != g_tables.tw.end()) { *out = (const cx<T> *)it->second; return cudaSuccess; }
+    std::vector<cx<T>> h(nt);
+    for (int m = 0; m < nt; ++m) {
+        const long double ang = -2.0L * 3.14159265358979323846264338327950288L * (long double)m /
+                                (long double)nt;
+        h[m] = mk(T(cosl(ang)), T(sinl(ang)));
+    }
+    void *d = nullptr;
+    cudaError_t e = cudaMalloc(&d, sizeof(cx<T>) * nt);
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpy(d, h.data(), sizeof(cx<T>) * nt, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { cudaFree(d); return e; }
+    g_tables.tw[key] = d;
+    *out = (const cx<T> *)d;
+    return cudaSuccess;
+}
+
+// lo_j = 1 - 1/(2j), hi_j = 1 + 1/(2j) (0 at j = 0), same FP64 expression as
+// the coefficients of Eq. (matrix1).
+template <typename T>
+cudaError_t get_lohi(int nr, const T **lo, const T **hi, const double **lo64, const double **hi64) {
+    const int prec = sizeof(T) == 8 ? FCN_FP64 : FCN_FP32_MIXED;
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto key = std::make_pair(prec, nr);
+    std::vector<double> h(2 * nr, 0.0);
+    for (int j = 1; j < nr; ++j) {
+        h[j] = 1.0 - 1.0 / (2.0 * j);
+        h[nr + j] = 1.0 + 1.0 / (2.0 * j);
+    }
+    cudaError_t e;
+    auto it = g_tables.lohi.find(key);
+    if (it == g_tables.lohi.end()) {
+        std::vector<T> ht(2 * nr);
+        for (int i = 0; i < 2 * nr; ++i) ht[i] = T(h[i]);
+        void *d = nullptr;
+        if ((e = cudaMalloc(&d, sizeof(T) * 2 * nr)) != cudaSuccess) return e;
+        if ((e = cudaMemcpy(d, ht.data(), sizeof(T) * 2 * nr, cudaMemcpyHostToDevice)) != cudaSuccess) {
+            cudaFree(d);
+            return e;
+        }
+        it = g_tables.lohi.emplace(key, d).first;
+    }
+    auto it64 = g_tables.lohi64.find(nr);
+    if (it64 == g_tables.lohi64.end()) {
+        double *d = nullptr;
+        if ((e = cudaMalloc(&d, sizeof(double) * 2 * nr)) != cudaSuccess) return e;
+        if ((e = cudaMemcpy(d, h.data(), sizeof(double) * 2 * nr, cudaMemcpyHostToDevice)) != cudaSuccess) {
+            cudaFree(d);
+            return e;
+        }
+        it64 = g_tables.lohi64.emplace(nr, d).first;
+    }
+    *lo = (const T *)it->second;
+    *hi = (const T *)it->second + nr;
+    *lo64 = it64->second;
+    *hi64 = it64->second + nr;
+    return cudaSuccess;
+}
+
+size_t csize(int prec) { return prec == FCN_FP64 ? 16 : 8; }
+size_t rsize(int prec) { return prec == FCN_FP64 ? 8 : 4; }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------
+
+struct Pulse {
+    fcn_grid g;
+    fcn_params p;
+    void *field = nullptr;     // current state (time domain between calls)
+    void *work1 = nullptr;     // adaptive: one-step result
+    void *work2 = nullptr;     // adaptive: two-half-step result
+    void *rho = nullptr;       // T[nr*nt]
+    double *stats = nullptr;   // [nr*NSTAT]
+    double *red = nullptr;     // [16] reduction outputs
+    double *rows = nullptr;    // [2*nr] row partials
+    double *stage = nullptr;   // double staging [2*nr*nt] for host transfers
+    const void *tw = nullptr;
+    const void *lo = nullptr, *hi = nullptr;
+    const double *lo64 = nullptr, *hi64 = nullptr;
+    std::map<uint64_t, void *> tables;   // dz bits -> pivot table
+    std::vector<uint64_t> table_lru;
+    double z = 0.0, dz_next = 0.0;
+    int64_t steps = 0, rejected = 0;
+    bool has_field = false;
+    int64_t points() const { return (int64_t)g.nr * g.nt; }
+};
+
+struct GraphKey {
+    int kind;        // 0 head, 1 mid x8, 2 mid x1, 3 tail
+    uint64_t dz;
+    bool operator<(const GraphKey &o) const { return kind != o.kind ? kind < o.kind : dz < o.dz; }
+};
+
+struct fcn_ctx {
+    int prec = FCN_FP64;
+    cudaStream_t st = nullptr;        // user stream (launch target)
+    cudaStream_t cap = nullptr;       // internal stream used for graph capture
+    std::vector<Pulse> pulses;
+    std::map<GraphKey, cudaGraphExec_t> graphs;
+    std::string err = "no error";
+    double *host_red = nullptr;       // pinned [16]
+    // kernel timing (fcn_profile_enable): one event pair per launch, by kind
+    bool profiling = false;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof_events;
+    double prof_ms[FCN_PROF_KINDS] = {0};
+    int64_t prof_n[FCN_PROF_KINDS] = {0};
+    float *mlp = nullptr;             // device FP32 master weights (FCN_MLP_NPARAM)
+    bool has_mlp = false;
+};
+
+namespace {
+
+int fail(fcn_ctx *c, int code, const std::string &msg) {
+    if (c) c->err = msg;
+    else g_create_error = msg;
+    return code;
+}
+
+int cuda_fail(fcn_ctx *c, cudaError_t e, const char *what) {
+    return fail(c, FCN_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                          \
+    do {                                                        \
+        cudaError_t e_ = (call);                                \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, what); \
+    } while (0)
+
+uint64_t dz_key(double dz) {
+    uint64_t k;
+    std::memcpy(&k, &dz, sizeof k);
+    return k;
+}
+
+template <typename T>
+int ensure_table(fcn_ctx *ctx, Pulse &pu, double dz, const cx<T> **out) {
+    const uint64_t key = dz_key(dz);
+    auto it = pu.tables.find(key);
+    if (it != pu.tables.end()) { *out = (const cx<T> *)it->second; return FCN_OK; }
+    // small LRU: at most 8 tables per pulse; graphs that captured an evicted
+    // table are dropped with it
+    if (pu.tables.size() >= 8) {
+        const uint64_t old = pu.table_lru.front();
+        pu.table_lru.erase(pu.table_lru.begin());
+        CK(cudaStreamSynchronize(ctx->st), "sync before table eviction");
+        for (int kind = 0; kind < 4; ++kind) {
+            auto g = ctx->graphs.find(GraphKey{kind, old});
+            if (g != ctx->graphs.end()) {
+                cudaGraphExecDestroy(g->second);
+                ctx->graphs.erase(g);
+            }
+        }
+        cudaFree(pu.tables[old]);
+        pu.tables.erase(old);
+    }
+    const size_t n = (size_t)pu.g.nr * (pu.g.nt / 2 + 1);
+    void *d = nullptr;
+    CK(cudaMalloc(&d, sizeof(cx<T>) * n), "pivot table allocation");
+    TableArgs ta;
+    ta.nr = pu.g.nr;
+    ta.nt = pu.g.nt;
+    cn_coefs(pu.g, pu.p, dz, &ta.s, &ta.dk);
+    ta.lo = pu.lo64;
+    ta.hi = pu.hi64;
+    CK(launch_cn_table<T>(ta, (cx<T> *)d, ctx->st), "pivot table kernel");
+    pu.tables[key] = d;
+    pu.table_lru.push_back(key);
+    *out = (const cx<T> *)d;
+    return FCN_OK;
+}
+
+template <typename T>
+RowArgs<T> row_args(Pulse &pu, void *field, int ops, double dz) {
+    RowArgs<T> a;
+    a.field = (cx<T> *)field;
+    a.tw = (const cx<T> *)pu.tw;
+    a.rho = (T *)pu.rho;
+    a.stats = pu.stats;
+    a.nr = pu.g.nr;
+    a.ops = ops;
+    a.nl = nl_coef<T>(pu.g, pu.p, 0.5 * dz);
+    return a;
+}
+
+template <typename T>
+ColArgs<T> col_args(Pulse &pu, void *field, const cx<T> *table, double dz) {
+    ColArgs<T> a;
+    a.field = (cx<T> *)field;
+    a.invden = table;
+    a.lo = (const T *)pu.lo;
+    a.hi = (const T *)pu.hi;
+    a.nr = pu.g.nr;
+    a.nt = pu.g.nt;
+    double s, dk;
+    cn_coefs(pu.g, pu.p, dz, &s, &dk);
+    a.s = T(s);
+    a.dk = T(dk);
+    return a;
+}
+
+// Records an event pair around one launch when profiling is on.
+template <typename F>
+cudaError_t timed(fcn_ctx *ctx, int kind, cudaStream_t st, F &&launch) {
+    if (!ctx->profiling) return launch();
+    cudaEvent_t e0, e1;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaEventCreate(&e1)) != cudaSuccess) { cudaEventDestroy(e0); return e; }
+    cudaEventRecord(e0, st);
+    e = launch();
+    cudaEventRecord(e1, st);
+    ctx->prof_events.push_back({kind, {e0, e1}});
+    return e;
+}
+
+void profile_collect(fcn_ctx *ctx) {
+    for (auto &pe : ctx->prof_events) {
+        float ms = 0.f;
+        cudaEventSynchronize(pe.second.second);
+        if (cudaEventElapsedTime(&ms, pe.second.first, pe.second.second) == cudaSuccess) {
+            ctx->prof_ms[pe.first] += ms;
+            ctx->prof_n[pe.first] += 1;
+        }
+        cudaEventDestroy(pe.second.first);
+        cudaEventDestroy(pe.second.second);
+    }
+    ctx->prof_events.clear();
+}
+
+constexpr int OPS_HEAD = OP_NL | OP_FFT;
+constexpr int OPS_MID = OP_IFFT | OP_NL | OP_NL2 | OP_FFT;
+constexpr int OPS_TAIL = OP_IFFT | OP_NL | OP_RHO | OP_STATS;
+
+// Launches `kind` for every pulse on stream st: 0 head, 1 eight (col, mid)
+// pairs, 2 one (col, mid) pair, 3 (col, tail).
+template <typename T>
+cudaError_t launch_block(fcn_ctx *ctx, int kind, double dz, cudaStream_t st,
+                         const std::vector<const cx<T> *> &tabs,
+                         const std::vector<void *> *fields = nullptr) {
+    cudaError_t e = cudaSuccess;
+    for (size_t i = 0; i < ctx->pulses.size() && e == cudaSuccess; ++i) {
+        Pulse &pu = ctx->pulses[i];
+        void *f = fields ? (*fields)[i] : pu.field;
+        auto rows = [&](int ops, int pk) {
+            return timed(ctx, pk, st, [&] { return launch_rows<T>(row_args<T>(pu, f, ops, dz), pu.g.nt, st); });
+        };
+        auto col = [&] {
+            return timed(ctx, FCN_PROF_COLUMN, st, [&] { return launch_cn<T>(col_args<T>(pu, f, tabs[i], dz), st); });
+        };
+        if (kind == 0) {
+            e = rows(OPS_HEAD, FCN_PROF_ROW_HEAD);
+        } else if (kind == 1 || kind == 2) {
+            const int reps = kind == 1 ? 8 : 1;
+            for (int r = 0; r < reps && e == cudaSuccess; ++r) {
+                e = col();
+                if (e == cudaSuccess) e = rows(OPS_MID, FCN_PROF_ROW_MID);
+            }
+        } else {
+            e = col();
+            if (e == cudaSuccess) e = rows(OPS_TAIL, FCN_PROF_ROW_TAIL);
+        }
+    }
+    return e;
+}
+
+template <typename T>
+int run_block(fcn_ctx *ctx, int kind, double dz, const std::vector<const cx<T> *> &tabs,
+              bool use_graph) {
+    if (!use_graph || ctx->profiling) {
+        CK(launch_block<T>(ctx, kind, dz, ctx->st, tabs), "kernel launch");
+        return FCN_OK;
+    }
+    GraphKey key{kind, dz_key(dz)};
+    auto it = ctx->graphs.find(key);
+    if (it == ctx->graphs.end()) {
+        // capture on the internal stream (the legacy default stream cannot
+        // be captured), then replay on the caller's stream
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
+        cudaError_t le = launch_block<T>(ctx, kind, dz, ctx->cap, tabs);
+        cudaError_t ce = cudaStreamEndCapture(ctx->cap, &g);
+        if (le != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_fail(ctx, le, "captured launch"); }
+        if (ce != cudaSuccess) return cuda_fail(ctx, ce, "end capture");
+        cudaGraphExec_t ex = nullptr;
+        cudaError_t ie = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        if (ie != cudaSuccess) return cuda_fail(ctx, ie, "graph instantiate");
+        it = ctx->graphs.emplace(key, ex).first;
+    }
+    CK(cudaGraphLaunch(it->second, ctx->st), "graph launch");
+    return FCN_OK;
+}
+
+template <typename T>
+int step_impl(fcn_ctx *ctx, double dz, int64_t n, bool use_graph) {
+    if (!(dz > 0) || !std::isfinite(dz)) return fail(ctx, FCN_ERR_ARG, "dz must be > 0 and finite");
+    if (n < 0) return fail(ctx, FCN_ERR_ARG, "n must be >= 0");
+    for (auto &pu : ctx->pulses)
+        if (!pu.has_field) return fail(ctx, FCN_ERR_STATE, "fcn_set_field has not been called");
+    if (n == 0) return FCN_OK;
+    std::vector<const cx<T> *> tabs(ctx->pulses.size());
+    for (size_t i = 0; i < ctx->pulses.size(); ++i) {
+        int rc = ensure_table<T>(ctx, ctx->pulses[i], dz, &tabs[i]);
+        if (rc) return rc;
+    }
+    int rc = run_block<T>(ctx, 0, dz, tabs, use_graph);
+    int64_t rem = n - 1;
+    while (rc == FCN_OK && rem >= 8) { rc = run_block<T>(ctx, 1, dz, tabs, use_graph); rem -= 8; }
+    while (rc == FCN_OK && rem >= 1) { rc = run_block<T>(ctx, 2, dz, tabs, use_graph); rem -= 1; }
+    if (rc == FCN_OK) rc = run_block<T>(ctx, 3, dz, tabs, use_graph);
+    if (rc) return rc;
+    for (auto &pu : ctx->pulses) {
+        pu.z += dz * double(n);
+        pu.steps += n;
+    }
+    return FCN_OK;
+}
+
+// One Strang step of length h (or two of h/2) on a work buffer, direct launches.
+template <typename T>
+int substeps(fcn_ctx *ctx, Pulse &pu, void *f, double h, int count) {
+    const cx<T> *tab = nullptr;
+    int rc = ensure_table<T>(ctx, pu, h, &tab);
+    if (rc) return rc;
+    CK(launch_rows<T>(row_args<T>(pu, f, OPS_HEAD, h), pu.g.nt, ctx->st), "head");
+    for (int i = 0; i < count; ++i) {
+        CK(launch_cn<T>(col_args<T>(pu, f, tab, h), ctx->st), "column");
+        const int ops = (i + 1 < count) ? OPS_MID : OPS_TAIL;
+        CK(launch_rows<T>(row_args<T>(pu, f, ops, h), pu.g.nt, ctx->st), "row");
+    }
+    return FCN_OK;
+}
+
+template <typename T>
+int diag_impl(fcn_ctx *ctx, Pulse &pu, fcn_diag *out) {
+    RowArgs<T> a = row_args<T>(pu, pu.field, OP_STATS | OP_FFT | OP_SPEC | OP_NOSTORE, 0.0);
+    CK(launch_rows<T>(a, pu.g.nt, ctx->st), "diagnostics row pass");
+    CK(launch_reduce_stats(pu.stats, pu.g.nr, pu.red, ctx->st), "diagnostics reduction");
+    CK(cudaMemcpyAsync(ctx->host_red, pu.red, sizeof(double) * 8, cudaMemcpyDeviceToHost, ctx->st),
+       "diagnostics copy");
+    CK(cudaStreamSynchronize(ctx->st), "diagnostics sync");
+    const double *r = ctx->host_red;
+    const Consts c = derive(pu.g, pu.p);
+    std::memset(out, 0, sizeof(*out));
+    out->z = pu.z;
+    out->energy = 2.0 * kPi * c.dr * c.dr * c.dtau * r[0];
+    out->peak_intensity = r[1];
+    out->peak_rho = r[2] * pu.p.rho_nt;
+    out->onaxis_peak = r[3];
+    if (r[4] > 0) {
+        const double mean = r[5] / r[4];
+        const double var = r[6] / r[4] - mean * mean;
+        out->spectral_rms = var > 0 ? std::sqrt(var) * c.domega : 0.0;
+    }
+    out->steps = pu.steps;
+    out->rejected = pu.rejected;
+    out->nonfinite = (r[7] > 0 || !std::isfinite(r[0])) ? 1 : 0;
+    return out->nonfinite ? fail(ctx, FCN_ERR_NONFINITE, "field holds NaN or Inf") : FCN_OK;
+}
+
+template <typename T>
+int propagate_impl(fcn_ctx *ctx, double z_end, double dz0, double rtol, double dz_min,
+                   int max_reject, int controller, fcn_stats *out) {
+    if (ctx->pulses.size() != 1) return fail(ctx, FCN_ERR_UNSUPPORTED, "adaptive propagation needs a single-pulse context");
+    Pulse &pu = ctx->pulses[0];
+    if (!pu.has_field) return fail(ctx, FCN_ERR_STATE, "fcn_set_field has not been called");
+    if (!(dz0 > 0) || !std::isfinite(dz0) || !(rtol > 0) || !std::isfinite(z_end) || !(dz_min > 0))
+        return fail(ctx, FCN_ERR_ARG, "bad adaptive arguments");
+    if (controller != 0) return fail(ctx, FCN_ERR_UNSUPPORTED, "controller not available");
+    const size_t bytes = csize(ctx->prec) * pu.points();
+    if (!pu.work1) CK(cudaMalloc(&pu.work1, bytes), "work buffer");
+    if (!pu.work2) CK(cudaMalloc(&pu.work2, bytes), "work buffer");
+    fcn_stats s;
+    std::memset(&s, 0, sizeof s);
+    double dz = dz0;
+    int consecutive = 0;
+    int status = FCN_OK;
+    while (pu.z < z_end) {
+        double h = dz;
+        bool last = false;
+        if (pu.z + h >= z_end) { h = z_end - pu.z; last = true; }
+        CK(cudaMemcpyAsync(pu.work1, pu.field, bytes, cudaMemcpyDeviceToDevice, ctx->st), "copy");
+        CK(cudaMemcpyAsync(pu.work2, pu.field, bytes, cudaMemcpyDeviceToDevice, ctx->st), "copy");
+        int rc = substeps<T>(ctx, pu, pu.work1, h, 1);
+        if (!rc) rc = substeps<T>(ctx, pu, pu.work2, 0.5 * h, 2);
+        if (rc) return rc;
+        CK(launch_diff_norm<T>((const cx<T> *)pu.work1, (const cx<T> *)pu.work2, pu.g.nr, pu.g.nt,
+                               pu.rows, pu.red, ctx->st), "error norm");
+        CK(cudaMemcpyAsync(ctx->host_red, pu.red, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->st),
+           "norm copy");
+        CK(cudaStreamSynchronize(ctx->st), "norm sync");
+        const double err = ctx->host_red[1] > 0 ? std::sqrt(ctx->host_red[0] / ctx->host_red[1])
+                                                : std::sqrt(ctx->host_red[0]);
+        s.substeps += 3;
+        s.last_err = err;
+        if (!std::isfinite(err)) { status = fail(ctx, FCN_ERR_NONFINITE, "non-finite step-doubling error"); break; }
+        double fac = err > 0 ? 0.9 * std::cbrt(rtol / err) : 2.0;
+        fac = fac < 0.2 ? 0.2 : (fac > 2.0 ? 2.0 : fac);
+        if (err <= rtol) {
+            std::swap(pu.field, pu.work2);
+            pu.z = last ? z_end : pu.z + h;
+            pu.steps++;
+            s.accepted++;
+            consecutive = 0;
+            dz = last ? dz : h * fac;
+        } else {
+            pu.rejected++;
+            s.rejected++;
+            consecutive++;
+            dz = h * fac;
+        }
+        if (dz < dz_min || consecutive > max_reject) {
+            status = fail(ctx, FCN_ERR_STEP_UNDERFLOW, "dz underflow or too many rejections");
+            break;
+        }
+    }
+    pu.dz_next = dz;
+    s.z = pu.z;
+    s.dz_next = dz;
+    if (out) *out = s;
+    return status;
+}
+
+Pulse *get_pulse(fcn_ctx *ctx, int pulse) {
+    if (!ctx || pulse < 0 || pulse >= (int)ctx->pulses.size()) return nullptr;
+    return &ctx->pulses[pulse];
+}
+
+int create_impl(int n, const fcn_grid *grids, const fcn_params *params, int prec, void *stream,
+                fcn_ctx **out) {
+    if (!out) return fail(nullptr, FCN_ERR_ARG, "out is null");
+    *out = nullptr;
+    if (n < 1 || !grids || !params) return fail(nullptr, FCN_ERR_ARG, "need n >= 1 grids and params");
+    for (int i = 0; i < n; ++i) {
+        std::string why;
+        int rc = check_grid_params(prec, &grids[i], &params[i], &why);
+        if (rc) return fail(nullptr, rc, "pulse " + std::to_string(i) + ": " + why);
+    }
+    fcn_ctx *ctx = new fcn_ctx();
+    ctx->prec = prec;
+    ctx->st = (cudaStream_t)stream;
+    ctx->pulses.resize(n);
+    int rc = FCN_OK;
+    auto bail = [&](int code) {
+        g_create_error = ctx->err;
+        fcn_destroy(ctx);
+        return code;
+    };
+    cudaError_t e = cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { cuda_fail(ctx, e, "stream"); return bail(FCN_ERR_CUDA); }
+    e = cudaMallocHost(&ctx->host_red, 16 * sizeof(double));
+    if (e != cudaSuccess) { cuda_fail(ctx, e, "pinned buffer"); return bail(FCN_ERR_NOMEM); }
+    for (int i = 0; i < n && rc == FCN_OK; ++i) {
+        Pulse &pu = ctx->pulses[i];
+        pu.g = grids[i];
+        pu.p = params[i];
+        const size_t np = (size_t)pu.points();
+        if ((e = cudaMalloc(&pu.field, csize(prec) * np)) != cudaSuccess ||
+            (e = cudaMalloc(&pu.rho, rsize(prec) * np)) != cudaSuccess ||
+            (e = cudaMalloc(&pu.stats, sizeof(double) * NSTAT * pu.g.nr)) != cudaSuccess ||
+            (e = cudaMalloc(&pu.red, sizeof(double) * 16)) != cudaSuccess ||
+            (e = cudaMalloc(&pu.rows, sizeof(double) * 2 * pu.g.nr)) != cudaSuccess) {
+            cuda_fail(ctx, e, "device allocation");
+            return bail(FCN_ERR_NOMEM);
+        }
+        cudaMemset(pu.field, 0, csize(prec) * np);
+        cudaMemset(pu.rho, 0, rsize(prec) * np);
+        cudaMemset(pu.stats, 0, sizeof(double) * NSTAT * pu.g.nr);
+        if (prec == FCN_FP64) {
+            const cx<double> *tw;
+            const double *lo, *hi;
+            if ((e = get_twiddles<double>(pu.g.nt, &tw)) != cudaSuccess ||
+                (e = get_lohi<double>(pu.g.nr, &lo, &hi, &pu.lo64, &pu.hi64)) != cudaSuccess) {
+                cuda_fail(ctx, e, "constant tables");
+                return bail(FCN_ERR_CUDA);
+            }
+            pu.tw = tw; pu.lo = lo; pu.hi = hi;
+            if ((e = prepare_rows<double>(pu.g.nt)) != cudaSuccess) {
+                cuda_fail(ctx, e, "row kernel attributes");
+                return bail(FCN_ERR_CUDA);
+            }
+        } else {
+            const cx<float> *tw;
+            const float *lo, *hi;
+            if ((e = get_twiddles<float>(pu.g.nt, &tw)) != cudaSuccess ||
+                (e = get_lohi<float>(pu.g.nr, &lo, &hi, &pu.lo64, &pu.hi64)) != cudaSuccess) {
+                cuda_fail(ctx, e, "constant tables");
+                return bail(FCN_ERR_CUDA);
+            }
+            pu.tw = tw; pu.lo = lo; pu.hi = hi;
+            if ((e = prepare_rows<float>(pu.g.nt)) != cudaSuccess) {
+                cuda_fail(ctx, e, "row kernel attributes");
+                return bail(FCN_ERR_CUDA);
+            }
+        }
+    }
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) { cuda_fail(ctx, e, "init sync"); return bail(FCN_ERR_CUDA); }
+    *out = ctx;
+    return FCN_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// exported C-ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char *fcn_version(void) { return "fcn-gb300 0.1 (sm_103a)"; }
+
+int fcn_create(const fcn_grid *grid, const fcn_params *params, int32_t precision, void *stream,
+               fcn_ctx **out) {
+    return create_impl(1, grid, params, precision, stream, out);
+}
+
+int fcn_create_batch(int32_t n, const fcn_grid *grids, const fcn_params *params, int32_t precision,
+                     void *stream, fcn_ctx **out) {
+    return create_impl(n, grids, params, precision, stream, out);
+}
+
+void fcn_destroy(fcn_ctx *ctx) {
+    if (!ctx) return;
+    if (ctx->st) cudaStreamSynchronize(ctx->st);
+    cudaDeviceSynchronize();
+    for (auto &kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
+    profile_collect(ctx);
+    for (auto &pu : ctx->pulses) {
+        cudaFree(pu.field);
+        cudaFree(pu.work1);
+        cudaFree(pu.work2);
+        cudaFree(pu.rho);
+        cudaFree(pu.stats);
+        cudaFree(pu.red);
+        cudaFree(pu.rows);
+        cudaFree(pu.stage);
+        for (auto &kv : pu.tables) cudaFree(kv.second);
+    }
+    if (ctx->mlp) cudaFree(ctx->mlp);
+    if (ctx->host_red) cudaFreeHost(ctx->host_red);
+    if (ctx->cap) cudaStreamDestroy(ctx->cap);
+    delete ctx;
+}
+
+const char *fcn_last_error(const fcn_ctx *ctx) {
+    return ctx ? ctx->err.c_str() : g_create_error.c_str();
+}
+
+int fcn_set_stream(fcn_ctx *ctx, void *stream) {
+    if (!ctx) return FCN_ERR_ARG;
+    ctx->st = (cudaStream_t)stream;
+    return FCN_OK;
+}
+
+int fcn_set_field(fcn_ctx *ctx, int32_t pulse, const double *host) {
+    Pulse *pu = get_pulse(ctx, pulse);
+    if (!pu || !host) return fail(ctx, FCN_ERR_ARG, "bad pulse index or null buffer");
+    const size_t np = (size_t)pu->points();
+    if (ctx->prec == FCN_FP64) {
+        CK(cudaMemcpyAsync(pu->field, host, 16 * np, cudaMemcpyHostToDevice, ctx->st), "H2D field");
+    } else {
+        if (!pu->stage) CK(cudaMalloc(&pu->stage, 16 * np), "staging buffer");
+        CK(cudaMemcpyAsync(pu->stage, host, 16 * np, cudaMemcpyHostToDevice, ctx->st), "H2D field");
+        CK(launch_narrow<float>(pu->stage, (cx<float> *)pu->field, (int64_t)np, ctx->st), "narrow");
+    }
+    CK(cudaMemsetAsync(pu->stats, 0, sizeof(double) * NSTAT * pu->g.nr, ctx->st), "reset stats");
+    CK(cudaMemsetAsync(pu->rho, 0, rsize(ctx->prec) * np, ctx->st), "reset rho");
+    pu->z = 0.0;
+    pu->steps = pu->rejected = 0;
+    pu->dz_next = 0.0;
+    pu->has_field = true;
+    return FCN_OK;
+}
+
+int fcn_set_field_device(fcn_ctx *ctx, int32_t pulse, const void *dev) {
+    Pulse *pu = get_pulse(ctx, pulse);
+    if (!pu || !dev) return fail(ctx, FCN_ERR_ARG, "bad pulse index or null buffer");
+    const size_t np = (size_t)pu->points();
+    CK(cudaMemcpyAsync(pu->field, dev, csize(ctx->prec) * np, cudaMemcpyDeviceToDevice, ctx->st), "D2D field");
+    CK(cudaMemsetAsync(pu->stats, 0, sizeof(double) * NSTAT * pu->g.nr, ctx->st), "reset stats");
+    CK(cudaMemsetAsync(pu->rho, 0, rsize(ctx->prec) * np, ctx->st), "reset rho");
+    pu->z = 0.0;
+    pu->steps = pu->rejected = 0;
+    pu->has_field = true;
+    return FCN_OK;
+}
+
+int fcn_get_field(fcn_ctx *ctx, int32_t pulse, double *host) {
+    Pulse *pu = get_pulse(ctx, pulse);
+    if (!pu || !host) return fail(ctx, FCN_ERR_ARG, "bad pulse index or null buffer");
+    const size_t np = (size_t)pu->points();
+    if (ctx->prec == FCN_FP64) {
+        CK(cudaMemcpyAsync(host, pu->field, 16 * np, cudaMemcpyDeviceToHost, ctx->st), "D2H field");
+    } else {
+        if (!pu->stage) CK(cudaMalloc(&pu->stage, 16 * np), "staging buffer");
+        CK(launch_widen<float>((const cx<float> *)pu->field, pu->stage, (int64_t)np, ctx->st), "widen");
+        CK(cudaMemcpyAsync(host, pu->stage, 16 * np, cudaMemcpyDeviceToHost, ctx->st), "D2H field");
+    }
+    CK(cudaStreamSynchronize(ctx->st), "sync");
+    return FCN_OK;
+}
+
+int fcn_get_field_device(fcn_ctx *ctx, int32_t pulse, void *dev) {
+    Pulse *pu = get_pulse(ctx, pulse);
+    if (!pu || !dev) return fail(ctx, FCN_ERR_ARG, "bad pulse index or null buffer");
+    CK(cudaMemcpyAsync(dev, pu->field, csize(ctx->prec) * pu->points(), cudaMemcpyDeviceToDevice, ctx->st),
+       "D2D field");
+    return FCN_OK;
+}
+
+int fcn_get_rho(fcn_ctx *ctx, int32_t pulse, double *host) {
+    Pulse *pu = get_pulse(ctx, pulse);
+    if (!pu || !host) return fail(ctx, FCN_ERR_ARG, "bad pulse index or null buffer");
+    const size_t np = (size_t)pu->points();
+    if (ctx->prec == FCN_FP64) {
+        CK(cudaMemcpyAsync(host, pu->rho, 8 * np, cudaMemcpyDeviceToHost, ctx->st), "D2H rho");
+    } else {
+        if (!pu->stage) CK(cudaMalloc(&pu->stage, 16 * np), "staging buffer");
+        CK(launch_widen_real<float>((const float *)pu->rho, pu->stage, (int64_t)np, ctx->st), "widen rho");
+        CK(cudaMemcpyAsync(host, pu->stage, 8 * np, cudaMemcpyDeviceToHost, ctx->st), "D2H rho");
+    }
+    CK(cudaStreamSynchronize(ctx->st), "sync");
+    return FCN_OK;
+}
+
+int fcn_step(fcn_ctx *ctx, double dz, int64_t n) {
+    if (!ctx) return FCN_ERR_ARG;
+    return ctx->prec == FCN_FP64 ? step_impl<double>(ctx, dz, n, true) : step_impl<float>(ctx, dz, n, true);
+}
+
+int fcn_step_nograph(fcn_ctx *ctx, double dz, int64_t n) {
+    if (!ctx) return FCN_ERR_ARG;
+    return ctx->prec == FCN_FP64 ? step_impl<double>(ctx, dz, n, false) : step_impl<float>(ctx, dz, n, false);
+}
+
+int fcn_propagate(fcn_ctx *ctx, double z_end, double dz0, double rtol, double dz_min, int32_t max_reject,
+                  int32_t controller, fcn_stats *out) {
+    if (!ctx) return FCN_ERR_ARG;
+    return ctx->prec == FCN_FP64
+               ? propagate_impl<double>(ctx, z_end, dz0, rtol, dz_min, max_reject, controller, out)
+               : propagate_impl<float>(ctx, z_end, dz0, rtol, dz_min, max_reject, controller, out);
+}
+
+int fcn_get_diag(fcn_ctx *ctx, int32_t pulse, fcn_diag *out) {
+    Pulse *pu = get_pulse(ctx, pulse);
+    if (!pu || !out) return fail(ctx, FCN_ERR_ARG, "bad pulse index or null output");
+    return ctx->prec == FCN_FP64 ? diag_impl<double>(ctx, *pu, out) : diag_impl<float>(ctx, *pu, out);
+}
+
+int fcn_get_profiles(fcn_ctx *ctx, int32_t pulse, double *power, double *fluence) {
+    Pulse *pu = get_pulse(ctx, pulse);
+    if (!pu) return fail(ctx, FCN_ERR_ARG, "bad pulse index");
+    const int nr = pu->g.nr, nt = pu->g.nt;
+    double *d = nullptr;
+    CK(cudaMalloc(&d, sizeof(double) * (nt + nr)), "profile buffer");
+    cudaError_t e = ctx->prec == FCN_FP64
+        ? launch_profiles<double>((const cx<double> *)pu->field, nr, nt, d, d + nt, ctx->st)
+        : launch_profiles<float>((const cx<float> *)pu->field, nr, nt, d, d + nt, ctx->st);
+    std::vector<double> h(nt + nr);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), d, sizeof(double) * (nt + nr), cudaMemcpyDeviceToHost, ctx->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->st);
+    cudaFree(d);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "profiles");
+    const Consts c = derive(pu->g, pu->p);
+    if (power)
+        for (int p = 0; p < nt; ++p) power[p] = 2.0 * kPi * c.dr * c.dr * h[p];
+    if (fluence)
+        for (int m = 0; m < nr; ++m) fluence[m] = c.dtau * h[nt + m];
+    return FCN_OK;
+}
+
+int fcn_get_state(fcn_ctx *ctx, int32_t pulse, double state[4]) {
+    Pulse *pu = get_pulse(ctx, pulse);
+    if (!pu || !state) return fail(ctx, FCN_ERR_ARG, "bad pulse index or null state");
+    state[0] = pu->z;
+    state[1] = double(pu->steps);
+    state[2] = double(pu->rejected);
+    state[3] = pu->dz_next;
+    return FCN_OK;
+}
+
+int fcn_set_state(fcn_ctx *ctx, int32_t pulse, const double state[4]) {
+    Pulse *pu = get_pulse(ctx, pulse);
+    if (!pu || !state) return fail(ctx, FCN_ERR_ARG, "bad pulse index or null state");
+    pu->z = state[0];
+    pu->steps = (int64_t)state[1];
+    pu->rejected = (int64_t)state[2];
+    pu->dz_next = state[3];
+    return FCN_OK;
+}
+
+int fcn_profile_enable(fcn_ctx *ctx, int32_t on) {
+    if (!ctx) return FCN_ERR_ARG;
+    CK(cudaStreamSynchronize(ctx->st), "profile sync");
+    profile_collect(ctx);
+    ctx->profiling = on != 0;
+    return FCN_OK;
+}
+
+int fcn_profile_read(fcn_ctx *ctx, double *ms, int64_t *count, int32_t reset) {
+    if (!ctx || !ms || !count) return FCN_ERR_ARG;
+    CK(cudaStreamSynchronize(ctx->st), "profile sync");
+    profile_collect(ctx);
+    for (int k = 0; k < FCN_PROF_KINDS; ++k) {
+        ms[k] = ctx->prof_ms[k];
+        count[k] = ctx->prof_n[k];
+        if (reset) { ctx->prof_ms[k] = 0; ctx->prof_n[k] = 0; }
+    }
+    return FCN_OK;
+}
+
+int fcn_mlp_set(fcn_ctx *ctx, const float *host) {
+    if (!ctx || !host) return FCN_ERR_ARG;
+    if (!ctx->mlp) CK(cudaMalloc(&ctx->mlp, sizeof(float) * FCN_MLP_NPARAM), "mlp weights");
+    CK(cudaMemcpy(ctx->mlp, host, sizeof(float) * FCN_MLP_NPARAM, cudaMemcpyHostToDevice), "mlp copy");
+    ctx->has_mlp = true;
+    return FCN_OK;
+}
+
+int fcn_mlp_get(fcn_ctx *ctx, float *host) {
+    if (!ctx || !host) return FCN_ERR_ARG;
+    if (!ctx->has_mlp) return fail(ctx, FCN_ERR_STATE, "no MLP weights loaded");
+    CK(cudaMemcpy(host, ctx->mlp, sizeof(float) * FCN_MLP_NPARAM, cudaMemcpyDeviceToHost), "mlp copy");
+    return FCN_OK;
+}
+
+// ---- stateless device operations ----
+
+int fcn_op_rows(const fcn_grid *grid, const fcn_params *params, int32_t precision, int32_t ops,
+                double dz_half, void *field, void *rho, void *stream) {
+    std::string why;
+    int rc = check_grid_params(precision, grid, params, &why);
+    fcn_ctx *ctx = nullptr;
+    if (rc) return fail(nullptr, rc, why);
+    if (!field || (ops & ~31) || ((ops & FCN_OP_RHO) && !rho) || !std::isfinite(dz_half))
+        return fail(nullptr, FCN_ERR_ARG, "bad field/rho pointer, ops or dz_half");
+    const cudaStream_t st = (cudaStream_t)stream;
+    if (precision == FCN_FP64) {
+        RowArgs<double> a;
+        const cx<double> *tw;
+        CK(get_twiddles<double>(grid->nt, &tw), "twiddles");
+        CK(prepare_rows<double>(grid->nt), "row kernel attributes");
+        a.field = (cx<double> *)field; a.tw = tw; a.rho = (double *)rho; a.stats = nullptr;
+        a.nr = grid->nr; a.ops = ops; a.nl = nl_coef<double>(*grid, *params, dz_half);
+        CK(launch_rows<double>(a, grid->nt, st), "row stage");
+    } else {
+        RowArgs<float> a;
+        const cx<float> *tw;
+        CK(get_twiddles<float>(grid->nt, &tw), "twiddles");
+        CK(prepare_rows<float>(grid->nt), "row kernel attributes");
+        a.field = (cx<float> *)field; a.tw = tw; a.rho = (float *)rho; a.stats = nullptr;
+        a.nr = grid->nr; a.ops = ops; a.nl = nl_coef<float>(*grid, *params, dz_half);
+        CK(launch_rows<float>(a, grid->nt, st), "row stage");
+    }
+    return FCN_OK;
+}
+
+int64_t fcn_cn_table_entries(const fcn_grid *grid) {
+    if (!grid || grid->nr < 1 || grid->nt < 2) return 0;
+    return (int64_t)grid->nr * (grid->nt / 2 + 1);
+}
+
+int fcn_op_cn_table(const fcn_grid *grid, const fcn_params *params, int32_t precision, double dz,
+                    void *table, void *stream) {
+    std::string why;
+    int rc = check_grid_params(precision, grid, params, &why);
+    fcn_ctx *ctx = nullptr;
+    if (rc) return fail(nullptr, rc, why);
+    if (!table || !(dz > 0) || !std::isfinite(dz)) return fail(nullptr, FCN_ERR_ARG, "bad table pointer or dz");
+    TableArgs ta;
+    ta.nr = grid->nr;
+    ta.nt = grid->nt;
+    cn_coefs(*grid, *params, dz, &ta.s, &ta.dk);
+    const double *lo64, *hi64;
+    if (precision == FCN_FP64) {
+        const double *lo, *hi;
+        CK(get_lohi<double>(grid->nr, &lo, &hi, &lo64, &hi64), "radial tables");
+        ta.lo = lo64; ta.hi = hi64;
+        CK(launch_cn_table<double>(ta, (cx<double> *)table, (cudaStream_t)stream), "table kernel");
+    } else {
+        const float *lo, *hi;
+        CK(get_lohi<float>(grid->nr, &lo, &hi, &lo64, &hi64), "radial tables");
+        ta.lo = lo64; ta.hi = hi64;
+        CK(launch_cn_table<float>(ta, (cx<float> *)table, (cudaStream_t)stream), "table kernel");
+    }
+    return FCN_OK;
+}
+
+int fcn_op_cn(const fcn_grid *grid, const fcn_params *params, int32_t precision, double dz,
+              const void *table, void *field, void *stream) {
+    std::string why;
+    int rc = check_grid_params(precision, grid, params, &why);
+    fcn_ctx *ctx = nullptr;
+    if (rc) return fail(nullptr, rc, why);
+    if (!table || !field || !(dz > 0) || !std::isfinite(dz)) return fail(nullptr, FCN_ERR_ARG, "bad pointers or dz");
+    double s, dk;
+    cn_coefs(*grid, *params, dz, &s, &dk);
+    const double *lo64, *hi64;
+    if (precision == FCN_FP64) {
+        const double *lo, *hi;
+        CK(get_lohi<double>(grid->nr, &lo, &hi, &lo64, &hi64), "radial tables");
+        ColArgs<double> a;
+        a.field = (cx<double> *)field; a.invden = (const cx<double> *)table; a.lo = lo; a.hi = hi;
+        a.nr = grid->nr; a.nt = grid->nt; a.s = s; a.dk = dk;
+        CK(launch_cn<double>(a, (cudaStream_t)stream), "column stage");
+    } else {
+        const float *lo, *hi;
+        CK(get_lohi<float>(grid->nr, &lo, &hi, &lo64, &hi64), "radial tables");
+        ColArgs<float> a;
+        a.field = (cx<float> *)field; a.invden = (const cx<float> *)table; a.lo = lo; a.hi = hi;
+        a.nr = grid->nr; a.nt = grid->nt; a.s = float(s); a.dk = float(dk);
+        CK(launch_cn<float>(a, (cudaStream_t)stream), "column stage");
+    }
+    return FCN_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,151 @@
+// fcn_device.cuh -- device types and kernel launch interfaces of the GB300
+// FCN z-step (Ma & Lin, arXiv:1507.05988, Sec. 3).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fcn {
+
+// Interleaved complex value; 8-byte aligned for float, 16 for double so that
+// one complex moves in one vector load/store.
+template <typename T>
+struct alignas(2 * sizeof(T)) cx {
+    T x, y;
+};
+
+template <typename T>
+__host__ __device__ __forceinline__ cx<T> mk(T x, T y) { cx<T> r; r.x = x; r.y = y; return r; }
+template <typename T>
+__device__ __forceinline__ cx<T> operator+(cx<T> a, cx<T> b) { return mk(a.x + b.x, a.y + b.y); }
+template <typename T>
+__device__ __forceinline__ cx<T> operator-(cx<T> a, cx<T> b) { return mk(a.x - b.x, a.y - b.y); }
+template <typename T>
+__device__ __forceinline__ cx<T> cmul(cx<T> a, cx<T> b) {
+    return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename T>
+__device__ __forceinline__ cx<T> cscale(cx<T> a, T s) { return mk(a.x * s, a.y * s); }
+// a * (i s) for real s
+template <typename T>
+__device__ __forceinline__ cx<T> cmul_i(cx<T> a, T s) { return mk(-a.y * s, a.x * s); }
+template <typename T>
+__device__ __forceinline__ T cnorm(cx<T> a) { return a.x * a.x + a.y * a.y; }
+
+// Read-only cached load of one complex value.
+__device__ __forceinline__ cx<float> ldg_cx(const cx<float> *p) {
+    const float2 v = __ldg(reinterpret_cast<const float2 *>(p));
+    return mk(v.x, v.y);
+}
+__device__ __forceinline__ cx<double> ldg_cx(const cx<double> *p) {
+    const double2 v = __ldg(reinterpret_cast<const double2 *>(p));
+    return mk(v.x, v.y);
+}
+
+// Physics switches (same bits as the C-ABI).
+enum : unsigned {
+    PH_DIFFRACTION = 1u, PH_DISPERSION = 2u, PH_KERR = 4u, PH_PLASMA = 8u,
+    PH_MPI = 16u, PH_MPI_SAT = 32u
+};
+
+// Row-stage operations (same bits as the C-ABI FCN_OP_*), plus internal ones.
+enum : int {
+    OP_IFFT = 1, OP_NL = 2, OP_NL2 = 4, OP_FFT = 8, OP_RHO = 16,
+    OP_STATS = 32,   // per-row FP64 statistics of the final time-domain row
+    OP_SPEC = 64,    // spectral moments of the final time-domain row (no store)
+    OP_NOSTORE = 128 // do not write the field back (diagnostics only)
+};
+
+// Coefficients of one nonlinear half step in scaled intensity units
+// Ihat = I / I_s (I_s a power of two, so the scaling is exact).
+//   phase rate  = sum_j kerr[j] Ihat^(j+1) - plasma * u        [rad/m]
+//   loss rate   = loss * Ihat^(K-1) [* (1 - u)]                [1/m]
+//   RK4 step of u = rho/rho_nt along tau uses x = sdt * Ihat^K (= dtau w)
+template <typename T>
+struct NLCoef {
+    T h;        // half-step length dz/2 [m]
+    T kerr[4];  // (k0/n0) n_2j I_s^j
+    T plasma;   // k0/(2 n0^2 rho_c) rho_nt
+    T loss;     // (beta_K/2) I_s^(K-1)
+    T sdt;      // sigma_K dtau I_s^K
+    T inv_is;   // 1 / I_s
+    T inv_nt;   // 1 / Nt (applied after the inverse FFT)
+    T rho_nt;   // rho = u rho_nt for the rho output
+    int K;
+    unsigned flags;
+};
+
+// Statistics written per row by the row stage (FP64).
+enum : int {
+    ST_SUM_I = 0,   // sum_p |A|^2
+    ST_MAX_I = 1,   // max_p |A|^2
+    ST_MAX_U = 2,   // max_p rho/rho_nt of the last half step
+    ST_NONFINITE = 3,
+    ST_S0 = 4,      // sum_q |A~_q|^2
+    ST_S1 = 5,      // sum_q omega_q |A~_q|^2 (omega in units of domega)
+    ST_S2 = 6,      // sum_q omega_q^2 |A~_q|^2
+    NSTAT = 8
+};
+
+// One row-stage work item list entry (batched launches): rows [row0, row0+nrows)
+// of the pulse whose field starts at `field`.
+template <typename T>
+struct RowArgs {
+    cx<T> *field;         // [nr][nt]
+    const cx<T> *tw;      // forward twiddles W_nt^m = exp(-2 pi i m / nt), m < nt
+    T *rho;               // [nr][nt] or null
+    double *stats;        // [nr][NSTAT] or null
+    int nr;
+    int ops;
+    NLCoef<T> nl;
+};
+
+template <typename T>
+struct ColArgs {
+    cx<T> *field;            // [nr][nt], frequency domain, in place
+    const cx<T> *invden;     // [nr][nt/2+1]: 1/pivot_j per |q|
+    const T *lo;             // [nr]: 1 - 1/(2j) (j >= 1), 0 at j = 0
+    const T *hi;             // [nr]: 1 + 1/(2j) (j >= 1), 0 at j = 0
+    int nr, nt;
+    T s;                     // dz / (4 k0 dr^2), 0 without diffraction
+    T dk;                    // k'' dz/4 domega^2, 0 without dispersion: delta_q = dk q^2
+};
+
+struct TableArgs {
+    int nr, nt;
+    double s, dk;
+    const double *lo, *hi;   // FP64 copies of the ratio tables
+};
+
+// ---- launchers (defined in the .cu files) ----
+template <typename T>
+cudaError_t launch_rows(const RowArgs<T> &a, int nt, cudaStream_t st);
+// Sets the kernel's shared-memory attribute for this Nt (call before the
+// first launch, outside stream capture).
+template <typename T>
+cudaError_t prepare_rows(int nt);
+template <typename T>
+cudaError_t launch_cn(const ColArgs<T> &a, cudaStream_t st);
+template <typename T>
+cudaError_t launch_cn_table(const TableArgs &a, cx<T> *table, cudaStream_t st);
+
+// reductions and conversions
+template <typename T>
+cudaError_t launch_widen(const cx<T> *src, double *dst, int64_t n, cudaStream_t st);
+template <typename T>
+cudaError_t launch_narrow(const double *src, cx<T> *dst, int64_t n, cudaStream_t st);
+template <typename T>
+cudaError_t launch_widen_real(const T *src, double *dst, int64_t n, cudaStream_t st);
+// Final FP64 reduction of per-row statistics into out[0..7]:
+// [energy_sum (sum_m W_m S_m), max I, max u, onaxis max I, S0, S1, S2, nonfinite]
+cudaError_t launch_reduce_stats(const double *stats, int nr, double *out, cudaStream_t st);
+// Per-row sums of |a-b|^2 and |b|^2 (FP64) then the final reduction into out[0..1].
+template <typename T>
+cudaError_t launch_diff_norm(const cx<T> *a, const cx<T> *b, int nr, int nt, double *rows,
+                             double *out, cudaStream_t st);
+// Power P(tau_p) (unscaled: sum_m W_m |A|^2) and fluence rows (sum_p |A|^2), FP64.
+template <typename T>
+cudaError_t launch_profiles(const cx<T> *f, int nr, int nt, double *power, double *rowsum,
+                            cudaStream_t st);
+
+}  // namespace fcn

@@ -1,0 +1,657 @@
+// row_kernel.cuh -- the row stage of the FCN z-step: FFTs along tau fused with
+// the nonlinear half steps (Ma & Lin, arXiv:1507.05988, Sec. 3.1 first/third
+// loops, Sec. 3.2, Eqs. (Anhalf)/(Anhalf1), and the re-organised step of
+// Sec. 4 where the nonlinear part and the transforms share the radial
+// decomposition).
+//
+// One row (fixed radial index m) is one independent unit of work.  Rows of
+// Nt <= 4096 points run on 256 threads (several rows per CTA for Nt < 4096);
+// Nt = 8192 runs on 512 threads.  Each thread owns E = 16 complex values
+// (E = Nt when Nt < 16).
+//
+// Transform: self-sorting Stockham FFT (radix-16 passes, then one radix 2/4/8
+// pass for the remaining factor), done in place in one padded shared-memory
+// buffer with the butterfly operands in registers.  The first inverse pass
+// reads HBM directly and the last forward pass writes HBM directly; both are
+// coalesced (consecutive threads touch consecutive complex values).  Shared
+// memory rows are padded by one value per 16 so that the strided Stockham
+// stores and the contiguous per-thread reads of the nonlinear stage are free
+// of bank conflicts.
+//
+// Nonlinear half step (Eq. (nonlinearpart)):  A <- A exp(h N(I, rho)).
+// rho(tau) follows Eq. (ionization) integrated by RK4 along tau from
+// rho(tau_min) = 0, with the RK4 midpoint intensity the mean of the two
+// neighbours.  Because the ODE is linear in u = rho/rho_nt, one RK4 step is
+// u_{p+1} = u_p + c_p (1 - u_p) with c_p a function of I_p and I_{p+1} only, so
+// u_p = c_0 (+) c_1 (+) ... (+) c_{p-1} for the associative, commutative
+// operation a (+) b = a + b - a b = 1 - (1-a)(1-b).  That makes the
+// integration an exclusive parallel scan: sequential over each thread's 16
+// points, warp shuffles across threads, and (rows wider than a warp) an FP64
+// scan of the warp totals.  (+) never cancels (all terms are in [0, 1]), so
+// the scan keeps the relative precision of the working type.
+#pragma once
+#include "fcn_device.cuh"
+
+namespace fcn {
+namespace {
+
+constexpr int ilog2(int n) { return n <= 1 ? 0 : 1 + ilog2(n / 2); }
+
+template <int NT>
+struct RowCfg {
+    static constexpr int E = NT < 16 ? NT : 16;             // values per thread
+    static constexpr int TPR = NT / E;                      // threads per row
+    static constexpr int THREADS = TPR >= 256 ? TPR : 256;  // CTA size
+    static constexpr int RPC = THREADS / TPR;               // rows per CTA
+    static constexpr int PADN = NT >= 16 ? NT + NT / 16 : NT;
+    static constexpr int LOG = ilog2(NT);
+    static constexpr int N16 = NT >= 16 ? LOG / 4 : 0;      // radix-16 passes
+    static constexpr int REM = NT >= 16 ? (1 << (LOG % 4)) : NT;  // last radix (1: none)
+    static constexpr int NPASS = N16 + (REM > 1 ? 1 : 0);
+    static constexpr int WARPS_PER_ROW = TPR > 32 ? TPR / 32 : 1;
+};
+
+template <int NT, int P>
+struct PassCfg {
+    using C = RowCfg<NT>;
+    static constexpr int R = (P < C::N16) ? 16 : C::REM;
+    // Ns = product of the radices of the earlier passes
+    static constexpr int NS = (P < C::N16) ? (1 << (4 * P)) : (1 << (4 * C::N16));
+};
+
+__device__ __forceinline__ int pidx(int i, int nt) { return nt >= 16 ? i + (i >> 4) : i; }
+
+// cos(2 pi m / 16)
+__host__ __device__ constexpr double cos16(int m) {
+    m &= 15;
+    return m == 0 ? 1.0
+         : m == 1 ? 0.92387953251128675613
+         : m == 2 ? 0.70710678118654752440
+         : m == 3 ? 0.38268343236508977173
+         : m == 4 ? 0.0
+         : m == 5 ? -0.38268343236508977173
+         : m == 6 ? -0.70710678118654752440
+         : m == 7 ? -0.92387953251128675613
+         : m == 8 ? -1.0
+         : m == 9 ? -0.92387953251128675613
+         : m == 10 ? -0.70710678118654752440
+         : m == 11 ? -0.38268343236508977173
+         : m == 12 ? 0.0
+         : m == 13 ? 0.38268343236508977173
+         : m == 14 ? 0.70710678118654752440
+         : 0.92387953251128675613;
+}
+
+// o * exp(DIR 2 pi i m / 16); exact shortcuts for the quarter turns
+template <typename T, int DIR>
+__device__ __forceinline__ cx<T> rot16(cx<T> o, int m) {
+    m &= 15;
+    if (m == 0) return o;
+    if (m == 8) return mk(-o.x, -o.y);
+    if (m == 4) return DIR > 0 ? mk(-o.y, o.x) : mk(o.y, -o.x);
+    if (m == 12) return DIR > 0 ? mk(o.y, -o.x) : mk(-o.y, o.x);
+    const T c = T(cos16(m));
+    const T s = T(DIR) * T(cos16(m - 4));
+    return mk(o.x * c - o.y * s, o.x * s + o.y * c);
+}
+
+// In-register DFT of size R (power of two <= 16), natural order in and out,
+// X_k = sum_n x_n exp(DIR 2 pi i n k / R), by radix-2 decimation in time.
+template <typename T, int R, int DIR>
+struct Dft {
+    __device__ __forceinline__ static void run(cx<T> *v) {
+        cx<T> e[R / 2], o[R / 2];
+#pragma unroll
+        for (int k = 0; k < R / 2; ++k) { e[k] = v[2 * k]; o[k] = v[2 * k + 1]; }
+        Dft<T, R / 2, DIR>::run(e);
+        Dft<T, R / 2, DIR>::run(o);
+#pragma unroll
+        for (int k = 0; k < R / 2; ++k) {
+            cx<T> t = rot16<T, DIR>(o[k], k * (16 / R));
+            v[k] = e[k] + t;
+            v[k + R / 2] = e[k] - t;
+        }
+    }
+};
+template <typename T, int DIR>
+struct Dft<T, 1, DIR> {
+    __device__ __forceinline__ static void run(cx<T> *) {}
+};
+
+// Twiddle and butterfly of pass P for this thread's butterflies (operands
+// already in v[i*R + r]).
+template <typename T, int NT, int P, int DIR>
+__device__ __forceinline__ void pass_compute(cx<T> (&v)[RowCfg<NT>::E], int t,
+                                             const cx<T> *__restrict__ tw) {
+    using C = RowCfg<NT>;
+    constexpr int R = PassCfg<NT, P>::R;
+    constexpr int NS = PassCfg<NT, P>::NS;
+    constexpr int NB = C::E / R;
+    constexpr int STRIDE = NT / (NS * R);
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+        const int j = t + C::TPR * i;
+        if (NS > 1) {
+            const int k = j & (NS - 1);
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                cx<T> w = ldg_cx(&tw[r * k * STRIDE]);
+                if (DIR > 0) w.y = -w.y;
+                v[i * R + r] = cmul(v[i * R + r], w);
+            }
+        }
+        Dft<T, R, DIR>::run(&v[i * R]);
+    }
+}
+
+template <typename T, int NT, int P>
+__device__ __forceinline__ void pass_load(cx<T> (&v)[RowCfg<NT>::E], const cx<T> *S, int t) {
+    using C = RowCfg<NT>;
+    constexpr int R = PassCfg<NT, P>::R;
+    constexpr int NB = C::E / R;
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+        const int j = t + C::TPR * i;
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[i * R + r] = S[pidx(j + r * (NT / R), NT)];
+    }
+}
+
+template <typename T, int NT, int P>
+__device__ __forceinline__ void pass_store(const cx<T> (&v)[RowCfg<NT>::E], cx<T> *S, int t) {
+    using C = RowCfg<NT>;
+    constexpr int R = PassCfg<NT, P>::R;
+    constexpr int NS = PassCfg<NT, P>::NS;
+    constexpr int NB = C::E / R;
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+        const int j = t + C::TPR * i;
+        const int base = (j / NS) * NS * R + (j & (NS - 1));
+#pragma unroll
+        for (int r = 0; r < R; ++r) S[pidx(base + r * NS, NT)] = v[i * R + r];
+    }
+}
+
+// Inverse transform (input already in registers in pass-0 order; result in S
+// in natural order, unscaled) and forward transform (input in S in natural
+// order; the last pass leaves its outputs in registers for the caller).
+template <typename T, int NT, int P, bool LAST>
+struct InvDispatch;
+template <typename T, int NT, int P>
+struct InvDispatch<T, NT, P, false> {
+    __device__ __forceinline__ static void run(cx<T> (&v)[RowCfg<NT>::E], cx<T> *S, int t,
+                                               const cx<T> *tw) {
+        if (P > 0) {
+            pass_load<T, NT, P>(v, S, t);
+            __syncthreads();
+        }
+        pass_compute<T, NT, P, +1>(v, t, tw);
+        pass_store<T, NT, P>(v, S, t);
+        __syncthreads();
+        InvDispatch<T, NT, P + 1, (P + 1 >= RowCfg<NT>::NPASS)>::run(v, S, t, tw);
+    }
+};
+template <typename T, int NT, int P>
+struct InvDispatch<T, NT, P, true> {
+    __device__ __forceinline__ static void run(cx<T> (&)[RowCfg<NT>::E], cx<T> *, int,
+                                               const cx<T> *) {}
+};
+
+template <typename T, int NT, int P, bool LAST>
+struct FwdDispatch;
+template <typename T, int NT, int P>
+struct FwdDispatch<T, NT, P, false> {
+    __device__ __forceinline__ static void run(cx<T> (&v)[RowCfg<NT>::E], cx<T> *S, int t,
+                                               const cx<T> *tw) {
+        pass_load<T, NT, P>(v, S, t);
+        __syncthreads();
+        pass_compute<T, NT, P, -1>(v, t, tw);
+        if (P + 1 < RowCfg<NT>::NPASS) {
+            pass_store<T, NT, P>(v, S, t);
+            __syncthreads();
+        }
+        FwdDispatch<T, NT, P + 1, (P + 1 >= RowCfg<NT>::NPASS)>::run(v, S, t, tw);
+    }
+};
+template <typename T, int NT, int P>
+struct FwdDispatch<T, NT, P, true> {
+    __device__ __forceinline__ static void run(cx<T> (&)[RowCfg<NT>::E], cx<T> *, int,
+                                               const cx<T> *) {}
+};
+
+// ---------------------------------------------------------------------------
+// Nonlinear half step
+// ---------------------------------------------------------------------------
+
+template <typename T>
+__device__ __forceinline__ T ipow(T x, int k) {
+    T r = T(1);
+    while (k) {
+        if (k & 1) r *= x;
+        x *= x;
+        k >>= 1;
+    }
+    return r;
+}
+
+// x^K with K a compile-time constant when KT > 0 (squarings unrolled), the
+// runtime exponent k otherwise.
+template <int KT, typename T>
+__device__ __forceinline__ T powk(T x, int k) {
+    if constexpr (KT == 8) {
+        const T x2 = x * x, x4 = x2 * x2;
+        return x4 * x4;
+    } else if constexpr (KT == 7) {
+        const T x2 = x * x, x4 = x2 * x2;
+        return x4 * x2 * x;
+    } else {
+        return ipow(x, k);
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ T uplus(T a, T b) { return a + b - a * b; }
+
+// RK4 increment of u over one dtau cell from the scaled intensities at its
+// ends: u_next = u + c (1 - u).
+template <int KT, typename T>
+__device__ __forceinline__ T rk4_coef(T ia, T ib, T xa, T xb, const NLCoef<T> &c) {
+    const T xm = c.sdt * powk<KT>((ia + ib) * T(0.5), c.K);
+    const T t1 = T(1) - T(0.5) * xa;
+    const T t2 = T(1) - T(0.5) * xm * t1;
+    const T t3 = T(1) - xm * t2;
+    return (xa + T(2) * xm * t1 + T(2) * xm * t2 + xb * t3) * T(1.0 / 6.0);
+}
+
+template <typename T>
+__device__ __forceinline__ void sincos_t(T x, T *s, T *c);
+// FP32: Cody-Waite reduction of x by 2 pi (two-constant split, 2 pi =
+// P2_HI + P2_LO with P2_HI the float nearest 2 pi) into [-pi, pi], then the
+// hardware sine/cosine.  The phase itself carries an FP32 relative error, so
+// the reduction is exact enough for |x| up to ~1e5.
+template <>
+__device__ __forceinline__ void sincos_t<float>(float x, float *s, float *c) {
+    constexpr float INV_2PI = 0.159154943091895335769f;
+    constexpr float P2_HI = 6.28318548202514648438f;
+    constexpr float P2_LO = -1.74845553146951715e-7f;
+    const float n = rintf(x * INV_2PI);
+    float r = fmaf(-n, P2_HI, x);
+    r = fmaf(-n, P2_LO, r);
+    __sincosf(r, s, c);
+}
+template <>
+__device__ __forceinline__ void sincos_t<double>(double x, double *s, double *c) { sincos(x, s, c); }
+template <typename T>
+__device__ __forceinline__ T exp_t(T x);
+template <>
+__device__ __forceinline__ float exp_t<float>(float x) { return __expf(x); }
+template <>
+__device__ __forceinline__ double exp_t<double>(double x) { return exp(x); }
+
+// A <- A exp(h N(Ihat, u))
+template <typename T>
+__device__ __forceinline__ cx<T> nl_apply(cx<T> a, T ih, T ihKm1, T u, const NLCoef<T> &c) {
+    T phase = T(0), loss = T(0);
+    if (c.flags & PH_KERR)
+        phase = ih * (c.kerr[0] + ih * (c.kerr[1] + ih * (c.kerr[2] + ih * c.kerr[3])));
+    if (c.flags & PH_PLASMA) phase -= c.plasma * u;
+    if (c.flags & PH_MPI) {
+        loss = c.loss * ihKm1;
+        if (c.flags & PH_MPI_SAT) loss *= (T(1) - u);
+    }
+    T s, co;
+    sincos_t<T>(c.h * phase, &s, &co);
+    const T amp = (c.flags & PH_MPI) ? exp_t<T>(-c.h * loss) : T(1);
+    const cx<T> e = mk(amp * co, amp * s);
+    return cmul(a, e);
+}
+
+// Exclusive (+)-scan of one value per thread across the TPR threads of a row.
+// Returns the carry entering this thread.  FP64 carries between warps.
+template <typename T, int NT>
+__device__ __forceinline__ T row_scan_exclusive(T tot, int t, double *scr, int rloc) {
+    using C = RowCfg<NT>;
+    if (C::TPR == 1) return T(0);
+    constexpr int W = C::TPR < 32 ? C::TPR : 32;
+    const int lane = t & (W - 1);
+    T incl = tot;
+#pragma unroll
+    for (int d = 1; d < W; d <<= 1) {
+        T y = __shfl_up_sync(0xffffffffu, incl, d, W);
+        if (lane >= d) incl = uplus(incl, y);
+    }
+    T excl = __shfl_up_sync(0xffffffffu, incl, 1, W);
+    if (lane == 0) excl = T(0);
+    if (C::WARPS_PER_ROW > 1) {
+        const int w = t >> 5;
+        double *ws = scr + rloc * C::WARPS_PER_ROW;
+        if (lane == 31) ws[w] = double(incl);
+        __syncthreads();
+        if (t < 32) {
+            // FP64 exclusive scan of the warp totals of this row (<= 16)
+            double x = (lane < C::WARPS_PER_ROW) ? ws[lane] : 0.0;
+            double in = x;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                double y = __shfl_up_sync(0xffffffffu, in, d, 32);
+                if (lane >= d) in = in + y - in * y;
+            }
+            double ex = __shfl_up_sync(0xffffffffu, in, 1, 32);
+            if (lane == 0) ex = 0.0;
+            __syncwarp();
+            if (lane < C::WARPS_PER_ROW) ws[lane] = ex;
+        }
+        __syncthreads();
+        const T wc = T(ws[w]);
+        __syncthreads();
+        excl = uplus(wc, excl);
+    }
+    return excl;
+}
+
+// One nonlinear half step on this thread's E contiguous values v (points
+// p = E t + e) and on the first value of the next thread (nb), which the
+// next half step needs for the RK4 cell that straddles the two threads.
+// u receives rho/rho_nt at the E points.  Intensity powers are recomputed
+// from v instead of being kept in arrays (register pressure).
+template <typename T, int NT, int KT>
+__device__ __forceinline__ void nl_half(cx<T> (&v)[RowCfg<NT>::E], cx<T> &nb, T (&u)[RowCfg<NT>::E],
+                                        int t, const NLCoef<T> &c, bool need_u, double *scr,
+                                        int rloc) {
+    using C = RowCfg<NT>;
+    constexpr int E = C::E;
+    const bool last_thread = (t == C::TPR - 1);
+    T u_nb = T(0);
+    if (need_u) {
+        T run = T(0);
+        T ih_a = cnorm(v[0]) * c.inv_is;
+        T x_a = c.sdt * powk<KT>(ih_a, c.K);
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            u[e] = run;
+            const cx<T> nxt = (e + 1 < E) ? v[e + 1] : nb;
+            const T ih_b = cnorm(nxt) * c.inv_is;
+            const T x_b = c.sdt * powk<KT>(ih_b, c.K);
+            const bool has_next = (e + 1 < E) || !last_thread;
+            const T cc = has_next ? rk4_coef<KT>(ih_a, ih_b, x_a, x_b, c) : T(0);
+            run = uplus(run, cc);
+            ih_a = ih_b;
+            x_a = x_b;
+        }
+        const T carry = row_scan_exclusive<T, NT>(run, t, scr, rloc);
+#pragma unroll
+        for (int e = 0; e < E; ++e) u[e] = uplus(carry, u[e]);
+        u_nb = uplus(carry, run);
+    } else {
+#pragma unroll
+        for (int e = 0; e < E; ++e) u[e] = T(0);
+    }
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const T ih = cnorm(v[e]) * c.inv_is;
+        v[e] = nl_apply(v[e], ih, powk<(KT > 0 ? KT - 1 : 0)>(ih, c.K - 1), u[e], c);
+    }
+    const T ihn = cnorm(nb) * c.inv_is;
+    nb = nl_apply(nb, ihn, powk<(KT > 0 ? KT - 1 : 0)>(ihn, c.K - 1), u_nb, c);
+}
+
+// Sum across the TPR threads of a row (FP64), result valid in thread t = 0.
+template <int NT>
+__device__ __forceinline__ double row_sum(double x, int t, double *scr, int rloc) {
+    using C = RowCfg<NT>;
+    constexpr int W = C::TPR < 32 ? C::TPR : 32;
+#pragma unroll
+    for (int d = W / 2; d >= 1; d >>= 1) x += __shfl_down_sync(0xffffffffu, x, d, W);
+    if (C::WARPS_PER_ROW > 1) {
+        double *ws = scr + rloc * C::WARPS_PER_ROW;
+        __syncthreads();
+        if ((t & 31) == 0) ws[t >> 5] = x;
+        __syncthreads();
+        if (t == 0) {
+            double s = 0.0;
+            for (int w = 0; w < C::WARPS_PER_ROW; ++w) s += ws[w];
+            x = s;
+        }
+        __syncthreads();
+    }
+    return x;
+}
+
+template <int NT>
+__device__ __forceinline__ double row_max(double x, int t, double *scr, int rloc) {
+    using C = RowCfg<NT>;
+    constexpr int W = C::TPR < 32 ? C::TPR : 32;
+#pragma unroll
+    for (int d = W / 2; d >= 1; d >>= 1) x = fmax(x, __shfl_down_sync(0xffffffffu, x, d, W));
+    if (C::WARPS_PER_ROW > 1) {
+        double *ws = scr + rloc * C::WARPS_PER_ROW;
+        __syncthreads();
+        if ((t & 31) == 0) ws[t >> 5] = x;
+        __syncthreads();
+        if (t == 0) {
+            double s = ws[0];
+            for (int w = 1; w < C::WARPS_PER_ROW; ++w) s = fmax(s, ws[w]);
+            x = s;
+        }
+        __syncthreads();
+    }
+    return x;
+}
+
+template <typename T, int NT, int KT>
+__global__ void __launch_bounds__(RowCfg<NT>::THREADS)
+row_kernel(RowArgs<T> a) {
+    using C = RowCfg<NT>;
+    constexpr int E = C::E;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cx<T> *S_all = reinterpret_cast<cx<T> *>(smem_raw);
+    double *scr = reinterpret_cast<double *>(S_all + C::RPC * C::PADN);
+
+    const int tid = threadIdx.x;
+    const int rloc = tid / C::TPR;
+    const int t = tid - rloc * C::TPR;
+    const int row = blockIdx.x * C::RPC + rloc;
+    const bool valid = row < a.nr;
+    cx<T> *S = S_all + rloc * C::PADN;
+    cx<T> *g = a.field + (size_t)(valid ? row : 0) * NT;
+    const int ops = a.ops;
+
+    cx<T> v[E];
+    if (ops & OP_IFFT) {
+        // pass-0 operands straight from HBM: X[t + r*TPR], coalesced
+#pragma unroll
+        for (int r = 0; r < E; ++r) v[r] = valid ? g[t + r * C::TPR] : mk(T(0), T(0));
+        InvDispatch<T, NT, 0, (C::NPASS <= 0)>::run(v, S, t, a.tw);
+    } else {
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+            const int idx = t + C::TPR * i;
+            S[pidx(idx, NT)] = valid ? g[idx] : mk(T(0), T(0));
+        }
+        __syncthreads();
+    }
+
+    // the time-domain stage runs whenever the row passes through tau space
+    // (nonlinear step, statistics, rho output) or the 1/Nt of an inverse
+    // transform has to be applied
+    const bool time_work = (ops & (OP_NL | OP_STATS | OP_RHO | OP_IFFT)) != 0;
+    if (time_work) {
+        // contiguous view: points E t .. E t + E-1 (+ the next thread's first)
+        const T sc = (ops & OP_IFFT) ? a.nl.inv_nt : T(1);
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            cx<T> x = S[pidx(E * t + e, NT)];
+            v[e] = mk(x.x * sc, x.y * sc);
+        }
+        cx<T> nb = mk(T(0), T(0));
+        if (t + 1 < C::TPR) {
+            cx<T> x = S[pidx(E * (t + 1), NT)];
+            nb = mk(x.x * sc, x.y * sc);
+        }
+        T u[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) u[e] = T(0);
+        const bool need_u = (a.nl.flags & (PH_PLASMA | PH_MPI_SAT)) || (ops & (OP_RHO | OP_STATS));
+        if (ops & OP_NL) nl_half<T, NT, KT>(v, nb, u, t, a.nl, need_u, scr, rloc);
+        if (ops & OP_NL2) nl_half<T, NT, KT>(v, nb, u, t, a.nl, need_u, scr, rloc);
+
+        if ((ops & OP_RHO) && valid && a.rho) {
+            T *rr = a.rho + (size_t)row * NT + E * t;
+#pragma unroll
+            for (int e = 0; e < E; ++e) rr[e] = u[e] * a.nl.rho_nt;
+        }
+        if ((ops & OP_STATS) && a.stats) {
+            double s = 0.0, mx = 0.0, mu = 0.0, bad = 0.0;
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const double i2 = double(v[e].x) * double(v[e].x) + double(v[e].y) * double(v[e].y);
+                if (!isfinite(i2)) bad += 1.0;
+                s += i2;
+                mx = fmax(mx, i2);
+                mu = fmax(mu, double(u[e]));
+            }
+            s = row_sum<NT>(s, t, scr, rloc);
+            mx = row_max<NT>(mx, t, scr, rloc);
+            mu = row_max<NT>(mu, t, scr, rloc);
+            bad = row_sum<NT>(bad, t, scr, rloc);
+            if (t == 0 && valid) {
+                double *st = a.stats + (size_t)row * NSTAT;
+                st[ST_SUM_I] = s;
+                st[ST_MAX_I] = mx;
+                if (ops & (OP_NL | OP_NL2)) st[ST_MAX_U] = mu;
+                st[ST_NONFINITE] = bad;
+            }
+        }
+        __syncthreads();  // every thread has read its neighbour before overwrite
+#pragma unroll
+        for (int e = 0; e < E; ++e) S[pidx(E * t + e, NT)] = v[e];
+        __syncthreads();
+        if (!(ops & OP_FFT) && !(ops & OP_NOSTORE) && valid) {
+#pragma unroll
+            for (int i = 0; i < E; ++i) {
+                const int idx = t + C::TPR * i;
+                g[idx] = S[pidx(idx, NT)];
+            }
+        }
+    }
+
+    if (ops & OP_FFT) {
+        FwdDispatch<T, NT, 0, (C::NPASS <= 0)>::run(v, S, t, a.tw);
+        // last-pass outputs: index j + r*NS, j = t + TPR*i
+        constexpr int PL = C::NPASS - 1;
+        constexpr int R = PassCfg<NT, PL>::R;
+        constexpr int NS = PassCfg<NT, PL>::NS;
+        constexpr int NB = E / R;
+        if (!(ops & OP_NOSTORE) && valid) {
+#pragma unroll
+            for (int i = 0; i < NB; ++i) {
+                const int j = t + C::TPR * i;
+#pragma unroll
+                for (int r = 0; r < R; ++r) g[j + r * NS] = v[i * R + r];
+            }
+        }
+        if ((ops & OP_SPEC) && a.stats) {
+            double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+#pragma unroll
+            for (int i = 0; i < NB; ++i) {
+                const int j = t + C::TPR * i;
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const int q = j + r * NS;
+                    const double w = double(q < NT / 2 ? q : q - NT);
+                    const cx<T> x = v[i * R + r];
+                    const double p2 = double(x.x) * double(x.x) + double(x.y) * double(x.y);
+                    s0 += p2;
+                    s1 += w * p2;
+                    s2 += w * w * p2;
+                }
+            }
+            s0 = row_sum<NT>(s0, t, scr, rloc);
+            s1 = row_sum<NT>(s1, t, scr, rloc);
+            s2 = row_sum<NT>(s2, t, scr, rloc);
+            if (t == 0 && valid) {
+                double *st = a.stats + (size_t)row * NSTAT;
+                st[ST_S0] = s0;
+                st[ST_S1] = s1;
+                st[ST_S2] = s2;
+            }
+        }
+    }
+}
+
+template <typename T, int NT>
+size_t smem_bytes() {
+    using C = RowCfg<NT>;
+    return sizeof(cx<T>) * C::RPC * C::PADN + sizeof(double) * 32;
+}
+
+// Sets the dynamic shared-memory limit of the kernel; must run before any
+// launch of it (and outside stream capture).
+template <typename T, int NT>
+cudaError_t prepare_nt() {
+    cudaError_t e = cudaFuncSetAttribute(row_kernel<T, NT, 8>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem_bytes<T, NT>());
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(row_kernel<T, NT, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem_bytes<T, NT>());
+}
+
+template <typename T, int NT>
+cudaError_t launch_nt(const RowArgs<T> &a, cudaStream_t st) {
+    using C = RowCfg<NT>;
+    const size_t smem = smem_bytes<T, NT>();
+    const int grid = (a.nr + C::RPC - 1) / C::RPC;
+    if (grid == 0) return cudaSuccess;
+    // K = 8 (the photon number of 800 nm in air) gets unrolled powers
+    if (a.nl.K == 8)
+        row_kernel<T, NT, 8><<<grid, C::THREADS, smem, st>>>(a);
+    else
+        row_kernel<T, NT, 0><<<grid, C::THREADS, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t prepare_rows(int nt) {
+    switch (nt) {
+        case 2: return prepare_nt<T, 2>();
+        case 4: return prepare_nt<T, 4>();
+        case 8: return prepare_nt<T, 8>();
+        case 16: return prepare_nt<T, 16>();
+        case 32: return prepare_nt<T, 32>();
+        case 64: return prepare_nt<T, 64>();
+        case 128: return prepare_nt<T, 128>();
+        case 256: return prepare_nt<T, 256>();
+        case 512: return prepare_nt<T, 512>();
+        case 1024: return prepare_nt<T, 1024>();
+        case 2048: return prepare_nt<T, 2048>();
+        case 4096: return prepare_nt<T, 4096>();
+        case 8192: return prepare_nt<T, 8192>();
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+// Dispatch on Nt (one compiled kernel per power of two).
+template <typename T>
+cudaError_t launch_rows(const RowArgs<T> &a, int nt, cudaStream_t st) {
+    switch (nt) {
+        case 2: return launch_nt<T, 2>(a, st);
+        case 4: return launch_nt<T, 4>(a, st);
+        case 8: return launch_nt<T, 8>(a, st);
+        case 16: return launch_nt<T, 16>(a, st);
+        case 32: return launch_nt<T, 32>(a, st);
+        case 64: return launch_nt<T, 64>(a, st);
+        case 128: return launch_nt<T, 128>(a, st);
+        case 256: return launch_nt<T, 256>(a, st);
+        case 512: return launch_nt<T, 512>(a, st);
+        case 1024: return launch_nt<T, 1024>(a, st);
+        case 2048: return launch_nt<T, 2048>(a, st);
+        case 4096: return launch_nt<T, 4096>(a, st);
+        case 8192: return launch_nt<T, 8192>(a, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace fcn
