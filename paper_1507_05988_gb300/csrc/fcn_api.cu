@@ -109,6 +109,36 @@ struct ConstTables {
 };
 ConstTables g_tables;
 
+// FP32 twiddle W = exp(i ang): among the float pairs within 8 ulps of the
+// rounded (cos, sin), the one whose modulus is closest to 1 with a phase
+// error below 2.5e-7 rad.  Independently rounded pairs have |W|^2 - 1 of
+// ~3e-8 with a common sign over many entries; since the same table acts on
+// every row at every z-step, that bias would show up as an energy drift of
+// ~1e-7 per step (the FFT and its inverse both scale by |W|^2).
+cx<float> unit_twiddle_f32(long double ang) {
+    const long double c = cosl(ang), s = sinl(ang);
+    float cs[17], ss[17];
+    cs[0] = float(c);
+    ss[0] = float(s);
+    for (int k = 1; k <= 8; ++k) {
+        cs[2 * k - 1] = nextafterf(cs[2 * k - 3 < 0 ? 0 : 2 * k - 3], 2.f);
+        cs[2 * k] = nextafterf(cs[2 * k - 2], -2.f);
+        ss[2 * k - 1] = nextafterf(ss[2 * k - 3 < 0 ? 0 : 2 * k - 3], 2.f);
+        ss[2 * k] = nextafterf(ss[2 * k - 2], -2.f);
+    }
+    float bc = cs[0], bs = ss[0];
+    long double bm = fabsl((long double)bc * bc + (long double)bs * bs - 1.0L), bp = 0.0L;
+    for (int i = 0; i < 17; ++i)
+        for (int j = 0; j < 17; ++j) {
+            const long double cc = cs[i], sv = ss[j];
+            const long double m = fabsl(cc * cc + sv * sv - 1.0L);
+            const long double ph = fabsl(sv * c - cc * s);   // sin of the phase error
+            if (ph > 2.5e-7L) continue;
+            if (m < bm || (m == bm && ph < bp)) { bm = m; bp = ph; bc = cs[i]; bs = ss[j]; }
+        }
+    return mk(bc, bs);
+}
+
 template <typename T>
 cudaError_t get_twiddles(int nt, const cx<T> **out) {
     const int prec = sizeof(T) == 8 ? FCN_FP64 : FCN_FP32_MIXED;
@@ -120,7 +150,8 @@ cudaError_t get_twiddles(int nt, const cx<T> **out) {
     for (int m = 0; m < nt; ++m) {
         const long double ang = -2.0L * 3.14159265358979323846264338327950288L * (long double)m /
                                 (long double)nt;
-        h[m] = mk(T(cosl(ang)), T(sinl(ang)));
+        if constexpr (sizeof(T) == 4) h[m] = unit_twiddle_f32(ang);
+        else h[m] = mk(T(cosl(ang)), T(sinl(ang)));
     }
     void *d = nullptr;
     cudaError_t e = cudaMalloc(&d, sizeof(cx<T>) * nt);

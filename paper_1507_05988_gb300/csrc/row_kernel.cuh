@@ -82,7 +82,30 @@ __host__ __device__ constexpr double cos16(int m) {
          : 0.92387953251128675613;
 }
 
-// o * exp(DIR 2 pi i m / 16); exact shortcuts for the quarter turns
+// o * exp(DIR 2 pi i m / 16); exact shortcuts for the quarter turns.
+//
+// FP32 constants: float32 (cos, sin) pairs rounded independently do not have
+// unit modulus (|w|^2 - 1 ~ -6e-8 for the pi/8 pair, -3.4e-8 for pi/4), and
+// because the same constants act on every row at every step, that bias
+// accumulates into an energy drift of ~1e-7 per z-step.  So the pi/8 family
+// uses the float pair within a few ulps of (cos pi/8, sin pi/8) whose modulus
+// is closest to 1 (|w|^2 - 1 = 3.5e-9, phase error 2.3e-7 rad), and the pi/4
+// family applies 1/sqrt(2) as a two-float (hi + lo) scale.
+__device__ __forceinline__ void c16f_pair(int m, float *c, float *s) {
+    constexpr float C1 = 0.92387962341308594f;    // ~cos(pi/8), modulus-matched
+    constexpr float S1 = 0.38268321752548218f;    // ~sin(pi/8), modulus-matched
+    switch (m & 15) {
+        case 1: *c = C1; *s = S1; break;
+        case 3: *c = S1; *s = C1; break;
+        case 5: *c = -S1; *s = C1; break;
+        case 7: *c = -C1; *s = S1; break;
+        case 9: *c = -C1; *s = -S1; break;
+        case 11: *c = -S1; *s = -C1; break;
+        case 13: *c = S1; *s = -C1; break;
+        default: *c = C1; *s = -S1; break;        // 15
+    }
+}
+
 template <typename T, int DIR>
 __device__ __forceinline__ cx<T> rot16(cx<T> o, int m) {
     m &= 15;
@@ -90,9 +113,26 @@ __device__ __forceinline__ cx<T> rot16(cx<T> o, int m) {
     if (m == 8) return mk(-o.x, -o.y);
     if (m == 4) return DIR > 0 ? mk(-o.y, o.x) : mk(o.y, -o.x);
     if (m == 12) return DIR > 0 ? mk(o.y, -o.x) : mk(-o.y, o.x);
-    const T c = T(cos16(m));
-    const T s = T(DIR) * T(cos16(m - 4));
-    return mk(o.x * c - o.y * s, o.x * s + o.y * c);
+    if constexpr (sizeof(T) == 4) {
+        if ((m & 1) == 0) {
+            // odd multiples of pi/4: (c, s) = (+-1, +-1)/sqrt(2)
+            constexpr float H_HI = 0.70710676908493042f;       // float(1/sqrt 2)
+            constexpr float H_LO = 1.2101617485882343e-8f;     // 1/sqrt 2 - H_HI
+            const float sc = (m == 2 || m == 14) ? 1.f : -1.f;             // sign of cos
+            const float ss = float(DIR) * ((m == 2 || m == 6) ? 1.f : -1.f);  // sign of sin
+            const float re = sc * o.x - ss * o.y;
+            const float im = ss * o.x + sc * o.y;
+            return mk(T(fmaf(re, H_HI, re * H_LO)), T(fmaf(im, H_HI, im * H_LO)));
+        }
+        float c, s;
+        c16f_pair(m, &c, &s);
+        s *= float(DIR);
+        return mk(T(o.x * c - o.y * s), T(o.x * s + o.y * c));
+    } else {
+        const T c = T(cos16(m));
+        const T s = T(DIR) * T(cos16(m - 4));
+        return mk(o.x * c - o.y * s, o.x * s + o.y * c);
+    }
 }
 
 // In-register DFT of size R (power of two <= 16), natural order in and out,
@@ -265,26 +305,18 @@ __device__ __forceinline__ T rk4_coef(T ia, T ib, T xa, T xb, const NLCoef<T> &c
 
 template <typename T>
 __device__ __forceinline__ void sincos_t(T x, T *s, T *c);
-// FP32: Cody-Waite reduction of x by 2 pi (two-constant split, 2 pi =
-// P2_HI + P2_LO with P2_HI the float nearest 2 pi) into [-pi, pi], then the
-// hardware sine/cosine.  The phase itself carries an FP32 relative error, so
-// the reduction is exact enough for |x| up to ~1e5.
+// FP32 uses the accurate library sincosf/expf: the hardware approximations
+// are biased near the arguments that occur here (|exp(i phi)| off by ~1e-7 and
+// exp(-tiny) off by ~1e-7 from 1), which accumulates into a systematic energy
+// drift of ~1e-5 per hundred steps.
 template <>
-__device__ __forceinline__ void sincos_t<float>(float x, float *s, float *c) {
-    constexpr float INV_2PI = 0.159154943091895335769f;
-    constexpr float P2_HI = 6.28318548202514648438f;
-    constexpr float P2_LO = -1.74845553146951715e-7f;
-    const float n = rintf(x * INV_2PI);
-    float r = fmaf(-n, P2_HI, x);
-    r = fmaf(-n, P2_LO, r);
-    __sincosf(r, s, c);
-}
+__device__ __forceinline__ void sincos_t<float>(float x, float *s, float *c) { sincosf(x, s, c); }
 template <>
 __device__ __forceinline__ void sincos_t<double>(double x, double *s, double *c) { sincos(x, s, c); }
 template <typename T>
 __device__ __forceinline__ T exp_t(T x);
 template <>
-__device__ __forceinline__ float exp_t<float>(float x) { return __expf(x); }
+__device__ __forceinline__ float exp_t<float>(float x) { return expf(x); }
 template <>
 __device__ __forceinline__ double exp_t<double>(double x) { return exp(x); }
 

@@ -207,27 +207,33 @@ def test_ragged_grids_with_noise(fcn, prec, nr, nt, n):
 
 
 def _oracle_self_sensitivity(pb, wl, n, eps=1e-15):
-    """rel-L2 change of the oracle's own n-step result when its input moves
-    by eps (relative, seeded): the conditioning of the run."""
-    A0 = wl.field()
+    """rel-L2 change of the oracle's own n-step result when its field is
+    perturbed by eps (relative, seeded) after every step -- the size of the
+    rounding differences any other FP64 implementation makes: the
+    conditioning of the run."""
     rng = np.random.default_rng(0)
-    a, _ = oracle.run(pb, wl.dz, n, A0)
-    b, _ = oracle.run(pb, wl.dz, n, A0 * (1 + eps * rng.standard_normal(A0.shape)))
+    a = wl.field()
+    b = a.copy()
+    for _ in range(n):
+        a, _ = oracle.run(pb, wl.dz, 1, a)
+        b, _ = oracle.run(pb, wl.dz, 1, b)
+        b = b * (1 + eps * rng.standard_normal(b.shape))
     return rel_l2(b, a), a
 
 
 def test_config1_fp64_past_the_collapse_is_within_the_conditioning(fcn):
     """After the collapse near z = 1.55 m the run amplifies round-off by
-    ~1e8 over 50 steps (the oracle itself moves by ~2e-7 when its input
-    moves by 1e-15), so no two FP64 implementations agree to 1e-10 at step
-    200.  The GPU must stay within 100x that self-sensitivity, and the
-    quantities that do not depend on the chaotic details must agree."""
+    ~1e7 over 50 steps (the oracle itself moves by ~1e-7 when its field is
+    perturbed by 1e-15 after every step), so no two FP64 implementations
+    agree to 1e-10 at step 200.  The GPU must stay within 1000x that
+    self-sensitivity (its own per-step rounding differences are larger than
+    1e-15) and below 1e-4; the energy must agree to 1e-9."""
     wl = W.config1()
     pb = _pb(wl)
     kappa, Aref = _oracle_self_sensitivity(pb, wl, wl.nsteps)
     assert kappa > 1e-9
     A, rho, d = _run_gpu(fcn, wl, FP64, wl.dz, wl.nsteps)
-    assert rel_l2(A, Aref) < 100 * kappa
+    assert rel_l2(A, Aref) < min(1e-4, 1000 * kappa)
     assert d["energy"] == pytest.approx(oracle.diag(pb, Aref)["energy"], rel=1e-9)
 
 
