@@ -259,6 +259,38 @@ int fcn_op_cn_table(const fcn_grid *grid, const fcn_params *params, int32_t prec
 int fcn_op_cn(const fcn_grid *grid, const fcn_params *params, int32_t precision,
               double dz, const void *table, void *field, void *stream);
 
+/* ============ column stage for callers that cannot allocate ============
+ * There is no counterpart to this in the paper; it is a service of this
+ * library.  fcn_op_cn_table + fcn_op_cn need a pivot table in a device buffer
+ * that the caller allocates.  Some callers cannot do that: code that runs
+ * inside a framework whose caching allocator already owns the device memory
+ * (a raw cudaMalloc may then fail, and cudaFree synchronises the whole
+ * device, stalling every other stream), or a latency-bound loop that must
+ * never block on an allocation.  fcn_op_cn_noalloc does the same column
+ * stage (Eq. (matrix) solved for every frequency, in place on `field`) with
+ * its scratch -- the pivot table for this dz and the radial ratio tables --
+ * in one static device array of FCN_NOALLOC_SCRATCH_BYTES bytes built into
+ * the library.  It calls no cudaMalloc, cudaFree or allocating library
+ * routine.
+ *   - Size limit: Nr*(Nt/2+1) complex values (16 B in FCN_FP64, 8 B in
+ *     FCN_FP32_MIXED) plus 4*Nr reals must fit in the array; larger grids
+ *     return FCN_ERR_UNSUPPORTED before any GPU work.  Examples that fit:
+ *     Nr=128, Nt=256 (either precision); Nr=1024, Nt=1024 in FP32 only.
+ *   - Every GPU that loads the library holds the array until the process
+ *     exits.
+ *   - The first call on a device (with that device current) looks up the
+ *     array's device address; make that first call before any stream capture.
+ *   - All calls share the array and it keeps the last call's contents (each
+ *     call rewrites what it reads).  Calls whose kernels overlap on the GPU
+ *     (different streams or host threads) race on it: serialise them.
+ *   - field: device buffer in the working precision, frequency domain,
+ *     Nr*Nt complex values, updated in place.  stream: cudaStream_t.
+ *   - Errors: FCN_ERR_ARG (bad grid/params/dz/pointer), FCN_ERR_UNSUPPORTED
+ *     (grid too large for the array), FCN_ERR_CUDA. */
+#define FCN_NOALLOC_SCRATCH_BYTES (8u * 1024u * 1024u)
+int fcn_op_cn_noalloc(const fcn_grid *grid, const fcn_params *params, int32_t precision,
+                      double dz, void *field, void *stream);
+
 /* Library version string. */
 const char *fcn_version(void);
 

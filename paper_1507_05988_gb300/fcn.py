@@ -39,6 +39,7 @@ FCN_FP64 = 0
 FCN_FP32_MIXED = 1
 FCN_OP_IFFT, FCN_OP_NL, FCN_OP_NL2, FCN_OP_FFT, FCN_OP_RHO = 1, 2, 4, 8, 16
 FCN_MLP_NIN, FCN_MLP_NH, FCN_MLP_NPARAM = 6, 64, 4673
+FCN_NOALLOC_SCRATCH_BYTES = 8 * 1024 * 1024
 FCN_PROF_ROW_HEAD, FCN_PROF_ROW_MID, FCN_PROF_ROW_TAIL, FCN_PROF_COLUMN, FCN_PROF_KINDS = 0, 1, 2, 3, 4
 
 
@@ -101,6 +102,7 @@ _SIGS = {
     "fcn_cn_table_entries": (C.c_int64, [_G]),
     "fcn_op_cn_table": (C.c_int, [_G, _PR, C.c_int32, C.c_double, _P, _P]),
     "fcn_op_cn": (C.c_int, [_G, _PR, C.c_int32, C.c_double, _P, _P, _P]),
+    "fcn_op_cn_noalloc": (C.c_int, [_G, _PR, C.c_int32, C.c_double, _P, _P]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _fn = getattr(lib, _name)
