@@ -197,6 +197,20 @@ int fcn_get_profiles(fcn_ctx *ctx, int32_t pulse, double *power, double *fluence
 int fcn_get_state(fcn_ctx *ctx, int32_t pulse, double state[4]);
 int fcn_set_state(fcn_ctx *ctx, int32_t pulse, const double state[4]);
 
+/* ======================= kernel variants (autotuner) ======================= */
+/* The row stage has 3 occupancy variants (FP32, K = 8) and the column stage 4
+ * (chunk length x CTA size).  By default (-1) the first fcn_step of a grid
+ * times every variant on a scratch copy of the field and keeps the fastest
+ * per (precision, Nr, Nt) for the process; if the environment variable
+ * FCN_TUNE_CACHE names a file, choices are read from and appended to it.
+ * row_variant in -1..2 and col_variant in -1..3 force a variant (-1: tune).
+ * Drops the context's captured graphs.  Synchronises. */
+int fcn_set_variants(fcn_ctx *ctx, int32_t row_variant, int32_t col_variant);
+
+/* Variants in use for pulse `pulse` (out[0] row, out[1] column; -1 before
+ * the first step). */
+int fcn_get_variants(fcn_ctx *ctx, int32_t pulse, int32_t out[2]);
+
 /* ========================= kernel timing ========================= */
 /* Kernel kinds reported by fcn_profile_read. */
 #define FCN_PROF_ROW_HEAD  0   /* nonlinear half step + forward FFT               */

@@ -251,11 +251,11 @@ cn_kernel(ColArgs<T> a, int C) {
 }
 
 template <typename T, int L>
-cudaError_t launch_cn_l(const ColArgs<T> &a, cudaStream_t st) {
+cudaError_t launch_cn_l(const ColArgs<T> &a, int target, cudaStream_t st) {
     constexpr int CMIN = 32 / int(sizeof(cx<T>));   // one 32-byte sector of columns
     const int P = (a.nr + L - 1) / L;
     int C = CMIN;
-    while (C * 2 * P <= 256 && C * 2 <= 32) C *= 2;
+    while (C * 2 * P <= target && C * 2 <= 32) C *= 2;
     if (C > a.nt) C = a.nt;
     // whole warps: chunks beyond P are empty (identity maps)
     const int threads = ((C * P + 31) / 32) * 32;
@@ -268,10 +268,19 @@ cudaError_t launch_cn_l(const ColArgs<T> &a, cudaStream_t st) {
 
 }  // namespace
 
+// Variants: bit 0 selects the shorter chunk (more threads, fewer registers
+// per thread), bit 1 a target CTA size of 512 instead of 256 threads.  A
+// variant that does not fit (more than 512 threads) falls back to variant 0.
 template <typename T>
 cudaError_t launch_cn(const ColArgs<T> &a, cudaStream_t st) {
-    if constexpr (sizeof(T) == 4) return launch_cn_l<T, 16>(a, st);
-    else return launch_cn_l<T, 8>(a, st);
+    constexpr int LL = sizeof(T) == 4 ? 16 : 8;     // long chunk
+    constexpr int LS = LL / 2;                      // short chunk
+    const int target = (a.variant & 2) ? 512 : 256;
+    cudaError_t e = cudaErrorInvalidConfiguration;
+    if (a.variant & 1) e = launch_cn_l<T, LS>(a, target, st);
+    if (e == cudaErrorInvalidConfiguration) e = launch_cn_l<T, LL>(a, target, st);
+    if (e == cudaErrorInvalidConfiguration) e = launch_cn_l<T, LL>(a, 256, st);
+    return e;
 }
 
 template <typename T>

@@ -8,8 +8,11 @@
 
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <fstream>
 #include <map>
+#include <tuple>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -91,6 +94,9 @@ NLCoef<T> nl_coef(const fcn_grid &g, const fcn_params &p, double h) {
     n.inv_nt = T(1.0 / double(g.nt));
     n.rho_nt = T(p.rho_nt);
     n.K = p.K;
+    n.nkerr = 1;
+    for (int j = 0; j < 4; ++j)
+        if (p.n2j[j] != 0.0) n.nkerr = j + 1;
     n.flags = p.flags;
     return n;
 }
@@ -233,6 +239,8 @@ struct Pulse {
     double z = 0.0, dz_next = 0.0;
     int64_t steps = 0, rejected = 0;
     bool has_field = false;
+    int row_var = 0, col_var = 0;   // kernel variants in use
+    bool tuned = false;
     int64_t points() const { return (int64_t)g.nr * g.nt; }
 };
 
@@ -257,6 +265,7 @@ struct fcn_ctx {
     int64_t prof_n[FCN_PROF_KINDS] = {0};
     float *mlp = nullptr;             // device FP32 master weights (FCN_MLP_NPARAM)
     bool has_mlp = false;
+    int force_row = -1, force_col = -1;   // -1: autotune; else forced variant
 };
 
 namespace {
@@ -329,6 +338,7 @@ RowArgs<T> row_args(Pulse &pu, void *field, int ops, double dz) {
     a.stats = pu.stats;
     a.nr = pu.g.nr;
     a.ops = ops;
+    a.variant = pu.row_var;
     a.nl = nl_coef<T>(pu.g, pu.p, 0.5 * dz);
     return a;
 }
@@ -442,6 +452,112 @@ int run_block(fcn_ctx *ctx, int kind, double dz, const std::vector<const cx<T> *
     return FCN_OK;
 }
 
+// ---- autotuner: kernel variants per (precision, Nr, Nt) ----
+// Variants change register allocation (row stage) or the chunk length and
+// CTA size (column stage); all compute the same step, the column variants
+// with a different rounding order.  The first fcn_step of a grid times every
+// variant on a scratch copy of the field (a few launches each, CUDA events)
+// and keeps the fastest in a process-wide table, optionally persisted in the
+// text file named by FCN_TUNE_CACHE ("prec nr nt row col" per line).
+std::map<std::tuple<int, int, int>, std::pair<int, int>> g_tune;
+bool g_tune_loaded = false;
+
+void tune_cache_load() {
+    if (g_tune_loaded) return;
+    g_tune_loaded = true;
+    const char *path = std::getenv("FCN_TUNE_CACHE");
+    if (!path) return;
+    std::ifstream f(path);
+    int prec, nr, nt, rv, cv;
+    while (f >> prec >> nr >> nt >> rv >> cv)
+        if (rv >= 0 && rv < kRowVariants && cv >= 0 && cv < kColVariants)
+            g_tune[std::make_tuple(prec, nr, nt)] = {rv, cv};
+}
+
+void tune_cache_store(int prec, int nr, int nt, int rv, int cv) {
+    const char *path = std::getenv("FCN_TUNE_CACHE");
+    if (!path) return;
+    std::ofstream f(path, std::ios::app);
+    f << prec << " " << nr << " " << nt << " " << rv << " " << cv << "\n";
+}
+
+template <typename F>
+int time_launches(fcn_ctx *ctx, F &&launch, float *ms_out) {
+    for (int i = 0; i < 2; ++i) CK(launch(), "tuning warm-up");
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0), "event");
+    CK(cudaEventCreate(&e1), "event");
+    cudaEventRecord(e0, ctx->st);
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < 5 && e == cudaSuccess; ++i) e = launch();
+    cudaEventRecord(e1, ctx->st);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "tuning launch");
+    *ms_out = ms;
+    return FCN_OK;
+}
+
+template <typename T>
+int tune_pulse(fcn_ctx *ctx, Pulse &pu, const cx<T> *tab, double dz) {
+    const int prec = ctx->prec;
+    std::lock_guard<std::mutex> lk(g_mu);
+    tune_cache_load();
+    auto key = std::make_tuple(prec, pu.g.nr, pu.g.nt);
+    auto it = g_tune.find(key);
+    if (it == g_tune.end()) {
+        const size_t bytes = csize(prec) * pu.points();
+        if (!pu.work1) CK(cudaMalloc(&pu.work1, bytes), "tuning scratch");
+        CK(cudaMemcpyAsync(pu.work1, pu.field, bytes, cudaMemcpyDeviceToDevice, ctx->st), "tuning copy");
+        int best_r = 0, best_c = 0;
+        float best = 1e30f;
+        const int nrv = (sizeof(T) == 4 && pu.p.K == 8) ? kRowVariants : 1;
+        for (int v = 0; v < nrv; ++v) {
+            RowArgs<T> a = row_args<T>(pu, pu.work1, OPS_MID, dz);
+            a.variant = v;
+            float ms;
+            int rc = time_launches(ctx, [&] { return launch_rows<T>(a, pu.g.nt, ctx->st); }, &ms);
+            if (rc) return rc;
+            if (ms < best) { best = ms; best_r = v; }
+        }
+        best = 1e30f;
+        for (int v = 0; v < kColVariants; ++v) {
+            ColArgs<T> a = col_args<T>(pu, pu.work1, tab, dz);
+            a.variant = v;
+            float ms;
+            int rc = time_launches(ctx, [&] { return launch_cn<T>(a, ctx->st); }, &ms);
+            if (rc) return rc;
+            if (ms < best) { best = ms; best_c = v; }
+        }
+        it = g_tune.emplace(key, std::make_pair(best_r, best_c)).first;
+        tune_cache_store(prec, pu.g.nr, pu.g.nt, best_r, best_c);
+    }
+    pu.row_var = ctx->force_row >= 0 ? ctx->force_row : it->second.first;
+    pu.col_var = ctx->force_col >= 0 ? ctx->force_col : it->second.second;
+    pu.tuned = true;
+    return FCN_OK;
+}
+
+template <typename T>
+int ensure_tuned(fcn_ctx *ctx, const std::vector<const cx<T> *> &tabs, double dz) {
+    for (size_t i = 0; i < ctx->pulses.size(); ++i) {
+        Pulse &pu = ctx->pulses[i];
+        if (pu.tuned) continue;
+        if (ctx->force_row >= 0 && ctx->force_col >= 0) {
+            pu.row_var = ctx->force_row;
+            pu.col_var = ctx->force_col;
+            pu.tuned = true;
+            continue;
+        }
+        int rc = tune_pulse<T>(ctx, pu, tabs[i], dz);
+        if (rc) return rc;
+    }
+    return FCN_OK;
+}
+
 template <typename T>
 int step_impl(fcn_ctx *ctx, double dz, int64_t n, bool use_graph) {
     if (!(dz > 0) || !std::isfinite(dz)) return fail(ctx, FCN_ERR_ARG, "dz must be > 0 and finite");
@@ -452,6 +568,10 @@ int step_impl(fcn_ctx *ctx, double dz, int64_t n, bool use_graph) {
     std::vector<const cx<T> *> tabs(ctx->pulses.size());
     for (size_t i = 0; i < ctx->pulses.size(); ++i) {
         int rc = ensure_table<T>(ctx, ctx->pulses[i], dz, &tabs[i]);
+        if (rc) return rc;
+    }
+    {
+        int rc = ensure_tuned<T>(ctx, tabs, dz);
         if (rc) return rc;
     }
     int rc = run_block<T>(ctx, 0, dz, tabs, use_graph);
@@ -473,6 +593,11 @@ int substeps(fcn_ctx *ctx, Pulse &pu, void *f, double h, int count) {
     const cx<T> *tab = nullptr;
     int rc = ensure_table<T>(ctx, pu, h, &tab);
     if (rc) return rc;
+    if (!pu.tuned) {
+        std::vector<const cx<T> *> tabs(ctx->pulses.size(), tab);
+        rc = ensure_tuned<T>(ctx, tabs, h);
+        if (rc) return rc;
+    }
     CK(launch_rows<T>(row_args<T>(pu, f, OPS_HEAD, h), pu.g.nt, ctx->st), "head");
     for (int i = 0; i < count; ++i) {
         CK(launch_cn<T>(col_args<T>(pu, f, tab, h), ctx->st), "column");
@@ -485,6 +610,7 @@ int substeps(fcn_ctx *ctx, Pulse &pu, void *f, double h, int count) {
 template <typename T>
 int diag_impl(fcn_ctx *ctx, Pulse &pu, fcn_diag *out) {
     RowArgs<T> a = row_args<T>(pu, pu.field, OP_STATS | OP_FFT | OP_SPEC | OP_NOSTORE, 0.0);
+    a.variant = 0;
     CK(launch_rows<T>(a, pu.g.nt, ctx->st), "diagnostics row pass");
     CK(launch_reduce_stats(pu.stats, pu.g.nr, pu.red, ctx->st), "diagnostics reduction");
     CK(cudaMemcpyAsync(ctx->host_red, pu.red, sizeof(double) * 8, cudaMemcpyDeviceToHost, ctx->st),
@@ -839,6 +965,27 @@ int fcn_set_state(fcn_ctx *ctx, int32_t pulse, const double state[4]) {
     return FCN_OK;
 }
 
+int fcn_set_variants(fcn_ctx *ctx, int32_t row_variant, int32_t col_variant) {
+    if (!ctx) return FCN_ERR_ARG;
+    if (row_variant < -1 || row_variant >= kRowVariants || col_variant < -1 || col_variant >= kColVariants)
+        return fail(ctx, FCN_ERR_ARG, "variant out of range");
+    CK(cudaStreamSynchronize(ctx->st), "sync");
+    ctx->force_row = row_variant;
+    ctx->force_col = col_variant;
+    for (auto &pu : ctx->pulses) pu.tuned = false;
+    for (auto &kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
+    ctx->graphs.clear();
+    return FCN_OK;
+}
+
+int fcn_get_variants(fcn_ctx *ctx, int32_t pulse, int32_t out[2]) {
+    Pulse *pu = get_pulse(ctx, pulse);
+    if (!pu || !out) return fail(ctx, FCN_ERR_ARG, "bad pulse index or null output");
+    out[0] = pu->tuned ? pu->row_var : -1;
+    out[1] = pu->tuned ? pu->col_var : -1;
+    return FCN_OK;
+}
+
 int fcn_profile_enable(fcn_ctx *ctx, int32_t on) {
     if (!ctx) return FCN_ERR_ARG;
     CK(cudaStreamSynchronize(ctx->st), "profile sync");
@@ -891,7 +1038,7 @@ int fcn_op_rows(const fcn_grid *grid, const fcn_params *params, int32_t precisio
         CK(get_twiddles<double>(grid->nt, &tw), "twiddles");
         CK(prepare_rows<double>(grid->nt), "row kernel attributes");
         a.field = (cx<double> *)field; a.tw = tw; a.rho = (double *)rho; a.stats = nullptr;
-        a.nr = grid->nr; a.ops = ops; a.nl = nl_coef<double>(*grid, *params, dz_half);
+        a.nr = grid->nr; a.ops = ops; a.variant = 0; a.nl = nl_coef<double>(*grid, *params, dz_half);
         CK(launch_rows<double>(a, grid->nt, st), "row stage");
     } else {
         RowArgs<float> a;
@@ -899,7 +1046,7 @@ int fcn_op_rows(const fcn_grid *grid, const fcn_params *params, int32_t precisio
         CK(get_twiddles<float>(grid->nt, &tw), "twiddles");
         CK(prepare_rows<float>(grid->nt), "row kernel attributes");
         a.field = (cx<float> *)field; a.tw = tw; a.rho = (float *)rho; a.stats = nullptr;
-        a.nr = grid->nr; a.ops = ops; a.nl = nl_coef<float>(*grid, *params, dz_half);
+        a.nr = grid->nr; a.ops = ops; a.variant = 0; a.nl = nl_coef<float>(*grid, *params, dz_half);
         CK(launch_rows<float>(a, grid->nt, st), "row stage");
     }
     return FCN_OK;
@@ -951,14 +1098,14 @@ int fcn_op_cn(const fcn_grid *grid, const fcn_params *params, int32_t precision,
         CK(get_lohi<double>(grid->nr, &lo, &hi, &lo64, &hi64), "radial tables");
         ColArgs<double> a;
         a.field = (cx<double> *)field; a.invden = (const cx<double> *)table; a.lo = lo; a.hi = hi;
-        a.nr = grid->nr; a.nt = grid->nt; a.s = s; a.dk = dk;
+        a.nr = grid->nr; a.nt = grid->nt; a.s = s; a.dk = dk; a.variant = 0;
         CK(launch_cn<double>(a, (cudaStream_t)stream), "column stage");
     } else {
         const float *lo, *hi;
         CK(get_lohi<float>(grid->nr, &lo, &hi, &lo64, &hi64), "radial tables");
         ColArgs<float> a;
         a.field = (cx<float> *)field; a.invden = (const cx<float> *)table; a.lo = lo; a.hi = hi;
-        a.nr = grid->nr; a.nt = grid->nt; a.s = float(s); a.dk = float(dk);
+        a.nr = grid->nr; a.nt = grid->nt; a.s = float(s); a.dk = float(dk); a.variant = 0;
         CK(launch_cn<float>(a, (cudaStream_t)stream), "column stage");
     }
     return FCN_OK;

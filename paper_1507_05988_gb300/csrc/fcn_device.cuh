@@ -72,6 +72,7 @@ struct NLCoef {
     T inv_nt;   // 1 / Nt (applied after the inverse FFT)
     T rho_nt;   // rho = u rho_nt for the rho output
     int K;
+    int nkerr;  // number of leading Kerr orders in use (1..4; trailing zeros dropped)
     unsigned flags;
 };
 
@@ -97,6 +98,7 @@ struct RowArgs {
     double *stats;        // [nr][NSTAT] or null
     int nr;
     int ops;
+    int variant;          // occupancy variant (0..2), chosen by the autotuner
     NLCoef<T> nl;
 };
 
@@ -109,6 +111,7 @@ struct ColArgs {
     int nr, nt;
     T s;                     // dz / (4 k0 dr^2), 0 without diffraction
     T dk;                    // k'' dz/4 domega^2, 0 without dispersion: delta_q = dk q^2
+    int variant;             // 0..3: chunk length (long/short) x CTA size (256/512)
 };
 
 struct TableArgs {
@@ -126,6 +129,8 @@ template <typename T>
 cudaError_t prepare_rows(int nt);
 template <typename T>
 cudaError_t launch_cn(const ColArgs<T> &a, cudaStream_t st);
+constexpr int kRowVariants = 3;
+constexpr int kColVariants = 4;
 template <typename T>
 cudaError_t launch_cn_table(const TableArgs &a, cx<T> *table, cudaStream_t st);
 

@@ -116,6 +116,7 @@ int run(const fcn_grid &g, const fcn_params &p, double dz, void *field, cudaStre
     ca.nt = g.nt;
     ca.s = T(s);
     ca.dk = T(dk);
+    ca.variant = 0;
     e = launch_cn<T>(ca, st);
     if (e != cudaSuccess) return FCN_ERR_CUDA;
     return FCN_OK;

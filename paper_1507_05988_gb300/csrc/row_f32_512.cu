@@ -1,0 +1,10 @@
+// row_f32_512.cu -- float row-stage kernels for Nt = 512
+// (see row_kernel.cuh); split by Nt so the build compiles them in parallel.
+#include "row_kernel.cuh"
+
+namespace fcn {
+namespace rowimpl {
+template cudaError_t launch_nt<float, 512>(const RowArgs<float> &, cudaStream_t);
+template cudaError_t prepare_nt<float, 512>();
+}  // namespace rowimpl
+}  // namespace fcn

@@ -305,12 +305,45 @@ __device__ __forceinline__ T rk4_coef(T ia, T ib, T xa, T xb, const NLCoef<T> &c
 
 template <typename T>
 __device__ __forceinline__ void sincos_t(T x, T *s, T *c);
-// FP32 uses the accurate library sincosf/expf: the hardware approximations
-// are biased near the arguments that occur here (|exp(i phi)| off by ~1e-7 and
-// exp(-tiny) off by ~1e-7 from 1), which accumulates into a systematic energy
-// drift of ~1e-5 per hundred steps.
+// FP32 sine and cosine of a nonlinear phase (|x| is a few rad at most in
+// practice).  The hardware approximations are biased near the arguments that
+// occur here (|exp(i phi)| off by ~1e-7), which accumulates into an energy
+// drift, so this is an accurate evaluation written from the series:
+// Cody & Waite's reduction x = n pi/2 + r with pi/2 split into two floats
+// (the product n*PIO2_HI is exact inside the FMA), then Taylor polynomials
+// of degree 9 (sin) and 10 (cos) on |r| <= pi/4, whose truncation errors are
+// below 2e-9 and 1.2e-10 -- under half an ulp.  Arguments beyond 1e4 rad,
+// where the two-float reduction loses digits, go to the library.
 template <>
-__device__ __forceinline__ void sincos_t<float>(float x, float *s, float *c) { sincosf(x, s, c); }
+__device__ __forceinline__ void sincos_t<float>(float x, float *s, float *c) {
+    if (fabsf(x) > 1.0e4f) {
+        sincosf(x, s, c);
+        return;
+    }
+    constexpr float TWO_OVER_PI = 0.636619772367581343076f;
+    constexpr float PIO2_HI = 1.57079637050628662109f;       // float nearest pi/2
+    constexpr float PIO2_LO = -4.37113900018624283e-8f;       // pi/2 - PIO2_HI
+    const float n = rintf(x * TWO_OVER_PI);
+    float r = fmaf(-n, PIO2_HI, x);
+    r = fmaf(-n, PIO2_LO, r);
+    const float r2 = r * r;
+    // sin r = r - r^3/3! + r^5/5! - r^7/7! + r^9/9!
+    float ps = fmaf(r2, 2.75573192239858906526e-6f, -1.98412698412698412698e-4f);
+    ps = fmaf(r2, ps, 8.33333333333333333333e-3f);
+    ps = fmaf(r2, ps, -1.66666666666666666667e-1f);
+    const float sr = fmaf(r * r2, ps, r);
+    // cos r = 1 - r^2/2! + r^4/4! - r^6/6! + r^8/8! - r^10/10!
+    float pc = fmaf(r2, -2.75573192239858906526e-7f, 2.48015873015873015873e-5f);
+    pc = fmaf(r2, pc, -1.38888888888888888889e-3f);
+    pc = fmaf(r2, pc, 4.16666666666666666667e-2f);
+    pc = fmaf(r2, pc, -0.5f);
+    const float cr = fmaf(r2, pc, 1.0f);
+    const int q = int(n) & 3;
+    const float ss = (q & 1) ? cr : sr;
+    const float cc = (q & 1) ? sr : cr;
+    *s = (q & 2) ? -ss : ss;
+    *c = ((q + 1) & 2) ? -cc : cc;
+}
 template <>
 __device__ __forceinline__ void sincos_t<double>(double x, double *s, double *c) { sincos(x, s, c); }
 template <typename T>
@@ -324,8 +357,12 @@ __device__ __forceinline__ double exp_t<double>(double x) { return exp(x); }
 template <typename T>
 __device__ __forceinline__ cx<T> nl_apply(cx<T> a, T ih, T ihKm1, T u, const NLCoef<T> &c) {
     T phase = T(0), loss = T(0);
-    if (c.flags & PH_KERR)
-        phase = ih * (c.kerr[0] + ih * (c.kerr[1] + ih * (c.kerr[2] + ih * c.kerr[3])));
+    if (c.flags & PH_KERR) {
+        // Horner over the Kerr orders in use (c.nkerr is uniform over the launch)
+        T poly = c.kerr[c.nkerr - 1];
+        for (int j = c.nkerr - 2; j >= 0; --j) poly = c.kerr[j] + ih * poly;
+        phase = ih * poly;
+    }
     if (c.flags & PH_PLASMA) phase -= c.plasma * u;
     if (c.flags & PH_MPI) {
         loss = c.loss * ihKm1;
@@ -470,8 +507,10 @@ __device__ __forceinline__ double row_max(double x, int t, double *scr, int rloc
     return x;
 }
 
-template <typename T, int NT, int KT>
-__global__ void __launch_bounds__(RowCfg<NT>::THREADS)
+// MB: minimum resident CTAs per SM requested from the compiler (register cap
+// 64K / (MB * THREADS)); the autotuner picks it per (precision, Nt).
+template <typename T, int NT, int KT, int MB>
+__global__ void __launch_bounds__(RowCfg<NT>::THREADS, MB)
 row_kernel(RowArgs<T> a) {
     using C = RowCfg<NT>;
     constexpr int E = C::E;
@@ -611,6 +650,10 @@ row_kernel(RowArgs<T> a) {
     }
 }
 
+}  // namespace
+
+namespace rowimpl {
+
 template <typename T, int NT>
 size_t smem_bytes() {
     using C = RowCfg<NT>;
@@ -619,14 +662,30 @@ size_t smem_bytes() {
 
 // Sets the dynamic shared-memory limit of the kernel; must run before any
 // launch of it (and outside stream capture).
+// Occupancy variants: v = 0 is the compiler's natural allocation; v = 1, 2
+// ask for 3 and 4 CTAs of 256 threads per SM (80 and 64 registers), or 2 CTAs
+// of 512 threads for Nt = 8192.  Only FP32 with K = 8 and Nt >= 512 has
+// variants (smaller rows are cheap; their variants map to v = 0).
+template <int NT>
+constexpr int mb_of(int v) {
+    return RowCfg<NT>::THREADS >= 512 ? (v == 0 ? 1 : 2) : (v == 0 ? 1 : (v == 1 ? 3 : 4));
+}
+
+template <typename T, int NT, int KT, int MB>
+cudaError_t set_smem_attr() {
+    return cudaFuncSetAttribute(row_kernel<T, NT, KT, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem_bytes<T, NT>());
+}
+
 template <typename T, int NT>
 cudaError_t prepare_nt() {
-    cudaError_t e = cudaFuncSetAttribute(row_kernel<T, NT, 8>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem_bytes<T, NT>());
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(row_kernel<T, NT, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem_bytes<T, NT>());
+    cudaError_t e = set_smem_attr<T, NT, 0, 1>();
+    if (e == cudaSuccess) e = set_smem_attr<T, NT, 8, 1>();
+    if constexpr (sizeof(T) == 4 && NT >= 512) {
+        if (e == cudaSuccess) e = set_smem_attr<T, NT, 8, mb_of<NT>(1)>();
+        if (e == cudaSuccess) e = set_smem_attr<T, NT, 8, mb_of<NT>(2)>();
+    }
+    return e;
 }
 
 template <typename T, int NT>
@@ -636,54 +695,21 @@ cudaError_t launch_nt(const RowArgs<T> &a, cudaStream_t st) {
     const int grid = (a.nr + C::RPC - 1) / C::RPC;
     if (grid == 0) return cudaSuccess;
     // K = 8 (the photon number of 800 nm in air) gets unrolled powers
-    if (a.nl.K == 8)
-        row_kernel<T, NT, 8><<<grid, C::THREADS, smem, st>>>(a);
-    else
-        row_kernel<T, NT, 0><<<grid, C::THREADS, smem, st>>>(a);
+    if (a.nl.K != 8) {
+        row_kernel<T, NT, 0, 1><<<grid, C::THREADS, smem, st>>>(a);
+    } else if constexpr (sizeof(T) == 4 && NT >= 512) {
+        if (a.variant == 1)
+            row_kernel<T, NT, 8, mb_of<NT>(1)><<<grid, C::THREADS, smem, st>>>(a);
+        else if (a.variant == 2)
+            row_kernel<T, NT, 8, mb_of<NT>(2)><<<grid, C::THREADS, smem, st>>>(a);
+        else
+            row_kernel<T, NT, 8, 1><<<grid, C::THREADS, smem, st>>>(a);
+    } else {
+        row_kernel<T, NT, 8, 1><<<grid, C::THREADS, smem, st>>>(a);
+    }
     return cudaGetLastError();
 }
 
-}  // namespace
-
-template <typename T>
-cudaError_t prepare_rows(int nt) {
-    switch (nt) {
-        case 2: return prepare_nt<T, 2>();
-        case 4: return prepare_nt<T, 4>();
-        case 8: return prepare_nt<T, 8>();
-        case 16: return prepare_nt<T, 16>();
-        case 32: return prepare_nt<T, 32>();
-        case 64: return prepare_nt<T, 64>();
-        case 128: return prepare_nt<T, 128>();
-        case 256: return prepare_nt<T, 256>();
-        case 512: return prepare_nt<T, 512>();
-        case 1024: return prepare_nt<T, 1024>();
-        case 2048: return prepare_nt<T, 2048>();
-        case 4096: return prepare_nt<T, 4096>();
-        case 8192: return prepare_nt<T, 8192>();
-        default: return cudaErrorInvalidValue;
-    }
-}
-
-// Dispatch on Nt (one compiled kernel per power of two).
-template <typename T>
-cudaError_t launch_rows(const RowArgs<T> &a, int nt, cudaStream_t st) {
-    switch (nt) {
-        case 2: return launch_nt<T, 2>(a, st);
-        case 4: return launch_nt<T, 4>(a, st);
-        case 8: return launch_nt<T, 8>(a, st);
-        case 16: return launch_nt<T, 16>(a, st);
-        case 32: return launch_nt<T, 32>(a, st);
-        case 64: return launch_nt<T, 64>(a, st);
-        case 128: return launch_nt<T, 128>(a, st);
-        case 256: return launch_nt<T, 256>(a, st);
-        case 512: return launch_nt<T, 512>(a, st);
-        case 1024: return launch_nt<T, 1024>(a, st);
-        case 2048: return launch_nt<T, 2048>(a, st);
-        case 4096: return launch_nt<T, 4096>(a, st);
-        case 8192: return launch_nt<T, 8192>(a, st);
-        default: return cudaErrorInvalidValue;
-    }
-}
+}  // namespace rowimpl
 
 }  // namespace fcn

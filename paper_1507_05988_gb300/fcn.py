@@ -94,6 +94,8 @@ _SIGS = {
     "fcn_get_profiles": (C.c_int, [_CTX, C.c_int32, _D, _D]),
     "fcn_get_state": (C.c_int, [_CTX, C.c_int32, _D]),
     "fcn_set_state": (C.c_int, [_CTX, C.c_int32, _D]),
+    "fcn_set_variants": (C.c_int, [_CTX, C.c_int32, C.c_int32]),
+    "fcn_get_variants": (C.c_int, [_CTX, C.c_int32, C.POINTER(C.c_int32)]),
     "fcn_profile_enable": (C.c_int, [_CTX, C.c_int32]),
     "fcn_profile_read": (C.c_int, [_CTX, _D, C.POINTER(C.c_int64), C.c_int32]),
     "fcn_mlp_set": (C.c_int, [_CTX, _F]),
@@ -233,6 +235,14 @@ class Solver:
         s = np.zeros(4, np.float64)
         check(fcn_get_state(self.ctx, pulse, s.ctypes.data_as(_D)), self.ctx)
         return s
+
+    def set_variants(self, row: int = -1, col: int = -1):
+        check(fcn_set_variants(self.ctx, int(row), int(col)), self.ctx)
+
+    def variants(self, pulse: int = 0):
+        out = (C.c_int32 * 2)()
+        check(fcn_get_variants(self.ctx, pulse, out), self.ctx)
+        return out[0], out[1]
 
     def profile(self, on: bool):
         check(fcn_profile_enable(self.ctx, 1 if on else 0), self.ctx)

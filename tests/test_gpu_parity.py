@@ -361,3 +361,38 @@ def test_adaptive_step_doubling_matches_oracle_controller(fcn, prec):
         assert rel_l2(A, Aref) < 1e-10
     else:
         assert rel_l2(A, Aref) < 1e-4
+
+
+# ------------------------------------------------- autotuner and variants
+
+@pytest.mark.parametrize("prec", [FP64, FP32])
+@pytest.mark.parametrize("row_v", [0, 1, 2])
+@pytest.mark.parametrize("col_v", [0, 1, 2, 3])
+def test_every_kernel_variant_matches_oracle(fcn, prec, row_v, col_v):
+    """Every variant the autotuner can pick computes the same step."""
+    wl = W.small(130, 1024, p_over_pcr=4.0, noise_seed=6).with_(n2j=(W.N2, W.N4, 0, 0))
+    pb = _pb(wl)
+    s = fcn.Solver(wl.physics(), precision=prec)
+    s.set_variants(row_v, col_v)
+    s.set_field(wl.field())
+    s.step(5e-3, 4)
+    A = s.get_field()
+    assert s.variants() == (row_v, col_v)
+    s.close()
+    Aref, _ = oracle.run(pb, 5e-3, 4, wl.field())
+    assert rel_l2(A, Aref) < (1e-10 if prec == FP64 else 1e-5)
+
+
+def test_autotuner_picks_a_valid_variant_and_stays_correct(fcn):
+    wl = W.small(256, 4096, p_over_pcr=4.0, noise_seed=8).with_(n2j=(W.N2, W.N4, 0, 0))
+    pb = _pb(wl)
+    s = fcn.Solver(wl.physics(), precision=FP32)
+    assert s.variants() == (-1, -1)
+    s.set_field(wl.field())
+    s.step(4e-3, 3)
+    rv, cv = s.variants()
+    assert 0 <= rv < 3 and 0 <= cv < 4
+    A = s.get_field()
+    s.close()
+    Aref, _ = oracle.run(pb, 4e-3, 3, wl.field())
+    assert rel_l2(A, Aref) < 1e-5
