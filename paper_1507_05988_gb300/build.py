@@ -21,6 +21,9 @@ BUILD = os.path.join(ROOT, "_build", "fcn")
 LIB = os.path.join(HERE, "libfcn_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
+if os.environ.get("FCN_CHECKED") == "1":      # self-checking kernels (range checks)
+    FLAGS.append("-DFCN_CHECKED")
+    BUILD = BUILD + "_checked"
 
 
 def nvcc() -> str:

@@ -61,9 +61,9 @@ __global__ void cn_table_kernel(TableArgs a, cx<T> *table) {
             b = mk(1.0, 4.0 * s - delta);
             c = mk(0.0, -4.0 * s);
         } else if (j < a.nr - 1) {
-            aa = mk(0.0, -s * a.lo[j]);
+            aa = mk(0.0, -s * a.lo[FCN_IDX(j, a.nr, 31)]);
             b = mk(1.0, 2.0 * s - delta);
-            c = mk(0.0, -s * a.hi[j]);
+            c = mk(0.0, -s * a.hi[FCN_IDX(j, a.nr, 32)]);
         } else {
             aa = mk(0.0, 0.0);
             b = mk(1.0, 0.0);
@@ -72,7 +72,7 @@ __global__ void cn_table_kernel(TableArgs a, cx<T> *table) {
         const cx<double> den = b - cmul(aa, cp);
         const cx<double> inv = crecip(den);
         cp = cmul(c, inv);
-        table[(size_t)j * nq + q] = mk(T(inv.x), T(inv.y));
+        table[FCN_IDX((size_t)j * nq + q, (size_t)a.nr * nq, 30)] = mk(T(inv.x), T(inv.y));
     }
 }
 
@@ -115,8 +115,8 @@ __device__ __forceinline__ cx<T> chunk_scan(cx<T> A, cx<T> B, int C, int col, cx
     cx<T> wc = czero<T>();
     if (nw > 1) {
         if (REV ? (ciw == 0) : (ciw == cpw - 1)) {
-            smA[w * C + col] = A;
-            smB[w * C + col] = B;
+            smA[FCN_IDX(w * C + col, nw * C, 38)] = A;
+            smB[FCN_IDX(w * C + col, nw * C, 39)] = B;
         }
         __syncthreads();
         if ((int)threadIdx.x < C) {
@@ -124,18 +124,18 @@ __device__ __forceinline__ cx<T> chunk_scan(cx<T> A, cx<T> B, int C, int col, cx
             cx<T> c = czero<T>();
             if (!REV) {
                 for (int k = 0; k < nw; ++k) {
-                    smC[k * C + c0] = c;
-                    c = cmul(smA[k * C + c0], c) + smB[k * C + c0];
+                    smC[FCN_IDX(k * C + c0, nw * C, 40)] = c;
+                    c = cmul(smA[FCN_IDX(k * C + c0, nw * C, 41)], c) + smB[FCN_IDX(k * C + c0, nw * C, 42)];
                 }
             } else {
                 for (int k = nw - 1; k >= 0; --k) {
-                    smC[k * C + c0] = c;
-                    c = cmul(smA[k * C + c0], c) + smB[k * C + c0];
+                    smC[FCN_IDX(k * C + c0, nw * C, 40)] = c;
+                    c = cmul(smA[FCN_IDX(k * C + c0, nw * C, 41)], c) + smB[FCN_IDX(k * C + c0, nw * C, 42)];
                 }
             }
         }
         __syncthreads();
-        wc = smC[w * C + col];
+        wc = smC[FCN_IDX(w * C + col, nw * C, 43)];
     }
     return cmul(Ae, wc) + Be;
 }
@@ -170,13 +170,13 @@ cn_kernel(ColArgs<T> a, int C) {
 #pragma unroll
     for (int k = 0; k < L + 2; ++k) {
         const int j = j0 - 1 + k;
-        x[k] = (j >= 0 && j < nr) ? colp[(size_t)j * nt] : czero<T>();
+        x[k] = (j >= 0 && j < nr) ? a.field[FCN_IDX((size_t)j * nt + q, (size_t)nr * nt, 33)] : czero<T>();
     }
     cx<T> inv[L];
 #pragma unroll
     for (int k = 0; k < L; ++k) {
         const int j = j0 + k;
-        inv[k] = (j < nr) ? ldg_cx(&a.invden[(size_t)j * nq + qq]) : czero<T>();
+        inv[k] = (j < nr) ? ldg_cx(&a.invden[FCN_IDX((size_t)j * nq + qq, (size_t)nr * nq, 34)]) : czero<T>();
     }
 
     // forward sweep, pass 1: beta_j and the chunk map y_end = PA y_in + PB
@@ -193,7 +193,7 @@ cn_kernel(ColArgs<T> a, int C) {
                 rhs = mk(x[k + 1].x - w.y, x[k + 1].y + w.x);
                 alpha = czero<T>();
             } else if (j < nr - 1) {
-                const T sl = s * a.lo[j], sh = s * a.hi[j];
+                const T sl = s * a.lo[FCN_IDX(j, nr, 35)], sh = s * a.hi[FCN_IDX(j, nr, 36)];
                 const cx<T> w = mk(sl * x[k].x + sh * x[k + 2].x - g1 * x[k + 1].x,
                                    sl * x[k].y + sh * x[k + 2].y - g1 * x[k + 1].y);
                 rhs = mk(x[k + 1].x - w.y, x[k + 1].y + w.x);
@@ -244,7 +244,7 @@ cn_kernel(ColArgs<T> a, int C) {
                 const cx<T> gamma = (j == 0) ? cmul_i(inv[k], T(4) * s)
                                   : (j < nr - 1) ? cmul_i(inv[k], s * a.hi[j]) : czero<T>();
                 xn = cmul(gamma, xn) + y[k];
-                colp[(size_t)j * nt] = xn;
+                a.field[FCN_IDX((size_t)j * nt + q, (size_t)nr * nt, 37)] = xn;
             }
         }
     }

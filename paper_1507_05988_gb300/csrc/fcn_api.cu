@@ -509,14 +509,20 @@ int tune_pulse(fcn_ctx *ctx, Pulse &pu, const cx<T> *tab, double dz) {
     auto key = std::make_tuple(prec, pu.g.nr, pu.g.nt);
     auto it = g_tune.find(key);
     if (it == g_tune.end()) {
+        // a private scratch copy: the context's work buffers may hold state
         const size_t bytes = csize(prec) * pu.points();
-        if (!pu.work1) CK(cudaMalloc(&pu.work1, bytes), "tuning scratch");
-        CK(cudaMemcpyAsync(pu.work1, pu.field, bytes, cudaMemcpyDeviceToDevice, ctx->st), "tuning copy");
+        void *scratch = nullptr;
+        CK(cudaMalloc(&scratch, bytes), "tuning scratch");
+        struct Free {
+            void *p;
+            ~Free() { cudaFree(p); }
+        } guard{scratch};
+        CK(cudaMemcpyAsync(scratch, pu.field, bytes, cudaMemcpyDeviceToDevice, ctx->st), "tuning copy");
         int best_r = 0, best_c = 0;
         float best = 1e30f;
         const int nrv = (sizeof(T) == 4 && pu.p.K == 8) ? kRowVariants : 1;
         for (int v = 0; v < nrv; ++v) {
-            RowArgs<T> a = row_args<T>(pu, pu.work1, OPS_MID, dz);
+            RowArgs<T> a = row_args<T>(pu, scratch, OPS_MID, dz);
             a.variant = v;
             float ms;
             int rc = time_launches(ctx, [&] { return launch_rows<T>(a, pu.g.nt, ctx->st); }, &ms);
@@ -525,13 +531,14 @@ int tune_pulse(fcn_ctx *ctx, Pulse &pu, const cx<T> *tab, double dz) {
         }
         best = 1e30f;
         for (int v = 0; v < kColVariants; ++v) {
-            ColArgs<T> a = col_args<T>(pu, pu.work1, tab, dz);
+            ColArgs<T> a = col_args<T>(pu, scratch, tab, dz);
             a.variant = v;
             float ms;
             int rc = time_launches(ctx, [&] { return launch_cn<T>(a, ctx->st); }, &ms);
             if (rc) return rc;
             if (ms < best) { best = ms; best_c = v; }
         }
+        CK(cudaStreamSynchronize(ctx->st), "tuning sync");
         it = g_tune.emplace(key, std::make_pair(best_r, best_c)).first;
         tune_cache_store(prec, pu.g.nr, pu.g.nt, best_r, best_c);
     }
@@ -645,6 +652,14 @@ int propagate_impl(fcn_ctx *ctx, double z_end, double dz0, double rtol, double d
         return fail(ctx, FCN_ERR_ARG, "bad adaptive arguments");
     if (controller != 0) return fail(ctx, FCN_ERR_UNSUPPORTED, "controller not available");
     const size_t bytes = csize(ctx->prec) * pu.points();
+    if (!pu.tuned) {
+        const cx<T> *tab = nullptr;
+        int rc = ensure_table<T>(ctx, pu, dz0, &tab);
+        if (rc) return rc;
+        std::vector<const cx<T> *> tabs(1, tab);
+        rc = ensure_tuned<T>(ctx, tabs, dz0);
+        if (rc) return rc;
+    }
     if (!pu.work1) CK(cudaMalloc(&pu.work1, bytes), "work buffer");
     if (!pu.work2) CK(cudaMalloc(&pu.work2, bytes), "work buffer");
     fcn_stats s;

@@ -5,6 +5,27 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+// Optional self-checking build (-DFCN_CHECKED, used to locate memory faults):
+// every indexed access in the kernels goes through FCN_IDX, which prints the
+// site and index of the first violations and redirects the access to index 0
+// instead of leaving the buffer.  Off by default (FCN_IDX is the identity).
+#ifdef FCN_CHECKED
+#include <cstdio>
+static __device__ int g_fcn_reports;
+__device__ __forceinline__ long long fcn_chk(long long i, long long n, int site) {
+    if (i < 0 || i >= n) {
+        if (atomicAdd(&g_fcn_reports, 1) < 16)
+            printf("FCN_CHECK site %d index %lld size %lld block %d thread %d\n", site, i, n,
+                   (int)blockIdx.x, (int)threadIdx.x);
+        return 0;
+    }
+    return i;
+}
+#define FCN_IDX(i, n, site) fcn_chk((long long)(i), (long long)(n), (site))
+#else
+#define FCN_IDX(i, n, site) (i)
+#endif
+
 namespace fcn {
 
 // Interleaved complex value; 8-byte aligned for float, 16 for double so that

@@ -175,7 +175,7 @@ __device__ __forceinline__ void pass_compute(cx<T> (&v)[RowCfg<NT>::E], int t,
             const int k = j & (NS - 1);
 #pragma unroll
             for (int r = 1; r < R; ++r) {
-                cx<T> w = ldg_cx(&tw[r * k * STRIDE]);
+                cx<T> w = ldg_cx(&tw[FCN_IDX(r * k * STRIDE, NT, 3)]);
                 if (DIR > 0) w.y = -w.y;
                 v[i * R + r] = cmul(v[i * R + r], w);
             }
@@ -193,7 +193,7 @@ __device__ __forceinline__ void pass_load(cx<T> (&v)[RowCfg<NT>::E], const cx<T>
     for (int i = 0; i < NB; ++i) {
         const int j = t + C::TPR * i;
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[i * R + r] = S[pidx(j + r * (NT / R), NT)];
+        for (int r = 0; r < R; ++r) v[i * R + r] = S[FCN_IDX(pidx(j + r * (NT / R), NT), C::PADN, 1)];
     }
 }
 
@@ -208,7 +208,7 @@ __device__ __forceinline__ void pass_store(const cx<T> (&v)[RowCfg<NT>::E], cx<T
         const int j = t + C::TPR * i;
         const int base = (j / NS) * NS * R + (j & (NS - 1));
 #pragma unroll
-        for (int r = 0; r < R; ++r) S[pidx(base + r * NS, NT)] = v[i * R + r];
+        for (int r = 0; r < R; ++r) S[FCN_IDX(pidx(base + r * NS, NT), C::PADN, 2)] = v[i * R + r];
     }
 }
 
@@ -358,9 +358,16 @@ template <typename T>
 __device__ __forceinline__ cx<T> nl_apply(cx<T> a, T ih, T ihKm1, T u, const NLCoef<T> &c) {
     T phase = T(0), loss = T(0);
     if (c.flags & PH_KERR) {
-        // Horner over the Kerr orders in use (c.nkerr is uniform over the launch)
-        T poly = c.kerr[c.nkerr - 1];
-        for (int j = c.nkerr - 2; j >= 0; --j) poly = c.kerr[j] + ih * poly;
+        // Horner over the Kerr orders in use (c.nkerr is uniform over the
+        // launch); the coefficients are read by constant index so that the
+        // parameter block stays in the constant bank (no local copy)
+        T poly;
+        switch (c.nkerr) {
+            case 4: poly = c.kerr[0] + ih * (c.kerr[1] + ih * (c.kerr[2] + ih * c.kerr[3])); break;
+            case 3: poly = c.kerr[0] + ih * (c.kerr[1] + ih * c.kerr[2]); break;
+            case 2: poly = c.kerr[0] + ih * c.kerr[1]; break;
+            default: poly = c.kerr[0]; break;
+        }
         phase = ih * poly;
     }
     if (c.flags & PH_PLASMA) phase -= c.plasma * u;
@@ -394,11 +401,11 @@ __device__ __forceinline__ T row_scan_exclusive(T tot, int t, double *scr, int r
     if (C::WARPS_PER_ROW > 1) {
         const int w = t >> 5;
         double *ws = scr + rloc * C::WARPS_PER_ROW;
-        if (lane == 31) ws[w] = double(incl);
+        if (lane == 31) scr[FCN_IDX(rloc * C::WARPS_PER_ROW + w, 32, 14)] = double(incl);
         __syncthreads();
         if (t < 32) {
             // FP64 exclusive scan of the warp totals of this row (<= 16)
-            double x = (lane < C::WARPS_PER_ROW) ? ws[lane] : 0.0;
+            double x = (lane < C::WARPS_PER_ROW) ? scr[FCN_IDX(rloc * C::WARPS_PER_ROW + lane, 32, 15)] : 0.0;
             double in = x;
 #pragma unroll
             for (int d = 1; d < 32; d <<= 1) {
@@ -408,10 +415,10 @@ __device__ __forceinline__ T row_scan_exclusive(T tot, int t, double *scr, int r
             double ex = __shfl_up_sync(0xffffffffu, in, 1, 32);
             if (lane == 0) ex = 0.0;
             __syncwarp();
-            if (lane < C::WARPS_PER_ROW) ws[lane] = ex;
+            if (lane < C::WARPS_PER_ROW) scr[FCN_IDX(rloc * C::WARPS_PER_ROW + lane, 32, 16)] = ex;
         }
         __syncthreads();
-        const T wc = T(ws[w]);
+        const T wc = T(scr[FCN_IDX(rloc * C::WARPS_PER_ROW + w, 32, 17)]);
         __syncthreads();
         excl = uplus(wc, excl);
     }
@@ -474,11 +481,11 @@ __device__ __forceinline__ double row_sum(double x, int t, double *scr, int rloc
     if (C::WARPS_PER_ROW > 1) {
         double *ws = scr + rloc * C::WARPS_PER_ROW;
         __syncthreads();
-        if ((t & 31) == 0) ws[t >> 5] = x;
+        if ((t & 31) == 0) scr[FCN_IDX(rloc * C::WARPS_PER_ROW + (t >> 5), 32, 18)] = x;
         __syncthreads();
         if (t == 0) {
             double s = 0.0;
-            for (int w = 0; w < C::WARPS_PER_ROW; ++w) s += ws[w];
+            for (int w = 0; w < C::WARPS_PER_ROW; ++w) s += scr[FCN_IDX(rloc * C::WARPS_PER_ROW + w, 32, 20)];
             x = s;
         }
         __syncthreads();
@@ -495,11 +502,11 @@ __device__ __forceinline__ double row_max(double x, int t, double *scr, int rloc
     if (C::WARPS_PER_ROW > 1) {
         double *ws = scr + rloc * C::WARPS_PER_ROW;
         __syncthreads();
-        if ((t & 31) == 0) ws[t >> 5] = x;
+        if ((t & 31) == 0) scr[FCN_IDX(rloc * C::WARPS_PER_ROW + (t >> 5), 32, 18)] = x;
         __syncthreads();
         if (t == 0) {
-            double s = ws[0];
-            for (int w = 1; w < C::WARPS_PER_ROW; ++w) s = fmax(s, ws[w]);
+            double s = scr[FCN_IDX(rloc * C::WARPS_PER_ROW, 32, 21)];
+            for (int w = 1; w < C::WARPS_PER_ROW; ++w) s = fmax(s, scr[FCN_IDX(rloc * C::WARPS_PER_ROW + w, 32, 22)]);
             x = s;
         }
         __syncthreads();
@@ -518,6 +525,14 @@ row_kernel(RowArgs<T> a) {
     cx<T> *S_all = reinterpret_cast<cx<T> *>(smem_raw);
     double *scr = reinterpret_cast<double *>(S_all + C::RPC * C::PADN);
 
+#ifdef FCN_CHECKED
+    {
+        unsigned dsm;
+        asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dsm));
+        if (threadIdx.x == 0)
+            FCN_IDX(sizeof(cx<T>) * C::RPC * C::PADN + sizeof(double) * 32 - 1, dsm, 25);
+    }
+#endif
     const int tid = threadIdx.x;
     const int rloc = tid / C::TPR;
     const int t = tid - rloc * C::TPR;
@@ -531,13 +546,13 @@ row_kernel(RowArgs<T> a) {
     if (ops & OP_IFFT) {
         // pass-0 operands straight from HBM: X[t + r*TPR], coalesced
 #pragma unroll
-        for (int r = 0; r < E; ++r) v[r] = valid ? g[t + r * C::TPR] : mk(T(0), T(0));
+        for (int r = 0; r < E; ++r) v[r] = valid ? g[FCN_IDX(t + r * C::TPR, NT, 4)] : mk(T(0), T(0));
         InvDispatch<T, NT, 0, (C::NPASS <= 0)>::run(v, S, t, a.tw);
     } else {
 #pragma unroll
         for (int i = 0; i < E; ++i) {
             const int idx = t + C::TPR * i;
-            S[pidx(idx, NT)] = valid ? g[idx] : mk(T(0), T(0));
+            S[FCN_IDX(pidx(idx, NT), C::PADN, 5)] = valid ? g[FCN_IDX(idx, NT, 6)] : mk(T(0), T(0));
         }
         __syncthreads();
     }
@@ -551,12 +566,12 @@ row_kernel(RowArgs<T> a) {
         const T sc = (ops & OP_IFFT) ? a.nl.inv_nt : T(1);
 #pragma unroll
         for (int e = 0; e < E; ++e) {
-            cx<T> x = S[pidx(E * t + e, NT)];
+            cx<T> x = S[FCN_IDX(pidx(E * t + e, NT), C::PADN, 7)];
             v[e] = mk(x.x * sc, x.y * sc);
         }
         cx<T> nb = mk(T(0), T(0));
         if (t + 1 < C::TPR) {
-            cx<T> x = S[pidx(E * (t + 1), NT)];
+            cx<T> x = S[FCN_IDX(pidx(E * (t + 1), NT), C::PADN, 8)];
             nb = mk(x.x * sc, x.y * sc);
         }
         T u[E];
@@ -569,7 +584,7 @@ row_kernel(RowArgs<T> a) {
         if ((ops & OP_RHO) && valid && a.rho) {
             T *rr = a.rho + (size_t)row * NT + E * t;
 #pragma unroll
-            for (int e = 0; e < E; ++e) rr[e] = u[e] * a.nl.rho_nt;
+            for (int e = 0; e < E; ++e) rr[FCN_IDX(E * t + e, NT, 12) - E * t] = u[e] * a.nl.rho_nt;
         }
         if ((ops & OP_STATS) && a.stats) {
             double s = 0.0, mx = 0.0, mu = 0.0, bad = 0.0;
@@ -586,7 +601,7 @@ row_kernel(RowArgs<T> a) {
             mu = row_max<NT>(mu, t, scr, rloc);
             bad = row_sum<NT>(bad, t, scr, rloc);
             if (t == 0 && valid) {
-                double *st = a.stats + (size_t)row * NSTAT;
+                double *st = a.stats + FCN_IDX((size_t)row * NSTAT, (size_t)a.nr * NSTAT, 23);
                 st[ST_SUM_I] = s;
                 st[ST_MAX_I] = mx;
                 if (ops & (OP_NL | OP_NL2)) st[ST_MAX_U] = mu;
@@ -595,13 +610,13 @@ row_kernel(RowArgs<T> a) {
         }
         __syncthreads();  // every thread has read its neighbour before overwrite
 #pragma unroll
-        for (int e = 0; e < E; ++e) S[pidx(E * t + e, NT)] = v[e];
+        for (int e = 0; e < E; ++e) S[FCN_IDX(pidx(E * t + e, NT), C::PADN, 9)] = v[e];
         __syncthreads();
         if (!(ops & OP_FFT) && !(ops & OP_NOSTORE) && valid) {
 #pragma unroll
             for (int i = 0; i < E; ++i) {
                 const int idx = t + C::TPR * i;
-                g[idx] = S[pidx(idx, NT)];
+                g[FCN_IDX(idx, NT, 10)] = S[FCN_IDX(pidx(idx, NT), C::PADN, 11)];
             }
         }
     }
@@ -618,7 +633,7 @@ row_kernel(RowArgs<T> a) {
             for (int i = 0; i < NB; ++i) {
                 const int j = t + C::TPR * i;
 #pragma unroll
-                for (int r = 0; r < R; ++r) g[j + r * NS] = v[i * R + r];
+                for (int r = 0; r < R; ++r) g[FCN_IDX(j + r * NS, NT, 13)] = v[i * R + r];
             }
         }
         if ((ops & OP_SPEC) && a.stats) {
@@ -641,7 +656,7 @@ row_kernel(RowArgs<T> a) {
             s1 = row_sum<NT>(s1, t, scr, rloc);
             s2 = row_sum<NT>(s2, t, scr, rloc);
             if (t == 0 && valid) {
-                double *st = a.stats + (size_t)row * NSTAT;
+                double *st = a.stats + FCN_IDX((size_t)row * NSTAT, (size_t)a.nr * NSTAT, 24);
                 st[ST_S0] = s0;
                 st[ST_S1] = s1;
                 st[ST_S2] = s2;
