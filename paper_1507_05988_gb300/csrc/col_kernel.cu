@@ -140,10 +140,11 @@ __device__ __forceinline__ cx<T> chunk_scan(cx<T> A, cx<T> B, int C, int col, cx
     return cmul(Ae, wc) + Be;
 }
 
+// One CTA solves columns [g C, g C + C) of one pulse; blockDim.x >= C P
+// (P = chunks per column), threads beyond C P hold empty chunks.  Every
+// thread of the CTA must call it (barriers inside).
 template <typename T, int L>
-__global__ void __launch_bounds__(512)
-cn_kernel(ColArgs<T> a, int C) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ __forceinline__ void cn_body(const ColArgs<T> &a, int C, int g, unsigned char *smem_raw) {
     const int nwarp = blockDim.x >> 5;
     cx<T> *smA = reinterpret_cast<cx<T> *>(smem_raw);
     cx<T> *smB = smA + nwarp * C;
@@ -152,9 +153,6 @@ cn_kernel(ColArgs<T> a, int C) {
     const int tid = threadIdx.x;
     const int col = tid % C;
     const int chunk = tid / C;
-    const int ngroups = a.nt / C;
-    const int b = blockIdx.x;
-    const int g = (b & 1) ? (ngroups - 1 - (b >> 1)) : (b >> 1);
     const int q = g * C + col;
     const int nt = a.nt, nr = a.nr;
     const int nq = nt / 2 + 1;
@@ -251,6 +249,45 @@ cn_kernel(ColArgs<T> a, int C) {
 }
 
 template <typename T, int L>
+__global__ void __launch_bounds__(512)
+cn_kernel(ColArgs<T> a, int C) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    // CTAs for bins q and Nt - q are launched next to each other
+    const int ngroups = a.nt / C;
+    const int b = blockIdx.x;
+    const int g = (b & 1) ? (ngroups - 1 - (b >> 1)) : (b >> 1);
+    cn_body<T, L>(a, C, g, smem_raw);
+}
+
+// Batched work list: item = (pulse, column group, C); 512-thread CTAs; a
+// persistent grid pulls items from a global counter.
+template <typename T, int L>
+__global__ void __launch_bounds__(512)
+cn_batch_kernel(const ColArgs<T> *__restrict__ pulses, const int4 *__restrict__ items, int nitems,
+                unsigned *counter) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int next;
+    for (;;) {
+        if (threadIdx.x == 0) next = (int)atomicAdd(counter, 1u);
+        __syncthreads();
+        const int it = next;
+        __syncthreads();
+        if (it >= nitems) break;
+        const int4 w = items[it];
+        const ColArgs<T> a = pulses[w.x];
+        cn_body<T, L>(a, w.z, w.y, smem_raw);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const unsigned done = atomicAdd(counter + 1, 1u) + 1;
+        if (done == gridDim.x) {
+            counter[0] = 0;
+            counter[1] = 0;
+        }
+    }
+}
+
+template <typename T, int L>
 cudaError_t launch_cn_l(const ColArgs<T> &a, int target, cudaStream_t st) {
     constexpr int CMIN = 32 / int(sizeof(cx<T>));   // one 32-byte sector of columns
     const int P = (a.nr + L - 1) / L;
@@ -291,7 +328,18 @@ cudaError_t launch_cn_table(const TableArgs &a, cx<T> *table, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_cn_batch(const ColArgs<T> *pulses, const int4 *items, int nitems, unsigned *counter,
+                            int grid, cudaStream_t st) {
+    constexpr int L = sizeof(T) == 4 ? 16 : 8;
+    const size_t smem = sizeof(cx<T>) * 3 * 16 * 32;     // 16 warps x C <= 32 x 3 maps
+    cn_batch_kernel<T, L><<<grid, 512, smem, st>>>(pulses, items, nitems, counter);
+    return cudaGetLastError();
+}
+
 template cudaError_t launch_cn<float>(const ColArgs<float> &, cudaStream_t);
+template cudaError_t launch_cn_batch<float>(const ColArgs<float> *, const int4 *, int, unsigned *, int,
+                                            cudaStream_t);
 template cudaError_t launch_cn<double>(const ColArgs<double> &, cudaStream_t);
 template cudaError_t launch_cn_table<float>(const TableArgs &, cx<float> *, cudaStream_t);
 template cudaError_t launch_cn_table<double>(const TableArgs &, cx<double> *, cudaStream_t);

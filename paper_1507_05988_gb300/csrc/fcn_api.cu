@@ -8,6 +8,7 @@
 
 #include <cmath>
 #include <cstdio>
+#include <algorithm>
 #include <cstdlib>
 #include <cstring>
 #include <fstream>
@@ -266,6 +267,16 @@ struct fcn_ctx {
     float *mlp = nullptr;             // device FP32 master weights (FCN_MLP_NPARAM)
     bool has_mlp = false;
     int force_row = -1, force_col = -1;   // -1: autotune; else forced variant
+    // batched work lists (FP32, K = 8, several pulses): one launch per stage
+    bool batched = false;
+    int2 *row_items = nullptr;
+    int nrow_items = 0;
+    int4 *col_items = nullptr;
+    int ncol_items = 0;
+    unsigned *counter = nullptr;
+    size_t row_smem = 0;
+    int row_grid = 0, col_grid = 0;
+    std::map<uint64_t, std::pair<void *, void *>> batch_args;   // dz -> (RowArgs[], ColArgs[])
 };
 
 namespace {
@@ -310,6 +321,12 @@ int ensure_table(fcn_ctx *ctx, Pulse &pu, double dz, const cx<T> **out) {
                 ctx->graphs.erase(g);
             }
         }
+        auto ba = ctx->batch_args.find(old);
+        if (ba != ctx->batch_args.end()) {
+            cudaFree(ba->second.first);
+            cudaFree(ba->second.second);
+            ctx->batch_args.erase(ba);
+        }
         cudaFree(pu.tables[old]);
         pu.tables.erase(old);
     }
@@ -337,6 +354,7 @@ RowArgs<T> row_args(Pulse &pu, void *field, int ops, double dz) {
     a.rho = (T *)pu.rho;
     a.stats = pu.stats;
     a.nr = pu.g.nr;
+    a.nt = pu.g.nt;
     a.ops = ops;
     a.variant = pu.row_var;
     a.nl = nl_coef<T>(pu.g, pu.p, 0.5 * dz);
@@ -394,10 +412,80 @@ constexpr int OPS_TAIL = OP_IFFT | OP_NL | OP_RHO | OP_STATS;
 
 // Launches `kind` for every pulse on stream st: 0 head, 1 eight (col, mid)
 // pairs, 2 one (col, mid) pair, 3 (col, tail).
+// Device argument arrays of the batched kernels for this dz (built once).
+template <typename T>
+cudaError_t batch_args(fcn_ctx *ctx, double dz, const std::vector<const cx<T> *> &tabs,
+                       const RowArgs<T> **ra, const ColArgs<T> **ca) {
+    const uint64_t key = dz_key(dz);
+    auto it = ctx->batch_args.find(key);
+    if (it == ctx->batch_args.end()) {
+        const size_t n = ctx->pulses.size();
+        std::vector<RowArgs<T>> hr(n);
+        std::vector<ColArgs<T>> hc(n);
+        for (size_t i = 0; i < n; ++i) {
+            hr[i] = row_args<T>(ctx->pulses[i], ctx->pulses[i].field, 0, dz);
+            hc[i] = col_args<T>(ctx->pulses[i], ctx->pulses[i].field, tabs[i], dz);
+        }
+        void *dr = nullptr, *dc = nullptr;
+        cudaError_t e = cudaMalloc(&dr, sizeof(RowArgs<T>) * n);
+        if (e == cudaSuccess) e = cudaMalloc(&dc, sizeof(ColArgs<T>) * n);
+        if (e == cudaSuccess) e = cudaMemcpy(dr, hr.data(), sizeof(RowArgs<T>) * n, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(dc, hc.data(), sizeof(ColArgs<T>) * n, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            cudaFree(dr);
+            cudaFree(dc);
+            return e;
+        }
+        it = ctx->batch_args.emplace(key, std::make_pair(dr, dc)).first;
+    }
+    *ra = (const RowArgs<T> *)it->second.first;
+    *ca = (const ColArgs<T> *)it->second.second;
+    return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t launch_block_batched(fcn_ctx *ctx, int kind, double dz, cudaStream_t st,
+                                 const std::vector<const cx<T> *> &tabs) {
+    if constexpr (sizeof(T) != 4) {
+        return cudaErrorNotSupported;
+    } else {
+        const RowArgs<T> *ra;
+        const ColArgs<T> *ca;
+        cudaError_t e = batch_args<T>(ctx, dz, tabs, &ra, &ca);
+        if (e != cudaSuccess) return e;
+        auto rows = [&](int ops, int pk) {
+            return timed(ctx, pk, st, [&] {
+                return launch_rows_batch<T>(ra, ctx->row_items, ctx->nrow_items, ops, ctx->counter,
+                                            ctx->row_smem, ctx->row_grid, st);
+            });
+        };
+        auto col = [&] {
+            return timed(ctx, FCN_PROF_COLUMN, st, [&] {
+                return launch_cn_batch<T>(ca, ctx->col_items, ctx->ncol_items, ctx->counter,
+                                          ctx->col_grid, st);
+            });
+        };
+        if (kind == 0) {
+            e = rows(OPS_HEAD, FCN_PROF_ROW_HEAD);
+        } else if (kind == 1 || kind == 2) {
+            const int reps = kind == 1 ? 8 : 1;
+            for (int r = 0; r < reps && e == cudaSuccess; ++r) {
+                e = col();
+                if (e == cudaSuccess) e = rows(OPS_MID, FCN_PROF_ROW_MID);
+            }
+        } else {
+            e = col();
+            if (e == cudaSuccess) e = rows(OPS_TAIL, FCN_PROF_ROW_TAIL);
+        }
+        return e;
+    }
+}
+
 template <typename T>
 cudaError_t launch_block(fcn_ctx *ctx, int kind, double dz, cudaStream_t st,
                          const std::vector<const cx<T> *> &tabs,
                          const std::vector<void *> *fields = nullptr) {
+    if (ctx->batched && !fields) return launch_block_batched<T>(ctx, kind, dz, st, tabs);
     cudaError_t e = cudaSuccess;
     for (size_t i = 0; i < ctx->pulses.size() && e == cudaSuccess; ++i) {
         Pulse &pu = ctx->pulses[i];
@@ -550,6 +638,7 @@ int tune_pulse(fcn_ctx *ctx, Pulse &pu, const cx<T> *tab, double dz) {
 
 template <typename T>
 int ensure_tuned(fcn_ctx *ctx, const std::vector<const cx<T> *> &tabs, double dz) {
+    if (ctx->batched) return FCN_OK;   // the work-list kernels have a single variant
     for (size_t i = 0; i < ctx->pulses.size(); ++i) {
         Pulse &pu = ctx->pulses[i];
         if (pu.tuned) continue;
@@ -580,6 +669,12 @@ int step_impl(fcn_ctx *ctx, double dz, int64_t n, bool use_graph) {
     {
         int rc = ensure_tuned<T>(ctx, tabs, dz);
         if (rc) return rc;
+    }
+    if (ctx->batched) {
+        // argument arrays are copied synchronously: never inside a capture
+        const RowArgs<T> *ra;
+        const ColArgs<T> *ca;
+        CK(batch_args<T>(ctx, dz, tabs, &ra, &ca), "batch arguments");
     }
     int rc = run_block<T>(ctx, 0, dz, tabs, use_graph);
     int64_t rem = n - 1;
@@ -718,6 +813,59 @@ Pulse *get_pulse(fcn_ctx *ctx, int pulse) {
     return &ctx->pulses[pulse];
 }
 
+// Work lists of the batched kernels: row items (pulse, first row) with
+// 512/(Nt/16) rows each, column items (pulse, group, C) with C P <= 512 (P =
+// chunks of 16 rows); both sorted largest first.  Only when every pulse runs
+// FP32 with K = 8 and Nt >= 512 (else per-pulse launches are used).
+int setup_batch(fcn_ctx *ctx) {
+    for (auto &pu : ctx->pulses)
+        if (pu.p.K != 8 || pu.g.nt < 512) return FCN_OK;
+    std::vector<std::pair<int64_t, int2>> rows;
+    std::vector<std::pair<int64_t, int4>> cols;
+    size_t smem = 0;
+    for (size_t i = 0; i < ctx->pulses.size(); ++i) {
+        const Pulse &pu = ctx->pulses[i];
+        const int nt = pu.g.nt, nr = pu.g.nr;
+        const int rpi = 512 / (nt / 16);
+        for (int r0 = 0; r0 < nr; r0 += rpi) rows.push_back({(int64_t)nt, make_int2((int)i, r0)});
+        const size_t sm = row_batch_smem(nt, 8);
+        if (sm > smem) smem = sm;
+        const int P = (nr + 15) / 16;
+        int C = 4;
+        while (C * 2 * P <= 512 && C * 2 <= 32) C *= 2;
+        if (C > nt) C = nt;
+        const int ng = nt / C;
+        for (int b = 0; b < ng; ++b) {
+            const int g = (b & 1) ? (ng - 1 - (b >> 1)) : (b >> 1);
+            cols.push_back({(int64_t)nr * C, make_int4((int)i, g, C, 0)});
+        }
+    }
+    std::stable_sort(rows.begin(), rows.end(), [](auto &x, auto &y) { return x.first > y.first; });
+    std::stable_sort(cols.begin(), cols.end(), [](auto &x, auto &y) { return x.first > y.first; });
+    std::vector<int2> hr;
+    std::vector<int4> hc;
+    for (auto &x : rows) hr.push_back(x.second);
+    for (auto &x : cols) hc.push_back(x.second);
+    cudaError_t e = cudaMalloc(&ctx->row_items, sizeof(int2) * hr.size());
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->col_items, sizeof(int4) * hc.size());
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->counter, 2 * sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemcpy(ctx->row_items, hr.data(), sizeof(int2) * hr.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(ctx->col_items, hc.data(), sizeof(int4) * hc.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(ctx->counter, 0, 2 * sizeof(unsigned));
+    if (e == cudaSuccess) e = prepare_rows_batch<float>(smem);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "batch work lists");
+    ctx->nrow_items = (int)hr.size();
+    ctx->ncol_items = (int)hc.size();
+    ctx->row_smem = smem;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    ctx->row_grid = sms;          // one 512-thread CTA per SM (128 registers)
+    ctx->col_grid = 2 * sms;      // column CTAs use fewer registers
+    ctx->batched = true;
+    return FCN_OK;
+}
+
 int create_impl(int n, const fcn_grid *grids, const fcn_params *params, int prec, void *stream,
                 fcn_ctx **out) {
     if (!out) return fail(nullptr, FCN_ERR_ARG, "out is null");
@@ -786,6 +934,10 @@ int create_impl(int n, const fcn_grid *grids, const fcn_params *params, int prec
             }
         }
     }
+    if (n > 1 && prec == FCN_FP32_MIXED) {
+        int rc = setup_batch(ctx);
+        if (rc) return bail(rc);
+    }
     if ((e = cudaDeviceSynchronize()) != cudaSuccess) { cuda_fail(ctx, e, "init sync"); return bail(FCN_ERR_CUDA); }
     *out = ctx;
     return FCN_OK;
@@ -828,6 +980,13 @@ void fcn_destroy(fcn_ctx *ctx) {
         for (auto &kv : pu.tables) cudaFree(kv.second);
     }
     if (ctx->mlp) cudaFree(ctx->mlp);
+    for (auto &kv : ctx->batch_args) {
+        cudaFree(kv.second.first);
+        cudaFree(kv.second.second);
+    }
+    cudaFree(ctx->row_items);
+    cudaFree(ctx->col_items);
+    cudaFree(ctx->counter);
     if (ctx->host_red) cudaFreeHost(ctx->host_red);
     if (ctx->cap) cudaStreamDestroy(ctx->cap);
     delete ctx;
@@ -1053,7 +1212,7 @@ int fcn_op_rows(const fcn_grid *grid, const fcn_params *params, int32_t precisio
         CK(get_twiddles<double>(grid->nt, &tw), "twiddles");
         CK(prepare_rows<double>(grid->nt), "row kernel attributes");
         a.field = (cx<double> *)field; a.tw = tw; a.rho = (double *)rho; a.stats = nullptr;
-        a.nr = grid->nr; a.ops = ops; a.variant = 0; a.nl = nl_coef<double>(*grid, *params, dz_half);
+        a.nr = grid->nr; a.nt = grid->nt; a.ops = ops; a.variant = 0; a.nl = nl_coef<double>(*grid, *params, dz_half);
         CK(launch_rows<double>(a, grid->nt, st), "row stage");
     } else {
         RowArgs<float> a;
@@ -1061,7 +1220,7 @@ int fcn_op_rows(const fcn_grid *grid, const fcn_params *params, int32_t precisio
         CK(get_twiddles<float>(grid->nt, &tw), "twiddles");
         CK(prepare_rows<float>(grid->nt), "row kernel attributes");
         a.field = (cx<float> *)field; a.tw = tw; a.rho = (float *)rho; a.stats = nullptr;
-        a.nr = grid->nr; a.ops = ops; a.variant = 0; a.nl = nl_coef<float>(*grid, *params, dz_half);
+        a.nr = grid->nr; a.nt = grid->nt; a.ops = ops; a.variant = 0; a.nl = nl_coef<float>(*grid, *params, dz_half);
         CK(launch_rows<float>(a, grid->nt, st), "row stage");
     }
     return FCN_OK;

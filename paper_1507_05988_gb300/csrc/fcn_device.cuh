@@ -118,6 +118,7 @@ struct RowArgs {
     T *rho;               // [nr][nt] or null
     double *stats;        // [nr][NSTAT] or null
     int nr;
+    int nt;
     int ops;
     int variant;          // occupancy variant (0..2), chosen by the autotuner
     NLCoef<T> nl;
@@ -154,6 +155,21 @@ constexpr int kRowVariants = 3;
 constexpr int kColVariants = 4;
 template <typename T>
 cudaError_t launch_cn_table(const TableArgs &a, cx<T> *table, cudaStream_t st);
+
+// Batched work lists (pulses of uneven grids in one launch per stage).
+// Row items: (pulse, first row), 512/(Nt/16) rows each, Nt in 512..8192.
+// Column items: (pulse, column group); every pulse uses 512-thread CTAs.
+// counter: 2 unsigned, zero before the first launch (kernels reset them).
+template <typename T>
+cudaError_t launch_rows_batch(const RowArgs<T> *pulses, const int2 *items, int nitems, int ops,
+                              unsigned *counter, size_t smem, int grid, cudaStream_t st);
+template <typename T>
+cudaError_t prepare_rows_batch(size_t smem);
+template <typename T>
+cudaError_t launch_cn_batch(const ColArgs<T> *pulses, const int4 *items, int nitems,
+                            unsigned *counter, int grid, cudaStream_t st);
+// shared-memory bytes of the batched row kernel for rows of nt points
+size_t row_batch_smem(int nt, int bytes_per_complex);
 
 // reductions and conversions
 template <typename T>

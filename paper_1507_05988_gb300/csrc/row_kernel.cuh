@@ -516,31 +516,34 @@ __device__ __forceinline__ double row_max(double x, int t, double *scr, int rloc
 
 // MB: minimum resident CTAs per SM requested from the compiler (register cap
 // 64K / (MB * THREADS)); the autotuner picks it per (precision, Nt).
-template <typename T, int NT, int KT, int MB>
-__global__ void __launch_bounds__(RowCfg<NT>::THREADS, MB)
-row_kernel(RowArgs<T> a) {
+// One CTA of TH threads processes rows [row_base, row_base + TH/TPR) of one
+// pulse: TH = RowCfg<NT>::THREADS in the per-Nt kernels, 512 in the batched
+// work-list kernel.  Every thread of the CTA must call it (barriers inside).
+template <typename T, int NT, int KT, int TH>
+__device__ __forceinline__ void row_body(const RowArgs<T> &a, int row_base, int ops,
+                                         unsigned char *smem_raw) {
     using C = RowCfg<NT>;
     constexpr int E = C::E;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int RPC = TH / C::TPR;
+    static_assert(RPC * C::TPR == TH, "CTA size must hold whole rows");
     cx<T> *S_all = reinterpret_cast<cx<T> *>(smem_raw);
-    double *scr = reinterpret_cast<double *>(S_all + C::RPC * C::PADN);
+    double *scr = reinterpret_cast<double *>(S_all + RPC * C::PADN);
 
 #ifdef FCN_CHECKED
     {
         unsigned dsm;
         asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dsm));
         if (threadIdx.x == 0)
-            FCN_IDX(sizeof(cx<T>) * C::RPC * C::PADN + sizeof(double) * 32 - 1, dsm, 25);
+            FCN_IDX(sizeof(cx<T>) * RPC * C::PADN + sizeof(double) * 32 - 1, dsm, 25);
     }
 #endif
     const int tid = threadIdx.x;
     const int rloc = tid / C::TPR;
     const int t = tid - rloc * C::TPR;
-    const int row = blockIdx.x * C::RPC + rloc;
+    const int row = row_base + rloc;
     const bool valid = row < a.nr;
     cx<T> *S = S_all + rloc * C::PADN;
     cx<T> *g = a.field + (size_t)(valid ? row : 0) * NT;
-    const int ops = a.ops;
 
     cx<T> v[E];
     if (ops & OP_IFFT) {
@@ -665,6 +668,48 @@ row_kernel(RowArgs<T> a) {
     }
 }
 
+template <typename T, int NT, int KT, int MB>
+__global__ void __launch_bounds__(RowCfg<NT>::THREADS, MB)
+row_kernel(RowArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    row_body<T, NT, KT, RowCfg<NT>::THREADS>(a, blockIdx.x * RowCfg<NT>::RPC, a.ops, smem_raw);
+}
+
+// Batched work list: each item (pulse, first row) covers 512 / (Nt/16) rows of
+// one pulse; pulses may have different Nr and Nt (Nt = 512 ... 8192).  A
+// persistent grid pulls items from a global counter, largest rows first.
+template <typename T, int KT>
+__global__ void __launch_bounds__(512, 1)
+row_batch_kernel(const RowArgs<T> *__restrict__ pulses, const int2 *__restrict__ items, int nitems,
+                 int ops, unsigned *counter) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int next;
+    for (;;) {
+        if (threadIdx.x == 0) next = (int)atomicAdd(counter, 1u);
+        __syncthreads();
+        const int it = next;
+        __syncthreads();
+        if (it >= nitems) break;
+        const int2 w = items[it];
+        const RowArgs<T> a = pulses[w.x];
+        switch (a.nt) {
+            case 512: row_body<T, 512, KT, 512>(a, w.y, ops, smem_raw); break;
+            case 1024: row_body<T, 1024, KT, 512>(a, w.y, ops, smem_raw); break;
+            case 2048: row_body<T, 2048, KT, 512>(a, w.y, ops, smem_raw); break;
+            case 4096: row_body<T, 4096, KT, 512>(a, w.y, ops, smem_raw); break;
+            default: row_body<T, 8192, KT, 512>(a, w.y, ops, smem_raw); break;
+        }
+        __syncthreads();
+    }
+    // the last CTA out resets the counter for the next launch
+    if (threadIdx.x == 0) {
+        const unsigned done = atomicAdd(counter + 1, 1u) + 1;
+        if (done == gridDim.x) {
+            counter[0] = 0;
+            counter[1] = 0;
+        }
+    }
+}
 }  // namespace
 
 namespace rowimpl {

@@ -396,3 +396,42 @@ def test_autotuner_picks_a_valid_variant_and_stays_correct(fcn):
     s.close()
     Aref, _ = oracle.run(pb, 4e-3, 3, wl.field())
     assert rel_l2(A, Aref) < 1e-5
+
+
+# ------------------------------------------- batched uneven grids (one launch/stage)
+
+def _batch_workloads():
+    """Six pulses with uneven grids (Nr 37..300, Nt 512..8192), config-4-like
+    draws of power, waist and duration."""
+    rng = np.random.default_rng(3)
+    out = []
+    for nr, nt in ((37, 512), (130, 1024), (64, 2048), (300, 4096), (48, 8192), (129, 512)):
+        out.append(W.Workload(f"b{nr}x{nt}", nr=nr, nt=nt, w0=float(rng.uniform(0.5e-3, 5e-3)),
+                              tp=float(rng.uniform(30e-15, 200e-15)),
+                              p_over_pcr=float(rng.uniform(1, 10)), noise_seed=int(nr)))
+    return out
+
+
+def test_batched_uneven_grids_match_the_oracle(fcn):
+    wls = _batch_workloads()
+    s = fcn.Solver([w.physics() for w in wls], precision=FP32)
+    for i, w in enumerate(wls):
+        s.set_field(w.field(), pulse=i)
+    s.profile(True)
+    s.step(2e-3, 5)
+    prof = s.profile_read()
+    s.profile(False)
+    # one launch per stage for the whole batch
+    assert prof["row_head"][1] == 1 and prof["row_mid"][1] == 4 and prof["column"][1] == 5
+    outs = [s.get_field(i) for i in range(len(wls))]
+    diags = [s.diag(i) for i in range(len(wls))]
+    s.step(2e-3, 3)                       # graph replay continues the same state
+    outs8 = [s.get_field(i) for i in range(len(wls))]
+    s.close()
+    for i, w in enumerate(wls):
+        pb = _pb(w)
+        ref, _ = oracle.run(pb, 2e-3, 5, w.field())
+        assert rel_l2(outs[i], ref) < 1e-5, w.name
+        assert diags[i]["energy"] == pytest.approx(oracle.diag(pb, ref)["energy"], rel=1e-6)
+        ref8, _ = oracle.run(pb, 2e-3, 3, ref)
+        assert rel_l2(outs8[i], ref8) < 1e-5, w.name
