@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--pulses", type=int, default=8, help="pulses per GPU")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--no-cfg4", action="store_true")
+    ap.add_argument("--cfg4-steps", type=int, default=20)
     return ap.parse_args()
 
 
@@ -115,6 +117,22 @@ class ClockSampler:
         os.unlink(self.path)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def reduce_max(x: float, pg, device) -> float:
+    """Maximum of x over the ranks of process group pg (x itself if None)."""
+    if pg is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_scaling_value(world: int, points_per_rank: int, steps: int, t_max_ms: float) -> float:
+    """Whole-job throughput: every rank advances points_per_rank points by
+    steps z-steps; the job takes as long as the slowest rank."""
+    return world * points_per_rank * steps / (t_max_ms * 1e-3)
 
 
 def rel_l2(a, b):
@@ -215,12 +233,8 @@ def run_ours(args):
     torch.cuda.synchronize()
     clk = clocks.stop()
     barrier()
-    t_ms = e0.elapsed_time(e1)
-    if pg:
-        t = torch.tensor([t_ms], device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        t_ms = float(t.item())
-    value = world * B * pts * args.steps / (t_ms * 1e-3)
+    t_ms = reduce_max(e0.elapsed_time(e1), pg, "cuda")
+    value = weak_scaling_value(world, B * pts, args.steps, t_ms)
 
     # ---- kernel roofline: replay the same steps with per-launch events ----
     solver.profile(True)
@@ -228,14 +242,20 @@ def run_ours(args):
     prof = solver.profile_read(reset=True)
     solver.profile(False)
     launches = int(sum(n for _, n in prof.values()))
-    dom = max(prof.items(), key=lambda kv: kv[1][0])
-    dom_name, (dom_ms, dom_n) = dom
-    bytes_per_launch = 2 * pts * 8          # one field read + one write (complex64)
+    # algorithmic bytes: one field read + one write (complex64) per point and
+    # stage execution; per pulse a K-step call runs 1 head, K-1 middle and
+    # 1 tail row stage and K column stages
+    execs = {"row_head": 1, "row_mid": args.steps - 1, "row_tail": 1, "column": args.steps}
+    stage_bytes = 2 * pts * 8
     peak, peak_src = measured_peaks()
-    achieved = bytes_per_launch / (dom_ms / dom_n * 1e-3) / 1e9
-    kernels = {k: {"launches": n, "avg_us": (ms / n * 1e3 if n else None),
-                   "alg_GBps": (bytes_per_launch / (ms / n * 1e-3) / 1e9 if n else None)}
-               for k, (ms, n) in prof.items()}
+    kernels = {}
+    for k, (ms, n) in prof.items():
+        tot = B * execs[k] * stage_bytes
+        kernels[k] = {"launches": n, "total_ms": ms, "avg_us": (ms / n * 1e3 if n else None),
+                      "alg_GBps": (tot / (ms * 1e-3) / 1e9 if ms else None)}
+    dom_name = max(prof.items(), key=lambda kv: kv[1][0])[0]
+    achieved = kernels[dom_name]["alg_GBps"]
+    bytes_per_launch = stage_bytes * (B if prof[dom_name][1] < B * execs[dom_name] else 1)
     traffic = None
     tpath = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tpath):
@@ -259,15 +279,32 @@ def run_ours(args):
             fcn.check(fcn.fcn_get_field(solver.ctx, i, C.cast(host_out[i].data_ptr(), fcn._D)),
                       solver.ctx)
     torch.cuda.synchronize()
-    t_e2e = time.perf_counter() - t0
-    if pg:
-        t = torch.tensor([t_e2e], device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        t_e2e = float(t.item())
-    e2e = {"value": world * B * pts * K2 / t_e2e, "unit": UNIT,
+    t_e2e = reduce_max(time.perf_counter() - t0, pg, "cuda")
+    e2e = {"value": weak_scaling_value(world, B * pts, K2, t_e2e * 1e3), "unit": UNIT,
            "h2d_bytes_per_step": B * pts * 16, "d2h_bytes_per_step": B * pts * 16,
            "steps": K2, "note": "set_field (host complex128) + fcn_step(dz,1) + get_field per step"}
     solver.close()
+
+    # ---- batched form on 64 uneven pulses (config-4 draws) ----
+    cfg4 = None
+    if not args.no_cfg4:
+        w4 = W.config4()
+        s4 = fcn.Solver([w.physics() for w in w4], precision=fcn.FCN_FP32_MIXED)
+        for i, w in enumerate(w4):
+            s4.set_field(w.field(), pulse=i)
+        pts4 = sum(w.points for w in w4)
+        cfg4 = {"pulses": len(w4), "points": pts4, "dz_m": w4[0].dz, "steps": args.cfg4_steps}
+        for mode, name in ((1, "batched_one_launch_per_stage"), (0, "per_pulse_launches")):
+            s4.set_batching(mode)
+            s4.step(w4[0].dz, 2)
+            torch.cuda.synchronize()
+            a4, b4 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a4.record()
+            s4.step(w4[0].dz, args.cfg4_steps)
+            b4.record()
+            torch.cuda.synchronize()
+            cfg4[name] = pts4 * args.cfg4_steps / (a4.elapsed_time(b4) * 1e-3)
+        s4.close()
 
     # ---- plain FP64 FCN on the same batch ----
     K64 = max(2, min(args.steps, 6))
@@ -281,7 +318,7 @@ def run_ours(args):
     s64.step(dz, K64)
     b.record()
     torch.cuda.synchronize()
-    v64 = world * B * pts * K64 / (a.elapsed_time(b) * 1e-3)
+    v64 = weak_scaling_value(world, B * pts, K64, reduce_max(a.elapsed_time(b), pg, "cuda"))
     s64.close()
 
     # ---- accuracy of the chosen form against the FP64 path, full 1000-step run ----
@@ -324,6 +361,7 @@ def run_ours(args):
                          "algorithmic_bytes_per_launch": bytes_per_launch,
                          "note": "achieved = algorithmic bytes / mean CUDA-event launch time"},
             "kernels": kernels,
+            "batched_cfg4": cfg4,
             "fp64_gpu": {"value": v64, "unit": UNIT, "steps": K64,
                          "speedup_of_chosen_form": value / v64},
             "accuracy_vs_fp64": acc,

@@ -207,6 +207,14 @@ int fcn_set_state(fcn_ctx *ctx, int32_t pulse, const double state[4]);
  * Drops the context's captured graphs.  Synchronises. */
 int fcn_set_variants(fcn_ctx *ctx, int32_t row_variant, int32_t col_variant);
 
+/* Batched work lists for multi-pulse FP32 contexts (every pulse K = 8,
+ * Nt >= 512): mode 1 runs each stage of all pulses as one persistent launch
+ * over (pulse, rows) and (pulse, column group) items; 0 launches each pulse
+ * separately (tuned per-Nt kernels, all inside one CUDA graph); -1 (the
+ * default) uses the work lists when the pulses' grids differ.  Drops the
+ * captured graphs.  FCN_ERR_UNSUPPORTED if mode 1 is not possible. */
+int fcn_set_batching(fcn_ctx *ctx, int32_t mode);
+
 /* Variants in use for pulse `pulse` (out[0] row, out[1] column; -1 before
  * the first step). */
 int fcn_get_variants(fcn_ctx *ctx, int32_t pulse, int32_t out[2]);

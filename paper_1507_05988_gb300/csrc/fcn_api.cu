@@ -820,6 +820,7 @@ Pulse *get_pulse(fcn_ctx *ctx, int pulse) {
 int setup_batch(fcn_ctx *ctx) {
     for (auto &pu : ctx->pulses)
         if (pu.p.K != 8 || pu.g.nt < 512) return FCN_OK;
+    if (ctx->row_items) return FCN_OK;   // already built
     std::vector<std::pair<int64_t, int2>> rows;
     std::vector<std::pair<int64_t, int4>> cols;
     size_t smem = 0;
@@ -862,8 +863,16 @@ int setup_batch(fcn_ctx *ctx) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     ctx->row_grid = sms;          // one 512-thread CTA per SM (128 registers)
     ctx->col_grid = 2 * sms;      // column CTAs use fewer registers
-    ctx->batched = true;
     return FCN_OK;
+}
+
+// Automatic choice: the work lists pay off when the grids differ (uneven
+// pulses would otherwise serialise small launches); identical grids run the
+// tuned per-Nt kernels, one launch per pulse inside the graph.
+bool grids_uneven(const fcn_ctx *ctx) {
+    for (auto &pu : ctx->pulses)
+        if (pu.g.nr != ctx->pulses[0].g.nr || pu.g.nt != ctx->pulses[0].g.nt) return true;
+    return false;
 }
 
 int create_impl(int n, const fcn_grid *grids, const fcn_params *params, int prec, void *stream,
@@ -937,6 +946,7 @@ int create_impl(int n, const fcn_grid *grids, const fcn_params *params, int prec
     if (n > 1 && prec == FCN_FP32_MIXED) {
         int rc = setup_batch(ctx);
         if (rc) return bail(rc);
+        ctx->batched = ctx->row_items != nullptr && grids_uneven(ctx);
     }
     if ((e = cudaDeviceSynchronize()) != cudaSuccess) { cuda_fail(ctx, e, "init sync"); return bail(FCN_ERR_CUDA); }
     *out = ctx;
@@ -1149,6 +1159,21 @@ int fcn_set_variants(fcn_ctx *ctx, int32_t row_variant, int32_t col_variant) {
     for (auto &pu : ctx->pulses) pu.tuned = false;
     for (auto &kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
     ctx->graphs.clear();
+    return FCN_OK;
+}
+
+int fcn_set_batching(fcn_ctx *ctx, int32_t mode) {
+    if (!ctx || mode < -1 || mode > 1) return FCN_ERR_ARG;
+    CK(cudaStreamSynchronize(ctx->st), "sync");
+    const bool possible = ctx->row_items != nullptr;
+    if (mode == 1 && !possible)
+        return fail(ctx, FCN_ERR_UNSUPPORTED, "work lists need several FP32 pulses with K = 8 and Nt >= 512");
+    const bool want = mode == 1 || (mode == -1 && possible && grids_uneven(ctx));
+    if (want != ctx->batched) {
+        for (auto &kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
+        ctx->graphs.clear();
+        ctx->batched = want;
+    }
     return FCN_OK;
 }
 

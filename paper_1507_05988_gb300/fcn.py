@@ -96,6 +96,7 @@ _SIGS = {
     "fcn_set_state": (C.c_int, [_CTX, C.c_int32, _D]),
     "fcn_set_variants": (C.c_int, [_CTX, C.c_int32, C.c_int32]),
     "fcn_get_variants": (C.c_int, [_CTX, C.c_int32, C.POINTER(C.c_int32)]),
+    "fcn_set_batching": (C.c_int, [_CTX, C.c_int32]),
     "fcn_profile_enable": (C.c_int, [_CTX, C.c_int32]),
     "fcn_profile_read": (C.c_int, [_CTX, _D, C.POINTER(C.c_int64), C.c_int32]),
     "fcn_mlp_set": (C.c_int, [_CTX, _F]),
@@ -238,6 +239,9 @@ class Solver:
 
     def set_variants(self, row: int = -1, col: int = -1):
         check(fcn_set_variants(self.ctx, int(row), int(col)), self.ctx)
+
+    def set_batching(self, mode: int):
+        check(fcn_set_batching(self.ctx, int(mode)), self.ctx)
 
     def variants(self, pulse: int = 0):
         out = (C.c_int32 * 2)()

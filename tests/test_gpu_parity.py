@@ -435,3 +435,28 @@ def test_batched_uneven_grids_match_the_oracle(fcn):
         assert diags[i]["energy"] == pytest.approx(oracle.diag(pb, ref)["energy"], rel=1e-6)
         ref8, _ = oracle.run(pb, 2e-3, 3, ref)
         assert rel_l2(outs8[i], ref8) < 1e-5, w.name
+
+
+def test_batching_modes_agree(fcn):
+    """Work lists (one launch per stage) and per-pulse launches compute the
+    same steps; identical grids default to per-pulse launches."""
+    wls = _batch_workloads()[:4]
+    res = {}
+    for mode in (1, 0):
+        s = fcn.Solver([w.physics() for w in wls], precision=FP32)
+        s.set_batching(mode)
+        for i, w in enumerate(wls):
+            s.set_field(w.field(), pulse=i)
+        s.step(2e-3, 6)
+        res[mode] = [s.get_field(i) for i in range(len(wls))]
+        s.close()
+    for a, b in zip(res[1], res[0]):
+        assert rel_l2(a, b) < 1e-5
+    same = fcn.Solver([wls[0].physics()] * 3, precision=FP32)
+    same.profile(True)
+    for i in range(3):
+        same.set_field(wls[0].field(), pulse=i)
+    same.step(2e-3, 2)
+    assert same.profile_read()["column"][1] == 6          # per-pulse launches
+    same.profile(False)
+    same.close()
