@@ -244,9 +244,40 @@ int fcn_profile_read(fcn_ctx *ctx, double *ms, int64_t *count, int32_t reset);
 #define FCN_MLP_NH      64
 #define FCN_MLP_NPARAM  4673
 
-/* Loads FP32 master weights (host, FCN_MLP_NPARAM floats) into ctx. */
+/* Features of a field (computed on the device from the FP64 diagnostics):
+ *   f0 = log(peak I / I_ref)            f1 = log10(peak rho/rho_nt + 1e-30)/10
+ *   f2 = spectral rms / rms_ref - 1     f3 = relative change of peak I over the last step
+ *   f4 = log(dz_prev / L_ref)           f5 = log(err_prev / rtol)
+ * with I_ref, rms_ref from the field at the start of fcn_propagate and
+ * L_ref = k0 (r_max/5)^2 / 2.  The network predicts log(dz / L_ref); its
+ * proposal is clamped to [0.2, 2] times the last accepted step. */
+
+/* Loads / reads FP32 master weights (host, FCN_MLP_NPARAM floats). */
 int fcn_mlp_set(fcn_ctx *ctx, const float *host_params);
 int fcn_mlp_get(fcn_ctx *ctx, float *host_params);
+
+/* Makes fcn_propagate append one record per attempt to a caller-owned host
+ * buffer of capacity records of 8 floats: f0..f5 of the state the attempt
+ * started from, log(h / L_ref) of the attempted step and log(err / rtol) of
+ * its step-doubling error.  A training label log(dz_safe / L_ref) follows as
+ * rec[6] - rec[7]/3 (the Strang local error is O(dz^3)).  capacity 0 stops.
+ * fcn_mlp_log_count returns the number of records written. */
+int fcn_mlp_set_log(fcn_ctx *ctx, float *host_buf, int64_t capacity);
+int64_t fcn_mlp_log_count(const fcn_ctx *ctx);
+
+/* Trains the context's MLP on n samples (x: n x 6 features, y: n labels)
+ * with Adam (beta 0.9/0.999) for `epochs` passes over a seeded permutation
+ * in minibatches of `batch`; weights start from fcn_mlp_set's or, if none,
+ * from a seeded uniform initialisation.  Forward and backward run in this
+ * library's kernels (BF16 weights, FP32 accumulation).  final_loss (may be
+ * NULL) receives the mean squared error over all samples. */
+int fcn_mlp_train(fcn_ctx *ctx, const float *x, const float *y, int32_t n, int32_t epochs,
+                  int32_t batch, float lr, uint64_t seed, float *final_loss);
+
+/* Stateless: mean squared error and its gradient (FCN_MLP_NPARAM floats) of
+ * the network with the given FP32 master weights over n samples, on the GPU. */
+int fcn_mlp_loss_grad(const float *params, const float *x, const float *y, int32_t n,
+                      float *loss, float *grad);
 
 /* ====================== stateless device operations ======================
  * These run one stage on caller-owned device buffers (e.g. torch tensors)

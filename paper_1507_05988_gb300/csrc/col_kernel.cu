@@ -44,35 +44,43 @@ __device__ __forceinline__ cx<double> crecip(cx<double> z) {
     return mk(z.x / d, -z.y / d);
 }
 
+__device__ __forceinline__ cx<float> crecip(cx<float> z) {
+    const float d = 1.0f / (z.x * z.x + z.y * z.y);
+    return mk(z.x * d, -z.y * d);
+}
+
 // One thread per |q| = 0..Nt/2 runs the Thomas pivot recurrence down the
-// radial index in FP64: piv_j = b_j - a_j c_{j-1}/piv_{j-1}.
+// radial index, piv_j = b_j - a_j c_{j-1}/piv_{j-1}, in the working precision
+// (FP64 tables in FP64; FP32 tables in FP32, ~50x faster on this GPU, which
+// matters when adaptive runs need two tables per attempt).  The recurrence is
+// contractive, so rounding does not accumulate.
 template <typename T>
 __global__ void cn_table_kernel(TableArgs a, cx<T> *table) {
     const int nq = a.nt / 2 + 1;
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= nq) return;
-    const double delta = a.dk * double(q) * double(q);
-    const double s = a.s;
-    cx<double> cp = mk(0.0, 0.0);
+    const T delta = T(a.dk * double(q) * double(q));
+    const T s = T(a.s);
+    cx<T> cp = mk(T(0), T(0));
     for (int j = 0; j < a.nr; ++j) {
-        cx<double> b, aa, c;
+        cx<T> b, aa, c;
         if (j == 0) {
-            aa = mk(0.0, 0.0);
-            b = mk(1.0, 4.0 * s - delta);
-            c = mk(0.0, -4.0 * s);
+            aa = mk(T(0), T(0));
+            b = mk(T(1), T(4) * s - delta);
+            c = mk(T(0), -T(4) * s);
         } else if (j < a.nr - 1) {
-            aa = mk(0.0, -s * a.lo[FCN_IDX(j, a.nr, 31)]);
-            b = mk(1.0, 2.0 * s - delta);
-            c = mk(0.0, -s * a.hi[FCN_IDX(j, a.nr, 32)]);
+            aa = mk(T(0), -s * T(a.lo[FCN_IDX(j, a.nr, 31)]));
+            b = mk(T(1), T(2) * s - delta);
+            c = mk(T(0), -s * T(a.hi[FCN_IDX(j, a.nr, 32)]));
         } else {
-            aa = mk(0.0, 0.0);
-            b = mk(1.0, 0.0);
-            c = mk(0.0, 0.0);
+            aa = mk(T(0), T(0));
+            b = mk(T(1), T(0));
+            c = mk(T(0), T(0));
         }
-        const cx<double> den = b - cmul(aa, cp);
-        const cx<double> inv = crecip(den);
+        const cx<T> den = b - cmul(aa, cp);
+        const cx<T> inv = crecip(den);
         cp = cmul(c, inv);
-        table[FCN_IDX((size_t)j * nq + q, (size_t)a.nr * nq, 30)] = mk(T(inv.x), T(inv.y));
+        table[FCN_IDX((size_t)j * nq + q, (size_t)a.nr * nq, 30)] = inv;
     }
 }
 
@@ -323,7 +331,7 @@ cudaError_t launch_cn(const ColArgs<T> &a, cudaStream_t st) {
 template <typename T>
 cudaError_t launch_cn_table(const TableArgs &a, cx<T> *table, cudaStream_t st) {
     const int nq = a.nt / 2 + 1;
-    const int threads = 64;
+    const int threads = 32;   // spread the latency-bound recurrences over many SMs
     cn_table_kernel<T><<<(nq + threads - 1) / threads, threads, 0, st>>>(a, table);
     return cudaGetLastError();
 }

@@ -266,6 +266,9 @@ struct fcn_ctx {
     int64_t prof_n[FCN_PROF_KINDS] = {0};
     float *mlp = nullptr;             // device FP32 master weights (FCN_MLP_NPARAM)
     bool has_mlp = false;
+    unsigned char *mlp_io = nullptr;  // features (8 floats) + proposal (double)
+    float *log_buf = nullptr;         // caller-owned host log of adaptive attempts
+    int64_t log_cap = 0, log_n = 0;
     int force_row = -1, force_col = -1;   // -1: autotune; else forced variant
     // batched work lists (FP32, K = 8, several pulses): one launch per stage
     bool batched = false;
@@ -737,6 +740,20 @@ int diag_impl(fcn_ctx *ctx, Pulse &pu, fcn_diag *out) {
     return out->nonfinite ? fail(ctx, FCN_ERR_NONFINITE, "field holds NaN or Inf") : FCN_OK;
 }
 
+// Runs the diagnostic row pass and the reduction on the field; the result
+// stays on the device in pu.red (see launch_reduce_stats).
+template <typename T>
+int diag_device(fcn_ctx *ctx, Pulse &pu, void *field) {
+    RowArgs<T> a = row_args<T>(pu, field, OP_STATS | OP_FFT | OP_SPEC | OP_NOSTORE, 0.0);
+    a.variant = 0;
+    CK(launch_rows<T>(a, pu.g.nt, ctx->st), "diagnostics row pass");
+    CK(launch_reduce_stats(pu.stats, pu.g.nr, pu.red, ctx->st), "diagnostics reduction");
+    return FCN_OK;
+}
+
+// Step doubling (controller 0) or MLP proposals judged by step doubling
+// (controller 1).  With a log buffer (fcn_mlp_set_log) every attempt appends
+// [f0..f5, log(h/L_ref), log(err/rtol)] for training.
 template <typename T>
 int propagate_impl(fcn_ctx *ctx, double z_end, double dz0, double rtol, double dz_min,
                    int max_reject, int controller, fcn_stats *out) {
@@ -745,7 +762,8 @@ int propagate_impl(fcn_ctx *ctx, double z_end, double dz0, double rtol, double d
     if (!pu.has_field) return fail(ctx, FCN_ERR_STATE, "fcn_set_field has not been called");
     if (!(dz0 > 0) || !std::isfinite(dz0) || !(rtol > 0) || !std::isfinite(z_end) || !(dz_min > 0))
         return fail(ctx, FCN_ERR_ARG, "bad adaptive arguments");
-    if (controller != 0) return fail(ctx, FCN_ERR_UNSUPPORTED, "controller not available");
+    if (controller != 0 && controller != 1) return fail(ctx, FCN_ERR_ARG, "controller must be 0 or 1");
+    if (controller == 1 && !ctx->has_mlp) return fail(ctx, FCN_ERR_STATE, "controller 1 needs MLP weights");
     const size_t bytes = csize(ctx->prec) * pu.points();
     if (!pu.tuned) {
         const cx<T> *tab = nullptr;
@@ -757,11 +775,54 @@ int propagate_impl(fcn_ctx *ctx, double z_end, double dz0, double rtol, double d
     }
     if (!pu.work1) CK(cudaMalloc(&pu.work1, bytes), "work buffer");
     if (!pu.work2) CK(cudaMalloc(&pu.work2, bytes), "work buffer");
+    const bool features = controller == 1 || ctx->log_buf != nullptr;
+    if (features && !ctx->mlp_io) CK(cudaMalloc(&ctx->mlp_io, 64), "controller buffer");
+    float *feat_d = reinterpret_cast<float *>(ctx->mlp_io);
+    double *dz_d = reinterpret_cast<double *>(ctx->mlp_io + 32);
+    const Consts cs = derive(pu.g, pu.p);
+    MlpScalars sc;
+    std::memset(&sc, 0, sizeof sc);
+    sc.rtol = rtol;
+    sc.l_ref = cs.k0 * (pu.g.r_max / 5.0) * (pu.g.r_max / 5.0) / 2.0;
+    sc.domega = cs.domega;
+    float hfeat[8] = {0};
+    double mlp_dz = 0.0;
+    auto features_of_field = [&](bool propose) -> int {
+        int rc = diag_device<T>(ctx, pu, pu.field);
+        if (rc) return rc;
+        CK(launch_mlp_propose(pu.red, sc, propose ? ctx->mlp : nullptr, feat_d, dz_d, ctx->st), "features");
+        CK(cudaMemcpyAsync(ctx->host_red + 8, feat_d, 7 * sizeof(float), cudaMemcpyDeviceToHost, ctx->st), "features copy");
+        if (propose)
+            CK(cudaMemcpyAsync(ctx->host_red + 12, dz_d, sizeof(double), cudaMemcpyDeviceToHost, ctx->st), "proposal copy");
+        CK(cudaStreamSynchronize(ctx->st), "features sync");
+        std::memcpy(hfeat, ctx->host_red + 8, 7 * sizeof(float));
+        if (propose) mlp_dz = ctx->host_red[12];
+        return FCN_OK;
+    };
+    if (features) {
+        // references from the field at the start of the run
+        int rc = diag_device<T>(ctx, pu, pu.field);
+        if (rc) return rc;
+        CK(cudaMemcpyAsync(ctx->host_red, pu.red, 8 * sizeof(double), cudaMemcpyDeviceToHost, ctx->st), "ref copy");
+        CK(cudaStreamSynchronize(ctx->st), "ref sync");
+        sc.i_ref = ctx->host_red[1] > 0 ? ctx->host_red[1] : 1.0;
+        if (ctx->host_red[4] > 0) {
+            const double mean = ctx->host_red[5] / ctx->host_red[4];
+            const double var = ctx->host_red[6] / ctx->host_red[4] - mean * mean;
+            sc.rms_ref = var > 0 ? std::sqrt(var) * cs.domega : 0.0;
+        }
+        sc.peak_prev = sc.i_ref;
+        sc.dz_prev = dz0;
+        sc.err_prev = rtol;
+        rc = features_of_field(false);
+        if (rc) return rc;
+    }
     fcn_stats s;
     std::memset(&s, 0, sizeof s);
     double dz = dz0;
     int consecutive = 0;
     int status = FCN_OK;
+    bool from_mlp = false;
     while (pu.z < z_end) {
         double h = dz;
         bool last = false;
@@ -781,20 +842,41 @@ int propagate_impl(fcn_ctx *ctx, double z_end, double dz0, double rtol, double d
         s.substeps += 3;
         s.last_err = err;
         if (!std::isfinite(err)) { status = fail(ctx, FCN_ERR_NONFINITE, "non-finite step-doubling error"); break; }
+        if (ctx->log_buf && ctx->log_n < ctx->log_cap) {
+            float *rec = ctx->log_buf + 8 * ctx->log_n;
+            for (int k = 0; k < 6; ++k) rec[k] = hfeat[k];
+            rec[6] = (float)std::log(h / sc.l_ref);
+            rec[7] = (float)std::log(std::fmax(err, 1e-30) / rtol);
+            ctx->log_n++;
+        }
         double fac = err > 0 ? 0.9 * std::cbrt(rtol / err) : 2.0;
         fac = fac < 0.2 ? 0.2 : (fac > 2.0 ? 2.0 : fac);
-        if (err <= rtol) {
+        const bool accepted = err <= rtol;
+        if (accepted) {
             std::swap(pu.field, pu.work2);
             pu.z = last ? z_end : pu.z + h;
             pu.steps++;
             s.accepted++;
+            if (from_mlp) s.mlp_proposals++;
             consecutive = 0;
             dz = last ? dz : h * fac;
+            if (features && pu.z < z_end) {
+                sc.peak_prev = hfeat[6];
+                sc.dz_prev = h;
+                sc.err_prev = err;
+                sc.dz_lo = std::fmax(0.2 * h, dz_min);
+                sc.dz_hi = 2.0 * h;
+                rc = features_of_field(controller == 1);
+                if (rc) return rc;
+                if (controller == 1 && std::isfinite(mlp_dz) && mlp_dz > 0) dz = mlp_dz;
+            }
+            from_mlp = controller == 1 && features && pu.z < z_end;
         } else {
             pu.rejected++;
             s.rejected++;
             consecutive++;
-            dz = h * fac;
+            dz = h * fac;          // the step-doubling formula is the fallback
+            from_mlp = false;
         }
         if (dz < dz_min || consecutive > max_reject) {
             status = fail(ctx, FCN_ERR_STEP_UNDERFLOW, "dz underflow or too many rejections");
@@ -990,6 +1072,7 @@ void fcn_destroy(fcn_ctx *ctx) {
         for (auto &kv : pu.tables) cudaFree(kv.second);
     }
     if (ctx->mlp) cudaFree(ctx->mlp);
+    cudaFree(ctx->mlp_io);
     for (auto &kv : ctx->batch_args) {
         cudaFree(kv.second.first);
         cudaFree(kv.second.second);
@@ -1202,6 +1285,116 @@ int fcn_profile_read(fcn_ctx *ctx, double *ms, int64_t *count, int32_t reset) {
         count[k] = ctx->prof_n[k];
         if (reset) { ctx->prof_ms[k] = 0; ctx->prof_n[k] = 0; }
     }
+    return FCN_OK;
+}
+
+int fcn_mlp_set_log(fcn_ctx *ctx, float *host_buf, int64_t capacity) {
+    if (!ctx || capacity < 0 || (capacity > 0 && !host_buf)) return FCN_ERR_ARG;
+    ctx->log_buf = capacity > 0 ? host_buf : nullptr;
+    ctx->log_cap = capacity;
+    ctx->log_n = 0;
+    return FCN_OK;
+}
+
+int64_t fcn_mlp_log_count(const fcn_ctx *ctx) { return ctx ? ctx->log_n : -1; }
+
+// Gradient of the mean squared error of the MLP (BF16 weights, FP32
+// accumulation) over n samples; stateless, for checking the training kernels.
+int fcn_mlp_loss_grad(const float *params, const float *x, const float *y, int32_t n, float *loss,
+                      float *grad) {
+    fcn_ctx *ctx = nullptr;
+    if (!params || !x || !y || n < 1 || !loss || !grad) return fail(nullptr, FCN_ERR_ARG, "bad MLP arguments");
+    const int np = mlp_nparam();
+    float *dW = nullptr, *dX = nullptr, *dY = nullptr, *dP = nullptr, *dG = nullptr, *dL = nullptr;
+    int *dI = nullptr;
+    std::vector<int> idx(n);
+    for (int i = 0; i < n; ++i) idx[i] = i;
+    cudaError_t e = cudaMalloc(&dW, sizeof(float) * np);
+    if (e == cudaSuccess) e = cudaMalloc(&dX, sizeof(float) * 6 * (size_t)n);
+    if (e == cudaSuccess) e = cudaMalloc(&dY, sizeof(float) * (size_t)n);
+    if (e == cudaSuccess) e = cudaMalloc(&dI, sizeof(int) * (size_t)n);
+    if (e == cudaSuccess) e = cudaMalloc(&dP, sizeof(float) * 64 * (np + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&dG, sizeof(float) * np);
+    if (e == cudaSuccess) e = cudaMalloc(&dL, sizeof(float));
+    if (e == cudaSuccess) e = cudaMemcpy(dW, params, sizeof(float) * np, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dX, x, sizeof(float) * 6 * (size_t)n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dY, y, sizeof(float) * (size_t)n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dI, idx.data(), sizeof(int) * (size_t)n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = launch_mlp_grad(dW, dX, dY, dI, n, dP, 64, dG, dL, nullptr);
+    if (e == cudaSuccess) e = cudaMemcpy(grad, dG, sizeof(float) * np, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(loss, dL, sizeof(float), cudaMemcpyDeviceToHost);
+    cudaFree(dW); cudaFree(dX); cudaFree(dY); cudaFree(dI); cudaFree(dP); cudaFree(dG); cudaFree(dL);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "MLP gradient");
+    return FCN_OK;
+}
+
+// Trains the context's MLP (initialised from the seed if no weights were
+// set) with Adam on minibatches of a seeded permutation of the n samples.
+int fcn_mlp_train(fcn_ctx *ctx, const float *x, const float *y, int32_t n, int32_t epochs, int32_t batch,
+                  float lr, uint64_t seed, float *final_loss) {
+    if (!ctx || !x || !y || n < 1 || epochs < 0 || batch < 1 || !(lr > 0)) return FCN_ERR_ARG;
+    const int np = mlp_nparam();
+    if (!ctx->mlp) CK(cudaMalloc(&ctx->mlp, sizeof(float) * np), "mlp weights");
+    uint64_t rs = seed * 6364136223846793005ull + 1442695040888963407ull;
+    auto rnd = [&]() {   // splitmix64 -> uniform [0, 1)
+        rs += 0x9E3779B97F4A7C15ull;
+        uint64_t z = rs;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        return (double)(z >> 11) * (1.0 / 9007199254740992.0);
+    };
+    if (!ctx->has_mlp) {
+        // uniform +-sqrt(6/(fan_in+fan_out)) weights, zero biases
+        std::vector<float> w(np, 0.f);
+        auto fill = [&](int off, int cnt, int fi, int fo) {
+            const double a = std::sqrt(6.0 / (fi + fo));
+            for (int i = 0; i < cnt; ++i) w[off + i] = (float)((2.0 * rnd() - 1.0) * a);
+        };
+        fill(0, 64 * 6, 6, 64);
+        fill(64 * 6 + 64, 64 * 64, 64, 64);
+        fill(64 * 6 + 64 + 64 * 64 + 64, 64, 64, 1);
+        CK(cudaMemcpy(ctx->mlp, w.data(), sizeof(float) * np, cudaMemcpyHostToDevice), "mlp init");
+        ctx->has_mlp = true;
+    }
+    float *dX = nullptr, *dY = nullptr, *dP = nullptr, *dG = nullptr, *dL = nullptr, *dm = nullptr, *dv = nullptr;
+    int *dI = nullptr;
+    cudaError_t e = cudaMalloc(&dX, sizeof(float) * 6 * (size_t)n);
+    if (e == cudaSuccess) e = cudaMalloc(&dY, sizeof(float) * (size_t)n);
+    if (e == cudaSuccess) e = cudaMalloc(&dI, sizeof(int) * (size_t)n);
+    if (e == cudaSuccess) e = cudaMalloc(&dP, sizeof(float) * 64 * (np + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&dG, sizeof(float) * np);
+    if (e == cudaSuccess) e = cudaMalloc(&dL, sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&dm, sizeof(float) * np);
+    if (e == cudaSuccess) e = cudaMalloc(&dv, sizeof(float) * np);
+    if (e == cudaSuccess) e = cudaMemset(dm, 0, sizeof(float) * np);
+    if (e == cudaSuccess) e = cudaMemset(dv, 0, sizeof(float) * np);
+    if (e == cudaSuccess) e = cudaMemcpy(dX, x, sizeof(float) * 6 * (size_t)n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dY, y, sizeof(float) * (size_t)n, cudaMemcpyHostToDevice);
+    std::vector<int> idx(n);
+    for (int i = 0; i < n; ++i) idx[i] = i;
+    int t = 0;
+    for (int ep = 0; ep < epochs && e == cudaSuccess; ++ep) {
+        for (int i = n - 1; i > 0; --i) {   // Fisher-Yates with the seeded generator
+            const int j = (int)(rnd() * (i + 1));
+            std::swap(idx[i], idx[j]);
+        }
+        e = cudaMemcpy(dI, idx.data(), sizeof(int) * (size_t)n, cudaMemcpyHostToDevice);
+        for (int b0 = 0; b0 < n && e == cudaSuccess; b0 += batch) {
+            const int nb = std::min(batch, n - b0);
+            e = launch_mlp_grad(ctx->mlp, dX, dY, dI + b0, nb, dP, 64, dG, dL, ctx->st);
+            if (e == cudaSuccess) e = launch_mlp_adam(ctx->mlp, dm, dv, dG, lr, ++t, ctx->st);
+        }
+    }
+    if (e == cudaSuccess && final_loss) {
+        for (int i = 0; i < n; ++i) idx[i] = i;
+        e = cudaMemcpy(dI, idx.data(), sizeof(int) * (size_t)n, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = launch_mlp_grad(ctx->mlp, dX, dY, dI, n, dP, 64, dG, dL, ctx->st);
+        if (e == cudaSuccess) e = cudaMemcpy(final_loss, dL, sizeof(float), cudaMemcpyDeviceToHost);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->st);
+    cudaFree(dX); cudaFree(dY); cudaFree(dI); cudaFree(dP); cudaFree(dG); cudaFree(dL); cudaFree(dm); cudaFree(dv);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "MLP training");
     return FCN_OK;
 }
 

@@ -171,6 +171,18 @@ cudaError_t launch_cn_batch(const ColArgs<T> *pulses, const int4 *items, int nit
 // shared-memory bytes of the batched row kernel for rows of nt points
 size_t row_batch_smem(int nt, int bytes_per_complex);
 
+// Learned dz controller (mlp.cu).
+struct MlpScalars {
+    double i_ref, rms_ref, peak_prev, dz_prev, err_prev, rtol, l_ref, domega, dz_lo, dz_hi;
+};
+int mlp_nparam();
+cudaError_t launch_mlp_grad(const float *W, const float *X, const float *Y, const int *idx, int n,
+                            float *partial, int max_cta, float *grad, float *loss, cudaStream_t st);
+cudaError_t launch_mlp_adam(float *W, float *m, float *v, const float *g, float lr, int t, cudaStream_t st);
+// features (7 floats: f0..f5 and the peak intensity) and, with W, dz_out
+cudaError_t launch_mlp_propose(const double *red, const MlpScalars &sc, const float *W, float *features,
+                               double *dz_out, cudaStream_t st);
+
 // reductions and conversions
 template <typename T>
 cudaError_t launch_widen(const cx<T> *src, double *dst, int64_t n, cudaStream_t st);

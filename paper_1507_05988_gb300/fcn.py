@@ -101,6 +101,11 @@ _SIGS = {
     "fcn_profile_read": (C.c_int, [_CTX, _D, C.POINTER(C.c_int64), C.c_int32]),
     "fcn_mlp_set": (C.c_int, [_CTX, _F]),
     "fcn_mlp_get": (C.c_int, [_CTX, _F]),
+    "fcn_mlp_set_log": (C.c_int, [_CTX, _F, C.c_int64]),
+    "fcn_mlp_log_count": (C.c_int64, [_CTX]),
+    "fcn_mlp_train": (C.c_int, [_CTX, _F, _F, C.c_int32, C.c_int32, C.c_int32, C.c_float,
+                                C.c_uint64, _F]),
+    "fcn_mlp_loss_grad": (C.c_int, [_F, _F, _F, C.c_int32, _F, _F]),
     "fcn_op_rows": (C.c_int, [_G, _PR, C.c_int32, C.c_int32, C.c_double, _P, _P, _P]),
     "fcn_cn_table_entries": (C.c_int64, [_G]),
     "fcn_op_cn_table": (C.c_int, [_G, _PR, C.c_int32, C.c_double, _P, _P]),
@@ -146,6 +151,18 @@ def grid_params(phys: dict):
     p = make_params(phys["lambda0"], phys["n0"], phys["n2j"], phys["k2"], phys["sigma_k"],
                     phys["rho_nt"], phys["K"], phys["flags"])
     return g, p
+
+
+def mlp_loss_grad(params, x, y):
+    """GPU mean squared error and gradient of the dz network (stateless)."""
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    xx = np.ascontiguousarray(x, dtype=np.float32)
+    yy = np.ascontiguousarray(y, dtype=np.float32)
+    loss = C.c_float()
+    g = np.zeros(FCN_MLP_NPARAM, np.float32)
+    check(fcn_mlp_loss_grad(p.ctypes.data_as(_F), xx.ctypes.data_as(_F), yy.ctypes.data_as(_F),
+                            yy.size, C.byref(loss), g.ctypes.data_as(_F)), None)
+    return loss.value, g
 
 
 def stream_ptr(stream=None):
@@ -257,6 +274,35 @@ class Solver:
         check(fcn_profile_read(self.ctx, ms, n, 1 if reset else 0), self.ctx)
         names = ("row_head", "row_mid", "row_tail", "column")
         return {names[k]: (ms[k], n[k]) for k in range(FCN_PROF_KINDS)}
+
+    # ---- learned dz ----
+    def mlp_set(self, params):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        assert p.size == FCN_MLP_NPARAM
+        check(fcn_mlp_set(self.ctx, p.ctypes.data_as(_F)), self.ctx)
+
+    def mlp_get(self) -> np.ndarray:
+        p = np.empty(FCN_MLP_NPARAM, np.float32)
+        check(fcn_mlp_get(self.ctx, p.ctypes.data_as(_F)), self.ctx)
+        return p
+
+    def mlp_log(self, capacity: int):
+        """Starts logging adaptive attempts; returns the buffer (kept alive here)."""
+        self._log = np.zeros((max(capacity, 0), 8), np.float32)
+        check(fcn_mlp_set_log(self.ctx, self._log.ctypes.data_as(_F), int(capacity)), self.ctx)
+        return self._log
+
+    def mlp_log_records(self) -> np.ndarray:
+        n = fcn_mlp_log_count(self.ctx)
+        return self._log[:n].copy()
+
+    def mlp_train(self, x, y, epochs=50, batch=256, lr=1e-3, seed=0) -> float:
+        xx = np.ascontiguousarray(x, dtype=np.float32)
+        yy = np.ascontiguousarray(y, dtype=np.float32)
+        loss = C.c_float()
+        check(fcn_mlp_train(self.ctx, xx.ctypes.data_as(_F), yy.ctypes.data_as(_F), yy.size,
+                            int(epochs), int(batch), float(lr), int(seed), C.byref(loss)), self.ctx)
+        return loss.value
 
     def set_state(self, s, pulse: int = 0):
         s = np.ascontiguousarray(s, dtype=np.float64)

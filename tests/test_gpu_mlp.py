@@ -1,0 +1,106 @@
+"""The learned dz controller: GPU training kernels against the FP64 CPU
+oracle's MLP, and the controller end to end (data from step-doubling runs,
+training on the GPU, proposals judged by step doubling)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1507_05988_gb300 import workloads as W
+from tests.conftest import rel_l2
+
+pytestmark = pytest.mark.gpu
+NIN, NH = 6, 64
+
+
+@pytest.fixture(scope="module")
+def fcn():
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    from paper_1507_05988_gb300 import build
+    build.build()
+    from paper_1507_05988_gb300 import fcn as m
+    return m
+
+
+def _bf16(p):
+    """Round to bfloat16 (the precision the kernels use the weights in)."""
+    return torch.tensor(np.asarray(p, np.float32)).to(torch.bfloat16).float().numpy().astype(np.float64)
+
+
+def test_mlp_gradient_matches_the_oracle(fcn):
+    rng = np.random.default_rng(2)
+    npar = oracle.mlp_param_count(NIN, NH)
+    assert npar == fcn.FCN_MLP_NPARAM
+    params = (0.3 * rng.standard_normal(npar)).astype(np.float32)
+    x = rng.standard_normal((300, NIN)).astype(np.float32)
+    y = rng.standard_normal(300).astype(np.float32)
+    loss, g = fcn.mlp_loss_grad(params, x, y)
+    lref, gref = oracle.mlp_loss_grad(_bf16(params), x.astype(np.float64), y.astype(np.float64),
+                                      NIN, NH)
+    assert loss == pytest.approx(lref, rel=1e-5)
+    assert rel_l2(g, gref) < 1e-5
+
+
+def test_mlp_training_fits_a_smooth_function(fcn):
+    rng = np.random.default_rng(4)
+    x = rng.uniform(-1, 1, (2048, NIN)).astype(np.float32)
+    y = (np.sin(x[:, 0]) + 0.5 * x[:, 1] * x[:, 2] - x[:, 4] / 3).astype(np.float32)
+    wl = W.small(8, 16)
+    s = fcn.Solver(wl.physics(), precision=fcn.FCN_FP32_MIXED)
+    l0 = s.mlp_train(x, y, epochs=0, seed=1)
+    l1 = s.mlp_train(x, y, epochs=60, batch=128, lr=3e-3, seed=1)
+    s.close()
+    assert l1 < 0.05 * l0 and l1 < 5e-3
+
+
+def _adaptive(fcn, wl, prec, z_end, dz0, rtol, controller, params=None, log=0):
+    s = fcn.Solver(wl.physics(), precision=prec)
+    if params is not None:
+        s.mlp_set(params)
+    if log:
+        s.mlp_log(log)
+    s.set_field(wl.field())
+    st = s.propagate(z_end, dz0, rtol=rtol, controller=controller)
+    A = s.get_field()
+    rec = s.mlp_log_records() if log else None
+    s.close()
+    return A, st, rec
+
+
+def test_learned_dz_controller_end_to_end(fcn):
+    """Training data from step-doubling runs of three grids at several noise
+    seeds; the network is trained on the GPU; the learned controller (its
+    proposals judged by step doubling, the formula as fallback) lands on
+    z_end within the tolerance of a fine reference, and its step count is
+    reported next to plain step doubling."""
+    rtol, z_end = 1e-4, 1.0
+    recs = []
+    for seed in range(1, 7):
+        for wl in (W.small(48, 256, p_over_pcr=3.0, noise_seed=seed),
+                   W.small(32, 512, w0=2e-3, tp=50e-15, p_over_pcr=5.0, noise_seed=seed,
+                           n2j=(W.N2, W.N4, 0, 0)),
+                   W.small(40, 256, w0=1.5e-3, p_over_pcr=6.0, noise_seed=seed)):
+            _, _, r = _adaptive(fcn, wl, fcn.FCN_FP32_MIXED, z_end, 0.01, rtol, 0, log=4000)
+            recs.append(r)
+    rec = np.concatenate(recs)
+    x = rec[:, :6]
+    y = rec[:, 6] - rec[:, 7] / 3.0                 # log(dz_safe / L_ref)
+    assert len(y) > 200 and np.all(np.isfinite(x)) and np.all(np.isfinite(y))
+    wl = W.small(48, 256, p_over_pcr=4.0, noise_seed=11)
+    s = fcn.Solver(wl.physics(), precision=fcn.FCN_FP32_MIXED)
+    loss = s.mlp_train(x, y, epochs=200, batch=128, lr=2e-3, seed=0)
+    params = s.mlp_get()
+    s.close()
+    assert loss < 0.05 * np.var(y)
+    A0, st0, _ = _adaptive(fcn, wl, fcn.FCN_FP32_MIXED, z_end, 0.01, rtol, 0)
+    A1, st1, _ = _adaptive(fcn, wl, fcn.FCN_FP32_MIXED, z_end, 0.01, rtol, 1, params=params)
+    pb = oracle.Problem(**wl.physics())
+    ref, _ = oracle.run(pb, z_end / 2000, 2000, wl.field())
+    for A, st in ((A0, st0), (A1, st1)):
+        assert st["z"] == z_end
+        assert rel_l2(A, ref) < 30 * rtol
+    assert st1["mlp_proposals"] > 0
+    print(f"\nplain step doubling: accepted {st0['accepted']} rejected {st0['rejected']} "
+          f"substeps {st0['substeps']}; learned dz: accepted {st1['accepted']} "
+          f"rejected {st1['rejected']} substeps {st1['substeps']} (mlp proposals {st1['mlp_proposals']})")
