@@ -235,14 +235,29 @@ struct Pulse {
     const void *tw = nullptr;
     const void *lo = nullptr, *hi = nullptr;
     const double *lo64 = nullptr, *hi64 = nullptr;
-    std::map<uint64_t, void *> tables;   // dz bits -> pivot table
-    std::vector<uint64_t> table_lru;
     double z = 0.0, dz_next = 0.0;
     int64_t steps = 0, rejected = 0;
     bool has_field = false;
     int row_var = 0, col_var = 0;   // kernel variants in use
     bool tuned = false;
     int64_t points() const { return (int64_t)g.nr * g.nt; }
+};
+
+struct TableKey {
+    int nr, nt;
+    uint64_t s, dk;   // bit patterns of s and the delta coefficient
+    bool operator<(const TableKey &o) const {
+        if (nr != o.nr) return nr < o.nr;
+        if (nt != o.nt) return nt < o.nt;
+        if (s != o.s) return s < o.s;
+        return dk < o.dk;
+    }
+};
+
+struct TableEntry {
+    void *ptr;
+    uint64_t dz;      // dz bits the table was built for (graphs keyed by dz)
+    uint64_t stamp;   // last use
 };
 
 struct GraphKey {
@@ -257,6 +272,8 @@ struct fcn_ctx {
     cudaStream_t cap = nullptr;       // internal stream used for graph capture
     std::vector<Pulse> pulses;
     std::map<GraphKey, cudaGraphExec_t> graphs;
+    std::map<TableKey, TableEntry> tables;   // shared pivot tables
+    uint64_t table_clock = 0;
     std::string err = "no error";
     double *host_red = nullptr;       // pinned [16]
     // kernel timing (fcn_profile_enable): one event pair per launch, by kind
@@ -306,32 +323,48 @@ uint64_t dz_key(double dz) {
     return k;
 }
 
+// Pivot tables are shared by every pulse of the context whose (Nr, Nt, s,
+// delta coefficient) match -- identical grids and physics at the same dz --
+// so a batch of equal pulses streams one table (L2-resident) instead of one
+// per pulse.  Least-recently used tables beyond 2 per pulse + 8 are freed,
+// together with the graphs and batch arguments captured with them.
 template <typename T>
 int ensure_table(fcn_ctx *ctx, Pulse &pu, double dz, const cx<T> **out) {
-    const uint64_t key = dz_key(dz);
-    auto it = pu.tables.find(key);
-    if (it != pu.tables.end()) { *out = (const cx<T> *)it->second; return FCN_OK; }
-    // small LRU: at most 8 tables per pulse; graphs that captured an evicted
-    // table are dropped with it
-    if (pu.tables.size() >= 8) {
-        const uint64_t old = pu.table_lru.front();
-        pu.table_lru.erase(pu.table_lru.begin());
+    TableKey key;
+    key.nr = pu.g.nr;
+    key.nt = pu.g.nt;
+    double s, dk;
+    cn_coefs(pu.g, pu.p, dz, &s, &dk);
+    key.s = dz_key(s);
+    key.dk = dz_key(dk);
+    auto it = ctx->tables.find(key);
+    if (it != ctx->tables.end()) {
+        it->second.stamp = ++ctx->table_clock;
+        *out = (const cx<T> *)it->second.ptr;
+        return FCN_OK;
+    }
+    const size_t cap = 2 * ctx->pulses.size() + 8;
+    if (ctx->tables.size() >= cap) {
+        auto old = ctx->tables.begin();
+        for (auto t = ctx->tables.begin(); t != ctx->tables.end(); ++t)
+            if (t->second.stamp < old->second.stamp) old = t;
         CK(cudaStreamSynchronize(ctx->st), "sync before table eviction");
+        const uint64_t odz = old->second.dz;
         for (int kind = 0; kind < 4; ++kind) {
-            auto g = ctx->graphs.find(GraphKey{kind, old});
+            auto g = ctx->graphs.find(GraphKey{kind, odz});
             if (g != ctx->graphs.end()) {
                 cudaGraphExecDestroy(g->second);
                 ctx->graphs.erase(g);
             }
         }
-        auto ba = ctx->batch_args.find(old);
+        auto ba = ctx->batch_args.find(odz);
         if (ba != ctx->batch_args.end()) {
             cudaFree(ba->second.first);
             cudaFree(ba->second.second);
             ctx->batch_args.erase(ba);
         }
-        cudaFree(pu.tables[old]);
-        pu.tables.erase(old);
+        cudaFree(old->second.ptr);
+        ctx->tables.erase(old);
     }
     const size_t n = (size_t)pu.g.nr * (pu.g.nt / 2 + 1);
     void *d = nullptr;
@@ -339,12 +372,12 @@ int ensure_table(fcn_ctx *ctx, Pulse &pu, double dz, const cx<T> **out) {
     TableArgs ta;
     ta.nr = pu.g.nr;
     ta.nt = pu.g.nt;
-    cn_coefs(pu.g, pu.p, dz, &ta.s, &ta.dk);
+    ta.s = s;
+    ta.dk = dk;
     ta.lo = pu.lo64;
     ta.hi = pu.hi64;
     CK(launch_cn_table<T>(ta, (cx<T> *)d, ctx->st), "pivot table kernel");
-    pu.tables[key] = d;
-    pu.table_lru.push_back(key);
+    ctx->tables[key] = TableEntry{d, dz_key(dz), ++ctx->table_clock};
     *out = (const cx<T> *)d;
     return FCN_OK;
 }
@@ -1069,8 +1102,8 @@ void fcn_destroy(fcn_ctx *ctx) {
         cudaFree(pu.red);
         cudaFree(pu.rows);
         cudaFree(pu.stage);
-        for (auto &kv : pu.tables) cudaFree(kv.second);
     }
+    for (auto &kv : ctx->tables) cudaFree(kv.second.ptr);
     if (ctx->mlp) cudaFree(ctx->mlp);
     cudaFree(ctx->mlp_io);
     for (auto &kv : ctx->batch_args) {

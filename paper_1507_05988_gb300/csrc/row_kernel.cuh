@@ -305,19 +305,27 @@ __device__ __forceinline__ T rk4_coef(T ia, T ib, T xa, T xb, const NLCoef<T> &c
 
 template <typename T>
 __device__ __forceinline__ void sincos_t(T x, T *s, T *c);
-// FP32 sine and cosine of a nonlinear phase (|x| is a few rad at most in
-// practice).  The hardware approximations are biased near the arguments that
-// occur here (|exp(i phi)| off by ~1e-7), which accumulates into an energy
-// drift, so this is an accurate evaluation written from the series:
-// Cody & Waite's reduction x = n pi/2 + r with pi/2 split into two floats
-// (the product n*PIO2_HI is exact inside the FMA), then Taylor polynomials
-// of degree 9 (sin) and 10 (cos) on |r| <= pi/4, whose truncation errors are
-// below 2e-9 and 1.2e-10 -- under half an ulp.  Arguments beyond 1e4 rad,
-// where the two-float reduction loses digits, go to the library.
-template <>
-__device__ __forceinline__ void sincos_t<float>(float x, float *s, float *c) {
+// FP32 sine and cosine minus one of a nonlinear phase.  The factor
+// exp(i x) is applied in delta form (A + A (exp(i x) - 1)), because a float
+// cosine that rounds to 1 for small x gives |(cos, sin)|^2 = 1 + x^2 > 1 --
+// a systematic energy gain in the weak tails of the pulse.  Evaluation:
+// |x| < 1e-3: series (next terms below 5e-14);  otherwise Cody & Waite's
+// reduction x = n pi/2 + r with pi/2 split into two floats (n*PIO2_HI exact
+// inside the FMA) and Taylor polynomials of degree 9 (sin) and 10 (cos) on
+// |r| <= pi/4, truncation below 2e-9 and 1.2e-10, with cos r - 1 kept
+// without adding 1 (no cancellation); arguments beyond 1e4 rad, where the
+// two-float reduction loses digits, go to the library.
+__device__ __forceinline__ void sincos_m1_f32(float x, float *s, float *cm1) {
+    if (fabsf(x) < 1.0e-3f) {
+        const float x2 = x * x;
+        *cm1 = -0.5f * x2;
+        *s = fmaf(x * x2, -1.66666666666666666667e-1f, x);
+        return;
+    }
     if (fabsf(x) > 1.0e4f) {
-        sincosf(x, s, c);
+        float c;
+        sincosf(x, s, &c);
+        *cm1 = c - 1.0f;
         return;
     }
     constexpr float TWO_OVER_PI = 0.636619772367581343076f;
@@ -332,18 +340,30 @@ __device__ __forceinline__ void sincos_t<float>(float x, float *s, float *c) {
     ps = fmaf(r2, ps, 8.33333333333333333333e-3f);
     ps = fmaf(r2, ps, -1.66666666666666666667e-1f);
     const float sr = fmaf(r * r2, ps, r);
-    // cos r = 1 - r^2/2! + r^4/4! - r^6/6! + r^8/8! - r^10/10!
+    // cos r - 1 = -r^2/2! + r^4/4! - r^6/6! + r^8/8! - r^10/10!
     float pc = fmaf(r2, -2.75573192239858906526e-7f, 2.48015873015873015873e-5f);
     pc = fmaf(r2, pc, -1.38888888888888888889e-3f);
     pc = fmaf(r2, pc, 4.16666666666666666667e-2f);
     pc = fmaf(r2, pc, -0.5f);
-    const float cr = fmaf(r2, pc, 1.0f);
-    const int q = int(n) & 3;
-    const float ss = (q & 1) ? cr : sr;
-    const float cc = (q & 1) ? sr : cr;
-    *s = (q & 2) ? -ss : ss;
-    *c = ((q + 1) & 2) ? -cc : cc;
+    const float crm1 = r2 * pc;
+    const float cr = crm1 + 1.0f;
+    switch (int(n) & 3) {
+        case 0: *s = sr; *cm1 = crm1; break;
+        case 1: *s = cr; *cm1 = -sr - 1.0f; break;
+        case 2: *s = -sr; *cm1 = -cr - 1.0f; break;
+        default: *s = -cr; *cm1 = sr - 1.0f; break;
+    }
 }
+
+// exp(x) - 1 in FP32: the loss exponent is tiny except near the peak; the
+// series x + x^2/2 is exact to float rounding there (x^3/6 < 2e-13).
+__device__ __forceinline__ float expm1_f32(float x) {
+    if (fabsf(x) < 1.0e-4f) return fmaf(0.5f * x, x, x);
+    return expm1f(x);
+}
+
+template <typename T>
+__device__ __forceinline__ void sincos_t(T x, T *s, T *c);
 template <>
 __device__ __forceinline__ void sincos_t<double>(double x, double *s, double *c) { sincos(x, s, c); }
 template <typename T>
@@ -375,11 +395,22 @@ __device__ __forceinline__ cx<T> nl_apply(cx<T> a, T ih, T ihKm1, T u, const NLC
         loss = c.loss * ihKm1;
         if (c.flags & PH_MPI_SAT) loss *= (T(1) - u);
     }
-    T s, co;
-    sincos_t<T>(c.h * phase, &s, &co);
-    const T amp = (c.flags & PH_MPI) ? exp_t<T>(-c.h * loss) : T(1);
-    const cx<T> e = mk(amp * co, amp * s);
-    return cmul(a, e);
+    if constexpr (sizeof(T) == 4) {
+        // delta form: A + A D with D = amp exp(i phi) - 1
+        //   = (em1 + cm1 + em1 cm1) + i s (1 + em1),  em1 = amp - 1
+        float sn, cm1;
+        sincos_m1_f32(c.h * phase, &sn, &cm1);
+        const float em1 = (c.flags & PH_MPI) ? expm1_f32(-c.h * loss) : 0.0f;
+        const float dre = fmaf(em1, cm1, em1 + cm1);
+        const float dim = fmaf(sn, em1, sn);
+        return mk(fmaf(a.x, dre, fmaf(-a.y, dim, a.x)), fmaf(a.x, dim, fmaf(a.y, dre, a.y)));
+    } else {
+        T s, co;
+        sincos_t<T>(c.h * phase, &s, &co);
+        const T amp = (c.flags & PH_MPI) ? exp_t<T>(-c.h * loss) : T(1);
+        const cx<T> e = mk(amp * co, amp * s);
+        return cmul(a, e);
+    }
 }
 
 // Exclusive (+)-scan of one value per thread across the TPR threads of a row.

@@ -54,6 +54,15 @@ def test_mlp_training_fits_a_smooth_function(fcn):
     assert l1 < 0.05 * l0 and l1 < 5e-3
 
 
+def training_set(rec):
+    """Features and labels from logged attempts: the step the controller can
+    take next, i.e. the safe step h (rtol/err)^(1/3) (Strang: O(dz^3) local
+    error) limited to [0.2, 2] h like the step-doubling formula, with a 0.95
+    margin; as log(dz / L_ref)."""
+    growth = np.clip(-rec[:, 7] / 3.0, np.log(0.2), np.log(2.0))
+    return rec[:, :6], rec[:, 6] + growth + np.log(0.95)
+
+
 def _adaptive(fcn, wl, prec, z_end, dz0, rtol, controller, params=None, log=0):
     s = fcn.Solver(wl.physics(), precision=prec)
     if params is not None:
@@ -84,8 +93,7 @@ def test_learned_dz_controller_end_to_end(fcn):
             _, _, r = _adaptive(fcn, wl, fcn.FCN_FP32_MIXED, z_end, 0.01, rtol, 0, log=4000)
             recs.append(r)
     rec = np.concatenate(recs)
-    x = rec[:, :6]
-    y = rec[:, 6] - rec[:, 7] / 3.0                 # log(dz_safe / L_ref)
+    x, y = training_set(rec)
     assert len(y) > 200 and np.all(np.isfinite(x)) and np.all(np.isfinite(y))
     wl = W.small(48, 256, p_over_pcr=4.0, noise_seed=11)
     s = fcn.Solver(wl.physics(), precision=fcn.FCN_FP32_MIXED)
