@@ -295,6 +295,187 @@ cn_batch_kernel(const ColArgs<T> *__restrict__ pulses, const int4 *__restrict__ 
     }
 }
 
+// ---------------------------------------------------------------------------
+// Staged variant.  Same chunked scan, but each thread first copies its chunk
+// (rows j0-1 .. j0+L of its column, and the L pivots) into private
+// shared-memory slots with cp.async, so no registers are held by loads in
+// flight, and the per-row coefficients come from one CnCoef row instead of
+// index tests.  The first sweep turns each slot into what the later sweeps
+// need (x_j -> alpha_j, 1/piv_j -> gamma_j), so every later pass is one
+// shared-memory load and one complex multiply-add per row.  Slot k of thread
+// t sits at k * blockDim + t: consecutive lanes, consecutive words.
+// ---------------------------------------------------------------------------
+
+// One complex value global -> shared, asynchronously; valid = false writes
+// zeros without reading the source.
+template <typename T>
+__device__ __forceinline__ void cp_async_cx(cx<T> *dst, const cx<T> *src, bool valid) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    const int n = valid ? int(sizeof(cx<T>)) : 0;
+    if constexpr (sizeof(cx<T>) == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+constexpr size_t kCnStagedSmemMax = 227 * 1024;
+
+template <typename T, int L>
+__device__ __forceinline__ void cn_staged_body(const ColArgs<T> &a, int C, int g, unsigned char *smem_raw) {
+    const int BD = blockDim.x;
+    const int tid = threadIdx.x;
+    const int nwarp = BD >> 5;
+    cx<T> *smA = reinterpret_cast<cx<T> *>(smem_raw);
+    cx<T> *smB = smA + nwarp * C;
+    cx<T> *smC = smB + nwarp * C;
+    cx<T> *Xt = smC + nwarp * C + tid;          // slot k: Xt[k * BD], k = 0 .. L+1
+    cx<T> *Gt = Xt + (L + 2) * BD;              // slot k: Gt[k * BD], k = 0 .. L-1
+
+    const int col = tid % C;
+    const int chunk = tid / C;
+    const int q = g * C + col;
+    const int nt = a.nt, nr = a.nr;
+    const int nq = nt / 2 + 1;
+    const int qq = (q <= nt / 2) ? q : nt - q;
+    const T delta = a.dk * T(qq) * T(qq);
+    const int j0 = chunk * L;
+
+    {
+        // rows outside 0..nr-1 are zero-filled (the source is then not read;
+        // the base address stands in for it)
+        const cx<T> *src = a.field + (ptrdiff_t)(j0 - 1) * nt + q;
+#pragma unroll
+        for (int k = 0; k < L + 2; ++k, src += nt) {
+            const int j = j0 - 1 + k;
+            const bool ok = j >= 0 && j < nr;
+            cp_async_cx(Xt + k * BD, ok ? src : a.field, ok);
+        }
+        const cx<T> *pv = a.invden + (size_t)j0 * nq + qq;
+#pragma unroll
+        for (int k = 0; k < L; ++k, pv += nq) {
+            const bool ok = j0 + k < nr;
+            cp_async_cx(Gt + k * BD, ok ? pv : a.invden, ok);
+        }
+    }
+    cp_async_wait_all();
+
+    // forward sweep, pass 1: beta_j, alpha_j, gamma_j and the chunk map
+    cx<T> y[L];
+    cx<T> PA = mk(T(1), T(0)), PB = czero<T>();
+    cx<T> xm = Xt[0], x0 = Xt[BD];
+#pragma unroll
+    for (int k = 0; k < L; ++k) {
+        const int j = j0 + k;
+        const cx<T> xp = Xt[(k + 2) * BD];
+        const cx<T> inv = Gt[k * BD];
+        CnCoef<T> cf;
+        if (j < nr - 1) {
+            cf = a.coef[FCN_IDX(j, nr, 46)];
+        } else {
+            cf.sl = T(0); cf.sh = T(0); cf.c0 = T(0); cf.d = T(0);
+        }
+        const T cd = cf.d * (cf.c0 - delta);
+        const T wx = cf.sl * xm.x + cf.sh * xp.x - cd * x0.x;
+        const T wy = cf.sl * xm.y + cf.sh * xp.y - cd * x0.y;
+        const cx<T> rhs = mk(cf.d * x0.x - wy, cf.d * x0.y + wx);
+        const cx<T> beta = cmul(rhs, inv);
+        const cx<T> al = cmul_i(inv, cf.sl);
+        Xt[(k + 1) * BD] = al;                  // x_j (slot k+1) is no longer read
+        Gt[k * BD] = cmul_i(inv, cf.sh);
+        PB = cmul(al, PB) + beta;
+        PA = cmul(al, PA);
+        y[k] = beta;
+        xm = x0;
+        x0 = xp;
+        asm volatile("" ::: "memory");          // keep the slot loads in row order
+    }
+    // forward sweep, pass 2: exact y from the carry entering the chunk
+    {
+        cx<T> yp = chunk_scan<T, false>(PA, PB, C, col, smA, smB, smC);
+#pragma unroll
+        for (int k = 0; k < L; ++k) {
+            y[k] = cmul(Xt[(k + 1) * BD], yp) + y[k];
+            yp = y[k];
+            asm volatile("" ::: "memory");
+        }
+    }
+    // backward sweep, pass 1: chunk map x_first = QA x_next + QB
+    cx<T> QA = mk(T(1), T(0)), QB = czero<T>();
+#pragma unroll
+    for (int k = L - 1; k >= 0; --k) {
+        const cx<T> ga = Gt[k * BD];
+        QB = cmul(ga, QB) + y[k];
+        QA = cmul(ga, QA);
+        asm volatile("" ::: "memory");
+    }
+    // backward sweep, pass 2 and store
+    cx<T> xn = chunk_scan<T, true>(QA, QB, C, col, smA, smB, smC);
+#pragma unroll
+    for (int k = L - 1; k >= 0; --k) {
+        const int j = j0 + k;
+        xn = cmul(Gt[k * BD], xn) + y[k];
+        if (j < nr) a.field[FCN_IDX((size_t)j * nt + q, (size_t)nr * nt, 47)] = xn;
+        asm volatile("" ::: "memory");
+    }
+}
+
+// Register budget: 3 CTAs of 256 threads per SM for 16-row chunks, 2 CTAs of
+// 512 threads for 8-row chunks (the launcher keeps the CTA within this size).
+template <typename T, int L>
+constexpr int staged_threads() { return L >= 16 ? 256 : 512; }
+
+template <typename T, int L>
+__global__ void __launch_bounds__(staged_threads<T, L>(), L >= 16 ? 3 : 2)
+cn_staged_kernel(ColArgs<T> a, int C) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int ngroups = a.nt / C;
+    const int b = blockIdx.x;
+    const int g = (b & 1) ? (ngroups - 1 - (b >> 1)) : (b >> 1);
+    cn_staged_body<T, L>(a, C, g, smem_raw);
+}
+
+template <typename T>
+__global__ void cn_coef_kernel(TableArgs a, CnCoef<T> *coef) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= a.nr) return;
+    const T s = T(a.s);
+    CnCoef<T> c;
+    if (j == 0) {
+        c.sl = T(0); c.sh = T(4) * s; c.c0 = T(4) * s; c.d = T(1);
+    } else if (j < a.nr - 1) {
+        c.sl = s * T(a.lo[j]); c.sh = s * T(a.hi[j]); c.c0 = T(2) * s; c.d = T(1);
+    } else {
+        c.sl = T(0); c.sh = T(0); c.c0 = T(0); c.d = T(0);
+    }
+    coef[j] = c;
+}
+
+// Chunk length L; C columns per CTA (one 32-byte sector when the column fits
+// the CTA size, fewer for tall grids, more for short ones).  Returns
+// cudaErrorInvalidConfiguration when the grid does not fit (the caller then
+// falls back to the register variant).
+template <typename T, int L>
+cudaError_t launch_cn_staged_l(const ColArgs<T> &a, cudaStream_t st) {
+    if (!a.coef) return cudaErrorInvalidConfiguration;
+    constexpr int CMIN = 32 / int(sizeof(cx<T>));
+    constexpr int TMAX = staged_threads<T, L>();
+    const int P = (a.nr + L - 1) / L;
+    int C = CMIN;
+    while (C > 1 && C * P > TMAX) C /= 2;                 // tall grids: fewer columns
+    while (C * 2 * P <= TMAX / 2 && C * 2 <= 32) C *= 2;  // short grids: more columns
+    if (C > a.nt) C = a.nt;
+    const int threads = ((C * P + 31) / 32) * 32;
+    if (threads > TMAX) return cudaErrorInvalidConfiguration;
+    const size_t smem = sizeof(cx<T>) * (3 * (size_t)(threads / 32) * C + (size_t)(2 * L + 2) * threads);
+    if (smem > kCnStagedSmemMax) return cudaErrorInvalidConfiguration;
+    cn_staged_kernel<T, L><<<a.nt / C, threads, smem, st>>>(a, C);
+    return cudaGetLastError();
+}
+
 template <typename T, int L>
 cudaError_t launch_cn_l(const ColArgs<T> &a, int target, cudaStream_t st) {
     constexpr int CMIN = 32 / int(sizeof(cx<T>));   // one 32-byte sector of columns
@@ -322,9 +503,30 @@ cudaError_t launch_cn(const ColArgs<T> &a, cudaStream_t st) {
     constexpr int LS = LL / 2;                      // short chunk
     const int target = (a.variant & 2) ? 512 : 256;
     cudaError_t e = cudaErrorInvalidConfiguration;
-    if (a.variant & 1) e = launch_cn_l<T, LS>(a, target, st);
+    if (a.variant >= kColStagedFirst) {
+        e = (a.variant == kColStagedFirst) ? launch_cn_staged_l<T, LL>(a, st) : launch_cn_staged_l<T, LS>(a, st);
+        if (e != cudaErrorInvalidConfiguration) return e;
+    }
+    if (a.variant < kColStagedFirst && (a.variant & 1)) e = launch_cn_l<T, LS>(a, target, st);
     if (e == cudaErrorInvalidConfiguration) e = launch_cn_l<T, LL>(a, target, st);
     if (e == cudaErrorInvalidConfiguration) e = launch_cn_l<T, LL>(a, 256, st);
+    return e;
+}
+
+template <typename T>
+cudaError_t launch_cn_coef(const TableArgs &a, CnCoef<T> *coef, cudaStream_t st) {
+    cn_coef_kernel<T><<<(a.nr + 127) / 128, 128, 0, st>>>(a, coef);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t prepare_cn() {
+    constexpr int LL = sizeof(T) == 4 ? 16 : 8;
+    cudaError_t e = cudaFuncSetAttribute(cn_staged_kernel<T, LL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kCnStagedSmemMax);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(cn_staged_kernel<T, LL / 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kCnStagedSmemMax);
     return e;
 }
 
@@ -350,6 +552,10 @@ template cudaError_t launch_cn_batch<float>(const ColArgs<float> *, const int4 *
                                             cudaStream_t);
 template cudaError_t launch_cn<double>(const ColArgs<double> &, cudaStream_t);
 template cudaError_t launch_cn_table<float>(const TableArgs &, cx<float> *, cudaStream_t);
+template cudaError_t launch_cn_coef<float>(const TableArgs &, CnCoef<float> *, cudaStream_t);
+template cudaError_t launch_cn_coef<double>(const TableArgs &, CnCoef<double> *, cudaStream_t);
+template cudaError_t prepare_cn<float>();
+template cudaError_t prepare_cn<double>();
 template cudaError_t launch_cn_table<double>(const TableArgs &, cx<double> *, cudaStream_t);
 
 }  // namespace fcn

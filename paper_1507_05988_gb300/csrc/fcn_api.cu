@@ -328,6 +328,14 @@ uint64_t dz_key(double dz) {
 // so a batch of equal pulses streams one table (L2-resident) instead of one
 // per pulse.  Least-recently used tables beyond 2 per pulse + 8 are freed,
 // together with the graphs and batch arguments captured with them.
+// A context table allocation holds the pivots ([nr][nt/2+1] complex) and,
+// from this byte offset on, the nr CnCoef rows of the staged column kernels.
+template <typename T>
+size_t coef_offset(int nr, int nt) {
+    const size_t b = sizeof(cx<T>) * (size_t)nr * (size_t)(nt / 2 + 1);
+    return (b + 255) / 256 * 256;
+}
+
 template <typename T>
 int ensure_table(fcn_ctx *ctx, Pulse &pu, double dz, const cx<T> **out) {
     TableKey key;
@@ -366,9 +374,8 @@ int ensure_table(fcn_ctx *ctx, Pulse &pu, double dz, const cx<T> **out) {
         cudaFree(old->second.ptr);
         ctx->tables.erase(old);
     }
-    const size_t n = (size_t)pu.g.nr * (pu.g.nt / 2 + 1);
     void *d = nullptr;
-    CK(cudaMalloc(&d, sizeof(cx<T>) * n), "pivot table allocation");
+    CK(cudaMalloc(&d, coef_offset<T>(pu.g.nr, pu.g.nt) + sizeof(CnCoef<T>) * pu.g.nr), "pivot table allocation");
     TableArgs ta;
     ta.nr = pu.g.nr;
     ta.nt = pu.g.nt;
@@ -377,6 +384,8 @@ int ensure_table(fcn_ctx *ctx, Pulse &pu, double dz, const cx<T> **out) {
     ta.lo = pu.lo64;
     ta.hi = pu.hi64;
     CK(launch_cn_table<T>(ta, (cx<T> *)d, ctx->st), "pivot table kernel");
+    CK(launch_cn_coef<T>(ta, (CnCoef<T> *)((char *)d + coef_offset<T>(pu.g.nr, pu.g.nt)), ctx->st),
+       "row coefficient kernel");
     ctx->tables[key] = TableEntry{d, dz_key(dz), ++ctx->table_clock};
     *out = (const cx<T> *)d;
     return FCN_OK;
@@ -402,6 +411,7 @@ ColArgs<T> col_args(Pulse &pu, void *field, const cx<T> *table, double dz) {
     ColArgs<T> a;
     a.field = (cx<T> *)field;
     a.invden = table;
+    a.coef = (const CnCoef<T> *)((const char *)table + coef_offset<T>(pu.g.nr, pu.g.nt));
     a.lo = (const T *)pu.lo;
     a.hi = (const T *)pu.hi;
     a.nr = pu.g.nr;
@@ -410,6 +420,7 @@ ColArgs<T> col_args(Pulse &pu, void *field, const cx<T> *table, double dz) {
     cn_coefs(pu.g, pu.p, dz, &s, &dk);
     a.s = T(s);
     a.dk = T(dk);
+    a.variant = pu.col_var;
     return a;
 }
 
@@ -1039,7 +1050,7 @@ int create_impl(int n, const fcn_grid *grids, const fcn_params *params, int prec
                 return bail(FCN_ERR_CUDA);
             }
             pu.tw = tw; pu.lo = lo; pu.hi = hi;
-            if ((e = prepare_rows<double>(pu.g.nt)) != cudaSuccess) {
+            if ((e = prepare_rows<double>(pu.g.nt)) != cudaSuccess || (e = prepare_cn<double>()) != cudaSuccess) {
                 cuda_fail(ctx, e, "row kernel attributes");
                 return bail(FCN_ERR_CUDA);
             }
@@ -1052,7 +1063,7 @@ int create_impl(int n, const fcn_grid *grids, const fcn_params *params, int prec
                 return bail(FCN_ERR_CUDA);
             }
             pu.tw = tw; pu.lo = lo; pu.hi = hi;
-            if ((e = prepare_rows<float>(pu.g.nt)) != cudaSuccess) {
+            if ((e = prepare_rows<float>(pu.g.nt)) != cudaSuccess || (e = prepare_cn<float>()) != cudaSuccess) {
                 cuda_fail(ctx, e, "row kernel attributes");
                 return bail(FCN_ERR_CUDA);
             }

@@ -124,16 +124,31 @@ struct RowArgs {
     NLCoef<T> nl;
 };
 
+// Per-row coefficients of the Crank-Nicolson system (Eqs. (Ma)-(Mb)) for one
+// dz, in the form the staged column kernel uses: with delta_q = dk q^2,
+//   explicit side  w_j = sl x_{j-1} + sh x_{j+1} - d (c0 - delta_q) x_j,
+//                  rhs_j = d x_j + i w_j,
+//   sweep factors  alpha_j = i sl / piv_j,  gamma_j = i sh / piv_j.
+// Row 0 (symmetry axis): sl = 0, sh = c0 = 4s, d = 1; rows 1..Nr-2:
+// sl = s lo_j, sh = s hi_j, c0 = 2s, d = 1; the boundary row Nr-1 and the
+// padding rows of a ragged last chunk are all zero (A = 0 there).
+template <typename T>
+struct alignas(4 * sizeof(T)) CnCoef {
+    T sl, sh, c0, d;
+};
+
 template <typename T>
 struct ColArgs {
     cx<T> *field;            // [nr][nt], frequency domain, in place
     const cx<T> *invden;     // [nr][nt/2+1]: 1/pivot_j per |q|
     const T *lo;             // [nr]: 1 - 1/(2j) (j >= 1), 0 at j = 0
     const T *hi;             // [nr]: 1 + 1/(2j) (j >= 1), 0 at j = 0
+    const CnCoef<T> *coef = nullptr;   // [nr] row coefficients (staged variants)
     int nr, nt;
     T s;                     // dz / (4 k0 dr^2), 0 without diffraction
     T dk;                    // k'' dz/4 domega^2, 0 without dispersion: delta_q = dk q^2
-    int variant;             // 0..3: chunk length (long/short) x CTA size (256/512)
+    int variant;             // 0..3: register chunks, long/short x CTA 256/512;
+                             // 4, 5: staged chunks of 16 / 8 rows (need coef)
 };
 
 struct TableArgs {
@@ -152,9 +167,16 @@ cudaError_t prepare_rows(int nt);
 template <typename T>
 cudaError_t launch_cn(const ColArgs<T> &a, cudaStream_t st);
 constexpr int kRowVariants = 3;
-constexpr int kColVariants = 4;
+constexpr int kColVariants = 6;
+constexpr int kColStagedFirst = 4;      // variants >= this need ColArgs::coef
 template <typename T>
 cudaError_t launch_cn_table(const TableArgs &a, cx<T> *table, cudaStream_t st);
+// Row coefficients for the staged column variants (nr rows).
+template <typename T>
+cudaError_t launch_cn_coef(const TableArgs &a, CnCoef<T> *coef, cudaStream_t st);
+// Sets the staged column kernels' shared-memory attribute (outside capture).
+template <typename T>
+cudaError_t prepare_cn();
 
 // Batched work lists (pulses of uneven grids in one launch per stage).
 // Row items: (pulse, first row), 512/(Nt/16) rows each, Nt in 512..8192.

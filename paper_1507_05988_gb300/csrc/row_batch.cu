@@ -6,10 +6,11 @@
 namespace fcn {
 
 size_t row_batch_smem(int nt, int bytes_per_complex) {
-    // 512 threads hold 512 / (Nt/16) rows of Nt + Nt/16 padded values
+    // 512 threads hold 512 / (Nt/16) rows of Nt + Nt/16 padded values and
+    // as many real u values
     const int tpr = nt / 16;
     const int rpc = 512 / tpr;
-    return (size_t)bytes_per_complex * rpc * (nt + nt / 16) + sizeof(double) * 32;
+    return (size_t)(bytes_per_complex + bytes_per_complex / 2) * rpc * (nt + nt / 16) + sizeof(double) * 32;
 }
 
 template <>

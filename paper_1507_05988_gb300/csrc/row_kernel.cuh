@@ -456,50 +456,55 @@ __device__ __forceinline__ T row_scan_exclusive(T tot, int t, double *scr, int r
     return excl;
 }
 
-// One nonlinear half step on this thread's E contiguous values v (points
-// p = E t + e) and on the first value of the next thread (nb), which the
-// next half step needs for the RK4 cell that straddles the two threads.
-// u receives rho/rho_nt at the E points.  Intensity powers are recomputed
-// from v instead of being kept in arrays (register pressure).
+// One nonlinear half step of this thread's E contiguous points p = E t + e
+// of the row in S (natural order, padded), in place, the values scaled by
+// sc on the way in.  Two phases: (A) the RK4 coefficients of the cells
+// (p, p+1) -- the last one needs the next thread's first point -- and the
+// thread-local exclusive (+)-scan into U, then the row scan for the carry;
+// (B) the update A <- A exp(h N), with U[p] replaced by the final u_p.
+// Phase B is a rolled loop: one copy of the transcendental code keeps the
+// kernel small and the values out of registers.  Callers put a barrier
+// between two half steps (phase A reads the neighbour's point).
 template <typename T, int NT, int KT>
-__device__ __forceinline__ void nl_half(cx<T> (&v)[RowCfg<NT>::E], cx<T> &nb, T (&u)[RowCfg<NT>::E],
-                                        int t, const NLCoef<T> &c, bool need_u, double *scr,
-                                        int rloc) {
+__device__ __forceinline__ void nl_half_smem(cx<T> *S, T *U, T sc, int t, const NLCoef<T> &c, bool need_u,
+                                             double *scr, int rloc) {
     using C = RowCfg<NT>;
     constexpr int E = C::E;
-    const bool last_thread = (t == C::TPR - 1);
-    T u_nb = T(0);
+    const int p0 = E * t;
+    T carry = T(0);
     if (need_u) {
+        const bool last_thread = (t == C::TPR - 1);
         T run = T(0);
-        T ih_a = cnorm(v[0]) * c.inv_is;
+        cx<T> xa = S[FCN_IDX(pidx(p0, NT), C::PADN, 7)];
+        T ih_a = cnorm(mk(xa.x * sc, xa.y * sc)) * c.inv_is;
         T x_a = c.sdt * powk<KT>(ih_a, c.K);
 #pragma unroll
         for (int e = 0; e < E; ++e) {
-            u[e] = run;
-            const cx<T> nxt = (e + 1 < E) ? v[e + 1] : nb;
-            const T ih_b = cnorm(nxt) * c.inv_is;
-            const T x_b = c.sdt * powk<KT>(ih_b, c.K);
-            const bool has_next = (e + 1 < E) || !last_thread;
-            const T cc = has_next ? rk4_coef<KT>(ih_a, ih_b, x_a, x_b, c) : T(0);
-            run = uplus(run, cc);
-            ih_a = ih_b;
-            x_a = x_b;
+            U[FCN_IDX(pidx(p0 + e, NT), C::PADN, 26)] = run;
+            if ((e + 1 < E) || !last_thread) {
+                const cx<T> xb = S[FCN_IDX(pidx(p0 + e + 1, NT), C::PADN, 8)];
+                const T ih_b = cnorm(mk(xb.x * sc, xb.y * sc)) * c.inv_is;
+                const T x_b = c.sdt * powk<KT>(ih_b, c.K);
+                run = uplus(run, rk4_coef<KT>(ih_a, ih_b, x_a, x_b, c));
+                ih_a = ih_b;
+                x_a = x_b;
+            }
         }
-        const T carry = row_scan_exclusive<T, NT>(run, t, scr, rloc);
-#pragma unroll
-        for (int e = 0; e < E; ++e) u[e] = uplus(carry, u[e]);
-        u_nb = uplus(carry, run);
-    } else {
-#pragma unroll
-        for (int e = 0; e < E; ++e) u[e] = T(0);
+        carry = row_scan_exclusive<T, NT>(run, t, scr, rloc);
     }
-#pragma unroll
+#pragma unroll 2
     for (int e = 0; e < E; ++e) {
-        const T ih = cnorm(v[e]) * c.inv_is;
-        v[e] = nl_apply(v[e], ih, powk<(KT > 0 ? KT - 1 : 0)>(ih, c.K - 1), u[e], c);
+        const int ip = pidx(p0 + e, NT);
+        const cx<T> x0 = S[FCN_IDX(ip, C::PADN, 27)];
+        const cx<T> x = mk(x0.x * sc, x0.y * sc);
+        T u = T(0);
+        if (need_u) {
+            u = uplus(carry, U[FCN_IDX(ip, C::PADN, 28)]);
+            U[ip] = u;
+        }
+        const T ih = cnorm(x) * c.inv_is;
+        S[ip] = nl_apply(x, ih, powk<(KT > 0 ? KT - 1 : 0)>(ih, c.K - 1), u, c);
     }
-    const T ihn = cnorm(nb) * c.inv_is;
-    nb = nl_apply(nb, ihn, powk<(KT > 0 ? KT - 1 : 0)>(ihn, c.K - 1), u_nb, c);
 }
 
 // Sum across the TPR threads of a row (FP64), result valid in thread t = 0.
@@ -558,14 +563,15 @@ __device__ __forceinline__ void row_body(const RowArgs<T> &a, int row_base, int 
     constexpr int RPC = TH / C::TPR;
     static_assert(RPC * C::TPR == TH, "CTA size must hold whole rows");
     cx<T> *S_all = reinterpret_cast<cx<T> *>(smem_raw);
-    double *scr = reinterpret_cast<double *>(S_all + RPC * C::PADN);
+    T *U_all = reinterpret_cast<T *>(S_all + RPC * C::PADN);
+    double *scr = reinterpret_cast<double *>(U_all + RPC * C::PADN);
 
 #ifdef FCN_CHECKED
     {
         unsigned dsm;
         asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dsm));
         if (threadIdx.x == 0)
-            FCN_IDX(sizeof(cx<T>) * RPC * C::PADN + sizeof(double) * 32 - 1, dsm, 25);
+            FCN_IDX((sizeof(cx<T>) + sizeof(T)) * RPC * C::PADN + sizeof(double) * 32 - 1, dsm, 25);
     }
 #endif
     const int tid = threadIdx.x;
@@ -574,6 +580,7 @@ __device__ __forceinline__ void row_body(const RowArgs<T> &a, int row_base, int 
     const int row = row_base + rloc;
     const bool valid = row < a.nr;
     cx<T> *S = S_all + rloc * C::PADN;
+    T *U = U_all + rloc * C::PADN;
     cx<T> *g = a.field + (size_t)(valid ? row : 0) * NT;
 
     cx<T> v[E];
@@ -593,59 +600,62 @@ __device__ __forceinline__ void row_body(const RowArgs<T> &a, int row_base, int 
 
     // the time-domain stage runs whenever the row passes through tau space
     // (nonlinear step, statistics, rho output) or the 1/Nt of an inverse
-    // transform has to be applied
+    // transform has to be applied; it works in place on S
     const bool time_work = (ops & (OP_NL | OP_STATS | OP_RHO | OP_IFFT)) != 0;
     if (time_work) {
-        // contiguous view: points E t .. E t + E-1 (+ the next thread's first)
-        const T sc = (ops & OP_IFFT) ? a.nl.inv_nt : T(1);
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-            cx<T> x = S[FCN_IDX(pidx(E * t + e, NT), C::PADN, 7)];
-            v[e] = mk(x.x * sc, x.y * sc);
-        }
-        cx<T> nb = mk(T(0), T(0));
-        if (t + 1 < C::TPR) {
-            cx<T> x = S[FCN_IDX(pidx(E * (t + 1), NT), C::PADN, 8)];
-            nb = mk(x.x * sc, x.y * sc);
-        }
-        T u[E];
-#pragma unroll
-        for (int e = 0; e < E; ++e) u[e] = T(0);
+        T sc = (ops & OP_IFFT) ? a.nl.inv_nt : T(1);
         const bool need_u = (a.nl.flags & (PH_PLASMA | PH_MPI_SAT)) || (ops & (OP_RHO | OP_STATS));
-        if (ops & OP_NL) nl_half<T, NT, KT>(v, nb, u, t, a.nl, need_u, scr, rloc);
-        if (ops & OP_NL2) nl_half<T, NT, KT>(v, nb, u, t, a.nl, need_u, scr, rloc);
-
-        if ((ops & OP_RHO) && valid && a.rho) {
-            T *rr = a.rho + (size_t)row * NT + E * t;
-#pragma unroll
-            for (int e = 0; e < E; ++e) rr[FCN_IDX(E * t + e, NT, 12) - E * t] = u[e] * a.nl.rho_nt;
+        bool have_u = false;
+        if (ops & OP_NL) {
+            nl_half_smem<T, NT, KT>(S, U, sc, t, a.nl, need_u, scr, rloc);
+            sc = T(1);
+            have_u = need_u;
+            __syncthreads();
         }
-        if ((ops & OP_STATS) && a.stats) {
+        if (ops & OP_NL2) {
+            nl_half_smem<T, NT, KT>(S, U, sc, t, a.nl, need_u, scr, rloc);
+            sc = T(1);
+            have_u = need_u;
+            __syncthreads();
+        }
+        // remaining 1/Nt (no half step ran), statistics and rho of the final row
+        if (sc != T(1) || (ops & (OP_STATS | OP_RHO))) {
             double s = 0.0, mx = 0.0, mu = 0.0, bad = 0.0;
-#pragma unroll
+            T *rr = (valid && a.rho) ? a.rho + (size_t)row * NT : nullptr;
+#pragma unroll 4
             for (int e = 0; e < E; ++e) {
-                const double i2 = double(v[e].x) * double(v[e].x) + double(v[e].y) * double(v[e].y);
-                if (!isfinite(i2)) bad += 1.0;
-                s += i2;
-                mx = fmax(mx, i2);
-                mu = fmax(mu, double(u[e]));
+                const int p = E * t + e;
+                const int ip = pidx(p, NT);
+                cx<T> x = S[FCN_IDX(ip, C::PADN, 29)];
+                if (sc != T(1)) {
+                    x = mk(x.x * sc, x.y * sc);
+                    S[ip] = x;
+                }
+                const T u = have_u ? U[ip] : T(0);
+                if ((ops & OP_RHO) && rr) rr[FCN_IDX(p, NT, 12)] = u * a.nl.rho_nt;
+                if (ops & OP_STATS) {
+                    const double i2 = double(x.x) * double(x.x) + double(x.y) * double(x.y);
+                    if (!isfinite(i2)) bad += 1.0;
+                    s += i2;
+                    mx = fmax(mx, i2);
+                    mu = fmax(mu, double(u));
+                }
             }
-            s = row_sum<NT>(s, t, scr, rloc);
-            mx = row_max<NT>(mx, t, scr, rloc);
-            mu = row_max<NT>(mu, t, scr, rloc);
-            bad = row_sum<NT>(bad, t, scr, rloc);
-            if (t == 0 && valid) {
-                double *st = a.stats + FCN_IDX((size_t)row * NSTAT, (size_t)a.nr * NSTAT, 23);
-                st[ST_SUM_I] = s;
-                st[ST_MAX_I] = mx;
-                if (ops & (OP_NL | OP_NL2)) st[ST_MAX_U] = mu;
-                st[ST_NONFINITE] = bad;
+            if ((ops & OP_STATS) && a.stats) {
+                s = row_sum<NT>(s, t, scr, rloc);
+                mx = row_max<NT>(mx, t, scr, rloc);
+                mu = row_max<NT>(mu, t, scr, rloc);
+                bad = row_sum<NT>(bad, t, scr, rloc);
+                if (t == 0 && valid) {
+                    double *st = a.stats + FCN_IDX((size_t)row * NSTAT, (size_t)a.nr * NSTAT, 23);
+                    st[ST_SUM_I] = s;
+                    st[ST_MAX_I] = mx;
+                    if (ops & (OP_NL | OP_NL2)) st[ST_MAX_U] = mu;
+                    st[ST_NONFINITE] = bad;
+                }
             }
+            __syncthreads();
         }
-        __syncthreads();  // every thread has read its neighbour before overwrite
-#pragma unroll
-        for (int e = 0; e < E; ++e) S[FCN_IDX(pidx(E * t + e, NT), C::PADN, 9)] = v[e];
-        __syncthreads();
         if (!(ops & OP_FFT) && !(ops & OP_NOSTORE) && valid) {
 #pragma unroll
             for (int i = 0; i < E; ++i) {
@@ -748,7 +758,7 @@ namespace rowimpl {
 template <typename T, int NT>
 size_t smem_bytes() {
     using C = RowCfg<NT>;
-    return sizeof(cx<T>) * C::RPC * C::PADN + sizeof(double) * 32;
+    return (sizeof(cx<T>) + sizeof(T)) * C::RPC * C::PADN + sizeof(double) * 32;
 }
 
 // Sets the dynamic shared-memory limit of the kernel; must run before any

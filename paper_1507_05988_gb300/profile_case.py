@@ -1,0 +1,50 @@
+"""Runs a few z-steps of one pulse with fixed kernel variants, for profilers.
+
+    python -m paper_1507_05988_gb300.profile_case --config 2 --precision fp32 \
+        --steps 3 --row-variant 0 --col-variant 0
+
+The pulse is one of the seeded workloads (config 1: 128 x 256, config 2:
+1024 x 4096, config 3: 2048 x 8192).  With variants given the autotuner does
+not run, so a profiler sees exactly one fused middle row launch and one
+column launch per step after the first step (which adds the opening row
+launch).  Steps run without CUDA graphs unless --graph is given.
+"""
+from __future__ import annotations
+
+import argparse
+
+import numpy as np
+
+from . import fcn, workloads
+
+
+def main(argv=None) -> int:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--pulses", type=int, default=1)
+    ap.add_argument("--row-variant", type=int, default=-1)
+    ap.add_argument("--col-variant", type=int, default=-1)
+    ap.add_argument("--graph", action="store_true")
+    a = ap.parse_args(argv)
+    make = {1: workloads.config1, 2: workloads.config2, 3: workloads.config3}[a.config]
+    wls = [make(seed=k) if a.config == 2 else make() for k in range(a.pulses)]
+    prec = fcn.FCN_FP32_MIXED if a.precision == "fp32" else fcn.FCN_FP64
+    s = fcn.Solver([w.physics() for w in wls] if a.pulses > 1 else wls[0].physics(), precision=prec)
+    if a.row_variant >= 0 or a.col_variant >= 0:
+        s.set_variants(a.row_variant, a.col_variant)
+    for k, w in enumerate(wls):
+        s.set_field(w.field(), pulse=k)
+    dz = wls[0].dz if wls[0].nsteps else 2e-3
+    s.step(dz, a.steps, graph=a.graph)
+    d = s.diag(0)
+    ok = np.isfinite(d["energy"]) and d["nonfinite"] == 0
+    print(f"profile_case: config {a.config} {a.precision} steps {a.steps} variants {s.variants(0)} "
+          f"energy {d['energy']:.6e}")
+    s.close()
+    return 0 if ok else 1
+
+
+if __name__ == "__main__":
+    raise SystemExit(main())
