@@ -99,6 +99,16 @@ NLCoef<T> nl_coef(const fcn_grid &g, const fcn_params &p, double h) {
     for (int j = 0; j < 4; ++j)
         if (p.n2j[j] != 0.0) n.nkerr = j + 1;
     n.flags = p.flags;
+    isj = kIs;
+    for (int j = 0; j < 4; ++j) {
+        n.hk[j] = (p.flags & FCN_KERR) ? T(h * (c.k0 / p.n0) * p.n2j[j] * isj) : T(0);
+        isj *= kIs;
+    }
+    n.hplasma = (p.flags & FCN_PLASMA) ? T(h * (c.k0 / (2.0 * p.n0 * p.n0 * c.rho_c) * p.rho_nt)) : T(0);
+    n.hloss = (p.flags & FCN_MPI) ? T(h * 0.5 * c.beta_k * std::pow(kIs, p.K - 1)) : T(0);
+    n.sat = (p.flags & FCN_MPI_SAT) ? T(1) : T(0);
+    const double sdt = p.sigma_k * c.dtau * std::pow(kIs, p.K);
+    n.is_root = T(sdt > 0.0 ? std::pow(sdt, 1.0 / p.K) / kIs : 0.0);
     return n;
 }
 

@@ -92,6 +92,14 @@ struct NLCoef {
     T inv_is;   // 1 / I_s
     T inv_nt;   // 1 / Nt (applied after the inverse FFT)
     T rho_nt;   // rho = u rho_nt for the rho output
+    // The same terms as the row kernel uses them, with the half-step length
+    // and the physics switches folded in (a switched-off term has a zero
+    // coefficient, so the kernel needs no per-point flag tests):
+    T hk[4];    // h kerr_j, or 0 without the Kerr term
+    T hplasma;  // h plasma, or 0 without plasma defocusing
+    T hloss;    // h loss, or 0 without MPI loss
+    T sat;      // 1 with saturation of the MPI loss (factor 1 - u), else 0
+    T is_root;  // sdt^(1/K) / I_s: with j = |A|^2 is_root, sdt (|A|^2/I_s)^K = j^K
     int K;
     int nkerr;  // number of leading Kerr orders in use (1..4; trailing zeros dropped)
     unsigned flags;

@@ -219,22 +219,27 @@ template <typename T, int NT, int P, bool LAST>
 struct InvDispatch;
 template <typename T, int NT, int P>
 struct InvDispatch<T, NT, P, false> {
+    // sc (the 1/Nt of the inverse transform) scales the last pass's outputs
     __device__ __forceinline__ static void run(cx<T> (&v)[RowCfg<NT>::E], cx<T> *S, int t,
-                                               const cx<T> *tw) {
+                                               const cx<T> *tw, T sc) {
         if (P > 0) {
             pass_load<T, NT, P>(v, S, t);
             __syncthreads();
         }
         pass_compute<T, NT, P, +1>(v, t, tw);
+        if (P + 1 == RowCfg<NT>::NPASS) {
+#pragma unroll
+            for (int e = 0; e < RowCfg<NT>::E; ++e) v[e] = mk(v[e].x * sc, v[e].y * sc);
+        }
         pass_store<T, NT, P>(v, S, t);
         __syncthreads();
-        InvDispatch<T, NT, P + 1, (P + 1 >= RowCfg<NT>::NPASS)>::run(v, S, t, tw);
+        InvDispatch<T, NT, P + 1, (P + 1 >= RowCfg<NT>::NPASS)>::run(v, S, t, tw, sc);
     }
 };
 template <typename T, int NT, int P>
 struct InvDispatch<T, NT, P, true> {
     __device__ __forceinline__ static void run(cx<T> (&)[RowCfg<NT>::E], cx<T> *, int,
-                                               const cx<T> *) {}
+                                               const cx<T> *, T) {}
 };
 
 template <typename T, int NT, int P, bool LAST>
@@ -292,15 +297,25 @@ __device__ __forceinline__ T powk(T x, int k) {
 template <typename T>
 __device__ __forceinline__ T uplus(T a, T b) { return a + b - a * b; }
 
-// RK4 increment of u over one dtau cell from the scaled intensities at its
-// ends: u_next = u + c (1 - u).
-template <int KT, typename T>
-__device__ __forceinline__ T rk4_coef(T ia, T ib, T xa, T xb, const NLCoef<T> &c) {
-    const T xm = c.sdt * powk<KT>((ia + ib) * T(0.5), c.K);
-    const T t1 = T(1) - T(0.5) * xa;
-    const T t2 = T(1) - T(0.5) * xm * t1;
-    const T t3 = T(1) - xm * t2;
-    return (xa + T(2) * xm * t1 + T(2) * xm * t2 + xb * t3) * T(1.0 / 6.0);
+// RK4 increment of u over one dtau cell (du/dtau = w (1 - u), w = sigma_K
+// I^K): with xa, xb, xm = dtau w at the cell's ends and midpoint,
+// u_next = u + c (1 - u),
+//   6 c = xa + 2 xm t1 + 2 xm t2 + xb t3,
+//   t1 = 1 - xa/2,  t2 = 1 - (xm/2) t1,  t3 = 1 - xm t2.
+// Returns 6 c (the caller folds the 1/6 into the (+) update).
+template <typename T>
+__device__ __forceinline__ T rk4_coef6(T xa, T xb, T xm) {
+    const T t1 = fma(T(-0.5), xa, T(1));
+    const T t2 = fma(T(-0.5) * xm, t1, T(1));
+    const T t3 = fma(-xm, t2, T(1));
+    const T acc = fma(xm + xm, t1 + t2, xa);
+    return fma(xb, t3, acc);
+}
+
+// run (+) c for c = c6 / 6: run + c (1 - run)
+template <typename T>
+__device__ __forceinline__ T uplus6(T run, T c6) {
+    return fma(c6, fma(-run, T(1.0 / 6.0), T(1.0 / 6.0)), run);
 }
 
 template <typename T>
@@ -373,43 +388,39 @@ __device__ __forceinline__ float exp_t<float>(float x) { return expf(x); }
 template <>
 __device__ __forceinline__ double exp_t<double>(double x) { return exp(x); }
 
-// A <- A exp(h N(Ihat, u))
+// A <- A exp(h N(Ihat, u)) with h folded into the coefficients:
+//   phi = Ihat (hk0 + Ihat (hk1 + Ihat (hk2 + Ihat hk3))) - hplasma u,
+//   lnamp = -hloss Ihat^(K-1) (1 - sat u),  A <- A exp(lnamp + i phi).
+// ihKm1 = Ihat^(K-1).
 template <typename T>
 __device__ __forceinline__ cx<T> nl_apply(cx<T> a, T ih, T ihKm1, T u, const NLCoef<T> &c) {
-    T phase = T(0), loss = T(0);
-    if (c.flags & PH_KERR) {
-        // Horner over the Kerr orders in use (c.nkerr is uniform over the
-        // launch); the coefficients are read by constant index so that the
-        // parameter block stays in the constant bank (no local copy)
-        T poly;
-        switch (c.nkerr) {
-            case 4: poly = c.kerr[0] + ih * (c.kerr[1] + ih * (c.kerr[2] + ih * c.kerr[3])); break;
-            case 3: poly = c.kerr[0] + ih * (c.kerr[1] + ih * c.kerr[2]); break;
-            case 2: poly = c.kerr[0] + ih * c.kerr[1]; break;
-            default: poly = c.kerr[0]; break;
-        }
-        phase = ih * poly;
-    }
-    if (c.flags & PH_PLASMA) phase -= c.plasma * u;
-    if (c.flags & PH_MPI) {
-        loss = c.loss * ihKm1;
-        if (c.flags & PH_MPI_SAT) loss *= (T(1) - u);
-    }
+    T phi = fma(ih, c.hk[3], c.hk[2]);
+    phi = fma(ih, phi, c.hk[1]);
+    phi = fma(ih, phi, c.hk[0]);
+    phi = fma(-c.hplasma, u, ih * phi);
+    const T lnamp = -(c.hloss * fma(-c.sat, u, T(1))) * ihKm1;
     if constexpr (sizeof(T) == 4) {
         // delta form: A + A D with D = amp exp(i phi) - 1
         //   = (em1 + cm1 + em1 cm1) + i s (1 + em1),  em1 = amp - 1
-        float sn, cm1;
-        sincos_m1_f32(c.h * phase, &sn, &cm1);
-        const float em1 = (c.flags & PH_MPI) ? expm1_f32(-c.h * loss) : 0.0f;
+        float sn, cm1, em1;
+        if (fabsf(phi) < 1.0e-3f && fabsf(lnamp) < 1.0e-4f) {
+            // both series exact to float rounding (see sincos_m1_f32, expm1_f32)
+            const float p2 = phi * phi;
+            cm1 = -0.5f * p2;
+            sn = fmaf(phi * p2, -1.66666666666666666667e-1f, phi);
+            em1 = fmaf(0.5f * lnamp, lnamp, lnamp);
+        } else {
+            sincos_m1_f32(phi, &sn, &cm1);
+            em1 = expm1_f32(lnamp);
+        }
         const float dre = fmaf(em1, cm1, em1 + cm1);
         const float dim = fmaf(sn, em1, sn);
         return mk(fmaf(a.x, dre, fmaf(-a.y, dim, a.x)), fmaf(a.x, dim, fmaf(a.y, dre, a.y)));
     } else {
         T s, co;
-        sincos_t<T>(c.h * phase, &s, &co);
-        const T amp = (c.flags & PH_MPI) ? exp_t<T>(-c.h * loss) : T(1);
-        const cx<T> e = mk(amp * co, amp * s);
-        return cmul(a, e);
+        sincos_t<T>(phi, &s, &co);
+        const T amp = exp_t<T>(lnamp);
+        return cmul(a, mk(amp * co, amp * s));
     }
 }
 
@@ -457,16 +468,16 @@ __device__ __forceinline__ T row_scan_exclusive(T tot, int t, double *scr, int r
 }
 
 // One nonlinear half step of this thread's E contiguous points p = E t + e
-// of the row in S (natural order, padded), in place, the values scaled by
-// sc on the way in.  Two phases: (A) the RK4 coefficients of the cells
-// (p, p+1) -- the last one needs the next thread's first point -- and the
-// thread-local exclusive (+)-scan into U, then the row scan for the carry;
-// (B) the update A <- A exp(h N), with U[p] replaced by the final u_p.
-// Phase B is a rolled loop: one copy of the transcendental code keeps the
-// kernel small and the values out of registers.  Callers put a barrier
+// of the row in S (natural order, padded, already scaled), in place.  Two
+// phases: (A) the RK4 coefficients of the cells (p, p+1) -- the last one
+// needs the next thread's first point -- and the thread-local exclusive
+// (+)-scan into U, then the row scan for the carry; (B) the update
+// A <- A exp(h N), four points per iteration of a rolled loop (one copy of
+// the rare general-argument code keeps the kernel small).  STORE_U writes the
+// final u_p back to U (statistics, rho output).  Callers put a barrier
 // between two half steps (phase A reads the neighbour's point).
-template <typename T, int NT, int KT>
-__device__ __forceinline__ void nl_half_smem(cx<T> *S, T *U, T sc, int t, const NLCoef<T> &c, bool need_u,
+template <typename T, int NT, int KT, bool STORE_U>
+__device__ __forceinline__ void nl_half_smem(cx<T> *S, T *U, int t, const NLCoef<T> &c, bool need_u,
                                              double *scr, int rloc) {
     using C = RowCfg<NT>;
     constexpr int E = C::E;
@@ -475,35 +486,42 @@ __device__ __forceinline__ void nl_half_smem(cx<T> *S, T *U, T sc, int t, const 
     if (need_u) {
         const bool last_thread = (t == C::TPR - 1);
         T run = T(0);
-        cx<T> xa = S[FCN_IDX(pidx(p0, NT), C::PADN, 7)];
-        T ih_a = cnorm(mk(xa.x * sc, xa.y * sc)) * c.inv_is;
-        T x_a = c.sdt * powk<KT>(ih_a, c.K);
+        // j = |A|^2 is_root: x = dtau sigma_K Ihat^K = j^K
+        T ja = cnorm(S[FCN_IDX(pidx(p0, NT), C::PADN, 7)]) * c.is_root;
+        T xa = powk<KT>(ja, c.K);
 #pragma unroll
         for (int e = 0; e < E; ++e) {
             U[FCN_IDX(pidx(p0 + e, NT), C::PADN, 26)] = run;
             if ((e + 1 < E) || !last_thread) {
-                const cx<T> xb = S[FCN_IDX(pidx(p0 + e + 1, NT), C::PADN, 8)];
-                const T ih_b = cnorm(mk(xb.x * sc, xb.y * sc)) * c.inv_is;
-                const T x_b = c.sdt * powk<KT>(ih_b, c.K);
-                run = uplus(run, rk4_coef<KT>(ih_a, ih_b, x_a, x_b, c));
-                ih_a = ih_b;
-                x_a = x_b;
+                const T jb = cnorm(S[FCN_IDX(pidx(p0 + e + 1, NT), C::PADN, 8)]) * c.is_root;
+                const T xb = powk<KT>(jb, c.K);
+                const T xm = powk<KT>(T(0.5) * (ja + jb), c.K);
+                run = uplus6(run, rk4_coef6(xa, xb, xm));
+                ja = jb;
+                xa = xb;
             }
         }
         carry = row_scan_exclusive<T, NT>(run, t, scr, rloc);
     }
-#pragma unroll 2
-    for (int e = 0; e < E; ++e) {
-        const int ip = pidx(p0 + e, NT);
-        const cx<T> x0 = S[FCN_IDX(ip, C::PADN, 27)];
-        const cx<T> x = mk(x0.x * sc, x0.y * sc);
-        T u = T(0);
-        if (need_u) {
-            u = uplus(carry, U[FCN_IDX(ip, C::PADN, 28)]);
-            U[ip] = u;
+    const T omc = T(1) - carry;
+    constexpr int UN = E >= 4 ? 4 : E;
+#pragma unroll 1
+    for (int e0 = 0; e0 < E; e0 += UN) {
+        cx<T> x[UN];
+        T u[UN];
+#pragma unroll
+        for (int k = 0; k < UN; ++k) {
+            const int ip = pidx(p0 + e0 + k, NT);
+            x[k] = S[FCN_IDX(ip, C::PADN, 27)];
+            u[k] = need_u ? fma(U[FCN_IDX(ip, C::PADN, 28)], omc, carry) : T(0);
         }
-        const T ih = cnorm(x) * c.inv_is;
-        S[ip] = nl_apply(x, ih, powk<(KT > 0 ? KT - 1 : 0)>(ih, c.K - 1), u, c);
+#pragma unroll
+        for (int k = 0; k < UN; ++k) {
+            const int ip = pidx(p0 + e0 + k, NT);
+            const T ih = cnorm(x[k]) * c.inv_is;
+            S[ip] = nl_apply(x[k], ih, powk<(KT > 0 ? KT - 1 : 0)>(ih, c.K - 1), u[k], c);
+            if (STORE_U) U[ip] = u[k];
+        }
     }
 }
 
@@ -588,7 +606,7 @@ __device__ __forceinline__ void row_body(const RowArgs<T> &a, int row_base, int 
         // pass-0 operands straight from HBM: X[t + r*TPR], coalesced
 #pragma unroll
         for (int r = 0; r < E; ++r) v[r] = valid ? g[FCN_IDX(t + r * C::TPR, NT, 4)] : mk(T(0), T(0));
-        InvDispatch<T, NT, 0, (C::NPASS <= 0)>::run(v, S, t, a.tw);
+        InvDispatch<T, NT, 0, (C::NPASS <= 0)>::run(v, S, t, a.tw, a.nl.inv_nt);
     } else {
 #pragma unroll
         for (int i = 0; i < E; ++i) {
@@ -603,34 +621,27 @@ __device__ __forceinline__ void row_body(const RowArgs<T> &a, int row_base, int 
     // transform has to be applied; it works in place on S
     const bool time_work = (ops & (OP_NL | OP_STATS | OP_RHO | OP_IFFT)) != 0;
     if (time_work) {
-        T sc = (ops & OP_IFFT) ? a.nl.inv_nt : T(1);
         const bool need_u = (a.nl.flags & (PH_PLASMA | PH_MPI_SAT)) || (ops & (OP_RHO | OP_STATS));
+        const bool keep_u = (ops & (OP_RHO | OP_STATS)) != 0;
         bool have_u = false;
-        if (ops & OP_NL) {
-            nl_half_smem<T, NT, KT>(S, U, sc, t, a.nl, need_u, scr, rloc);
-            sc = T(1);
+        const int nhalf = ((ops & OP_NL) ? 1 : 0) + ((ops & OP_NL2) ? 1 : 0);
+        for (int hs = 0; hs < nhalf; ++hs) {
+            if (keep_u && hs + 1 == nhalf)
+                nl_half_smem<T, NT, KT, true>(S, U, t, a.nl, need_u, scr, rloc);
+            else
+                nl_half_smem<T, NT, KT, false>(S, U, t, a.nl, need_u, scr, rloc);
             have_u = need_u;
             __syncthreads();
         }
-        if (ops & OP_NL2) {
-            nl_half_smem<T, NT, KT>(S, U, sc, t, a.nl, need_u, scr, rloc);
-            sc = T(1);
-            have_u = need_u;
-            __syncthreads();
-        }
-        // remaining 1/Nt (no half step ran), statistics and rho of the final row
-        if (sc != T(1) || (ops & (OP_STATS | OP_RHO))) {
+        // statistics and rho of the final row
+        if (ops & (OP_STATS | OP_RHO)) {
             double s = 0.0, mx = 0.0, mu = 0.0, bad = 0.0;
             T *rr = (valid && a.rho) ? a.rho + (size_t)row * NT : nullptr;
 #pragma unroll 4
             for (int e = 0; e < E; ++e) {
                 const int p = E * t + e;
                 const int ip = pidx(p, NT);
-                cx<T> x = S[FCN_IDX(ip, C::PADN, 29)];
-                if (sc != T(1)) {
-                    x = mk(x.x * sc, x.y * sc);
-                    S[ip] = x;
-                }
+                const cx<T> x = S[FCN_IDX(ip, C::PADN, 29)];
                 const T u = have_u ? U[ip] : T(0);
                 if ((ops & OP_RHO) && rr) rr[FCN_IDX(p, NT, 12)] = u * a.nl.rho_nt;
                 if (ops & OP_STATS) {

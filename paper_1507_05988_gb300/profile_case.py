@@ -27,6 +27,9 @@ def main(argv=None) -> int:
     ap.add_argument("--row-variant", type=int, default=-1)
     ap.add_argument("--col-variant", type=int, default=-1)
     ap.add_argument("--graph", action="store_true")
+    ap.add_argument("--time", type=int, default=0,
+                    help="then time this many graph-replayed steps (wall clock around a "
+                         "synchronising call) and as many per-launch event-timed steps")
     a = ap.parse_args(argv)
     make = {1: workloads.config1, 2: workloads.config2, 3: workloads.config3}[a.config]
     wls = [make(seed=k) if a.config == 2 else make() for k in range(a.pulses)]
@@ -40,6 +43,23 @@ def main(argv=None) -> int:
     s.step(dz, a.steps, graph=a.graph)
     d = s.diag(0)
     ok = np.isfinite(d["energy"]) and d["nonfinite"] == 0
+    if a.time > 0:
+        import time
+        s.step(dz, 16)
+        s.diag(0)
+        t0 = time.perf_counter()
+        s.step(dz, a.time)
+        s.diag(0)
+        dt = time.perf_counter() - t0
+        print(f"profile_case: graph replay {1e6 * dt / (a.time * a.pulses):.2f} us per pulse-step "
+              f"({a.pulses} pulses)")
+        s.profile(True)
+        s.step(dz, a.time)
+        s.diag(0)
+        for k, (ms, n) in s.profile_read().items():
+            if n:
+                print(f"profile_case: {k} {n} launches, {1e3 * ms / n:.2f} us per launch (events)")
+        s.profile(False)
     print(f"profile_case: config {a.config} {a.precision} steps {a.steps} variants {s.variants(0)} "
           f"energy {d['energy']:.6e}")
     s.close()
