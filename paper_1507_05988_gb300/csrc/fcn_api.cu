@@ -163,17 +163,25 @@ cudaError_t get_twiddles(int nt, const cx<T> **out) {
     auto key = std::make_pair(prec, nt);
     auto it = g_tables.tw.find(key);
     if (it != g_tables.tw.end()) { *out = (const cx<T> *)it->second; return cudaSuccess; }
-    std::vector<cx<T>> h(nt);
+    std::vector<cx<T>> w(nt);
     for (int m = 0; m < nt; ++m) {
         const long double ang = -2.0L * 3.14159265358979323846264338327950288L * (long double)m /
                                 (long double)nt;
-        if constexpr (sizeof(T) == 4) h[m] = unit_twiddle_f32(ang);
-        else h[m] = mk(T(cosl(ang)), T(sinl(ang)));
+        if constexpr (sizeof(T) == 4) w[m] = unit_twiddle_f32(ang);
+        else w[m] = mk(T(cosl(ang)), T(sinl(ang)));
+    }
+    // per-pass blocks (layout in fcn_device.cuh: tw_offset)
+    const size_t n = std::max(1, tw_size(nt));
+    std::vector<cx<T>> h(n, mk(T(1), T(0)));
+    for (int p = 1; p < fft_npass(nt); ++p) {
+        const int R = fft_radix(nt, p), NS = fft_ns(nt, p), stride = nt / (NS * R);
+        for (int r = 1; r < R; ++r)
+            for (int k = 0; k < NS; ++k) h[tw_offset(nt, p) + (r - 1) * NS + k] = w[r * k * stride];
     }
     void *d = nullptr;
-    cudaError_t e = cudaMalloc(&d, sizeof(cx<T>) * nt);
+    cudaError_t e = cudaMalloc(&d, sizeof(cx<T>) * n);
     if (e != cudaSuccess) return e;
-    e = cudaMemcpy(d, h.data(), sizeof(cx<T>) * nt, cudaMemcpyHostToDevice);
+    e = cudaMemcpy(d, h.data(), sizeof(cx<T>) * n, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) { cudaFree(d); return e; }
     g_tables.tw[key] = d;
     *out = (const cx<T> *)d;

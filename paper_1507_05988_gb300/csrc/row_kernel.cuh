@@ -167,7 +167,8 @@ __device__ __forceinline__ void pass_compute(cx<T> (&v)[RowCfg<NT>::E], int t,
     constexpr int R = PassCfg<NT, P>::R;
     constexpr int NS = PassCfg<NT, P>::NS;
     constexpr int NB = C::E / R;
-    constexpr int STRIDE = NT / (NS * R);
+    constexpr int OFF = tw_offset(NT, P);
+    static_assert(R == fft_radix(NT, P) && NS == fft_ns(NT, P), "pass structure");
 #pragma unroll
     for (int i = 0; i < NB; ++i) {
         const int j = t + C::TPR * i;
@@ -175,7 +176,7 @@ __device__ __forceinline__ void pass_compute(cx<T> (&v)[RowCfg<NT>::E], int t,
             const int k = j & (NS - 1);
 #pragma unroll
             for (int r = 1; r < R; ++r) {
-                cx<T> w = ldg_cx(&tw[FCN_IDX(r * k * STRIDE, NT, 3)]);
+                cx<T> w = ldg_cx(&tw[FCN_IDX(OFF + (r - 1) * NS + k, tw_size(NT), 3)]);
                 if (DIR > 0) w.y = -w.y;
                 v[i * R + r] = cmul(v[i * R + r], w);
             }
