@@ -127,7 +127,30 @@ __device__ __forceinline__ cx<T> chunk_scan(cx<T> A, cx<T> B, int C, int col, cx
             smB[FCN_IDX(w * C + col, nw * C, 39)] = B;
         }
         __syncthreads();
-        if ((int)threadIdx.x < C) {
+        if (nw * C <= 32) {
+            // one warp scans the warp totals of all C columns at once:
+            // lane l holds warp l / C of column l % C
+            if (threadIdx.x < 32) {
+                const int kw = lane / C, c0 = lane % C;
+                const bool on = kw < nw;
+                cx<T> A2 = mk(T(1), T(0)), B2 = czero<T>();
+                if (on) {
+                    A2 = smA[FCN_IDX(kw * C + c0, nw * C, 48)];
+                    B2 = smB[FCN_IDX(kw * C + c0, nw * C, 49)];
+                }
+                for (int d = 1; d < nw; d <<= 1) {
+                    const cx<T> Ao = REV ? shfl_down_cx(A2, d * C) : shfl_up_cx(A2, d * C);
+                    const cx<T> Bo = REV ? shfl_down_cx(B2, d * C) : shfl_up_cx(B2, d * C);
+                    if (REV ? (kw + d < nw) : (kw >= d)) {
+                        B2 = cmul(A2, Bo) + B2;
+                        A2 = cmul(A2, Ao);
+                    }
+                }
+                cx<T> ex = REV ? shfl_down_cx(B2, C) : shfl_up_cx(B2, C);
+                if (REV ? (kw == nw - 1) : (kw == 0)) ex = czero<T>();
+                if (on) smC[FCN_IDX(kw * C + c0, nw * C, 50)] = ex;
+            }
+        } else if ((int)threadIdx.x < C) {
             const int c0 = threadIdx.x;
             cx<T> c = czero<T>();
             if (!REV) {
@@ -318,13 +341,65 @@ __device__ __forceinline__ void cp_async_cx(cx<T> *dst, const cx<T> *src, bool v
         asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
 }
 
+template <typename T>
+__device__ __forceinline__ void cp_async_cx_full(cx<T> *dst, const cx<T> *src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    if constexpr (sizeof(cx<T>) == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+
 __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
 constexpr size_t kCnStagedSmemMax = 227 * 1024;
 
-template <typename T, int L>
+// Forward sweep, pass 1, of the register-fed staged variant: x and 1/piv
+// are read from global memory straight into registers (the compiler
+// hoists the loads of the unrolled loop), alpha_j and gamma_j go to the
+// thread's shared-memory slots.  EDGE: the chunk touches row -1 or row nr.
+template <typename T, int L, bool EDGE>
+__device__ __forceinline__ void cn_f1_reg(const ColArgs<T> &a, int q, int qq, int j0, T delta, cx<T> *At,
+                                          cx<T> *Gt, int BD, cx<T> (&y)[L], cx<T> &PA, cx<T> &PB) {
+    const int nt = a.nt, nr = a.nr, nq = nt / 2 + 1;
+    const cx<T> *fx = a.field + q;
+    const cx<T> *fi = a.invden + qq;
+    auto X = [&](int j) -> cx<T> {
+        if (EDGE && (j < 0 || j >= nr)) return czero<T>();
+        return ldg_cx(fx + FCN_IDX((size_t)j * nt, (size_t)nr * nt, 51));
+    };
+    cx<T> xm = X(j0 - 1), x0 = X(j0);
+#pragma unroll
+    for (int k = 0; k < L; ++k) {
+        const int j = j0 + k;
+        const cx<T> xp = X(j + 1);
+        cx<T> inv = czero<T>();
+        if (!EDGE || j < nr) inv = ldg_cx(fi + FCN_IDX((size_t)j * nq, (size_t)nr * nq, 52));
+        CnCoef<T> cf;
+        if (!EDGE || j < nr - 1) {
+            cf = a.coef[FCN_IDX(j, nr, 53)];
+        } else {
+            cf.sl = T(0); cf.sh = T(0); cf.c0 = T(0); cf.d = T(0);
+        }
+        const T cd = cf.d * (cf.c0 - delta);
+        const T wx = cf.sl * xm.x + cf.sh * xp.x - cd * x0.x;
+        const T wy = cf.sl * xm.y + cf.sh * xp.y - cd * x0.y;
+        const cx<T> rhs = mk(cf.d * x0.x - wy, cf.d * x0.y + wx);
+        const cx<T> beta = cmul(rhs, inv);
+        const cx<T> al = cmul_i(inv, cf.sl);
+        At[k * BD] = al;
+        Gt[k * BD] = cmul_i(inv, cf.sh);
+        PB = cmul(al, PB) + beta;
+        PA = cmul(al, PA);
+        y[k] = beta;
+        xm = x0;
+        x0 = xp;
+    }
+}
+
+template <typename T, int L, bool REG>
 __device__ __forceinline__ void cn_staged_body(const ColArgs<T> &a, int C, int g, unsigned char *smem_raw) {
     const int BD = blockDim.x;
     const int tid = threadIdx.x;
@@ -332,8 +407,10 @@ __device__ __forceinline__ void cn_staged_body(const ColArgs<T> &a, int C, int g
     cx<T> *smA = reinterpret_cast<cx<T> *>(smem_raw);
     cx<T> *smB = smA + nwarp * C;
     cx<T> *smC = smB + nwarp * C;
-    cx<T> *Xt = smC + nwarp * C + tid;          // slot k: Xt[k * BD], k = 0 .. L+1
-    cx<T> *Gt = Xt + (L + 2) * BD;              // slot k: Gt[k * BD], k = 0 .. L-1
+    cx<T> *Xt = smC + nwarp * C + tid;          // slot k: Xt[k * BD]
+    // staged: L+2 x slots then L pivot slots; register-fed: L alpha slots
+    // then L gamma slots
+    cx<T> *Gt = Xt + (REG ? L : L + 2) * BD;    // slot k: Gt[k * BD], k = 0 .. L-1
 
     const int col = tid % C;
     const int chunk = tid / C;
@@ -344,7 +421,25 @@ __device__ __forceinline__ void cn_staged_body(const ColArgs<T> &a, int C, int g
     const T delta = a.dk * T(qq) * T(qq);
     const int j0 = chunk * L;
 
-    {
+    cx<T> y[L];
+    cx<T> PA = mk(T(1), T(0)), PB = czero<T>();
+    // slot of alpha_j: Xt[(k+1) BD] (staged: where x_j was), At[k BD] below
+    cx<T> *At = REG ? Xt : Xt + BD;
+    if constexpr (REG) {
+        if (j0 >= 1 && j0 + L < nr)
+            cn_f1_reg<T, L, false>(a, q, qq, j0, delta, At, Gt, BD, y, PA, PB);
+        else
+            cn_f1_reg<T, L, true>(a, q, qq, j0, delta, At, Gt, BD, y, PA, PB);
+    } else {
+    if (j0 >= 1 && j0 + L < nr) {
+        // interior chunk: every row j0-1 .. j0+L exists
+        const cx<T> *src = a.field + (size_t)(j0 - 1) * nt + q;
+#pragma unroll
+        for (int k = 0; k < L + 2; ++k) cp_async_cx_full(Xt + k * BD, src + (size_t)k * nt);
+        const cx<T> *pv = a.invden + (size_t)j0 * nq + qq;
+#pragma unroll
+        for (int k = 0; k < L; ++k) cp_async_cx_full(Gt + k * BD, pv + (size_t)k * nq);
+    } else {
         // rows outside 0..nr-1 are zero-filled (the source is then not read;
         // the base address stands in for it)
         const cx<T> *src = a.field + (ptrdiff_t)(j0 - 1) * nt + q;
@@ -364,8 +459,6 @@ __device__ __forceinline__ void cn_staged_body(const ColArgs<T> &a, int C, int g
     cp_async_wait_all();
 
     // forward sweep, pass 1: beta_j, alpha_j, gamma_j and the chunk map
-    cx<T> y[L];
-    cx<T> PA = mk(T(1), T(0)), PB = czero<T>();
     cx<T> xm = Xt[0], x0 = Xt[BD];
 #pragma unroll
     for (int k = 0; k < L; ++k) {
@@ -393,12 +486,13 @@ __device__ __forceinline__ void cn_staged_body(const ColArgs<T> &a, int C, int g
         x0 = xp;
         asm volatile("" ::: "memory");          // keep the slot loads in row order
     }
+    }
     // forward sweep, pass 2: exact y from the carry entering the chunk
     {
         cx<T> yp = chunk_scan<T, false>(PA, PB, C, col, smA, smB, smC);
 #pragma unroll
         for (int k = 0; k < L; ++k) {
-            y[k] = cmul(Xt[(k + 1) * BD], yp) + y[k];
+            y[k] = cmul(At[k * BD], yp) + y[k];
             yp = y[k];
             asm volatile("" ::: "memory");
         }
@@ -428,14 +522,14 @@ __device__ __forceinline__ void cn_staged_body(const ColArgs<T> &a, int C, int g
 template <typename T, int L>
 constexpr int staged_threads() { return L >= 16 ? 256 : 512; }
 
-template <typename T, int L>
+template <typename T, int L, bool REG>
 __global__ void __launch_bounds__(staged_threads<T, L>(), L >= 16 ? 3 : 2)
 cn_staged_kernel(ColArgs<T> a, int C) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int ngroups = a.nt / C;
     const int b = blockIdx.x;
     const int g = (b & 1) ? (ngroups - 1 - (b >> 1)) : (b >> 1);
-    cn_staged_body<T, L>(a, C, g, smem_raw);
+    cn_staged_body<T, L, REG>(a, C, g, smem_raw);
 }
 
 template <typename T>
@@ -458,7 +552,7 @@ __global__ void cn_coef_kernel(TableArgs a, CnCoef<T> *coef) {
 // the CTA size, fewer for tall grids, more for short ones).  Returns
 // cudaErrorInvalidConfiguration when the grid does not fit (the caller then
 // falls back to the register variant).
-template <typename T, int L>
+template <typename T, int L, bool REG>
 cudaError_t launch_cn_staged_l(const ColArgs<T> &a, cudaStream_t st) {
     if (!a.coef) return cudaErrorInvalidConfiguration;
     constexpr int CMIN = 32 / int(sizeof(cx<T>));
@@ -470,9 +564,10 @@ cudaError_t launch_cn_staged_l(const ColArgs<T> &a, cudaStream_t st) {
     if (C > a.nt) C = a.nt;
     const int threads = ((C * P + 31) / 32) * 32;
     if (threads > TMAX) return cudaErrorInvalidConfiguration;
-    const size_t smem = sizeof(cx<T>) * (3 * (size_t)(threads / 32) * C + (size_t)(2 * L + 2) * threads);
+    const size_t slots = REG ? 2 * L : 2 * L + 2;
+    const size_t smem = sizeof(cx<T>) * (3 * (size_t)(threads / 32) * C + slots * threads);
     if (smem > kCnStagedSmemMax) return cudaErrorInvalidConfiguration;
-    cn_staged_kernel<T, L><<<a.nt / C, threads, smem, st>>>(a, C);
+    cn_staged_kernel<T, L, REG><<<a.nt / C, threads, smem, st>>>(a, C);
     return cudaGetLastError();
 }
 
@@ -504,7 +599,12 @@ cudaError_t launch_cn(const ColArgs<T> &a, cudaStream_t st) {
     const int target = (a.variant & 2) ? 512 : 256;
     cudaError_t e = cudaErrorInvalidConfiguration;
     if (a.variant >= kColStagedFirst) {
-        e = (a.variant == kColStagedFirst) ? launch_cn_staged_l<T, LL>(a, st) : launch_cn_staged_l<T, LS>(a, st);
+        switch (a.variant - kColStagedFirst) {
+            case 0: e = launch_cn_staged_l<T, LL, false>(a, st); break;
+            case 1: e = launch_cn_staged_l<T, LS, false>(a, st); break;
+            case 2: e = launch_cn_staged_l<T, LL, true>(a, st); break;
+            default: e = launch_cn_staged_l<T, LS, true>(a, st); break;
+        }
         if (e != cudaErrorInvalidConfiguration) return e;
     }
     if (a.variant < kColStagedFirst && (a.variant & 1)) e = launch_cn_l<T, LS>(a, target, st);
@@ -522,11 +622,14 @@ cudaError_t launch_cn_coef(const TableArgs &a, CnCoef<T> *coef, cudaStream_t st)
 template <typename T>
 cudaError_t prepare_cn() {
     constexpr int LL = sizeof(T) == 4 ? 16 : 8;
-    cudaError_t e = cudaFuncSetAttribute(cn_staged_kernel<T, LL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kCnStagedSmemMax);
+    const int mx = (int)kCnStagedSmemMax;
+    cudaError_t e = cudaFuncSetAttribute(cn_staged_kernel<T, LL, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(cn_staged_kernel<T, LL / 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)kCnStagedSmemMax);
+        e = cudaFuncSetAttribute(cn_staged_kernel<T, LL / 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(cn_staged_kernel<T, LL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(cn_staged_kernel<T, LL / 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     return e;
 }
 

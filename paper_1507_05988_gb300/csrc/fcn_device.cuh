@@ -178,7 +178,9 @@ struct ColArgs {
     T s;                     // dz / (4 k0 dr^2), 0 without diffraction
     T dk;                    // k'' dz/4 domega^2, 0 without dispersion: delta_q = dk q^2
     int variant;             // 0..3: register chunks, long/short x CTA 256/512;
-                             // 4, 5: staged chunks of 16 / 8 rows (need coef)
+                             // 4, 5: cp.async-staged chunks of 16 / 8 rows (FP32);
+                             // 6, 7: register-fed staged chunks of 16 / 8 rows
+                             // (4..7 need coef)
 };
 
 struct TableArgs {
@@ -197,7 +199,7 @@ cudaError_t prepare_rows(int nt);
 template <typename T>
 cudaError_t launch_cn(const ColArgs<T> &a, cudaStream_t st);
 constexpr int kRowVariants = 3;
-constexpr int kColVariants = 6;
+constexpr int kColVariants = 8;
 constexpr int kColStagedFirst = 4;      // variants >= this need ColArgs::coef
 template <typename T>
 cudaError_t launch_cn_table(const TableArgs &a, cx<T> *table, cudaStream_t st);

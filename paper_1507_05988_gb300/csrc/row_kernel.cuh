@@ -392,31 +392,45 @@ __device__ __forceinline__ double exp_t<double>(double x) { return exp(x); }
 // A <- A exp(h N(Ihat, u)) with h folded into the coefficients:
 //   phi = Ihat (hk0 + Ihat (hk1 + Ihat (hk2 + Ihat hk3))) - hplasma u,
 //   lnamp = -hloss Ihat^(K-1) (1 - sat u),  A <- A exp(lnamp + i phi).
-// ihKm1 = Ihat^(K-1).
+// nl_terms gives (phi, lnamp); ihKm1 = Ihat^(K-1).
 template <typename T>
-__device__ __forceinline__ cx<T> nl_apply(cx<T> a, T ih, T ihKm1, T u, const NLCoef<T> &c) {
-    T phi = fma(ih, c.hk[3], c.hk[2]);
-    phi = fma(ih, phi, c.hk[1]);
-    phi = fma(ih, phi, c.hk[0]);
-    phi = fma(-c.hplasma, u, ih * phi);
-    const T lnamp = -(c.hloss * fma(-c.sat, u, T(1))) * ihKm1;
+__device__ __forceinline__ void nl_terms(T ih, T ihKm1, T u, const NLCoef<T> &c, T *phi, T *lnamp) {
+    T p = fma(ih, c.hk[3], c.hk[2]);
+    p = fma(ih, p, c.hk[1]);
+    p = fma(ih, p, c.hk[0]);
+    *phi = fma(-c.hplasma, u, ih * p);
+    *lnamp = -(c.hloss * fma(-c.sat, u, T(1))) * ihKm1;
+}
+
+// FP32 delta form: A + A D with D = amp exp(i phi) - 1
+//   = (em1 + cm1 + em1 cm1) + i s (1 + em1),  em1 = amp - 1.
+__device__ __forceinline__ cx<float> nl_delta(cx<float> a, float sn, float cm1, float em1) {
+    const float dre = fmaf(em1, cm1, em1 + cm1);
+    const float dim = fmaf(sn, em1, sn);
+    return mk(fmaf(a.x, dre, fmaf(-a.y, dim, a.x)), fmaf(a.x, dim, fmaf(a.y, dre, a.y)));
+}
+
+// Small arguments (|phi| < 1e-3, |lnamp| < 1e-4): the series of sin, cos - 1
+// and exp - 1 are exact to float rounding there (see sincos_m1_f32 and
+// expm1_f32 for the bounds).
+__device__ __forceinline__ bool nl_small(float phi, float lnamp) {
+    return fabsf(phi) < 1.0e-3f && fabsf(lnamp) < 1.0e-4f;
+}
+__device__ __forceinline__ cx<float> nl_apply_small(cx<float> a, float phi, float lnamp) {
+    const float p2 = phi * phi;
+    const float cm1 = -0.5f * p2;
+    const float sn = fmaf(phi * p2, -1.66666666666666666667e-1f, phi);
+    const float em1 = fmaf(0.5f * lnamp, lnamp, lnamp);
+    return nl_delta(a, sn, cm1, em1);
+}
+
+template <typename T>
+__device__ __forceinline__ cx<T> nl_apply_terms(cx<T> a, T phi, T lnamp) {
     if constexpr (sizeof(T) == 4) {
-        // delta form: A + A D with D = amp exp(i phi) - 1
-        //   = (em1 + cm1 + em1 cm1) + i s (1 + em1),  em1 = amp - 1
-        float sn, cm1, em1;
-        if (fabsf(phi) < 1.0e-3f && fabsf(lnamp) < 1.0e-4f) {
-            // both series exact to float rounding (see sincos_m1_f32, expm1_f32)
-            const float p2 = phi * phi;
-            cm1 = -0.5f * p2;
-            sn = fmaf(phi * p2, -1.66666666666666666667e-1f, phi);
-            em1 = fmaf(0.5f * lnamp, lnamp, lnamp);
-        } else {
-            sincos_m1_f32(phi, &sn, &cm1);
-            em1 = expm1_f32(lnamp);
-        }
-        const float dre = fmaf(em1, cm1, em1 + cm1);
-        const float dim = fmaf(sn, em1, sn);
-        return mk(fmaf(a.x, dre, fmaf(-a.y, dim, a.x)), fmaf(a.x, dim, fmaf(a.y, dre, a.y)));
+        if (nl_small(phi, lnamp)) return nl_apply_small(a, phi, lnamp);
+        float sn, cm1;
+        sincos_m1_f32(phi, &sn, &cm1);
+        return nl_delta(a, sn, cm1, expm1_f32(lnamp));
     } else {
         T s, co;
         sincos_t<T>(phi, &s, &co);
@@ -516,12 +530,31 @@ __device__ __forceinline__ void nl_half_smem(cx<T> *S, T *U, int t, const NLCoef
             x[k] = S[FCN_IDX(ip, C::PADN, 27)];
             u[k] = need_u ? fma(U[FCN_IDX(ip, C::PADN, 28)], omc, carry) : T(0);
         }
+        T phi[UN], lna[UN];
 #pragma unroll
         for (int k = 0; k < UN; ++k) {
-            const int ip = pidx(p0 + e0 + k, NT);
             const T ih = cnorm(x[k]) * c.inv_is;
-            S[ip] = nl_apply(x[k], ih, powk<(KT > 0 ? KT - 1 : 0)>(ih, c.K - 1), u[k], c);
-            if (STORE_U) U[ip] = u[k];
+            nl_terms(ih, powk<(KT > 0 ? KT - 1 : 0)>(ih, c.K - 1), u[k], c, &phi[k], &lna[k]);
+        }
+        bool small = false;
+        if constexpr (sizeof(T) == 4) {
+            small = true;
+#pragma unroll
+            for (int k = 0; k < UN; ++k) small = small && nl_small(phi[k], lna[k]);
+        }
+        if (small) {
+            // the common case, decided once for the group of points
+#pragma unroll
+            for (int k = 0; k < UN; ++k) {
+                if constexpr (sizeof(T) == 4) S[pidx(p0 + e0 + k, NT)] = nl_apply_small(x[k], phi[k], lna[k]);
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < UN; ++k) S[pidx(p0 + e0 + k, NT)] = nl_apply_terms(x[k], phi[k], lna[k]);
+        }
+        if (STORE_U) {
+#pragma unroll
+            for (int k = 0; k < UN; ++k) U[pidx(p0 + e0 + k, NT)] = u[k];
         }
     }
 }

@@ -367,7 +367,7 @@ def test_adaptive_step_doubling_matches_oracle_controller(fcn, prec):
 
 @pytest.mark.parametrize("prec", [FP64, FP32])
 @pytest.mark.parametrize("row_v", [0, 1, 2])
-@pytest.mark.parametrize("col_v", [0, 1, 2, 3, 4, 5])
+@pytest.mark.parametrize("col_v", [0, 1, 2, 3, 4, 5, 6, 7])
 def test_every_kernel_variant_matches_oracle(fcn, prec, row_v, col_v):
     """Every variant the autotuner can pick computes the same step."""
     wl = W.small(130, 1024, p_over_pcr=4.0, noise_seed=6).with_(n2j=(W.N2, W.N4, 0, 0))
@@ -385,7 +385,7 @@ def test_every_kernel_variant_matches_oracle(fcn, prec, row_v, col_v):
 
 @pytest.mark.parametrize("prec", [FP64, FP32])
 @pytest.mark.parametrize("nr,nt", [(3, 64), (17, 128), (1000, 256), (2048, 64)])
-@pytest.mark.parametrize("col_v", [4, 5])
+@pytest.mark.parametrize("col_v", [4, 5, 6, 7])
 def test_staged_column_variants_on_ragged_and_tall_grids(fcn, prec, nr, nt, col_v):
     """Staged column kernels: chunks that overhang Nr, CTAs narrowed for tall
     grids (Nr = 2048) and widened for short ones, against the oracle."""
@@ -409,7 +409,7 @@ def test_autotuner_picks_a_valid_variant_and_stays_correct(fcn):
     s.set_field(wl.field())
     s.step(4e-3, 3)
     rv, cv = s.variants()
-    assert 0 <= rv < 3 and 0 <= cv < 6
+    assert 0 <= rv < 3 and 0 <= cv < 8
     A = s.get_field()
     s.close()
     Aref, _ = oracle.run(pb, 4e-3, 3, wl.field())
