@@ -360,10 +360,11 @@ constexpr size_t kCnStagedSmemMax = 227 * 1024;
 // are read from global memory straight into registers (the compiler
 // hoists the loads of the unrolled loop), alpha_j and gamma_j go to the
 // thread's shared-memory slots.  EDGE: the chunk touches row -1 or row nr.
-template <typename T, int L, bool EDGE>
+template <typename T, int L, bool EDGE, int NTC>
 __device__ __forceinline__ void cn_f1_reg(const ColArgs<T> &a, int q, int qq, int j0, T delta, cx<T> *At,
                                           cx<T> *Gt, int BD, cx<T> (&y)[L], cx<T> &PA, cx<T> &PB) {
-    const int nt = a.nt, nr = a.nr, nq = nt / 2 + 1;
+    // NTC: Nt as a compile-time constant (row strides become immediates), 0: a.nt
+    const int nt = NTC ? NTC : a.nt, nr = a.nr, nq = nt / 2 + 1;
     const cx<T> *fx = a.field + q;
     const cx<T> *fi = a.invden + qq;
     auto X = [&](int j) -> cx<T> {
@@ -399,7 +400,7 @@ __device__ __forceinline__ void cn_f1_reg(const ColArgs<T> &a, int q, int qq, in
     }
 }
 
-template <typename T, int L, bool REG>
+template <typename T, int L, bool REG, int NTC = 0>
 __device__ __forceinline__ void cn_staged_body(const ColArgs<T> &a, int C, int g, unsigned char *smem_raw) {
     const int BD = blockDim.x;
     const int tid = threadIdx.x;
@@ -415,7 +416,7 @@ __device__ __forceinline__ void cn_staged_body(const ColArgs<T> &a, int C, int g
     const int col = tid % C;
     const int chunk = tid / C;
     const int q = g * C + col;
-    const int nt = a.nt, nr = a.nr;
+    const int nt = NTC ? NTC : a.nt, nr = a.nr;
     const int nq = nt / 2 + 1;
     const int qq = (q <= nt / 2) ? q : nt - q;
     const T delta = a.dk * T(qq) * T(qq);
@@ -427,9 +428,9 @@ __device__ __forceinline__ void cn_staged_body(const ColArgs<T> &a, int C, int g
     cx<T> *At = REG ? Xt : Xt + BD;
     if constexpr (REG) {
         if (j0 >= 1 && j0 + L < nr)
-            cn_f1_reg<T, L, false>(a, q, qq, j0, delta, At, Gt, BD, y, PA, PB);
+            cn_f1_reg<T, L, false, NTC>(a, q, qq, j0, delta, At, Gt, BD, y, PA, PB);
         else
-            cn_f1_reg<T, L, true>(a, q, qq, j0, delta, At, Gt, BD, y, PA, PB);
+            cn_f1_reg<T, L, true, NTC>(a, q, qq, j0, delta, At, Gt, BD, y, PA, PB);
     } else {
     if (j0 >= 1 && j0 + L < nr) {
         // interior chunk: every row j0-1 .. j0+L exists
@@ -508,11 +509,12 @@ __device__ __forceinline__ void cn_staged_body(const ColArgs<T> &a, int C, int g
     }
     // backward sweep, pass 2 and store
     cx<T> xn = chunk_scan<T, true>(QA, QB, C, col, smA, smB, smC);
+    cx<T> *fo = a.field + (size_t)j0 * nt + q;
 #pragma unroll
     for (int k = L - 1; k >= 0; --k) {
         const int j = j0 + k;
         xn = cmul(Gt[k * BD], xn) + y[k];
-        if (j < nr) a.field[FCN_IDX((size_t)j * nt + q, (size_t)nr * nt, 47)] = xn;
+        if (j < nr) fo[FCN_IDX((size_t)k * nt, (size_t)(nr - j0) * nt, 47)] = xn;
         asm volatile("" ::: "memory");
     }
 }
@@ -522,14 +524,14 @@ __device__ __forceinline__ void cn_staged_body(const ColArgs<T> &a, int C, int g
 template <typename T, int L>
 constexpr int staged_threads() { return L >= 16 ? 256 : 512; }
 
-template <typename T, int L, bool REG>
+template <typename T, int L, bool REG, int NTC>
 __global__ void __launch_bounds__(staged_threads<T, L>(), L >= 16 ? 3 : 2)
 cn_staged_kernel(ColArgs<T> a, int C) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int ngroups = a.nt / C;
     const int b = blockIdx.x;
     const int g = (b & 1) ? (ngroups - 1 - (b >> 1)) : (b >> 1);
-    cn_staged_body<T, L, REG>(a, C, g, smem_raw);
+    cn_staged_body<T, L, REG, NTC>(a, C, g, smem_raw);
 }
 
 template <typename T>
@@ -552,7 +554,7 @@ __global__ void cn_coef_kernel(TableArgs a, CnCoef<T> *coef) {
 // the CTA size, fewer for tall grids, more for short ones).  Returns
 // cudaErrorInvalidConfiguration when the grid does not fit (the caller then
 // falls back to the register variant).
-template <typename T, int L, bool REG>
+template <typename T, int L, bool REG, int NTC>
 cudaError_t launch_cn_staged_l(const ColArgs<T> &a, cudaStream_t st) {
     if (!a.coef) return cudaErrorInvalidConfiguration;
     constexpr int CMIN = 32 / int(sizeof(cx<T>));
@@ -567,7 +569,7 @@ cudaError_t launch_cn_staged_l(const ColArgs<T> &a, cudaStream_t st) {
     const size_t slots = REG ? 2 * L : 2 * L + 2;
     const size_t smem = sizeof(cx<T>) * (3 * (size_t)(threads / 32) * C + slots * threads);
     if (smem > kCnStagedSmemMax) return cudaErrorInvalidConfiguration;
-    cn_staged_kernel<T, L, REG><<<a.nt / C, threads, smem, st>>>(a, C);
+    cn_staged_kernel<T, L, REG, NTC><<<a.nt / C, threads, smem, st>>>(a, C);
     return cudaGetLastError();
 }
 
@@ -587,6 +589,29 @@ cudaError_t launch_cn_l(const ColArgs<T> &a, int target, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// Register-fed variant with Nt as a compile-time constant for the grids of
+// 512 .. 8192 points in FP32 (every row offset an immediate), generic otherwise.
+template <typename T, int L>
+cudaError_t launch_cn_reg_nt(const ColArgs<T> &a, cudaStream_t st) {
+    if constexpr (sizeof(T) == 4) {
+        switch (a.nt) {
+            case 512: return launch_cn_staged_l<T, L, true, 512>(a, st);
+            case 1024: return launch_cn_staged_l<T, L, true, 1024>(a, st);
+            case 2048: return launch_cn_staged_l<T, L, true, 2048>(a, st);
+            case 4096: return launch_cn_staged_l<T, L, true, 4096>(a, st);
+            case 8192: return launch_cn_staged_l<T, L, true, 8192>(a, st);
+            default: break;
+        }
+    }
+    return launch_cn_staged_l<T, L, true, 0>(a, st);
+}
+
+template <typename T, int L, bool REG, int NTC>
+cudaError_t set_staged_attr() {
+    return cudaFuncSetAttribute(cn_staged_kernel<T, L, REG, NTC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)kCnStagedSmemMax);
+}
+
 }  // namespace
 
 // Variants: bit 0 selects the shorter chunk (more threads, fewer registers
@@ -600,10 +625,10 @@ cudaError_t launch_cn(const ColArgs<T> &a, cudaStream_t st) {
     cudaError_t e = cudaErrorInvalidConfiguration;
     if (a.variant >= kColStagedFirst) {
         switch (a.variant - kColStagedFirst) {
-            case 0: e = launch_cn_staged_l<T, LL, false>(a, st); break;
-            case 1: e = launch_cn_staged_l<T, LS, false>(a, st); break;
-            case 2: e = launch_cn_staged_l<T, LL, true>(a, st); break;
-            default: e = launch_cn_staged_l<T, LS, true>(a, st); break;
+            case 0: e = launch_cn_staged_l<T, LL, false, 0>(a, st); break;
+            case 1: e = launch_cn_staged_l<T, LS, false, 0>(a, st); break;
+            case 2: e = launch_cn_reg_nt<T, LL>(a, st); break;
+            default: e = launch_cn_reg_nt<T, LS>(a, st); break;
         }
         if (e != cudaErrorInvalidConfiguration) return e;
     }
@@ -621,15 +646,23 @@ cudaError_t launch_cn_coef(const TableArgs &a, CnCoef<T> *coef, cudaStream_t st)
 
 template <typename T>
 cudaError_t prepare_cn() {
-    constexpr int LL = sizeof(T) == 4 ? 16 : 8;
-    const int mx = (int)kCnStagedSmemMax;
-    cudaError_t e = cudaFuncSetAttribute(cn_staged_kernel<T, LL, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(cn_staged_kernel<T, LL / 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(cn_staged_kernel<T, LL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(cn_staged_kernel<T, LL / 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    constexpr int LL = sizeof(T) == 4 ? 16 : 8, LS = LL / 2;
+    cudaError_t e = set_staged_attr<T, LL, false, 0>();
+    if (e == cudaSuccess) e = set_staged_attr<T, LS, false, 0>();
+    if (e == cudaSuccess) e = set_staged_attr<T, LL, true, 0>();
+    if (e == cudaSuccess) e = set_staged_attr<T, LS, true, 0>();
+    if constexpr (sizeof(T) == 4) {
+        if (e == cudaSuccess) e = set_staged_attr<T, LL, true, 512>();
+        if (e == cudaSuccess) e = set_staged_attr<T, LS, true, 512>();
+        if (e == cudaSuccess) e = set_staged_attr<T, LL, true, 1024>();
+        if (e == cudaSuccess) e = set_staged_attr<T, LS, true, 1024>();
+        if (e == cudaSuccess) e = set_staged_attr<T, LL, true, 2048>();
+        if (e == cudaSuccess) e = set_staged_attr<T, LS, true, 2048>();
+        if (e == cudaSuccess) e = set_staged_attr<T, LL, true, 4096>();
+        if (e == cudaSuccess) e = set_staged_attr<T, LS, true, 4096>();
+        if (e == cudaSuccess) e = set_staged_attr<T, LL, true, 8192>();
+        if (e == cudaSuccess) e = set_staged_attr<T, LS, true, 8192>();
+    }
     return e;
 }
 

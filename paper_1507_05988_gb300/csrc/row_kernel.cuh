@@ -135,6 +135,29 @@ __device__ __forceinline__ cx<T> rot16(cx<T> o, int m) {
     }
 }
 
+// Complex add / subtract; FP32 as one packed f32x2 instruction (each lane an
+// IEEE single add, the same result as two scalar adds).
+__device__ __forceinline__ cx<float> cadd2(cx<float> a, cx<float> b) {
+    unsigned long long ra, rb, rc;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(ra) : "f"(a.x), "f"(a.y));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(rb) : "f"(b.x), "f"(b.y));
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(rc) : "l"(ra), "l"(rb));
+    cx<float> r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(rc));
+    return r;
+}
+__device__ __forceinline__ cx<float> csub2(cx<float> a, cx<float> b) {
+    unsigned long long ra, rb, rc;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(ra) : "f"(a.x), "f"(a.y));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(rb) : "f"(b.x), "f"(b.y));
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(rc) : "l"(ra), "l"(rb));
+    cx<float> r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(rc));
+    return r;
+}
+__device__ __forceinline__ cx<double> cadd2(cx<double> a, cx<double> b) { return a + b; }
+__device__ __forceinline__ cx<double> csub2(cx<double> a, cx<double> b) { return a - b; }
+
 // In-register DFT of size R (power of two <= 16), natural order in and out,
 // X_k = sum_n x_n exp(DIR 2 pi i n k / R), by radix-2 decimation in time.
 template <typename T, int R, int DIR>
@@ -147,9 +170,17 @@ struct Dft {
         Dft<T, R / 2, DIR>::run(o);
 #pragma unroll
         for (int k = 0; k < R / 2; ++k) {
-            cx<T> t = rot16<T, DIR>(o[k], k * (16 / R));
-            v[k] = e[k] + t;
-            v[k + R / 2] = e[k] - t;
+            const int m = k * (16 / R);
+            cx<T> t = rot16<T, DIR>(o[k], m);
+            if ((m & 7) == 4) {
+                // quarter turn: t is o with its parts swapped, which the
+                // scalar adds take as operands at no cost
+                v[k] = e[k] + t;
+                v[k + R / 2] = e[k] - t;
+            } else {
+                v[k] = cadd2(e[k], t);
+                v[k + R / 2] = csub2(e[k], t);
+            }
         }
     }
 };
