@@ -50,37 +50,120 @@ __device__ __forceinline__ cx<float> crecip(cx<float> z) {
 }
 
 // One thread per |q| = 0..Nt/2 runs the Thomas pivot recurrence down the
-// radial index, piv_j = b_j - a_j c_{j-1}/piv_{j-1}, in the working precision
-// (FP64 tables in FP64; FP32 tables in FP32, ~50x faster on this GPU, which
-// matters when adaptive runs need two tables per attempt).  The recurrence is
-// contractive, so rounding does not accumulate.
+// radial index, piv_j = b_j - a_j c_{j-1}/piv_{j-1}, in FP64 (FP64 tables;
+// FP32 tables use cn_table_kernel_f32 below with the same accuracy: pivots
+// computed in plain FP32 carry ~1e-7 relative errors that make the discrete
+// Crank-Nicolson step slightly non-unitary, the same way at every z-step,
+// which showed as an energy drift of ~1e-8 per step).  The radial ratio
+// tables are staged in shared memory first, so the serial recurrence waits
+// on no global load.
 template <typename T>
 __global__ void cn_table_kernel(TableArgs a, cx<T> *table) {
+    extern __shared__ double sh_lohi[];    // lo[nr], hi[nr]
+    for (int j = threadIdx.x; j < a.nr; j += blockDim.x) {
+        sh_lohi[j] = a.lo[FCN_IDX(j, a.nr, 31)];
+        sh_lohi[a.nr + j] = a.hi[FCN_IDX(j, a.nr, 32)];
+    }
+    __syncthreads();
     const int nq = a.nt / 2 + 1;
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= nq) return;
-    const T delta = T(a.dk * double(q) * double(q));
-    const T s = T(a.s);
-    cx<T> cp = mk(T(0), T(0));
+    const double delta = a.dk * double(q) * double(q);
+    const double s = a.s;
+    cx<double> cp = mk(0.0, 0.0);
     for (int j = 0; j < a.nr; ++j) {
-        cx<T> b, aa, c;
+        cx<double> b, aa, c;
         if (j == 0) {
-            aa = mk(T(0), T(0));
-            b = mk(T(1), T(4) * s - delta);
-            c = mk(T(0), -T(4) * s);
+            aa = mk(0.0, 0.0);
+            b = mk(1.0, 4.0 * s - delta);
+            c = mk(0.0, -4.0 * s);
         } else if (j < a.nr - 1) {
-            aa = mk(T(0), -s * T(a.lo[FCN_IDX(j, a.nr, 31)]));
-            b = mk(T(1), T(2) * s - delta);
-            c = mk(T(0), -s * T(a.hi[FCN_IDX(j, a.nr, 32)]));
+            aa = mk(0.0, -s * sh_lohi[j]);
+            b = mk(1.0, 2.0 * s - delta);
+            c = mk(0.0, -s * sh_lohi[a.nr + j]);
         } else {
-            aa = mk(T(0), T(0));
-            b = mk(T(1), T(0));
-            c = mk(T(0), T(0));
+            aa = mk(0.0, 0.0);
+            b = mk(1.0, 0.0);
+            c = mk(0.0, 0.0);
         }
-        const cx<T> den = b - cmul(aa, cp);
-        const cx<T> inv = crecip(den);
+        const cx<double> den = b - cmul(aa, cp);
+        const cx<double> inv = crecip(den);
         cp = cmul(c, inv);
-        table[FCN_IDX((size_t)j * nq + q, (size_t)a.nr * nq, 30)] = inv;
+        table[FCN_IDX((size_t)j * nq + q, (size_t)a.nr * nq, 30)] = mk(T(inv.x), T(inv.y));
+    }
+}
+
+// ---- FP32 tables in double-float arithmetic --------------------------------
+// A value h + l (two floats, |l| <= ulp(h)/2) carries ~48 significant bits
+// with FP32 latencies (Dekker / Knuth error-free transformations; products
+// through fmaf).  With aa_j c_{j-1} = -s^2 lo_j hi'_{j-1} (hi'_0 = 4 from
+// the axis row, hi'_j = hi_j otherwise) the pivot recurrence is
+//   1/piv_j = 1 / (b_j + kappa_j / piv_{j-1}),   kappa_j = s^2 lo_j hi'_{j-1},
+// evaluated here in double-float and rounded to float once.
+struct f2 {
+    float h, l;
+};
+__device__ __forceinline__ f2 fast_two_sum(float a, float b) {   // |a| >= |b|
+    const float s = a + b;
+    return {s, b - (s - a)};
+}
+__device__ __forceinline__ f2 two_sum(float a, float b) {
+    const float s = a + b;
+    const float bb = s - a;
+    return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ f2 df_add(f2 a, f2 b) {
+    const f2 s = two_sum(a.h, b.h);
+    return fast_two_sum(s.h, s.l + (a.l + b.l));
+}
+__device__ __forceinline__ f2 df_mul(f2 a, f2 b) {
+    const float p = a.h * b.h;
+    float e = fmaf(a.h, b.h, -p);
+    e = fmaf(a.h, b.l, e);
+    e = fmaf(a.l, b.h, e);
+    return fast_two_sum(p, e);
+}
+__device__ __forceinline__ f2 df_recip(f2 a) {
+    const float r0 = __frcp_rn(a.h);
+    // e = 1 - a r0 (exact leading part by Sterbenz), then r = r0 + r0 e
+    const float p = a.h * r0;
+    const float pe = fmaf(a.h, r0, -p);
+    const float e = ((1.0f - p) - pe) - a.l * r0;
+    return fast_two_sum(r0, r0 * e);
+}
+__device__ __forceinline__ f2 to_f2(double x) {
+    const float h = float(x);
+    return {h, float(x - double(h))};
+}
+
+__global__ void cn_table_kernel_f32(TableArgs a, cx<float> *table) {
+    extern __shared__ double sh_kappa[];     // kappa_j as double-float pairs (2 floats)
+    f2 *kap = reinterpret_cast<f2 *>(sh_kappa);
+    const double s2 = a.s * a.s;
+    for (int j = threadIdx.x; j < a.nr; j += blockDim.x) {
+        double k = 0.0;
+        if (j == 1) k = s2 * a.lo[FCN_IDX(1, a.nr, 31)] * 4.0;
+        else if (j >= 2 && j < a.nr - 1) k = s2 * a.lo[FCN_IDX(j, a.nr, 31)] * a.hi[FCN_IDX(j - 1, a.nr, 32)];
+        kap[j] = to_f2(k);
+    }
+    __syncthreads();
+    const int nq = a.nt / 2 + 1;
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nq) return;
+    const double delta = a.dk * double(q) * double(q);
+    const f2 by0 = to_f2(4.0 * a.s - delta), by1 = to_f2(2.0 * a.s - delta);
+    f2 ix = {0.f, 0.f}, iy = {0.f, 0.f};
+    const f2 one = {1.f, 0.f};
+    for (int j = 0; j < a.nr; ++j) {
+        const f2 kp = kap[j];
+        const f2 by = (j == 0) ? by0 : ((j < a.nr - 1) ? by1 : f2{0.f, 0.f});
+        const f2 wx = df_add(df_mul(kp, ix), one);
+        const f2 wy = df_add(df_mul(kp, iy), by);
+        const f2 rn = df_recip(df_add(df_mul(wx, wx), df_mul(wy, wy)));
+        ix = df_mul(wx, rn);
+        iy = df_mul(wy, rn);
+        iy = {-iy.h, -iy.l};
+        table[FCN_IDX((size_t)j * nq + q, (size_t)a.nr * nq, 30)] = mk(ix.h + ix.l, iy.h + iy.l);
     }
 }
 
@@ -670,7 +753,10 @@ template <typename T>
 cudaError_t launch_cn_table(const TableArgs &a, cx<T> *table, cudaStream_t st) {
     const int nq = a.nt / 2 + 1;
     const int threads = 32;   // spread the latency-bound recurrences over many SMs
-    cn_table_kernel<T><<<(nq + threads - 1) / threads, threads, 0, st>>>(a, table);
+    if constexpr (sizeof(T) == 4)
+        cn_table_kernel_f32<<<(nq + threads - 1) / threads, threads, sizeof(double) * a.nr, st>>>(a, table);
+    else
+        cn_table_kernel<T><<<(nq + threads - 1) / threads, threads, sizeof(double) * 2 * a.nr, st>>>(a, table);
     return cudaGetLastError();
 }
 

@@ -88,12 +88,16 @@ __host__ __device__ constexpr double cos16(int m) {
 // unit modulus (|w|^2 - 1 ~ -6e-8 for the pi/8 pair, -3.4e-8 for pi/4), and
 // because the same constants act on every row at every step, that bias
 // accumulates into an energy drift of ~1e-7 per z-step.  So the pi/8 family
-// uses the float pair within a few ulps of (cos pi/8, sin pi/8) whose modulus
-// is closest to 1 (|w|^2 - 1 = 3.5e-9, phase error 2.3e-7 rad), and the pi/4
-// family applies 1/sqrt(2) as a two-float (hi + lo) scale.
+// uses float pairs within a few ulps of (cos pi/8, sin pi/8) of nearly unit
+// modulus, one per direction with opposite modulus errors (+3.53e-9 forward,
+// -3.62e-9 inverse; phase errors -2.3e-7 and +3.8e-7 rad), so that a
+// transform and its inverse leave no net bias; the pi/4 family applies
+// 1/sqrt(2) as a two-float (hi + lo) scale.
+template <int DIR>
 __device__ __forceinline__ void c16f_pair(int m, float *c, float *s) {
-    constexpr float C1 = 0.92387962341308594f;    // ~cos(pi/8), modulus-matched
-    constexpr float S1 = 0.38268321752548218f;    // ~sin(pi/8), modulus-matched
+    // ~(cos, sin)(pi/8), modulus-matched, per direction
+    constexpr float C1 = DIR < 0 ? 0.92387962341308594f : 0.92387938499450684f;
+    constexpr float S1 = DIR < 0 ? 0.38268321752548218f : 0.38268378376960754f;
     switch (m & 15) {
         case 1: *c = C1; *s = S1; break;
         case 3: *c = S1; *s = C1; break;
@@ -125,7 +129,7 @@ __device__ __forceinline__ cx<T> rot16(cx<T> o, int m) {
             return mk(T(fmaf(re, H_HI, re * H_LO)), T(fmaf(im, H_HI, im * H_LO)));
         }
         float c, s;
-        c16f_pair(m, &c, &s);
+        c16f_pair<DIR>(m, &c, &s);
         s *= float(DIR);
         return mk(T(o.x * c - o.y * s), T(o.x * s + o.y * c));
     } else {
