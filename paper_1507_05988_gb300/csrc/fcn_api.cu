@@ -276,6 +276,7 @@ struct TableEntry {
     void *ptr;
     uint64_t dz;      // dz bits the table was built for (graphs keyed by dz)
     uint64_t stamp;   // last use
+    size_t bytes;     // allocation size
 };
 
 struct GraphKey {
@@ -369,31 +370,45 @@ int ensure_table(fcn_ctx *ctx, Pulse &pu, double dz, const cx<T> **out) {
         *out = (const cx<T> *)it->second.ptr;
         return FCN_OK;
     }
+    const size_t need = coef_offset<T>(pu.g.nr, pu.g.nt) + sizeof(CnCoef<T>) * pu.g.nr;
+    void *d = nullptr;
     const size_t cap = 2 * ctx->pulses.size() + 8;
     if (ctx->tables.size() >= cap) {
         auto old = ctx->tables.begin();
         for (auto t = ctx->tables.begin(); t != ctx->tables.end(); ++t)
             if (t->second.stamp < old->second.stamp) old = t;
-        CK(cudaStreamSynchronize(ctx->st), "sync before table eviction");
         const uint64_t odz = old->second.dz;
-        for (int kind = 0; kind < 4; ++kind) {
-            auto g = ctx->graphs.find(GraphKey{kind, odz});
-            if (g != ctx->graphs.end()) {
-                cudaGraphExecDestroy(g->second);
-                ctx->graphs.erase(g);
+        bool dropped = false;
+        for (int kind = 0; kind < 4; ++kind) dropped |= ctx->graphs.count(GraphKey{kind, odz}) > 0;
+        dropped |= ctx->batch_args.count(odz) > 0;
+        if (dropped) {
+            // graphs and argument arrays that refer to the table go with it
+            CK(cudaStreamSynchronize(ctx->st), "sync before table eviction");
+            for (int kind = 0; kind < 4; ++kind) {
+                auto g = ctx->graphs.find(GraphKey{kind, odz});
+                if (g != ctx->graphs.end()) {
+                    cudaGraphExecDestroy(g->second);
+                    ctx->graphs.erase(g);
+                }
+            }
+            auto ba = ctx->batch_args.find(odz);
+            if (ba != ctx->batch_args.end()) {
+                cudaFree(ba->second.first);
+                cudaFree(ba->second.second);
+                ctx->batch_args.erase(ba);
             }
         }
-        auto ba = ctx->batch_args.find(odz);
-        if (ba != ctx->batch_args.end()) {
-            cudaFree(ba->second.first);
-            cudaFree(ba->second.second);
-            ctx->batch_args.erase(ba);
+        if (old->second.bytes == need) {
+            // reused in stream order: the kernels that read the old table run
+            // on this stream before the ones that rebuild it (an adaptive run
+            // replaces tables at every new dz, so no allocation per attempt)
+            d = old->second.ptr;
+        } else {
+            cudaFree(old->second.ptr);
         }
-        cudaFree(old->second.ptr);
         ctx->tables.erase(old);
     }
-    void *d = nullptr;
-    CK(cudaMalloc(&d, coef_offset<T>(pu.g.nr, pu.g.nt) + sizeof(CnCoef<T>) * pu.g.nr), "pivot table allocation");
+    if (!d) CK(cudaMalloc(&d, need), "pivot table allocation");
     TableArgs ta;
     ta.nr = pu.g.nr;
     ta.nt = pu.g.nt;
@@ -404,7 +419,7 @@ int ensure_table(fcn_ctx *ctx, Pulse &pu, double dz, const cx<T> **out) {
     CK(launch_cn_table<T>(ta, (cx<T> *)d, ctx->st), "pivot table kernel");
     CK(launch_cn_coef<T>(ta, (CnCoef<T> *)((char *)d + coef_offset<T>(pu.g.nr, pu.g.nt)), ctx->st),
        "row coefficient kernel");
-    ctx->tables[key] = TableEntry{d, dz_key(dz), ++ctx->table_clock};
+    ctx->tables[key] = TableEntry{d, dz_key(dz), ++ctx->table_clock, need};
     *out = (const cx<T> *)d;
     return FCN_OK;
 }

@@ -1,6 +1,9 @@
 // mlp.cu -- the learned dz controller: a 6 -> 64 -> 64 -> 1 MLP (tanh hidden
-// layers, linear output) that proposes log(dz / L_ref) from features of the
-// current field.  Weights are used in BF16 (rounded from FP32 master weights)
+// layers, linear output) whose output y corrects the step-doubling law: the
+// proposal is log(dz / L_ref) = f4 - f5/3 + y, the step that would bring the
+// last attempt's error to rtol (Strang: local error O(dz^3)) times exp(y),
+// so an untrained (zero) network reproduces the law without its safety
+// factor and training learns how the error constant moves with the field.  Weights are used in BF16 (rounded from FP32 master weights)
 // with FP32 accumulation; training runs on the GPU with these kernels
 // (per-CTA gradient partials reduced in a fixed order, then Adam).  Not in
 // the paper, which uses a fixed dz; step doubling still judges every step.
@@ -147,7 +150,7 @@ __global__ void mlp_adam(float *W, float *m, float *v, const float *__restrict__
 
 // Features of the current field from the diagnostic reduction `red` (see
 // launch_reduce_stats) and the controller's scalars; with W non-null also
-// the MLP's proposal dz = L_ref exp(y), clamped to [lo, hi].
+// the MLP's proposal dz = L_ref exp(f4 - f5/3 + y), clamped to [lo, hi].
 __global__ void mlp_propose(const double *__restrict__ red, MlpScalars sc, const float *__restrict__ W,
                             float *features, double *dz_out) {
     __shared__ float sw[NP];
@@ -180,7 +183,7 @@ __global__ void mlp_propose(const double *__restrict__ red, MlpScalars sc, const
     load_weights(W, sw);
     const float y = forward_one(sw, sx, h1, h2, r);
     if (threadIdx.x == 0) {
-        double dz = sc.l_ref * exp((double)y);
+        double dz = sc.l_ref * exp((double)sx[4] - (double)sx[5] / 3.0 + (double)y);
         dz = fmin(fmax(dz, sc.dz_lo), sc.dz_hi);
         *dz_out = dz;
     }

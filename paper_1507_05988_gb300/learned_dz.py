@@ -1,0 +1,162 @@
+"""Trains the learned dz controller and compares it with plain step doubling.
+
+    python -m paper_1507_05988_gb300.learned_dz --seeds 1-8 --z-train 2,50,5 \
+        --z-test 1000 --json out.json
+
+1. Data: adaptive runs (plain step doubling, rtol 1e-4, FP32-mixed) of the
+   three seeded pulses of configs 1-3 (1 % amplitude noise, seeds as given),
+   config 1 to z_train[0] m, config 2 to z_train[1] m, config 3 to
+   z_train[2] m, every attempt logged (features of the state it started
+   from, its step and its step-doubling error).
+2. Labels: the network output y corrects the step-doubling law, dz =
+   L_ref exp(f4 - f5/3 + y); its target is log(safe step of the state) -
+   (f4 - f5/3), the safe step being h (rtol/err)^(1/3) (Strang: local error
+   O(dz^3)), limited to [0.2, 2] like the law.  Features are standardised for
+   training and the scaling is folded into the first layer afterwards.
+3. Training on the GPU (this library's forward and backward kernels, Adam).
+4. Margin: the output bias is lowered by m for m on a small grid, each
+   candidate run on held-out pulses (noise seed 100 of configs 1 and 2); the
+   one with the fewest substeps is kept.
+5. Test: the config-2 pulse (noise seed 0) over z_test m, plain step doubling
+   against the learned controller: accepted and rejected steps, substeps,
+   wall time, and the difference of their final fields.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+import numpy as np
+
+from . import fcn, workloads as W
+
+
+def _ranges(spec: str) -> list[int]:
+    out = []
+    for part in spec.split(","):
+        if "-" in part:
+            a, b = part.split("-")
+            out.extend(range(int(a), int(b) + 1))
+        elif part:
+            out.append(int(part))
+    return out
+
+
+def pulses(seed: int):
+    """The three pulse families of configs 1-3 with noise seed `seed`,
+    with their first proposals dz0."""
+    return [(W.config1().with_(noise_seed=seed), 1e-2),
+            (W.config2(seed=seed), 2e-3),
+            (W.config3().with_(noise_seed=seed), 1e-2)]
+
+
+def run(wl, z_end, dz0, controller=0, params=None, log=0, rtol=1e-4):
+    s = fcn.Solver(wl.physics(), precision=fcn.FCN_FP32_MIXED)
+    if params is not None:
+        s.mlp_set(params)
+    if log:
+        s.mlp_log(log)
+    s.set_field(wl.field())
+    t0 = time.perf_counter()
+    st = s.propagate(z_end, dz0, rtol=rtol, controller=controller, max_reject=40)
+    st["wall_s"] = time.perf_counter() - t0
+    rec = s.mlp_log_records() if log else None
+    A = s.get_field()
+    s.close()
+    return A, st, rec
+
+
+def labels(rec):
+    safe = rec[:, 6] - rec[:, 7] / 3.0
+    base = rec[:, 4] - rec[:, 5] / 3.0
+    return rec[:, :6].astype(np.float64), np.clip(safe - base, np.log(0.2), np.log(2.0))
+
+
+def train(x, y, epochs, lr, seed=0):
+    """Standardised training; returns FP32 master weights for raw features."""
+    mu, sd = x.mean(0), x.std(0)
+    sd[sd < 1e-6] = 1.0
+    xn = ((x - mu) / sd).astype(np.float32)
+    wl = W.small(8, 16)
+    s = fcn.Solver(wl.physics(), precision=fcn.FCN_FP32_MIXED)
+    loss = s.mlp_train(xn, y.astype(np.float32), epochs=epochs, batch=128, lr=lr, seed=seed)
+    p = s.mlp_get().astype(np.float64)
+    s.close()
+    nin, nh = fcn.FCN_MLP_NIN, fcn.FCN_MLP_NH
+    w1 = p[:nh * nin].reshape(nh, nin)
+    b1 = p[nh * nin:nh * nin + nh]
+    # W1 ((x - mu) / sd) + b1 = (W1 / sd) x + (b1 - W1 (mu / sd))
+    p[nh * nin:nh * nin + nh] = b1 - w1 @ (mu / sd)
+    p[:nh * nin] = (w1 / sd[None, :]).reshape(-1)
+    return p.astype(np.float32), float(loss)
+
+
+def with_margin(params, m):
+    q = params.copy()
+    q[-1] -= m           # output bias b3
+    return q
+
+
+def main(argv=None) -> int:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--seeds", default="1-8")
+    ap.add_argument("--z-train", default="2,50,5", help="config 1, 2, 3 training distances [m]")
+    ap.add_argument("--z-val", default="2,20")
+    ap.add_argument("--z-test", type=float, default=1000.0)
+    ap.add_argument("--epochs", type=int, default=300)
+    ap.add_argument("--lr", type=float, default=2e-3)
+    ap.add_argument("--margins", default="0,0.05,0.1,0.15,0.2")
+    ap.add_argument("--json", default="")
+    a = ap.parse_args(argv)
+    zt = [float(v) for v in a.z_train.split(",")]
+    zv = [float(v) for v in a.z_val.split(",")]
+    out = {"seeds": a.seeds, "z_train_m": zt, "z_val_m": zv, "z_test_m": a.z_test}
+
+    recs, t0 = [], time.perf_counter()
+    for seed in _ranges(a.seeds):
+        for (wl, dz0), z in zip(pulses(seed), zt):
+            if z > 0:
+                _, _, r = run(wl, z, dz0, log=200000)
+                recs.append(r)
+    rec = np.concatenate(recs)
+    x, y = labels(rec)
+    out["records"] = int(len(y))
+    out["data_s"] = time.perf_counter() - t0
+    params, loss = train(x, y, a.epochs, a.lr)
+    out["train_mse"] = loss
+    out["label_var"] = float(np.var(y))
+    print(f"learned_dz: {len(y)} records, label var {np.var(y):.4g}, training mse {loss:.4g}", flush=True)
+
+    val = [(wl, dz0, z) for (wl, dz0), z in zip(pulses(100)[:2], zv)]
+    scores = {}
+    for m in [float(v) for v in a.margins.split(",")]:
+        tot = 0
+        for wl, dz0, z in val:
+            _, st, _ = run(wl, z, dz0, controller=1, params=with_margin(params, m))
+            tot += st["substeps"]
+        scores[m] = tot
+    plain_val = sum(run(wl, z, dz0)[1]["substeps"] for wl, dz0, z in val)
+    m_best = min(scores, key=scores.get)
+    out["validation_substeps"] = {"plain": plain_val, "learned_by_margin": scores, "margin": m_best}
+    print(f"learned_dz: validation substeps plain {plain_val}, learned {scores}", flush=True)
+
+    wl = W.config5(seed=0)
+    A0, s0, _ = run(wl, a.z_test, 2e-3)
+    A1, s1, _ = run(wl, a.z_test, 2e-3, controller=1, params=with_margin(params, m_best))
+    diff = float(np.linalg.norm(A1 - A0) / np.linalg.norm(A0))
+    keys = ("accepted", "rejected", "substeps", "mlp_proposals", "wall_s")
+    out["test"] = {"workload": f"config-5 pulse (config-2 grid 1024x4096, noise seed 0), "
+                               f"0 -> {a.z_test} m, rtol 1e-4, FP32-mixed",
+                   "plain": {k: s0[k] for k in keys if k != "mlp_proposals"},
+                   "learned": {k: s1[k] for k in keys},
+                   "final_field_rel_l2_learned_vs_plain": diff}
+    print(json.dumps(out["test"]), flush=True)
+    if a.json:
+        with open(a.json, "w") as f:
+            json.dump(out, f, indent=1)
+    return 0
+
+
+if __name__ == "__main__":
+    raise SystemExit(main())

@@ -54,13 +54,16 @@ def test_mlp_training_fits_a_smooth_function(fcn):
     assert l1 < 0.05 * l0 and l1 < 5e-3
 
 
-def training_set(rec):
-    """Features and labels from logged attempts: the step the controller can
-    take next, i.e. the safe step h (rtol/err)^(1/3) (Strang: O(dz^3) local
-    error) limited to [0.2, 2] h like the step-doubling formula, with a 0.95
-    margin; as log(dz / L_ref)."""
-    growth = np.clip(-rec[:, 7] / 3.0, np.log(0.2), np.log(2.0))
-    return rec[:, :6], rec[:, 6] + growth + np.log(0.95)
+def training_set(rec, margin=0.95):
+    """Features and labels from logged attempts.  The safe step of the state
+    an attempt started from is h (rtol/err)^(1/3) (Strang: O(dz^3) local
+    error); the controller proposes exp(f4 - f5/3 + y) L_ref (the law applied
+    to the previous accepted attempt) so the label of y is log(safe step) -
+    (f4 - f5/3), with a margin, limited to the [0.2, 2] range of the law."""
+    safe = rec[:, 6] - rec[:, 7] / 3.0
+    base = rec[:, 4] - rec[:, 5] / 3.0
+    y = np.clip(safe - base + np.log(margin), np.log(0.2), np.log(2.0))
+    return rec[:, :6], y
 
 
 def _adaptive(fcn, wl, prec, z_end, dz0, rtol, controller, params=None, log=0):
