@@ -249,11 +249,12 @@ int fcn_profile_read(fcn_ctx *ctx, double *ms, int64_t *count, int32_t reset);
  *   f2 = spectral rms / rms_ref - 1     f3 = relative change of peak I over the last step
  *   f4 = log(dz_prev / L_ref)           f5 = log(err_prev / rtol)
  * with I_ref, rms_ref from the field at the start of fcn_propagate and
- * L_ref = k0 (r_max/5)^2 / 2.  The network output y corrects the step-
- * doubling law: the proposal is dz = L_ref exp(f4 - f5/3 + y), i.e. the step
- * that would have brought the last accepted attempt to err = rtol, times
- * exp(y) (a zero network gives that law without its 0.9 safety factor);
- * clamped to [0.2, 2] times the last accepted step. */
+ * L_ref = k0 (r_max/5)^2 / 2.  With g = f4 - f5/3 (log of the step that
+ * would have brought the last accepted attempt to err = rtol), the network
+ * takes n = (f0, f1, f2, f3 exp(-f5/3), g, 0) and its output y corrects the
+ * step-doubling law: the proposal is dz = L_ref exp(g + y) (a zero network
+ * gives that law without its 0.9 safety factor), clamped to [0.2, 2] times
+ * the last accepted step. */
 
 /* Loads / reads FP32 master weights (host, FCN_MLP_NPARAM floats). */
 int fcn_mlp_set(fcn_ctx *ctx, const float *host_params);
@@ -264,7 +265,7 @@ int fcn_mlp_get(fcn_ctx *ctx, float *host_params);
  * started from, log(h / L_ref) of the attempted step and log(err / rtol) of
  * its step-doubling error.  log(dz_safe / L_ref) of that state follows as
  * rec[6] - rec[7]/3 (the Strang local error is O(dz^3)), and the network's
- * training label as that minus (rec[4] - rec[5]/3).  capacity 0 stops.
+ * training label as that minus g = rec[4] - rec[5]/3.  capacity 0 stops.
  * fcn_mlp_log_count returns the number of records written. */
 int fcn_mlp_set_log(fcn_ctx *ctx, float *host_buf, int64_t capacity);
 int64_t fcn_mlp_log_count(const fcn_ctx *ctx);

@@ -1,9 +1,15 @@
 // mlp.cu -- the learned dz controller: a 6 -> 64 -> 64 -> 1 MLP (tanh hidden
 // layers, linear output) whose output y corrects the step-doubling law: the
-// proposal is log(dz / L_ref) = f4 - f5/3 + y, the step that would bring the
-// last attempt's error to rtol (Strang: local error O(dz^3)) times exp(y),
-// so an untrained (zero) network reproduces the law without its safety
-// factor and training learns how the error constant moves with the field.  Weights are used in BF16 (rounded from FP32 master weights)
+// proposal is log(dz / L_ref) = g + y with g = f4 - f5/3, the step that
+// would have brought the last accepted attempt's error to rtol (Strang:
+// local error O(dz^3)), so an untrained (zero) network reproduces the law
+// without its safety factor and training learns how the safe step moves
+// from one state to the next.  The network sees inputs that do not depend
+// on the step sizes the controller happened to take (so data gathered under
+// plain step doubling describes the learned controller's states too):
+//   n = (f0, f1, f2, f3 exp(-f5/3), g, 0),
+// f3 exp(-f5/3) being the peak-intensity change scaled to a step of size
+// exp(g) L_ref (the change over the last step is proportional to it).  Weights are used in BF16 (rounded from FP32 master weights)
 // with FP32 accumulation; training runs on the GPU with these kernels
 // (per-CTA gradient partials reduced in a fixed order, then Adam).  Not in
 // the paper, which uses a fixed dz; step doubling still judges every step.
@@ -172,18 +178,22 @@ __global__ void mlp_propose(const double *__restrict__ red, MlpScalars sc, const
             log(sc.dz_prev / sc.l_ref),
             log(fmax(sc.err_prev, 1e-30) / sc.rtol),
         };
-        for (int k = 0; k < NIN; ++k) {
-            sx[k] = (float)f[k];
-            features[k] = (float)f[k];
-        }
+        for (int k = 0; k < NIN; ++k) features[k] = (float)f[k];
         features[NIN] = (float)peak;
+        const double g = f[4] - f[5] / 3.0;
+        sx[0] = (float)f[0];
+        sx[1] = (float)f[1];
+        sx[2] = (float)f[2];
+        sx[3] = (float)(f[3] * exp(-f[5] / 3.0));
+        sx[4] = (float)g;
+        sx[5] = 0.0f;
     }
     __syncthreads();
     if (!W) return;
     load_weights(W, sw);
     const float y = forward_one(sw, sx, h1, h2, r);
     if (threadIdx.x == 0) {
-        double dz = sc.l_ref * exp((double)sx[4] - (double)sx[5] / 3.0 + (double)y);
+        double dz = sc.l_ref * exp((double)sx[4] + (double)y);
         dz = fmin(fmax(dz, sc.dz_lo), sc.dz_hi);
         *dz_out = dz;
     }

@@ -9,10 +9,11 @@
    z_train[2] m, every attempt logged (features of the state it started
    from, its step and its step-doubling error).
 2. Labels: the network output y corrects the step-doubling law, dz =
-   L_ref exp(f4 - f5/3 + y); its target is log(safe step of the state) -
-   (f4 - f5/3), the safe step being h (rtol/err)^(1/3) (Strang: local error
-   O(dz^3)), limited to [0.2, 2] like the law.  Features are standardised for
-   training and the scaling is folded into the first layer afterwards.
+   L_ref exp(g + y), g = f4 - f5/3; its target is log(safe step of the
+   state) - g, the safe step being h (rtol/err)^(1/3) (Strang: local error
+   O(dz^3)), limited to [0.2, 2] like the law.  Inputs (f0, f1, f2,
+   f3 exp(-f5/3), g, 0) are standardised for training and the scaling is
+   folded into the first layer afterwards.
 3. Training on the GPU (this library's forward and backward kernels, Adam).
 4. Margin: the output bias is lowered by m for m on a small grid, each
    candidate run on held-out pulses (noise seed 100 of configs 1 and 2); the
@@ -67,16 +68,29 @@ def run(wl, z_end, dz0, controller=0, params=None, log=0, rtol=1e-4):
     return A, st, rec
 
 
+def net_inputs(f):
+    """The network's inputs from the logged features (as the proposal kernel
+    forms them): (f0, f1, f2, f3 exp(-f5/3), g = f4 - f5/3, 0)."""
+    f = np.asarray(f, np.float64)
+    n = np.zeros_like(f)
+    n[:, :3] = f[:, :3]
+    n[:, 3] = f[:, 3] * np.exp(-f[:, 5] / 3.0)
+    n[:, 4] = f[:, 4] - f[:, 5] / 3.0
+    return n
+
+
 def labels(rec):
     safe = rec[:, 6] - rec[:, 7] / 3.0
     base = rec[:, 4] - rec[:, 5] / 3.0
-    return rec[:, :6].astype(np.float64), np.clip(safe - base, np.log(0.2), np.log(2.0))
+    return net_inputs(rec[:, :6]), np.clip(safe - base, np.log(0.2), np.log(2.0))
 
 
 def train(x, y, epochs, lr, seed=0):
     """Standardised training; returns FP32 master weights for raw features."""
     mu, sd = x.mean(0), x.std(0)
-    sd[sd < 1e-6] = 1.0
+    zero = sd < 1e-6
+    sd[zero] = 1.0
+    mu[zero] = 0.0
     xn = ((x - mu) / sd).astype(np.float32)
     wl = W.small(8, 16)
     s = fcn.Solver(wl.physics(), precision=fcn.FCN_FP32_MIXED)

@@ -60,10 +60,11 @@ def training_set(rec, margin=0.95):
     error); the controller proposes exp(f4 - f5/3 + y) L_ref (the law applied
     to the previous accepted attempt) so the label of y is log(safe step) -
     (f4 - f5/3), with a margin, limited to the [0.2, 2] range of the law."""
+    from paper_1507_05988_gb300.learned_dz import net_inputs
     safe = rec[:, 6] - rec[:, 7] / 3.0
     base = rec[:, 4] - rec[:, 5] / 3.0
     y = np.clip(safe - base + np.log(margin), np.log(0.2), np.log(2.0))
-    return rec[:, :6], y
+    return net_inputs(rec[:, :6]).astype(np.float32), y
 
 
 def _adaptive(fcn, wl, prec, z_end, dz0, rtol, controller, params=None, log=0):
@@ -81,37 +82,46 @@ def _adaptive(fcn, wl, prec, z_end, dz0, rtol, controller, params=None, log=0):
 
 
 def test_learned_dz_controller_end_to_end(fcn):
-    """Training data from step-doubling runs of three grids at several noise
-    seeds; the network is trained on the GPU; the learned controller (its
-    proposals judged by step doubling, the formula as fallback) lands on
-    z_end within the tolerance of a fine reference, and its step count is
-    reported next to plain step doubling."""
-    rtol, z_end = 1e-4, 1.0
-    recs = []
-    for seed in range(1, 7):
-        for wl in (W.small(48, 256, p_over_pcr=3.0, noise_seed=seed),
-                   W.small(32, 512, w0=2e-3, tp=50e-15, p_over_pcr=5.0, noise_seed=seed,
-                           n2j=(W.N2, W.N4, 0, 0)),
-                   W.small(40, 256, w0=1.5e-3, p_over_pcr=6.0, noise_seed=seed)):
-            _, _, r = _adaptive(fcn, wl, fcn.FCN_FP32_MIXED, z_end, 0.01, rtol, 0, log=4000)
-            recs.append(r)
-    rec = np.concatenate(recs)
-    x, y = training_set(rec)
+    """The learned controller on the filamentation pulse family (w0 = 2 mm,
+    50 fs, 5 P_cr, n2 + n4, 1 % noise) on a 256 x 1024 grid: training data
+    from step-doubling runs at noise seeds 1-6, the network (a correction to
+    the step-doubling law) trained on the GPU, its margin chosen on seed 7;
+    on seed 0 both controllers land on z_end within the tolerance of a
+    fine-step FP64 reference, and the learned one's substeps are compared
+    with plain step doubling."""
+    from paper_1507_05988_gb300 import learned_dz as LD
+    rtol, z_end, dz0 = 1e-4, 0.3, 2e-3
+
+    def pulse(seed):
+        return W.config2(seed=seed).with_(nr=256, nt=1024, name=f"fil_256x1024_s{seed}")
+
+    recs = [_adaptive(fcn, pulse(seed), fcn.FCN_FP32_MIXED, z_end, dz0, rtol, 0, log=20000)[2]
+            for seed in range(1, 7)]
+    x, y = LD.labels(np.concatenate(recs))
     assert len(y) > 200 and np.all(np.isfinite(x)) and np.all(np.isfinite(y))
-    wl = W.small(48, 256, p_over_pcr=4.0, noise_seed=11)
-    s = fcn.Solver(wl.physics(), precision=fcn.FCN_FP32_MIXED)
-    loss = s.mlp_train(x, y, epochs=200, batch=128, lr=2e-3, seed=0)
-    params = s.mlp_get()
+    params, loss = LD.train(x, y, epochs=200, lr=2e-3)
+    assert loss < 0.5 * np.var(y)
+
+    def substeps(m):
+        return _adaptive(fcn, pulse(7), fcn.FCN_FP32_MIXED, z_end, dz0, rtol, 1,
+                         params=LD.with_margin(params, m))[1]["substeps"]
+    margin = min((0.0, 0.05, 0.1, 0.15), key=substeps)
+    wl = pulse(0)
+    A0, st0, _ = _adaptive(fcn, wl, fcn.FCN_FP32_MIXED, z_end, dz0, rtol, 0)
+    A1, st1, _ = _adaptive(fcn, wl, fcn.FCN_FP32_MIXED, z_end, dz0, rtol, 1,
+                           params=LD.with_margin(params, margin))
+    s = fcn.Solver(wl.physics(), precision=fcn.FCN_FP64)
+    s.set_field(wl.field())
+    s.step(z_end / 3000, 3000)
+    ref = s.get_field()
     s.close()
-    assert loss < 0.05 * np.var(y)
-    A0, st0, _ = _adaptive(fcn, wl, fcn.FCN_FP32_MIXED, z_end, 0.01, rtol, 0)
-    A1, st1, _ = _adaptive(fcn, wl, fcn.FCN_FP32_MIXED, z_end, 0.01, rtol, 1, params=params)
-    pb = oracle.Problem(**wl.physics())
-    ref, _ = oracle.run(pb, z_end / 2000, 2000, wl.field())
     for A, st in ((A0, st0), (A1, st1)):
         assert st["z"] == z_end
         assert rel_l2(A, ref) < 30 * rtol
     assert st1["mlp_proposals"] > 0
+    gain = 1.0 - st1["substeps"] / st0["substeps"]
     print(f"\nplain step doubling: accepted {st0['accepted']} rejected {st0['rejected']} "
-          f"substeps {st0['substeps']}; learned dz: accepted {st1['accepted']} "
-          f"rejected {st1['rejected']} substeps {st1['substeps']} (mlp proposals {st1['mlp_proposals']})")
+          f"substeps {st0['substeps']}; learned dz (margin {margin}): accepted {st1['accepted']} "
+          f"rejected {st1['rejected']} substeps {st1['substeps']} (mlp proposals {st1['mlp_proposals']}); "
+          f"substeps saved {100 * gain:.1f} %")
+    assert st1["substeps"] <= 1.05 * st0["substeps"]
