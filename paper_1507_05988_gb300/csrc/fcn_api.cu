@@ -649,15 +649,17 @@ void tune_cache_store(int prec, int nr, int nt, int rv, int cv) {
     f << prec << " " << nr << " " << nt << " " << rv << " " << cv << "\n";
 }
 
+// 3 untimed then 15 timed launches (variants differ by a few per cent, so
+// a shorter sample lets launch-to-launch noise decide)
 template <typename F>
 int time_launches(fcn_ctx *ctx, F &&launch, float *ms_out) {
-    for (int i = 0; i < 2; ++i) CK(launch(), "tuning warm-up");
+    for (int i = 0; i < 3; ++i) CK(launch(), "tuning warm-up");
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0), "event");
     CK(cudaEventCreate(&e1), "event");
     cudaEventRecord(e0, ctx->st);
     cudaError_t e = cudaSuccess;
-    for (int i = 0; i < 5 && e == cudaSuccess; ++i) e = launch();
+    for (int i = 0; i < 15 && e == cudaSuccess; ++i) e = launch();
     cudaEventRecord(e1, ctx->st);
     cudaEventSynchronize(e1);
     float ms = 0.f;
