@@ -215,6 +215,16 @@ int fcn_set_variants(fcn_ctx *ctx, int32_t row_variant, int32_t col_variant);
  * captured graphs.  FCN_ERR_UNSUPPORTED if mode 1 is not possible. */
 int fcn_set_batching(fcn_ctx *ctx, int32_t mode);
 
+/* Paired column launches for FP32 contexts whose pulses all share one grid
+ * (and so, for one dz, one pivot table): the column stage of pulses 2i and
+ * 2i+1 runs as one launch that reads each pivot, coefficient row and sweep
+ * factor once for both (Eqs. (matrix), (matrix1) are the same for both).
+ * mode 1 on, 0 off, -1 (default) decided on the first step by timing one
+ * paired launch against two single ones.  Drops the captured graphs.
+ * fcn_get_pairing returns the decision: 1, 0, or -1 before the first step. */
+int fcn_set_pairing(fcn_ctx *ctx, int32_t mode);
+int fcn_get_pairing(const fcn_ctx *ctx);
+
 /* Variants in use for pulse `pulse` (out[0] row, out[1] column; -1 before
  * the first step). */
 int fcn_get_variants(fcn_ctx *ctx, int32_t pulse, int32_t out[2]);

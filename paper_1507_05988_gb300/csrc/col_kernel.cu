@@ -672,6 +672,226 @@ cudaError_t launch_cn_l(const ColArgs<T> &a, int target, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Paired variant: one CTA solves the same column group of two pulses that
+// share the grid and the pivot table (a batch of equal pulses).  The pivots,
+// alpha_j, gamma_j, the row coefficients and the A part of every chunk map
+// are the same for both; each thread runs the two pulses' recurrences side by
+// side (two independent dependency chains).  Register-fed, chunks of L rows.
+// ---------------------------------------------------------------------------
+
+// chunk_scan for NP right-hand sides sharing one A: returns the value entering
+// this thread's chunk for each of them.  smB, smC hold NP * nwarp * C values.
+template <typename T, bool REV, int NP>
+__device__ __forceinline__ void chunk_scan_n(cx<T> A, cx<T> (&B)[NP], int C, int col, cx<T> *smA,
+                                             cx<T> *smB, cx<T> *smC, cx<T> (&out)[NP]) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int cpw = 32 / C;
+    const int ciw = lane / C;
+    for (int d = 1; d < cpw; d <<= 1) {
+        const cx<T> Ao = REV ? shfl_down_cx(A, d * C) : shfl_up_cx(A, d * C);
+        cx<T> Bo[NP];
+#pragma unroll
+        for (int i = 0; i < NP; ++i) Bo[i] = REV ? shfl_down_cx(B[i], d * C) : shfl_up_cx(B[i], d * C);
+        const bool take = REV ? (ciw + d < cpw) : (ciw >= d);
+        if (take) {
+#pragma unroll
+            for (int i = 0; i < NP; ++i) B[i] = cmul(A, Bo[i]) + B[i];
+            A = cmul(A, Ao);
+        }
+    }
+    cx<T> Ae = REV ? shfl_down_cx(A, C) : shfl_up_cx(A, C);
+    cx<T> Be[NP];
+#pragma unroll
+    for (int i = 0; i < NP; ++i) Be[i] = REV ? shfl_down_cx(B[i], C) : shfl_up_cx(B[i], C);
+    if (REV ? (ciw == cpw - 1) : (ciw == 0)) {
+        Ae = mk(T(1), T(0));
+#pragma unroll
+        for (int i = 0; i < NP; ++i) Be[i] = czero<T>();
+    }
+    const int nw = blockDim.x >> 5;
+    const int nwc = nw * C;
+#pragma unroll
+    for (int i = 0; i < NP; ++i) out[i] = Be[i];
+    if (nw > 1) {
+        if (REV ? (ciw == 0) : (ciw == cpw - 1)) {
+            smA[FCN_IDX(w * C + col, nwc, 54)] = A;
+#pragma unroll
+            for (int i = 0; i < NP; ++i) smB[FCN_IDX(i * nwc + w * C + col, NP * nwc, 55)] = B[i];
+        }
+        __syncthreads();
+        if ((int)threadIdx.x < C) {
+            const int c0 = threadIdx.x;
+            cx<T> c[NP];
+#pragma unroll
+            for (int i = 0; i < NP; ++i) c[i] = czero<T>();
+            for (int kk = 0; kk < nw; ++kk) {
+                const int k = REV ? nw - 1 - kk : kk;
+                const cx<T> Ak = smA[FCN_IDX(k * C + c0, nwc, 56)];
+#pragma unroll
+                for (int i = 0; i < NP; ++i) {
+                    smC[FCN_IDX(i * nwc + k * C + c0, NP * nwc, 57)] = c[i];
+                    c[i] = cmul(Ak, c[i]) + smB[FCN_IDX(i * nwc + k * C + c0, NP * nwc, 58)];
+                }
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < NP; ++i)
+            out[i] = cmul(Ae, smC[FCN_IDX(i * nwc + w * C + col, NP * nwc, 59)]) + Be[i];
+    }
+}
+
+template <typename T, int L, bool EDGE, int NTC>
+__device__ __forceinline__ void cn_f1_pair(const ColArgs<T> &a, const cx<T> *f2, int q, int qq, int j0,
+                                           T delta, cx<T> *At, cx<T> *Gt, int BD, cx<T> (&y1)[L],
+                                           cx<T> (&y2)[L], cx<T> &PA, cx<T> &PB1, cx<T> &PB2) {
+    const int nt = NTC ? NTC : a.nt, nr = a.nr, nq = nt / 2 + 1;
+    const cx<T> *fx = a.field + q;
+    const cx<T> *fy = f2 + q;
+    const cx<T> *fi = a.invden + qq;
+    auto X = [&](const cx<T> *f, int j) -> cx<T> {
+        if (EDGE && (j < 0 || j >= nr)) return czero<T>();
+        return ldg_cx(f + FCN_IDX((size_t)j * nt, (size_t)nr * nt, 60));
+    };
+    cx<T> xm1 = X(fx, j0 - 1), x01 = X(fx, j0);
+    cx<T> xm2 = X(fy, j0 - 1), x02 = X(fy, j0);
+#pragma unroll
+    for (int k = 0; k < L; ++k) {
+        const int j = j0 + k;
+        const cx<T> xp1 = X(fx, j + 1), xp2 = X(fy, j + 1);
+        cx<T> inv = czero<T>();
+        if (!EDGE || j < nr) inv = ldg_cx(fi + FCN_IDX((size_t)j * nq, (size_t)nr * nq, 61));
+        CnCoef<T> cf;
+        if (!EDGE || j < nr - 1) {
+            cf = a.coef[FCN_IDX(j, nr, 62)];
+        } else {
+            cf.sl = T(0); cf.sh = T(0); cf.c0 = T(0); cf.d = T(0);
+        }
+        const T cd = cf.d * (cf.c0 - delta);
+        const cx<T> al = cmul_i(inv, cf.sl);
+        At[k * BD] = al;
+        Gt[k * BD] = cmul_i(inv, cf.sh);
+        {
+            const T wx = cf.sl * xm1.x + cf.sh * xp1.x - cd * x01.x;
+            const T wy = cf.sl * xm1.y + cf.sh * xp1.y - cd * x01.y;
+            const cx<T> beta = cmul(mk(cf.d * x01.x - wy, cf.d * x01.y + wx), inv);
+            PB1 = cmul(al, PB1) + beta;
+            y1[k] = beta;
+        }
+        {
+            const T wx = cf.sl * xm2.x + cf.sh * xp2.x - cd * x02.x;
+            const T wy = cf.sl * xm2.y + cf.sh * xp2.y - cd * x02.y;
+            const cx<T> beta = cmul(mk(cf.d * x02.x - wy, cf.d * x02.y + wx), inv);
+            PB2 = cmul(al, PB2) + beta;
+            y2[k] = beta;
+        }
+        PA = cmul(al, PA);
+        xm1 = x01; x01 = xp1;
+        xm2 = x02; x02 = xp2;
+    }
+}
+
+template <typename T, int L, int NTC>
+__device__ __forceinline__ void cn_pair_body(const ColArgs<T> &a, cx<T> *field2, int C, int g,
+                                             unsigned char *smem_raw) {
+    const int BD = blockDim.x;
+    const int tid = threadIdx.x;
+    const int nwarp = BD >> 5;
+    cx<T> *smA = reinterpret_cast<cx<T> *>(smem_raw);
+    cx<T> *smB = smA + nwarp * C;
+    cx<T> *smC = smB + 2 * nwarp * C;
+    cx<T> *At = smC + 2 * nwarp * C + tid;     // alpha slot k: At[k * BD]
+    cx<T> *Gt = At + L * BD;                   // gamma slot k: Gt[k * BD]
+
+    const int col = tid % C;
+    const int chunk = tid / C;
+    const int q = g * C + col;
+    const int nt = NTC ? NTC : a.nt, nr = a.nr;
+    const int qq = (q <= nt / 2) ? q : nt - q;
+    const T delta = a.dk * T(qq) * T(qq);
+    const int j0 = chunk * L;
+
+    cx<T> y1[L], y2[L];
+    cx<T> PA = mk(T(1), T(0)), PB[2] = {czero<T>(), czero<T>()};
+    if (j0 >= 1 && j0 + L < nr)
+        cn_f1_pair<T, L, false, NTC>(a, field2, q, qq, j0, delta, At, Gt, BD, y1, y2, PA, PB[0], PB[1]);
+    else
+        cn_f1_pair<T, L, true, NTC>(a, field2, q, qq, j0, delta, At, Gt, BD, y1, y2, PA, PB[0], PB[1]);
+    {
+        cx<T> yp[2];
+        chunk_scan_n<T, false, 2>(PA, PB, C, col, smA, smB, smC, yp);
+#pragma unroll
+        for (int k = 0; k < L; ++k) {
+            const cx<T> al = At[k * BD];
+            y1[k] = cmul(al, yp[0]) + y1[k];
+            y2[k] = cmul(al, yp[1]) + y2[k];
+            yp[0] = y1[k];
+            yp[1] = y2[k];
+            asm volatile("" ::: "memory");
+        }
+    }
+    cx<T> QA = mk(T(1), T(0)), QB[2] = {czero<T>(), czero<T>()};
+#pragma unroll
+    for (int k = L - 1; k >= 0; --k) {
+        const cx<T> ga = Gt[k * BD];
+        QB[0] = cmul(ga, QB[0]) + y1[k];
+        QB[1] = cmul(ga, QB[1]) + y2[k];
+        QA = cmul(ga, QA);
+        asm volatile("" ::: "memory");
+    }
+    cx<T> xn[2];
+    chunk_scan_n<T, true, 2>(QA, QB, C, col, smA, smB, smC, xn);
+    cx<T> *fo1 = a.field + (size_t)j0 * nt + q;
+    cx<T> *fo2 = field2 + (size_t)j0 * nt + q;
+#pragma unroll
+    for (int k = L - 1; k >= 0; --k) {
+        const int j = j0 + k;
+        const cx<T> ga = Gt[k * BD];
+        xn[0] = cmul(ga, xn[0]) + y1[k];
+        xn[1] = cmul(ga, xn[1]) + y2[k];
+        if (j < nr) {
+            fo1[FCN_IDX((size_t)k * nt, (size_t)(nr - j0) * nt, 63)] = xn[0];
+            fo2[FCN_IDX((size_t)k * nt, (size_t)(nr - j0) * nt, 64)] = xn[1];
+        }
+        asm volatile("" ::: "memory");
+    }
+}
+
+template <typename T, int L, int NTC>
+__global__ void __launch_bounds__(512, 2)
+cn_pair_kernel(ColArgs<T> a, cx<T> *field2, int C) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int ngroups = a.nt / C;
+    const int b = blockIdx.x;
+    const int g = (b & 1) ? (ngroups - 1 - (b >> 1)) : (b >> 1);
+    cn_pair_body<T, L, NTC>(a, field2, C, g, smem_raw);
+}
+
+template <typename T, int L, int NTC>
+cudaError_t launch_cn_pair_l(const ColArgs<T> &a, cx<T> *field2, cudaStream_t st) {
+    if (!a.coef) return cudaErrorInvalidConfiguration;
+    constexpr int CMIN = 32 / int(sizeof(cx<T>));
+    constexpr int TMAX = 512;
+    const int P = (a.nr + L - 1) / L;
+    int C = CMIN;
+    while (C > 1 && C * P > TMAX) C /= 2;
+    while (C * 2 * P <= TMAX / 2 && C * 2 <= 32) C *= 2;
+    if (C > a.nt) C = a.nt;
+    const int threads = ((C * P + 31) / 32) * 32;
+    if (threads > TMAX) return cudaErrorInvalidConfiguration;
+    const size_t smem = sizeof(cx<T>) * (5 * (size_t)(threads / 32) * C + 2 * (size_t)L * threads);
+    if (smem > kCnStagedSmemMax) return cudaErrorInvalidConfiguration;
+    cn_pair_kernel<T, L, NTC><<<a.nt / C, threads, smem, st>>>(a, field2, C);
+    return cudaGetLastError();
+}
+
+template <typename T, int L, int NTC>
+cudaError_t set_pair_attr() {
+    return cudaFuncSetAttribute(cn_pair_kernel<T, L, NTC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)kCnStagedSmemMax);
+}
+
 // Register-fed variant with Nt as a compile-time constant for the grids of
 // 512 .. 8192 points in FP32 (every row offset an immediate), generic otherwise.
 template <typename T, int L>
@@ -722,6 +942,22 @@ cudaError_t launch_cn(const ColArgs<T> &a, cudaStream_t st) {
 }
 
 template <typename T>
+cudaError_t launch_cn_pair(const ColArgs<T> &a, cx<T> *field2, cudaStream_t st) {
+    constexpr int L = 8;
+    if constexpr (sizeof(T) == 4) {
+        switch (a.nt) {
+            case 512: return launch_cn_pair_l<T, L, 512>(a, field2, st);
+            case 1024: return launch_cn_pair_l<T, L, 1024>(a, field2, st);
+            case 2048: return launch_cn_pair_l<T, L, 2048>(a, field2, st);
+            case 4096: return launch_cn_pair_l<T, L, 4096>(a, field2, st);
+            case 8192: return launch_cn_pair_l<T, L, 8192>(a, field2, st);
+            default: break;
+        }
+    }
+    return launch_cn_pair_l<T, L, 0>(a, field2, st);
+}
+
+template <typename T>
 cudaError_t launch_cn_coef(const TableArgs &a, CnCoef<T> *coef, cudaStream_t st) {
     cn_coef_kernel<T><<<(a.nr + 127) / 128, 128, 0, st>>>(a, coef);
     return cudaGetLastError();
@@ -734,7 +970,13 @@ cudaError_t prepare_cn() {
     if (e == cudaSuccess) e = set_staged_attr<T, LS, false, 0>();
     if (e == cudaSuccess) e = set_staged_attr<T, LL, true, 0>();
     if (e == cudaSuccess) e = set_staged_attr<T, LS, true, 0>();
+    if (e == cudaSuccess) e = set_pair_attr<T, 8, 0>();
     if constexpr (sizeof(T) == 4) {
+        if (e == cudaSuccess) e = set_pair_attr<T, 8, 512>();
+        if (e == cudaSuccess) e = set_pair_attr<T, 8, 1024>();
+        if (e == cudaSuccess) e = set_pair_attr<T, 8, 2048>();
+        if (e == cudaSuccess) e = set_pair_attr<T, 8, 4096>();
+        if (e == cudaSuccess) e = set_pair_attr<T, 8, 8192>();
         if (e == cudaSuccess) e = set_staged_attr<T, LL, true, 512>();
         if (e == cudaSuccess) e = set_staged_attr<T, LS, true, 512>();
         if (e == cudaSuccess) e = set_staged_attr<T, LL, true, 1024>();
@@ -777,6 +1019,8 @@ template cudaError_t launch_cn_table<float>(const TableArgs &, cx<float> *, cuda
 template cudaError_t launch_cn_coef<float>(const TableArgs &, CnCoef<float> *, cudaStream_t);
 template cudaError_t launch_cn_coef<double>(const TableArgs &, CnCoef<double> *, cudaStream_t);
 template cudaError_t prepare_cn<float>();
+template cudaError_t launch_cn_pair<float>(const ColArgs<float> &, cx<float> *, cudaStream_t);
+template cudaError_t launch_cn_pair<double>(const ColArgs<double> &, cx<double> *, cudaStream_t);
 template cudaError_t prepare_cn<double>();
 template cudaError_t launch_cn_table<double>(const TableArgs &, cx<double> *, cudaStream_t);
 

@@ -306,6 +306,9 @@ struct fcn_ctx {
     float *log_buf = nullptr;         // caller-owned host log of adaptive attempts
     int64_t log_cap = 0, log_n = 0;
     int force_row = -1, force_col = -1;   // -1: autotune; else forced variant
+    // paired column launches for pulses sharing a grid and table (FP32):
+    // mode -1 decides by timing, 0 off, 1 on; pairs is the decision (-1 open)
+    int pair_mode = -1, pairs = -1;
     // batched work lists (FP32, K = 8, several pulses): one launch per stage
     bool batched = false;
     int2 *row_items = nullptr;
@@ -561,33 +564,54 @@ cudaError_t launch_block_batched(fcn_ctx *ctx, int kind, double dz, cudaStream_t
     }
 }
 
+// Whether pulses i and i+1 take one paired column launch: pairing chosen,
+// FP32, same grid and the same pivot table.
+template <typename T>
+bool pairable(const fcn_ctx *ctx, const std::vector<const cx<T> *> &tabs, size_t i) {
+    if (sizeof(T) != 4 || ctx->pairs != 1 || i + 1 >= ctx->pulses.size()) return false;
+    const Pulse &a = ctx->pulses[i], &b = ctx->pulses[i + 1];
+    return a.g.nr == b.g.nr && a.g.nt == b.g.nt && tabs[i] == tabs[i + 1];
+}
+
 template <typename T>
 cudaError_t launch_block(fcn_ctx *ctx, int kind, double dz, cudaStream_t st,
                          const std::vector<const cx<T> *> &tabs,
                          const std::vector<void *> *fields = nullptr) {
     if (ctx->batched && !fields) return launch_block_batched<T>(ctx, kind, dz, st, tabs);
     cudaError_t e = cudaSuccess;
-    for (size_t i = 0; i < ctx->pulses.size() && e == cudaSuccess; ++i) {
-        Pulse &pu = ctx->pulses[i];
-        void *f = fields ? (*fields)[i] : pu.field;
-        auto rows = [&](int ops, int pk) {
+    const size_t n = ctx->pulses.size();
+    for (size_t i = 0; i < n && e == cudaSuccess;) {
+        // pulses i and i+1 share the column launch when pairing is on and
+        // they have the same grid and pivot table
+        const bool pair = kind != 0 && pairable(ctx, tabs, i);
+        const size_t m = pair ? 2 : 1;
+        auto rows = [&](size_t k, int ops, int pk) {
+            Pulse &pu = ctx->pulses[k];
+            void *f = fields ? (*fields)[k] : pu.field;
             return timed(ctx, pk, st, [&] { return launch_rows<T>(row_args<T>(pu, f, ops, dz), pu.g.nt, st); });
         };
         auto col = [&] {
-            return timed(ctx, FCN_PROF_COLUMN, st, [&] { return launch_cn<T>(col_args<T>(pu, f, tabs[i], dz), st); });
+            Pulse &pu = ctx->pulses[i];
+            void *f = fields ? (*fields)[i] : pu.field;
+            if (!pair)
+                return timed(ctx, FCN_PROF_COLUMN, st, [&] { return launch_cn<T>(col_args<T>(pu, f, tabs[i], dz), st); });
+            void *f2 = fields ? (*fields)[i + 1] : ctx->pulses[i + 1].field;
+            return timed(ctx, FCN_PROF_COLUMN, st,
+                         [&] { return launch_cn_pair<T>(col_args<T>(pu, f, tabs[i], dz), (cx<T> *)f2, st); });
         };
         if (kind == 0) {
-            e = rows(OPS_HEAD, FCN_PROF_ROW_HEAD);
+            e = rows(i, OPS_HEAD, FCN_PROF_ROW_HEAD);
         } else if (kind == 1 || kind == 2) {
             const int reps = kind == 1 ? 8 : 1;
             for (int r = 0; r < reps && e == cudaSuccess; ++r) {
                 e = col();
-                if (e == cudaSuccess) e = rows(OPS_MID, FCN_PROF_ROW_MID);
+                for (size_t k = i; k < i + m && e == cudaSuccess; ++k) e = rows(k, OPS_MID, FCN_PROF_ROW_MID);
             }
         } else {
             e = col();
-            if (e == cudaSuccess) e = rows(OPS_TAIL, FCN_PROF_ROW_TAIL);
+            for (size_t k = i; k < i + m && e == cudaSuccess; ++k) e = rows(k, OPS_TAIL, FCN_PROF_ROW_TAIL);
         }
+        i += m;
     }
     return e;
 }
@@ -732,6 +756,42 @@ int ensure_tuned(fcn_ctx *ctx, const std::vector<const cx<T> *> &tabs, double dz
         }
         int rc = tune_pulse<T>(ctx, pu, tabs[i], dz);
         if (rc) return rc;
+    }
+    if (ctx->pairs < 0) {
+        ctx->pairs = 0;
+        bool eligible = sizeof(T) == 4 && ctx->pulses.size() >= 2;
+        for (size_t i = 1; eligible && i < ctx->pulses.size(); ++i)
+            eligible = ctx->pulses[i].g.nr == ctx->pulses[0].g.nr && ctx->pulses[i].g.nt == ctx->pulses[0].g.nt &&
+                       tabs[i] == tabs[0];
+        if (eligible && ctx->pair_mode == 1) ctx->pairs = 1;
+        if (eligible && ctx->pair_mode == -1) {
+            // one paired launch against the tuned single launch twice, on
+            // private scratch copies of the first pulse
+            Pulse &pu = ctx->pulses[0];
+            const size_t bytes = csize(ctx->prec) * pu.points();
+            void *s1 = nullptr, *s2 = nullptr;
+            CK(cudaMalloc(&s1, bytes), "pairing scratch");
+            struct Free {
+                void *p;
+                ~Free() { cudaFree(p); }
+            } g1{s1};
+            CK(cudaMalloc(&s2, bytes), "pairing scratch");
+            Free g2{s2};
+            CK(cudaMemcpyAsync(s1, pu.field, bytes, cudaMemcpyDeviceToDevice, ctx->st), "pairing copy");
+            CK(cudaMemcpyAsync(s2, pu.field, bytes, cudaMemcpyDeviceToDevice, ctx->st), "pairing copy");
+            float t_pair = 0.f, t_single = 0.f;
+            int rc = time_launches(ctx, [&] {
+                return launch_cn_pair<T>(col_args<T>(pu, s1, tabs[0], dz), (cx<T> *)s2, ctx->st);
+            }, &t_pair);
+            if (rc) return rc;
+            rc = time_launches(ctx, [&] {
+                cudaError_t e = launch_cn<T>(col_args<T>(pu, s1, tabs[0], dz), ctx->st);
+                return e == cudaSuccess ? launch_cn<T>(col_args<T>(pu, s2, tabs[0], dz), ctx->st) : e;
+            }, &t_single);
+            if (rc) return rc;
+            CK(cudaStreamSynchronize(ctx->st), "pairing sync");
+            ctx->pairs = t_pair < t_single ? 1 : 0;
+        }
     }
     return FCN_OK;
 }
@@ -1318,6 +1378,7 @@ int fcn_set_variants(fcn_ctx *ctx, int32_t row_variant, int32_t col_variant) {
     CK(cudaStreamSynchronize(ctx->st), "sync");
     ctx->force_row = row_variant;
     ctx->force_col = col_variant;
+    ctx->pairs = -1;
     for (auto &pu : ctx->pulses) pu.tuned = false;
     for (auto &kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
     ctx->graphs.clear();
@@ -1338,6 +1399,18 @@ int fcn_set_batching(fcn_ctx *ctx, int32_t mode) {
     }
     return FCN_OK;
 }
+
+int fcn_set_pairing(fcn_ctx *ctx, int32_t mode) {
+    if (!ctx || mode < -1 || mode > 1) return FCN_ERR_ARG;
+    CK(cudaStreamSynchronize(ctx->st), "sync");
+    ctx->pair_mode = mode;
+    ctx->pairs = -1;
+    for (auto &kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
+    ctx->graphs.clear();
+    return FCN_OK;
+}
+
+int fcn_get_pairing(const fcn_ctx *ctx) { return ctx ? ctx->pairs : FCN_ERR_ARG; }
 
 int fcn_get_variants(fcn_ctx *ctx, int32_t pulse, int32_t out[2]) {
     Pulse *pu = get_pulse(ctx, pulse);

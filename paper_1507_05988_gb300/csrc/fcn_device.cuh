@@ -206,6 +206,10 @@ cudaError_t launch_cn_table(const TableArgs &a, cx<T> *table, cudaStream_t st);
 // Row coefficients for the staged column variants (nr rows).
 template <typename T>
 cudaError_t launch_cn_coef(const TableArgs &a, CnCoef<T> *coef, cudaStream_t st);
+// Column stage of two pulses with the same grid and pivot table in one launch
+// (a.field and field2; a's other arguments serve both).
+template <typename T>
+cudaError_t launch_cn_pair(const ColArgs<T> &a, cx<T> *field2, cudaStream_t st);
 // Sets the staged column kernels' shared-memory attribute (outside capture).
 template <typename T>
 cudaError_t prepare_cn();

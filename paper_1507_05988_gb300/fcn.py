@@ -97,6 +97,8 @@ _SIGS = {
     "fcn_set_variants": (C.c_int, [_CTX, C.c_int32, C.c_int32]),
     "fcn_get_variants": (C.c_int, [_CTX, C.c_int32, C.POINTER(C.c_int32)]),
     "fcn_set_batching": (C.c_int, [_CTX, C.c_int32]),
+    "fcn_set_pairing": (C.c_int, [_CTX, C.c_int32]),
+    "fcn_get_pairing": (C.c_int, [_CTX]),
     "fcn_profile_enable": (C.c_int, [_CTX, C.c_int32]),
     "fcn_profile_read": (C.c_int, [_CTX, _D, C.POINTER(C.c_int64), C.c_int32]),
     "fcn_mlp_set": (C.c_int, [_CTX, _F]),
@@ -259,6 +261,12 @@ class Solver:
 
     def set_batching(self, mode: int):
         check(fcn_set_batching(self.ctx, int(mode)), self.ctx)
+
+    def set_pairing(self, mode: int):
+        check(fcn_set_pairing(self.ctx, int(mode)), self.ctx)
+
+    def pairing(self) -> int:
+        return int(fcn_get_pairing(self.ctx))
 
     def variants(self, pulse: int = 0):
         out = (C.c_int32 * 2)()
