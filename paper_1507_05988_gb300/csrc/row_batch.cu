@@ -10,7 +10,7 @@ size_t row_batch_smem(int nt, int bytes_per_complex) {
     // as many real u values
     const int tpr = nt / 16;
     const int rpc = 512 / tpr;
-    return (size_t)(bytes_per_complex + bytes_per_complex / 2) * rpc * (nt + nt / 16) + sizeof(double) * 32;
+    return (size_t)(bytes_per_complex + bytes_per_complex / 2) * rpc * (nt + nt / 16) + sizeof(double) * kRowScratch;
 }
 
 template <>

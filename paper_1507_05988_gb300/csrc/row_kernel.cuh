@@ -37,6 +37,10 @@ namespace {
 
 constexpr int ilog2(int n) { return n <= 1 ? 0 : 1 + ilog2(n / 2); }
 
+// FP64 scratch per CTA for the cross-warp parts of the row scans and
+// reductions (rows per CTA x warps per row x values <= 64)
+constexpr int kRowScratch = 64;
+
 template <int NT>
 struct RowCfg {
     static constexpr int E = NT < 16 ? NT : 16;             // values per thread
@@ -639,48 +643,58 @@ __device__ __forceinline__ void nl_half_smem(cx<T> *S, T *U, int t, const NLCoef
     }
 }
 
-// Sum across the TPR threads of a row (FP64), result valid in thread t = 0.
-template <int NT>
-__device__ __forceinline__ double row_sum(double x, int t, double *scr, int rloc) {
+// Reduction of NV FP64 values across the TPR threads of a row in one pass
+// (warp shuffles, then one exchange of the warp partials); mx[k] selects max
+// instead of sum for value k.  Results valid in thread t = 0.
+template <int NT, int NV>
+__device__ __forceinline__ void row_reduce(double (&x)[NV], const bool (&mx)[NV], int t, double *scr,
+                                           int rloc) {
     using C = RowCfg<NT>;
     constexpr int W = C::TPR < 32 ? C::TPR : 32;
 #pragma unroll
-    for (int d = W / 2; d >= 1; d >>= 1) x += __shfl_down_sync(0xffffffffu, x, d, W);
+    for (int d = W / 2; d >= 1; d >>= 1) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            const double o = __shfl_down_sync(0xffffffffu, x[k], d, W);
+            x[k] = mx[k] ? fmax(x[k], o) : x[k] + o;
+        }
+    }
     if (C::WARPS_PER_ROW > 1) {
-        double *ws = scr + rloc * C::WARPS_PER_ROW;
+        static_assert(C::WARPS_PER_ROW * NV <= kRowScratch, "row scratch");
         __syncthreads();
-        if ((t & 31) == 0) scr[FCN_IDX(rloc * C::WARPS_PER_ROW + (t >> 5), 32, 18)] = x;
+        if ((t & 31) == 0) {
+#pragma unroll
+            for (int k = 0; k < NV; ++k)
+                scr[FCN_IDX((rloc * C::WARPS_PER_ROW + (t >> 5)) * NV + k, kRowScratch, 18)] = x[k];
+        }
         __syncthreads();
         if (t == 0) {
-            double s = 0.0;
-            for (int w = 0; w < C::WARPS_PER_ROW; ++w) s += scr[FCN_IDX(rloc * C::WARPS_PER_ROW + w, 32, 20)];
-            x = s;
+#pragma unroll
+            for (int k = 0; k < NV; ++k) {
+                double acc = scr[FCN_IDX(rloc * C::WARPS_PER_ROW * NV + k, kRowScratch, 20)];
+                for (int w = 1; w < C::WARPS_PER_ROW; ++w) {
+                    const double o = scr[FCN_IDX((rloc * C::WARPS_PER_ROW + w) * NV + k, kRowScratch, 21)];
+                    acc = mx[k] ? fmax(acc, o) : acc + o;
+                }
+                x[k] = acc;
+            }
         }
         __syncthreads();
     }
-    return x;
 }
 
-template <int NT>
-__device__ __forceinline__ double row_max(double x, int t, double *scr, int rloc) {
-    using C = RowCfg<NT>;
-    constexpr int W = C::TPR < 32 ? C::TPR : 32;
-#pragma unroll
-    for (int d = W / 2; d >= 1; d >>= 1) x = fmax(x, __shfl_down_sync(0xffffffffu, x, d, W));
-    if (C::WARPS_PER_ROW > 1) {
-        double *ws = scr + rloc * C::WARPS_PER_ROW;
-        __syncthreads();
-        if ((t & 31) == 0) scr[FCN_IDX(rloc * C::WARPS_PER_ROW + (t >> 5), 32, 18)] = x;
-        __syncthreads();
-        if (t == 0) {
-            double s = scr[FCN_IDX(rloc * C::WARPS_PER_ROW, 32, 21)];
-            for (int w = 1; w < C::WARPS_PER_ROW; ++w) s = fmax(s, scr[FCN_IDX(rloc * C::WARPS_PER_ROW + w, 32, 22)]);
-            x = s;
-        }
-        __syncthreads();
+// Compensated (Kahan) FP32 running sum: the per-thread partials of the FP32
+// path keep float relative accuracy whatever the count; rows and the final
+// reductions are FP64.
+struct KahanF {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float v) {
+        const float y = v - c;
+        const float t2 = s + y;
+        c = (t2 - s) - y;
+        s = t2;
     }
-    return x;
-}
+};
 
 // MB: minimum resident CTAs per SM requested from the compiler (register cap
 // 64K / (MB * THREADS)); the autotuner picks it per (precision, Nt).
@@ -703,7 +717,7 @@ __device__ __forceinline__ void row_body(const RowArgs<T> &a, int row_base, int 
         unsigned dsm;
         asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dsm));
         if (threadIdx.x == 0)
-            FCN_IDX((sizeof(cx<T>) + sizeof(T)) * RPC * C::PADN + sizeof(double) * 32 - 1, dsm, 25);
+            FCN_IDX((sizeof(cx<T>) + sizeof(T)) * RPC * C::PADN + sizeof(double) * kRowScratch - 1, dsm, 25);
     }
 #endif
     const int tid = threadIdx.x;
@@ -747,39 +761,62 @@ __device__ __forceinline__ void row_body(const RowArgs<T> &a, int row_base, int 
             have_u = need_u;
             __syncthreads();
         }
-        // statistics and rho of the final row
+        // statistics of the final row; rho is written below, coalesced
         if (ops & (OP_STATS | OP_RHO)) {
-            double s = 0.0, mx = 0.0, mu = 0.0, bad = 0.0;
-            T *rr = (valid && a.rho) ? a.rho + (size_t)row * NT : nullptr;
+            // v = {sum |A|^2, max |A|^2, max u, count of non-finite |A|^2}
+            double v4[4] = {0.0, 0.0, 0.0, 0.0};
+            if (ops & OP_STATS) {
+                if constexpr (sizeof(T) == 4) {
+                    KahanF ks;
+                    float mxf = 0.f, muf = 0.f, badf = 0.f;
 #pragma unroll 4
-            for (int e = 0; e < E; ++e) {
-                const int p = E * t + e;
-                const int ip = pidx(p, NT);
-                const cx<T> x = S[FCN_IDX(ip, C::PADN, 29)];
-                const T u = have_u ? U[ip] : T(0);
-                if ((ops & OP_RHO) && rr) rr[FCN_IDX(p, NT, 12)] = u * a.nl.rho_nt;
-                if (ops & OP_STATS) {
-                    const double i2 = double(x.x) * double(x.x) + double(x.y) * double(x.y);
-                    if (!isfinite(i2)) bad += 1.0;
-                    s += i2;
-                    mx = fmax(mx, i2);
-                    mu = fmax(mu, double(u));
+                    for (int e = 0; e < E; ++e) {
+                        const int ip = pidx(E * t + e, NT);
+                        const cx<T> x = S[FCN_IDX(ip, C::PADN, 29)];
+                        const float i2 = fmaf(x.x, x.x, x.y * x.y);
+                        if (!isfinite(i2)) badf += 1.f;
+                        ks.add(i2);
+                        mxf = fmaxf(mxf, i2);
+                        if (have_u) muf = fmaxf(muf, U[ip]);
+                    }
+                    v4[0] = double(ks.s) - double(ks.c);
+                    v4[1] = mxf;
+                    v4[2] = muf;
+                    v4[3] = badf;
+                } else {
+#pragma unroll 4
+                    for (int e = 0; e < E; ++e) {
+                        const int ip = pidx(E * t + e, NT);
+                        const cx<T> x = S[FCN_IDX(ip, C::PADN, 29)];
+                        const double i2 = double(x.x) * double(x.x) + double(x.y) * double(x.y);
+                        if (!isfinite(i2)) v4[3] += 1.0;
+                        v4[0] += i2;
+                        v4[1] = fmax(v4[1], i2);
+                        if (have_u) v4[2] = fmax(v4[2], double(U[ip]));
+                    }
                 }
             }
             if ((ops & OP_STATS) && a.stats) {
-                s = row_sum<NT>(s, t, scr, rloc);
-                mx = row_max<NT>(mx, t, scr, rloc);
-                mu = row_max<NT>(mu, t, scr, rloc);
-                bad = row_sum<NT>(bad, t, scr, rloc);
+                const bool mxk[4] = {false, true, true, false};
+                row_reduce<NT, 4>(v4, mxk, t, scr, rloc);
                 if (t == 0 && valid) {
                     double *st = a.stats + FCN_IDX((size_t)row * NSTAT, (size_t)a.nr * NSTAT, 23);
-                    st[ST_SUM_I] = s;
-                    st[ST_MAX_I] = mx;
-                    if (ops & (OP_NL | OP_NL2)) st[ST_MAX_U] = mu;
-                    st[ST_NONFINITE] = bad;
+                    st[ST_SUM_I] = v4[0];
+                    st[ST_MAX_I] = v4[1];
+                    if (ops & (OP_NL | OP_NL2)) st[ST_MAX_U] = v4[2];
+                    st[ST_NONFINITE] = v4[3];
                 }
             }
             __syncthreads();
+            if ((ops & OP_RHO) && valid && a.rho) {
+                // consecutive threads write consecutive tau points
+                T *rr = a.rho + (size_t)row * NT;
+#pragma unroll
+                for (int i = 0; i < E; ++i) {
+                    const int idx = t + C::TPR * i;
+                    rr[FCN_IDX(idx, NT, 12)] = have_u ? U[FCN_IDX(pidx(idx, NT), C::PADN, 30)] * a.nl.rho_nt : T(0);
+                }
+            }
         }
         if (!(ops & OP_FFT) && !(ops & OP_NOSTORE) && valid) {
 #pragma unroll
@@ -806,29 +843,50 @@ __device__ __forceinline__ void row_body(const RowArgs<T> &a, int row_base, int 
             }
         }
         if ((ops & OP_SPEC) && a.stats) {
-            double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+            // spectral moments sum_q w^k |A_q|^2, w = signed bin, k = 0, 1, 2
+            double m3[3] = {0.0, 0.0, 0.0};
+            if constexpr (sizeof(T) == 4) {
+                KahanF k0, k1, k2;
 #pragma unroll
-            for (int i = 0; i < NB; ++i) {
-                const int j = t + C::TPR * i;
+                for (int i = 0; i < NB; ++i) {
+                    const int j = t + C::TPR * i;
 #pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    const int q = j + r * NS;
-                    const double w = double(q < NT / 2 ? q : q - NT);
-                    const cx<T> x = v[i * R + r];
-                    const double p2 = double(x.x) * double(x.x) + double(x.y) * double(x.y);
-                    s0 += p2;
-                    s1 += w * p2;
-                    s2 += w * w * p2;
+                    for (int r = 0; r < R; ++r) {
+                        const int q = j + r * NS;
+                        const float w = float(q < NT / 2 ? q : q - NT);
+                        const cx<T> x = v[i * R + r];
+                        const float p2 = fmaf(x.x, x.x, x.y * x.y);
+                        k0.add(p2);
+                        k1.add(w * p2);
+                        k2.add(w * w * p2);
+                    }
+                }
+                m3[0] = double(k0.s) - double(k0.c);
+                m3[1] = double(k1.s) - double(k1.c);
+                m3[2] = double(k2.s) - double(k2.c);
+            } else {
+#pragma unroll
+                for (int i = 0; i < NB; ++i) {
+                    const int j = t + C::TPR * i;
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        const int q = j + r * NS;
+                        const double w = double(q < NT / 2 ? q : q - NT);
+                        const cx<T> x = v[i * R + r];
+                        const double p2 = double(x.x) * double(x.x) + double(x.y) * double(x.y);
+                        m3[0] += p2;
+                        m3[1] += w * p2;
+                        m3[2] += w * w * p2;
+                    }
                 }
             }
-            s0 = row_sum<NT>(s0, t, scr, rloc);
-            s1 = row_sum<NT>(s1, t, scr, rloc);
-            s2 = row_sum<NT>(s2, t, scr, rloc);
+            const bool mxk[3] = {false, false, false};
+            row_reduce<NT, 3>(m3, mxk, t, scr, rloc);
             if (t == 0 && valid) {
                 double *st = a.stats + FCN_IDX((size_t)row * NSTAT, (size_t)a.nr * NSTAT, 24);
-                st[ST_S0] = s0;
-                st[ST_S1] = s1;
-                st[ST_S2] = s2;
+                st[ST_S0] = m3[0];
+                st[ST_S1] = m3[1];
+                st[ST_S2] = m3[2];
             }
         }
     }
@@ -883,7 +941,7 @@ namespace rowimpl {
 template <typename T, int NT>
 size_t smem_bytes() {
     using C = RowCfg<NT>;
-    return (sizeof(cx<T>) + sizeof(T)) * C::RPC * C::PADN + sizeof(double) * 32;
+    return (sizeof(cx<T>) + sizeof(T)) * C::RPC * C::PADN + sizeof(double) * kRowScratch;
 }
 
 // Sets the dynamic shared-memory limit of the kernel; must run before any
