@@ -43,8 +43,8 @@ def build(force: bool = False) -> str:
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".{os.getpid()}.tmp"
         subprocess.check_call(
-            ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fno-fast-math",
-             "-ffp-contract=off", "-o", tmp, _SRC, "-lm"])
+            ["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-fno-fast-math",
+             "-ffp-contract=off", "-pthread", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -97,6 +97,7 @@ def _load():
             "orc_linear_step": (C.c_int, [P, C.c_double, _D]),
             "orc_step": (C.c_int, [P, C.c_double, _D, _D]),
             "orc_run": (C.c_int, [P, C.c_double, C.c_long, _D, _D]),
+            "orc_run_threads": (C.c_int, [P, C.c_double, C.c_long, _D, _D, C.c_int]),
             "orc_diag_compute": (None, [P, _D, _D, C.POINTER(_Diag), _D, _D]),
             "orc_propagate_adaptive": (C.c_int, [P, _D, _D, C.c_double, C.c_double,
                                                   C.c_double, C.c_double, C.c_double,
@@ -225,12 +226,17 @@ def linear_step(pb: Problem, dz: float, A) -> np.ndarray:
     return a
 
 
-def run(pb: Problem, dz: float, nsteps: int, A):
-    """nsteps Strang steps of length dz; returns (field, rho of the last half step)."""
+def run(pb: Problem, dz: float, nsteps: int, A, threads: int = 1):
+    """nsteps Strang steps of length dz; returns (field, rho of the last half step).
+    threads > 1 runs the paper's row/column thread decomposition (same bits)."""
     a = _c128(A).copy()
     assert a.shape == (pb.nr, pb.nt)
     rho = np.zeros((pb.nr, pb.nt), np.float64)
-    rc = _load().orc_run(C.byref(pb._c()), float(dz), int(nsteps), _ptr(a), _ptr(rho))
+    if threads > 1:
+        rc = _load().orc_run_threads(C.byref(pb._c()), float(dz), int(nsteps), _ptr(a), _ptr(rho),
+                                     int(threads))
+    else:
+        rc = _load().orc_run(C.byref(pb._c()), float(dz), int(nsteps), _ptr(a), _ptr(rho))
     if rc != 0:
         raise RuntimeError(f"orc_run failed ({rc})")
     return a, rho

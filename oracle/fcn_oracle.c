@@ -33,6 +33,7 @@
 
 #include <complex.h>
 #include <math.h>
+#include <pthread.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -289,6 +290,29 @@ void orc_nl_half(const orc_problem *pb, double h, double *rowd, double *rho)
 /* Linear step (Sec. 3.1: three loops)                                 */
 /* ------------------------------------------------------------------ */
 
+/* Column q of the second loop: A~_{.,q} <- (M_abc^q)^{-1} M_def^q A~_{.,q}.
+ * co: scratch of 8 nr complex values. */
+static int cn_column(const orc_problem *pb, double dz, cplx *A, int q, cplx *co)
+{
+    int nr = pb->nr, nt = pb->nt;
+    cplx *a = co, *b = co + nr, *c = co + 2 * nr, *d = co + 3 * nr;
+    cplx *e = co + 4 * nr, *f = co + 5 * nr, *col = co + 6 * nr, *rhs = co + 7 * nr;
+    orc_cn_coeffs(pb, dz, q, (double *)a, (double *)b, (double *)c,
+                  (double *)d, (double *)e, (double *)f);
+    for (int j = 0; j < nr; ++j) col[j] = A[(size_t)j * nt + q];
+    /* rhs = M_def^q * A~_{.,q} */
+    for (int j = 0; j < nr; ++j) {
+        cplx v = e[j] * col[j];
+        if (j > 0) v += d[j] * col[j - 1];
+        if (j < nr - 1) v += f[j] * col[j + 1];
+        rhs[j] = v;
+    }
+    int rc = orc_thomas(nr, (double *)a, (double *)b, (double *)c,
+                        (double *)rhs, (double *)col);
+    for (int j = 0; j < nr; ++j) A[(size_t)j * nt + q] = col[j];
+    return rc;
+}
+
 /* A <- F^{-1}( (M_abc^q)^{-1} M_def^q F(A) ) for the whole nr x nt field. */
 int orc_linear_step(const orc_problem *pb, double dz, double *Ad)
 {
@@ -299,24 +323,8 @@ int orc_linear_step(const orc_problem *pb, double dz, double *Ad)
         if (orc_fft((double *)(A + (size_t)m * nt), nt, 0)) return -1;
     /* second loop: one tridiagonal system per frequency */
     cplx *co = (cplx *)malloc(sizeof(cplx) * (size_t)nr * 8);
-    cplx *a = co, *b = co + nr, *c = co + 2 * nr, *d = co + 3 * nr;
-    cplx *e = co + 4 * nr, *f = co + 5 * nr, *col = co + 6 * nr, *rhs = co + 7 * nr;
     int rc = 0;
-    for (int q = 0; q < nt && rc == 0; ++q) {
-        orc_cn_coeffs(pb, dz, q, (double *)a, (double *)b, (double *)c,
-                      (double *)d, (double *)e, (double *)f);
-        for (int j = 0; j < nr; ++j) col[j] = A[(size_t)j * nt + q];
-        /* rhs = M_def^q * A~_{.,q} */
-        for (int j = 0; j < nr; ++j) {
-            cplx v = e[j] * col[j];
-            if (j > 0) v += d[j] * col[j - 1];
-            if (j < nr - 1) v += f[j] * col[j + 1];
-            rhs[j] = v;
-        }
-        rc = orc_thomas(nr, (double *)a, (double *)b, (double *)c,
-                        (double *)rhs, (double *)col);
-        for (int j = 0; j < nr; ++j) A[(size_t)j * nt + q] = col[j];
-    }
+    for (int q = 0; q < nt && rc == 0; ++q) rc = cn_column(pb, dz, A, q, co);
     free(co);
     if (rc) return -2;
     /* third loop: inverse transform of every row */
@@ -352,6 +360,76 @@ int orc_run(const orc_problem *pb, double dz, long nsteps, double *A, double *rh
         if (rc) return rc;
     }
     return 0;
+}
+
+/* The same steps with the paper's shared-memory decomposition (Sec. 4,
+ * Fig. 2), for timing on a multi-core host: thread k owns a contiguous block
+ * of rows (nonlinear half step and transform of each) and a contiguous block
+ * of frequency columns (the tridiagonal solves), with a barrier between the
+ * row and column phases.  Every row and column is computed by exactly the
+ * code orc_step runs, so the result is bit-identical to orc_run. */
+typedef struct {
+    const orc_problem *pb;
+    double dz;
+    long nsteps;
+    cplx *A;
+    double *rho;
+    int nthreads, tid, rc;
+    pthread_barrier_t *bar;
+} orc_worker;
+
+static void *orc_worker_run(void *arg)
+{
+    orc_worker *w = (orc_worker *)arg;
+    const orc_problem *pb = w->pb;
+    int nr = pb->nr, nt = pb->nt;
+    int m0 = (int)((long)nr * w->tid / w->nthreads), m1 = (int)((long)nr * (w->tid + 1) / w->nthreads);
+    int q0 = (int)((long)nt * w->tid / w->nthreads), q1 = (int)((long)nt * (w->tid + 1) / w->nthreads);
+    double *tmp = (double *)malloc(sizeof(double) * (size_t)nt);
+    cplx *co = (cplx *)malloc(sizeof(cplx) * (size_t)nr * 8);
+    for (long n = 0; n < w->nsteps; ++n) {
+        for (int m = m0; m < m1; ++m) {
+            double *row = (double *)(w->A + (size_t)m * nt);
+            orc_nl_half(pb, 0.5 * w->dz, row, tmp);
+            if (orc_fft(row, nt, 0)) w->rc = -1;
+        }
+        pthread_barrier_wait(w->bar);
+        for (int q = q0; q < q1; ++q)
+            if (cn_column(pb, w->dz, w->A, q, co)) w->rc = -2;
+        pthread_barrier_wait(w->bar);
+        for (int m = m0; m < m1; ++m) {
+            double *row = (double *)(w->A + (size_t)m * nt);
+            if (orc_fft(row, nt, 1)) w->rc = -1;
+            orc_nl_half(pb, 0.5 * w->dz, row, w->rho ? w->rho + (size_t)m * nt : tmp);
+        }
+    }
+    free(co);
+    free(tmp);
+    return NULL;
+}
+
+int orc_run_threads(const orc_problem *pb, double dz, long nsteps, double *A, double *rho, int nthreads)
+{
+    if (nthreads < 1) nthreads = 1;
+    pthread_barrier_t bar;
+    if (pthread_barrier_init(&bar, NULL, (unsigned)nthreads)) return -3;
+    orc_worker *w = (orc_worker *)calloc((size_t)nthreads, sizeof(orc_worker));
+    pthread_t *th = (pthread_t *)calloc((size_t)nthreads, sizeof(pthread_t));
+    int rc = 0;
+    for (int k = 0; k < nthreads; ++k) {
+        w[k].pb = pb; w[k].dz = dz; w[k].nsteps = nsteps; w[k].A = (cplx *)A; w[k].rho = rho;
+        w[k].nthreads = nthreads; w[k].tid = k; w[k].rc = 0; w[k].bar = &bar;
+    }
+    for (int k = 1; k < nthreads; ++k)
+        if (pthread_create(&th[k], NULL, orc_worker_run, &w[k])) rc = -3;
+    if (rc == 0) orc_worker_run(&w[0]);
+    for (int k = 1; k < nthreads; ++k) pthread_join(th[k], NULL);
+    for (int k = 0; k < nthreads; ++k)
+        if (w[k].rc) rc = w[k].rc;
+    pthread_barrier_destroy(&bar);
+    free(th);
+    free(w);
+    return rc;
 }
 
 /* ------------------------------------------------------------------ */

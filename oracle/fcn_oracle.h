@@ -94,6 +94,10 @@ void orc_nl_half(const orc_problem *pb, double h, double *row, double *rho);
 int  orc_linear_step(const orc_problem *pb, double dz, double *A);
 int  orc_step(const orc_problem *pb, double dz, double *A, double *rho);
 int  orc_run(const orc_problem *pb, double dz, long nsteps, double *A, double *rho);
+/* orc_run with the paper's row/column thread decomposition (Sec. 4);
+ * bit-identical results; for timing on multi-core hosts. */
+int  orc_run_threads(const orc_problem *pb, double dz, long nsteps, double *A, double *rho,
+                     int nthreads);
 void orc_diag_compute(const orc_problem *pb, const double *A, const double *rho,
                       orc_diag *out, double *power, double *fluence);
 int  orc_propagate_adaptive(const orc_problem *pb, double *A, double *rho,

@@ -165,3 +165,15 @@ def test_linear_step_equals_dense_column_solves():
         At[:, q] = np.linalg.solve(Mabc, Mdef @ At[:, q])
     ref = np.fft.ifft(At, axis=1)
     assert rel_l2(oracle.linear_step(pb, dz, A), ref) < 1e-13
+
+
+def test_threaded_run_is_bit_identical():
+    """The paper's row/column thread decomposition (timing mode) computes
+    every row and column with the same code as the serial run."""
+    from paper_1507_05988_gb300 import workloads as W
+    wl = W.small(40, 128, p_over_pcr=4.0, noise_seed=5).with_(n2j=(W.N2, W.N4, 0, 0))
+    pb = oracle.Problem(**wl.physics())
+    a1, r1 = oracle.run(pb, 5e-3, 4, wl.field())
+    for th in (2, 3, 7):
+        a, r = oracle.run(pb, 5e-3, 4, wl.field(), threads=th)
+        assert np.array_equal(a, a1) and np.array_equal(r, r1)
