@@ -153,6 +153,18 @@ def config5(seed: int | None = 0) -> Workload:
     return config2(seed).with_(name="cfg5_1024x4096_1km", nsteps=0)
 
 
+def application_1km() -> Workload:
+    """The paper's application run (Sec. 5, Fig. 4): Nr = 1350, Nt = 1024,
+    1.1e6 steps over 1.1 km; peak intensity 3.14e14 W/m^2, r0 = 18 mm,
+    tau0 = 300 fs (P = 53.3 P_cr), n2 only.  The paper gives no windows:
+    R = 5 r0 and T = 16 tau0 as for the other workloads."""
+    w0, i0 = 18e-3, 3.14e14
+    p_cr = 3.77 * LAMBDA0 ** 2 / (8.0 * np.pi * N0 * N2)
+    p = i0 * np.pi * w0 ** 2 / 2.0
+    return Workload("app_1350x1024_1km", nr=1350, nt=1024, w0=w0, tp=300e-15,
+                    p_over_pcr=p / p_cr, dz=1e-3, nsteps=1_100_000)
+
+
 def small(nr: int = 48, nt: int = 64, **kw) -> Workload:
     """A small grid with config-1 physics for fast tests."""
     base = dict(name=f"small_{nr}x{nt}", nr=nr, nt=nt, w0=1e-3, tp=100e-15, p_over_pcr=3.0,
