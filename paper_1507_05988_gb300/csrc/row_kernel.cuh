@@ -503,8 +503,10 @@ __device__ __forceinline__ T row_scan_exclusive(T tot, int t, double *scr, int r
             // FP64 exclusive scan of the warp totals of this row (<= 16)
             double x = (lane < C::WARPS_PER_ROW) ? scr[FCN_IDX(rloc * C::WARPS_PER_ROW + lane, 32, 15)] : 0.0;
             double in = x;
+            // log2(warps per row) levels: the FP64 latency of this serial
+            // part is paid while the row's other warps wait at the barrier
 #pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
+            for (int d = 1; d < C::WARPS_PER_ROW; d <<= 1) {
                 double y = __shfl_up_sync(0xffffffffu, in, d, 32);
                 if (lane >= d) in = in + y - in * y;
             }
