@@ -516,8 +516,8 @@ __device__ __forceinline__ T row_scan_exclusive(T tot, int t, double *scr, int r
             if (lane < C::WARPS_PER_ROW) scr[FCN_IDX(rloc * C::WARPS_PER_ROW + lane, 32, 16)] = ex;
         }
         __syncthreads();
+        // the carries are not rewritten before the caller's next barrier
         const T wc = T(scr[FCN_IDX(rloc * C::WARPS_PER_ROW + w, 32, 17)]);
-        __syncthreads();
         excl = uplus(wc, excl);
     }
     return excl;
