@@ -276,6 +276,8 @@ def run_ours(args):
         solver.set_field(f, pulse=i)
     solver.step(dz, args.warmup)
     torch.cuda.synchronize()
+    variants = {"row": solver.variants(0)[0], "column": solver.variants(0)[1],
+                "paired_columns": solver.pairing()}
 
     def barrier():
         if pg:
@@ -406,6 +408,7 @@ def run_ours(args):
                       f"per GPU vs 129 MB L2",
                 "timed": f"one fcn_step(dz, {args.steps}) call (CUDA graphs), CUDA events on "
                          "the launch stream",
+                "kernel_variants": variants,
             },
             "ms_per_z_step_per_pulse": t_ms / args.steps / B,
             "gpu_launches": launches,

@@ -712,26 +712,30 @@ int tune_pulse(fcn_ctx *ctx, Pulse &pu, const cx<T> *tab, double dz) {
             ~Free() { cudaFree(p); }
         } guard{scratch};
         CK(cudaMemcpyAsync(scratch, pu.field, bytes, cudaMemcpyDeviceToDevice, ctx->st), "tuning copy");
-        int best_r = 0, best_c = 0;
-        float best = 1e30f;
+        // three interleaved rounds over the variants, each variant's best
+        // round counts (a burst of noise on the GPU then decides nothing)
         const int nrv = (sizeof(T) == 4 && pu.p.K == 8) ? kRowVariants : 1;
-        for (int v = 0; v < nrv; ++v) {
-            RowArgs<T> a = row_args<T>(pu, scratch, OPS_MID, dz);
-            a.variant = v;
-            float ms;
-            int rc = time_launches(ctx, [&] { return launch_rows<T>(a, pu.g.nt, ctx->st); }, &ms);
-            if (rc) return rc;
-            if (ms < best) { best = ms; best_r = v; }
+        std::vector<float> tr(nrv, 1e30f), tc(kColVariants, 1e30f);
+        for (int round = 0; round < 3; ++round) {
+            for (int v = 0; v < nrv; ++v) {
+                RowArgs<T> a = row_args<T>(pu, scratch, OPS_MID, dz);
+                a.variant = v;
+                float ms;
+                int rc = time_launches(ctx, [&] { return launch_rows<T>(a, pu.g.nt, ctx->st); }, &ms);
+                if (rc) return rc;
+                tr[v] = std::min(tr[v], ms);
+            }
+            for (int v = 0; v < kColVariants; ++v) {
+                ColArgs<T> a = col_args<T>(pu, scratch, tab, dz);
+                a.variant = v;
+                float ms;
+                int rc = time_launches(ctx, [&] { return launch_cn<T>(a, ctx->st); }, &ms);
+                if (rc) return rc;
+                tc[v] = std::min(tc[v], ms);
+            }
         }
-        best = 1e30f;
-        for (int v = 0; v < kColVariants; ++v) {
-            ColArgs<T> a = col_args<T>(pu, scratch, tab, dz);
-            a.variant = v;
-            float ms;
-            int rc = time_launches(ctx, [&] { return launch_cn<T>(a, ctx->st); }, &ms);
-            if (rc) return rc;
-            if (ms < best) { best = ms; best_c = v; }
-        }
+        const int best_r = int(std::min_element(tr.begin(), tr.end()) - tr.begin());
+        const int best_c = int(std::min_element(tc.begin(), tc.end()) - tc.begin());
         CK(cudaStreamSynchronize(ctx->st), "tuning sync");
         it = g_tune.emplace(key, std::make_pair(best_r, best_c)).first;
         tune_cache_store(prec, pu.g.nr, pu.g.nt, best_r, best_c);
