@@ -320,12 +320,15 @@ def run_ours(args):
                       "alg_GBps": gbps, "frac_of_hbm_peak": (gbps / peak if gbps else None)}
     dom_name = max(prof.items(), key=lambda kv: kv[1][0])[0]
     achieved = kernels[dom_name]["alg_GBps"]
-    bytes_per_launch = stage_bytes * (B if prof[dom_name][1] < B * execs[dom_name] else 1)
+    # a launch processes one pulse, two (paired column stage) or the whole
+    # batch (batched stage): the pulses it covers on average
+    bytes_per_launch = stage_bytes * B * execs[dom_name] / prof[dom_name][1]
     traffic = None
     tpath = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tpath):
+        tkey = dom_name + ("_pair" if dom_name == "column" and variants["paired_columns"] else "")
         with open(tpath) as f:
-            traffic = json.load(f).get(dom_name)
+            traffic = json.load(f).get(tkey)
 
     # ---- end to end through the C-ABI with pinned host buffers ----
     host_in = [torch.from_numpy(f).pin_memory() for f in fields]
