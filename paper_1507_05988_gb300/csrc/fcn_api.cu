@@ -126,36 +126,6 @@ struct ConstTables {
 };
 ConstTables g_tables;
 
-// FP32 twiddle W = exp(i ang): among the float pairs within 8 ulps of the
-// rounded (cos, sin), the one whose modulus is closest to 1 with a phase
-// error below 2.5e-7 rad.  Independently rounded pairs have |W|^2 - 1 of
-// ~3e-8 with a common sign over many entries; since the same table acts on
-// every row at every z-step, that bias would show up as an energy drift of
-// ~1e-7 per step (the FFT and its inverse both scale by |W|^2).
-cx<float> unit_twiddle_f32(long double ang) {
-    const long double c = cosl(ang), s = sinl(ang);
-    float cs[17], ss[17];
-    cs[0] = float(c);
-    ss[0] = float(s);
-    for (int k = 1; k <= 8; ++k) {
-        cs[2 * k - 1] = nextafterf(cs[2 * k - 3 < 0 ? 0 : 2 * k - 3], 2.f);
-        cs[2 * k] = nextafterf(cs[2 * k - 2], -2.f);
-        ss[2 * k - 1] = nextafterf(ss[2 * k - 3 < 0 ? 0 : 2 * k - 3], 2.f);
-        ss[2 * k] = nextafterf(ss[2 * k - 2], -2.f);
-    }
-    float bc = cs[0], bs = ss[0];
-    long double bm = fabsl((long double)bc * bc + (long double)bs * bs - 1.0L), bp = 0.0L;
-    for (int i = 0; i < 17; ++i)
-        for (int j = 0; j < 17; ++j) {
-            const long double cc = cs[i], sv = ss[j];
-            const long double m = fabsl(cc * cc + sv * sv - 1.0L);
-            const long double ph = fabsl(sv * c - cc * s);   // sin of the phase error
-            if (ph > 2.5e-7L) continue;
-            if (m < bm || (m == bm && ph < bp)) { bm = m; bp = ph; bc = cs[i]; bs = ss[j]; }
-        }
-    return mk(bc, bs);
-}
-
 template <typename T>
 cudaError_t get_twiddles(int nt, const cx<T> **out) {
     const int prec = sizeof(T) == 8 ? FCN_FP64 : FCN_FP32_MIXED;
@@ -163,25 +133,38 @@ cudaError_t get_twiddles(int nt, const cx<T> **out) {
     auto key = std::make_pair(prec, nt);
     auto it = g_tables.tw.find(key);
     if (it != g_tables.tw.end()) { *out = (const cx<T> *)it->second; return cudaSuccess; }
-    std::vector<cx<T>> w(nt);
+    // W^m = exp(-2 pi i m / nt); FP32 entries as two-float pairs (hi, lo):
+    // hi the nearest float, lo the nearest float to the remainder, so that
+    // hi + lo carries the twiddle to ~1e-15 in phase and modulus
+    constexpr int PER = sizeof(T) == 4 ? 2 : 1;        // cx<T> values per entry
+    std::vector<cx<T>> w((size_t)nt * PER);
     for (int m = 0; m < nt; ++m) {
         const long double ang = -2.0L * 3.14159265358979323846264338327950288L * (long double)m /
                                 (long double)nt;
-        if constexpr (sizeof(T) == 4) w[m] = unit_twiddle_f32(ang);
-        else w[m] = mk(T(cosl(ang)), T(sinl(ang)));
+        const long double c = cosl(ang), sn = sinl(ang);
+        if constexpr (sizeof(T) == 4) {
+            const float ch = float(c), sh = float(sn);
+            w[2 * (size_t)m] = mk(ch, sh);
+            w[2 * (size_t)m + 1] = mk(float(c - (long double)ch), float(sn - (long double)sh));
+        } else {
+            w[m] = mk(T(c), T(sn));
+        }
     }
     // per-pass blocks (layout in fcn_device.cuh: tw_offset)
     const size_t n = std::max(1, tw_size(nt));
-    std::vector<cx<T>> h(n, mk(T(1), T(0)));
+    std::vector<cx<T>> h(n * PER, mk(T(0), T(0)));
     for (int p = 1; p < fft_npass(nt); ++p) {
         const int R = fft_radix(nt, p), NS = fft_ns(nt, p), stride = nt / (NS * R);
         for (int r = 1; r < R; ++r)
-            for (int k = 0; k < NS; ++k) h[tw_offset(nt, p) + (r - 1) * NS + k] = w[r * k * stride];
+            for (int k = 0; k < NS; ++k)
+                for (int u = 0; u < PER; ++u)
+                    h[((size_t)tw_offset(nt, p) + (r - 1) * NS + k) * PER + u] =
+                        w[(size_t)(r * k * stride) * PER + u];
     }
     void *d = nullptr;
-    cudaError_t e = cudaMalloc(&d, sizeof(cx<T>) * n);
+    cudaError_t e = cudaMalloc(&d, sizeof(cx<T>) * n * PER);
     if (e != cudaSuccess) return e;
-    e = cudaMemcpy(d, h.data(), sizeof(cx<T>) * n, cudaMemcpyHostToDevice);
+    e = cudaMemcpy(d, h.data(), sizeof(cx<T>) * n * PER, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) { cudaFree(d); return e; }
     g_tables.tw[key] = d;
     *out = (const cx<T> *)d;

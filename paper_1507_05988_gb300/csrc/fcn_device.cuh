@@ -111,7 +111,8 @@ struct NLCoef {
 // p >= 1 (radix R_p, Ns_p = product of the earlier radices) one block of
 // (R_p - 1) Ns_p factors, entry (r - 1) Ns_p + k = W^(r k Nt / (Ns_p R_p)),
 // W = exp(-2 pi i / Nt), r = 1..R_p-1, k = 0..Ns_p-1: the threads of a warp
-// (consecutive k) read consecutive entries.
+// (consecutive k) read consecutive entries.  An FP32 entry is a two-float
+// pair (hi, lo) of complex floats, 16 bytes; an FP64 entry one complex double.
 __host__ __device__ constexpr int fft_log2(int n) { return n <= 1 ? 0 : 1 + fft_log2(n / 2); }
 __host__ __device__ constexpr int fft_n16(int nt) { return nt >= 16 ? fft_log2(nt) / 4 : 0; }
 __host__ __device__ constexpr int fft_rem(int nt) { return nt >= 16 ? (1 << (fft_log2(nt) % 4)) : nt; }

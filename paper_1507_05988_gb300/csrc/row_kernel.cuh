@@ -11,9 +11,11 @@
 //
 // Transform: self-sorting Stockham FFT (radix-16 passes, then one radix 2/4/8
 // pass for the remaining factor), done in place in one padded shared-memory
-// buffer with the butterfly operands in registers.  The first inverse pass
-// reads HBM directly and the last forward pass writes HBM directly; both are
-// coalesced (consecutive threads touch consecutive complex values).  Shared
+// buffer with the butterfly operands in registers.  The inverse transform is
+// the exact adjoint of the forward one (the forward passes in reverse order,
+// transposed, with conjugate constants).  The first inverse pass reads HBM
+// directly and the last forward pass writes HBM directly, in the same order;
+// both are coalesced (consecutive threads touch consecutive complex values).  Shared
 // memory rows are padded by one value per 16 so that the strided Stockham
 // stores and the contiguous per-thread reads of the nonlinear stage are free
 // of bank conflicts.
@@ -88,29 +90,30 @@ __host__ __device__ constexpr double cos16(int m) {
 
 // o * exp(DIR 2 pi i m / 16); exact shortcuts for the quarter turns.
 //
-// FP32 constants: float32 (cos, sin) pairs rounded independently do not have
-// unit modulus (|w|^2 - 1 ~ -6e-8 for the pi/8 pair, -3.4e-8 for pi/4), and
-// because the same constants act on every row at every step, that bias
-// accumulates into an energy drift of ~1e-7 per z-step.  So the pi/8 family
-// uses float pairs within a few ulps of (cos pi/8, sin pi/8) of nearly unit
-// modulus, one per direction with opposite modulus errors (+3.53e-9 forward,
-// -3.62e-9 inverse; phase errors -2.3e-7 and +3.8e-7 rad), so that a
-// transform and its inverse leave no net bias; the pi/4 family applies
-// 1/sqrt(2) as a two-float (hi + lo) scale.
-template <int DIR>
-__device__ __forceinline__ void c16f_pair(int m, float *c, float *s) {
-    // ~(cos, sin)(pi/8), modulus-matched, per direction
-    constexpr float C1 = DIR < 0 ? 0.92387962341308594f : 0.92387938499450684f;
-    constexpr float S1 = DIR < 0 ? 0.38268321752548218f : 0.38268378376960754f;
+// FP32 constants: a float (cos, sin) pair of a codelet or twiddle angle
+// carries a phase and a modulus error of up to ~6e-8.  The same constants act
+// on every row at every z-step, so such errors do not average out: they add
+// up coherently over the steps (field error ~5e-7 per step, energy drift
+// ~1e-8 per step on a 1024 x 4096 pulse).  So every non-trivial FP32 constant
+// is applied as a two-float (hi + lo) pair inside the FMAs that multiply by
+// it: the pi/8 family here, 1/sqrt(2) for the pi/4 family, and the twiddles
+// (tw_mul).  Together with the inverse transform being the exact adjoint of
+// the forward one (InvDispatch), the constants then leave errors at the
+// level of the random rounding of the arithmetic only.
+__device__ __forceinline__ void c16f_pair2(int m, float *ch, float *cl, float *sh, float *sl) {
+    // cos(pi/8), sin(pi/8) = hi + lo (hi the nearest float, lo the nearest
+    // float to the rest; residual below 7e-16)
+    constexpr float C8H = 0.9238795042037964f, C8L = 2.830748968563057e-08f;
+    constexpr float S8H = 0.3826834261417389f, S8L = 6.2233507236442165e-09f;
     switch (m & 15) {
-        case 1: *c = C1; *s = S1; break;
-        case 3: *c = S1; *s = C1; break;
-        case 5: *c = -S1; *s = C1; break;
-        case 7: *c = -C1; *s = S1; break;
-        case 9: *c = -C1; *s = -S1; break;
-        case 11: *c = -S1; *s = -C1; break;
-        case 13: *c = S1; *s = -C1; break;
-        default: *c = C1; *s = -S1; break;        // 15
+        case 1: *ch = C8H; *cl = C8L; *sh = S8H; *sl = S8L; break;
+        case 3: *ch = S8H; *cl = S8L; *sh = C8H; *sl = C8L; break;
+        case 5: *ch = -S8H; *cl = -S8L; *sh = C8H; *sl = C8L; break;
+        case 7: *ch = -C8H; *cl = -C8L; *sh = S8H; *sl = S8L; break;
+        case 9: *ch = -C8H; *cl = -C8L; *sh = -S8H; *sl = -S8L; break;
+        case 11: *ch = -S8H; *cl = -S8L; *sh = -C8H; *sl = -C8L; break;
+        case 13: *ch = S8H; *cl = S8L; *sh = -C8H; *sl = -C8L; break;
+        default: *ch = C8H; *cl = C8L; *sh = -S8H; *sl = -S8L; break;        // 15
     }
 }
 
@@ -132,10 +135,13 @@ __device__ __forceinline__ cx<T> rot16(cx<T> o, int m) {
             const float im = ss * o.x + sc * o.y;
             return mk(T(fmaf(re, H_HI, re * H_LO)), T(fmaf(im, H_HI, im * H_LO)));
         }
-        float c, s;
-        c16f_pair<DIR>(m, &c, &s);
-        s *= float(DIR);
-        return mk(T(o.x * c - o.y * s), T(o.x * s + o.y * c));
+        float ch, cl, sh, sl;
+        c16f_pair2(m, &ch, &cl, &sh, &sl);
+        if (DIR < 0) { sh = -sh; sl = -sl; }
+        // (o.x + i o.y)(c + i s), the lo parts first
+        const float lre = fmaf(o.x, cl, -o.y * sl);
+        const float lim = fmaf(o.x, sl, o.y * cl);
+        return mk(T(fmaf(o.x, ch, fmaf(-o.y, sh, lre))), T(fmaf(o.x, sh, fmaf(o.y, ch, lim))));
     } else {
         const T c = T(cos16(m));
         const T s = T(DIR) * T(cos16(m - 4));
@@ -197,9 +203,60 @@ struct Dft<T, 1, DIR> {
     __device__ __forceinline__ static void run(cx<T> *) {}
 };
 
-// Twiddle and butterfly of pass P for this thread's butterflies (operands
-// already in v[i*R + r]).
-template <typename T, int NT, int P, int DIR>
+// v * W_e (DIR < 0) or v * conj(W_e) (DIR > 0) for twiddle entry e.  FP32
+// tables hold each twiddle as a two-float pair, 16 bytes per entry
+// (hi.x, hi.y, lo.x, lo.y); FP64 tables one complex double.
+template <typename T, int DIR>
+__device__ __forceinline__ cx<T> tw_mul(cx<T> v, const cx<T> *__restrict__ tw, int e, int entries) {
+    if constexpr (sizeof(T) == 4) {
+        const float4 w = __ldg(reinterpret_cast<const float4 *>(tw) + FCN_IDX(e, entries, 3));
+        const float hy = DIR > 0 ? -w.y : w.y;
+        const float ly = DIR > 0 ? -w.w : w.w;
+        const float lre = fmaf(v.x, w.z, -v.y * ly);
+        const float lim = fmaf(v.x, ly, v.y * w.z);
+        return mk(T(fmaf(v.x, w.x, fmaf(-v.y, hy, lre))), T(fmaf(v.x, hy, fmaf(v.y, w.x, lim))));
+    } else {
+        cx<T> w = ldg_cx(&tw[FCN_IDX(e, entries, 3)]);
+        if (DIR > 0) w.y = -w.y;
+        return cmul(v, w);
+    }
+}
+
+// Adjoint of Dft<T, R, -1>: the same butterflies transposed, with the
+// conjugate constants (decimation in frequency).  Exact transpose in exact
+// arithmetic, so that Inverse(Forward(x)) = x to first order in the errors of
+// the rounded constants.
+template <typename T, int R>
+struct DftAdj {
+    __device__ __forceinline__ static void run(cx<T> *v) {
+        cx<T> e[R / 2], o[R / 2];
+#pragma unroll
+        for (int k = 0; k < R / 2; ++k) {
+            const int m = k * (16 / R);
+            const cx<T> a = v[k], b = v[k + R / 2];
+            e[k] = cadd2(a, b);
+            if (m == 4) {
+                o[k] = mk(b.y - a.y, a.x - b.x);          // i (a - b)
+            } else if (m == 12) {
+                o[k] = mk(a.y - b.y, b.x - a.x);          // -i (a - b)
+            } else {
+                o[k] = rot16<T, +1>(csub2(a, b), m);
+            }
+        }
+        DftAdj<T, R / 2>::run(e);
+        DftAdj<T, R / 2>::run(o);
+#pragma unroll
+        for (int k = 0; k < R / 2; ++k) { v[2 * k] = e[k]; v[2 * k + 1] = o[k]; }
+    }
+};
+template <typename T>
+struct DftAdj<T, 1> {
+    __device__ __forceinline__ static void run(cx<T> *) {}
+};
+
+// Twiddle and butterfly of forward pass P for this thread's butterflies
+// (operands already in v[i*R + r]).
+template <typename T, int NT, int P>
 __device__ __forceinline__ void pass_compute(cx<T> (&v)[RowCfg<NT>::E], int t,
                                              const cx<T> *__restrict__ tw) {
     using C = RowCfg<NT>;
@@ -214,13 +271,32 @@ __device__ __forceinline__ void pass_compute(cx<T> (&v)[RowCfg<NT>::E], int t,
         if (NS > 1) {
             const int k = j & (NS - 1);
 #pragma unroll
-            for (int r = 1; r < R; ++r) {
-                cx<T> w = ldg_cx(&tw[FCN_IDX(OFF + (r - 1) * NS + k, tw_size(NT), 3)]);
-                if (DIR > 0) w.y = -w.y;
-                v[i * R + r] = cmul(v[i * R + r], w);
-            }
+            for (int r = 1; r < R; ++r)
+                v[i * R + r] = tw_mul<T, -1>(v[i * R + r], tw, OFF + (r - 1) * NS + k, tw_size(NT));
         }
-        Dft<T, R, DIR>::run(&v[i * R]);
+        Dft<T, R, -1>::run(&v[i * R]);
+    }
+}
+
+// Adjoint of forward pass P: the transposed butterfly, then the conjugate
+// twiddles.
+template <typename T, int NT, int P>
+__device__ __forceinline__ void pass_compute_adj(cx<T> (&v)[RowCfg<NT>::E], int t,
+                                                 const cx<T> *__restrict__ tw) {
+    using C = RowCfg<NT>;
+    constexpr int R = PassCfg<NT, P>::R;
+    constexpr int NS = PassCfg<NT, P>::NS;
+    constexpr int NB = C::E / R;
+    constexpr int OFF = tw_offset(NT, P);
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+        DftAdj<T, R>::run(&v[i * R]);
+        if (NS > 1) {
+            const int k = (t + C::TPR * i) & (NS - 1);
+#pragma unroll
+            for (int r = 1; r < R; ++r)
+                v[i * R + r] = tw_mul<T, +1>(v[i * R + r], tw, OFF + (r - 1) * NS + k, tw_size(NT));
+        }
     }
 }
 
@@ -252,28 +328,45 @@ __device__ __forceinline__ void pass_store(const cx<T> (&v)[RowCfg<NT>::E], cx<T
     }
 }
 
-// Inverse transform (input already in registers in pass-0 order; result in S
-// in natural order, unscaled) and forward transform (input in S in natural
-// order; the last pass leaves its outputs in registers for the caller).
-template <typename T, int NT, int P, bool LAST>
+// Inverse transform: the exact adjoint of the forward transform, i.e. the
+// forward passes in reverse order, each reading its operands from where the
+// forward pass writes them and writing to where it reads them (input already
+// in registers in the last forward pass's output order; result in S in
+// natural order, unscaled but for sc).
+template <typename T, int NT, int P, bool DONE>
 struct InvDispatch;
 template <typename T, int NT, int P>
 struct InvDispatch<T, NT, P, false> {
     // sc (the 1/Nt of the inverse transform) scales the last pass's outputs
     __device__ __forceinline__ static void run(cx<T> (&v)[RowCfg<NT>::E], cx<T> *S, int t,
                                                const cx<T> *tw, T sc) {
-        if (P > 0) {
-            pass_load<T, NT, P>(v, S, t);
+        using C = RowCfg<NT>;
+        constexpr int R = PassCfg<NT, P>::R;
+        constexpr int NS = PassCfg<NT, P>::NS;
+        constexpr int NB = C::E / R;
+        if (P + 1 < C::NPASS) {
+#pragma unroll
+            for (int i = 0; i < NB; ++i) {
+                const int j = t + C::TPR * i;
+                const int base = (j / NS) * NS * R + (j & (NS - 1));
+#pragma unroll
+                for (int r = 0; r < R; ++r) v[i * R + r] = S[FCN_IDX(pidx(base + r * NS, NT), C::PADN, 1)];
+            }
             __syncthreads();
         }
-        pass_compute<T, NT, P, +1>(v, t, tw);
-        if (P + 1 == RowCfg<NT>::NPASS) {
+        pass_compute_adj<T, NT, P>(v, t, tw);
+        if (P == 0) {
 #pragma unroll
-            for (int e = 0; e < RowCfg<NT>::E; ++e) v[e] = mk(v[e].x * sc, v[e].y * sc);
+            for (int e = 0; e < C::E; ++e) v[e] = mk(v[e].x * sc, v[e].y * sc);
         }
-        pass_store<T, NT, P>(v, S, t);
+#pragma unroll
+        for (int i = 0; i < NB; ++i) {
+            const int j = t + C::TPR * i;
+#pragma unroll
+            for (int r = 0; r < R; ++r) S[FCN_IDX(pidx(j + r * (NT / R), NT), C::PADN, 2)] = v[i * R + r];
+        }
         __syncthreads();
-        InvDispatch<T, NT, P + 1, (P + 1 >= RowCfg<NT>::NPASS)>::run(v, S, t, tw, sc);
+        InvDispatch<T, NT, P - 1, (P < 1)>::run(v, S, t, tw, sc);
     }
 };
 template <typename T, int NT, int P>
@@ -290,7 +383,7 @@ struct FwdDispatch<T, NT, P, false> {
                                                const cx<T> *tw) {
         pass_load<T, NT, P>(v, S, t);
         __syncthreads();
-        pass_compute<T, NT, P, -1>(v, t, tw);
+        pass_compute<T, NT, P>(v, t, tw);
         if (P + 1 < RowCfg<NT>::NPASS) {
             pass_store<T, NT, P>(v, S, t);
             __syncthreads();
@@ -733,10 +826,19 @@ __device__ __forceinline__ void row_body(const RowArgs<T> &a, int row_base, int 
 
     cx<T> v[E];
     if (ops & OP_IFFT) {
-        // pass-0 operands straight from HBM: X[t + r*TPR], coalesced
+        // the inverse's first pass (the adjoint of the last forward pass) takes
+        // its operands straight from HBM: X[j + r*NS], j = t + TPR*i, coalesced
+        constexpr int PL = C::NPASS - 1;
+        constexpr int RL = PassCfg<NT, PL>::R;
+        constexpr int NSL = PassCfg<NT, PL>::NS;
 #pragma unroll
-        for (int r = 0; r < E; ++r) v[r] = valid ? g[FCN_IDX(t + r * C::TPR, NT, 4)] : mk(T(0), T(0));
-        InvDispatch<T, NT, 0, (C::NPASS <= 0)>::run(v, S, t, a.tw, a.nl.inv_nt);
+        for (int i = 0; i < E / RL; ++i) {
+            const int j = t + C::TPR * i;
+#pragma unroll
+            for (int r = 0; r < RL; ++r)
+                v[i * RL + r] = valid ? g[FCN_IDX(j + r * NSL, NT, 4)] : mk(T(0), T(0));
+        }
+        InvDispatch<T, NT, PL, (PL < 0)>::run(v, S, t, a.tw, a.nl.inv_nt);
     } else {
 #pragma unroll
         for (int i = 0; i < E; ++i) {
