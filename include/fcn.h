@@ -225,6 +225,35 @@ int fcn_set_batching(fcn_ctx *ctx, int32_t mode);
 int fcn_set_pairing(fcn_ctx *ctx, int32_t mode);
 int fcn_get_pairing(const fcn_ctx *ctx);
 
+/* Graph branches for multi-pulse contexts.  The pulses (or pulse pairs of a
+ * paired column launch) are independent between the row and column stages
+ * of the split step (Sec. 3: each pulse is its own problem), so with n > 1
+ * the captured CUDA graphs hold one chain of launches per pulse group,
+ * spread round-robin over n forked branches that the GPU may run
+ * concurrently (filling the tail of one group's launch with another's).
+ * Each pulse's launches and their order are unchanged, so results are
+ * bit-identical for every n.  n in 1..8 (default 1; batched work lists
+ * ignore it).  Drops the captured graphs.  Synchronises.
+ * fcn_get_graph_branches returns the setting. */
+int fcn_set_graph_branches(fcn_ctx *ctx, int32_t n);
+int fcn_get_graph_branches(const fcn_ctx *ctx);
+
+/* Multi-pulse row launches: the row stage of pulses whose launches differ
+ * only in their field, rho and statistics buffers (same grid, physics
+ * coefficients, dz and kernel variant) as one launch (blockIdx.y = pulse).
+ *   mode 0: one row launch per pulse;
+ *   mode 1: per z-step, the column stage of every pulse group, then the
+ *           row stage of up to 8 consecutive pulses per launch;
+ *   mode 2 (default): per pulse group (the two pulses of a paired column
+ *           launch), its column launch and then one row launch for both,
+ *           which keeps each group's chain of launches on data still in L2.
+ * Each pulse's own sequence of operations is the same in every mode, so
+ * results are bit-identical.  Graph branches > 1 use modes 0 and 2 only.
+ * Drops the captured graphs.  Synchronises.  fcn_get_multi_launch returns
+ * the mode. */
+int fcn_set_multi_launch(fcn_ctx *ctx, int32_t mode);
+int fcn_get_multi_launch(const fcn_ctx *ctx);
+
 /* Variants in use for pulse `pulse` (out[0] row, out[1] column; -1 before
  * the first step). */
 int fcn_get_variants(fcn_ctx *ctx, int32_t pulse, int32_t out[2]);

@@ -366,6 +366,7 @@ template <typename T, int L>
 __global__ void __launch_bounds__(512)
 cn_kernel(ColArgs<T> a, int C) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    pdl_enter();
     // CTAs for bins q and Nt - q are launched next to each other
     const int ngroups = a.nt / C;
     const int b = blockIdx.x;
@@ -611,6 +612,7 @@ template <typename T, int L, bool REG, int NTC>
 __global__ void __launch_bounds__(staged_threads<T, L>(), L >= 16 ? 3 : 2)
 cn_staged_kernel(ColArgs<T> a, int C) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    pdl_enter();
     const int ngroups = a.nt / C;
     const int b = blockIdx.x;
     const int g = (b & 1) ? (ngroups - 1 - (b >> 1)) : (b >> 1);
@@ -652,8 +654,7 @@ cudaError_t launch_cn_staged_l(const ColArgs<T> &a, cudaStream_t st) {
     const size_t slots = REG ? 2 * L : 2 * L + 2;
     const size_t smem = sizeof(cx<T>) * (3 * (size_t)(threads / 32) * C + slots * threads);
     if (smem > kCnStagedSmemMax) return cudaErrorInvalidConfiguration;
-    cn_staged_kernel<T, L, REG, NTC><<<a.nt / C, threads, smem, st>>>(a, C);
-    return cudaGetLastError();
+    return launch_k(cn_staged_kernel<T, L, REG, NTC>, dim3(a.nt / C), dim3(threads), smem, st, a, C);
 }
 
 template <typename T, int L>
@@ -668,8 +669,7 @@ cudaError_t launch_cn_l(const ColArgs<T> &a, int target, cudaStream_t st) {
     if (threads > 512) return cudaErrorInvalidConfiguration;
     const size_t smem = sizeof(cx<T>) * 3 * (size_t)(threads / 32) * C;
     const int grid = a.nt / C;
-    cn_kernel<T, L><<<grid, threads, smem, st>>>(a, C);
-    return cudaGetLastError();
+    return launch_k(cn_kernel<T, L>, dim3(grid), dim3(threads), smem, st, a, C);
 }
 
 // ---------------------------------------------------------------------------
@@ -864,6 +864,7 @@ template <typename T, int L, int NTC>
 __global__ void __launch_bounds__(512, 1)
 cn_pair_kernel(ColArgs<T> a, cx<T> *field2, int C) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    pdl_enter();
     const int ngroups = a.nt / C;
     const int b = blockIdx.x;
     const int g = (b & 1) ? (ngroups - 1 - (b >> 1)) : (b >> 1);
@@ -884,14 +885,20 @@ cudaError_t launch_cn_pair_l(const ColArgs<T> &a, cx<T> *field2, cudaStream_t st
     if (threads > TMAX) return cudaErrorInvalidConfiguration;
     const size_t smem = sizeof(cx<T>) * (5 * (size_t)(threads / 32) * C + 2 * (size_t)L * threads);
     if (smem > kCnStagedSmemMax) return cudaErrorInvalidConfiguration;
-    cn_pair_kernel<T, L, NTC><<<a.nt / C, threads, smem, st>>>(a, field2, C);
-    return cudaGetLastError();
+    return launch_k(cn_pair_kernel<T, L, NTC>, dim3(a.nt / C), dim3(threads), smem, st, a, field2, C);
+}
+
+// The column kernels keep the driver's carveout choice: forcing the largest
+// shared-memory carveout (the row kernels') measured slower, as the column
+// stage's loads lean on L1.
+template <typename Kern>
+cudaError_t set_col_attrs(Kern k) {
+    return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCnStagedSmemMax);
 }
 
 template <typename T, int L, int NTC>
 cudaError_t set_pair_attr() {
-    return cudaFuncSetAttribute(cn_pair_kernel<T, L, NTC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)kCnStagedSmemMax);
+    return set_col_attrs(cn_pair_kernel<T, L, NTC>);
 }
 
 // Register-fed variant with Nt as a compile-time constant for the grids of
@@ -913,8 +920,7 @@ cudaError_t launch_cn_reg_nt(const ColArgs<T> &a, cudaStream_t st) {
 
 template <typename T, int L, bool REG, int NTC>
 cudaError_t set_staged_attr() {
-    return cudaFuncSetAttribute(cn_staged_kernel<T, L, REG, NTC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)kCnStagedSmemMax);
+    return set_col_attrs(cn_staged_kernel<T, L, REG, NTC>);
 }
 
 }  // namespace

@@ -262,6 +262,8 @@ struct TableEntry {
     size_t bytes;     // allocation size
 };
 
+constexpr int kMaxBranches = 8;
+
 struct GraphKey {
     int kind;        // 0 head, 1 mid x8, 2 mid x1, 3 tail
     uint64_t dz;
@@ -272,6 +274,16 @@ struct fcn_ctx {
     int prec = FCN_FP64;
     cudaStream_t st = nullptr;        // user stream (launch target)
     cudaStream_t cap = nullptr;       // internal stream used for graph capture
+    // graph branches: the pulse groups (pairs or single pulses) of a captured
+    // block are independent chains; with branches > 1 they are captured on
+    // that many forked streams so that the GPU overlaps them
+    int branches = 1;
+    // multi-pulse row launches: 0 one launch per pulse; 1 per z-step the
+    // column launches of all groups, then one row launch over all pulses;
+    // 2 per group (a paired column launch's two pulses) one row launch
+    int multi_mode = 2;
+    cudaStream_t bst[kMaxBranches] = {};
+    cudaEvent_t fork_ev = nullptr, join_ev[kMaxBranches] = {};
     std::vector<Pulse> pulses;
     std::map<GraphKey, cudaGraphExec_t> graphs;
     std::map<TableKey, TableEntry> tables;   // shared pivot tables
@@ -556,22 +568,63 @@ bool pairable(const fcn_ctx *ctx, const std::vector<const cx<T> *> &tabs, size_t
     return a.g.nr == b.g.nr && a.g.nt == b.g.nt && tabs[i] == tabs[i + 1];
 }
 
+// Whether two pulses' row launches differ only in their field, rho and
+// statistics pointers (same grid, twiddles, operations, variant and
+// coefficients), so that one multi-pulse launch serves both.
 template <typename T>
-cudaError_t launch_block(fcn_ctx *ctx, int kind, double dz, cudaStream_t st,
-                         const std::vector<const cx<T> *> &tabs,
-                         const std::vector<void *> *fields = nullptr) {
-    if (ctx->batched && !fields) return launch_block_batched<T>(ctx, kind, dz, st, tabs);
+bool same_row_launch(const RowArgs<T> &a, const RowArgs<T> &b) {
+    const NLCoef<T> &x = a.nl, &y = b.nl;
+    bool same = a.nr == b.nr && a.nt == b.nt && a.tw == b.tw && a.ops == b.ops && a.variant == b.variant &&
+                x.h == y.h && x.plasma == y.plasma && x.loss == y.loss && x.sdt == y.sdt &&
+                x.inv_is == y.inv_is && x.inv_nt == y.inv_nt && x.rho_nt == y.rho_nt &&
+                x.hplasma == y.hplasma && x.hloss == y.hloss && x.sat == y.sat && x.is_root == y.is_root &&
+                x.K == y.K && x.nkerr == y.nkerr && x.flags == y.flags;
+    for (int j = 0; j < 4; ++j) same = same && x.kerr[j] == y.kerr[j] && x.hk[j] == y.hk[j];
+    return same;
+}
+
+// The launches of one block for the pulse group starting at pulse i (pulses
+// i and i+1 when they share a paired column launch); *m receives the group
+// size.  Groups are independent of one another.  kind -1: the group's
+// column launch alone.
+template <typename T>
+cudaError_t launch_group(fcn_ctx *ctx, int kind, double dz, cudaStream_t st,
+                         const std::vector<const cx<T> *> &tabs, const std::vector<void *> *fields,
+                         size_t i, size_t *m_out) {
     cudaError_t e = cudaSuccess;
-    const size_t n = ctx->pulses.size();
-    for (size_t i = 0; i < n && e == cudaSuccess;) {
+    {
         // pulses i and i+1 share the column launch when pairing is on and
         // they have the same grid and pivot table
         const bool pair = kind != 0 && pairable(ctx, tabs, i);
         const size_t m = pair ? 2 : 1;
-        auto rows = [&](size_t k, int ops, int pk) {
+        *m_out = m;
+        auto rows1 = [&](size_t k, int ops, int pk) {
             Pulse &pu = ctx->pulses[k];
             void *f = fields ? (*fields)[k] : pu.field;
             return timed(ctx, pk, st, [&] { return launch_rows<T>(row_args<T>(pu, f, ops, dz), pu.g.nt, st); });
+        };
+        // the row stage of the group's pulses (one two-pulse launch when the
+        // pair's launches differ only in their buffers and mode 2 is set)
+        auto rows_group = [&](int ops, int pk) {
+            if (m == 2 && ctx->multi_mode == 2) {
+                Pulse &p0 = ctx->pulses[i], &p1 = ctx->pulses[i + 1];
+                RowMultiArgs<T> ma;
+                ma.a = row_args<T>(p0, fields ? (*fields)[i] : p0.field, ops, dz);
+                const RowArgs<T> a1 = row_args<T>(p1, fields ? (*fields)[i + 1] : p1.field, ops, dz);
+                if (same_row_launch(ma.a, a1)) {
+                    for (int c = 0; c < kRowMulti; ++c) {
+                        ma.field[c] = nullptr;
+                        ma.rho[c] = nullptr;
+                        ma.stats[c] = nullptr;
+                    }
+                    ma.field[0] = ma.a.field; ma.rho[0] = ma.a.rho; ma.stats[0] = ma.a.stats;
+                    ma.field[1] = a1.field; ma.rho[1] = a1.rho; ma.stats[1] = a1.stats;
+                    return timed(ctx, pk, st, [&] { return launch_rows_multi<T>(ma, 2, p0.g.nt, st); });
+                }
+            }
+            cudaError_t r = cudaSuccess;
+            for (size_t k = i; k < i + m && r == cudaSuccess; ++k) r = rows1(k, ops, pk);
+            return r;
         };
         auto col = [&] {
             Pulse &pu = ctx->pulses[i];
@@ -582,19 +635,104 @@ cudaError_t launch_block(fcn_ctx *ctx, int kind, double dz, cudaStream_t st,
             return timed(ctx, FCN_PROF_COLUMN, st,
                          [&] { return launch_cn_pair<T>(col_args<T>(pu, f, tabs[i], dz), (cx<T> *)f2, st); });
         };
-        if (kind == 0) {
-            e = rows(i, OPS_HEAD, FCN_PROF_ROW_HEAD);
+        if (kind == -1) {
+            e = col();
+        } else if (kind == 0) {
+            e = rows1(i, OPS_HEAD, FCN_PROF_ROW_HEAD);
         } else if (kind == 1 || kind == 2) {
             const int reps = kind == 1 ? 8 : 1;
             for (int r = 0; r < reps && e == cudaSuccess; ++r) {
                 e = col();
-                for (size_t k = i; k < i + m && e == cudaSuccess; ++k) e = rows(k, OPS_MID, FCN_PROF_ROW_MID);
+                if (e == cudaSuccess) e = rows_group(OPS_MID, FCN_PROF_ROW_MID);
             }
         } else {
             e = col();
-            for (size_t k = i; k < i + m && e == cudaSuccess; ++k) e = rows(k, OPS_TAIL, FCN_PROF_ROW_TAIL);
+            if (e == cudaSuccess) e = rows_group(OPS_TAIL, FCN_PROF_ROW_TAIL);
         }
-        i += m;
+    }
+    return e;
+}
+
+// Row stage of every pulse with operations `ops`: consecutive pulses whose
+// launches differ only in their pointers go into one multi-pulse launch (at
+// most kRowMulti per launch).
+template <typename T>
+cudaError_t launch_rows_all(fcn_ctx *ctx, int ops, int pk, double dz, cudaStream_t st,
+                            const std::vector<void *> *fields) {
+    const size_t n = ctx->pulses.size();
+    cudaError_t e = cudaSuccess;
+    for (size_t i = 0; i < n && e == cudaSuccess;) {
+        Pulse &p0 = ctx->pulses[i];
+        RowMultiArgs<T> m;
+        m.a = row_args<T>(p0, fields ? (*fields)[i] : p0.field, ops, dz);
+        int cnt = 0;
+        size_t k = i;
+        for (; k < n && cnt < kRowMulti; ++k) {
+            Pulse &pk_ = ctx->pulses[k];
+            const RowArgs<T> ak = row_args<T>(pk_, fields ? (*fields)[k] : pk_.field, ops, dz);
+            if (k > i && !same_row_launch(m.a, ak)) break;
+            m.field[cnt] = ak.field;
+            m.rho[cnt] = ak.rho;
+            m.stats[cnt] = ak.stats;
+            ++cnt;
+        }
+        for (int c = cnt; c < kRowMulti; ++c) {
+            m.field[c] = nullptr;
+            m.rho[c] = nullptr;
+            m.stats[c] = nullptr;
+        }
+        e = timed(ctx, pk, st, [&] {
+            return cnt == 1 ? launch_rows<T>(m.a, p0.g.nt, st) : launch_rows_multi<T>(m, cnt, p0.g.nt, st);
+        });
+        i = k;
+    }
+    return e;
+}
+
+template <typename T>
+cudaError_t launch_block(fcn_ctx *ctx, int kind, double dz, cudaStream_t st,
+                         const std::vector<const cx<T> *> &tabs,
+                         const std::vector<void *> *fields = nullptr) {
+    if (ctx->batched && !fields) return launch_block_batched<T>(ctx, kind, dz, st, tabs);
+    cudaError_t e = cudaSuccess;
+    const size_t n = ctx->pulses.size();
+    size_t m = 1;
+    if (ctx->multi_mode != 1 || n == 1) {
+        for (size_t i = 0; i < n && e == cudaSuccess; i += m) e = launch_group<T>(ctx, kind, dz, st, tabs, fields, i, &m);
+        return e;
+    }
+    // multi-pulse row launches: per z-step the column stage of every pulse
+    // group, then the row stage of all pulses (each pulse still runs head,
+    // (column, row) per step and tail in order)
+    if (kind == 0) return launch_rows_all<T>(ctx, OPS_HEAD, FCN_PROF_ROW_HEAD, dz, st, fields);
+    const int reps = kind == 1 ? 8 : 1;
+    for (int r = 0; r < reps && e == cudaSuccess; ++r) {
+        for (size_t i = 0; i < n && e == cudaSuccess; i += m) e = launch_group<T>(ctx, -1, dz, st, tabs, fields, i, &m);
+        if (e == cudaSuccess)
+            e = kind == 3 ? launch_rows_all<T>(ctx, OPS_TAIL, FCN_PROF_ROW_TAIL, dz, st, fields)
+                          : launch_rows_all<T>(ctx, OPS_MID, FCN_PROF_ROW_MID, dz, st, fields);
+    }
+    return e;
+}
+
+// Capture of one block with the pulse groups spread round-robin over
+// ctx->branches forked streams (fork and join through events on `st`).
+template <typename T>
+cudaError_t launch_block_branched(fcn_ctx *ctx, int kind, double dz, cudaStream_t st,
+                                  const std::vector<const cx<T> *> &tabs) {
+    const int nb = ctx->branches;
+    cudaError_t e = cudaEventRecord(ctx->fork_ev, st);
+    for (int b = 0; b < nb && e == cudaSuccess; ++b) e = cudaStreamWaitEvent(ctx->bst[b], ctx->fork_ev, 0);
+    const size_t n = ctx->pulses.size();
+    size_t m = 1;
+    int g = 0;
+    for (size_t i = 0; i < n && e == cudaSuccess; i += m, ++g)
+        e = launch_group<T>(ctx, kind, dz, ctx->bst[g % nb], tabs, nullptr, i, &m);
+    for (int b = 0; b < nb; ++b) {
+        // join every branch, also after an error, so that the capture ends cleanly
+        cudaError_t r = cudaEventRecord(ctx->join_ev[b], ctx->bst[b]);
+        if (r == cudaSuccess) r = cudaStreamWaitEvent(st, ctx->join_ev[b], 0);
+        if (e == cudaSuccess) e = r;
     }
     return e;
 }
@@ -613,7 +751,9 @@ int run_block(fcn_ctx *ctx, int kind, double dz, const std::vector<const cx<T> *
         // be captured), then replay on the caller's stream
         cudaGraph_t g = nullptr;
         CK(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
-        cudaError_t le = launch_block<T>(ctx, kind, dz, ctx->cap, tabs);
+        cudaError_t le = (ctx->branches > 1 && !ctx->batched)
+                             ? launch_block_branched<T>(ctx, kind, dz, ctx->cap, tabs)
+                             : launch_block<T>(ctx, kind, dz, ctx->cap, tabs);
         cudaError_t ce = cudaStreamEndCapture(ctx->cap, &g);
         if (le != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_fail(ctx, le, "captured launch"); }
         if (ce != cudaSuccess) return cuda_fail(ctx, ce, "end capture");
@@ -1207,6 +1347,11 @@ void fcn_destroy(fcn_ctx *ctx) {
     cudaFree(ctx->col_items);
     cudaFree(ctx->counter);
     if (ctx->host_red) cudaFreeHost(ctx->host_red);
+    for (int b = 0; b < kMaxBranches; ++b) {
+        if (ctx->bst[b]) cudaStreamDestroy(ctx->bst[b]);
+        if (ctx->join_ev[b]) cudaEventDestroy(ctx->join_ev[b]);
+    }
+    if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
     if (ctx->cap) cudaStreamDestroy(ctx->cap);
     delete ctx;
 }
@@ -1398,6 +1543,36 @@ int fcn_set_pairing(fcn_ctx *ctx, int32_t mode) {
 }
 
 int fcn_get_pairing(const fcn_ctx *ctx) { return ctx ? ctx->pairs : FCN_ERR_ARG; }
+
+int fcn_set_graph_branches(fcn_ctx *ctx, int32_t n) {
+    if (!ctx) return FCN_ERR_ARG;
+    if (n < 1 || n > kMaxBranches) return fail(ctx, FCN_ERR_ARG, "branches must be in 1..8");
+    CK(cudaStreamSynchronize(ctx->st), "sync");
+    if (!ctx->fork_ev) CK(cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming), "fork event");
+    for (int b = 0; b < n; ++b) {
+        if (!ctx->bst[b]) CK(cudaStreamCreateWithFlags(&ctx->bst[b], cudaStreamNonBlocking), "branch stream");
+        if (!ctx->join_ev[b]) CK(cudaEventCreateWithFlags(&ctx->join_ev[b], cudaEventDisableTiming), "join event");
+    }
+    ctx->branches = n;
+    for (auto &kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
+    ctx->graphs.clear();
+    return FCN_OK;
+}
+
+int fcn_get_graph_branches(const fcn_ctx *ctx) { return ctx ? ctx->branches : FCN_ERR_ARG; }
+
+int fcn_set_multi_launch(fcn_ctx *ctx, int32_t mode) {
+    if (!ctx || mode < 0 || mode > 2) return FCN_ERR_ARG;
+    CK(cudaStreamSynchronize(ctx->st), "sync");
+    if (mode != ctx->multi_mode) {
+        ctx->multi_mode = mode;
+        for (auto &kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
+        ctx->graphs.clear();
+    }
+    return FCN_OK;
+}
+
+int fcn_get_multi_launch(const fcn_ctx *ctx) { return ctx ? ctx->multi_mode : FCN_ERR_ARG; }
 
 int fcn_get_variants(fcn_ctx *ctx, int32_t pulse, int32_t out[2]) {
     Pulse *pu = get_pulse(ctx, pulse);

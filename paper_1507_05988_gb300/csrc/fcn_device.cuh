@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <cstdlib>
 
 // Optional self-checking build (-DFCN_CHECKED, used to locate memory faults):
 // every indexed access in the kernels goes through FCN_IDX, which prints the
@@ -52,6 +53,44 @@ template <typename T>
 __device__ __forceinline__ cx<T> cmul_i(cx<T> a, T s) { return mk(-a.y * s, a.x * s); }
 template <typename T>
 __device__ __forceinline__ T cnorm(cx<T> a) { return a.x * a.x + a.y * a.y; }
+
+// Programmatic dependent launch of the z-step kernels (off unless the
+// environment has FCN_PDL=1).  Each kernel first lets the next kernel of its
+// stream be scheduled (which happens once every CTA of this kernel has
+// started, so the next kernel's CTAs only take the slots this one frees in
+// its last wave), then waits until its predecessor has completed and its
+// memory is visible, before any access.  Launched without the attribute,
+// both instructions return at once.  Measured on the 1024 x 4096 pulses it
+// is slower (column CTAs placed early on SMs that still hold row CTAs run
+// with the row kernel's small L1), hence off by default.
+__device__ __forceinline__ void pdl_enter() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+inline bool pdl_enabled() {
+    static const bool on = [] {
+        const char *e = std::getenv("FCN_PDL");
+        return e && e[0] == '1';
+    }();
+    return on;
+}
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                     Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = pdl_enabled() ? 1 : 0;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
 
 // Read-only cached load of one complex value.
 __device__ __forceinline__ cx<float> ldg_cx(const cx<float> *p) {
@@ -155,6 +194,18 @@ struct RowArgs {
     NLCoef<T> nl;
 };
 
+// One launch of the row stage over up to kRowMulti pulses that share the
+// grid, the coefficients and the kernel variant: a's own field, rho and
+// stats are ignored; pulse y (blockIdx.y) uses field[y], rho[y], stats[y].
+constexpr int kRowMulti = 8;
+template <typename T>
+struct RowMultiArgs {
+    RowArgs<T> a;
+    cx<T> *field[kRowMulti];
+    T *rho[kRowMulti];
+    double *stats[kRowMulti];
+};
+
 // Per-row coefficients of the Crank-Nicolson system (Eqs. (Ma)-(Mb)) for one
 // dz, in the form the staged column kernel uses: with delta_q = dk q^2,
 //   explicit side  w_j = sl x_{j-1} + sh x_{j+1} - d (c0 - delta_q) x_j,
@@ -193,6 +244,8 @@ struct TableArgs {
 // ---- launchers (defined in the .cu files) ----
 template <typename T>
 cudaError_t launch_rows(const RowArgs<T> &a, int nt, cudaStream_t st);
+template <typename T>
+cudaError_t launch_rows_multi(const RowMultiArgs<T> &m, int npulse, int nt, cudaStream_t st);
 // Sets the kernel's shared-memory attribute for this Nt (call before the
 // first launch, outside stream capture).
 template <typename T>

@@ -5,6 +5,7 @@
 namespace fcn {
 namespace rowimpl {
 template cudaError_t launch_nt<float, 8192>(const RowArgs<float> &, cudaStream_t);
+template cudaError_t launch_nt_multi<float, 8192>(const RowMultiArgs<float> &, int, cudaStream_t);
 template cudaError_t prepare_nt<float, 8192>();
 }  // namespace rowimpl
 }  // namespace fcn

@@ -5,10 +5,13 @@
 namespace fcn {
 namespace rowimpl {
 template cudaError_t launch_nt<float, 64>(const RowArgs<float> &, cudaStream_t);
+template cudaError_t launch_nt_multi<float, 64>(const RowMultiArgs<float> &, int, cudaStream_t);
 template cudaError_t prepare_nt<float, 64>();
 template cudaError_t launch_nt<float, 128>(const RowArgs<float> &, cudaStream_t);
+template cudaError_t launch_nt_multi<float, 128>(const RowMultiArgs<float> &, int, cudaStream_t);
 template cudaError_t prepare_nt<float, 128>();
 template cudaError_t launch_nt<float, 256>(const RowArgs<float> &, cudaStream_t);
+template cudaError_t launch_nt_multi<float, 256>(const RowMultiArgs<float> &, int, cudaStream_t);
 template cudaError_t prepare_nt<float, 256>();
 }  // namespace rowimpl
 }  // namespace fcn

@@ -5,6 +5,7 @@
 namespace fcn {
 namespace rowimpl {
 template cudaError_t launch_nt<double, 1024>(const RowArgs<double> &, cudaStream_t);
+template cudaError_t launch_nt_multi<double, 1024>(const RowMultiArgs<double> &, int, cudaStream_t);
 template cudaError_t prepare_nt<double, 1024>();
 }  // namespace rowimpl
 }  // namespace fcn

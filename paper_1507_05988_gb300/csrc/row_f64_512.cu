@@ -5,6 +5,7 @@
 namespace fcn {
 namespace rowimpl {
 template cudaError_t launch_nt<double, 512>(const RowArgs<double> &, cudaStream_t);
+template cudaError_t launch_nt_multi<double, 512>(const RowMultiArgs<double> &, int, cudaStream_t);
 template cudaError_t prepare_nt<double, 512>();
 }  // namespace rowimpl
 }  // namespace fcn

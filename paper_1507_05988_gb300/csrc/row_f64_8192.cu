@@ -5,6 +5,7 @@
 namespace fcn {
 namespace rowimpl {
 template cudaError_t launch_nt<double, 8192>(const RowArgs<double> &, cudaStream_t);
+template cudaError_t launch_nt_multi<double, 8192>(const RowMultiArgs<double> &, int, cudaStream_t);
 template cudaError_t prepare_nt<double, 8192>();
 }  // namespace rowimpl
 }  // namespace fcn

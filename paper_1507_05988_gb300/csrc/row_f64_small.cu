@@ -5,10 +5,13 @@
 namespace fcn {
 namespace rowimpl {
 template cudaError_t launch_nt<double, 64>(const RowArgs<double> &, cudaStream_t);
+template cudaError_t launch_nt_multi<double, 64>(const RowMultiArgs<double> &, int, cudaStream_t);
 template cudaError_t prepare_nt<double, 64>();
 template cudaError_t launch_nt<double, 128>(const RowArgs<double> &, cudaStream_t);
+template cudaError_t launch_nt_multi<double, 128>(const RowMultiArgs<double> &, int, cudaStream_t);
 template cudaError_t prepare_nt<double, 128>();
 template cudaError_t launch_nt<double, 256>(const RowArgs<double> &, cudaStream_t);
+template cudaError_t launch_nt_multi<double, 256>(const RowMultiArgs<double> &, int, cudaStream_t);
 template cudaError_t prepare_nt<double, 256>();
 }  // namespace rowimpl
 }  // namespace fcn

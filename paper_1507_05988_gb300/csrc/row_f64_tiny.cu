@@ -5,14 +5,19 @@
 namespace fcn {
 namespace rowimpl {
 template cudaError_t launch_nt<double, 2>(const RowArgs<double> &, cudaStream_t);
+template cudaError_t launch_nt_multi<double, 2>(const RowMultiArgs<double> &, int, cudaStream_t);
 template cudaError_t prepare_nt<double, 2>();
 template cudaError_t launch_nt<double, 4>(const RowArgs<double> &, cudaStream_t);
+template cudaError_t launch_nt_multi<double, 4>(const RowMultiArgs<double> &, int, cudaStream_t);
 template cudaError_t prepare_nt<double, 4>();
 template cudaError_t launch_nt<double, 8>(const RowArgs<double> &, cudaStream_t);
+template cudaError_t launch_nt_multi<double, 8>(const RowMultiArgs<double> &, int, cudaStream_t);
 template cudaError_t prepare_nt<double, 8>();
 template cudaError_t launch_nt<double, 16>(const RowArgs<double> &, cudaStream_t);
+template cudaError_t launch_nt_multi<double, 16>(const RowMultiArgs<double> &, int, cudaStream_t);
 template cudaError_t prepare_nt<double, 16>();
 template cudaError_t launch_nt<double, 32>(const RowArgs<double> &, cudaStream_t);
+template cudaError_t launch_nt_multi<double, 32>(const RowMultiArgs<double> &, int, cudaStream_t);
 template cudaError_t prepare_nt<double, 32>();
 }  // namespace rowimpl
 }  // namespace fcn

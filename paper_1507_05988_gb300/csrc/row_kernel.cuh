@@ -1000,6 +1000,23 @@ template <typename T, int NT, int KT, int MB>
 __global__ void __launch_bounds__(RowCfg<NT>::THREADS, MB)
 row_kernel(RowArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    pdl_enter();
+    row_body<T, NT, KT, RowCfg<NT>::THREADS>(a, blockIdx.x * RowCfg<NT>::RPC, a.ops, smem_raw);
+}
+
+// Several pulses of one grid and one set of coefficients in one launch:
+// blockIdx.y selects the pulse (its field, rho and statistics pointers; all
+// else is shared).  One launch over all pulses fills the waves that a launch
+// per pulse leaves part-empty.
+template <typename T, int NT, int KT, int MB>
+__global__ void __launch_bounds__(RowCfg<NT>::THREADS, MB)
+row_kernel_multi(const __grid_constant__ RowMultiArgs<T> m) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    pdl_enter();
+    RowArgs<T> a = m.a;
+    a.field = m.field[blockIdx.y];
+    a.rho = m.rho[blockIdx.y];
+    a.stats = m.stats[blockIdx.y];
     row_body<T, NT, KT, RowCfg<NT>::THREADS>(a, blockIdx.x * RowCfg<NT>::RPC, a.ops, smem_raw);
 }
 
@@ -1061,8 +1078,12 @@ constexpr int mb_of(int v) {
 
 template <typename T, int NT, int KT, int MB>
 cudaError_t set_smem_attr() {
-    return cudaFuncSetAttribute(row_kernel<T, NT, KT, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem_bytes<T, NT>());
+    cudaError_t e = cudaFuncSetAttribute(row_kernel<T, NT, KT, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem_bytes<T, NT>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(row_kernel_multi<T, NT, KT, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem_bytes<T, NT>());
+    return e;
 }
 
 template <typename T, int NT>
@@ -1077,25 +1098,38 @@ cudaError_t prepare_nt() {
 }
 
 template <typename T, int NT>
+cudaError_t launch_nt_multi(const RowMultiArgs<T> &m, int npulse, cudaStream_t st) {
+    using C = RowCfg<NT>;
+    const RowArgs<T> &a = m.a;
+    const size_t smem = smem_bytes<T, NT>();
+    const dim3 grid((a.nr + C::RPC - 1) / C::RPC, npulse);
+    if (grid.x == 0 || npulse <= 0) return cudaSuccess;
+    if (npulse > kRowMulti) return cudaErrorInvalidValue;
+    void (*k)(const RowMultiArgs<T>) = row_kernel_multi<T, NT, 8, 1>;
+    if (a.nl.K != 8) {
+        k = row_kernel_multi<T, NT, 0, 1>;
+    } else if constexpr (sizeof(T) == 4 && NT >= 512) {
+        if (a.variant == 1) k = row_kernel_multi<T, NT, 8, mb_of<NT>(1)>;
+        else if (a.variant == 2) k = row_kernel_multi<T, NT, 8, mb_of<NT>(2)>;
+    }
+    return launch_k(k, grid, dim3(C::THREADS), smem, st, m);
+}
+
+template <typename T, int NT>
 cudaError_t launch_nt(const RowArgs<T> &a, cudaStream_t st) {
     using C = RowCfg<NT>;
     const size_t smem = smem_bytes<T, NT>();
     const int grid = (a.nr + C::RPC - 1) / C::RPC;
     if (grid == 0) return cudaSuccess;
     // K = 8 (the photon number of 800 nm in air) gets unrolled powers
+    void (*k)(RowArgs<T>) = row_kernel<T, NT, 8, 1>;
     if (a.nl.K != 8) {
-        row_kernel<T, NT, 0, 1><<<grid, C::THREADS, smem, st>>>(a);
+        k = row_kernel<T, NT, 0, 1>;
     } else if constexpr (sizeof(T) == 4 && NT >= 512) {
-        if (a.variant == 1)
-            row_kernel<T, NT, 8, mb_of<NT>(1)><<<grid, C::THREADS, smem, st>>>(a);
-        else if (a.variant == 2)
-            row_kernel<T, NT, 8, mb_of<NT>(2)><<<grid, C::THREADS, smem, st>>>(a);
-        else
-            row_kernel<T, NT, 8, 1><<<grid, C::THREADS, smem, st>>>(a);
-    } else {
-        row_kernel<T, NT, 8, 1><<<grid, C::THREADS, smem, st>>>(a);
+        if (a.variant == 1) k = row_kernel<T, NT, 8, mb_of<NT>(1)>;
+        else if (a.variant == 2) k = row_kernel<T, NT, 8, mb_of<NT>(2)>;
     }
-    return cudaGetLastError();
+    return launch_k(k, dim3(grid), dim3(C::THREADS), smem, st, a);
 }
 
 }  // namespace rowimpl

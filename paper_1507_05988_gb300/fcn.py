@@ -99,6 +99,10 @@ _SIGS = {
     "fcn_set_batching": (C.c_int, [_CTX, C.c_int32]),
     "fcn_set_pairing": (C.c_int, [_CTX, C.c_int32]),
     "fcn_get_pairing": (C.c_int, [_CTX]),
+    "fcn_set_graph_branches": (C.c_int, [_CTX, C.c_int32]),
+    "fcn_get_graph_branches": (C.c_int, [_CTX]),
+    "fcn_set_multi_launch": (C.c_int, [_CTX, C.c_int32]),
+    "fcn_get_multi_launch": (C.c_int, [_CTX]),
     "fcn_profile_enable": (C.c_int, [_CTX, C.c_int32]),
     "fcn_profile_read": (C.c_int, [_CTX, _D, C.POINTER(C.c_int64), C.c_int32]),
     "fcn_mlp_set": (C.c_int, [_CTX, _F]),
@@ -267,6 +271,18 @@ class Solver:
 
     def pairing(self) -> int:
         return int(fcn_get_pairing(self.ctx))
+
+    def set_graph_branches(self, n: int):
+        check(fcn_set_graph_branches(self.ctx, int(n)), self.ctx)
+
+    def graph_branches(self) -> int:
+        return int(fcn_get_graph_branches(self.ctx))
+
+    def set_multi_launch(self, mode: int):
+        check(fcn_set_multi_launch(self.ctx, int(mode)), self.ctx)
+
+    def multi_launch(self) -> int:
+        return int(fcn_get_multi_launch(self.ctx))
 
     def variants(self, pulse: int = 0):
         out = (C.c_int32 * 2)()

@@ -27,6 +27,8 @@ def main(argv=None) -> int:
     ap.add_argument("--row-variant", type=int, default=-1)
     ap.add_argument("--col-variant", type=int, default=-1)
     ap.add_argument("--graph", action="store_true")
+    ap.add_argument("--branches", type=int, default=1, help="graph branches (pulse groups run concurrently)")
+    ap.add_argument("--multi", type=int, default=2, help="multi-pulse row launch mode (0, 1, 2)")
     ap.add_argument("--time", type=int, default=0,
                     help="then time this many graph-replayed steps (wall clock around a "
                          "synchronising call) and as many per-launch event-timed steps")
@@ -39,6 +41,9 @@ def main(argv=None) -> int:
         s.set_variants(a.row_variant, a.col_variant)
     for k, w in enumerate(wls):
         s.set_field(w.field(), pulse=k)
+    if a.branches > 1:
+        s.set_graph_branches(a.branches)
+    s.set_multi_launch(a.multi)
     dz = wls[0].dz if wls[0].nsteps else 2e-3
     s.step(dz, a.steps, graph=a.graph)
     d = s.diag(0)
@@ -52,7 +57,8 @@ def main(argv=None) -> int:
         s.diag(0)
         dt = time.perf_counter() - t0
         print(f"profile_case: graph replay {1e6 * dt / (a.time * a.pulses):.2f} us per pulse-step "
-              f"({a.pulses} pulses)")
+              f"({a.pulses} pulses, {a.branches} graph branches, "
+              f"multi-pulse row launch mode {a.multi})")
         s.profile(True)
         s.step(dz, a.time)
         s.diag(0)

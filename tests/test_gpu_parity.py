@@ -279,19 +279,26 @@ def test_graph_replay_equals_direct_launches_and_is_reproducible(fcn, prec):
     assert np.array_equal(a1, a3) and np.array_equal(r1, r3)
 
 
-def test_profiling_counts_every_launch(fcn):
+@pytest.mark.parametrize("multi", [0, 1, 2])
+def test_profiling_counts_every_launch(fcn, multi):
     wl = W.small(32, 256, p_over_pcr=3.0)
     s = fcn.Solver([wl.physics(), wl.physics()], precision=FP32)
+    s.set_multi_launch(multi)
     for i in range(2):
         s.set_field(wl.field(), pulse=i)
     s.profile(True)
     s.step(1e-2, 5)
     prof = s.profile_read()
     s.profile(False)
-    assert prof["row_head"][1] == 2 and prof["row_tail"][1] == 2
-    # equal grids may share each column launch (pairing, decided by timing)
+    # equal grids may share each column launch (pairing, decided by timing);
+    # the two pulses share each row launch in mode 1, and in mode 2 when paired
     assert s.pairing() in (0, 1)
-    assert prof["row_mid"][1] == 8 and prof["column"][1] == (5 if s.pairing() == 1 else 10)
+    per = 1 if multi == 1 else 2
+    assert prof["row_head"][1] == per
+    if multi == 2 and s.pairing() == 1:
+        per = 1
+    assert prof["row_tail"][1] == per
+    assert prof["row_mid"][1] == 4 * per and prof["column"][1] == (5 if s.pairing() == 1 else 10)
     assert all(ms > 0 for ms, n in prof.values())
     a, b = s.get_field(0), s.get_field(1)
     assert np.array_equal(a, b)          # identical pulses in a batch stay identical
@@ -429,6 +436,74 @@ def test_paired_column_launch_equals_single_launches(fcn, npulse):
         assert np.array_equal(out[0][2], out[1][2])     # the odd pulse runs alone
     Aref, _ = oracle.run(_pb(wls[-1]), 4e-3, 5, wls[-1].field())
     assert rel_l2(out[1][-1], Aref) < 1e-5
+
+
+@pytest.mark.parametrize("pairing", [0, 1])
+def test_graph_branches_are_bit_identical(fcn, pairing):
+    """Pulse groups captured on concurrent graph branches run the same
+    launches in the same order per pulse as the single-chain graph: the
+    results are bit-identical, through head, middle blocks of 8 and 1 and
+    the tail."""
+    wls = [W.small(80, 512, p_over_pcr=4.0, noise_seed=40 + k).with_(n2j=(W.N2, W.N4, 0, 0))
+           for k in range(5)]
+    out = {}
+    for nb in (1, 3):
+        s = fcn.Solver([w.physics() for w in wls], precision=FP32)
+        s.set_variants(0, 7)
+        s.set_pairing(pairing)
+        s.set_graph_branches(nb)
+        assert s.graph_branches() == nb
+        for k, w in enumerate(wls):
+            s.set_field(w.field(), pulse=k)
+        s.step(4e-3, 11)
+        out[nb] = [s.get_field(pulse=k) for k in range(len(wls))]
+        s.close()
+    for a, b in zip(out[1], out[3]):
+        assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("graph", [True, False])
+def test_multi_pulse_row_launch_is_bit_identical(fcn, graph):
+    """The row stage of pulses sharing grid and coefficients as one launch
+    (blockIdx.y = pulse) computes exactly what one launch per pulse does;
+    a pulse with other physics (a different power) is split off into its
+    own launch and stays exact too."""
+    wls = [W.small(72, 512, p_over_pcr=4.0, noise_seed=50 + k).with_(n2j=(W.N2, W.N4, 0, 0))
+           for k in range(4)]
+    wls.insert(2, W.small(72, 512, p_over_pcr=4.0, noise_seed=60).with_(n2j=(W.N2, 0, 0, 0)))
+    out = {}
+    for multi in (0, 1, 2):
+        s = fcn.Solver([w.physics() for w in wls], precision=FP32)
+        s.set_variants(0, 7)
+        s.set_pairing(1)
+        s.set_multi_launch(multi)
+        assert s.multi_launch() == multi
+        for k, w in enumerate(wls):
+            s.set_field(w.field(), pulse=k)
+        if graph:
+            s.step(4e-3, 11)
+        else:
+            s.step(4e-3, 11, graph=False)
+        out[multi] = [(s.get_field(pulse=k), s.get_rho(pulse=k)) for k in range(len(wls))]
+        s.close()
+    for mode in (1, 2):
+        for (a, ra), (b, rb) in zip(out[0], out[mode]):
+            assert np.array_equal(a, b)
+            assert np.array_equal(ra, rb)
+
+
+def test_graph_branches_argument_checked(fcn):
+    wl = W.small(16, 64)
+    s = fcn.Solver(wl.physics(), precision=FP32)
+    with pytest.raises(Exception):
+        s.set_graph_branches(0)
+    with pytest.raises(Exception):
+        s.set_graph_branches(9)
+    s.set_graph_branches(8)
+    s.set_field(wl.field())
+    s.step(1e-3, 3)
+    assert np.isfinite(s.get_field()).all()
+    s.close()
 
 
 def test_pairing_decided_by_timing_on_equal_grids(fcn):
