@@ -320,15 +320,23 @@ def run_ours(args):
                       "alg_GBps": gbps, "frac_of_hbm_peak": (gbps / peak if gbps else None)}
     dom_name = max(prof.items(), key=lambda kv: kv[1][0])[0]
     achieved = kernels[dom_name]["alg_GBps"]
-    # a launch processes one pulse, two (paired column stage) or the whole
-    # batch (batched stage): the pulses it covers on average
-    bytes_per_launch = stage_bytes * B * execs[dom_name] / prof[dom_name][1]
+    # a launch processes one pulse, two (paired column stage, two-pulse row
+    # launch) or the whole batch (batched stage): the pulses it covers on average
+    units = B * execs[dom_name] / prof[dom_name][1]
+    bytes_per_launch = stage_bytes * units
+    # measured DRAM bytes (ncu) per pulse of the row stage, per paired column
+    # launch (two pulses) of the column stage, scaled to this launch's pulses
     traffic = None
     tpath = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tpath):
-        tkey = dom_name + ("_pair" if dom_name == "column" and variants["paired_columns"] else "")
         with open(tpath) as f:
-            traffic = json.load(f).get(tkey)
+            tj = json.load(f)
+        if dom_name == "column" and variants["paired_columns"]:
+            t = tj.get("column_pair")
+            traffic = t * units / 2 if t else None
+        else:
+            t = tj.get(dom_name)
+            traffic = t * units if t else None
 
     # ---- end to end through the C-ABI with pinned host buffers ----
     host_in = [torch.from_numpy(f).pin_memory() for f in fields]
