@@ -557,6 +557,17 @@ __device__ __forceinline__ cx<float> nl_apply_small(cx<float> a, float phi, floa
 }
 
 template <typename T>
+__device__ __forceinline__ cx<T> nl_apply_terms(cx<T> a, T phi, T lnamp);
+
+// The update of a group of points that is not all small-argument, kept out
+// of line: the unrolled nonlinear loop inlines only the common FP32
+// small-argument path (the general one is rare: the pulse's core).
+template <typename T>
+__device__ __noinline__ cx<T> nl_apply_general(cx<T> a, T phi, T lnamp) {
+    return nl_apply_terms<T>(a, phi, lnamp);
+}
+
+template <typename T>
 __device__ __forceinline__ cx<T> nl_apply_terms(cx<T> a, T phi, T lnamp) {
     if constexpr (sizeof(T) == 4) {
         if (nl_small(phi, lnamp)) return nl_apply_small(a, phi, lnamp);
@@ -641,6 +652,12 @@ __device__ __forceinline__ void nl_half_smem(cx<T> *S, T *U, int t, const NLCoef
 #pragma unroll
     for (int e = 0; e < E; ++e) cmax = fmax(cmax, cn[e]);
     T carry = T(0), umax = T(0);
+    // the thread's exclusive local prefixes of the (+)-scan; u at point e is
+    // carry (+) lp[e] once the carry is known (registers: U exists only when
+    // the caller keeps u for rho or statistics)
+    T lp[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) lp[e] = T(0);
     if (need_u) {
         T run = T(0);
         // j = |A|^2 is_root: x = dtau sigma_K Ihat^K = j^K
@@ -655,15 +672,12 @@ __device__ __forceinline__ void nl_half_smem(cx<T> *S, T *U, int t, const NLCoef
         // every RK4 increment is exactly zero and u keeps its entering value:
         // the arithmetic below would give the same bits.
         const bool idle = (KT == 8) && jmax < (sizeof(T) == 4 ? T(2e-6) : T(1e-41));
-        if (idle) {
-#pragma unroll
-            for (int e = 0; e < E; ++e) U[FCN_IDX(pidx(p0 + e, NT), C::PADN, 26)] = T(0);
-        } else {
+        if (!idle) {
             T ja = jv[0];
             T xa = powk<KT>(ja, c.K);
 #pragma unroll
             for (int e = 0; e < E; ++e) {
-                U[FCN_IDX(pidx(p0 + e, NT), C::PADN, 26)] = run;
+                lp[e] = run;
                 if ((e + 1 < E) || !last_thread) {
                     const T jb = jv[e + 1];
                     const T xb = powk<KT>(jb, c.K);
@@ -690,16 +704,13 @@ __device__ __forceinline__ void nl_half_smem(cx<T> *S, T *U, int t, const NLCoef
         if (phib < T(7.450580596923828e-9) && lnab < T(7.450580596923828e-9)) {
             if (STORE_U && need_u) {
 #pragma unroll
-                for (int e = 0; e < E; ++e) {
-                    const int ip = pidx(p0 + e, NT);
-                    U[ip] = fma(U[FCN_IDX(ip, C::PADN, 28)], omc, carry);
-                }
+                for (int e = 0; e < E; ++e) U[FCN_IDX(pidx(p0 + e, NT), C::PADN, 28)] = fma(lp[e], omc, carry);
             }
             return;
         }
     }
     constexpr int UN = E >= 4 ? 4 : E;
-#pragma unroll 1
+#pragma unroll
     for (int e0 = 0; e0 < E; e0 += UN) {
         cx<T> x[UN];
         T u[UN];
@@ -707,7 +718,7 @@ __device__ __forceinline__ void nl_half_smem(cx<T> *S, T *U, int t, const NLCoef
         for (int k = 0; k < UN; ++k) {
             const int ip = pidx(p0 + e0 + k, NT);
             x[k] = S[FCN_IDX(ip, C::PADN, 27)];
-            u[k] = need_u ? fma(U[FCN_IDX(ip, C::PADN, 28)], omc, carry) : T(0);
+            u[k] = need_u ? fma(lp[e0 + k], omc, carry) : T(0);
         }
         T phi[UN], lna[UN];
 #pragma unroll
@@ -729,11 +740,11 @@ __device__ __forceinline__ void nl_half_smem(cx<T> *S, T *U, int t, const NLCoef
             }
         } else {
 #pragma unroll
-            for (int k = 0; k < UN; ++k) S[pidx(p0 + e0 + k, NT)] = nl_apply_terms(x[k], phi[k], lna[k]);
+            for (int k = 0; k < UN; ++k) S[pidx(p0 + e0 + k, NT)] = nl_apply_general(x[k], phi[k], lna[k]);
         }
         if (STORE_U) {
 #pragma unroll
-            for (int k = 0; k < UN; ++k) U[pidx(p0 + e0 + k, NT)] = u[k];
+            for (int k = 0; k < UN; ++k) U[FCN_IDX(pidx(p0 + e0 + k, NT), C::PADN, 31)] = u[k];
         }
     }
 }
@@ -803,16 +814,20 @@ __device__ __forceinline__ void row_body(const RowArgs<T> &a, int row_base, int 
     constexpr int E = C::E;
     constexpr int RPC = TH / C::TPR;
     static_assert(RPC * C::TPR == TH, "CTA size must hold whole rows");
+    // shared memory: the rows S, the FP64 scratch, then the u rows U, which
+    // only launches with rho or statistics output allocate
     cx<T> *S_all = reinterpret_cast<cx<T> *>(smem_raw);
-    T *U_all = reinterpret_cast<T *>(S_all + RPC * C::PADN);
-    double *scr = reinterpret_cast<double *>(U_all + RPC * C::PADN);
+    double *scr = reinterpret_cast<double *>(S_all + RPC * C::PADN);
+    T *U_all = reinterpret_cast<T *>(scr + kRowScratch);
 
 #ifdef FCN_CHECKED
     {
         unsigned dsm;
         asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dsm));
+        const bool with_u = (ops & (OP_RHO | OP_STATS)) != 0;
         if (threadIdx.x == 0)
-            FCN_IDX((sizeof(cx<T>) + sizeof(T)) * RPC * C::PADN + sizeof(double) * kRowScratch - 1, dsm, 25);
+            FCN_IDX((sizeof(cx<T>) + (with_u ? sizeof(T) : 0)) * RPC * C::PADN + sizeof(double) * kRowScratch - 1,
+                    dsm, 25);
     }
 #endif
     const int tid = threadIdx.x;
@@ -1059,10 +1074,12 @@ row_batch_kernel(const RowArgs<T> *__restrict__ pulses, const int2 *__restrict__
 
 namespace rowimpl {
 
+// Rows S and the FP64 scratch, plus the u rows when the launch outputs rho
+// or statistics.
 template <typename T, int NT>
-size_t smem_bytes() {
+size_t smem_bytes(bool with_u = true) {
     using C = RowCfg<NT>;
-    return (sizeof(cx<T>) + sizeof(T)) * C::RPC * C::PADN + sizeof(double) * kRowScratch;
+    return (sizeof(cx<T>) + (with_u ? sizeof(T) : 0)) * C::RPC * C::PADN + sizeof(double) * kRowScratch;
 }
 
 // Sets the dynamic shared-memory limit of the kernel; must run before any
@@ -1101,7 +1118,7 @@ template <typename T, int NT>
 cudaError_t launch_nt_multi(const RowMultiArgs<T> &m, int npulse, cudaStream_t st) {
     using C = RowCfg<NT>;
     const RowArgs<T> &a = m.a;
-    const size_t smem = smem_bytes<T, NT>();
+    const size_t smem = smem_bytes<T, NT>((a.ops & (OP_RHO | OP_STATS)) != 0);
     const dim3 grid((a.nr + C::RPC - 1) / C::RPC, npulse);
     if (grid.x == 0 || npulse <= 0) return cudaSuccess;
     if (npulse > kRowMulti) return cudaErrorInvalidValue;
@@ -1118,7 +1135,7 @@ cudaError_t launch_nt_multi(const RowMultiArgs<T> &m, int npulse, cudaStream_t s
 template <typename T, int NT>
 cudaError_t launch_nt(const RowArgs<T> &a, cudaStream_t st) {
     using C = RowCfg<NT>;
-    const size_t smem = smem_bytes<T, NT>();
+    const size_t smem = smem_bytes<T, NT>((a.ops & (OP_RHO | OP_STATS)) != 0);
     const int grid = (a.nr + C::RPC - 1) / C::RPC;
     if (grid == 0) return cudaSuccess;
     // K = 8 (the photon number of 800 nm in air) gets unrolled powers
