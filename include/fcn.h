@@ -145,6 +145,14 @@ int fcn_set_stream(fcn_ctx *ctx, void *stream);
  * Resets z, the step counters and the diagnostics of that pulse. */
 int fcn_set_field(fcn_ctx *ctx, int32_t pulse, const double *host_field);
 
+/* As fcn_set_field and fcn_get_field with host buffers of interleaved
+ * complex64 (2*Nr*Nt floats, the same layout): half the bytes over the host
+ * link, and for FCN_FP32_MIXED contexts a plain copy of the working state
+ * (no conversion); FCN_FP64 contexts convert on the device (get rounds the
+ * double field to float).  fcn_get_field_c64 synchronises. */
+int fcn_set_field_c64(fcn_ctx *ctx, int32_t pulse, const float *host_field);
+int fcn_get_field_c64(fcn_ctx *ctx, int32_t pulse, float *host_out);
+
 /* As fcn_set_field but from a device buffer already in the working
  * precision (float or double interleaved, Nr*Nt complex).  Device-to-device
  * copy on the context stream. */

@@ -1414,6 +1414,41 @@ int fcn_get_field(fcn_ctx *ctx, int32_t pulse, double *host) {
     return FCN_OK;
 }
 
+int fcn_set_field_c64(fcn_ctx *ctx, int32_t pulse, const float *host) {
+    Pulse *pu = get_pulse(ctx, pulse);
+    if (!pu || !host) return fail(ctx, FCN_ERR_ARG, "bad pulse index or null buffer");
+    const size_t np = (size_t)pu->points();
+    if (ctx->prec == FCN_FP32_MIXED) {
+        CK(cudaMemcpyAsync(pu->field, host, 8 * np, cudaMemcpyHostToDevice, ctx->st), "H2D field");
+    } else {
+        if (!pu->stage) CK(cudaMalloc(&pu->stage, 16 * np), "staging buffer");
+        CK(cudaMemcpyAsync(pu->stage, host, 8 * np, cudaMemcpyHostToDevice, ctx->st), "H2D field");
+        CK(launch_widen<float>((const cx<float> *)pu->stage, (double *)pu->field, (int64_t)np, ctx->st), "widen");
+    }
+    CK(cudaMemsetAsync(pu->stats, 0, sizeof(double) * NSTAT * pu->g.nr, ctx->st), "reset stats");
+    CK(cudaMemsetAsync(pu->rho, 0, rsize(ctx->prec) * np, ctx->st), "reset rho");
+    pu->z = 0.0;
+    pu->steps = pu->rejected = 0;
+    pu->dz_next = 0.0;
+    pu->has_field = true;
+    return FCN_OK;
+}
+
+int fcn_get_field_c64(fcn_ctx *ctx, int32_t pulse, float *host) {
+    Pulse *pu = get_pulse(ctx, pulse);
+    if (!pu || !host) return fail(ctx, FCN_ERR_ARG, "bad pulse index or null buffer");
+    const size_t np = (size_t)pu->points();
+    if (ctx->prec == FCN_FP32_MIXED) {
+        CK(cudaMemcpyAsync(host, pu->field, 8 * np, cudaMemcpyDeviceToHost, ctx->st), "D2H field");
+    } else {
+        if (!pu->stage) CK(cudaMalloc(&pu->stage, 16 * np), "staging buffer");
+        CK(launch_narrow<float>((const double *)pu->field, (cx<float> *)pu->stage, (int64_t)np, ctx->st), "narrow");
+        CK(cudaMemcpyAsync(host, pu->stage, 8 * np, cudaMemcpyDeviceToHost, ctx->st), "D2H field");
+    }
+    CK(cudaStreamSynchronize(ctx->st), "sync");
+    return FCN_OK;
+}
+
 int fcn_get_field_device(fcn_ctx *ctx, int32_t pulse, void *dev) {
     Pulse *pu = get_pulse(ctx, pulse);
     if (!pu || !dev) return fail(ctx, FCN_ERR_ARG, "bad pulse index or null buffer");

@@ -70,6 +70,7 @@ class fcn_stats(C.Structure):
 _P = C.c_void_p
 _D = C.POINTER(C.c_double)
 _F = C.POINTER(C.c_float)
+_F = C.POINTER(C.c_float)
 _G = C.POINTER(fcn_grid)
 _PR = C.POINTER(fcn_params)
 _CTX = C.c_void_p
@@ -99,6 +100,8 @@ _SIGS = {
     "fcn_set_batching": (C.c_int, [_CTX, C.c_int32]),
     "fcn_set_pairing": (C.c_int, [_CTX, C.c_int32]),
     "fcn_get_pairing": (C.c_int, [_CTX]),
+    "fcn_set_field_c64": (C.c_int, [_CTX, C.c_int32, C.POINTER(C.c_float)]),
+    "fcn_get_field_c64": (C.c_int, [_CTX, C.c_int32, C.POINTER(C.c_float)]),
     "fcn_set_graph_branches": (C.c_int, [_CTX, C.c_int32]),
     "fcn_get_graph_branches": (C.c_int, [_CTX]),
     "fcn_set_multi_launch": (C.c_int, [_CTX, C.c_int32]),
@@ -225,6 +228,16 @@ class Solver:
     def get_field(self, pulse: int = 0, out: np.ndarray | None = None) -> np.ndarray:
         out = np.empty(self._shape(pulse), np.complex128) if out is None else out
         check(fcn_get_field(self.ctx, pulse, out.ctypes.data_as(_D)), self.ctx)
+        return out
+
+    def set_field_c64(self, a: np.ndarray, pulse: int = 0):
+        a = np.ascontiguousarray(a, dtype=np.complex64)
+        assert a.shape == self._shape(pulse)
+        check(fcn_set_field_c64(self.ctx, pulse, a.ctypes.data_as(_F)), self.ctx)
+
+    def get_field_c64(self, pulse: int = 0, out: np.ndarray | None = None) -> np.ndarray:
+        out = np.empty(self._shape(pulse), np.complex64) if out is None else out
+        check(fcn_get_field_c64(self.ctx, pulse, out.ctypes.data_as(_F)), self.ctx)
         return out
 
     def get_rho(self, pulse: int = 0) -> np.ndarray:

@@ -492,6 +492,29 @@ def test_multi_pulse_row_launch_is_bit_identical(fcn, graph):
             assert np.array_equal(ra, rb)
 
 
+@pytest.mark.parametrize("prec", [FP64, FP32])
+def test_complex64_host_field_calls(fcn, prec):
+    """set/get of complex64 host buffers: exact for the FP32-mixed state (a
+    plain copy), rounded to float for FP64 contexts; a step from a complex64
+    upload equals a step from the same values uploaded as complex128."""
+    wl = W.small(48, 256, p_over_pcr=3.0, noise_seed=9)
+    a64 = wl.field()
+    a32 = a64.astype(np.complex64)
+    s1 = fcn.Solver(wl.physics(), precision=prec)
+    s1.set_field_c64(a32)
+    if prec == FP32:
+        assert np.array_equal(s1.get_field_c64(), a32)
+    assert np.array_equal(s1.get_field(), a32.astype(np.complex128))
+    s2 = fcn.Solver(wl.physics(), precision=prec)
+    s2.set_field(a32.astype(np.complex128))
+    s1.step(1e-2, 3)
+    s2.step(1e-2, 3)
+    assert np.array_equal(s1.get_field(), s2.get_field())
+    assert np.array_equal(s1.get_field_c64(), s2.get_field().astype(np.complex64))
+    s1.close()
+    s2.close()
+
+
 def test_graph_branches_argument_checked(fcn):
     wl = W.small(16, 64)
     s = fcn.Solver(wl.physics(), precision=FP32)
