@@ -144,21 +144,25 @@ struct NLCoef {
     unsigned flags;
 };
 
-// Pass structure of the row stage's self-sorting FFT of Nt points (radix-16
-// passes, then one radix 2/4/8 pass for the remaining factor; Nt < 16: one
-// pass of radix Nt) and the layout of its twiddle table: for every pass
-// p >= 1 (radix R_p, Ns_p = product of the earlier radices) one block of
-// (R_p - 1) Ns_p factors, entry (r - 1) Ns_p + k = W^(r k Nt / (Ns_p R_p)),
-// W = exp(-2 pi i / Nt), r = 1..R_p-1, k = 0..Ns_p-1: the threads of a warp
-// (consecutive k) read consecutive entries.  An FP32 entry is a two-float
-// pair (hi, lo) of complex floats, 16 bytes; an FP64 entry one complex double.
+// Pass structure of the row stage's in-place FFT of Nt points (one radix
+// 2/4/8 pass first for the factor left over by radix 16, then radix-16
+// passes; Nt < 16: one pass of radix Nt) and the layout of its twiddle
+// table: for every pass p >= 1 (radix R_p, Ns_p = product of the earlier
+// radices) one block of (R_p - 1) Ns_p factors, entry (r - 1) Ns_p + k =
+// W^(r k Nt / (Ns_p R_p)), W = exp(-2 pi i / Nt), r = 1..R_p-1,
+// k = 0..Ns_p-1: the threads of a warp (consecutive k) read consecutive
+// entries.  An FP32 entry is a two-float pair (hi, lo) of complex floats,
+// 16 bytes; an FP64 entry one complex double.
 __host__ __device__ constexpr int fft_log2(int n) { return n <= 1 ? 0 : 1 + fft_log2(n / 2); }
 __host__ __device__ constexpr int fft_n16(int nt) { return nt >= 16 ? fft_log2(nt) / 4 : 0; }
 __host__ __device__ constexpr int fft_rem(int nt) { return nt >= 16 ? (1 << (fft_log2(nt) % 4)) : nt; }
 __host__ __device__ constexpr int fft_npass(int nt) { return fft_n16(nt) + (fft_rem(nt) > 1 ? 1 : 0); }
-__host__ __device__ constexpr int fft_radix(int nt, int p) { return p < fft_n16(nt) ? 16 : fft_rem(nt); }
+__host__ __device__ constexpr int fft_radix(int nt, int p) {
+    return nt < 16 ? nt : ((fft_rem(nt) > 1 && p == 0) ? fft_rem(nt) : 16);
+}
 __host__ __device__ constexpr int fft_ns(int nt, int p) {
-    return p < fft_n16(nt) ? (1 << (4 * p)) : (1 << (4 * fft_n16(nt)));
+    return nt < 16 ? 1
+                   : (fft_rem(nt) > 1 ? (p == 0 ? 1 : fft_rem(nt) << (4 * (p - 1))) : (1 << (4 * p)));
 }
 __host__ __device__ constexpr int tw_offset(int nt, int p) {
     int o = 0;

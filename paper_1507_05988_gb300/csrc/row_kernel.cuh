@@ -57,12 +57,13 @@ struct RowCfg {
     static constexpr int WARPS_PER_ROW = TPR > 32 ? TPR / 32 : 1;
 };
 
+// Pass P of the transform: radix R (the radix 2/4/8 pass first when Nt is
+// not a power of 16, then radix-16 passes) and Ns, the product of the
+// radices of the earlier passes.
 template <int NT, int P>
 struct PassCfg {
-    using C = RowCfg<NT>;
-    static constexpr int R = (P < C::N16) ? 16 : C::REM;
-    // Ns = product of the radices of the earlier passes
-    static constexpr int NS = (P < C::N16) ? (1 << (4 * P)) : (1 << (4 * C::N16));
+    static constexpr int R = fft_radix(NT, P);
+    static constexpr int NS = fft_ns(NT, P);
 };
 
 __device__ __forceinline__ int pidx(int i, int nt) { return nt >= 16 ? i + (i >> 4) : i; }
@@ -300,16 +301,21 @@ __device__ __forceinline__ void pass_compute_adj(cx<T> (&v)[RowCfg<NT>::E], int 
     }
 }
 
+// Operands of forward pass P (in-place decimation in time): butterfly
+// j = t + TPR i combines the positions base + r NS (r < R), base =
+// (j / NS) NS R + j mod NS, and writes its outputs back to them.
 template <typename T, int NT, int P>
 __device__ __forceinline__ void pass_load(cx<T> (&v)[RowCfg<NT>::E], const cx<T> *S, int t) {
     using C = RowCfg<NT>;
     constexpr int R = PassCfg<NT, P>::R;
+    constexpr int NS = PassCfg<NT, P>::NS;
     constexpr int NB = C::E / R;
 #pragma unroll
     for (int i = 0; i < NB; ++i) {
         const int j = t + C::TPR * i;
+        const int base = (j / NS) * NS * R + (j & (NS - 1));
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[i * R + r] = S[FCN_IDX(pidx(j + r * (NT / R), NT), C::PADN, 1)];
+        for (int r = 0; r < R; ++r) v[i * R + r] = S[FCN_IDX(pidx(base + r * NS, NT), C::PADN, 1)];
     }
 }
 
@@ -329,10 +335,12 @@ __device__ __forceinline__ void pass_store(const cx<T> (&v)[RowCfg<NT>::E], cx<T
 }
 
 // Inverse transform: the exact adjoint of the forward transform, i.e. the
-// forward passes in reverse order, each reading its operands from where the
-// forward pass writes them and writing to where it reads them (input already
-// in registers in the last forward pass's output order; result in S in
-// natural order, unscaled but for sc).
+// forward passes in reverse order, each applying the transposed butterfly
+// and the conjugate twiddles in place (input already in registers in the
+// last forward pass's order, i.e. natural frequency order; result in S in
+// the forward transform's input order, scaled by sc in its last pass).
+// Every pass reads and writes the same positions in the same thread, so one
+// barrier per pass (before other threads read them) suffices.
 template <typename T, int NT, int P, bool DONE>
 struct InvDispatch;
 template <typename T, int NT, int P>
@@ -341,30 +349,14 @@ struct InvDispatch<T, NT, P, false> {
     __device__ __forceinline__ static void run(cx<T> (&v)[RowCfg<NT>::E], cx<T> *S, int t,
                                                const cx<T> *tw, T sc) {
         using C = RowCfg<NT>;
-        constexpr int R = PassCfg<NT, P>::R;
-        constexpr int NS = PassCfg<NT, P>::NS;
-        constexpr int NB = C::E / R;
-        if (P + 1 < C::NPASS) {
-#pragma unroll
-            for (int i = 0; i < NB; ++i) {
-                const int j = t + C::TPR * i;
-                const int base = (j / NS) * NS * R + (j & (NS - 1));
-#pragma unroll
-                for (int r = 0; r < R; ++r) v[i * R + r] = S[FCN_IDX(pidx(base + r * NS, NT), C::PADN, 1)];
-            }
-            __syncthreads();
-        }
+        if (P + 1 < C::NPASS) pass_load<T, NT, P>(v, S, t);
+        asm volatile("" ::: "memory");
         pass_compute_adj<T, NT, P>(v, t, tw);
         if (P == 0) {
 #pragma unroll
             for (int e = 0; e < C::E; ++e) v[e] = mk(v[e].x * sc, v[e].y * sc);
         }
-#pragma unroll
-        for (int i = 0; i < NB; ++i) {
-            const int j = t + C::TPR * i;
-#pragma unroll
-            for (int r = 0; r < R; ++r) S[FCN_IDX(pidx(j + r * (NT / R), NT), C::PADN, 2)] = v[i * R + r];
-        }
+        pass_store<T, NT, P>(v, S, t);
         __syncthreads();
         InvDispatch<T, NT, P - 1, (P < 1)>::run(v, S, t, tw, sc);
     }
@@ -375,6 +367,10 @@ struct InvDispatch<T, NT, P, true> {
                                                const cx<T> *, T) {}
 };
 
+// Forward transform in place: input in S in the digit-reversed order of
+// tpos, output of the last pass (natural frequency order, positions
+// j + r NS) left in registers for the caller.  The caller's barrier before
+// the first pass makes S complete.
 template <typename T, int NT, int P, bool LAST>
 struct FwdDispatch;
 template <typename T, int NT, int P>
@@ -382,7 +378,9 @@ struct FwdDispatch<T, NT, P, false> {
     __device__ __forceinline__ static void run(cx<T> (&v)[RowCfg<NT>::E], cx<T> *S, int t,
                                                const cx<T> *tw) {
         pass_load<T, NT, P>(v, S, t);
-        __syncthreads();
+        // compiler-only fence: the twiddle loads stay behind the operand
+        // loads (issuing them together costs registers the 4-CTA variant lacks)
+        asm volatile("" ::: "memory");
         pass_compute<T, NT, P>(v, t, tw);
         if (P + 1 < RowCfg<NT>::NPASS) {
             pass_store<T, NT, P>(v, S, t);
@@ -396,6 +394,33 @@ struct FwdDispatch<T, NT, P, true> {
     __device__ __forceinline__ static void run(cx<T> (&)[RowCfg<NT>::E], cx<T> *, int,
                                                const cx<T> *) {}
 };
+
+// Padded shared-memory index of the e-th of the E samples a thread owns,
+// whose first sits at unpadded position p0 (tpos): when the sample stride
+// NSL is a multiple of 16 the padding is linear in e, so that the indices
+// are one base plus compile-time offsets.
+template <int NT, int NSL>
+__device__ __forceinline__ int own_idx(int q0, int p0, int e) {
+    if constexpr (NT >= 16 && NSL % 16 == 0) return q0 + e * (NSL + NSL / 16);
+    else return pidx(p0 + e * NSL, NT);
+}
+
+// Position in S of time sample tau.  The forward transform takes its input
+// in mixed-radix digit-reversed order: the least significant digit of tau
+// (radix R of the last pass) is the most significant digit of the position
+// (place value NS of the last pass), and so on.  With the last pass of
+// radix E, a thread's E consecutive samples tau = E t + e sit at
+// tpos(E t) + e NS_last.
+template <int NT>
+__device__ __forceinline__ int tpos(int tau) {
+    int p = 0;
+#pragma unroll
+    for (int s = RowCfg<NT>::NPASS - 1; s >= 0; --s) {
+        p += (tau % fft_radix(NT, s)) * fft_ns(NT, s);
+        tau /= fft_radix(NT, s);
+    }
+    return p;
+}
 
 // ---------------------------------------------------------------------------
 // Nonlinear half step
@@ -641,13 +666,17 @@ __device__ __forceinline__ void nl_half_smem(cx<T> *S, T *U, int t, const NLCoef
                                              double *scr, int rloc) {
     using C = RowCfg<NT>;
     constexpr int E = C::E;
-    const int p0 = E * t;
+    constexpr int NSL = PassCfg<NT, C::NPASS - 1>::NS;
+    static_assert(PassCfg<NT, C::NPASS - 1>::R == E, "a thread's samples differ in the last digit only");
+    // the thread's samples tau = E t + e sit at p0 + e NSL (tpos)
+    const int p0 = tpos<NT>(E * t);
+    const int q0 = pidx(p0, NT);
     const bool last_thread = (t == C::TPR - 1);
     // |A|^2 of the thread's points and of the next thread's first point
     T cn[E + 1];
 #pragma unroll
-    for (int e = 0; e <= E; ++e)
-        cn[e] = (e < E || !last_thread) ? cnorm(S[FCN_IDX(pidx(p0 + e, NT), C::PADN, 8)]) : T(0);
+    for (int e = 0; e < E; ++e) cn[e] = cnorm(S[FCN_IDX((own_idx<NT, NSL>(q0, p0, e)), C::PADN, 8)]);
+    cn[E] = last_thread ? T(0) : cnorm(S[FCN_IDX(pidx(tpos<NT>(E * (t + 1)), NT), C::PADN, 8)]);
     T cmax = T(0);
 #pragma unroll
     for (int e = 0; e < E; ++e) cmax = fmax(cmax, cn[e]);
@@ -704,7 +733,8 @@ __device__ __forceinline__ void nl_half_smem(cx<T> *S, T *U, int t, const NLCoef
         if (phib < T(7.450580596923828e-9) && lnab < T(7.450580596923828e-9)) {
             if (STORE_U && need_u) {
 #pragma unroll
-                for (int e = 0; e < E; ++e) U[FCN_IDX(pidx(p0 + e, NT), C::PADN, 28)] = fma(lp[e], omc, carry);
+                for (int e = 0; e < E; ++e)
+                    U[FCN_IDX((own_idx<NT, NSL>(q0, p0, e)), C::PADN, 28)] = fma(lp[e], omc, carry);
             }
             return;
         }
@@ -716,7 +746,7 @@ __device__ __forceinline__ void nl_half_smem(cx<T> *S, T *U, int t, const NLCoef
         T u[UN];
 #pragma unroll
         for (int k = 0; k < UN; ++k) {
-            const int ip = pidx(p0 + e0 + k, NT);
+            const int ip = own_idx<NT, NSL>(q0, p0, e0 + k);
             x[k] = S[FCN_IDX(ip, C::PADN, 27)];
             u[k] = need_u ? fma(lp[e0 + k], omc, carry) : T(0);
         }
@@ -736,15 +766,16 @@ __device__ __forceinline__ void nl_half_smem(cx<T> *S, T *U, int t, const NLCoef
             // the common case, decided once for the group of points
 #pragma unroll
             for (int k = 0; k < UN; ++k) {
-                if constexpr (sizeof(T) == 4) S[pidx(p0 + e0 + k, NT)] = nl_apply_small(x[k], phi[k], lna[k]);
+                if constexpr (sizeof(T) == 4)
+                    S[own_idx<NT, NSL>(q0, p0, e0 + k)] = nl_apply_small(x[k], phi[k], lna[k]);
             }
         } else {
 #pragma unroll
-            for (int k = 0; k < UN; ++k) S[pidx(p0 + e0 + k, NT)] = nl_apply_general(x[k], phi[k], lna[k]);
+            for (int k = 0; k < UN; ++k) S[own_idx<NT, NSL>(q0, p0, e0 + k)] = nl_apply_general(x[k], phi[k], lna[k]);
         }
         if (STORE_U) {
 #pragma unroll
-            for (int k = 0; k < UN; ++k) U[FCN_IDX(pidx(p0 + e0 + k, NT), C::PADN, 31)] = u[k];
+            for (int k = 0; k < UN; ++k) U[FCN_IDX((own_idx<NT, NSL>(q0, p0, e0 + k)), C::PADN, 31)] = u[k];
         }
     }
 }
@@ -858,7 +889,7 @@ __device__ __forceinline__ void row_body(const RowArgs<T> &a, int row_base, int 
 #pragma unroll
         for (int i = 0; i < E; ++i) {
             const int idx = t + C::TPR * i;
-            S[FCN_IDX(pidx(idx, NT), C::PADN, 5)] = valid ? g[FCN_IDX(idx, NT, 6)] : mk(T(0), T(0));
+            S[FCN_IDX(pidx(tpos<NT>(idx), NT), C::PADN, 5)] = valid ? g[FCN_IDX(idx, NT, 6)] : mk(T(0), T(0));
         }
         __syncthreads();
     }
@@ -890,7 +921,8 @@ __device__ __forceinline__ void row_body(const RowArgs<T> &a, int row_base, int 
                     float mxf = 0.f, muf = 0.f, badf = 0.f;
 #pragma unroll 4
                     for (int e = 0; e < E; ++e) {
-                        const int ip = pidx(E * t + e, NT);
+                        const int ip = own_idx<NT, PassCfg<NT, C::NPASS - 1>::NS>(pidx(tpos<NT>(E * t), NT),
+                                                                                  tpos<NT>(E * t), e);
                         const cx<T> x = S[FCN_IDX(ip, C::PADN, 29)];
                         const float i2 = fmaf(x.x, x.x, x.y * x.y);
                         if (!isfinite(i2)) badf += 1.f;
@@ -905,7 +937,8 @@ __device__ __forceinline__ void row_body(const RowArgs<T> &a, int row_base, int 
                 } else {
 #pragma unroll 4
                     for (int e = 0; e < E; ++e) {
-                        const int ip = pidx(E * t + e, NT);
+                        const int ip = own_idx<NT, PassCfg<NT, C::NPASS - 1>::NS>(pidx(tpos<NT>(E * t), NT),
+                                                                                  tpos<NT>(E * t), e);
                         const cx<T> x = S[FCN_IDX(ip, C::PADN, 29)];
                         const double i2 = double(x.x) * double(x.x) + double(x.y) * double(x.y);
                         if (!isfinite(i2)) v4[3] += 1.0;
@@ -933,7 +966,8 @@ __device__ __forceinline__ void row_body(const RowArgs<T> &a, int row_base, int 
 #pragma unroll
                 for (int i = 0; i < E; ++i) {
                     const int idx = t + C::TPR * i;
-                    rr[FCN_IDX(idx, NT, 12)] = have_u ? U[FCN_IDX(pidx(idx, NT), C::PADN, 30)] * a.nl.rho_nt : T(0);
+                    rr[FCN_IDX(idx, NT, 12)] =
+                        have_u ? U[FCN_IDX(pidx(tpos<NT>(idx), NT), C::PADN, 30)] * a.nl.rho_nt : T(0);
                 }
             }
         }
@@ -941,7 +975,7 @@ __device__ __forceinline__ void row_body(const RowArgs<T> &a, int row_base, int 
 #pragma unroll
             for (int i = 0; i < E; ++i) {
                 const int idx = t + C::TPR * i;
-                g[FCN_IDX(idx, NT, 10)] = S[FCN_IDX(pidx(idx, NT), C::PADN, 11)];
+                g[FCN_IDX(idx, NT, 10)] = S[FCN_IDX(pidx(tpos<NT>(idx), NT), C::PADN, 11)];
             }
         }
     }
