@@ -284,6 +284,11 @@ struct fcn_ctx {
     int multi_mode = 2;
     cudaStream_t bst[kMaxBranches] = {};
     cudaEvent_t fork_ev = nullptr, join_ev[kMaxBranches] = {};
+    // pivot tables built off the launch stream (adaptive steps need two new
+    // tables per attempt, for dz and dz/2): streams, "launch stream reached
+    // here" events and "table ready" events
+    cudaStream_t tside[2] = {};
+    cudaEvent_t tbefore[2] = {}, tready[2] = {};
     std::vector<Pulse> pulses;
     std::map<GraphKey, cudaGraphExec_t> graphs;
     std::map<TableKey, TableEntry> tables;   // shared pivot tables
@@ -353,8 +358,15 @@ size_t coef_offset(int nr, int nt) {
     return (b + 255) / 256 * 256;
 }
 
+// The pivot table of (grid, dz), built on first use.  side = -1 builds it on
+// the launch stream; side = 0 or 1 builds it on a side stream (after all
+// work already queued on the launch stream, which may still read an evicted
+// buffer) and sets *ready to an event that the launch stream must wait on
+// before the table is read (null when the table was cached).
 template <typename T>
-int ensure_table(fcn_ctx *ctx, Pulse &pu, double dz, const cx<T> **out) {
+int ensure_table(fcn_ctx *ctx, Pulse &pu, double dz, const cx<T> **out, int side = -1,
+                 cudaEvent_t *ready = nullptr) {
+    if (ready) *ready = nullptr;
     TableKey key;
     key.nr = pu.g.nr;
     key.nt = pu.g.nt;
@@ -414,9 +426,25 @@ int ensure_table(fcn_ctx *ctx, Pulse &pu, double dz, const cx<T> **out) {
     ta.dk = dk;
     ta.lo = pu.lo64;
     ta.hi = pu.hi64;
-    CK(launch_cn_table<T>(ta, (cx<T> *)d, ctx->st), "pivot table kernel");
-    CK(launch_cn_coef<T>(ta, (CnCoef<T> *)((char *)d + coef_offset<T>(pu.g.nr, pu.g.nt)), ctx->st),
+    cudaStream_t bs = ctx->st;
+    if (side >= 0) {
+        if (!ctx->tside[side]) {
+            CK(cudaStreamCreateWithFlags(&ctx->tside[side], cudaStreamNonBlocking), "table stream");
+            CK(cudaEventCreateWithFlags(&ctx->tbefore[side], cudaEventDisableTiming), "table event");
+            CK(cudaEventCreateWithFlags(&ctx->tready[side], cudaEventDisableTiming), "table event");
+        }
+        bs = ctx->tside[side];
+        CK(cudaEventRecord(ctx->tbefore[side], ctx->st), "table event");
+        CK(cudaStreamWaitEvent(bs, ctx->tbefore[side], 0), "table wait");
+    }
+    CK(launch_cn_table<T>(ta, (cx<T> *)d, bs), "pivot table kernel");
+    CK(launch_cn_coef<T>(ta, (CnCoef<T> *)((char *)d + coef_offset<T>(pu.g.nr, pu.g.nt)), bs),
        "row coefficient kernel");
+    if (side >= 0) {
+        CK(cudaEventRecord(ctx->tready[side], bs), "table event");
+        if (ready) *ready = ctx->tready[side];
+        else CK(cudaStreamWaitEvent(ctx->st, ctx->tready[side], 0), "table wait");
+    }
     ctx->tables[key] = TableEntry{d, dz_key(dz), ++ctx->table_clock, need};
     *out = (const cx<T> *)d;
     return FCN_OK;
@@ -960,16 +988,21 @@ int step_impl(fcn_ctx *ctx, double dz, int64_t n, bool use_graph) {
 
 // One Strang step of length h (or two of h/2) on a work buffer, direct launches.
 template <typename T>
-int substeps(fcn_ctx *ctx, Pulse &pu, void *f, double h, int count) {
-    const cx<T> *tab = nullptr;
-    int rc = ensure_table<T>(ctx, pu, h, &tab);
-    if (rc) return rc;
+int substeps(fcn_ctx *ctx, Pulse &pu, void *f, double h, int count, const cx<T> *tab = nullptr,
+             cudaEvent_t table_ready = nullptr) {
+    if (!tab) {
+        int rc = ensure_table<T>(ctx, pu, h, &tab);
+        if (rc) return rc;
+    }
     if (!pu.tuned) {
         std::vector<const cx<T> *> tabs(ctx->pulses.size(), tab);
-        rc = ensure_tuned<T>(ctx, tabs, h);
+        int rc = ensure_tuned<T>(ctx, tabs, h);
         if (rc) return rc;
     }
     CK(launch_rows<T>(row_args<T>(pu, f, OPS_HEAD, h), pu.g.nt, ctx->st), "head");
+    // the opening row stage does not read the table: a table built on a side
+    // stream has until here
+    if (table_ready) CK(cudaStreamWaitEvent(ctx->st, table_ready, 0), "table wait");
     for (int i = 0; i < count; ++i) {
         CK(launch_cn<T>(col_args<T>(pu, f, tab, h), ctx->st), "column");
         const int ops = (i + 1 < count) ? OPS_MID : OPS_TAIL;
@@ -1093,10 +1126,18 @@ int propagate_impl(fcn_ctx *ctx, double z_end, double dz0, double rtol, double d
         double h = dz;
         bool last = false;
         if (pu.z + h >= z_end) { h = z_end - pu.z; last = true; }
+        // the pivot tables of h and h/2 (new at almost every attempt) build on
+        // side streams, side by side and behind the copies and opening row
+        // stages; the column stages wait for them
+        const cx<T> *tab1 = nullptr, *tab2 = nullptr;
+        cudaEvent_t ev1 = nullptr, ev2 = nullptr;
+        int rc = ensure_table<T>(ctx, pu, h, &tab1, 0, &ev1);
+        if (!rc) rc = ensure_table<T>(ctx, pu, 0.5 * h, &tab2, 1, &ev2);
+        if (rc) return rc;
         CK(cudaMemcpyAsync(pu.work1, pu.field, bytes, cudaMemcpyDeviceToDevice, ctx->st), "copy");
         CK(cudaMemcpyAsync(pu.work2, pu.field, bytes, cudaMemcpyDeviceToDevice, ctx->st), "copy");
-        int rc = substeps<T>(ctx, pu, pu.work1, h, 1);
-        if (!rc) rc = substeps<T>(ctx, pu, pu.work2, 0.5 * h, 2);
+        rc = substeps<T>(ctx, pu, pu.work1, h, 1, tab1, ev1);
+        if (!rc) rc = substeps<T>(ctx, pu, pu.work2, 0.5 * h, 2, tab2, ev2);
         if (rc) return rc;
         CK(launch_diff_norm<T>((const cx<T> *)pu.work1, (const cx<T> *)pu.work2, pu.g.nr, pu.g.nt,
                                pu.rows, pu.red, ctx->st), "error norm");
@@ -1350,6 +1391,11 @@ void fcn_destroy(fcn_ctx *ctx) {
     for (int b = 0; b < kMaxBranches; ++b) {
         if (ctx->bst[b]) cudaStreamDestroy(ctx->bst[b]);
         if (ctx->join_ev[b]) cudaEventDestroy(ctx->join_ev[b]);
+    }
+    for (int k = 0; k < 2; ++k) {
+        if (ctx->tside[k]) cudaStreamDestroy(ctx->tside[k]);
+        if (ctx->tbefore[k]) cudaEventDestroy(ctx->tbefore[k]);
+        if (ctx->tready[k]) cudaEventDestroy(ctx->tready[k]);
     }
     if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
     if (ctx->cap) cudaStreamDestroy(ctx->cap);
