@@ -989,7 +989,7 @@ int step_impl(fcn_ctx *ctx, double dz, int64_t n, bool use_graph) {
 // One Strang step of length h (or two of h/2) on a work buffer, direct launches.
 template <typename T>
 int substeps(fcn_ctx *ctx, Pulse &pu, void *f, double h, int count, const cx<T> *tab = nullptr,
-             cudaEvent_t table_ready = nullptr) {
+             cudaEvent_t table_ready = nullptr, int tail_extra = 0) {
     if (!tab) {
         int rc = ensure_table<T>(ctx, pu, h, &tab);
         if (rc) return rc;
@@ -1005,7 +1005,7 @@ int substeps(fcn_ctx *ctx, Pulse &pu, void *f, double h, int count, const cx<T> 
     if (table_ready) CK(cudaStreamWaitEvent(ctx->st, table_ready, 0), "table wait");
     for (int i = 0; i < count; ++i) {
         CK(launch_cn<T>(col_args<T>(pu, f, tab, h), ctx->st), "column");
-        const int ops = (i + 1 < count) ? OPS_MID : OPS_TAIL;
+        const int ops = (i + 1 < count) ? OPS_MID : (OPS_TAIL | tail_extra);
         CK(launch_rows<T>(row_args<T>(pu, f, ops, h), pu.g.nt, ctx->st), "row");
     }
     return FCN_OK;
@@ -1137,10 +1137,33 @@ int propagate_impl(fcn_ctx *ctx, double z_end, double dz0, double rtol, double d
         CK(cudaMemcpyAsync(pu.work1, pu.field, bytes, cudaMemcpyDeviceToDevice, ctx->st), "copy");
         CK(cudaMemcpyAsync(pu.work2, pu.field, bytes, cudaMemcpyDeviceToDevice, ctx->st), "copy");
         rc = substeps<T>(ctx, pu, pu.work1, h, 1, tab1, ev1);
-        if (!rc) rc = substeps<T>(ctx, pu, pu.work2, 0.5 * h, 2, tab2, ev2);
+        // with features, the closing launch of the two half steps also gives
+        // the statistics and spectral moments of the field it leaves, so the
+        // features and the proposal of an accepted attempt need no pass of
+        // their own
+        const bool next_feat = features && !last;
+        if (!rc) rc = substeps<T>(ctx, pu, pu.work2, 0.5 * h, 2, tab2, ev2,
+                                  next_feat ? (OP_FFT | OP_SPEC | OP_SPEC_OF_TIME) : 0);
         if (rc) return rc;
         CK(launch_diff_norm<T>((const cx<T> *)pu.work1, (const cx<T> *)pu.work2, pu.g.nr, pu.g.nt,
                                pu.rows, pu.red, ctx->st), "error norm");
+        if (next_feat) {
+            // speculative: the features of work2 and the proposal after it,
+            // used only if the attempt is accepted
+            sc.peak_prev = hfeat[6];
+            sc.dz_prev = h;
+            sc.dz_lo = std::fmax(0.2 * h, dz_min);
+            sc.dz_hi = 2.0 * h;
+            CK(launch_reduce_stats(pu.stats, pu.g.nr, pu.red + 8, ctx->st), "feature reduction");
+            CK(launch_mlp_propose(pu.red + 8, sc, controller == 1 ? ctx->mlp : nullptr, feat_d, dz_d, ctx->st,
+                                  pu.red),
+               "features");
+            CK(cudaMemcpyAsync(ctx->host_red + 8, feat_d, 7 * sizeof(float), cudaMemcpyDeviceToHost, ctx->st),
+               "features copy");
+            if (controller == 1)
+                CK(cudaMemcpyAsync(ctx->host_red + 12, dz_d, sizeof(double), cudaMemcpyDeviceToHost, ctx->st),
+                   "proposal copy");
+        }
         CK(cudaMemcpyAsync(ctx->host_red, pu.red, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->st),
            "norm copy");
         CK(cudaStreamSynchronize(ctx->st), "norm sync");
@@ -1167,15 +1190,13 @@ int propagate_impl(fcn_ctx *ctx, double z_end, double dz0, double rtol, double d
             if (from_mlp) s.mlp_proposals++;
             consecutive = 0;
             dz = last ? dz : h * fac;
-            if (features && pu.z < z_end) {
-                sc.peak_prev = hfeat[6];
-                sc.dz_prev = h;
+            if (next_feat) {
+                std::memcpy(hfeat, ctx->host_red + 8, 7 * sizeof(float));
                 sc.err_prev = err;
-                sc.dz_lo = std::fmax(0.2 * h, dz_min);
-                sc.dz_hi = 2.0 * h;
-                rc = features_of_field(controller == 1);
-                if (rc) return rc;
-                if (controller == 1 && std::isfinite(mlp_dz) && mlp_dz > 0) dz = mlp_dz;
+                if (controller == 1) {
+                    mlp_dz = ctx->host_red[12];
+                    if (std::isfinite(mlp_dz) && mlp_dz > 0) dz = mlp_dz;
+                }
             }
             from_mlp = controller == 1 && features && pu.z < z_end;
         } else {

@@ -113,7 +113,10 @@ enum : int {
     OP_IFFT = 1, OP_NL = 2, OP_NL2 = 4, OP_FFT = 8, OP_RHO = 16,
     OP_STATS = 32,   // per-row FP64 statistics of the final time-domain row
     OP_SPEC = 64,    // spectral moments of the final time-domain row (no store)
-    OP_NOSTORE = 128 // do not write the field back (diagnostics only)
+    OP_NOSTORE = 128, // do not write the field back (diagnostics only)
+    // with OP_FFT | OP_SPEC: store the time-domain row as without OP_FFT and
+    // transform it only for the spectral moments (the spectrum is not stored)
+    OP_SPEC_OF_TIME = 256
 };
 
 // Coefficients of one nonlinear half step in scaled intensity units
@@ -295,9 +298,11 @@ int mlp_nparam();
 cudaError_t launch_mlp_grad(const float *W, const float *X, const float *Y, const int *idx, int n,
                             float *partial, int max_cta, float *grad, float *loss, cudaStream_t st);
 cudaError_t launch_mlp_adam(float *W, float *m, float *v, const float *g, float lr, int t, cudaStream_t st);
-// features (7 floats: f0..f5 and the peak intensity) and, with W, dz_out
+// features (7 floats: f0..f5 and the peak intensity) and, with W, dz_out;
+// with norm non-null the error of f5 is sqrt(norm[0] / norm[1]) (the step-
+// doubling norm on the device) instead of sc.err_prev
 cudaError_t launch_mlp_propose(const double *red, const MlpScalars &sc, const float *W, float *features,
-                               double *dz_out, cudaStream_t st);
+                               double *dz_out, cudaStream_t st, const double *norm = nullptr);
 
 // reductions and conversions
 template <typename T>

@@ -158,10 +158,11 @@ __global__ void mlp_adam(float *W, float *m, float *v, const float *__restrict__
 // launch_reduce_stats) and the controller's scalars; with W non-null also
 // the MLP's proposal dz = L_ref exp(f4 - f5/3 + y), clamped to [lo, hi].
 __global__ void mlp_propose(const double *__restrict__ red, MlpScalars sc, const float *__restrict__ W,
-                            float *features, double *dz_out) {
+                            float *features, double *dz_out, const double *__restrict__ norm) {
     __shared__ float sw[NP];
     __shared__ float sx[NIN], h1[NH], h2[NH], r[2];
     if (threadIdx.x == 0) {
+        if (norm) sc.err_prev = norm[1] > 0 ? sqrt(norm[0] / norm[1]) : sqrt(norm[0]);
         const double peak = red[1];
         const double s0 = red[4];
         double rms = 0.0;
@@ -221,8 +222,8 @@ cudaError_t launch_mlp_adam(float *W, float *m, float *v, const float *g, float 
 }
 
 cudaError_t launch_mlp_propose(const double *red, const MlpScalars &sc, const float *W, float *features,
-                               double *dz_out, cudaStream_t st) {
-    mlp_propose<<<1, NH, 0, st>>>(red, sc, W, features, dz_out);
+                               double *dz_out, cudaStream_t st, const double *norm) {
+    mlp_propose<<<1, NH, 0, st>>>(red, sc, W, features, dz_out, norm);
     return cudaGetLastError();
 }
 

@@ -971,13 +971,15 @@ __device__ __forceinline__ void row_body(const RowArgs<T> &a, int row_base, int 
                 }
             }
         }
-        if (!(ops & OP_FFT) && !(ops & OP_NOSTORE) && valid) {
+        if ((!(ops & OP_FFT) || (ops & OP_SPEC_OF_TIME)) && !(ops & OP_NOSTORE) && valid) {
 #pragma unroll
             for (int i = 0; i < E; ++i) {
                 const int idx = t + C::TPR * i;
                 g[FCN_IDX(idx, NT, 10)] = S[FCN_IDX(pidx(tpos<NT>(idx), NT), C::PADN, 11)];
             }
         }
+        // the in-place transform below overwrites S: every thread's store first
+        if (ops & OP_SPEC_OF_TIME) __syncthreads();
     }
 
     if (ops & OP_FFT) {
@@ -987,7 +989,7 @@ __device__ __forceinline__ void row_body(const RowArgs<T> &a, int row_base, int 
         constexpr int R = PassCfg<NT, PL>::R;
         constexpr int NS = PassCfg<NT, PL>::NS;
         constexpr int NB = E / R;
-        if (!(ops & OP_NOSTORE) && valid) {
+        if (!(ops & (OP_NOSTORE | OP_SPEC_OF_TIME)) && valid) {
 #pragma unroll
             for (int i = 0; i < NB; ++i) {
                 const int j = t + C::TPR * i;
