@@ -9,16 +9,19 @@
 // Nt = 8192 runs on 512 threads.  Each thread owns E = 16 complex values
 // (E = Nt when Nt < 16).
 //
-// Transform: self-sorting Stockham FFT (radix-16 passes, then one radix 2/4/8
-// pass for the remaining factor), done in place in one padded shared-memory
-// buffer with the butterfly operands in registers.  The inverse transform is
-// the exact adjoint of the forward one (the forward passes in reverse order,
-// transposed, with conjugate constants).  The first inverse pass reads HBM
-// directly and the last forward pass writes HBM directly, in the same order;
-// both are coalesced (consecutive threads touch consecutive complex values).  Shared
-// memory rows are padded by one value per 16 so that the strided Stockham
-// stores and the contiguous per-thread reads of the nonlinear stage are free
-// of bank conflicts.
+// Transform: in-place decimation-in-time FFT (one radix 2/4/8 pass for the
+// factor left by radix 16, then radix-16 passes) in one padded shared-memory
+// buffer with the butterfly operands in registers; every pass reads and
+// writes the same positions in the same thread, so one barrier per pass
+// suffices.  The forward transform takes the time samples in mixed-radix
+// digit-reversed order (tpos) and leaves natural frequency order; the
+// inverse transform is its exact adjoint (the forward passes in reverse
+// order, transposed, with conjugate constants).  The first inverse pass
+// reads HBM directly and the last forward pass writes HBM directly, in
+// natural frequency order; both are coalesced (consecutive threads touch
+// consecutive complex values).  Shared-memory rows are padded by one value
+// per 16 so that the passes and the nonlinear stage's per-thread samples are
+// free of bank conflicts.
 //
 // Nonlinear half step (Eq. (nonlinearpart)):  A <- A exp(h N(I, rho)).
 // rho(tau) follows Eq. (ionization) integrated by RK4 along tau from
