@@ -219,7 +219,8 @@ int fcn_set_variants(fcn_ctx *ctx, int32_t row_variant, int32_t col_variant);
  * Nt >= 512): mode 1 runs each stage of all pulses as one persistent launch
  * over (pulse, rows) and (pulse, column group) items; 0 launches each pulse
  * separately (tuned per-Nt kernels, all inside one CUDA graph); -1 (the
- * default) uses the work lists when the pulses' grids differ.  Drops the
+ * default) uses the work lists when the grids differ and most points lie in
+ * pulses too small to fill the GPU with a launch of their own.  Drops the
  * captured graphs.  FCN_ERR_UNSUPPORTED if mode 1 is not possible. */
 int fcn_set_batching(fcn_ctx *ctx, int32_t mode);
 

@@ -594,6 +594,26 @@ def test_batched_uneven_grids_match_the_oracle(fcn):
         assert rel_l2(outs8[i], ref8) < 1e-5, w.name
 
 
+def test_automatic_batching_follows_pulse_size(fcn):
+    """Uneven grids: work lists when most points sit in pulses too small to
+    fill the GPU with their own launch, per-pulse launches when a large pulse
+    dominates."""
+    small = _batch_workloads()[:3]
+    big = [W.small(700, 4096, p_over_pcr=3.0, noise_seed=70), W.small(40, 512, p_over_pcr=3.0, noise_seed=71)]
+    counts = {}
+    for name, wls in (("small", small), ("big", big)):
+        s = fcn.Solver([w.physics() for w in wls], precision=FP32)
+        for i, w in enumerate(wls):
+            s.set_field(w.field(), pulse=i)
+        s.profile(True)
+        s.step(2e-3, 2)
+        counts[name] = s.profile_read()["row_head"][1]
+        s.profile(False)
+        s.close()
+    assert counts["small"] == 1           # one work-list launch for all pulses
+    assert counts["big"] == 2             # one launch per pulse
+
+
 def test_batching_modes_agree(fcn):
     """Work lists (one launch per stage) and per-pulse launches compute the
     same steps; identical grids default to per-pulse launches."""
