@@ -35,6 +35,7 @@ PLASMA = 8
 MPI = 16
 MPI_SAT = 32
 PRINTED_CJ = 64
+EXACT_DISPERSION = 128
 ALL_PHYSICS = DIFFRACTION | DISPERSION | KERR | PLASMA | MPI
 
 

@@ -172,6 +172,8 @@ int orc_thomas(int n, const double *ad, const double *bd, const double *cd,
  *   1<=j<=nr-2 : a = -is(1 - 1/2j), b = 1 + 2is - i delta, c = -is(1 + 1/2j)
  *                d =  is(1 - 1/2j), e = 1 - 2is + i delta, f =  is(1 + 1/2j)
  *   row nr-1   : b = 1, a = c = d = e = f = 0       (A = 0 at r = R)
+ * (delta_q = 0 under ORC_EXACT_DISPERSION, whose exact factor cn_column
+ * applies after the solve.)
  * The row-0 entries come from the r -> 0 limit Delta_perp -> 2 d^2/dr^2 with
  * the mirror point A_{-1} = A_1 (dA/dr = 0 at r = 0, Eq. (bound)). */
 void orc_cn_coeffs(const orc_problem *pb, double dz, int q,
@@ -185,7 +187,9 @@ void orc_cn_coeffs(const orc_problem *pb, double dz, int q,
     double k0 = orc_k0(pb);
     double s = (pb->flags & ORC_DIFFRACTION) ? dz / (4.0 * k0 * dr * dr) : 0.0;
     double w = orc_omega(pb, q);
-    double delta = (pb->flags & ORC_DISPERSION) ? pb->k2 * w * w * dz / 4.0 : 0.0;
+    /* with ORC_EXACT_DISPERSION the CN system carries diffraction alone */
+    double delta = ((pb->flags & ORC_DISPERSION) && !(pb->flags & ORC_EXACT_DISPERSION))
+                       ? pb->k2 * w * w * dz / 4.0 : 0.0;
 
     a[0] = 0;
     b[0] = 1.0 + I * (4.0 * s) - I * delta;
@@ -309,7 +313,14 @@ static int cn_column(const orc_problem *pb, double dz, cplx *A, int q, cplx *co)
     }
     int rc = orc_thomas(nr, (double *)a, (double *)b, (double *)c,
                         (double *)rhs, (double *)col);
-    for (int j = 0; j < nr; ++j) A[(size_t)j * nt + q] = col[j];
+    cplx ph = 1.0;
+    if ((pb->flags & ORC_DISPERSION) && (pb->flags & ORC_EXACT_DISPERSION)) {
+        /* exact dispersion over dz: dA~/dz = (i k''/2) omega^2 A~ from the
+           -(i k''/2) d^2/dtau^2 term of Eq. (linearpart) */
+        double w = orc_omega(pb, q);
+        ph = cexp(I * (pb->k2 * w * w * dz / 2.0));
+    }
+    for (int j = 0; j < nr; ++j) A[(size_t)j * nt + q] = ph * col[j];
     return rc;
 }
 

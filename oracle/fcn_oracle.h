@@ -39,6 +39,11 @@ extern "C" {
 #define ORC_PRINTED_CJ   64u   /* use c_j, f_j exactly as printed in Sec. 3
                                   (factor 1 - 1/(2j)); only for demonstrating
                                   that the pins reject that reading          */
+#define ORC_EXACT_DISPERSION 128u /* variant of reading R7: the CN system for
+                                  diffraction alone, then each frequency
+                                  column times its exact dispersion factor
+                                  exp(i k'' omega_q^2 dz / 2) (the two linear
+                                  operators act on r and on omega and commute) */
 
 typedef struct {
     int    nr;          /* radial points, >= 3; dr = r_max / (nr - 1)      */

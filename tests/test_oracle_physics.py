@@ -84,6 +84,41 @@ def test_gvd_broadening_matches_closed_form():
     assert width == pytest.approx(tp * np.sqrt(1 + (2 * k2 * 2.0 / tp ** 2) ** 2), rel=1e-5)
 
 
+def test_exact_dispersion_matches_continuous_gvd():
+    """Dispersion as its exact factor (variant of reading R7): a Gaussian
+    exp(-tau^2/tp^2) under dA/dz = -(i k''/2) d^2A/dtau^2 (Eq. (linearpart))
+    is tp / sqrt(tp^2 - 2 i k'' z) exp(-tau^2 / (tp^2 - 2 i k'' z)) at z,
+    which a wide periodic window reproduces to rounding; the CN form (the
+    Cayley factor per step) does not."""
+    tp = 100e-15
+    k2 = tp ** 2 / 2.0                       # dispersion length 1 m
+    wl = W.Workload("gvd", nr=3, nt=1024, w0=1e-3, tp=tp, p_over_pcr=1.0, t_window=64 * tp)
+    z, n = 1.5, 150
+    tau = -wl.t_window / 2 + np.arange(wl.nt) * (wl.t_window / wl.nt)
+    T2 = tp ** 2 - 2j * k2 * z
+    exact = np.sqrt(wl.i0) * tp / np.sqrt(T2) * np.exp(-tau ** 2 / T2)
+    pb = _pb(wl, flags=W.DISPERSION | oracle.EXACT_DISPERSION, k2=k2)
+    A, _ = oracle.run(pb, z / n, n, wl.field())
+    assert rel_l2(A[0], exact) < 1e-11
+    cn, _ = oracle.run(_pb(wl, flags=W.DISPERSION, k2=k2), z / n, n, wl.field())
+    assert rel_l2(cn[0], exact) > 1e-6       # the CN form carries its O(dz^2) phase error
+
+
+def test_exact_dispersion_keeps_the_energy_with_diffraction():
+    """Diffraction (CN, unitary in the radial weight) and the exact
+    dispersion factor (unit modulus) together conserve the discrete energy;
+    the result differs from the CN form by the CN's dispersion phase error."""
+    wl = W.small(48, 64, p_over_pcr=3.0).with_(tp=30e-15, t_window=480e-15)
+    A0 = wl.field()
+    A0[-1] = 0
+    flags = W.DIFFRACTION | W.DISPERSION | W.KERR | W.PLASMA
+    pb = _pb(wl, flags=flags | oracle.EXACT_DISPERSION, k2=2e-27)
+    A, _ = oracle.run(pb, 1e-2, 100, A0)
+    assert abs(oracle.diag(pb, A)["energy"] / oracle.diag(pb, A0)["energy"] - 1) < 1e-12
+    B, _ = oracle.run(_pb(wl, flags=flags, k2=2e-27), 1e-2, 100, A0)
+    assert rel_l2(A, B) > 1e-6
+
+
 def _waist(pb, A):
     r = np.arange(pb.nr) * pb.dr
     w = _weights(pb.nr)
