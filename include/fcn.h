@@ -54,6 +54,12 @@ extern "C" {
 #define FCN_MPI          16u   /* -(beta_K/2)|A|^(2K-2) of Eq. (nonlinearpart)          */
 #define FCN_MPI_SAT      32u   /* optional extra factor (1 - rho/rho_nt) on the loss    */
 #define FCN_ALL_PHYSICS  31u
+/* Variant of the dispersion term (with FCN_DISPERSION): the Crank-Nicolson
+ * system carries diffraction alone and every frequency column is multiplied
+ * by the exact factor exp(i k'' omega_q^2 dz / 2) of the -(i k''/2) d^2/dt^2
+ * term of Eq. (linearpart), instead of the term sitting on the CN diagonal
+ * (the two operators act on r and on omega and commute). */
+#define FCN_EXACT_DISPERSION 128u
 
 /* ---- working precision ---- */
 #define FCN_FP64        0      /* complex128 everywhere                                   */

@@ -257,6 +257,41 @@ __device__ __forceinline__ cx<T> chunk_scan(cx<T> A, cx<T> B, int C, int col, cx
 // One CTA solves columns [g C, g C + C) of one pulse; blockDim.x >= C P
 // (P = chunks per column), threads beyond C P hold empty chunks.  Every
 // thread of the CTA must call it (barriers inside).
+// Exact dispersion factor exp(2 i disp qq^2) of column q (FCN_EXACT_DISPERSION;
+// disp = 0: none).  Computed in FP64 once per thread; in FP32 applied as a
+// two-float pair (hi + lo) inside the FMAs, so that its rounding does not
+// act identically at every step.
+template <typename T>
+struct DispPhase {
+    cx<T> hi, lo;
+    bool on;
+};
+template <typename T>
+__device__ __forceinline__ DispPhase<T> disp_phase(double disp, int qq) {
+    DispPhase<T> p;
+    p.on = disp != 0.0;
+    p.hi = mk(T(1), T(0));
+    p.lo = czero<T>();
+    if (p.on) {
+        double sn, cs;
+        sincos(2.0 * disp * (double)qq * (double)qq, &sn, &cs);
+        p.hi = mk(T(cs), T(sn));
+        p.lo = mk(T(cs - (double)p.hi.x), T(sn - (double)p.hi.y));
+    }
+    return p;
+}
+template <typename T>
+__device__ __forceinline__ cx<T> disp_apply(cx<T> x, const DispPhase<T> &p) {
+    if (!p.on) return x;
+    if constexpr (sizeof(T) == 4) {
+        const float lre = fmaf(x.x, p.lo.x, -x.y * p.lo.y);
+        const float lim = fmaf(x.x, p.lo.y, x.y * p.lo.x);
+        return mk(fmaf(x.x, p.hi.x, fmaf(-x.y, p.hi.y, lre)), fmaf(x.x, p.hi.y, fmaf(x.y, p.hi.x, lim)));
+    } else {
+        return cmul(x, p.hi);
+    }
+}
+
 template <typename T, int L>
 __device__ __forceinline__ void cn_body(const ColArgs<T> &a, int C, int g, unsigned char *smem_raw) {
     const int nwarp = blockDim.x >> 5;
@@ -349,6 +384,7 @@ __device__ __forceinline__ void cn_body(const ColArgs<T> &a, int C, int g, unsig
     // backward sweep, pass 2 and store
     {
         cx<T> xn = chunk_scan<T, true>(QA, QB, C, col, smA, smB, smC);
+        const DispPhase<T> ph = disp_phase<T>(a.disp, qq);
 #pragma unroll
         for (int k = L - 1; k >= 0; --k) {
             const int j = j0 + k;
@@ -356,7 +392,7 @@ __device__ __forceinline__ void cn_body(const ColArgs<T> &a, int C, int g, unsig
                 const cx<T> gamma = (j == 0) ? cmul_i(inv[k], T(4) * s)
                                   : (j < nr - 1) ? cmul_i(inv[k], s * a.hi[j]) : czero<T>();
                 xn = cmul(gamma, xn) + y[k];
-                a.field[FCN_IDX((size_t)j * nt + q, (size_t)nr * nt, 37)] = xn;
+                a.field[FCN_IDX((size_t)j * nt + q, (size_t)nr * nt, 37)] = disp_apply(xn, ph);
             }
         }
     }
@@ -593,12 +629,13 @@ __device__ __forceinline__ void cn_staged_body(const ColArgs<T> &a, int C, int g
     }
     // backward sweep, pass 2 and store
     cx<T> xn = chunk_scan<T, true>(QA, QB, C, col, smA, smB, smC);
+    const DispPhase<T> ph = disp_phase<T>(a.disp, qq);
     cx<T> *fo = a.field + (size_t)j0 * nt + q;
 #pragma unroll
     for (int k = L - 1; k >= 0; --k) {
         const int j = j0 + k;
         xn = cmul(Gt[k * BD], xn) + y[k];
-        if (j < nr) fo[FCN_IDX((size_t)k * nt, (size_t)(nr - j0) * nt, 47)] = xn;
+        if (j < nr) fo[FCN_IDX((size_t)k * nt, (size_t)(nr - j0) * nt, 47)] = disp_apply(xn, ph);
         asm volatile("" ::: "memory");
     }
 }
@@ -842,6 +879,7 @@ __device__ __forceinline__ void cn_pair_body(const ColArgs<T> &a, cx<T> *field2,
     }
     cx<T> xn[2];
     chunk_scan_n<T, true, 2>(QA, QB, C, col, smA, smB, smC, xn);
+    const DispPhase<T> ph = disp_phase<T>(a.disp, qq);
     cx<T> *fo1 = a.field + (size_t)j0 * nt + q;
     cx<T> *fo2 = field2 + (size_t)j0 * nt + q;
 #pragma unroll
@@ -851,8 +889,8 @@ __device__ __forceinline__ void cn_pair_body(const ColArgs<T> &a, cx<T> *field2,
         xn[0] = cmul(ga, xn[0]) + y1[k];
         xn[1] = cmul(ga, xn[1]) + y2[k];
         if (j < nr) {
-            fo1[FCN_IDX((size_t)k * nt, (size_t)(nr - j0) * nt, 63)] = xn[0];
-            fo2[FCN_IDX((size_t)k * nt, (size_t)(nr - j0) * nt, 64)] = xn[1];
+            fo1[FCN_IDX((size_t)k * nt, (size_t)(nr - j0) * nt, 63)] = disp_apply(xn[0], ph);
+            fo2[FCN_IDX((size_t)k * nt, (size_t)(nr - j0) * nt, 64)] = disp_apply(xn[1], ph);
         }
         asm volatile("" ::: "memory");
     }

@@ -52,7 +52,7 @@ int check_grid_params(int prec, const fcn_grid *g, const fcn_params *p, std::str
     if (!(g->t_window > 0) || !std::isfinite(g->t_window)) { *why = "t_window must be > 0"; return FCN_ERR_ARG; }
     if (!(p->lambda0 > 0) || !(p->n0 > 0)) { *why = "lambda0 and n0 must be > 0"; return FCN_ERR_ARG; }
     if (p->K < 1 || p->K > 16) { *why = "K must be in 1..16"; return FCN_ERR_ARG; }
-    if (p->flags & ~63u) { *why = "unknown physics flag"; return FCN_ERR_ARG; }
+    if (p->flags & ~(63u | FCN_EXACT_DISPERSION)) { *why = "unknown physics flag"; return FCN_ERR_ARG; }
     if (!(p->sigma_k >= 0) || !(p->rho_nt >= 0) || !std::isfinite(p->k2)) {
         *why = "sigma_k, rho_nt must be >= 0 and k2 finite"; return FCN_ERR_ARG;
     }
@@ -112,10 +112,17 @@ NLCoef<T> nl_coef(const fcn_grid &g, const fcn_params &p, double h) {
     return n;
 }
 
-void cn_coefs(const fcn_grid &g, const fcn_params &p, double dz, double *s, double *dk) {
+// s and dk of the CN system (delta_q = dk q^2 on its diagonal); with
+// FCN_EXACT_DISPERSION dk = 0 and *disp receives the coefficient of the exact
+// factor exp(2 i disp q^2) the column stage applies instead.
+void cn_coefs(const fcn_grid &g, const fcn_params &p, double dz, double *s, double *dk,
+              double *disp = nullptr) {
     const Consts c = derive(g, p);
     *s = (p.flags & FCN_DIFFRACTION) ? dz / (4.0 * c.k0 * c.dr * c.dr) : 0.0;
-    *dk = (p.flags & FCN_DISPERSION) ? p.k2 * dz / 4.0 * c.domega * c.domega : 0.0;
+    const double d = (p.flags & FCN_DISPERSION) ? p.k2 * dz / 4.0 * c.domega * c.domega : 0.0;
+    const bool exact = (p.flags & FCN_EXACT_DISPERSION) != 0;
+    *dk = exact ? 0.0 : d;
+    if (disp) *disp = exact ? d : 0.0;
 }
 
 // ---- process-wide constant tables (twiddles, radial ratios) ----
@@ -475,10 +482,11 @@ ColArgs<T> col_args(Pulse &pu, void *field, const cx<T> *table, double dz) {
     a.hi = (const T *)pu.hi;
     a.nr = pu.g.nr;
     a.nt = pu.g.nt;
-    double s, dk;
-    cn_coefs(pu.g, pu.p, dz, &s, &dk);
+    double s, dk, disp;
+    cn_coefs(pu.g, pu.p, dz, &s, &dk, &disp);
     a.s = T(s);
     a.dk = T(dk);
+    a.disp = disp;
     a.variant = pu.col_var;
     return a;
 }
@@ -1918,22 +1926,22 @@ int fcn_op_cn(const fcn_grid *grid, const fcn_params *params, int32_t precision,
     fcn_ctx *ctx = nullptr;
     if (rc) return fail(nullptr, rc, why);
     if (!table || !field || !(dz > 0) || !std::isfinite(dz)) return fail(nullptr, FCN_ERR_ARG, "bad pointers or dz");
-    double s, dk;
-    cn_coefs(*grid, *params, dz, &s, &dk);
+    double s, dk, disp;
+    cn_coefs(*grid, *params, dz, &s, &dk, &disp);
     const double *lo64, *hi64;
     if (precision == FCN_FP64) {
         const double *lo, *hi;
         CK(get_lohi<double>(grid->nr, &lo, &hi, &lo64, &hi64), "radial tables");
         ColArgs<double> a;
         a.field = (cx<double> *)field; a.invden = (const cx<double> *)table; a.lo = lo; a.hi = hi;
-        a.nr = grid->nr; a.nt = grid->nt; a.s = s; a.dk = dk; a.variant = 0;
+        a.nr = grid->nr; a.nt = grid->nt; a.s = s; a.dk = dk; a.disp = disp; a.variant = 0;
         CK(launch_cn<double>(a, (cudaStream_t)stream), "column stage");
     } else {
         const float *lo, *hi;
         CK(get_lohi<float>(grid->nr, &lo, &hi, &lo64, &hi64), "radial tables");
         ColArgs<float> a;
         a.field = (cx<float> *)field; a.invden = (const cx<float> *)table; a.lo = lo; a.hi = hi;
-        a.nr = grid->nr; a.nt = grid->nt; a.s = float(s); a.dk = float(dk); a.variant = 0;
+        a.nr = grid->nr; a.nt = grid->nt; a.s = float(s); a.dk = float(dk); a.disp = disp; a.variant = 0;
         CK(launch_cn<float>(a, (cudaStream_t)stream), "column stage");
     }
     return FCN_OK;

@@ -236,6 +236,8 @@ struct ColArgs {
     int nr, nt;
     T s;                     // dz / (4 k0 dr^2), 0 without diffraction
     T dk;                    // k'' dz/4 domega^2, 0 without dispersion: delta_q = dk q^2
+    double disp = 0.0;       // FCN_EXACT_DISPERSION: dk goes here instead, and the
+                             // stage multiplies column q by exp(2 i disp q^2)
     int variant;             // 0..3: register chunks, long/short x CTA 256/512;
                              // 4, 5: cp.async-staged chunks of 16 / 8 rows (FP32);
                              // 6, 7: register-fed staged chunks of 16 / 8 rows

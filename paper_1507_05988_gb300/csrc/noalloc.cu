@@ -93,7 +93,11 @@ int run(const fcn_grid &g, const fcn_params &p, double dz, void *field, cudaStre
     const double dr = g.r_max / double(g.nr - 1);
     const double domega = 2.0 * kPi / g.t_window;
     const double s = (p.flags & FCN_DIFFRACTION) ? dz / (4.0 * k0 * dr * dr) : 0.0;
-    const double dk = (p.flags & FCN_DISPERSION) ? p.k2 * dz / 4.0 * domega * domega : 0.0;
+    const double dk_all = (p.flags & FCN_DISPERSION) ? p.k2 * dz / 4.0 * domega * domega : 0.0;
+    // FCN_EXACT_DISPERSION: the CN system without the dispersion term, which
+    // the column stage applies as its exact factor exp(2 i disp q^2)
+    const bool exact = (p.flags & FCN_EXACT_DISPERSION) != 0;
+    const double dk = exact ? 0.0 : dk_all;
 
     lohi_kernel<T><<<(g.nr + 127) / 128, 128, 0, st>>>(g.nr, lo64, hi64, lo, hi);
     cudaError_t e = cudaGetLastError();
@@ -116,6 +120,7 @@ int run(const fcn_grid &g, const fcn_params &p, double dz, void *field, cudaStre
     ca.nt = g.nt;
     ca.s = T(s);
     ca.dk = T(dk);
+    ca.disp = exact ? dk_all : 0.0;
     ca.variant = 0;
     e = launch_cn<T>(ca, st);
     if (e != cudaSuccess) return FCN_ERR_CUDA;

@@ -35,6 +35,7 @@ FCN_ERR_NOMEM = -6
 FCN_ERR_STATE = -7
 FCN_DIFFRACTION, FCN_DISPERSION, FCN_KERR, FCN_PLASMA, FCN_MPI, FCN_MPI_SAT = 1, 2, 4, 8, 16, 32
 FCN_ALL_PHYSICS = 31
+FCN_EXACT_DISPERSION = 128
 FCN_FP64 = 0
 FCN_FP32_MIXED = 1
 FCN_OP_IFFT, FCN_OP_NL, FCN_OP_NL2, FCN_OP_FFT, FCN_OP_RHO = 1, 2, 4, 8, 16

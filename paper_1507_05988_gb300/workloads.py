@@ -36,6 +36,7 @@ RHO_NT = 5.4e18 * 1e6        # m^-3
 # physics switches (same bit meaning on both sides of the parity tests)
 DIFFRACTION, DISPERSION, KERR, PLASMA, MPI, MPI_SAT = 1, 2, 4, 8, 16, 32
 ALL_PHYSICS = DIFFRACTION | DISPERSION | KERR | PLASMA | MPI
+EXACT_DISPERSION = 128        # dispersion as its exact factor per frequency (variant of R7)
 
 
 def critical_power(lambda0: float = LAMBDA0, n0: float = N0, n2: float = N2) -> float:

@@ -661,10 +661,13 @@ def _variant_workloads():
         "mpi_saturated": base(flags=W.ALL_PHYSICS | W.MPI_SAT),
         # sigma_10 chosen so that sigma_10 I^10 = sigma_8 I^8 at 5e17 W/m^2
         "k10": base(K=10, sigma_k=W.SIGMA_K / 2.5e35),
+        # dispersion as its exact factor per frequency (variant of reading
+        # R7), strongly dispersive so that it differs from the CN form
+        "exact_dispersion": base(flags=W.ALL_PHYSICS | W.EXACT_DISPERSION, k2=2e-27),
     }
 
 
-@pytest.mark.parametrize("name", ["kerr_n2_to_n8", "chirp", "mpi_saturated", "k10"])
+@pytest.mark.parametrize("name", ["kerr_n2_to_n8", "chirp", "mpi_saturated", "k10", "exact_dispersion"])
 @pytest.mark.parametrize("prec", [FP64, FP32])
 def test_physics_variants_match_the_oracle(fcn, name, prec):
     wl = _variant_workloads()[name]
@@ -676,5 +679,25 @@ def test_physics_variants_match_the_oracle(fcn, name, prec):
     assert rel_l2(rho, rho_ref) < (1e-9 if prec == FP64 else 1e-4), name
     # the variant changes the result (it is not silently ignored)
     plain = _variant_workloads()["plain"]
+    if name == "exact_dispersion":
+        plain = wl.with_(flags=W.ALL_PHYSICS)      # the same pulse, dispersion on the CN diagonal
     other, _ = oracle.run(_pb(plain), plain.dz, n, plain.field())
     assert rel_l2(ref, other) > 1e-6, name
+
+
+@pytest.mark.parametrize("col_variant", list(range(8)))
+def test_exact_dispersion_in_every_column_variant(fcn, col_variant):
+    """Every column kernel applies the exact dispersion factor at its final
+    store; FP32 (variants 4-7 are FP32-only paths of the tuner) against the
+    oracle over 3 steps, and the paired kernel for two pulses."""
+    wl = _variant_workloads()["exact_dispersion"]
+    ref, _ = oracle.run(_pb(wl), wl.dz, 3, wl.field())
+    s = fcn.Solver([wl.physics(), wl.physics()], precision=FP32)
+    s.set_variants(0, col_variant)
+    s.set_pairing(1 if col_variant == 7 else 0)
+    for k in range(2):
+        s.set_field(wl.field(), pulse=k)
+    s.step(wl.dz, 3)
+    for k in range(2):
+        assert rel_l2(s.get_field(pulse=k), ref) < 1e-5
+    s.close()
