@@ -11,7 +11,8 @@ copies in and out, so the caller's arrays are never aliased.
 
 Parity status (per function; the pins live in ``tests/test_oracle_*.py``):
 pinned: fft, thomas, cn_coeffs, rho_row, nl_half, linear_step, step, diag,
-propagate_adaptive, mlp_forward, mlp_loss_grad.  The full coupled run with
+propagate_adaptive, mlp_forward, mlp_loss_grad, and the Cartesian-grid
+functions xy_cn_coeffs, xy_linear_step, xy_run, xy_diag.  The full coupled run with
 all physics on is parity unpinned beyond the invariants those tests check,
 because the paper prints no values for it.
 """
@@ -77,6 +78,10 @@ class _Adaptive(C.Structure):
     ]
 
 
+class _GridXY(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("x_width", C.c_double), ("y_width", C.c_double)]
+
+
 _lib = None
 _D = C.POINTER(C.c_double)
 
@@ -103,6 +108,11 @@ def _load():
             "orc_propagate_adaptive": (C.c_int, [P, _D, _D, C.c_double, C.c_double,
                                                   C.c_double, C.c_double, C.c_double,
                                                   C.c_int, C.POINTER(_Adaptive)]),
+            "orc_xy_cn_coeffs": (None, [P, C.c_double, C.c_int, C.c_int, C.c_double, C.c_int,
+                                        _D, _D, _D, _D, _D, _D]),
+            "orc_xy_linear_step": (C.c_int, [P, C.POINTER(_GridXY), C.c_double, _D]),
+            "orc_xy_run": (C.c_int, [P, C.POINTER(_GridXY), C.c_double, C.c_long, _D, _D]),
+            "orc_xy_diag": (None, [P, C.POINTER(_GridXY), _D, _D, C.POINTER(_Diag)]),
             "orc_mlp_forward": (C.c_int, [C.c_int, C.c_int, C.c_int, _D, _D, _D]),
             "orc_mlp_loss_grad": (C.c_int, [C.c_int, C.c_int, C.c_int, _D, _D, _D, _D, _D]),
         }
@@ -271,6 +281,77 @@ def propagate_adaptive(pb: Problem, A, z0: float, z_end: float, dz0: float,
                                    int(max_reject), C.byref(res))
     return a, rho, dict(z=res.z, dz_next=res.dz_next, accepted=res.accepted,
                         rejected=res.rejected, last_err=res.last_err, status=res.status)
+
+
+@dataclass
+class GridXY:
+    """Cartesian transverse grid (mirrors orc_xy_grid): nx x ny nodes over
+    widths x_width, y_width [m]; the walls (first and last node of each axis)
+    hold A = 0.  The field is complex128 of shape (nx, ny, nt)."""
+    nx: int
+    ny: int
+    x_width: float
+    y_width: float
+
+    def _c(self) -> _GridXY:
+        g = _GridXY()
+        g.nx, g.ny = int(self.nx), int(self.ny)
+        g.x_width, g.y_width = float(self.x_width), float(self.y_width)
+        return g
+
+    @property
+    def dx(self) -> float:
+        return self.x_width / (self.nx - 1)
+
+    @property
+    def dy(self) -> float:
+        return self.y_width / (self.ny - 1)
+
+    def x(self) -> np.ndarray:
+        return -0.5 * self.x_width + self.dx * np.arange(self.nx)
+
+    def y(self) -> np.ndarray:
+        return -0.5 * self.y_width + self.dy * np.arange(self.ny)
+
+
+def xy_cn_coeffs(pb: Problem, dz: float, q: int, n: int, h: float, with_disp: bool):
+    """(a, b, c, d, e, f) of one transverse line's Crank-Nicolson system."""
+    arrs = [np.zeros(n, np.complex128) for _ in range(6)]
+    _load().orc_xy_cn_coeffs(C.byref(pb._c()), float(dz), int(q), int(n), float(h),
+                             1 if with_disp else 0, *[_ptr(v) for v in arrs])
+    return tuple(arrs)
+
+
+def xy_linear_step(pb: Problem, g: GridXY, dz: float, A) -> np.ndarray:
+    a = _c128(A).copy()
+    assert a.shape == (g.nx, g.ny, pb.nt)
+    rc = _load().orc_xy_linear_step(C.byref(pb._c()), C.byref(g._c()), float(dz), _ptr(a))
+    if rc != 0:
+        raise RuntimeError(f"orc_xy_linear_step failed ({rc})")
+    return a
+
+
+def xy_run(pb: Problem, g: GridXY, dz: float, nsteps: int, A):
+    """nsteps Strang steps on the Cartesian grid; returns (field, rho)."""
+    a = _c128(A).copy()
+    assert a.shape == (g.nx, g.ny, pb.nt)
+    rho = np.zeros(a.shape, np.float64)
+    rc = _load().orc_xy_run(C.byref(pb._c()), C.byref(g._c()), float(dz), int(nsteps), _ptr(a),
+                            _ptr(rho))
+    if rc != 0:
+        raise RuntimeError(f"orc_xy_run failed ({rc})")
+    return a, rho
+
+
+def xy_diag(pb: Problem, g: GridXY, A, rho=None) -> dict:
+    a = _c128(A)
+    r = _f64(rho) if rho is not None else None
+    out = _Diag()
+    _load().orc_xy_diag(C.byref(pb._c()), C.byref(g._c()), _ptr(a),
+                        _ptr(r) if r is not None else None, C.byref(out))
+    return dict(energy=out.energy, peak_intensity=out.peak_intensity, peak_rho=out.peak_rho,
+                onaxis_peak=out.onaxis_peak, spectral_rms=out.spectral_rms,
+                nonfinite=bool(out.nonfinite))
 
 
 def mlp_param_count(nin: int, nh: int) -> int:

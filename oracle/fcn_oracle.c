@@ -28,6 +28,18 @@
  *       /(Nt dtau) for q < Nt/2 and 2 pi (q - Nt)/(Nt dtau) otherwise.
  *   R6  The forward transform is exp(-2 pi i p q / Nt), unnormalised; the
  *       inverse carries 1/Nt (Eq. (antifourier)).
+ *   R9  Cartesian transverse grid (Sec. 2 names Delta_perp = d^2/dx^2 +
+ *       d^2/dy^2 but Sec. 3 discretises only the radial operator): each axis
+ *       takes the second difference of Eq. (diff2) with the Crank-Nicolson
+ *       average of Eq. (diff1); the walls carry A = 0 (Eq. (bound) at
+ *       r = max, on all four sides).  The two-dimensional system is not
+ *       tridiagonal, so the linear step is the product of the two 1-D
+ *       Cayley factors, x first, then y (the Peaceman-Rachford alternating
+ *       direction form); the factors commute, and the product differs from
+ *       the unsplit 2-D Crank-Nicolson step by O(dz^3) per step, the order
+ *       of the Strang split itself.  The dispersion term goes into the y
+ *       factor whole, so a transversely uniform field sees exactly the
+ *       radial scheme's factor (1 + i delta_q)/(1 - i delta_q).
  */
 #include "fcn_oracle.h"
 
@@ -502,6 +514,166 @@ void orc_diag_compute(const orc_problem *pb, const double *Ad, const double *rho
         }
     }
     free(row);
+    if (s0 > 0) {
+        double mean = s1 / s0;
+        double var = s2 / s0 - mean * mean;
+        out->spectral_rms = var > 0 ? sqrt(var) : 0.0;
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Cartesian transverse grid (reading R9)                              */
+/* ------------------------------------------------------------------ */
+
+/* Line of n nodes, spacing h, walls at nodes 0 and n-1.  With
+ * s = dz/(4 k0 h^2) (Eqs. (diff1)-(diff2) on one axis) and
+ * delta_q = k'' omega_q^2 dz/4 when with_disp:
+ *   rows 0, n-1 : b = 1, a = c = d = e = f = 0               (A = 0)
+ *   1..n-2      : a = c = -is, b = 1 + 2is - i delta
+ *                 d = f =  is, e = 1 - 2is + i delta          */
+void orc_xy_cn_coeffs(const orc_problem *pb, double dz, int q, int n, double h, int with_disp,
+                      double *ad, double *bd, double *cd, double *dd, double *ed, double *fd)
+{
+    cplx *a = (cplx *)ad, *b = (cplx *)bd, *c = (cplx *)cd;
+    cplx *d = (cplx *)dd, *e = (cplx *)ed, *f = (cplx *)fd;
+    double k0 = orc_k0(pb);
+    double s = (pb->flags & ORC_DIFFRACTION) ? dz / (4.0 * k0 * h * h) : 0.0;
+    double w = orc_omega(pb, q);
+    double delta = (with_disp && (pb->flags & ORC_DISPERSION) && !(pb->flags & ORC_EXACT_DISPERSION))
+                       ? pb->k2 * w * w * dz / 4.0 : 0.0;
+    for (int j = 0; j < n; ++j) {
+        if (j == 0 || j == n - 1) {
+            a[j] = 0; b[j] = 1.0; c[j] = 0; d[j] = 0; e[j] = 0; f[j] = 0;
+        } else {
+            a[j] = -I * s;
+            b[j] = 1.0 + I * (2.0 * s) - I * delta;
+            c[j] = -I * s;
+            d[j] = I * s;
+            e[j] = 1.0 - I * (2.0 * s) + I * delta;
+            f[j] = I * s;
+        }
+    }
+}
+
+/* One transverse line of bin q: the n values at A[off + k stride],
+ * k = 0..n-1, replaced by (M_abc)^-1 M_def times them (and, in the y factor
+ * under ORC_EXACT_DISPERSION, by the exact dispersion factor).
+ * co: scratch of 8 n complex values. */
+static int xy_line(const orc_problem *pb, double dz, int q, int n, double h, int with_disp,
+                   cplx *A, size_t off, size_t stride, cplx *co)
+{
+    cplx *a = co, *b = co + n, *c = co + 2 * n, *d = co + 3 * n;
+    cplx *e = co + 4 * n, *f = co + 5 * n, *col = co + 6 * n, *rhs = co + 7 * n;
+    orc_xy_cn_coeffs(pb, dz, q, n, h, with_disp, (double *)a, (double *)b, (double *)c,
+                     (double *)d, (double *)e, (double *)f);
+    for (int k = 0; k < n; ++k) col[k] = A[off + (size_t)k * stride];
+    for (int k = 0; k < n; ++k) {
+        cplx v = e[k] * col[k];
+        if (k > 0) v += d[k] * col[k - 1];
+        if (k < n - 1) v += f[k] * col[k + 1];
+        rhs[k] = v;
+    }
+    int rc = orc_thomas(n, (double *)a, (double *)b, (double *)c, (double *)rhs, (double *)col);
+    cplx ph = 1.0;
+    if (with_disp && (pb->flags & ORC_DISPERSION) && (pb->flags & ORC_EXACT_DISPERSION)) {
+        double w = orc_omega(pb, q);
+        ph = cexp(I * (pb->k2 * w * w * dz / 2.0));
+    }
+    for (int k = 0; k < n; ++k) A[off + (size_t)k * stride] = ph * col[k];
+    return rc;
+}
+
+/* A <- F^-1( C_y C_x F(A) ): transform every (x, y) row along tau, then per
+ * frequency bin the x factor on every x line and the y factor on every y
+ * line, then the inverse transform. */
+int orc_xy_linear_step(const orc_problem *pb, const orc_xy_grid *g, double dz, double *Ad)
+{
+    int nx = g->nx, ny = g->ny, nt = pb->nt;
+    double dx = g->x_width / (double)(nx - 1), dy = g->y_width / (double)(ny - 1);
+    size_t rows = (size_t)nx * ny;
+    cplx *A = (cplx *)Ad;
+    for (size_t m = 0; m < rows; ++m)
+        if (orc_fft((double *)(A + m * nt), nt, 0)) return -1;
+    int nmax = nx > ny ? nx : ny;
+    cplx *co = (cplx *)malloc(sizeof(cplx) * (size_t)nmax * 8);
+    int rc = 0;
+    for (int q = 0; q < nt && rc == 0; ++q) {
+        /* x factor: line (j, q) holds A[i][j][q], i = 0..nx-1 */
+        for (int j = 0; j < ny && rc == 0; ++j)
+            rc = xy_line(pb, dz, q, nx, dx, 0, A, (size_t)j * nt + q, (size_t)ny * nt, co);
+        /* y factor with the dispersion term: line (i, q) holds A[i][j][q] */
+        for (int i = 0; i < nx && rc == 0; ++i)
+            rc = xy_line(pb, dz, q, ny, dy, 1, A, (size_t)i * ny * nt + q, (size_t)nt, co);
+    }
+    free(co);
+    if (rc) return -2;
+    for (size_t m = 0; m < rows; ++m)
+        if (orc_fft((double *)(A + m * nt), nt, 1)) return -1;
+    return 0;
+}
+
+/* One Strang step (Eq. (nlseq)) on the Cartesian grid: the nonlinear half
+ * steps act on each (x, y) row exactly as on a radial row. */
+int orc_xy_step(const orc_problem *pb, const orc_xy_grid *g, double dz, double *Ad, double *rho)
+{
+    int nt = pb->nt;
+    size_t rows = (size_t)g->nx * g->ny;
+    double *tmp = (double *)malloc(sizeof(double) * (size_t)nt);
+    for (size_t m = 0; m < rows; ++m) orc_nl_half(pb, 0.5 * dz, Ad + 2 * m * nt, tmp);
+    int rc = orc_xy_linear_step(pb, g, dz, Ad);
+    for (size_t m = 0; m < rows && rc == 0; ++m)
+        orc_nl_half(pb, 0.5 * dz, Ad + 2 * m * nt, rho ? rho + m * nt : tmp);
+    free(tmp);
+    return rc;
+}
+
+int orc_xy_run(const orc_problem *pb, const orc_xy_grid *g, double dz, long nsteps, double *A,
+               double *rho)
+{
+    for (long n = 0; n < nsteps; ++n) {
+        int rc = orc_xy_step(pb, g, dz, A, rho);
+        if (rc) return rc;
+    }
+    return 0;
+}
+
+void orc_xy_diag(const orc_problem *pb, const orc_xy_grid *g, const double *Ad, const double *rho,
+                 orc_diag *out)
+{
+    int nx = g->nx, ny = g->ny, nt = pb->nt;
+    size_t rows = (size_t)nx * ny;
+    size_t centre = (size_t)((nx - 1) / 2) * ny + (size_t)((ny - 1) / 2);
+    double dx = g->x_width / (double)(nx - 1), dy = g->y_width / (double)(ny - 1);
+    double dtau = pb->t_window / nt;
+    const cplx *A = (const cplx *)Ad;
+    memset(out, 0, sizeof(*out));
+    double esum = 0.0, s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    double *row = (double *)malloc(sizeof(double) * 2 * (size_t)nt);
+    for (size_t m = 0; m < rows; ++m) {
+        for (int p = 0; p < nt; ++p) {
+            cplx v = A[m * nt + p];
+            double re = creal(v), im = cimag(v);
+            if (!isfinite(re) || !isfinite(im)) out->nonfinite = 1;
+            double i2 = re * re + im * im;
+            esum += i2;
+            if (i2 > out->peak_intensity) out->peak_intensity = i2;
+            if (m == centre && i2 > out->onaxis_peak) out->onaxis_peak = i2;
+        }
+        memcpy(row, A + m * nt, sizeof(double) * 2 * (size_t)nt);
+        orc_fft(row, nt, 0);
+        for (int q = 0; q < nt; ++q) {
+            double sq = row[2 * q] * row[2 * q] + row[2 * q + 1] * row[2 * q + 1];
+            double w = orc_omega(pb, q);
+            s0 += sq;
+            s1 += sq * w;
+            s2 += sq * w * w;
+        }
+    }
+    free(row);
+    out->energy = dx * dy * dtau * esum;
+    if (rho)
+        for (size_t i = 0; i < rows * nt; ++i)
+            if (rho[i] > out->peak_rho) out->peak_rho = rho[i];
     if (s0 > 0) {
         double mean = s1 / s0;
         double var = s2 / s0 - mean * mean;

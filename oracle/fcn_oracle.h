@@ -19,6 +19,9 @@
  *   orc_propagate_adaptive : pinned (controller arithmetic and exact
  *     landing on z_end; the step it wraps is pinned above).
  *   orc_mlp_* : pinned (finite differences, closed-form tiny nets).
+ *   orc_xy_* (Cartesian transverse grid) : pinned (elliptical Gaussian beam
+ *     in closed form, dense solves of the 1-D systems, energy, the discrete
+ *     dispersion factor, pure SPM, agreement with the radial solver).
  *   Full coupled run (all physics on) : parity unpinned beyond the
  *     invariants above -- the paper prints no values for it.
  */
@@ -109,6 +112,33 @@ int  orc_propagate_adaptive(const orc_problem *pb, double *A, double *rho,
                             double z0, double z_end, double dz0, double rtol,
                             double dz_min, int max_reject,
                             orc_adaptive_result *res);
+
+/* Cartesian transverse grid (Sec. 2: Delta_perp = d^2/dx^2 + d^2/dy^2 for
+ * beams without cylindrical symmetry).  The physics and the time grid come
+ * from an orc_problem (nr and r_max unused); the field is A[i][j][p] with
+ * x_i = -x_width/2 + i dx, dx = x_width/(nx - 1), likewise y_j, and A = 0 on
+ * the four walls i = 0, nx-1, j = 0, ny-1.  The linear step is the product
+ * of the Crank-Nicolson (Cayley) factors of the x and the y part (reading
+ * R9 in fcn_oracle.c). */
+typedef struct {
+    int    nx, ny;      /* >= 3 */
+    double x_width;     /* m */
+    double y_width;     /* m */
+} orc_xy_grid;
+
+/* Diagonals of the Crank-Nicolson system of one transverse line of n nodes
+ * with spacing h (nodes 0 and n-1 are the walls); with_disp = 1 puts the
+ * dispersion term of bin q into it. */
+void orc_xy_cn_coeffs(const orc_problem *pb, double dz, int q, int n, double h, int with_disp,
+                      double *a, double *b, double *c, double *d, double *e, double *f);
+int  orc_xy_linear_step(const orc_problem *pb, const orc_xy_grid *g, double dz, double *A);
+int  orc_xy_step(const orc_problem *pb, const orc_xy_grid *g, double dz, double *A, double *rho);
+int  orc_xy_run(const orc_problem *pb, const orc_xy_grid *g, double dz, long nsteps, double *A,
+                double *rho);
+/* energy = dx dy dtau sum |A|^2; onaxis_peak on the row nearest the centre
+ * (i = (nx-1)/2, j = (ny-1)/2); spectral_rms from the unweighted spectrum. */
+void orc_xy_diag(const orc_problem *pb, const orc_xy_grid *g, const double *A, const double *rho,
+                 orc_diag *out);
 
 /* Learned-dz MLP (6 -> H -> H -> 1, tanh hidden, linear output), FP64. */
 int  orc_mlp_forward(int batch, int nin, int nh, const double *params,

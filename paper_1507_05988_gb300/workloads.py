@@ -166,6 +166,104 @@ def application_1km() -> Workload:
                     p_over_pcr=p / p_cr, dz=1e-3, nsteps=1_100_000)
 
 
+@dataclass
+class WorkloadXY:
+    """One pulse on a Cartesian transverse grid (Sec. 2: Delta_perp = d^2/dx^2
+    + d^2/dy^2): nx x ny nodes over x_width x y_width (default 10 w0 each,
+    walls at +-5 w0 holding A = 0), Nt points over t_window (default 16 tp).
+    Input: sqrt(I0) exp(-x^2/wx^2 - y^2/wy^2 - tau^2/tp^2 - i C tau^2/tp^2)
+    with I0 = 2 P/(pi wx wy) (the peak intensity of an elliptical Gaussian
+    beam of power P), times (1 + u) with optional noise as for Workload."""
+    name: str
+    nx: int
+    ny: int
+    nt: int
+    w0: float
+    tp: float
+    p_over_pcr: float
+    w0y: float = 0.0            # default w0 (round beam)
+    x_width: float = 0.0        # default 10 w0
+    y_width: float = 0.0        # default 10 w0y
+    t_window: float = 0.0       # default 16 tp
+    chirp: float = 0.0
+    n2j: tuple = (N2, 0.0, 0.0, 0.0)
+    k2: float = K2
+    sigma_k: float = SIGMA_K
+    rho_nt: float = RHO_NT
+    K: int = K_MPI
+    lambda0: float = LAMBDA0
+    n0: float = N0
+    flags: int = ALL_PHYSICS
+    dz: float = 1e-2
+    nsteps: int = 200
+    noise_seed: int | None = None
+    noise_amp: float = 0.01
+
+    def __post_init__(self):
+        if self.w0y <= 0:
+            self.w0y = self.w0
+        if self.x_width <= 0:
+            self.x_width = 10.0 * self.w0
+        if self.y_width <= 0:
+            self.y_width = 10.0 * self.w0y
+        if self.t_window <= 0:
+            self.t_window = 16.0 * self.tp
+
+    @property
+    def i0(self) -> float:
+        p = self.p_over_pcr * critical_power(self.lambda0, self.n0, self.n2j[0])
+        return 2.0 * p / (np.pi * self.w0 * self.w0y)
+
+    @property
+    def points(self) -> int:
+        return self.nx * self.ny * self.nt
+
+    def grid(self) -> dict:
+        """Keyword arguments of the Cartesian grid (oracle.GridXY and the binding)."""
+        return dict(nx=self.nx, ny=self.ny, x_width=self.x_width, y_width=self.y_width)
+
+    def physics(self) -> dict:
+        """Physics and time grid, as Workload.physics (nr, r_max unused: 3, 0)."""
+        return dict(nr=3, nt=self.nt, r_max=0.0, t_window=self.t_window, lambda0=self.lambda0,
+                    n0=self.n0, n2j=tuple(self.n2j), k2=self.k2, sigma_k=self.sigma_k,
+                    rho_nt=self.rho_nt, K=self.K, flags=self.flags)
+
+    def with_(self, **kw) -> "WorkloadXY":
+        return replace(self, **kw)
+
+    def field(self) -> np.ndarray:
+        """Initial field (nx, ny, nt) complex128."""
+        x = -0.5 * self.x_width + np.arange(self.nx) * (self.x_width / (self.nx - 1))
+        y = -0.5 * self.y_width + np.arange(self.ny) * (self.y_width / (self.ny - 1))
+        tau = -0.5 * self.t_window + np.arange(self.nt) * (self.t_window / self.nt)
+        tt = (tau / self.tp) ** 2
+        a = (np.sqrt(self.i0) * np.exp(-(x / self.w0) ** 2)[:, None, None]
+             * np.exp(-(y / self.w0y) ** 2)[None, :, None]
+             * np.exp(-tt - 1j * self.chirp * tt)[None, None, :])
+        if self.noise_seed is not None:
+            rng = np.random.Generator(np.random.PCG64(self.noise_seed))
+            u = rng.uniform(-self.noise_amp, self.noise_amp, size=a.shape)
+            a = a * (1.0 + u)
+        return np.ascontiguousarray(a.astype(np.complex128))
+
+
+def cartesian_config1() -> WorkloadXY:
+    """Config 1's pulse (w0 = 1 mm, tp = 100 fs, 3 P_cr, n2 only, 200 steps
+    of 1 cm) on a Cartesian grid of 255 x 255 x 256: the walls at +-5 w0 and
+    dx = dy = 10 mm/254, the radial grid's dr, so the centre node and the
+    nodes along the axes coincide with the radial grid's."""
+    return WorkloadXY("cart_cfg1_255x255x256", nx=255, ny=255, nt=256, w0=1e-3, tp=100e-15,
+                      p_over_pcr=3.0, dz=1e-2, nsteps=200)
+
+
+def small_xy(nx: int = 21, ny: int = 17, nt: int = 32, **kw) -> WorkloadXY:
+    """A small Cartesian grid with config-1 physics for fast tests."""
+    base = dict(name=f"small_xy_{nx}x{ny}x{nt}", nx=nx, ny=ny, nt=nt, w0=1e-3, tp=100e-15,
+                p_over_pcr=3.0, dz=1e-2, nsteps=10)
+    base.update(kw)
+    return WorkloadXY(**base)
+
+
 def small(nr: int = 48, nt: int = 64, **kw) -> Workload:
     """A small grid with config-1 physics for fast tests."""
     base = dict(name=f"small_{nr}x{nt}", nr=nr, nt=nt, w0=1e-3, tp=100e-15, p_over_pcr=3.0,
