@@ -403,6 +403,81 @@ int fcn_op_cn(const fcn_grid *grid, const fcn_params *params, int32_t precision,
 int fcn_op_cn_noalloc(const fcn_grid *grid, const fcn_params *params, int32_t precision,
                       double dz, void *field, void *stream);
 
+/* ================= Cartesian transverse grid (3D+1) =================
+ * Sec. 2 of the paper gives Delta_perp = d^2/dx^2 + d^2/dy^2 for beams
+ * without cylindrical symmetry; Sec. 3 discretises only the radial operator.
+ * This context advances A(x, y, tau) by the same Strang step (Eq. (nlseq)):
+ * the nonlinear half steps and the rho(tau) integration act on every (x, y)
+ * row exactly as on a radial row, and the linear step is, per frequency bin,
+ * the Crank-Nicolson factor of the x part (Eqs. (diff1)-(diff2) on the x
+ * axis) followed by that of the y part with the dispersion term on its
+ * diagonal (the x and y factors commute; their product differs from the
+ * unsplit two-dimensional Crank-Nicolson step by O(dz^3) per step).  The
+ * walls carry A = 0 (Eq. (bound) at r = max, on all four sides).
+ *   - A field is Nx x Ny x Nt complex values, row-major A[i][j][p]:
+ *     x_i = -x_width/2 + i dx, dx = x_width/(Nx-1), likewise y_j; p as for
+ *     the radial grid.  Host buffers: 2*Nx*Ny*Nt interleaved doubles (or
+ *     floats for the _c64 calls).
+ *   - Nx, Ny in [3, 2048]; Nt a power of two in [2, 8192].
+ *   - Diagnostics (fcn_diag): energy = dx dy dtau sum |A|^2; onaxis_peak is
+ *     the maximum over tau of the row nearest the centre, i = (Nx-1)/2,
+ *     j = (Ny-1)/2; spectral_rms weighs every row equally; rejected = 0.
+ *   - Errors, streams and ownership as for the radial context. */
+typedef struct {
+    int32_t nx;          /* x nodes (walls at i = 0 and Nx-1)              */
+    int32_t ny;          /* y nodes (walls at j = 0 and Ny-1)              */
+    int32_t nt;          /* time points (power of two)                     */
+    int32_t pad_;
+    double  x_width;     /* [m]: dx = x_width/(Nx-1)                       */
+    double  y_width;     /* [m]: dy = y_width/(Ny-1)                       */
+    double  t_window;    /* T [s]: dtau = T/Nt, tau_min = -T/2             */
+} fcn_grid_xy;
+
+typedef struct fcn_xy_ctx fcn_xy_ctx;
+
+/* Creates a Cartesian-grid context (physics as in fcn_params, all flags
+ * allowed).  The field is zero until fcn_xy_set_field.
+ * Errors: FCN_ERR_ARG, FCN_ERR_UNSUPPORTED, FCN_ERR_NOMEM, FCN_ERR_CUDA. */
+int  fcn_xy_create(const fcn_grid_xy *grid, const fcn_params *params, int32_t precision,
+                   void *stream, fcn_xy_ctx **out);
+void fcn_xy_destroy(fcn_xy_ctx *ctx);
+/* Message of the context's last error (NULL: of the last failed create). */
+const char *fcn_xy_last_error(const fcn_xy_ctx *ctx);
+/* Host field in/out (complex128 / complex64 interleaved, layout above);
+ * setting a field resets z, the step count and rho.  The get calls
+ * synchronise the stream. */
+int  fcn_xy_set_field(fcn_xy_ctx *ctx, const double *host);
+int  fcn_xy_get_field(fcn_xy_ctx *ctx, double *host);
+int  fcn_xy_set_field_c64(fcn_xy_ctx *ctx, const float *host);
+int  fcn_xy_get_field_c64(fcn_xy_ctx *ctx, float *host);
+/* rho [m^-3] of the last nonlinear half step, Nx*Ny*Nt doubles. */
+int  fcn_xy_get_rho(fcn_xy_ctx *ctx, double *host);
+/* n Strang steps of length dz (n >= 0, dz > 0 finite); blocks of eight
+ * middle steps replay a CUDA graph (captured on first use per dz).  The
+ * first step of a grid times the kernel variants once per process.
+ * _nograph launches every kernel directly.  Asynchronous.
+ * Errors: FCN_ERR_ARG, FCN_ERR_STATE (no field set), FCN_ERR_CUDA. */
+int  fcn_xy_step(fcn_xy_ctx *ctx, double dz, int64_t n);
+int  fcn_xy_step_nograph(fcn_xy_ctx *ctx, double dz, int64_t n);
+/* FP64 diagnostics of the current field (synchronises the stream).
+ * Returns FCN_ERR_NONFINITE if the field holds NaN or Inf. */
+int  fcn_xy_get_diag(fcn_xy_ctx *ctx, fcn_diag *out);
+/* Forces the row-stage variant (0..2) and the line variant (0: chunks of
+ * 16 nodes in FP32 / 8 in FP64, 1: half that); -1 returns to timing. */
+int  fcn_xy_set_variants(fcn_xy_ctx *ctx, int32_t row_variant, int32_t line_variant);
+int  fcn_xy_get_variants(const fcn_xy_ctx *ctx, int32_t out[2]);
+/* Per-launch CUDA-event timing (off by default; while on, steps launch
+ * directly instead of replaying graphs).  ms and count receive
+ * FCN_XY_PROF_KINDS totals; reset = 1 clears them. */
+#define FCN_XY_PROF_ROW_HEAD  0   /* nonlinear half step + forward FFT          */
+#define FCN_XY_PROF_ROW_MID   1   /* inverse FFT + two half steps + forward FFT */
+#define FCN_XY_PROF_ROW_TAIL  2   /* inverse FFT + half step + rho + statistics */
+#define FCN_XY_PROF_LINE_X    3   /* x Crank-Nicolson factor                    */
+#define FCN_XY_PROF_LINE_Y    4   /* y Crank-Nicolson factor (with dispersion)  */
+#define FCN_XY_PROF_KINDS     5
+int  fcn_xy_profile_enable(fcn_xy_ctx *ctx, int32_t on);
+int  fcn_xy_profile_read(fcn_xy_ctx *ctx, double *ms, int64_t *count, int32_t reset);
+
 /* Library version string. */
 const char *fcn_version(void);
 

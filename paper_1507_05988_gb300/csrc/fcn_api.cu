@@ -20,6 +20,7 @@
 
 #include "../../include/fcn.h"
 #include "fcn_device.cuh"
+#include "fcn_host.h"
 
 using namespace fcn;
 
@@ -224,6 +225,34 @@ size_t csize(int prec) { return prec == FCN_FP64 ? 16 : 8; }
 size_t rsize(int prec) { return prec == FCN_FP64 ? 8 : 4; }
 
 }  // namespace
+
+// Host helpers shared with the Cartesian-grid API (xy_api.cu; fcn_host.h).
+namespace fcn {
+namespace hostx {
+int check_params(int prec, const fcn_grid *g, const fcn_params *p, std::string *why) {
+    return check_grid_params(prec, g, p, why);
+}
+template <typename T>
+NLCoef<T> nl(const fcn_grid &g, const fcn_params &p, double h) {
+    return nl_coef<T>(g, p, h);
+}
+template NLCoef<float> nl<float>(const fcn_grid &, const fcn_params &, double);
+template NLCoef<double> nl<double>(const fcn_grid &, const fcn_params &, double);
+template <typename T>
+cudaError_t twiddles(int nt, const cx<T> **out) {
+    return get_twiddles<T>(nt, out);
+}
+template cudaError_t twiddles<float>(int, const cx<float> **);
+template cudaError_t twiddles<double>(int, const cx<double> **);
+void consts(const fcn_grid &g, const fcn_params &p, double *k0, double *dtau, double *domega) {
+    const Consts c = derive(g, p);
+    *k0 = c.k0;
+    *dtau = c.dtau;
+    *domega = c.domega;
+}
+}  // namespace hostx
+}  // namespace fcn
+
 
 // ---------------------------------------------------------------------------
 // context

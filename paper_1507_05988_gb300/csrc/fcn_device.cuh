@@ -292,6 +292,31 @@ cudaError_t launch_cn_batch(const ColArgs<T> *pulses, const int4 *items, int nit
 // shared-memory bytes of the batched row kernel for rows of nt points
 size_t row_batch_smem(int nt, int bytes_per_complex);
 
+// Cartesian transverse grid (xy_kernel.cu).  One launch solves the
+// Crank-Nicolson system of every transverse line of one axis for every
+// frequency bin: line (b, c) holds the n values
+//   field[b * bstride + j * pitch + c],  j = 0..n-1 (j = 0, n-1 the walls),
+// for b = 0..batch-1 and columns c = 0..width-1; the column's frequency bin
+// is q = c mod nt.  The y lines of an [nx][ny][nt] field are (b = x, c = q):
+// batch nx, width nt, pitch nt, bstride ny nt; the x lines are (c = y nt + q):
+// batch 1, width ny nt, pitch ny nt.
+template <typename T>
+struct XYLine {
+    cx<T> *field;
+    const cx<T> *invden;     // [n][nt/2+1]: 1/pivot_j per |q|
+    int n, nt, width, batch;
+    long long pitch, bstride;
+    T s;                     // dz / (4 k0 h^2), 0 without diffraction
+    T dk;                    // delta_q = dk q^2 (0 in a line without dispersion)
+    double disp;             // exact dispersion factor exp(2 i disp q^2), 0: none
+    int variant;             // 0: chunks of 16 (FP32) / 8 (FP64) rows, 1: half that
+};
+template <typename T>
+cudaError_t launch_xy_table(int n, int nt, double s, double dk, cx<T> *table, cudaStream_t st);
+template <typename T>
+cudaError_t launch_xy_line(const XYLine<T> &a, cudaStream_t st);
+constexpr int kXYVariants = 2;
+
 // Learned dz controller (mlp.cu).
 struct MlpScalars {
     double i_ref, rms_ref, peak_prev, dz_prev, err_prev, rtol, l_ref, domega, dz_lo, dz_hi;
@@ -316,6 +341,10 @@ cudaError_t launch_widen_real(const T *src, double *dst, int64_t n, cudaStream_t
 // Final FP64 reduction of per-row statistics into out[0..7]:
 // [energy_sum (sum_m W_m S_m), max I, max u, onaxis max I, S0, S1, S2, nonfinite]
 cudaError_t launch_reduce_stats(const double *stats, int nr, double *out, cudaStream_t st);
+// The same with weight 1 for every row (Cartesian grid) and out[3] the
+// maximum of row axis_row.
+cudaError_t launch_reduce_stats_flat(const double *stats, int nrows, int axis_row, double *out,
+                                     cudaStream_t st);
 // Per-row sums of |a-b|^2 and |b|^2 (FP64) then the final reduction into out[0..1].
 template <typename T>
 cudaError_t launch_diff_norm(const cx<T> *a, const cx<T> *b, int nr, int nt, double *rows,

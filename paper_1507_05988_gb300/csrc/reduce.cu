@@ -63,13 +63,15 @@ __global__ void widen_real_kernel(const T *src, double *dst, int64_t n) {
         dst[i] = double(src[i]);
 }
 
-// out: [energy_sum, max I, max u, onaxis max I, S0, S1, S2, nonfinite]
-__global__ void reduce_stats_kernel(const double *st, int nr, double *out) {
+// out: [energy_sum, max I, max u, onaxis max I, S0, S1, S2, nonfinite];
+// FLAT: every row weighs 1 (Cartesian grid) and the on-axis row is axis_row.
+template <bool FLAT>
+__global__ void reduce_stats_kernel(const double *st, int nr, int axis_row, double *out) {
     __shared__ double sh[32];
     double e = 0, mi = 0, mu = 0, s0 = 0, s1 = 0, s2 = 0, bad = 0;
     for (int m = threadIdx.x; m < nr; m += blockDim.x) {
         const double *r = st + (size_t)m * NSTAT;
-        const double w = radial_weight(m);
+        const double w = FLAT ? 1.0 : radial_weight(m);
         e += w * r[ST_SUM_I];
         mi = fmax(mi, r[ST_MAX_I]);
         mu = fmax(mu, r[ST_MAX_U]);
@@ -85,7 +87,7 @@ __global__ void reduce_stats_kernel(const double *st, int nr, double *out) {
     if (threadIdx.x == 0) out[1] = mi;
     mu = block_max(mu, sh);
     if (threadIdx.x == 0) out[2] = mu;
-    if (threadIdx.x == 0) out[3] = st[ST_MAX_I];
+    if (threadIdx.x == 0) out[3] = st[(size_t)axis_row * NSTAT + ST_MAX_I];
     s0 = block_sum(s0, sh);
     if (threadIdx.x == 0) out[4] = s0;
     s1 = block_sum(s1, sh);
@@ -178,7 +180,13 @@ cudaError_t launch_widen_real(const T *src, double *dst, int64_t n, cudaStream_t
     return cudaGetLastError();
 }
 cudaError_t launch_reduce_stats(const double *stats, int nr, double *out, cudaStream_t st) {
-    reduce_stats_kernel<<<1, RT, 0, st>>>(stats, nr, out);
+    reduce_stats_kernel<false><<<1, RT, 0, st>>>(stats, nr, 0, out);
+    return cudaGetLastError();
+}
+cudaError_t launch_reduce_stats_flat(const double *stats, int nrows, int axis_row, double *out,
+                                     cudaStream_t st) {
+    if (axis_row < 0 || axis_row >= nrows) return cudaErrorInvalidValue;
+    reduce_stats_kernel<true><<<1, 1024, 0, st>>>(stats, nrows, axis_row, out);
     return cudaGetLastError();
 }
 template <typename T>

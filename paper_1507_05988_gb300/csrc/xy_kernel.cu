@@ -1,0 +1,206 @@
+// xy_kernel.cu -- transverse stage of the FCN z-step on a Cartesian grid
+// (Ma & Lin, arXiv:1507.05988, Sec. 2: Delta_perp = d^2/dx^2 + d^2/dy^2 for
+// beams without cylindrical symmetry).
+//
+// Each axis takes the Crank-Nicolson step of Eqs. (diff1)-(diff2) with the
+// walls held at A = 0 (Eq. (bound) at r = max, on all four sides); the
+// two-dimensional system is not tridiagonal, so the stage applies the x and
+// the y factor one after the other (Peaceman-Rachford alternating
+// directions; the factors commute, and the product differs from the unsplit
+// two-dimensional step by O(dz^3) per step, the order of the Strang split).
+// On a line of n nodes, spacing h, s = dz/(4 k0 h^2):
+//   walls (j = 0, n-1) : b = 1, everything else 0
+//   1..n-2             : a = c = -is, b = 1 + i(2s - delta_q)
+//                        d = f =  is, e = 1 - i(2s - delta_q)
+// with delta_q = k'' omega_q^2 dz/4 in the y factor and 0 in the x factor.
+//
+// The matrix depends on (j, |q|, dz) only; its Thomas pivots are computed
+// once per dz (xy_table_kernel, FP64, stored as 1/pivot in the working
+// precision), and the two sweeps run as the chunked parallel scan of affine
+// maps that the radial column stage uses (colscan::chunk_scan): a thread
+// owns L consecutive nodes of one line in registers.  The lines of one
+// launch are addressed as base + j * pitch + c (see XYLine), so the x lines
+// (stride ny*nt) and the y lines (stride nt) use the same kernel, with C
+// adjacent columns per CTA for whole-sector row accesses.
+#include "col_scan.cuh"
+
+namespace fcn {
+namespace {
+
+using namespace colscan;
+
+// One thread per |q| = 0..nt/2: piv_0 = 1 (wall), piv_1 = b,
+// piv_j = b - a c / piv_{j-1} = b + s^2 / piv_{j-1} (2 <= j <= n-2),
+// piv_{n-1} = 1 (wall); the table holds 1/piv_j, row j at j * (nt/2+1).
+template <typename T>
+__global__ void xy_table_kernel(int n, int nt, double s, double dk, cx<T> *table) {
+    const int nq = nt / 2 + 1;
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nq) return;
+    const double delta = dk * double(q) * double(q);
+    const cx<double> b = mk(1.0, 2.0 * s - delta);
+    cx<double> inv = mk(1.0, 0.0);
+    for (int j = 0; j < n; ++j) {
+        cx<double> piv;
+        if (j == 0 || j == n - 1) piv = mk(1.0, 0.0);
+        else if (j == 1) piv = b;
+        else piv = b + mk(s * s * inv.x, s * s * inv.y);
+        inv = crecip(piv);
+        table[FCN_IDX((size_t)j * nq + q, (size_t)n * nq, 70)] = mk(T(inv.x), T(inv.y));
+    }
+}
+
+template <typename T, int L>
+__global__ void __launch_bounds__(512)
+xy_line_kernel(XYLine<T> a, int C) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nwarp = blockDim.x >> 5;
+    cx<T> *smA = reinterpret_cast<cx<T> *>(smem_raw);
+    cx<T> *smB = smA + nwarp * C;
+    cx<T> *smC = smB + nwarp * C;
+
+    const int tid = threadIdx.x;
+    const int col = tid % C;
+    const int chunk = tid / C;
+    const int c = blockIdx.x * C + col;               // < width (width % C == 0)
+    const int nt = a.nt, n = a.n;
+    const int q = c & (nt - 1);
+    const int nq = nt / 2 + 1;
+    const int qq = (q <= nt / 2) ? q : nt - q;
+    const T s = a.s;
+    const T g1 = T(2) * s - a.dk * T(qq) * T(qq);   // interior: e = 1 - i g1
+    const int j0 = chunk * L;
+    // the field holds (batch - 1) bstride + n pitch elements; this line starts
+    // at `off` of them
+    const size_t off = (size_t)blockIdx.y * (size_t)a.bstride + c;
+    const size_t room = (size_t)(a.batch - 1) * (size_t)a.bstride + (size_t)n * a.pitch - off;
+    cx<T> *line = a.field + off;
+
+    cx<T> x[L + 2];
+#pragma unroll
+    for (int k = 0; k < L + 2; ++k) {
+        const int j = j0 - 1 + k;
+        x[k] = (j >= 0 && j < n)
+                   ? line[FCN_IDX((size_t)j * a.pitch, room, 71)]
+                   : czero<T>();
+    }
+    cx<T> inv[L];
+#pragma unroll
+    for (int k = 0; k < L; ++k) {
+        const int j = j0 + k;
+        inv[k] = (j < n) ? ldg_cx(&a.invden[FCN_IDX((size_t)j * nq + qq, (size_t)n * nq, 72)]) : czero<T>();
+    }
+
+    // forward sweep, pass 1: y_j = alpha_j y_{j-1} + beta_j per node, and the
+    // chunk's composed map y_end = PA y_in + PB
+    cx<T> y[L];
+    cx<T> PA = mk(T(1), T(0)), PB = czero<T>();
+#pragma unroll
+    for (int k = 0; k < L; ++k) {
+        const int j = j0 + k;
+        const bool inner = j >= 1 && j < n - 1;
+        if (inner) {
+            const cx<T> w = mk(s * (x[k].x + x[k + 2].x) - g1 * x[k + 1].x,
+                               s * (x[k].y + x[k + 2].y) - g1 * x[k + 1].y);
+            const cx<T> rhs = mk(x[k + 1].x - w.y, x[k + 1].y + w.x);
+            const cx<T> alpha = cmul_i(inv[k], s);
+            y[k] = cmul(rhs, inv[k]);
+            PB = cmul(alpha, PB) + y[k];
+            PA = cmul(alpha, PA);
+        } else {
+            // walls (and nodes past the end): y = 0, the map sends all to 0
+            y[k] = czero<T>();
+            if (j < n) {
+                PA = czero<T>();
+                PB = czero<T>();
+            }
+        }
+    }
+    // forward sweep, pass 2: exact y from the carry entering the chunk
+    {
+        cx<T> yp = chunk_scan<T, false>(PA, PB, C, col, smA, smB, smC);
+#pragma unroll
+        for (int k = 0; k < L; ++k) {
+            const int j = j0 + k;
+            if (j >= 1 && j < n - 1) {
+                y[k] = cmul(cmul_i(inv[k], s), yp) + y[k];
+                yp = y[k];
+            } else if (j < n) {
+                yp = czero<T>();
+            }
+        }
+    }
+    // backward sweep, pass 1: chunk map x_first = QA x_next + QB, with
+    // x_j = gamma_j x_{j+1} + y_j, gamma_j = is / piv_j inside, 0 at walls
+    cx<T> QA = mk(T(1), T(0)), QB = czero<T>();
+#pragma unroll
+    for (int k = L - 1; k >= 0; --k) {
+        const int j = j0 + k;
+        if (j < n) {
+            const cx<T> gamma = (j >= 1 && j < n - 1) ? cmul_i(inv[k], s) : czero<T>();
+            QB = cmul(gamma, QB) + y[k];
+            QA = cmul(gamma, QA);
+        }
+    }
+    // backward sweep, pass 2 and store
+    {
+        cx<T> xn = chunk_scan<T, true>(QA, QB, C, col, smA, smB, smC);
+        const DispPhase<T> ph = disp_phase<T>(a.disp, qq);
+#pragma unroll
+        for (int k = L - 1; k >= 0; --k) {
+            const int j = j0 + k;
+            if (j < n) {
+                const cx<T> gamma = (j >= 1 && j < n - 1) ? cmul_i(inv[k], s) : czero<T>();
+                xn = cmul(gamma, xn) + y[k];
+                line[FCN_IDX((size_t)j * a.pitch, room, 73)] =
+                    disp_apply(xn, ph);
+            }
+        }
+    }
+}
+
+// C columns per CTA: at least one 32-byte sector, doubled while the CTA
+// stays within `target` threads; whole warps (chunks past the line's end
+// are identity maps).
+template <typename T, int L>
+cudaError_t launch_xy_l(const XYLine<T> &a, int target, cudaStream_t st) {
+    constexpr int CMIN = 32 / int(sizeof(cx<T>));
+    const int P = (a.n + L - 1) / L;
+    int C = CMIN;
+    while (C * 2 * P <= target && C * 2 <= 32) C *= 2;
+    if (C > a.nt) C = a.nt;
+    const int threads = ((C * P + 31) / 32) * 32;
+    if (threads > 512) return cudaErrorInvalidConfiguration;
+    if (a.width % C != 0) return cudaErrorInvalidValue;
+    const size_t smem = sizeof(cx<T>) * 3 * (size_t)(threads / 32) * C;
+    return launch_k(xy_line_kernel<T, L>, dim3(a.width / C, a.batch), dim3(threads), smem, st, a, C);
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_xy_table(int n, int nt, double s, double dk, cx<T> *table, cudaStream_t st) {
+    const int nq = nt / 2 + 1;
+    xy_table_kernel<T><<<(nq + 127) / 128, 128, 0, st>>>(n, nt, s, dk, table);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_xy_line(const XYLine<T> &a, cudaStream_t st) {
+    if (a.n < 3 || a.nt < 1 || (a.nt & (a.nt - 1)) || a.width < a.nt || a.batch < 1)
+        return cudaErrorInvalidValue;
+    if (a.width == 0) return cudaSuccess;
+    constexpr int LL = sizeof(T) == 4 ? 16 : 8;
+    constexpr int LS = LL / 2;
+    cudaError_t e = cudaErrorInvalidConfiguration;
+    if (a.variant == 1) e = launch_xy_l<T, LS>(a, 512, st);
+    if (e == cudaErrorInvalidConfiguration) e = launch_xy_l<T, LL>(a, 512, st);
+    return e;
+}
+
+template cudaError_t launch_xy_table<float>(int, int, double, double, cx<float> *, cudaStream_t);
+template cudaError_t launch_xy_table<double>(int, int, double, double, cx<double> *, cudaStream_t);
+template cudaError_t launch_xy_line<float>(const XYLine<float> &, cudaStream_t);
+template cudaError_t launch_xy_line<double>(const XYLine<double> &, cudaStream_t);
+
+}  // namespace fcn

@@ -42,6 +42,7 @@ FCN_OP_IFFT, FCN_OP_NL, FCN_OP_NL2, FCN_OP_FFT, FCN_OP_RHO = 1, 2, 4, 8, 16
 FCN_MLP_NIN, FCN_MLP_NH, FCN_MLP_NPARAM = 6, 64, 4673
 FCN_NOALLOC_SCRATCH_BYTES = 8 * 1024 * 1024
 FCN_PROF_ROW_HEAD, FCN_PROF_ROW_MID, FCN_PROF_ROW_TAIL, FCN_PROF_COLUMN, FCN_PROF_KINDS = 0, 1, 2, 3, 4
+FCN_XY_PROF_KINDS = 5
 
 
 class fcn_grid(C.Structure):
@@ -53,6 +54,11 @@ class fcn_params(C.Structure):
     _fields_ = [("lambda0", C.c_double), ("n0", C.c_double), ("n2j", C.c_double * 4),
                 ("k2", C.c_double), ("sigma_k", C.c_double), ("rho_nt", C.c_double),
                 ("K", C.c_int32), ("flags", C.c_uint32)]
+
+
+class fcn_grid_xy(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nt", C.c_int32), ("pad_", C.c_int32),
+                ("x_width", C.c_double), ("y_width", C.c_double), ("t_window", C.c_double)]
 
 
 class fcn_diag(C.Structure):
@@ -121,6 +127,21 @@ _SIGS = {
     "fcn_op_cn_table": (C.c_int, [_G, _PR, C.c_int32, C.c_double, _P, _P]),
     "fcn_op_cn": (C.c_int, [_G, _PR, C.c_int32, C.c_double, _P, _P, _P]),
     "fcn_op_cn_noalloc": (C.c_int, [_G, _PR, C.c_int32, C.c_double, _P, _P]),
+    "fcn_xy_create": (C.c_int, [C.POINTER(fcn_grid_xy), _PR, C.c_int32, _P, C.POINTER(_CTX)]),
+    "fcn_xy_destroy": (None, [_CTX]),
+    "fcn_xy_last_error": (C.c_char_p, [_CTX]),
+    "fcn_xy_set_field": (C.c_int, [_CTX, _D]),
+    "fcn_xy_get_field": (C.c_int, [_CTX, _D]),
+    "fcn_xy_set_field_c64": (C.c_int, [_CTX, _F]),
+    "fcn_xy_get_field_c64": (C.c_int, [_CTX, _F]),
+    "fcn_xy_get_rho": (C.c_int, [_CTX, _D]),
+    "fcn_xy_step": (C.c_int, [_CTX, C.c_double, C.c_int64]),
+    "fcn_xy_step_nograph": (C.c_int, [_CTX, C.c_double, C.c_int64]),
+    "fcn_xy_get_diag": (C.c_int, [_CTX, C.POINTER(fcn_diag)]),
+    "fcn_xy_set_variants": (C.c_int, [_CTX, C.c_int32, C.c_int32]),
+    "fcn_xy_get_variants": (C.c_int, [_CTX, C.POINTER(C.c_int32)]),
+    "fcn_xy_profile_enable": (C.c_int, [_CTX, C.c_int32]),
+    "fcn_xy_profile_read": (C.c_int, [_CTX, _D, C.POINTER(C.c_int64), C.c_int32]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _fn = getattr(lib, _name)
@@ -345,3 +366,92 @@ class Solver:
     def set_state(self, s, pulse: int = 0):
         s = np.ascontiguousarray(s, dtype=np.float64)
         check(fcn_set_state(self.ctx, pulse, s.ctypes.data_as(_D)), self.ctx)
+
+
+def check_xy(rc: int, ctx=None) -> int:
+    if rc != FCN_OK:
+        raise FcnError(rc, (fcn_xy_last_error(ctx) or b"").decode())
+    return rc
+
+
+class SolverXY:
+    """One Cartesian-grid (3D+1) context: field (nx, ny, nt)."""
+
+    def __init__(self, grid: dict, phys: dict, precision=FCN_FP64, stream=None):
+        """grid: nx, ny, x_width, y_width (WorkloadXY.grid()); phys: the
+        physics and time-grid keys of Workload.physics() (nr, r_max unused)."""
+        self.g = fcn_grid_xy(int(grid["nx"]), int(grid["ny"]), int(phys["nt"]), 0,
+                             float(grid["x_width"]), float(grid["y_width"]), float(phys["t_window"]))
+        _, p = grid_params(phys)
+        self.precision = precision
+        ctx = _CTX()
+        st = stream if stream is not None else C.c_void_p(0)
+        check_xy(fcn_xy_create(C.byref(self.g), C.byref(p), precision, st, C.byref(ctx)), None)
+        self.ctx = ctx
+
+    @property
+    def shape(self):
+        return self.g.nx, self.g.ny, self.g.nt
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            fcn_xy_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_field(self, a: np.ndarray):
+        a = np.ascontiguousarray(a, dtype=np.complex128)
+        assert a.shape == self.shape
+        check_xy(fcn_xy_set_field(self.ctx, a.ctypes.data_as(_D)), self.ctx)
+
+    def get_field(self, out: np.ndarray | None = None) -> np.ndarray:
+        out = np.empty(self.shape, np.complex128) if out is None else out
+        check_xy(fcn_xy_get_field(self.ctx, out.ctypes.data_as(_D)), self.ctx)
+        return out
+
+    def set_field_c64(self, a: np.ndarray):
+        a = np.ascontiguousarray(a, dtype=np.complex64)
+        assert a.shape == self.shape
+        check_xy(fcn_xy_set_field_c64(self.ctx, a.ctypes.data_as(_F)), self.ctx)
+
+    def get_field_c64(self, out: np.ndarray | None = None) -> np.ndarray:
+        out = np.empty(self.shape, np.complex64) if out is None else out
+        check_xy(fcn_xy_get_field_c64(self.ctx, out.ctypes.data_as(_F)), self.ctx)
+        return out
+
+    def get_rho(self) -> np.ndarray:
+        out = np.empty(self.shape, np.float64)
+        check_xy(fcn_xy_get_rho(self.ctx, out.ctypes.data_as(_D)), self.ctx)
+        return out
+
+    def step(self, dz: float, n: int = 1, graph: bool = True):
+        fn = fcn_xy_step if graph else fcn_xy_step_nograph
+        check_xy(fn(self.ctx, float(dz), int(n)), self.ctx)
+
+    def diag(self) -> dict:
+        d = fcn_diag()
+        check_xy(fcn_xy_get_diag(self.ctx, C.byref(d)), self.ctx)
+        return {k: getattr(d, k) for k, _ in fcn_diag._fields_ if k != "pad_"}
+
+    def set_variants(self, row: int = -1, line: int = -1):
+        check_xy(fcn_xy_set_variants(self.ctx, int(row), int(line)), self.ctx)
+
+    def variants(self):
+        out = (C.c_int32 * 2)()
+        check_xy(fcn_xy_get_variants(self.ctx, out), self.ctx)
+        return out[0], out[1]
+
+    def profile(self, on: bool):
+        check_xy(fcn_xy_profile_enable(self.ctx, 1 if on else 0), self.ctx)
+
+    def profile_read(self, reset: bool = True) -> dict:
+        ms = (C.c_double * FCN_XY_PROF_KINDS)()
+        n = (C.c_int64 * FCN_XY_PROF_KINDS)()
+        check_xy(fcn_xy_profile_read(self.ctx, ms, n, 1 if reset else 0), self.ctx)
+        names = ("row_head", "row_mid", "row_tail", "line_x", "line_y")
+        return {names[k]: (ms[k], n[k]) for k in range(FCN_XY_PROF_KINDS)}

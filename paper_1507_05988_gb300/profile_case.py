@@ -4,7 +4,8 @@
         --steps 3 --row-variant 0 --col-variant 0
 
 The pulse is one of the seeded workloads (config 1: 128 x 256, config 2:
-1024 x 4096, config 3: 2048 x 8192).  With variants given the autotuner does
+1024 x 4096, config 3: 2048 x 8192), or with --cartesian config 1's pulse on
+the 255 x 255 x 256 Cartesian grid (row variant, then line variant).  With variants given the autotuner does
 not run, so a profiler sees exactly one fused middle row launch and one
 column launch per step after the first step (which adds the opening row
 launch).  Steps run without CUDA graphs unless --graph is given.
@@ -32,7 +33,10 @@ def main(argv=None) -> int:
     ap.add_argument("--time", type=int, default=0,
                     help="then time this many graph-replayed steps (wall clock around a "
                          "synchronising call) and as many per-launch event-timed steps")
+    ap.add_argument("--cartesian", action="store_true")
     a = ap.parse_args(argv)
+    if a.cartesian:
+        return _cartesian(a)
     make = {1: workloads.config1, 2: workloads.config2, 3: workloads.config3}[a.config]
     wls = [make(seed=k) if a.config == 2 else make() for k in range(a.pulses)]
     prec = fcn.FCN_FP32_MIXED if a.precision == "fp32" else fcn.FCN_FP64
@@ -68,6 +72,39 @@ def main(argv=None) -> int:
         s.profile(False)
     print(f"profile_case: config {a.config} {a.precision} steps {a.steps} variants {s.variants(0)} "
           f"energy {d['energy']:.6e}")
+    s.close()
+    return 0 if ok else 1
+
+
+def _cartesian(a) -> int:
+    import time
+    wl = workloads.cartesian_config1()
+    prec = fcn.FCN_FP32_MIXED if a.precision == "fp32" else fcn.FCN_FP64
+    s = fcn.SolverXY(wl.grid(), wl.physics(), precision=prec)
+    if a.row_variant >= 0 or a.col_variant >= 0:
+        s.set_variants(a.row_variant, a.col_variant)
+    s.set_field(wl.field())
+    s.step(wl.dz, a.steps, graph=a.graph)
+    d = s.diag()
+    ok = np.isfinite(d["energy"]) and d["nonfinite"] == 0
+    if a.time > 0:
+        s.step(wl.dz, 16)
+        s.diag()
+        t0 = time.perf_counter()
+        s.step(wl.dz, a.time)
+        s.diag()
+        dt = time.perf_counter() - t0
+        print(f"profile_case: cartesian graph replay {1e6 * dt / a.time:.2f} us per step "
+              f"({wl.points / (dt / a.time):.3e} point-steps/s)")
+        s.profile(True)
+        s.step(wl.dz, a.time)
+        s.diag()
+        for k, (ms, n) in s.profile_read().items():
+            if n:
+                print(f"profile_case: {k} {n} launches, {1e3 * ms / n:.2f} us per launch (events)")
+        s.profile(False)
+    print(f"profile_case: cartesian {wl.nx}x{wl.ny}x{wl.nt} {a.precision} steps {a.steps} "
+          f"variants {s.variants()} energy {d['energy']:.6e}")
     s.close()
     return 0 if ok else 1
 

@@ -74,3 +74,22 @@ def test_context_calls_reject_null_context(fcn):
     assert fcn.fcn_step(None, 1e-3, 1) == -1
     assert fcn.fcn_set_stream(None, None) == -1
     fcn.fcn_destroy(None)
+
+
+@pytest.mark.parametrize("nx,ny,nt,xw,code", [(2, 8, 16, 1e-3, -1), (8, 2, 16, 1e-3, -1),
+                                              (8, 8, 12, 1e-3, -1), (4096, 8, 16, 1e-3, -5),
+                                              (8, 8, 16384, 1e-3, -5), (8, 8, 16, -1.0, -1)])
+def test_xy_create_rejects_bad_grids_without_gpu(fcn, nx, ny, nt, xw, code):
+    g = fcn.fcn_grid_xy(nx, ny, nt, 0, xw, 1e-3, 1e-12)
+    p = fcn.make_params()
+    ctx = C.c_void_p()
+    assert fcn.fcn_xy_create(C.byref(g), C.byref(p), fcn.FCN_FP64, None, C.byref(ctx)) == code
+    assert ctx.value is None
+    assert len(fcn.fcn_xy_last_error(None)) > 0
+
+
+def test_xy_calls_reject_null_context(fcn):
+    assert fcn.fcn_xy_step(None, 1e-3, 1) == -1
+    assert fcn.fcn_xy_get_diag(None, None) == -1
+    assert fcn.fcn_xy_profile_read(None, None, None, 0) == -1
+    fcn.fcn_xy_destroy(None)
