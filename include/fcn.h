@@ -462,8 +462,10 @@ int  fcn_xy_step_nograph(fcn_xy_ctx *ctx, double dz, int64_t n);
 /* FP64 diagnostics of the current field (synchronises the stream).
  * Returns FCN_ERR_NONFINITE if the field holds NaN or Inf. */
 int  fcn_xy_get_diag(fcn_xy_ctx *ctx, fcn_diag *out);
-/* Forces the row-stage variant (0..2) and the line variant (0: chunks of
- * 16 nodes in FP32 / 8 in FP64, 1: half that); -1 returns to timing. */
+/* Forces the row-stage variant (0..2) and the line variant (0..5: the chunk
+ * of nodes a thread owns, 16 or 8 in FP32 and 8 or 4 in FP64, one or two
+ * lines per thread, CTAs of up to 512 or 256 threads); -1 returns to
+ * timing.  Every variant computes the same step (up to rounding order). */
 int  fcn_xy_set_variants(fcn_xy_ctx *ctx, int32_t row_variant, int32_t line_variant);
 int  fcn_xy_get_variants(const fcn_xy_ctx *ctx, int32_t out[2]);
 /* Per-launch CUDA-event timing (off by default; while on, steps launch

@@ -146,5 +146,67 @@ __device__ __forceinline__ cx<T> disp_apply(cx<T> x, const DispPhase<T> &p) {
     }
 }
 
+// chunk_scan for NP right-hand sides sharing one A: returns the value entering
+// this thread's chunk for each of them.  smB, smC hold NP * nwarp * C values.
+template <typename T, bool REV, int NP>
+__device__ __forceinline__ void chunk_scan_n(cx<T> A, cx<T> (&B)[NP], int C, int col, cx<T> *smA,
+                                             cx<T> *smB, cx<T> *smC, cx<T> (&out)[NP]) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int cpw = 32 / C;
+    const int ciw = lane / C;
+    for (int d = 1; d < cpw; d <<= 1) {
+        const cx<T> Ao = REV ? shfl_down_cx(A, d * C) : shfl_up_cx(A, d * C);
+        cx<T> Bo[NP];
+#pragma unroll
+        for (int i = 0; i < NP; ++i) Bo[i] = REV ? shfl_down_cx(B[i], d * C) : shfl_up_cx(B[i], d * C);
+        const bool take = REV ? (ciw + d < cpw) : (ciw >= d);
+        if (take) {
+#pragma unroll
+            for (int i = 0; i < NP; ++i) B[i] = cmul(A, Bo[i]) + B[i];
+            A = cmul(A, Ao);
+        }
+    }
+    cx<T> Ae = REV ? shfl_down_cx(A, C) : shfl_up_cx(A, C);
+    cx<T> Be[NP];
+#pragma unroll
+    for (int i = 0; i < NP; ++i) Be[i] = REV ? shfl_down_cx(B[i], C) : shfl_up_cx(B[i], C);
+    if (REV ? (ciw == cpw - 1) : (ciw == 0)) {
+        Ae = mk(T(1), T(0));
+#pragma unroll
+        for (int i = 0; i < NP; ++i) Be[i] = czero<T>();
+    }
+    const int nw = blockDim.x >> 5;
+    const int nwc = nw * C;
+#pragma unroll
+    for (int i = 0; i < NP; ++i) out[i] = Be[i];
+    if (nw > 1) {
+        if (REV ? (ciw == 0) : (ciw == cpw - 1)) {
+            smA[FCN_IDX(w * C + col, nwc, 54)] = A;
+#pragma unroll
+            for (int i = 0; i < NP; ++i) smB[FCN_IDX(i * nwc + w * C + col, NP * nwc, 55)] = B[i];
+        }
+        __syncthreads();
+        if ((int)threadIdx.x < C) {
+            const int c0 = threadIdx.x;
+            cx<T> c[NP];
+#pragma unroll
+            for (int i = 0; i < NP; ++i) c[i] = czero<T>();
+            for (int kk = 0; kk < nw; ++kk) {
+                const int k = REV ? nw - 1 - kk : kk;
+                const cx<T> Ak = smA[FCN_IDX(k * C + c0, nwc, 56)];
+#pragma unroll
+                for (int i = 0; i < NP; ++i) {
+                    smC[FCN_IDX(i * nwc + k * C + c0, NP * nwc, 57)] = c[i];
+                    c[i] = cmul(Ak, c[i]) + smB[FCN_IDX(i * nwc + k * C + c0, NP * nwc, 58)];
+                }
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < NP; ++i)
+            out[i] = cmul(Ae, smC[FCN_IDX(i * nwc + w * C + col, NP * nwc, 59)]) + Be[i];
+    }
+}
+
 }  // namespace colscan
 }  // namespace fcn

@@ -298,24 +298,28 @@ size_t row_batch_smem(int nt, int bytes_per_complex);
 //   field[b * bstride + j * pitch + c],  j = 0..n-1 (j = 0, n-1 the walls),
 // for b = 0..batch-1 and columns c = 0..width-1; the column's frequency bin
 // is q = c mod nt.  The y lines of an [nx][ny][nt] field are (b = x, c = q):
-// batch nx, width nt, pitch nt, bstride ny nt; the x lines are (c = y nt + q):
-// batch 1, width ny nt, pitch ny nt.
+// batch nx, width nt, pitch nt, bstride ny nt; the x lines are (b = y, c = q):
+// batch ny, width nt, pitch ny nt, bstride nt.
 template <typename T>
 struct XYLine {
     cx<T> *field;
     const cx<T> *invden;     // [n][nt/2+1]: 1/pivot_j per |q|
     int n, nt, width, batch;
     long long pitch, bstride;
+    long long total;         // elements of the field buffer
     T s;                     // dz / (4 k0 h^2), 0 without diffraction
     T dk;                    // delta_q = dk q^2 (0 in a line without dispersion)
     double disp;             // exact dispersion factor exp(2 i disp q^2), 0: none
-    int variant;             // 0: chunks of 16 (FP32) / 8 (FP64) rows, 1: half that
+    // chunk length L (long: 16 nodes in FP32, 8 in FP64; short: half),
+    // lines per thread NP and CTA size: 0 long/1/512, 1 short/1/512,
+    // 2 short/2/512, 3 short/2/256, 4 long/1/256, 5 short/1/256
+    int variant;
 };
 template <typename T>
 cudaError_t launch_xy_table(int n, int nt, double s, double dk, cx<T> *table, cudaStream_t st);
 template <typename T>
 cudaError_t launch_xy_line(const XYLine<T> &a, cudaStream_t st);
-constexpr int kXYVariants = 2;
+constexpr int kXYVariants = 6;
 
 // Learned dz controller (mlp.cu).
 struct MlpScalars {

@@ -119,13 +119,15 @@ RowArgs<T> row_args(fcn_xy_ctx *ctx, void *field, int ops, double dz) {
     return a;
 }
 
-// axis 0: the x lines (c = y nt + q, stride ny nt); axis 1: the y lines of
-// every x (c = q, stride nt), with the dispersion term.
+// axis 0: the x lines (b = y, c = q, stride ny nt); axis 1: the y lines
+// (b = x, c = q, stride nt), with the dispersion term.
 template <typename T>
 XYLine<T> line_args(fcn_xy_ctx *ctx, void *field, int axis, double dz) {
     XYLine<T> a;
     a.field = (cx<T> *)field;
     a.nt = ctx->g.nt;
+    a.width = ctx->g.nt;
+    a.total = ctx->points();
     double s, dk, disp;
     if (axis == 0) {
         line_coefs(ctx, dz, dx_of(ctx), &s, &dk, &disp);
@@ -133,15 +135,13 @@ XYLine<T> line_args(fcn_xy_ctx *ctx, void *field, int axis, double dz) {
         disp = 0.0;
         a.invden = (const cx<T> *)ctx->tab_x;
         a.n = ctx->g.nx;
-        a.width = ctx->g.ny * ctx->g.nt;
-        a.batch = 1;
+        a.batch = ctx->g.ny;
         a.pitch = (long long)ctx->g.ny * ctx->g.nt;
-        a.bstride = 0;
+        a.bstride = ctx->g.nt;
     } else {
         line_coefs(ctx, dz, dy_of(ctx), &s, &dk, &disp);
         a.invden = (const cx<T> *)ctx->tab_y;
         a.n = ctx->g.ny;
-        a.width = ctx->g.nt;
         a.batch = ctx->g.nx;
         a.pitch = ctx->g.nt;
         a.bstride = (long long)ctx->g.ny * ctx->g.nt;

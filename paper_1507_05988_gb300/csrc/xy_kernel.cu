@@ -18,10 +18,11 @@
 // once per dz (xy_table_kernel, FP64, stored as 1/pivot in the working
 // precision), and the two sweeps run as the chunked parallel scan of affine
 // maps that the radial column stage uses (colscan::chunk_scan): a thread
-// owns L consecutive nodes of one line in registers.  The lines of one
-// launch are addressed as base + j * pitch + c (see XYLine), so the x lines
-// (stride ny*nt) and the y lines (stride nt) use the same kernel, with C
-// adjacent columns per CTA for whole-sector row accesses.
+// owns L consecutive nodes of one line (or of NP lines of the same
+// frequency bin, which share the pivots) in registers.  The lines of one
+// launch are addressed as b * bstride + j * pitch + c (see XYLine), so the x
+// lines (stride ny*nt) and the y lines (stride nt) use the same kernel, with
+// C adjacent frequency columns per CTA for whole-sector row accesses.
 #include "col_scan.cuh"
 
 namespace fcn {
@@ -50,14 +51,17 @@ __global__ void xy_table_kernel(int n, int nt, double s, double dk, cx<T> *table
     }
 }
 
-template <typename T, int L>
+// NP lines per thread: batch items b = NP blockIdx.y + i (i < NP) at the
+// same column c share the frequency bin, hence the pivots and the A part of
+// every affine map; their recurrences run side by side (independent chains).
+template <typename T, int L, int NP>
 __global__ void __launch_bounds__(512)
 xy_line_kernel(XYLine<T> a, int C) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nwarp = blockDim.x >> 5;
     cx<T> *smA = reinterpret_cast<cx<T> *>(smem_raw);
     cx<T> *smB = smA + nwarp * C;
-    cx<T> *smC = smB + nwarp * C;
+    cx<T> *smC = smB + NP * nwarp * C;
 
     const int tid = threadIdx.x;
     const int col = tid % C;
@@ -70,20 +74,25 @@ xy_line_kernel(XYLine<T> a, int C) {
     const T s = a.s;
     const T g1 = T(2) * s - a.dk * T(qq) * T(qq);   // interior: e = 1 - i g1
     const int j0 = chunk * L;
-    // the field holds (batch - 1) bstride + n pitch elements; this line starts
-    // at `off` of them
-    const size_t off = (size_t)blockIdx.y * (size_t)a.bstride + c;
-    const size_t room = (size_t)(a.batch - 1) * (size_t)a.bstride + (size_t)n * a.pitch - off;
-    cx<T> *line = a.field + off;
-
-    cx<T> x[L + 2];
+    cx<T> *line[NP];
+    bool on[NP];
 #pragma unroll
-    for (int k = 0; k < L + 2; ++k) {
-        const int j = j0 - 1 + k;
-        x[k] = (j >= 0 && j < n)
-                   ? line[FCN_IDX((size_t)j * a.pitch, room, 71)]
-                   : czero<T>();
+    for (int i = 0; i < NP; ++i) {
+        const int b = blockIdx.y * NP + i;
+        on[i] = b < a.batch;
+        line[i] = a.field + (size_t)(on[i] ? b : 0) * (size_t)a.bstride + c;
     }
+
+    cx<T> x[NP][L + 2];
+#pragma unroll
+    for (int i = 0; i < NP; ++i)
+#pragma unroll
+        for (int k = 0; k < L + 2; ++k) {
+            const int j = j0 - 1 + k;
+            x[i][k] = (on[i] && j >= 0 && j < n)
+                          ? a.field[FCN_IDX(line[i] - a.field + (size_t)j * a.pitch, a.total, 71)]
+                          : czero<T>();
+        }
     cx<T> inv[L];
 #pragma unroll
     for (int k = 0; k < L; ++k) {
@@ -93,67 +102,87 @@ xy_line_kernel(XYLine<T> a, int C) {
 
     // forward sweep, pass 1: y_j = alpha_j y_{j-1} + beta_j per node, and the
     // chunk's composed map y_end = PA y_in + PB
-    cx<T> y[L];
-    cx<T> PA = mk(T(1), T(0)), PB = czero<T>();
+    cx<T> y[NP][L];
+    cx<T> PA = mk(T(1), T(0)), PB[NP];
+#pragma unroll
+    for (int i = 0; i < NP; ++i) PB[i] = czero<T>();
 #pragma unroll
     for (int k = 0; k < L; ++k) {
         const int j = j0 + k;
-        const bool inner = j >= 1 && j < n - 1;
-        if (inner) {
-            const cx<T> w = mk(s * (x[k].x + x[k + 2].x) - g1 * x[k + 1].x,
-                               s * (x[k].y + x[k + 2].y) - g1 * x[k + 1].y);
-            const cx<T> rhs = mk(x[k + 1].x - w.y, x[k + 1].y + w.x);
+        if (j >= 1 && j < n - 1) {
             const cx<T> alpha = cmul_i(inv[k], s);
-            y[k] = cmul(rhs, inv[k]);
-            PB = cmul(alpha, PB) + y[k];
+#pragma unroll
+            for (int i = 0; i < NP; ++i) {
+                const cx<T> w = mk(s * (x[i][k].x + x[i][k + 2].x) - g1 * x[i][k + 1].x,
+                                   s * (x[i][k].y + x[i][k + 2].y) - g1 * x[i][k + 1].y);
+                const cx<T> rhs = mk(x[i][k + 1].x - w.y, x[i][k + 1].y + w.x);
+                y[i][k] = cmul(rhs, inv[k]);
+                PB[i] = cmul(alpha, PB[i]) + y[i][k];
+            }
             PA = cmul(alpha, PA);
         } else {
-            // walls (and nodes past the end): y = 0, the map sends all to 0
-            y[k] = czero<T>();
-            if (j < n) {
-                PA = czero<T>();
-                PB = czero<T>();
+            // walls: y = 0 and the map sends everything to 0; nodes past the
+            // end of the line: identity
+#pragma unroll
+            for (int i = 0; i < NP; ++i) {
+                y[i][k] = czero<T>();
+                if (j < n) PB[i] = czero<T>();
             }
+            if (j < n) PA = czero<T>();
         }
     }
     // forward sweep, pass 2: exact y from the carry entering the chunk
     {
-        cx<T> yp = chunk_scan<T, false>(PA, PB, C, col, smA, smB, smC);
+        cx<T> yp[NP];
+        chunk_scan_n<T, false, NP>(PA, PB, C, col, smA, smB, smC, yp);
 #pragma unroll
         for (int k = 0; k < L; ++k) {
             const int j = j0 + k;
-            if (j >= 1 && j < n - 1) {
-                y[k] = cmul(cmul_i(inv[k], s), yp) + y[k];
-                yp = y[k];
-            } else if (j < n) {
-                yp = czero<T>();
+            const bool inner = j >= 1 && j < n - 1;
+            const cx<T> alpha = cmul_i(inv[k], s);
+#pragma unroll
+            for (int i = 0; i < NP; ++i) {
+                if (inner) {
+                    y[i][k] = cmul(alpha, yp[i]) + y[i][k];
+                    yp[i] = y[i][k];
+                } else if (j < n) {
+                    yp[i] = czero<T>();
+                }
             }
         }
     }
     // backward sweep, pass 1: chunk map x_first = QA x_next + QB, with
     // x_j = gamma_j x_{j+1} + y_j, gamma_j = is / piv_j inside, 0 at walls
-    cx<T> QA = mk(T(1), T(0)), QB = czero<T>();
+    cx<T> QA = mk(T(1), T(0)), QB[NP];
+#pragma unroll
+    for (int i = 0; i < NP; ++i) QB[i] = czero<T>();
 #pragma unroll
     for (int k = L - 1; k >= 0; --k) {
         const int j = j0 + k;
         if (j < n) {
             const cx<T> gamma = (j >= 1 && j < n - 1) ? cmul_i(inv[k], s) : czero<T>();
-            QB = cmul(gamma, QB) + y[k];
+#pragma unroll
+            for (int i = 0; i < NP; ++i) QB[i] = cmul(gamma, QB[i]) + y[i][k];
             QA = cmul(gamma, QA);
         }
     }
     // backward sweep, pass 2 and store
     {
-        cx<T> xn = chunk_scan<T, true>(QA, QB, C, col, smA, smB, smC);
+        cx<T> xn[NP];
+        chunk_scan_n<T, true, NP>(QA, QB, C, col, smA, smB, smC, xn);
         const DispPhase<T> ph = disp_phase<T>(a.disp, qq);
 #pragma unroll
         for (int k = L - 1; k >= 0; --k) {
             const int j = j0 + k;
             if (j < n) {
                 const cx<T> gamma = (j >= 1 && j < n - 1) ? cmul_i(inv[k], s) : czero<T>();
-                xn = cmul(gamma, xn) + y[k];
-                line[FCN_IDX((size_t)j * a.pitch, room, 73)] =
-                    disp_apply(xn, ph);
+#pragma unroll
+                for (int i = 0; i < NP; ++i) {
+                    xn[i] = cmul(gamma, xn[i]) + y[i][k];
+                    if (on[i])
+                        a.field[FCN_IDX(line[i] - a.field + (size_t)j * a.pitch, a.total, 73)] =
+                            disp_apply(xn[i], ph);
+                }
             }
         }
     }
@@ -162,7 +191,7 @@ xy_line_kernel(XYLine<T> a, int C) {
 // C columns per CTA: at least one 32-byte sector, doubled while the CTA
 // stays within `target` threads; whole warps (chunks past the line's end
 // are identity maps).
-template <typename T, int L>
+template <typename T, int L, int NP>
 cudaError_t launch_xy_l(const XYLine<T> &a, int target, cudaStream_t st) {
     constexpr int CMIN = 32 / int(sizeof(cx<T>));
     const int P = (a.n + L - 1) / L;
@@ -172,8 +201,9 @@ cudaError_t launch_xy_l(const XYLine<T> &a, int target, cudaStream_t st) {
     const int threads = ((C * P + 31) / 32) * 32;
     if (threads > 512) return cudaErrorInvalidConfiguration;
     if (a.width % C != 0) return cudaErrorInvalidValue;
-    const size_t smem = sizeof(cx<T>) * 3 * (size_t)(threads / 32) * C;
-    return launch_k(xy_line_kernel<T, L>, dim3(a.width / C, a.batch), dim3(threads), smem, st, a, C);
+    const size_t smem = sizeof(cx<T>) * (1 + 2 * NP) * (size_t)(threads / 32) * C;
+    const dim3 grid(a.width / C, (a.batch + NP - 1) / NP);
+    return launch_k(xy_line_kernel<T, L, NP>, grid, dim3(threads), smem, st, a, C);
 }
 
 }  // namespace
@@ -187,14 +217,20 @@ cudaError_t launch_xy_table(int n, int nt, double s, double dk, cx<T> *table, cu
 
 template <typename T>
 cudaError_t launch_xy_line(const XYLine<T> &a, cudaStream_t st) {
-    if (a.n < 3 || a.nt < 1 || (a.nt & (a.nt - 1)) || a.width < a.nt || a.batch < 1)
+    if (a.n < 3 || a.nt < 1 || (a.nt & (a.nt - 1)) || a.width < 1 || (a.width % a.nt) || a.batch < 1)
         return cudaErrorInvalidValue;
-    if (a.width == 0) return cudaSuccess;
-    constexpr int LL = sizeof(T) == 4 ? 16 : 8;
-    constexpr int LS = LL / 2;
+    constexpr int LL = sizeof(T) == 4 ? 16 : 8;   // long chunk
+    constexpr int LS = LL / 2;                     // short chunk
     cudaError_t e = cudaErrorInvalidConfiguration;
-    if (a.variant == 1) e = launch_xy_l<T, LS>(a, 512, st);
-    if (e == cudaErrorInvalidConfiguration) e = launch_xy_l<T, LL>(a, 512, st);
+    switch (a.variant) {
+        case 1: e = launch_xy_l<T, LS, 1>(a, 512, st); break;
+        case 2: e = launch_xy_l<T, LS, 2>(a, 512, st); break;
+        case 3: e = launch_xy_l<T, LS, 2>(a, 256, st); break;
+        case 4: e = launch_xy_l<T, LL, 1>(a, 256, st); break;
+        case 5: e = launch_xy_l<T, LS, 1>(a, 256, st); break;
+        default: break;
+    }
+    if (e == cudaErrorInvalidConfiguration) e = launch_xy_l<T, LL, 1>(a, 512, st);
     return e;
 }
 
