@@ -13,8 +13,10 @@ Also reported on the same line: the kernel roofline of the dominant kernel
 (CUDA-event durations of a profiled replay of the timed steps), the
 end-to-end figure through the C-ABI with host buffers, the plain FP64 path on
 the same batch, the FP32-vs-FP64 field difference after the full 1000-step
-run of one pulse, SM clocks sampled during the timed region, and the FP64
-CPU oracle timed on a bounded sample (rank 0, N = 1).
+run of one pulse, SM clocks sampled during the timed region, the FP64
+CPU oracle timed on a bounded sample (rank 0, N = 1), and the Cartesian
+(3D+1) grid: config 1's pulse on 255 x 255 x 256 nodes, 200 steps of 1 cm,
+FP32-mixed against FP64, with its own kernel fractions and roofline.
 
 --impl reference times that oracle (the deliberately slow CPU program the
 CUDA path is checked against) on the same metric.
@@ -48,6 +50,7 @@ def parse():
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-cfg4", action="store_true")
     ap.add_argument("--cfg4-steps", type=int, default=20)
+    ap.add_argument("--no-cartesian", action="store_true")
     ap.add_argument("--oracle-scaling", action="store_true",
                     help="only run the oracle's thread-scaling table on the paper's grid (CPU)")
     return ap.parse_args()
@@ -242,46 +245,110 @@ def oracle_thread_scaling(steps=3):
     return 0
 
 
-def accuracy_leg(fcn, wl, field, dz):
+def accuracy_leg(fcn, wl, field, dz, make=None, checkpoints=None):
     """FP32-mixed against the FP64 GPU path over the full fixed-step run, at
     checkpoints; beside it the same FP64 path started from the field times
     (1 + 6e-8 xi), xi uniform in [-1, 1] (a perturbation of FP32 rounding
     size): where that run drifts as far from the unperturbed one as FP32
-    does, the difference is the problem's conditioning, not the arithmetic."""
+    does, the difference is the problem's conditioning, not the arithmetic.
+    make(precision) builds the solver (default: a radial Solver of wl)."""
     import numpy as np
+    if make is None:
+        def make(prec):
+            return fcn.Solver(wl.physics(), precision=prec)
     rng = np.random.default_rng(12345)
     pert = field * (1.0 + 6e-8 * rng.uniform(-1.0, 1.0, field.shape))
-    runs = {"fp32": (fcn.FCN_FP32_MIXED, field), "fp64": (fcn.FCN_FP64, field),
-            "fp64_perturbed": (fcn.FCN_FP64, pert)}
-    checkpoints = [c for c in (100, 200, 300, 400, 500, 750, 1000) if c <= wl.nsteps]
-    if wl.nsteps not in checkpoints:
-        checkpoints.append(wl.nsteps)
-    snaps = {}
-    for name, (prec, f0) in runs.items():
-        s = fcn.Solver(wl.physics(), precision=prec)
+    if checkpoints is None:
+        checkpoints = [c for c in (100, 200, 300, 400, 500, 750, 1000) if c <= wl.nsteps]
+        if wl.nsteps not in checkpoints:
+            checkpoints.append(wl.nsteps)
+
+    def run(prec, f0, visit):
+        s = make(prec)
         s.set_field(f0)
         done = 0
         for c in checkpoints:
             s.step(dz, c - done)
             done = c
-            snaps[(name, c)] = (s.get_field(), s.diag()["energy"])
+            visit(c, s.get_field(), s.diag()["energy"])
         s.close()
-    table = []
-    for c in checkpoints:
-        ref, eref = snaps[("fp64", c)]
-        table.append({
-            "steps": c,
-            "fp32_field_rel_l2": rel_l2(snaps[("fp32", c)][0], ref),
-            "fp32_energy_rel": abs(snaps[("fp32", c)][1] / eref - 1),
-            "fp64_perturbed_field_rel_l2": rel_l2(snaps[("fp64_perturbed", c)][0], ref),
-            "fp64_perturbed_energy_rel": abs(snaps[("fp64_perturbed", c)][1] / eref - 1),
-        })
+
+    ref = {}
+    run(fcn.FCN_FP64, field, lambda c, a, e: ref.__setitem__(c, (a, e)))
+    table = {c: {"steps": c} for c in checkpoints}
+    for name, prec, f0 in (("fp32", fcn.FCN_FP32_MIXED, field), ("fp64_perturbed", fcn.FCN_FP64, pert)):
+        def visit(c, a, e, name=name):
+            table[c][name + "_field_rel_l2"] = rel_l2(a, ref[c][0])
+            table[c][name + "_energy_rel"] = abs(e / ref[c][1] - 1)
+        run(prec, f0, visit)
+    table = [table[c] for c in checkpoints]
     last = table[-1]
     return {"field_rel_l2": last["fp32_field_rel_l2"], "energy_rel": last["fp32_energy_rel"],
-            "run": f"{wl.nsteps} steps of dz = {dz} m, pulse seed 0, FP32-mixed vs FP64 GPU path",
+            "run": f"{checkpoints[-1]} steps of dz = {dz} m, FP32-mixed vs FP64 GPU path",
             "checkpoints": table,
             "conditioning": "fp64_perturbed_*: the FP64 path from the field times (1 + 6e-8 xi), "
                             "xi ~ U[-1, 1], against the unperturbed FP64 path"}
+
+
+def cartesian_leg(fcn, W, pg, world, accuracy=True):
+    """Config 1's pulse on the 255 x 255 x 256 Cartesian grid (x and y
+    Crank-Nicolson factors): the full 200-step run timed in FP32-mixed and in
+    FP64 (CUDA events on the launch stream), the FP32 field and energy
+    against the FP64 path at checkpoints (accuracy_leg), and per-kernel CUDA-event times of
+    a profiled replay with their algorithmic HBM fractions (one complex64
+    field read and write per point and launch)."""
+    import torch
+    wl = W.cartesian_config1()
+    pts, K = wl.points, wl.nsteps
+    f = wl.field()
+    out = {"workload": f"{wl.name}: {wl.nx}x{wl.ny}x{wl.nt} nodes over 10 w0 x 10 w0 x 16 tp "
+                       f"(w0=1 mm, tp=100 fs, 3 Pcr, n2), {K} steps of {wl.dz} m",
+           "points": pts, "steps": K,
+           "l2": f"field {pts * 8 / 1e6:.0f} MB complex64 vs 129 MB L2"}
+    for prec, name in ((fcn.FCN_FP32_MIXED, "fp32"), (fcn.FCN_FP64, "fp64")):
+        s = fcn.SolverXY(wl.grid(), wl.physics(), precision=prec)
+        s.set_field(f)
+        s.step(wl.dz, 3)                         # warm-up (and variant timing)
+        s.set_field(f)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        s.step(wl.dz, K)
+        b.record()
+        torch.cuda.synchronize()
+        t = reduce_max(a.elapsed_time(b), pg, "cuda")
+        out[name] = {"value": weak_scaling_value(world, pts, K, t), "ms_per_step": t / K,
+                     "variants": {"row": s.variants()[0], "line": s.variants()[1]}}
+        if name == "fp32":
+            s.profile(True)
+            s.step(wl.dz, K)
+            prof = s.profile_read(reset=True)
+            s.profile(False)
+            peak, peak_src = measured_peaks()
+            kernels = {}
+            for k, (ms, n) in prof.items():
+                gbps = n * 2 * pts * 8 / (ms * 1e-3) / 1e9 if ms else None
+                kernels[k] = {"launches": n, "total_ms": ms, "avg_us": (ms / n * 1e3 if n else None),
+                              "alg_GBps": gbps, "frac_of_hbm_peak": (gbps / peak if gbps else None)}
+            dom = max(prof.items(), key=lambda kv: kv[1][0])[0]
+            traffic = None
+            tpath = os.path.join(ROOT, "profiles", "traffic.json")
+            if os.path.exists(tpath):
+                with open(tpath) as fh:
+                    traffic = json.load(fh).get("cart_" + dom)
+            out["gpu_launches"] = int(sum(n for _, n in prof.values()))
+            out["kernels"] = kernels
+            out["roofline"] = {"bound": "hbm", "achieved": kernels[dom]["alg_GBps"], "peak": peak,
+                               "unit": "GB/s", "frac": kernels[dom]["alg_GBps"] / peak,
+                               "traffic": traffic, "kernel": dom, "peak_source": peak_src,
+                               "algorithmic_bytes_per_launch": 2 * pts * 8}
+        s.close()
+    out["speedup_fp32_over_fp64"] = out["fp32"]["value"] / out["fp64"]["value"]
+    if accuracy:
+        out["accuracy_vs_fp64"] = accuracy_leg(
+            fcn, wl, f, wl.dz, make=lambda prec: fcn.SolverXY(wl.grid(), wl.physics(), precision=prec),
+            checkpoints=[25, 50, 100, 150, K])
+    return out
 
 
 def run_ours(args):
@@ -428,6 +495,10 @@ def run_ours(args):
             cfg4[name] = pts4 * args.cfg4_steps / (a4.elapsed_time(b4) * 1e-3)
         s4.close()
 
+    # ---- Cartesian transverse grid (3D+1) ----
+    cart = None if args.no_cartesian else cartesian_leg(fcn, W, pg, world,
+                                                        accuracy=rank == 0 and not args.no_accuracy)
+
     # ---- plain FP64 FCN on the same batch ----
     K64 = max(2, min(args.steps, 6))
     s64 = fcn.Solver([w.physics() for w in wls], precision=fcn.FCN_FP64)
@@ -476,6 +547,7 @@ def run_ours(args):
                          "note": "achieved = algorithmic bytes / mean CUDA-event launch time"},
             "kernels": kernels,
             "batched_cfg4": cfg4,
+            "cartesian_3d1": cart,
             "fp64_gpu": {"value": v64, "unit": UNIT, "steps": K64,
                          "speedup_of_chosen_form": value / v64},
             "accuracy_vs_fp64": acc,
