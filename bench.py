@@ -450,15 +450,21 @@ def run_ours(args):
     def e2e_run(dtype, setf, getf, ptr):
         host_in = [torch.from_numpy(f.astype(dtype)).pin_memory() for f in fields]
         host_out = [torch.empty_like(h).pin_memory() for h in host_in]
-        torch.cuda.synchronize()
-        barrier()
-        t0 = time.perf_counter()
-        for _ in range(K2):
+
+        def one_step():
             for i in range(B):
                 fcn.check(setf(solver.ctx, i, C.cast(host_in[i].data_ptr(), ptr)), solver.ctx)
             solver.step(dz, 1)
             for i in range(B):
                 fcn.check(getf(solver.ctx, i, C.cast(host_out[i].data_ptr(), ptr)), solver.ctx)
+
+        for _ in range(3):       # untimed warm-up (first touch of the pinned buffers)
+            one_step()
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(K2):
+            one_step()
         torch.cuda.synchronize()
         return reduce_max(time.perf_counter() - t0, pg, "cuda")
 

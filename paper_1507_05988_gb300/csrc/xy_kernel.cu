@@ -54,8 +54,8 @@ __global__ void xy_table_kernel(int n, int nt, double s, double dk, cx<T> *table
 // NP lines per thread: batch items b = NP blockIdx.y + i (i < NP) at the
 // same column c share the frequency bin, hence the pivots and the A part of
 // every affine map; their recurrences run side by side (independent chains).
-template <typename T, int L, int NP>
-__global__ void __launch_bounds__(512)
+template <typename T, int L, int NP, int MAXT = 512, int MINB = 1>
+__global__ void __launch_bounds__(MAXT, MINB)
 xy_line_kernel(XYLine<T> a, int C) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nwarp = blockDim.x >> 5;
@@ -191,7 +191,7 @@ xy_line_kernel(XYLine<T> a, int C) {
 // C columns per CTA: at least one 32-byte sector, doubled while the CTA
 // stays within `target` threads; whole warps (chunks past the line's end
 // are identity maps).
-template <typename T, int L, int NP>
+template <typename T, int L, int NP, int MAXT = 512, int MINB = 1>
 cudaError_t launch_xy_l(const XYLine<T> &a, int target, cudaStream_t st) {
     constexpr int CMIN = 32 / int(sizeof(cx<T>));
     const int P = (a.n + L - 1) / L;
@@ -199,11 +199,11 @@ cudaError_t launch_xy_l(const XYLine<T> &a, int target, cudaStream_t st) {
     while (C * 2 * P <= target && C * 2 <= 32) C *= 2;
     if (C > a.nt) C = a.nt;
     const int threads = ((C * P + 31) / 32) * 32;
-    if (threads > 512) return cudaErrorInvalidConfiguration;
+    if (threads > MAXT) return cudaErrorInvalidConfiguration;
     if (a.width % C != 0) return cudaErrorInvalidValue;
     const size_t smem = sizeof(cx<T>) * (1 + 2 * NP) * (size_t)(threads / 32) * C;
     const dim3 grid(a.width / C, (a.batch + NP - 1) / NP);
-    return launch_k(xy_line_kernel<T, L, NP>, grid, dim3(threads), smem, st, a, C);
+    return launch_k(xy_line_kernel<T, L, NP, MAXT, MINB>, grid, dim3(threads), smem, st, a, C);
 }
 
 }  // namespace
@@ -228,6 +228,7 @@ cudaError_t launch_xy_line(const XYLine<T> &a, cudaStream_t st) {
         case 3: e = launch_xy_l<T, LS, 2>(a, 256, st); break;
         case 4: e = launch_xy_l<T, LL, 1>(a, 256, st); break;
         case 5: e = launch_xy_l<T, LS, 1>(a, 256, st); break;
+        case 6: e = launch_xy_l<T, LS, 2, 256, 3>(a, 256, st); break;
         default: break;
     }
     if (e == cudaErrorInvalidConfiguration) e = launch_xy_l<T, LL, 1>(a, 512, st);

@@ -90,7 +90,7 @@ def test_graph_replay_equals_direct_launches_and_variants_agree(fcn, prec):
     assert np.array_equal(A0, A1)
     ref = _oracle_run(wl, 17)[2]
     tol = 1e-10 if prec == FP64 else 1e-4
-    for v in ((0, 0), (0, 1), (0, 2), (0, 3), (0, 4), (2, 5)):
+    for v in ((0, 0), (0, 1), (0, 2), (0, 3), (0, 4), (2, 5), (1, 6)):
         A, _, _ = _gpu_run(fcn, wl, 17, prec, variants=v)
         assert rel_l2(A, ref) < tol, v
 
