@@ -462,7 +462,7 @@ int  fcn_xy_step_nograph(fcn_xy_ctx *ctx, double dz, int64_t n);
 /* FP64 diagnostics of the current field (synchronises the stream).
  * Returns FCN_ERR_NONFINITE if the field holds NaN or Inf. */
 int  fcn_xy_get_diag(fcn_xy_ctx *ctx, fcn_diag *out);
-/* Forces the row-stage variant (0..2) and the line variant (0..6: the chunk
+/* Forces the row-stage variant (0..2) and the line variant (0..7: the chunk
  * of nodes a thread owns, 16 or 8 in FP32 and 8 or 4 in FP64, one or two
  * lines per thread, CTAs of up to 512 or 256 threads); -1 returns to
  * timing.  Every variant computes the same step (up to rounding order). */

@@ -313,14 +313,14 @@ struct XYLine {
     // chunk length L (long: 16 nodes in FP32, 8 in FP64; short: half),
     // lines per thread NP and CTA size: 0 long/1/512, 1 short/1/512,
     // 2 short/2/512, 3 short/2/256, 4 long/1/256, 5 short/1/256,
-    // 6 short/2/256 compiled for three CTAs per SM
+    // 6 short/2/256 compiled for three CTAs per SM, 7 short/1/256 for four
     int variant;
 };
 template <typename T>
 cudaError_t launch_xy_table(int n, int nt, double s, double dk, cx<T> *table, cudaStream_t st);
 template <typename T>
 cudaError_t launch_xy_line(const XYLine<T> &a, cudaStream_t st);
-constexpr int kXYVariants = 7;
+constexpr int kXYVariants = 8;
 
 // Learned dz controller (mlp.cu).
 struct MlpScalars {

@@ -1125,7 +1125,7 @@ size_t smem_bytes(bool with_u = true) {
 // launch of it (and outside stream capture).
 // Occupancy variants: v = 0 is the compiler's natural allocation; v = 1, 2
 // ask for 3 and 4 CTAs of 256 threads per SM (80 and 64 registers), or 2 CTAs
-// of 512 threads for Nt = 8192.  Only FP32 with K = 8 and Nt >= 512 has
+// of 512 threads for Nt = 8192.  Only FP32 with K = 8 and Nt >= 256 has
 // variants (smaller rows are cheap; their variants map to v = 0).
 template <int NT>
 constexpr int mb_of(int v) {
@@ -1146,7 +1146,7 @@ template <typename T, int NT>
 cudaError_t prepare_nt() {
     cudaError_t e = set_smem_attr<T, NT, 0, 1>();
     if (e == cudaSuccess) e = set_smem_attr<T, NT, 8, 1>();
-    if constexpr (sizeof(T) == 4 && NT >= 512) {
+    if constexpr (sizeof(T) == 4 && NT >= 256) {
         if (e == cudaSuccess) e = set_smem_attr<T, NT, 8, mb_of<NT>(1)>();
         if (e == cudaSuccess) e = set_smem_attr<T, NT, 8, mb_of<NT>(2)>();
     }
@@ -1164,7 +1164,7 @@ cudaError_t launch_nt_multi(const RowMultiArgs<T> &m, int npulse, cudaStream_t s
     void (*k)(const RowMultiArgs<T>) = row_kernel_multi<T, NT, 8, 1>;
     if (a.nl.K != 8) {
         k = row_kernel_multi<T, NT, 0, 1>;
-    } else if constexpr (sizeof(T) == 4 && NT >= 512) {
+    } else if constexpr (sizeof(T) == 4 && NT >= 256) {
         if (a.variant == 1) k = row_kernel_multi<T, NT, 8, mb_of<NT>(1)>;
         else if (a.variant == 2) k = row_kernel_multi<T, NT, 8, mb_of<NT>(2)>;
     }
@@ -1181,7 +1181,7 @@ cudaError_t launch_nt(const RowArgs<T> &a, cudaStream_t st) {
     void (*k)(RowArgs<T>) = row_kernel<T, NT, 8, 1>;
     if (a.nl.K != 8) {
         k = row_kernel<T, NT, 0, 1>;
-    } else if constexpr (sizeof(T) == 4 && NT >= 512) {
+    } else if constexpr (sizeof(T) == 4 && NT >= 256) {
         if (a.variant == 1) k = row_kernel<T, NT, 8, mb_of<NT>(1)>;
         else if (a.variant == 2) k = row_kernel<T, NT, 8, mb_of<NT>(2)>;
     }

@@ -229,6 +229,7 @@ cudaError_t launch_xy_line(const XYLine<T> &a, cudaStream_t st) {
         case 4: e = launch_xy_l<T, LL, 1>(a, 256, st); break;
         case 5: e = launch_xy_l<T, LS, 1>(a, 256, st); break;
         case 6: e = launch_xy_l<T, LS, 2, 256, 3>(a, 256, st); break;
+        case 7: e = launch_xy_l<T, LS, 1, 256, 4>(a, 256, st); break;
         default: break;
     }
     if (e == cudaErrorInvalidConfiguration) e = launch_xy_l<T, LL, 1>(a, 512, st);

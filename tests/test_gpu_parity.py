@@ -392,6 +392,21 @@ def test_every_kernel_variant_matches_oracle(fcn, prec, row_v, col_v):
     assert rel_l2(A, Aref) < (1e-10 if prec == FP64 else 1e-5)
 
 
+@pytest.mark.parametrize("row_v", [0, 1, 2])
+def test_row_occupancy_variants_at_nt_256(fcn, row_v):
+    """Nt = 256 rows (config 1, the Cartesian grid) have their own FP32
+    occupancy variants (3 and 4 CTAs per SM)."""
+    wl = W.small(70, 256, p_over_pcr=4.0, noise_seed=8)
+    s = fcn.Solver(wl.physics(), precision=FP32)
+    s.set_variants(row_v, 0)
+    s.set_field(wl.field())
+    s.step(1e-2, 6)
+    A = s.get_field()
+    s.close()
+    Aref, _ = oracle.run(_pb(wl), 1e-2, 6, wl.field())
+    assert rel_l2(A, Aref) < 1e-5
+
+
 @pytest.mark.parametrize("prec", [FP64, FP32])
 @pytest.mark.parametrize("nr,nt", [(3, 64), (17, 128), (1000, 256), (2048, 64)])
 @pytest.mark.parametrize("col_v", [4, 5, 6, 7])

@@ -84,13 +84,13 @@ def test_fp64_physics_variants_match_the_oracle(fcn):
 
 @pytest.mark.parametrize("prec", [FP64, FP32])
 def test_graph_replay_equals_direct_launches_and_variants_agree(fcn, prec):
-    wl = W.small_xy(25, 19, 128, noise_seed=1, dz=1e-2)
+    wl = W.small_xy(25, 19, 256, noise_seed=1, dz=1e-2)
     A0, _, _ = _gpu_run(fcn, wl, 17, prec, graph=True)
     A1, _, _ = _gpu_run(fcn, wl, 17, prec, graph=False)
     assert np.array_equal(A0, A1)
     ref = _oracle_run(wl, 17)[2]
     tol = 1e-10 if prec == FP64 else 1e-4
-    for v in ((0, 0), (0, 1), (0, 2), (0, 3), (0, 4), (2, 5), (1, 6)):
+    for v in ((0, 0), (1, 1), (2, 2), (0, 3), (1, 4), (2, 5), (1, 6), (2, 7)):
         A, _, _ = _gpu_run(fcn, wl, 17, prec, variants=v)
         assert rel_l2(A, ref) < tol, v
 
