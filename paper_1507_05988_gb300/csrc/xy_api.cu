@@ -13,6 +13,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <tuple>
 #include <utility>
 #include <vector>
 
@@ -208,10 +209,10 @@ int ensure_tables(fcn_xy_ctx *ctx, double dz) {
     return FCN_OK;
 }
 
-// Variant timing per (precision, nx, ny, nt), process-wide: every row
-// variant (FP32, K = 8) and line variant, three interleaved rounds of a few
-// launches on a scratch copy of the field, the best round counting.
-std::map<std::tuple<int, int, int, int>, std::pair<int, int>> g_xy_tune;
+// Variant timing per (precision, nx, ny, nt, K = 8 or not), process-wide:
+// every row variant (FP32, K = 8) and line variant, three interleaved rounds
+// of a few launches on a scratch copy of the field, the best round counting.
+std::map<std::tuple<int, int, int, int, bool>, std::pair<int, int>> g_xy_tune;
 
 template <typename F>
 int time_launches(fcn_xy_ctx *ctx, F &&launch, float *ms_out) {
@@ -235,7 +236,7 @@ template <typename T>
 int ensure_tuned(fcn_xy_ctx *ctx, double dz) {
     if (ctx->tuned) return FCN_OK;
     std::lock_guard<std::mutex> lk(g_xy_mu);
-    auto key = std::make_tuple(ctx->prec, ctx->g.nx, ctx->g.ny, ctx->g.nt);
+    auto key = std::make_tuple(ctx->prec, ctx->g.nx, ctx->g.ny, ctx->g.nt, ctx->p.K == 8);
     auto it = g_xy_tune.find(key);
     const bool need = (ctx->force_row < 0 || ctx->force_line < 0) && it == g_xy_tune.end();
     if (need) {
@@ -577,10 +578,11 @@ int fcn_xy_get_diag(fcn_xy_ctx *ctx, fcn_diag *out) {
 
 int fcn_xy_set_variants(fcn_xy_ctx *ctx, int32_t row_variant, int32_t line_variant) {
     if (!ctx) return FCN_ERR_ARG;
-    if (row_variant >= kRowVariants || line_variant >= kXYVariants)
+    if (row_variant < -1 || row_variant >= kRowVariants || line_variant < -1 || line_variant >= kXYVariants)
         return fail(ctx, FCN_ERR_ARG, "variant out of range");
-    ctx->force_row = row_variant < 0 ? -1 : row_variant;
-    ctx->force_line = line_variant < 0 ? -1 : line_variant;
+    CK(cudaStreamSynchronize(ctx->st), "sync");
+    ctx->force_row = row_variant;
+    ctx->force_line = line_variant;
     ctx->tuned = false;
     for (auto &kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
     ctx->graphs.clear();
