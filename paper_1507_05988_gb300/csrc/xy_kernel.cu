@@ -17,7 +17,7 @@
 // The matrix depends on (j, |q|, dz) only; its Thomas pivots are computed
 // once per dz (xy_table_kernel, FP64, stored as 1/pivot in the working
 // precision), and the two sweeps run as the chunked parallel scan of affine
-// maps that the radial column stage uses (colscan::chunk_scan): a thread
+// maps that the radial column stage uses (colscan::chunk_scan_n): a thread
 // owns L consecutive nodes of one line (or of NP lines of the same
 // frequency bin, which share the pivots) in registers.  The lines of one
 // launch are addressed as b * bstride + j * pitch + c (see XYLine), so the x
