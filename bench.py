@@ -176,6 +176,27 @@ def cpu_oracle_sample(wl, budget_s=15.0):
             "single_thread_value": wl.points / dt1}
 
 
+def cpu_oracle_sample_xy(wl, budget_s=12.0):
+    """Times the FP64 CPU oracle on the Cartesian workload: whole z-steps,
+    one thread (the Cartesian oracle has no threaded mode), as many as fit
+    in ~budget_s (at least one)."""
+    import oracle
+    pb = oracle.Problem(**wl.physics())
+    g = oracle.GridXY(**wl.grid())
+    a = wl.field()
+    t0 = time.perf_counter()
+    a, _ = oracle.xy_run(pb, g, wl.dz, 1, a)
+    total = time.perf_counter() - t0
+    n = max(0, int(budget_s / max(total, 1e-3)) - 1)
+    if n:
+        t0 = time.perf_counter()
+        oracle.xy_run(pb, g, wl.dz, n, a)
+        total += time.perf_counter() - t0
+    return {"value": wl.points * (1 + n) / total, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{1 + n} z-steps of the {wl.nx}x{wl.ny}x{wl.nt} field, FP64 C oracle, one "
+                      f"thread, {total:.1f} s"}
+
+
 def run_reference(args, budget_s=150.0):
     """The oracle as the reference arm: whole z-steps of one cfg2 pulse with
     the paper's thread decomposition on all host cores; the timed steps are
@@ -290,13 +311,14 @@ def accuracy_leg(fcn, wl, field, dz, make=None, checkpoints=None):
                             "xi ~ U[-1, 1], against the unperturbed FP64 path"}
 
 
-def cartesian_leg(fcn, W, pg, world, accuracy=True):
+def cartesian_leg(fcn, W, pg, world, accuracy=True, cpu=True):
     """Config 1's pulse on the 255 x 255 x 256 Cartesian grid (x and y
     Crank-Nicolson factors): the full 200-step run timed in FP32-mixed and in
     FP64 (CUDA events on the launch stream), the FP32 field and energy
     against the FP64 path at checkpoints (accuracy_leg), and per-kernel CUDA-event times of
     a profiled replay with their algorithmic HBM fractions (one complex64
-    field read and write per point and launch)."""
+    field read and write per point and launch), and the FP64 oracle timed on
+    the host beside it (cpu_oracle_sample_xy)."""
     import torch
     wl = W.cartesian_config1()
     pts, K = wl.points, wl.nsteps
@@ -348,6 +370,8 @@ def cartesian_leg(fcn, W, pg, world, accuracy=True):
         out["accuracy_vs_fp64"] = accuracy_leg(
             fcn, wl, f, wl.dz, make=lambda prec: fcn.SolverXY(wl.grid(), wl.physics(), precision=prec),
             checkpoints=[25, 50, 100, 150, K])
+    if cpu:
+        out["cpu_baseline"] = cpu_oracle_sample_xy(wl)
     return out
 
 
@@ -502,8 +526,9 @@ def run_ours(args):
         s4.close()
 
     # ---- Cartesian transverse grid (3D+1) ----
-    cart = None if args.no_cartesian else cartesian_leg(fcn, W, pg, world,
-                                                        accuracy=rank == 0 and not args.no_accuracy)
+    cart = None if args.no_cartesian else cartesian_leg(
+        fcn, W, pg, world, accuracy=rank == 0 and not args.no_accuracy,
+        cpu=rank == 0 and world == 1 and not args.no_cpu_baseline)
 
     # ---- plain FP64 FCN on the same batch ----
     K64 = max(2, min(args.steps, 6))

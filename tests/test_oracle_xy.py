@@ -195,3 +195,26 @@ def test_diag_sums():
     assert d["peak_intensity"] == pytest.approx(I.max(), rel=1e-15)
     assert d["onaxis_peak"] == pytest.approx(I[4, 3].max(), rel=1e-15)
     assert not d["nonfinite"]
+
+
+def test_cartesian_workload_grid_and_power():
+    """The Cartesian input: nodes symmetric about 0 with the walls at +-5 w0,
+    config 1's dr as spacing, and I0 = 2P/(pi wx wy) so that the transverse
+    integral of |A|^2 at the pulse peak is the beam power P."""
+    wl = W.cartesian_config1()
+    g = oracle.GridXY(**wl.grid())
+    assert g.x()[0] == pytest.approx(-5e-3) and g.x()[-1] == pytest.approx(5e-3)
+    assert g.x()[(wl.nx - 1) // 2] == pytest.approx(0.0, abs=1e-15)
+    assert g.dx == pytest.approx(W.config1().r_max / (W.config1().nr - 1))
+    we = W.small_xy(161, 121, 8, w0y=0.6e-3)
+    A = we.field()
+    ge = oracle.GridXY(**we.grid())
+    peak = np.abs(A[:, :, we.nt // 2]) ** 2
+    p = peak.sum() * ge.dx * ge.dy
+    assert p == pytest.approx(we.p_over_pcr * W.critical_power(), rel=1e-9)
+
+
+def test_cpu_oracle_sample_of_the_cartesian_bench_leg():
+    import bench
+    r = bench.cpu_oracle_sample_xy(W.small_xy(9, 7, 16), budget_s=0.2)
+    assert r["kind"] == "oracle" and r["cores"] == 1 and r["value"] > 0
