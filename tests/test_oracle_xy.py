@@ -218,3 +218,41 @@ def test_cpu_oracle_sample_of_the_cartesian_bench_leg():
     import bench
     r = bench.cpu_oracle_sample_xy(W.small_xy(9, 7, 16), budget_s=0.2)
     assert r["kind"] == "oracle" and r["cores"] == 1 and r["value"] > 0
+
+
+def test_factored_step_differs_from_the_unsplit_2d_step_at_third_order():
+    """Reading R9: the product of the x and y Cayley factors differs from the
+    unsplit two-dimensional Crank-Nicolson step (Kronecker-sum operator,
+    solved densely by LAPACK) by O(dz^3) per step: halving dz divides the
+    one-step difference by about 8, while both stay unitary."""
+    wl = W.small_xy(9, 7, 4, flags=W.DIFFRACTION | W.DISPERSION, k2=2e-27)
+    pb = _pb(wl)
+    g = oracle.GridXY(**wl.grid())
+    rng = np.random.default_rng(11)
+    A0 = rng.normal(size=(9, 7, 4)) + 1j * rng.normal(size=(9, 7, 4))
+    A0[[0, -1]] = 0
+    A0[:, [0, -1]] = 0
+    k0 = pb.k0()
+    mx, my = 7, 5
+
+    def d2(m, h):
+        return (np.diag(-2.0 * np.ones(m)) + np.diag(np.ones(m - 1), 1)
+                + np.diag(np.ones(m - 1), -1)) / h ** 2
+
+    omega = 2 * np.pi * np.fft.fftfreq(4, wl.t_window / 4)
+    diffs = []
+    for dz in (1.0, 0.5):
+        F = np.fft.fft(A0, axis=2)
+        out = np.zeros_like(F)
+        for q in range(4):
+            L = (1j / (2 * k0) * (np.kron(d2(mx, g.dx), np.eye(my)) + np.kron(np.eye(mx), d2(my, g.dy)))
+                 + 1j * wl.k2 * omega[q] ** 2 / 2 * np.eye(mx * my))
+            I = np.eye(mx * my)
+            v = F[1:-1, 1:-1, q].reshape(-1)
+            out[1:-1, 1:-1, q] = np.linalg.solve(I - dz / 2 * L, (I + dz / 2 * L) @ v).reshape(mx, my)
+        unsplit = np.fft.ifft(out, axis=2)
+        adi = oracle.xy_linear_step(pb, g, dz, A0)
+        assert np.linalg.norm(adi) == pytest.approx(np.linalg.norm(A0), rel=1e-12)
+        diffs.append(rel_l2(adi, unsplit))
+    assert diffs[0] > 1e-6
+    assert 6.5 < diffs[0] / diffs[1] < 9.5
