@@ -12,7 +12,7 @@ copies in and out, so the caller's arrays are never aliased.
 Parity status (per function; the pins live in ``tests/test_oracle_*.py``):
 pinned: fft, thomas, cn_coeffs, rho_row, nl_half, linear_step, step, diag,
 propagate_adaptive, mlp_forward, mlp_loss_grad, and the Cartesian-grid
-functions xy_cn_coeffs, xy_linear_step, xy_run, xy_diag.  The full coupled run with
+functions xy_cn_coeffs, xy_linear_step, xy_run (serial and threaded), xy_diag.  The full coupled run with
 all physics on is parity unpinned beyond the invariants those tests check,
 because the paper prints no values for it.
 """
@@ -112,6 +112,8 @@ def _load():
                                         _D, _D, _D, _D, _D, _D]),
             "orc_xy_linear_step": (C.c_int, [P, C.POINTER(_GridXY), C.c_double, _D]),
             "orc_xy_run": (C.c_int, [P, C.POINTER(_GridXY), C.c_double, C.c_long, _D, _D]),
+            "orc_xy_run_threads": (C.c_int, [P, C.POINTER(_GridXY), C.c_double, C.c_long, _D, _D,
+                                             C.c_int]),
             "orc_xy_diag": (None, [P, C.POINTER(_GridXY), _D, _D, C.POINTER(_Diag)]),
             "orc_mlp_forward": (C.c_int, [C.c_int, C.c_int, C.c_int, _D, _D, _D]),
             "orc_mlp_loss_grad": (C.c_int, [C.c_int, C.c_int, C.c_int, _D, _D, _D, _D, _D]),
@@ -331,13 +333,18 @@ def xy_linear_step(pb: Problem, g: GridXY, dz: float, A) -> np.ndarray:
     return a
 
 
-def xy_run(pb: Problem, g: GridXY, dz: float, nsteps: int, A):
-    """nsteps Strang steps on the Cartesian grid; returns (field, rho)."""
+def xy_run(pb: Problem, g: GridXY, dz: float, nsteps: int, A, threads: int = 1):
+    """nsteps Strang steps on the Cartesian grid; returns (field, rho).
+    threads > 1 splits rows and frequency bins over threads (same bits)."""
     a = _c128(A).copy()
     assert a.shape == (g.nx, g.ny, pb.nt)
     rho = np.zeros(a.shape, np.float64)
-    rc = _load().orc_xy_run(C.byref(pb._c()), C.byref(g._c()), float(dz), int(nsteps), _ptr(a),
-                            _ptr(rho))
+    if threads > 1:
+        rc = _load().orc_xy_run_threads(C.byref(pb._c()), C.byref(g._c()), float(dz), int(nsteps),
+                                        _ptr(a), _ptr(rho), int(threads))
+    else:
+        rc = _load().orc_xy_run(C.byref(pb._c()), C.byref(g._c()), float(dz), int(nsteps), _ptr(a),
+                                _ptr(rho))
     if rc != 0:
         raise RuntimeError(f"orc_xy_run failed ({rc})")
     return a, rho

@@ -637,6 +637,118 @@ int orc_xy_run(const orc_problem *pb, const orc_xy_grid *g, double dz, long nste
     return 0;
 }
 
+/* orc_xy_run with the paper's shared-memory decomposition (Sec. 4, Fig. 2)
+ * carried to the Cartesian grid, for timing on multi-core hosts: thread k
+ * owns a contiguous block of (x, y) rows (nonlinear half steps and
+ * transforms) and a contiguous block of frequency bins (both factors of
+ * each bin: its x lines, then its y lines), with a barrier between the row
+ * and bin phases.  Every row and bin is computed by exactly the code
+ * orc_xy_step runs, in the same order, so the result is bit-identical. */
+typedef struct {
+    pthread_mutex_t mu;
+    pthread_cond_t cv;
+    int state;               /* 0 wait, 1 run, -1 abort */
+} orc_gate;
+
+typedef struct {
+    const orc_problem *pb;
+    const orc_xy_grid *g;
+    double dz;
+    long nsteps;
+    cplx *A;
+    double *rho;
+    int nthreads, tid, rc;
+    pthread_barrier_t *bar;
+    orc_gate *gate;
+} orc_xy_worker;
+
+static void *orc_xy_worker_run(void *arg)
+{
+    orc_xy_worker *w = (orc_xy_worker *)arg;
+    /* every thread starts only once all of them exist (or none runs) */
+    pthread_mutex_lock(&w->gate->mu);
+    while (w->gate->state == 0) pthread_cond_wait(&w->gate->cv, &w->gate->mu);
+    int go = w->gate->state == 1;
+    pthread_mutex_unlock(&w->gate->mu);
+    if (!go) return NULL;
+    const orc_problem *pb = w->pb;
+    const orc_xy_grid *g = w->g;
+    int nx = g->nx, ny = g->ny, nt = pb->nt;
+    double dx = g->x_width / (double)(nx - 1), dy = g->y_width / (double)(ny - 1);
+    long rows = (long)nx * ny;
+    long m0 = rows * w->tid / w->nthreads, m1 = rows * (w->tid + 1) / w->nthreads;
+    int q0 = (int)((long)nt * w->tid / w->nthreads), q1 = (int)((long)nt * (w->tid + 1) / w->nthreads);
+    int nmax = nx > ny ? nx : ny;
+    double *tmp = (double *)malloc(sizeof(double) * (size_t)nt);
+    cplx *co = (cplx *)malloc(sizeof(cplx) * (size_t)nmax * 8);
+    for (long n = 0; n < w->nsteps; ++n) {
+        for (long m = m0; m < m1; ++m) {
+            double *row = (double *)(w->A + (size_t)m * nt);
+            orc_nl_half(pb, 0.5 * w->dz, row, tmp);
+            if (orc_fft(row, nt, 0)) w->rc = -1;
+        }
+        pthread_barrier_wait(w->bar);
+        for (int q = q0; q < q1; ++q) {
+            for (int j = 0; j < ny; ++j)
+                if (xy_line(pb, w->dz, q, nx, dx, 0, w->A, (size_t)j * nt + q, (size_t)ny * nt, co)) w->rc = -2;
+            for (int i = 0; i < nx; ++i)
+                if (xy_line(pb, w->dz, q, ny, dy, 1, w->A, (size_t)i * ny * nt + q, (size_t)nt, co)) w->rc = -2;
+        }
+        pthread_barrier_wait(w->bar);
+        for (long m = m0; m < m1; ++m) {
+            double *row = (double *)(w->A + (size_t)m * nt);
+            if (orc_fft(row, nt, 1)) w->rc = -1;
+            orc_nl_half(pb, 0.5 * w->dz, row, w->rho ? w->rho + (size_t)m * nt : tmp);
+        }
+    }
+    free(co);
+    free(tmp);
+    return NULL;
+}
+
+int orc_xy_run_threads(const orc_problem *pb, const orc_xy_grid *g, double dz, long nsteps, double *A,
+                       double *rho, int nthreads)
+{
+    if (nthreads < 1) nthreads = 1;
+    orc_xy_worker *w = (orc_xy_worker *)calloc((size_t)nthreads, sizeof(orc_xy_worker));
+    pthread_t *th = (pthread_t *)calloc((size_t)nthreads, sizeof(pthread_t));
+    pthread_barrier_t bar;
+    orc_gate gate;
+    if (!w || !th || pthread_barrier_init(&bar, NULL, (unsigned)nthreads)) {
+        free(w);
+        free(th);
+        return -3;
+    }
+    pthread_mutex_init(&gate.mu, NULL);
+    pthread_cond_init(&gate.cv, NULL);
+    gate.state = 0;
+    for (int k = 0; k < nthreads; ++k) {
+        w[k].pb = pb; w[k].g = g; w[k].dz = dz; w[k].nsteps = nsteps; w[k].A = (cplx *)A;
+        w[k].rho = rho; w[k].nthreads = nthreads; w[k].tid = k; w[k].rc = 0; w[k].bar = &bar;
+        w[k].gate = &gate;
+    }
+    int started = 1;
+    for (int k = 1; k < nthreads; ++k) {
+        if (pthread_create(&th[k], NULL, orc_xy_worker_run, &w[k])) break;
+        ++started;
+    }
+    pthread_mutex_lock(&gate.mu);
+    gate.state = started == nthreads ? 1 : -1;
+    pthread_cond_broadcast(&gate.cv);
+    pthread_mutex_unlock(&gate.mu);
+    int rc = started == nthreads ? 0 : -3;
+    if (rc == 0) orc_xy_worker_run(&w[0]);
+    for (int k = 1; k < started; ++k) pthread_join(th[k], NULL);
+    for (int k = 0; k < nthreads; ++k)
+        if (w[k].rc) rc = w[k].rc;
+    pthread_barrier_destroy(&bar);
+    pthread_cond_destroy(&gate.cv);
+    pthread_mutex_destroy(&gate.mu);
+    free(th);
+    free(w);
+    return rc;
+}
+
 void orc_xy_diag(const orc_problem *pb, const orc_xy_grid *g, const double *Ad, const double *rho,
                  orc_diag *out)
 {

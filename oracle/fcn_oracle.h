@@ -21,7 +21,8 @@
  *   orc_mlp_* : pinned (finite differences, closed-form tiny nets).
  *   orc_xy_* (Cartesian transverse grid) : pinned (elliptical Gaussian beam
  *     in closed form, dense solves of the 1-D systems, energy, the discrete
- *     dispersion factor, pure SPM, agreement with the radial solver).
+ *     dispersion factor, pure SPM, agreement with the radial solver, the
+ *     unsplit 2-D step at third order; the threaded run bit-identical).
  *   Full coupled run (all physics on) : parity unpinned beyond the
  *     invariants above -- the paper prints no values for it.
  */
@@ -135,6 +136,10 @@ int  orc_xy_linear_step(const orc_problem *pb, const orc_xy_grid *g, double dz, 
 int  orc_xy_step(const orc_problem *pb, const orc_xy_grid *g, double dz, double *A, double *rho);
 int  orc_xy_run(const orc_problem *pb, const orc_xy_grid *g, double dz, long nsteps, double *A,
                 double *rho);
+/* orc_xy_run with rows and frequency bins split over nthreads threads
+ * (Sec. 4's decomposition); bit-identical results; for timing. */
+int  orc_xy_run_threads(const orc_problem *pb, const orc_xy_grid *g, double dz, long nsteps,
+                        double *A, double *rho, int nthreads);
 /* energy = dx dy dtau sum |A|^2; onaxis_peak on the row nearest the centre
  * (i = (nx-1)/2, j = (ny-1)/2); spectral_rms from the unweighted spectrum. */
 void orc_xy_diag(const orc_problem *pb, const orc_xy_grid *g, const double *A, const double *rho,
