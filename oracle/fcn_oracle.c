@@ -391,6 +391,15 @@ int orc_run(const orc_problem *pb, double dz, long nsteps, double *A, double *rh
  * of frequency columns (the tridiagonal solves), with a barrier between the
  * row and column phases.  Every row and column is computed by exactly the
  * code orc_step runs, so the result is bit-identical to orc_run. */
+/* Start gate of the worker threads: every worker waits until all of them
+ * exist (state 1) or one could not be created (state -1, nobody runs), so
+ * that no worker waits forever at a barrier that lacks a thread. */
+typedef struct {
+    pthread_mutex_t mu;
+    pthread_cond_t cv;
+    int state;               /* 0 wait, 1 run, -1 abort */
+} orc_gate;
+
 typedef struct {
     const orc_problem *pb;
     double dz;
@@ -399,11 +408,31 @@ typedef struct {
     double *rho;
     int nthreads, tid, rc;
     pthread_barrier_t *bar;
+    orc_gate *gate;
 } orc_worker;
+
+/* Waits at the gate; 1 when the workers run. */
+static int orc_gate_wait(orc_gate *g)
+{
+    pthread_mutex_lock(&g->mu);
+    while (g->state == 0) pthread_cond_wait(&g->cv, &g->mu);
+    int go = g->state == 1;
+    pthread_mutex_unlock(&g->mu);
+    return go;
+}
+
+static void orc_gate_open(orc_gate *g, int state)
+{
+    pthread_mutex_lock(&g->mu);
+    g->state = state;
+    pthread_cond_broadcast(&g->cv);
+    pthread_mutex_unlock(&g->mu);
+}
 
 static void *orc_worker_run(void *arg)
 {
     orc_worker *w = (orc_worker *)arg;
+    if (!orc_gate_wait(w->gate)) return NULL;
     const orc_problem *pb = w->pb;
     int nr = pb->nr, nt = pb->nt;
     int m0 = (int)((long)nr * w->tid / w->nthreads), m1 = (int)((long)nr * (w->tid + 1) / w->nthreads);
@@ -434,22 +463,36 @@ static void *orc_worker_run(void *arg)
 int orc_run_threads(const orc_problem *pb, double dz, long nsteps, double *A, double *rho, int nthreads)
 {
     if (nthreads < 1) nthreads = 1;
-    pthread_barrier_t bar;
-    if (pthread_barrier_init(&bar, NULL, (unsigned)nthreads)) return -3;
     orc_worker *w = (orc_worker *)calloc((size_t)nthreads, sizeof(orc_worker));
     pthread_t *th = (pthread_t *)calloc((size_t)nthreads, sizeof(pthread_t));
-    int rc = 0;
+    pthread_barrier_t bar;
+    orc_gate gate;
+    if (!w || !th || pthread_barrier_init(&bar, NULL, (unsigned)nthreads)) {
+        free(w);
+        free(th);
+        return -3;
+    }
+    pthread_mutex_init(&gate.mu, NULL);
+    pthread_cond_init(&gate.cv, NULL);
+    gate.state = 0;
     for (int k = 0; k < nthreads; ++k) {
         w[k].pb = pb; w[k].dz = dz; w[k].nsteps = nsteps; w[k].A = (cplx *)A; w[k].rho = rho;
-        w[k].nthreads = nthreads; w[k].tid = k; w[k].rc = 0; w[k].bar = &bar;
+        w[k].nthreads = nthreads; w[k].tid = k; w[k].rc = 0; w[k].bar = &bar; w[k].gate = &gate;
     }
-    for (int k = 1; k < nthreads; ++k)
-        if (pthread_create(&th[k], NULL, orc_worker_run, &w[k])) rc = -3;
+    int started = 1;
+    for (int k = 1; k < nthreads; ++k) {
+        if (pthread_create(&th[k], NULL, orc_worker_run, &w[k])) break;
+        ++started;
+    }
+    orc_gate_open(&gate, started == nthreads ? 1 : -1);
+    int rc = started == nthreads ? 0 : -3;
     if (rc == 0) orc_worker_run(&w[0]);
-    for (int k = 1; k < nthreads; ++k) pthread_join(th[k], NULL);
+    for (int k = 1; k < started; ++k) pthread_join(th[k], NULL);
     for (int k = 0; k < nthreads; ++k)
         if (w[k].rc) rc = w[k].rc;
     pthread_barrier_destroy(&bar);
+    pthread_cond_destroy(&gate.cv);
+    pthread_mutex_destroy(&gate.mu);
     free(th);
     free(w);
     return rc;
@@ -645,12 +688,6 @@ int orc_xy_run(const orc_problem *pb, const orc_xy_grid *g, double dz, long nste
  * and bin phases.  Every row and bin is computed by exactly the code
  * orc_xy_step runs, in the same order, so the result is bit-identical. */
 typedef struct {
-    pthread_mutex_t mu;
-    pthread_cond_t cv;
-    int state;               /* 0 wait, 1 run, -1 abort */
-} orc_gate;
-
-typedef struct {
     const orc_problem *pb;
     const orc_xy_grid *g;
     double dz;
@@ -665,12 +702,7 @@ typedef struct {
 static void *orc_xy_worker_run(void *arg)
 {
     orc_xy_worker *w = (orc_xy_worker *)arg;
-    /* every thread starts only once all of them exist (or none runs) */
-    pthread_mutex_lock(&w->gate->mu);
-    while (w->gate->state == 0) pthread_cond_wait(&w->gate->cv, &w->gate->mu);
-    int go = w->gate->state == 1;
-    pthread_mutex_unlock(&w->gate->mu);
-    if (!go) return NULL;
+    if (!orc_gate_wait(w->gate)) return NULL;
     const orc_problem *pb = w->pb;
     const orc_xy_grid *g = w->g;
     int nx = g->nx, ny = g->ny, nt = pb->nt;
@@ -732,10 +764,7 @@ int orc_xy_run_threads(const orc_problem *pb, const orc_xy_grid *g, double dz, l
         if (pthread_create(&th[k], NULL, orc_xy_worker_run, &w[k])) break;
         ++started;
     }
-    pthread_mutex_lock(&gate.mu);
-    gate.state = started == nthreads ? 1 : -1;
-    pthread_cond_broadcast(&gate.cv);
-    pthread_mutex_unlock(&gate.mu);
+    orc_gate_open(&gate, started == nthreads ? 1 : -1);
     int rc = started == nthreads ? 0 : -3;
     if (rc == 0) orc_xy_worker_run(&w[0]);
     for (int k = 1; k < started; ++k) pthread_join(th[k], NULL);
