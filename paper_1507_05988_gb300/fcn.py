@@ -77,7 +77,6 @@ class fcn_stats(C.Structure):
 _P = C.c_void_p
 _D = C.POINTER(C.c_double)
 _F = C.POINTER(C.c_float)
-_F = C.POINTER(C.c_float)
 _G = C.POINTER(fcn_grid)
 _PR = C.POINTER(fcn_params)
 _CTX = C.c_void_p

@@ -1,8 +1,6 @@
 """Pins of the oracle's building blocks against facts that do not come from
 the oracle itself: brute-force DFTs, dense linear algebra, exact discrete
 operator identities and the Crank-Nicolson structure of Sec. 3.1."""
-import math
-
 import mpmath
 import numpy as np
 import pytest
