@@ -5,7 +5,8 @@
 
 The pulse is one of the seeded workloads (config 1: 128 x 256, config 2:
 1024 x 4096, config 3: 2048 x 8192), or with --cartesian config 1's pulse on
-the 255 x 255 x 256 Cartesian grid (row variant, then line variant).  With variants given the autotuner does
+the 255 x 255 x 256 Cartesian grid (--nxy for another node count per axis;
+row variant, then line variant).  With variants given the autotuner does
 not run, so a profiler sees exactly one fused middle row launch and one
 column launch per step after the first step (which adds the opening row
 launch).  Steps run without CUDA graphs unless --graph is given.
@@ -34,6 +35,8 @@ def main(argv=None) -> int:
                     help="then time this many graph-replayed steps (wall clock around a "
                          "synchronising call) and as many per-launch event-timed steps")
     ap.add_argument("--cartesian", action="store_true")
+    ap.add_argument("--nxy", type=int, default=255,
+                    help="Cartesian nodes per transverse axis (the walls stay at +-5 w0)")
     a = ap.parse_args(argv)
     if a.cartesian:
         return _cartesian(a)
@@ -79,6 +82,8 @@ def main(argv=None) -> int:
 def _cartesian(a) -> int:
     import time
     wl = workloads.cartesian_config1()
+    if a.nxy != wl.nx:
+        wl = wl.with_(nx=a.nxy, ny=a.nxy, name=f"cart_cfg1_{a.nxy}x{a.nxy}x{wl.nt}")
     prec = fcn.FCN_FP32_MIXED if a.precision == "fp32" else fcn.FCN_FP64
     s = fcn.SolverXY(wl.grid(), wl.physics(), precision=prec)
     if a.row_variant >= 0 or a.col_variant >= 0:
