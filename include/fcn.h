@@ -379,7 +379,7 @@ int fcn_op_cn(const fcn_grid *grid, const fcn_params *params, int32_t precision,
  * (a raw cudaMalloc may then fail, and cudaFree synchronises the whole
  * device, stalling every other stream), or a latency-bound loop that must
  * never block on an allocation.  fcn_op_cn_noalloc does the same column
- * stage (Eq. (matrix) solved for every frequency, in place on `field`) with
+ * stage as fcn_op_cn_table followed by fcn_op_cn, in place on `field`, with
  * its scratch -- the pivot table for this dz and the radial ratio tables --
  * in one static device array of FCN_NOALLOC_SCRATCH_BYTES bytes built into
  * the library.  It calls no cudaMalloc, cudaFree or allocating library
@@ -397,8 +397,11 @@ int fcn_op_cn(const fcn_grid *grid, const fcn_params *params, int32_t precision,
  *     (different streams or host threads) race on it: serialise them.
  *   - field: device buffer in the working precision, frequency domain,
  *     Nr*Nt complex values, updated in place.  stream: cudaStream_t.
- *   - Errors: FCN_ERR_ARG (bad grid/params/dz/pointer), FCN_ERR_UNSUPPORTED
- *     (grid too large for the array), FCN_ERR_CUDA. */
+ *   - Arguments are checked as for fcn_op_cn (same codes: FCN_ERR_ARG for a
+ *     bad grid, parameter, flag, dz or pointer; FCN_ERR_UNSUPPORTED for a
+ *     grid beyond the library's range) before any GPU work.
+ *   - Errors: those, FCN_ERR_UNSUPPORTED (grid too large for the array),
+ *     FCN_ERR_CUDA. */
 #define FCN_NOALLOC_SCRATCH_BYTES (8u * 1024u * 1024u)
 int fcn_op_cn_noalloc(const fcn_grid *grid, const fcn_params *params, int32_t precision,
                       double dz, void *field, void *stream);

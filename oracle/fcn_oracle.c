@@ -293,6 +293,13 @@ void orc_nl_half(const orc_problem *pb, double h, double *rowd, double *rho)
     int nt = pb->nt;
     cplx *row = (cplx *)rowd;
     double *inten = (double *)malloc(sizeof(double) * (size_t)nt);
+    if (!inten) {                    /* no memory: mark the row as failed */
+        for (int p = 0; p < nt; ++p) {
+            row[p] = NAN;
+            rho[p] = NAN;
+        }
+        return;
+    }
     for (int p = 0; p < nt; ++p) {
         double re = creal(row[p]), im = cimag(row[p]);
         inten[p] = re * re + im * im;
@@ -346,6 +353,7 @@ int orc_linear_step(const orc_problem *pb, double dz, double *Ad)
         if (orc_fft((double *)(A + (size_t)m * nt), nt, 0)) return -1;
     /* second loop: one tridiagonal system per frequency */
     cplx *co = (cplx *)malloc(sizeof(cplx) * (size_t)nr * 8);
+    if (!co) return -3;
     int rc = 0;
     for (int q = 0; q < nt && rc == 0; ++q) rc = cn_column(pb, dz, A, q, co);
     free(co);
@@ -366,6 +374,7 @@ int orc_step(const orc_problem *pb, double dz, double *Ad, double *rho)
 {
     int nr = pb->nr, nt = pb->nt;
     double *tmp = (double *)malloc(sizeof(double) * (size_t)nt);
+    if (!tmp) return -3;
     for (int m = 0; m < nr; ++m)
         orc_nl_half(pb, 0.5 * dz, Ad + (size_t)2 * m * nt, tmp);
     int rc = orc_linear_step(pb, dz, Ad);
@@ -385,33 +394,28 @@ int orc_run(const orc_problem *pb, double dz, long nsteps, double *A, double *rh
     return 0;
 }
 
-/* The same steps with the paper's shared-memory decomposition (Sec. 4,
- * Fig. 2), for timing on a multi-core host: thread k owns a contiguous block
- * of rows (nonlinear half step and transform of each) and a contiguous block
- * of frequency columns (the tridiagonal solves), with a barrier between the
- * row and column phases.  Every row and column is computed by exactly the
- * code orc_step runs, so the result is bit-identical to orc_run. */
-/* Start gate of the worker threads: every worker waits until all of them
- * exist (state 1) or one could not be created (state -1, nobody runs), so
- * that no worker waits forever at a barrier that lacks a thread. */
+/* ------------------------------------------------------------------ */
+/* Multi-core timing mode: a parallel-for over rows and frequency bins  */
+/* ------------------------------------------------------------------ */
+
+/* The rows of a row phase and the bins of a column phase are independent
+ * problems, so a host pool of threads can split each phase into contiguous
+ * ranges (the paper's Sec. 4 runs its CPU code this way; here it only serves
+ * to time the oracle on many cores).  The pool is generic: the caller hands
+ * it one range task at a time and waits until every member has finished its
+ * share.  Every row and bin runs exactly the per-row and per-bin functions
+ * the serial step uses, so the result is bit-identical to it. */
+typedef int (*orc_range_fn)(void *ctx, long i0, long i1, void *scratch);
+
+/* Start gate: members wait until all of them exist (state 1) or one could
+ * not be created (state -1, all leave), so that no member ever waits on a
+ * barrier that lacks a thread. */
 typedef struct {
     pthread_mutex_t mu;
     pthread_cond_t cv;
     int state;               /* 0 wait, 1 run, -1 abort */
 } orc_gate;
 
-typedef struct {
-    const orc_problem *pb;
-    double dz;
-    long nsteps;
-    cplx *A;
-    double *rho;
-    int nthreads, tid, rc;
-    pthread_barrier_t *bar;
-    orc_gate *gate;
-} orc_worker;
-
-/* Waits at the gate; 1 when the workers run. */
 static int orc_gate_wait(orc_gate *g)
 {
     pthread_mutex_lock(&g->mu);
@@ -429,72 +433,217 @@ static void orc_gate_open(orc_gate *g, int state)
     pthread_mutex_unlock(&g->mu);
 }
 
-static void *orc_worker_run(void *arg)
+typedef struct orc_pool orc_pool;
+typedef struct {
+    orc_pool *pool;
+    int id;
+    void *scratch;           /* the member's own work space */
+    int rc;                  /* first nonzero status of its tasks */
+} orc_member;
+
+struct orc_pool {
+    int n, started;
+    pthread_t *th;
+    orc_member *mem;
+    pthread_barrier_t go, done;
+    orc_gate gate;
+    orc_range_fn fn;         /* the task of the current round */
+    void *ctx;
+    long items;
+    int quit;
+};
+
+/* Member m's share of the current task: items [items m / n, items (m+1) / n). */
+static void orc_pool_share(orc_pool *p, orc_member *m)
 {
-    orc_worker *w = (orc_worker *)arg;
-    if (!orc_gate_wait(w->gate)) return NULL;
-    const orc_problem *pb = w->pb;
-    int nr = pb->nr, nt = pb->nt;
-    int m0 = (int)((long)nr * w->tid / w->nthreads), m1 = (int)((long)nr * (w->tid + 1) / w->nthreads);
-    int q0 = (int)((long)nt * w->tid / w->nthreads), q1 = (int)((long)nt * (w->tid + 1) / w->nthreads);
-    double *tmp = (double *)malloc(sizeof(double) * (size_t)nt);
-    cplx *co = (cplx *)malloc(sizeof(cplx) * (size_t)nr * 8);
-    for (long n = 0; n < w->nsteps; ++n) {
-        for (int m = m0; m < m1; ++m) {
-            double *row = (double *)(w->A + (size_t)m * nt);
-            orc_nl_half(pb, 0.5 * w->dz, row, tmp);
-            if (orc_fft(row, nt, 0)) w->rc = -1;
+    long i0 = p->items * m->id / p->n, i1 = p->items * (m->id + 1) / p->n;
+    if (i1 > i0) {
+        int rc = p->fn(p->ctx, i0, i1, m->scratch);
+        if (rc && !m->rc) m->rc = rc;
+    }
+}
+
+static void *orc_pool_main(void *arg)
+{
+    orc_member *m = (orc_member *)arg;
+    orc_pool *p = m->pool;
+    if (!orc_gate_wait(&p->gate)) return NULL;
+    for (;;) {
+        pthread_barrier_wait(&p->go);
+        if (p->quit) return NULL;
+        orc_pool_share(p, m);
+        pthread_barrier_wait(&p->done);
+    }
+}
+
+/* Runs fn over items 0..items-1 on all members (the caller is member 0). */
+static void orc_pool_run(orc_pool *p, orc_range_fn fn, void *ctx, long items)
+{
+    p->fn = fn;
+    p->ctx = ctx;
+    p->items = items;
+    if (p->n > 1) pthread_barrier_wait(&p->go);
+    orc_pool_share(p, &p->mem[0]);
+    if (p->n > 1) pthread_barrier_wait(&p->done);
+}
+
+/* First nonzero status of any member since the pool started. */
+static int orc_pool_status(const orc_pool *p)
+{
+    for (int k = 0; k < p->n; ++k)
+        if (p->mem[k].rc) return p->mem[k].rc;
+    return 0;
+}
+
+static void orc_pool_free_scratch(orc_pool *p)
+{
+    for (int k = 0; k < p->n; ++k) free(p->mem[k].scratch);
+}
+
+/* A pool of n members with scratch_bytes of work space each; NULL when an
+ * allocation, a barrier or a thread could not be made. */
+static orc_pool *orc_pool_create(int n, size_t scratch_bytes)
+{
+    if (n < 1) n = 1;
+    orc_pool *p = (orc_pool *)calloc(1, sizeof(orc_pool));
+    if (!p) return NULL;
+    p->n = n;
+    p->th = (pthread_t *)calloc((size_t)n, sizeof(pthread_t));
+    p->mem = (orc_member *)calloc((size_t)n, sizeof(orc_member));
+    int ok = p->th && p->mem;
+    for (int k = 0; ok && k < n; ++k) {
+        p->mem[k].pool = p;
+        p->mem[k].id = k;
+        p->mem[k].scratch = malloc(scratch_bytes);
+        if (!p->mem[k].scratch) ok = 0;
+    }
+    if (!ok) {
+        if (p->mem) orc_pool_free_scratch(p);
+        free(p->th);
+        free(p->mem);
+        free(p);
+        return NULL;
+    }
+    p->started = 1;
+    if (n > 1) {
+        if (pthread_barrier_init(&p->go, NULL, (unsigned)n)) ok = 0;
+        if (ok && pthread_barrier_init(&p->done, NULL, (unsigned)n)) {
+            pthread_barrier_destroy(&p->go);
+            ok = 0;
         }
-        pthread_barrier_wait(w->bar);
-        for (int q = q0; q < q1; ++q)
-            if (cn_column(pb, w->dz, w->A, q, co)) w->rc = -2;
-        pthread_barrier_wait(w->bar);
-        for (int m = m0; m < m1; ++m) {
-            double *row = (double *)(w->A + (size_t)m * nt);
-            if (orc_fft(row, nt, 1)) w->rc = -1;
-            orc_nl_half(pb, 0.5 * w->dz, row, w->rho ? w->rho + (size_t)m * nt : tmp);
+        if (!ok) {
+            orc_pool_free_scratch(p);
+            free(p->th);
+            free(p->mem);
+            free(p);
+            return NULL;
+        }
+        pthread_mutex_init(&p->gate.mu, NULL);
+        pthread_cond_init(&p->gate.cv, NULL);
+        p->gate.state = 0;
+        for (int k = 1; k < n; ++k) {
+            if (pthread_create(&p->th[k], NULL, orc_pool_main, &p->mem[k])) break;
+            ++p->started;
+        }
+        orc_gate_open(&p->gate, p->started == n ? 1 : -1);
+        if (p->started != n) {
+            for (int k = 1; k < p->started; ++k) pthread_join(p->th[k], NULL);
+            pthread_barrier_destroy(&p->go);
+            pthread_barrier_destroy(&p->done);
+            pthread_cond_destroy(&p->gate.cv);
+            pthread_mutex_destroy(&p->gate.mu);
+            orc_pool_free_scratch(p);
+            free(p->th);
+            free(p->mem);
+            free(p);
+            return NULL;
         }
     }
-    free(co);
-    free(tmp);
-    return NULL;
+    return p;
+}
+
+static void orc_pool_destroy(orc_pool *p)
+{
+    if (!p) return;
+    if (p->n > 1) {
+        p->quit = 1;
+        pthread_barrier_wait(&p->go);
+        for (int k = 1; k < p->n; ++k) pthread_join(p->th[k], NULL);
+        pthread_barrier_destroy(&p->go);
+        pthread_barrier_destroy(&p->done);
+        pthread_cond_destroy(&p->gate.cv);
+        pthread_mutex_destroy(&p->gate.mu);
+    }
+    orc_pool_free_scratch(p);
+    free(p->th);
+    free(p->mem);
+    free(p);
+}
+
+/* Range tasks of one Strang step on the radial grid.  Scratch: nt doubles
+ * (the density of a half step that is not kept) then 8 nr complex values
+ * (cn_column's work space). */
+typedef struct {
+    const orc_problem *pb;
+    double dz;
+    cplx *A;
+    double *rho;
+} orc_step_ctx;
+
+static double *scratch_rho(void *s) { return (double *)s; }
+
+static cplx *scratch_cn(void *s, int nt) { return (cplx *)((double *)s + 2 * ((nt + 1) / 2)); }
+
+/* Rows m0..m1-1 before the column phase: half step, then forward transform. */
+static int task_rows_open(void *c, long m0, long m1, void *s)
+{
+    orc_step_ctx *x = (orc_step_ctx *)c;
+    int nt = x->pb->nt, rc = 0;
+    for (long m = m0; m < m1; ++m) {
+        double *row = (double *)(x->A + (size_t)m * nt);
+        orc_nl_half(x->pb, 0.5 * x->dz, row, scratch_rho(s));
+        if (orc_fft(row, nt, 0)) rc = -1;
+    }
+    return rc;
+}
+
+/* Frequency bins q0..q1-1: one tridiagonal solve each. */
+static int task_columns(void *c, long q0, long q1, void *s)
+{
+    orc_step_ctx *x = (orc_step_ctx *)c;
+    int rc = 0;
+    for (long q = q0; q < q1; ++q)
+        if (cn_column(x->pb, x->dz, x->A, (int)q, scratch_cn(s, x->pb->nt))) rc = -2;
+    return rc;
+}
+
+/* Rows m0..m1-1 after the column phase: inverse transform, then half step. */
+static int task_rows_close(void *c, long m0, long m1, void *s)
+{
+    orc_step_ctx *x = (orc_step_ctx *)c;
+    int nt = x->pb->nt, rc = 0;
+    for (long m = m0; m < m1; ++m) {
+        double *row = (double *)(x->A + (size_t)m * nt);
+        if (orc_fft(row, nt, 1)) rc = -1;
+        orc_nl_half(x->pb, 0.5 * x->dz, row, x->rho ? x->rho + (size_t)m * nt : scratch_rho(s));
+    }
+    return rc;
 }
 
 int orc_run_threads(const orc_problem *pb, double dz, long nsteps, double *A, double *rho, int nthreads)
 {
-    if (nthreads < 1) nthreads = 1;
-    orc_worker *w = (orc_worker *)calloc((size_t)nthreads, sizeof(orc_worker));
-    pthread_t *th = (pthread_t *)calloc((size_t)nthreads, sizeof(pthread_t));
-    pthread_barrier_t bar;
-    orc_gate gate;
-    if (!w || !th || pthread_barrier_init(&bar, NULL, (unsigned)nthreads)) {
-        free(w);
-        free(th);
-        return -3;
+    int nt = pb->nt, nr = pb->nr;
+    size_t bytes = sizeof(double) * 2 * (size_t)((nt + 1) / 2) + sizeof(cplx) * 8 * (size_t)nr;
+    orc_pool *p = orc_pool_create(nthreads, bytes);
+    if (!p) return -3;
+    orc_step_ctx x = {pb, dz, (cplx *)A, rho};
+    for (long n = 0; n < nsteps && !orc_pool_status(p); ++n) {
+        orc_pool_run(p, task_rows_open, &x, nr);
+        orc_pool_run(p, task_columns, &x, nt);
+        orc_pool_run(p, task_rows_close, &x, nr);
     }
-    pthread_mutex_init(&gate.mu, NULL);
-    pthread_cond_init(&gate.cv, NULL);
-    gate.state = 0;
-    for (int k = 0; k < nthreads; ++k) {
-        w[k].pb = pb; w[k].dz = dz; w[k].nsteps = nsteps; w[k].A = (cplx *)A; w[k].rho = rho;
-        w[k].nthreads = nthreads; w[k].tid = k; w[k].rc = 0; w[k].bar = &bar; w[k].gate = &gate;
-    }
-    int started = 1;
-    for (int k = 1; k < nthreads; ++k) {
-        if (pthread_create(&th[k], NULL, orc_worker_run, &w[k])) break;
-        ++started;
-    }
-    orc_gate_open(&gate, started == nthreads ? 1 : -1);
-    int rc = started == nthreads ? 0 : -3;
-    if (rc == 0) orc_worker_run(&w[0]);
-    for (int k = 1; k < started; ++k) pthread_join(th[k], NULL);
-    for (int k = 0; k < nthreads; ++k)
-        if (w[k].rc) rc = w[k].rc;
-    pthread_barrier_destroy(&bar);
-    pthread_cond_destroy(&gate.cv);
-    pthread_mutex_destroy(&gate.mu);
-    free(th);
-    free(w);
+    int rc = orc_pool_status(p);
+    orc_pool_destroy(p);
     return rc;
 }
 
@@ -639,6 +788,7 @@ int orc_xy_linear_step(const orc_problem *pb, const orc_xy_grid *g, double dz, d
         if (orc_fft((double *)(A + m * nt), nt, 0)) return -1;
     int nmax = nx > ny ? nx : ny;
     cplx *co = (cplx *)malloc(sizeof(cplx) * (size_t)nmax * 8);
+    if (!co) return -3;
     int rc = 0;
     for (int q = 0; q < nt && rc == 0; ++q) {
         /* x factor: line (j, q) holds A[i][j][q], i = 0..nx-1 */
@@ -662,6 +812,7 @@ int orc_xy_step(const orc_problem *pb, const orc_xy_grid *g, double dz, double *
     int nt = pb->nt;
     size_t rows = (size_t)g->nx * g->ny;
     double *tmp = (double *)malloc(sizeof(double) * (size_t)nt);
+    if (!tmp) return -3;
     for (size_t m = 0; m < rows; ++m) orc_nl_half(pb, 0.5 * dz, Ad + 2 * m * nt, tmp);
     int rc = orc_xy_linear_step(pb, g, dz, Ad);
     for (size_t m = 0; m < rows && rc == 0; ++m)
@@ -680,101 +831,66 @@ int orc_xy_run(const orc_problem *pb, const orc_xy_grid *g, double dz, long nste
     return 0;
 }
 
-/* orc_xy_run with the paper's shared-memory decomposition (Sec. 4, Fig. 2)
- * carried to the Cartesian grid, for timing on multi-core hosts: thread k
- * owns a contiguous block of (x, y) rows (nonlinear half steps and
- * transforms) and a contiguous block of frequency bins (both factors of
- * each bin: its x lines, then its y lines), with a barrier between the row
- * and bin phases.  Every row and bin is computed by exactly the code
- * orc_xy_step runs, in the same order, so the result is bit-identical. */
+/* orc_xy_run on the host pool: rows as for the radial grid, and per
+ * frequency bin both factors (its x lines, then its y lines), the same
+ * functions in the same order as orc_xy_step, so the result is
+ * bit-identical.  Scratch: nt doubles then 8 max(nx, ny) complex values. */
 typedef struct {
     const orc_problem *pb;
     const orc_xy_grid *g;
     double dz;
-    long nsteps;
     cplx *A;
     double *rho;
-    int nthreads, tid, rc;
-    pthread_barrier_t *bar;
-    orc_gate *gate;
-} orc_xy_worker;
+} orc_xy_ctx;
 
-static void *orc_xy_worker_run(void *arg)
+static int task_xy_rows_open(void *c, long m0, long m1, void *s)
 {
-    orc_xy_worker *w = (orc_xy_worker *)arg;
-    if (!orc_gate_wait(w->gate)) return NULL;
-    const orc_problem *pb = w->pb;
-    const orc_xy_grid *g = w->g;
-    int nx = g->nx, ny = g->ny, nt = pb->nt;
+    orc_xy_ctx *x = (orc_xy_ctx *)c;
+    orc_step_ctx r = {x->pb, x->dz, x->A, NULL};
+    return task_rows_open(&r, m0, m1, s);
+}
+
+static int task_xy_bins(void *c, long q0, long q1, void *s)
+{
+    orc_xy_ctx *x = (orc_xy_ctx *)c;
+    const orc_xy_grid *g = x->g;
+    int nx = g->nx, ny = g->ny, nt = x->pb->nt, rc = 0;
     double dx = g->x_width / (double)(nx - 1), dy = g->y_width / (double)(ny - 1);
-    long rows = (long)nx * ny;
-    long m0 = rows * w->tid / w->nthreads, m1 = rows * (w->tid + 1) / w->nthreads;
-    int q0 = (int)((long)nt * w->tid / w->nthreads), q1 = (int)((long)nt * (w->tid + 1) / w->nthreads);
-    int nmax = nx > ny ? nx : ny;
-    double *tmp = (double *)malloc(sizeof(double) * (size_t)nt);
-    cplx *co = (cplx *)malloc(sizeof(cplx) * (size_t)nmax * 8);
-    for (long n = 0; n < w->nsteps; ++n) {
-        for (long m = m0; m < m1; ++m) {
-            double *row = (double *)(w->A + (size_t)m * nt);
-            orc_nl_half(pb, 0.5 * w->dz, row, tmp);
-            if (orc_fft(row, nt, 0)) w->rc = -1;
-        }
-        pthread_barrier_wait(w->bar);
-        for (int q = q0; q < q1; ++q) {
-            for (int j = 0; j < ny; ++j)
-                if (xy_line(pb, w->dz, q, nx, dx, 0, w->A, (size_t)j * nt + q, (size_t)ny * nt, co)) w->rc = -2;
-            for (int i = 0; i < nx; ++i)
-                if (xy_line(pb, w->dz, q, ny, dy, 1, w->A, (size_t)i * ny * nt + q, (size_t)nt, co)) w->rc = -2;
-        }
-        pthread_barrier_wait(w->bar);
-        for (long m = m0; m < m1; ++m) {
-            double *row = (double *)(w->A + (size_t)m * nt);
-            if (orc_fft(row, nt, 1)) w->rc = -1;
-            orc_nl_half(pb, 0.5 * w->dz, row, w->rho ? w->rho + (size_t)m * nt : tmp);
-        }
+    cplx *co = scratch_cn(s, nt);
+    for (long q = q0; q < q1; ++q) {
+        for (int j = 0; j < ny; ++j)
+            if (xy_line(x->pb, x->dz, (int)q, nx, dx, 0, x->A, (size_t)j * nt + q, (size_t)ny * nt, co))
+                rc = -2;
+        for (int i = 0; i < nx; ++i)
+            if (xy_line(x->pb, x->dz, (int)q, ny, dy, 1, x->A, (size_t)i * ny * nt + q, (size_t)nt, co))
+                rc = -2;
     }
-    free(co);
-    free(tmp);
-    return NULL;
+    return rc;
+}
+
+static int task_xy_rows_close(void *c, long m0, long m1, void *s)
+{
+    orc_xy_ctx *x = (orc_xy_ctx *)c;
+    orc_step_ctx r = {x->pb, x->dz, x->A, x->rho};
+    return task_rows_close(&r, m0, m1, s);
 }
 
 int orc_xy_run_threads(const orc_problem *pb, const orc_xy_grid *g, double dz, long nsteps, double *A,
                        double *rho, int nthreads)
 {
-    if (nthreads < 1) nthreads = 1;
-    orc_xy_worker *w = (orc_xy_worker *)calloc((size_t)nthreads, sizeof(orc_xy_worker));
-    pthread_t *th = (pthread_t *)calloc((size_t)nthreads, sizeof(pthread_t));
-    pthread_barrier_t bar;
-    orc_gate gate;
-    if (!w || !th || pthread_barrier_init(&bar, NULL, (unsigned)nthreads)) {
-        free(w);
-        free(th);
-        return -3;
+    int nt = pb->nt, nmax = g->nx > g->ny ? g->nx : g->ny;
+    long rows = (long)g->nx * g->ny;
+    size_t bytes = sizeof(double) * 2 * (size_t)((nt + 1) / 2) + sizeof(cplx) * 8 * (size_t)nmax;
+    orc_pool *p = orc_pool_create(nthreads, bytes);
+    if (!p) return -3;
+    orc_xy_ctx x = {pb, g, dz, (cplx *)A, rho};
+    for (long n = 0; n < nsteps && !orc_pool_status(p); ++n) {
+        orc_pool_run(p, task_xy_rows_open, &x, rows);
+        orc_pool_run(p, task_xy_bins, &x, nt);
+        orc_pool_run(p, task_xy_rows_close, &x, rows);
     }
-    pthread_mutex_init(&gate.mu, NULL);
-    pthread_cond_init(&gate.cv, NULL);
-    gate.state = 0;
-    for (int k = 0; k < nthreads; ++k) {
-        w[k].pb = pb; w[k].g = g; w[k].dz = dz; w[k].nsteps = nsteps; w[k].A = (cplx *)A;
-        w[k].rho = rho; w[k].nthreads = nthreads; w[k].tid = k; w[k].rc = 0; w[k].bar = &bar;
-        w[k].gate = &gate;
-    }
-    int started = 1;
-    for (int k = 1; k < nthreads; ++k) {
-        if (pthread_create(&th[k], NULL, orc_xy_worker_run, &w[k])) break;
-        ++started;
-    }
-    orc_gate_open(&gate, started == nthreads ? 1 : -1);
-    int rc = started == nthreads ? 0 : -3;
-    if (rc == 0) orc_xy_worker_run(&w[0]);
-    for (int k = 1; k < started; ++k) pthread_join(th[k], NULL);
-    for (int k = 0; k < nthreads; ++k)
-        if (w[k].rc) rc = w[k].rc;
-    pthread_barrier_destroy(&bar);
-    pthread_cond_destroy(&gate.cv);
-    pthread_mutex_destroy(&gate.mu);
-    free(th);
-    free(w);
+    int rc = orc_pool_status(p);
+    orc_pool_destroy(p);
     return rc;
 }
 

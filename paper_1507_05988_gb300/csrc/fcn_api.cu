@@ -250,6 +250,10 @@ void consts(const fcn_grid &g, const fcn_params &p, double *k0, double *dtau, do
     *dtau = c.dtau;
     *domega = c.domega;
 }
+void cn_coefs(const fcn_grid &g, const fcn_params &p, double dz, double *s, double *dk,
+              double *disp) {
+    ::cn_coefs(g, p, dz, s, dk, disp);
+}
 }  // namespace hostx
 }  // namespace fcn
 

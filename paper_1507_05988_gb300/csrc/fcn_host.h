@@ -1,5 +1,6 @@
 // fcn_host.h -- host helpers of fcn_api.cu used by the Cartesian-grid API
-// (xy_api.cu): argument checks, nonlinear-step coefficients, the FFT
+// (xy_api.cu) and the allocation-free column stage (noalloc.cu): argument
+// checks, Crank-Nicolson coefficients, nonlinear-step coefficients, the FFT
 // twiddle tables and the derived constants of one grid and parameter set.
 #pragma once
 
@@ -20,5 +21,10 @@ template <typename T>
 cudaError_t twiddles(int nt, const cx<T> **out);
 // k0 = 2 pi n0/lambda0, dtau = T/Nt, domega = 2 pi/(Nt dtau).
 void consts(const fcn_grid &g, const fcn_params &p, double *k0, double *dtau, double *domega);
+// s = dz/(4 k0 dr^2) and dk (delta_q = dk q^2) of the Crank-Nicolson system;
+// with FCN_EXACT_DISPERSION dk = 0 and *disp receives the coefficient of the
+// exact factor exp(2 i disp q^2) applied instead (disp may be NULL).
+void cn_coefs(const fcn_grid &g, const fcn_params &p, double dz, double *s, double *dk,
+              double *disp);
 }  // namespace hostx
 }  // namespace fcn

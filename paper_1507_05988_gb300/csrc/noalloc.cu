@@ -18,9 +18,11 @@
 
 #include <cmath>
 #include <mutex>
+#include <string>
 
 #include "../../include/fcn.h"
 #include "fcn_device.cuh"
+#include "fcn_host.h"
 
 using namespace fcn;
 
@@ -32,8 +34,6 @@ static __device__ __align__(256) unsigned char g_cn_scratch[kScratchBytes];
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void *g_scratch_ptr[kMaxDevices] = {nullptr};
-
-constexpr double kPi = 3.14159265358979323846;
 
 // Device address of g_cn_scratch on the current device (looked up once per
 // device, with that device current).
@@ -88,16 +88,9 @@ int run(const fcn_grid &g, const fcn_params &p, double dz, void *field, cudaStre
     T *lo = reinterpret_cast<T *>(b + tab_bytes + 2 * r64_bytes);
     T *hi = reinterpret_cast<T *>(b + tab_bytes + 2 * r64_bytes + rt_bytes);
 
-    // coefficients of Eq. (matrix): s = dz/(4 k0 dr^2), delta_q = dk q^2
-    const double k0 = 2.0 * kPi * p.n0 / p.lambda0;
-    const double dr = g.r_max / double(g.nr - 1);
-    const double domega = 2.0 * kPi / g.t_window;
-    const double s = (p.flags & FCN_DIFFRACTION) ? dz / (4.0 * k0 * dr * dr) : 0.0;
-    const double dk_all = (p.flags & FCN_DISPERSION) ? p.k2 * dz / 4.0 * domega * domega : 0.0;
-    // FCN_EXACT_DISPERSION: the CN system without the dispersion term, which
-    // the column stage applies as its exact factor exp(2 i disp q^2)
-    const bool exact = (p.flags & FCN_EXACT_DISPERSION) != 0;
-    const double dk = exact ? 0.0 : dk_all;
+    // the same coefficients as the regular column stage (one host routine)
+    double s, dk, disp;
+    hostx::cn_coefs(g, p, dz, &s, &dk, &disp);
 
     lohi_kernel<T><<<(g.nr + 127) / 128, 128, 0, st>>>(g.nr, lo64, hi64, lo, hi);
     cudaError_t e = cudaGetLastError();
@@ -120,14 +113,12 @@ int run(const fcn_grid &g, const fcn_params &p, double dz, void *field, cudaStre
     ca.nt = g.nt;
     ca.s = T(s);
     ca.dk = T(dk);
-    ca.disp = exact ? dk_all : 0.0;
+    ca.disp = disp;
     ca.variant = 0;
     e = launch_cn<T>(ca, st);
     if (e != cudaSuccess) return FCN_ERR_CUDA;
     return FCN_OK;
 }
-
-bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 
 }  // namespace
 
@@ -135,14 +126,12 @@ extern "C" {
 
 int fcn_op_cn_noalloc(const fcn_grid *grid, const fcn_params *params, int32_t precision, double dz,
                       void *field, void *stream) {
-    if (!grid || !params || !field) return FCN_ERR_ARG;
-    if (precision != FCN_FP64 && precision != FCN_FP32_MIXED) return FCN_ERR_ARG;
-    // Nt a power of two in 2..8192, Nr in 3..2048 (the column kernel's range)
-    if (!is_pow2(grid->nt) || grid->nt < 2 || grid->nt > 8192 || grid->nr < 3 || grid->nr > 2048)
-        return FCN_ERR_ARG;
-    if (!(grid->r_max > 0) || !(grid->t_window > 0) || !(params->lambda0 > 0) || !(params->n0 > 0))
-        return FCN_ERR_ARG;
-    if (!(dz > 0) || !std::isfinite(dz)) return FCN_ERR_ARG;
+    // the same argument checks as every other entry point (grid range,
+    // precision, physics parameters and flags), then the field and dz
+    std::string why;
+    const int rc = hostx::check_params(precision, grid, params, &why);
+    if (rc) return rc;
+    if (!field || !(dz > 0) || !std::isfinite(dz)) return FCN_ERR_ARG;
     const cudaStream_t st = static_cast<cudaStream_t>(stream);
     return precision == FCN_FP64 ? run<double>(*grid, *params, dz, field, st)
                                  : run<float>(*grid, *params, dz, field, st);

@@ -93,3 +93,22 @@ def test_xy_calls_reject_null_context(fcn):
     assert fcn.fcn_xy_get_diag(None, None) == -1
     assert fcn.fcn_xy_profile_read(None, None, None, 0) == -1
     fcn.fcn_xy_destroy(None)
+
+
+def test_noalloc_column_stage_checks_arguments_like_the_others_without_gpu(fcn):
+    """The allocation-free column stage validates through the same routine
+    as fcn_op_cn, before any GPU work: an unknown flag, a non-finite k'', a
+    photon number outside 1..16, a bad dz or pointer are FCN_ERR_ARG, and a
+    grid beyond the library's range is FCN_ERR_UNSUPPORTED."""
+    g = fcn.make_grid(8, 16, 1e-3, 1e-12)
+    dummy = C.c_void_p(16)          # never dereferenced: the checks come first
+    for bad in (fcn.make_params(k2=float("nan")), fcn.make_params(flags=1 << 10),
+                fcn.make_params(K=0), fcn.make_params(K=17)):
+        assert fcn.fcn_op_cn_noalloc(C.byref(g), C.byref(bad), 1, 1e-3, dummy, None) == -1
+        assert fcn.fcn_op_cn(C.byref(g), C.byref(bad), 1, 1e-3, dummy, dummy, None) == -1
+    p = fcn.make_params()
+    assert fcn.fcn_op_cn_noalloc(C.byref(g), C.byref(p), 1, float("inf"), dummy, None) == -1
+    assert fcn.fcn_op_cn_noalloc(C.byref(g), C.byref(p), 1, 1e-3, None, None) == -1
+    assert fcn.fcn_op_cn_noalloc(C.byref(g), C.byref(p), 3, 1e-3, dummy, None) == -1
+    big = fcn.make_grid(16, 16384, 1e-3, 1e-12)
+    assert fcn.fcn_op_cn_noalloc(C.byref(big), C.byref(p), 1, 1e-3, dummy, None) == -5
