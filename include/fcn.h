@@ -212,13 +212,21 @@ int fcn_get_state(fcn_ctx *ctx, int32_t pulse, double state[4]);
 int fcn_set_state(fcn_ctx *ctx, int32_t pulse, const double state[4]);
 
 /* ======================= kernel variants (autotuner) ======================= */
-/* The row stage has 3 occupancy variants (FP32, K = 8) and the column stage 4
- * (chunk length x CTA size).  By default (-1) the first fcn_step of a grid
- * times every variant on a scratch copy of the field and keeps the fastest
- * per (precision, Nr, Nt) for the process; if the environment variable
- * FCN_TUNE_CACHE names a file, choices are read from and appended to it.
- * row_variant in -1..2 and col_variant in -1..3 force a variant (-1: tune).
- * Drops the context's captured graphs.  Synchronises. */
+/* The row stage has 3 occupancy variants (FP32, K = 8) and the column stage 9:
+ *   0-3  chunked affine-map scans of the two Thomas sweeps, chunks in
+ *        registers (chunk length x CTA size);
+ *   4-7  the same with chunks staged in shared memory (cp.async) or fed to
+ *        registers, row coefficients from a per-dz table;
+ *   8    one sequential Thomas sweep per column, 32 columns per warp, rows
+ *        streamed through a shared-memory ring by TMA (Nt a multiple of 64;
+ *        other grids fall back to variant 7).
+ * By default (-1) the first fcn_step of a grid times every variant on a
+ * scratch copy of the field and keeps the fastest per (precision, Nr, Nt)
+ * for the process; if the environment variable FCN_TUNE_CACHE names a file,
+ * choices are read from and appended to it.  row_variant in -1..2 and
+ * col_variant in -1..8 force a variant (-1: tune).  Every variant computes
+ * the same step up to rounding.  Drops the context's captured graphs.
+ * Synchronises. */
 int fcn_set_variants(fcn_ctx *ctx, int32_t row_variant, int32_t col_variant);
 
 /* Batched work lists for multi-pulse FP32 contexts (every pulse K = 8,
@@ -239,6 +247,22 @@ int fcn_set_batching(fcn_ctx *ctx, int32_t mode);
  * fcn_get_pairing returns the decision: 1, 0, or -1 before the first step. */
 int fcn_set_pairing(fcn_ctx *ctx, int32_t mode);
 int fcn_get_pairing(const fcn_ctx *ctx);
+
+/* Sequential column kernel over all pulses at once, for contexts of 2..8
+ * pulses that share one grid (Nt a multiple of 64) and, for one dz, one
+ * pivot table: the Crank-Nicolson systems of Eq. (matrix) are solved by one
+ * Thomas sweep per frequency column and pulse (the "chasing" method of
+ * Sec. 3.1, forward elimination then back substitution), 32 columns per
+ * warp and two pulses per thread, rows streamed through shared memory by
+ * TMA, all pulses in one launch; the row stage then runs as one launch over
+ * all pulses per z-step as in fcn_set_multi_launch mode 1.
+ * mode 1 on, 0 off, -1 (default) decided on the first step by timing one
+ * such launch against the per-group launches of the tuned column variant
+ * (on scratch copies).  Graph branches > 1 turn it off.  Drops the captured
+ * graphs.  fcn_get_sequential_columns returns the decision: 1, 0, or -1
+ * before the first step. */
+int fcn_set_sequential_columns(fcn_ctx *ctx, int32_t mode);
+int fcn_get_sequential_columns(const fcn_ctx *ctx);
 
 /* Graph branches for multi-pulse contexts.  The pulses (or pulse pairs of a
  * paired column launch) are independent between the row and column stages

@@ -54,6 +54,7 @@ __global__ void cn_table_kernel(TableArgs a, cx<T> *table) {
     }
     __syncthreads();
     const int nq = a.nt / 2 + 1;
+    const int tp = a.tp ? a.tp : nq;
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= nq) return;
     const double delta = a.dk * double(q) * double(q);
@@ -77,7 +78,7 @@ __global__ void cn_table_kernel(TableArgs a, cx<T> *table) {
         const cx<double> den = b - cmul(aa, cp);
         const cx<double> inv = crecip(den);
         cp = cmul(c, inv);
-        table[FCN_IDX((size_t)j * nq + q, (size_t)a.nr * nq, 30)] = mk(T(inv.x), T(inv.y));
+        table[FCN_IDX((size_t)j * tp + q, (size_t)a.nr * tp, 30)] = mk(T(inv.x), T(inv.y));
     }
 }
 
@@ -136,6 +137,7 @@ __global__ void cn_table_kernel_f32(TableArgs a, cx<float> *table) {
     }
     __syncthreads();
     const int nq = a.nt / 2 + 1;
+    const int tp = a.tp ? a.tp : nq;
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= nq) return;
     const double delta = a.dk * double(q) * double(q);
@@ -151,7 +153,7 @@ __global__ void cn_table_kernel_f32(TableArgs a, cx<float> *table) {
         ix = df_mul(wx, rn);
         iy = df_mul(wy, rn);
         iy = {-iy.h, -iy.l};
-        table[FCN_IDX((size_t)j * nq + q, (size_t)a.nr * nq, 30)] = mk(ix.h + ix.l, iy.h + iy.l);
+        table[FCN_IDX((size_t)j * tp + q, (size_t)a.nr * tp, 30)] = mk(ix.h + ix.l, iy.h + iy.l);
     }
 }
 
@@ -170,7 +172,7 @@ __device__ __forceinline__ void cn_body(const ColArgs<T> &a, int C, int g, unsig
     const int chunk = tid / C;
     const int q = g * C + col;
     const int nt = a.nt, nr = a.nr;
-    const int nq = nt / 2 + 1;
+    const int nq = a.tp;
     const int qq = (q <= nt / 2) ? q : nt - q;
     const T delta = a.dk * T(qq) * T(qq);
     const T s = a.s;
@@ -350,7 +352,7 @@ template <typename T, int L, bool EDGE, int NTC>
 __device__ __forceinline__ void cn_f1_reg(const ColArgs<T> &a, int q, int qq, int j0, T delta, cx<T> *At,
                                           cx<T> *Gt, int BD, cx<T> (&y)[L], cx<T> &PA, cx<T> &PB) {
     // NTC: Nt as a compile-time constant (row strides become immediates), 0: a.nt
-    const int nt = NTC ? NTC : a.nt, nr = a.nr, nq = nt / 2 + 1;
+    const int nt = NTC ? NTC : a.nt, nr = a.nr, nq = a.tp;
     const cx<T> *fx = a.field + q;
     const cx<T> *fi = a.invden + qq;
     auto X = [&](int j) -> cx<T> {
@@ -403,7 +405,7 @@ __device__ __forceinline__ void cn_staged_body(const ColArgs<T> &a, int C, int g
     const int chunk = tid / C;
     const int q = g * C + col;
     const int nt = NTC ? NTC : a.nt, nr = a.nr;
-    const int nq = nt / 2 + 1;
+    const int nq = a.tp;
     const int qq = (q <= nt / 2) ? q : nt - q;
     const T delta = a.dk * T(qq) * T(qq);
     const int j0 = chunk * L;
@@ -588,7 +590,7 @@ template <typename T, int L, bool EDGE, int NTC>
 __device__ __forceinline__ void cn_f1_pair(const ColArgs<T> &a, const cx<T> *f2, int q, int qq, int j0,
                                            T delta, cx<T> *At, cx<T> *Gt, int BD, cx<T> (&y1)[L],
                                            cx<T> (&y2)[L], cx<T> &PA, cx<T> &PB1, cx<T> &PB2) {
-    const int nt = NTC ? NTC : a.nt, nr = a.nr, nq = nt / 2 + 1;
+    const int nt = NTC ? NTC : a.nt, nr = a.nr, nq = a.tp;
     const cx<T> *fx = a.field + q;
     const cx<T> *fy = f2 + q;
     const cx<T> *fi = a.invden + qq;
@@ -772,11 +774,19 @@ cudaError_t set_staged_attr() {
 // per thread), bit 1 a target CTA size of 512 instead of 256 threads.  A
 // variant that does not fit (more than 512 threads) falls back to variant 0.
 template <typename T>
-cudaError_t launch_cn(const ColArgs<T> &a, cudaStream_t st) {
+cudaError_t launch_cn(const ColArgs<T> &a_in, cudaStream_t st) {
     constexpr int LL = sizeof(T) == 4 ? 16 : 8;     // long chunk
     constexpr int LS = LL / 2;                      // short chunk
+    ColArgs<T> a = a_in;
+    if (!a.tp) a.tp = a.nt / 2 + 1;
     const int target = (a.variant & 2) ? 512 : 256;
     cudaError_t e = cudaErrorInvalidConfiguration;
+    if (a.variant == kColSeq) {
+        cx<T> *f = a.field;
+        e = launch_cn_seq<T>(a, &f, 1, st);
+        if (e != cudaErrorInvalidConfiguration) return e;
+        a.variant = kColStagedFirst + 3;            // not supported here: register-fed
+    }
     if (a.variant >= kColStagedFirst) {
         switch (a.variant - kColStagedFirst) {
             case 0: e = launch_cn_staged_l<T, LL, false, 0>(a, st); break;
@@ -793,8 +803,15 @@ cudaError_t launch_cn(const ColArgs<T> &a, cudaStream_t st) {
 }
 
 template <typename T>
-cudaError_t launch_cn_pair(const ColArgs<T> &a, cx<T> *field2, cudaStream_t st) {
+cudaError_t launch_cn_pair(const ColArgs<T> &a_in, cx<T> *field2, cudaStream_t st) {
     constexpr int L = 8;
+    ColArgs<T> a = a_in;
+    if (!a.tp) a.tp = a.nt / 2 + 1;
+    if (a.variant == kColSeq) {
+        cx<T> *f[2] = {a.field, field2};
+        const cudaError_t e = launch_cn_seq<T>(a, f, 2, st);
+        if (e != cudaErrorInvalidConfiguration) return e;
+    }
     if constexpr (sizeof(T) == 4) {
         switch (a.nt) {
             case 512: return launch_cn_pair_l<T, L, 512>(a, field2, st);

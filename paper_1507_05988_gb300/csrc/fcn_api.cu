@@ -273,6 +273,7 @@ struct Pulse {
     double *red = nullptr;     // [16] reduction outputs
     double *rows = nullptr;    // [2*nr] row partials
     double *stage = nullptr;   // double staging [2*nr*nt] for host transfers
+    int *err = nullptr;        // [1] set by a kernel whose bounded wait gave up
     const void *tw = nullptr;
     const void *lo = nullptr, *hi = nullptr;
     const double *lo64 = nullptr, *hi64 = nullptr;
@@ -349,6 +350,10 @@ struct fcn_ctx {
     // paired column launches for pulses sharing a grid and table (FP32):
     // mode -1 decides by timing, 0 off, 1 on; pairs is the decision (-1 open)
     int pair_mode = -1, pairs = -1;
+    // the sequential column kernel over all pulses in one launch (equal
+    // grids, one pivot table): mode -1 decide by timing, 0 off, 1 on;
+    // seq_all is the decision (-1 before the first step)
+    int seq_mode = -1, seq_all = -1;
     // batched work lists (FP32, K = 8, several pulses): one launch per stage
     bool batched = false;
     int2 *row_items = nullptr;
@@ -394,7 +399,7 @@ uint64_t dz_key(double dz) {
 // from this byte offset on, the nr CnCoef rows of the staged column kernels.
 template <typename T>
 size_t coef_offset(int nr, int nt) {
-    const size_t b = sizeof(cx<T>) * (size_t)nr * (size_t)(nt / 2 + 1);
+    const size_t b = sizeof(cx<T>) * (size_t)nr * (size_t)table_pitch(nt);
     return (b + 255) / 256 * 256;
 }
 
@@ -466,6 +471,7 @@ int ensure_table(fcn_ctx *ctx, Pulse &pu, double dz, const cx<T> **out, int side
     ta.dk = dk;
     ta.lo = pu.lo64;
     ta.hi = pu.hi64;
+    ta.tp = table_pitch(pu.g.nt);
     cudaStream_t bs = ctx->st;
     if (side >= 0) {
         if (!ctx->tside[side]) {
@@ -521,6 +527,8 @@ ColArgs<T> col_args(Pulse &pu, void *field, const cx<T> *table, double dz) {
     a.dk = T(dk);
     a.disp = disp;
     a.variant = pu.col_var;
+    a.tp = table_pitch(pu.g.nt);
+    a.err = pu.err;
     return a;
 }
 
@@ -766,17 +774,29 @@ cudaError_t launch_block(fcn_ctx *ctx, int kind, double dz, cudaStream_t st,
     cudaError_t e = cudaSuccess;
     const size_t n = ctx->pulses.size();
     size_t m = 1;
-    if (ctx->multi_mode != 1 || n == 1) {
+    const bool seq_all = ctx->seq_all == 1 && n >= 2;
+    if ((ctx->multi_mode != 1 && !seq_all) || n == 1) {
         for (size_t i = 0; i < n && e == cudaSuccess; i += m) e = launch_group<T>(ctx, kind, dz, st, tabs, fields, i, &m);
         return e;
     }
-    // multi-pulse row launches: per z-step the column stage of every pulse
-    // group, then the row stage of all pulses (each pulse still runs head,
-    // (column, row) per step and tail in order)
+    // multi-pulse row launches (mode 1, and always with the sequential
+    // column kernel over all pulses): per z-step the column stage of every
+    // pulse group, then the row stage of all pulses (each pulse still runs
+    // head, (column, row) per step and tail in order)
     if (kind == 0) return launch_rows_all<T>(ctx, OPS_HEAD, FCN_PROF_ROW_HEAD, dz, st, fields);
     const int reps = kind == 1 ? 8 : 1;
+    // with the sequential column kernel chosen, all pulses (same grid and
+    // pivot table) take one column launch together
     for (int r = 0; r < reps && e == cudaSuccess; ++r) {
-        for (size_t i = 0; i < n && e == cudaSuccess; i += m) e = launch_group<T>(ctx, -1, dz, st, tabs, fields, i, &m);
+        if (seq_all) {
+            std::vector<cx<T> *> f(n);
+            for (size_t i = 0; i < n; ++i) f[i] = (cx<T> *)(fields ? (*fields)[i] : ctx->pulses[i].field);
+            e = timed(ctx, FCN_PROF_COLUMN, st, [&] {
+                return launch_cn_seq<T>(col_args<T>(ctx->pulses[0], f[0], tabs[0], dz), f.data(), (int)n, st);
+            });
+        } else {
+            for (size_t i = 0; i < n && e == cudaSuccess; i += m) e = launch_group<T>(ctx, -1, dz, st, tabs, fields, i, &m);
+        }
         if (e == cudaSuccess)
             e = kind == 3 ? launch_rows_all<T>(ctx, OPS_TAIL, FCN_PROF_ROW_TAIL, dz, st, fields)
                           : launch_rows_all<T>(ctx, OPS_MID, FCN_PROF_ROW_MID, dz, st, fields);
@@ -987,6 +1007,49 @@ int ensure_tuned(fcn_ctx *ctx, const std::vector<const cx<T> *> &tabs, double dz
             if (rc) return rc;
             CK(cudaStreamSynchronize(ctx->st), "pairing sync");
             ctx->pairs = t_pair < t_single ? 1 : 0;
+        }
+    }
+    if (ctx->seq_all < 0) {
+        ctx->seq_all = 0;
+        const size_t n = ctx->pulses.size();
+        Pulse &p0 = ctx->pulses[0];
+        bool eligible = n >= 2 && n <= 8 && ctx->branches == 1 && ctx->seq_mode != 0 &&
+                        cn_seq_supported<T>(col_args<T>(p0, p0.field, tabs[0], dz));
+        for (size_t i = 1; eligible && i < n; ++i)
+            eligible = ctx->pulses[i].g.nr == p0.g.nr && ctx->pulses[i].g.nt == p0.g.nt && tabs[i] == tabs[0];
+        if (eligible && ctx->seq_mode == 1) ctx->seq_all = 1;
+        if (eligible && ctx->seq_mode == -1) {
+            // one launch over all pulses against the per-group launches of
+            // the tuned variants, on private scratch copies of the fields
+            const size_t bytes = csize(ctx->prec) * p0.points();
+            void *scratch = nullptr;
+            CK(cudaMalloc(&scratch, bytes * n), "sequential-column scratch");
+            struct Free {
+                void *p;
+                ~Free() { cudaFree(p); }
+            } guard{scratch};
+            std::vector<void *> f(n);
+            std::vector<cx<T> *> fc(n);
+            for (size_t i = 0; i < n; ++i) {
+                f[i] = (char *)scratch + i * bytes;
+                fc[i] = (cx<T> *)f[i];
+                CK(cudaMemcpyAsync(f[i], ctx->pulses[i].field, bytes, cudaMemcpyDeviceToDevice, ctx->st),
+                   "sequential-column copy");
+            }
+            float t_all = 0.f, t_groups = 0.f;
+            int rc = time_launches(ctx, [&] {
+                return launch_cn_seq<T>(col_args<T>(p0, f[0], tabs[0], dz), fc.data(), (int)n, ctx->st);
+            }, &t_all);
+            if (rc) return rc;
+            rc = time_launches(ctx, [&] {
+                cudaError_t e = cudaSuccess;
+                size_t m = 1;
+                for (size_t i = 0; i < n && e == cudaSuccess; i += m) e = launch_group<T>(ctx, -1, dz, ctx->st, tabs, &f, i, &m);
+                return e;
+            }, &t_groups);
+            if (rc) return rc;
+            CK(cudaStreamSynchronize(ctx->st), "sequential-column sync");
+            ctx->seq_all = t_all < t_groups ? 1 : 0;
         }
     }
     return FCN_OK;
@@ -1379,10 +1442,12 @@ int create_impl(int n, const fcn_grid *grids, const fcn_params *params, int prec
             (e = cudaMalloc(&pu.rho, rsize(prec) * np)) != cudaSuccess ||
             (e = cudaMalloc(&pu.stats, sizeof(double) * NSTAT * pu.g.nr)) != cudaSuccess ||
             (e = cudaMalloc(&pu.red, sizeof(double) * 16)) != cudaSuccess ||
-            (e = cudaMalloc(&pu.rows, sizeof(double) * 2 * pu.g.nr)) != cudaSuccess) {
+            (e = cudaMalloc(&pu.rows, sizeof(double) * 2 * pu.g.nr)) != cudaSuccess ||
+            (e = cudaMalloc(&pu.err, sizeof(int))) != cudaSuccess) {
             cuda_fail(ctx, e, "device allocation");
             return bail(FCN_ERR_NOMEM);
         }
+        cudaMemset(pu.err, 0, sizeof(int));
         cudaMemset(pu.field, 0, csize(prec) * np);
         cudaMemset(pu.rho, 0, rsize(prec) * np);
         cudaMemset(pu.stats, 0, sizeof(double) * NSTAT * pu.g.nr);
@@ -1458,6 +1523,7 @@ void fcn_destroy(fcn_ctx *ctx) {
         cudaFree(pu.red);
         cudaFree(pu.rows);
         cudaFree(pu.stage);
+        cudaFree(pu.err);
     }
     for (auto &kv : ctx->tables) cudaFree(kv.second.ptr);
     if (ctx->mlp) cudaFree(ctx->mlp);
@@ -1527,6 +1593,16 @@ int fcn_set_field_device(fcn_ctx *ctx, int32_t pulse, const void *dev) {
     return FCN_OK;
 }
 
+// FCN_ERR_CUDA when a kernel of this pulse recorded that a bounded wait gave
+// up (the field is then not valid); synchronises the context stream.
+static int check_wait_flag(fcn_ctx *ctx, const Pulse &pu) {
+    int h = 0;
+    CK(cudaMemcpyAsync(&h, pu.err, sizeof(int), cudaMemcpyDeviceToHost, ctx->st), "error flag");
+    CK(cudaStreamSynchronize(ctx->st), "sync");
+    if (h) return fail(ctx, FCN_ERR_CUDA, "column stage: a bounded wait for a TMA copy gave up");
+    return FCN_OK;
+}
+
 int fcn_get_field(fcn_ctx *ctx, int32_t pulse, double *host) {
     Pulse *pu = get_pulse(ctx, pulse);
     if (!pu || !host) return fail(ctx, FCN_ERR_ARG, "bad pulse index or null buffer");
@@ -1538,8 +1614,7 @@ int fcn_get_field(fcn_ctx *ctx, int32_t pulse, double *host) {
         CK(launch_widen<float>((const cx<float> *)pu->field, pu->stage, (int64_t)np, ctx->st), "widen");
         CK(cudaMemcpyAsync(host, pu->stage, 16 * np, cudaMemcpyDeviceToHost, ctx->st), "D2H field");
     }
-    CK(cudaStreamSynchronize(ctx->st), "sync");
-    return FCN_OK;
+    return check_wait_flag(ctx, *pu);
 }
 
 int fcn_set_field_c64(fcn_ctx *ctx, int32_t pulse, const float *host) {
@@ -1573,8 +1648,7 @@ int fcn_get_field_c64(fcn_ctx *ctx, int32_t pulse, float *host) {
         CK(launch_narrow<float>((const double *)pu->field, (cx<float> *)pu->stage, (int64_t)np, ctx->st), "narrow");
         CK(cudaMemcpyAsync(host, pu->stage, 8 * np, cudaMemcpyDeviceToHost, ctx->st), "D2H field");
     }
-    CK(cudaStreamSynchronize(ctx->st), "sync");
-    return FCN_OK;
+    return check_wait_flag(ctx, *pu);
 }
 
 int fcn_get_field_device(fcn_ctx *ctx, int32_t pulse, void *dev) {
@@ -1621,6 +1695,8 @@ int fcn_propagate(fcn_ctx *ctx, double z_end, double dz0, double rtol, double dz
 int fcn_get_diag(fcn_ctx *ctx, int32_t pulse, fcn_diag *out) {
     Pulse *pu = get_pulse(ctx, pulse);
     if (!pu || !out) return fail(ctx, FCN_ERR_ARG, "bad pulse index or null output");
+    const int rc = check_wait_flag(ctx, *pu);
+    if (rc) return rc;
     return ctx->prec == FCN_FP64 ? diag_impl<double>(ctx, *pu, out) : diag_impl<float>(ctx, *pu, out);
 }
 
@@ -1675,6 +1751,7 @@ int fcn_set_variants(fcn_ctx *ctx, int32_t row_variant, int32_t col_variant) {
     ctx->force_col = col_variant;
     ctx->pairs = -1;
     for (auto &pu : ctx->pulses) pu.tuned = false;
+    ctx->seq_all = -1;
     for (auto &kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
     ctx->graphs.clear();
     return FCN_OK;
@@ -1700,12 +1777,25 @@ int fcn_set_pairing(fcn_ctx *ctx, int32_t mode) {
     CK(cudaStreamSynchronize(ctx->st), "sync");
     ctx->pair_mode = mode;
     ctx->pairs = -1;
+    ctx->seq_all = -1;
     for (auto &kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
     ctx->graphs.clear();
     return FCN_OK;
 }
 
 int fcn_get_pairing(const fcn_ctx *ctx) { return ctx ? ctx->pairs : FCN_ERR_ARG; }
+
+int fcn_set_sequential_columns(fcn_ctx *ctx, int32_t mode) {
+    if (!ctx || mode < -1 || mode > 1) return FCN_ERR_ARG;
+    CK(cudaStreamSynchronize(ctx->st), "sync");
+    ctx->seq_mode = mode;
+    ctx->seq_all = -1;
+    for (auto &kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
+    ctx->graphs.clear();
+    return FCN_OK;
+}
+
+int fcn_get_sequential_columns(const fcn_ctx *ctx) { return ctx ? ctx->seq_all : FCN_ERR_ARG; }
 
 int fcn_set_graph_branches(fcn_ctx *ctx, int32_t n) {
     if (!ctx) return FCN_ERR_ARG;
@@ -1717,6 +1807,7 @@ int fcn_set_graph_branches(fcn_ctx *ctx, int32_t n) {
         if (!ctx->join_ev[b]) CK(cudaEventCreateWithFlags(&ctx->join_ev[b], cudaEventDisableTiming), "join event");
     }
     ctx->branches = n;
+    ctx->seq_all = -1;
     for (auto &kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
     ctx->graphs.clear();
     return FCN_OK;
@@ -1729,6 +1820,7 @@ int fcn_set_multi_launch(fcn_ctx *ctx, int32_t mode) {
     CK(cudaStreamSynchronize(ctx->st), "sync");
     if (mode != ctx->multi_mode) {
         ctx->multi_mode = mode;
+        ctx->seq_all = -1;
         for (auto &kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
         ctx->graphs.clear();
     }

@@ -229,7 +229,7 @@ struct alignas(4 * sizeof(T)) CnCoef {
 template <typename T>
 struct ColArgs {
     cx<T> *field;            // [nr][nt], frequency domain, in place
-    const cx<T> *invden;     // [nr][nt/2+1]: 1/pivot_j per |q|
+    const cx<T> *invden;     // [nr][tp]: 1/pivot_j per |q| = 0..nt/2
     const T *lo;             // [nr]: 1 - 1/(2j) (j >= 1), 0 at j = 0
     const T *hi;             // [nr]: 1 + 1/(2j) (j >= 1), 0 at j = 0
     const CnCoef<T> *coef = nullptr;   // [nr] row coefficients (staged variants)
@@ -240,15 +240,23 @@ struct ColArgs {
                              // stage multiplies column q by exp(2 i disp q^2)
     int variant;             // 0..3: register chunks, long/short x CTA 256/512;
                              // 4, 5: cp.async-staged chunks of 16 / 8 rows (FP32);
-                             // 6, 7: register-fed staged chunks of 16 / 8 rows
-                             // (4..7 need coef)
+                             // 6, 7: register-fed staged chunks of 16 / 8 rows;
+                             // 8: one sequential sweep per column, TMA-fed
+                             // (4..8 need coef)
+    int tp = 0;              // row pitch of invden in complex values (>= nt/2 + 1)
+    int *err = nullptr;      // set nonzero by a kernel whose bounded wait gave up
 };
 
 struct TableArgs {
     int nr, nt;
     double s, dk;
     const double *lo, *hi;   // FP64 copies of the ratio tables
+    int tp = 0;              // row pitch of the table in complex values (0: nt/2 + 1)
 };
+
+// Row pitch (complex values) of the pivot tables a context builds: nt/2 + 1
+// rounded up to even, so that every row starts on 16 bytes (a TMA row stride).
+inline int table_pitch(int nt) { return (nt / 2 + 1 + 1) & ~1; }
 
 // ---- launchers (defined in the .cu files) ----
 template <typename T>
@@ -262,8 +270,16 @@ cudaError_t prepare_rows(int nt);
 template <typename T>
 cudaError_t launch_cn(const ColArgs<T> &a, cudaStream_t st);
 constexpr int kRowVariants = 3;
-constexpr int kColVariants = 8;
+constexpr int kColVariants = 9;
 constexpr int kColStagedFirst = 4;      // variants >= this need ColArgs::coef
+constexpr int kColSeq = 8;              // the sequential TMA-fed column kernel (col_seq.cu)
+// Sequential column stage of npulse (1..8) pulses sharing the grid, the
+// coefficients and the pivot table (fields[k], blockIdx.y = k);
+// cudaErrorInvalidConfiguration when cn_seq_supported(a) is false.
+template <typename T>
+cudaError_t launch_cn_seq(const ColArgs<T> &a, cx<T> *const *fields, int npulse, cudaStream_t st);
+template <typename T>
+bool cn_seq_supported(const ColArgs<T> &a);
 template <typename T>
 cudaError_t launch_cn_table(const TableArgs &a, cx<T> *table, cudaStream_t st);
 // Row coefficients for the staged column variants (nr rows).

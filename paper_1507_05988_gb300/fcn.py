@@ -106,6 +106,8 @@ _SIGS = {
     "fcn_set_batching": (C.c_int, [_CTX, C.c_int32]),
     "fcn_set_pairing": (C.c_int, [_CTX, C.c_int32]),
     "fcn_get_pairing": (C.c_int, [_CTX]),
+    "fcn_set_sequential_columns": (C.c_int, [_CTX, C.c_int32]),
+    "fcn_get_sequential_columns": (C.c_int, [_CTX]),
     "fcn_set_field_c64": (C.c_int, [_CTX, C.c_int32, C.POINTER(C.c_float)]),
     "fcn_get_field_c64": (C.c_int, [_CTX, C.c_int32, C.POINTER(C.c_float)]),
     "fcn_set_graph_branches": (C.c_int, [_CTX, C.c_int32]),
@@ -305,6 +307,12 @@ class Solver:
 
     def pairing(self) -> int:
         return int(fcn_get_pairing(self.ctx))
+
+    def set_sequential_columns(self, mode: int):
+        check(fcn_set_sequential_columns(self.ctx, int(mode)), self.ctx)
+
+    def sequential_columns(self) -> int:
+        return int(fcn_get_sequential_columns(self.ctx))
 
     def set_graph_branches(self, n: int):
         check(fcn_set_graph_branches(self.ctx, int(n)), self.ctx)

@@ -355,6 +355,7 @@ def test_profiling_counts_every_launch(fcn, multi):
     wl = W.small(32, 256, p_over_pcr=3.0)
     s = fcn.Solver([wl.physics(), wl.physics()], precision=FP32)
     s.set_multi_launch(multi)
+    s.set_sequential_columns(0)
     for i in range(2):
         s.set_field(wl.field(), pulse=i)
     s.profile(True)
@@ -447,7 +448,7 @@ def test_adaptive_step_doubling_matches_oracle_controller(fcn, prec):
 
 @pytest.mark.parametrize("prec", [FP64, FP32])
 @pytest.mark.parametrize("row_v", [0, 1, 2])
-@pytest.mark.parametrize("col_v", [0, 1, 2, 3, 4, 5, 6, 7])
+@pytest.mark.parametrize("col_v", [0, 1, 2, 3, 4, 5, 6, 7, 8])
 def test_every_kernel_variant_matches_oracle(fcn, prec, row_v, col_v):
     """Every variant the autotuner can pick computes the same step."""
     wl = W.small(130, 1024, p_over_pcr=4.0, noise_seed=6).with_(n2j=(W.N2, W.N4, 0, 0))
@@ -479,11 +480,14 @@ def test_row_occupancy_variants_at_nt_256(fcn, row_v):
 
 
 @pytest.mark.parametrize("prec", [FP64, FP32])
-@pytest.mark.parametrize("nr,nt", [(3, 64), (17, 128), (1000, 256), (2048, 64)])
-@pytest.mark.parametrize("col_v", [4, 5, 6, 7])
+@pytest.mark.parametrize("nr,nt", [(3, 64), (17, 128), (1000, 256), (2048, 64), (37, 32)])
+@pytest.mark.parametrize("col_v", [4, 5, 6, 7, 8])
 def test_staged_column_variants_on_ragged_and_tall_grids(fcn, prec, nr, nt, col_v):
     """Staged column kernels: chunks that overhang Nr, CTAs narrowed for tall
-    grids (Nr = 2048) and widened for short ones, against the oracle."""
+    grids (Nr = 2048) and widened for short ones, against the oracle.  The
+    sequential TMA-fed kernel (8): a ragged last block of rows (Nr = 3, 17,
+    1000), the tallest grid, and Nt = 32, which it does not take (the
+    launcher falls back to another kernel)."""
     wl = W.small(nr, nt, p_over_pcr=3.0, noise_seed=11).with_(n2j=(W.N2, W.N4, 0, 0))
     pb = _pb(wl)
     s = fcn.Solver(wl.physics(), precision=prec)
@@ -496,20 +500,24 @@ def test_staged_column_variants_on_ragged_and_tall_grids(fcn, prec, nr, nt, col_
     assert rel_l2(A, Aref) < (1e-10 if prec == FP64 else 1e-5)
 
 
+@pytest.mark.parametrize("col_v", [7, 8])
 @pytest.mark.parametrize("npulse", [2, 3])
-def test_paired_column_launch_equals_single_launches(fcn, npulse):
-    """Pulses sharing a grid: the paired column kernel computes what the
-    register-fed single kernel (variant 7) does for each pulse (the same
+def test_paired_column_launch_equals_single_launches(fcn, npulse, col_v):
+    """Pulses sharing a grid: the paired column launch computes what the
+    single launch of the same variant does for each pulse -- variant 7: the
+    paired chunked-scan kernel against the register-fed one (the same
     operations; the compiler may contract them into FMAs differently, so to
-    FP32 rounding rather than bit for bit), the odd pulse runs alone, and
+    FP32 rounding rather than bit for bit); variant 8: the sequential
+    TMA-fed kernel over both pulses at once -- the odd pulse runs alone, and
     the result stays on the oracle."""
     wls = [W.small(96, 512, p_over_pcr=4.0, noise_seed=20 + k).with_(n2j=(W.N2, W.N4, 0, 0))
            for k in range(npulse)]
     out = {}
     for mode in (0, 1):
         s = fcn.Solver([w.physics() for w in wls], precision=FP32)
-        s.set_variants(0, 7)
+        s.set_variants(0, col_v)
         s.set_pairing(mode)
+        s.set_sequential_columns(0)
         for k, w in enumerate(wls):
             s.set_field(w.field(), pulse=k)
         s.step(4e-3, 5)
@@ -522,6 +530,43 @@ def test_paired_column_launch_equals_single_launches(fcn, npulse):
         assert np.array_equal(out[0][2], out[1][2])     # the odd pulse runs alone
     Aref, _ = oracle.run(_pb(wls[-1]), 4e-3, 5, wls[-1].field())
     assert rel_l2(out[1][-1], Aref) < 1e-5
+
+
+@pytest.mark.parametrize("prec,npulse,exact", [(FP32, 4, False), (FP32, 5, False), (FP32, 2, True),
+                                                (FP64, 2, False), (FP64, 3, True)])
+def test_sequential_columns_over_all_pulses(fcn, prec, npulse, exact):
+    """The sequential TMA-fed column kernel over every pulse of a context in
+    one launch (two pulses per thread, or one for an odd count) computes the
+    same steps as the per-group launches, stays on the oracle, and makes one
+    column launch per z-step; with the dispersion as its exact factor too."""
+    flags = W.ALL_PHYSICS | (W.EXACT_DISPERSION if exact else 0)
+    wls = [W.small(90, 256, p_over_pcr=4.0, noise_seed=80 + k).with_(n2j=(W.N2, W.N4, 0, 0), flags=flags,
+                                                                     k2=2e-27 if exact else W.K2)
+           for k in range(npulse)]
+    out = {}
+    for mode in (0, 1):
+        s = fcn.Solver([w.physics() for w in wls], precision=prec)
+        s.set_sequential_columns(mode)
+        for k, w in enumerate(wls):
+            s.set_field(w.field(), pulse=k)
+        s.profile(True)
+        s.step(4e-3, 5)
+        prof = s.profile_read()
+        s.profile(False)
+        assert s.sequential_columns() == mode
+        if mode == 1:
+            assert prof["column"][1] == 5
+        s.step(4e-3, 4)                     # graph replay continues the same state
+        out[mode] = [s.get_field(pulse=k) for k in range(npulse)]
+        s.close()
+    # the two column methods round differently (one sequential sweep against
+    # chunked scans), so in FP32 they agree to the rounding of the working
+    # type over these steps, the tolerance each is held to against the oracle
+    tol = 1e-10 if prec == FP64 else 1e-5
+    for k, w in enumerate(wls):
+        assert rel_l2(out[1][k], out[0][k]) < (1e-12 if prec == FP64 else 1e-5)
+        ref, _ = oracle.run(_pb(w), 4e-3, 9, w.field())
+        assert rel_l2(out[1][k], ref) < tol
 
 
 @pytest.mark.parametrize("pairing", [0, 1])
@@ -537,6 +582,7 @@ def test_graph_branches_are_bit_identical(fcn, pairing):
         s = fcn.Solver([w.physics() for w in wls], precision=FP32)
         s.set_variants(0, 7)
         s.set_pairing(pairing)
+        s.set_sequential_columns(0)
         s.set_graph_branches(nb)
         assert s.graph_branches() == nb
         for k, w in enumerate(wls):
@@ -562,6 +608,7 @@ def test_multi_pulse_row_launch_is_bit_identical(fcn, graph):
         s = fcn.Solver([w.physics() for w in wls], precision=FP32)
         s.set_variants(0, 7)
         s.set_pairing(1)
+        s.set_sequential_columns(0)
         s.set_multi_launch(multi)
         assert s.multi_launch() == multi
         for k, w in enumerate(wls):
@@ -634,7 +681,7 @@ def test_autotuner_picks_a_valid_variant_and_stays_correct(fcn):
     s.set_field(wl.field())
     s.step(4e-3, 3)
     rv, cv = s.variants()
-    assert 0 <= rv < 3 and 0 <= cv < 8
+    assert 0 <= rv < 3 and 0 <= cv < 9
     A = s.get_field()
     s.close()
     Aref, _ = oracle.run(pb, 4e-3, 3, wl.field())
@@ -716,6 +763,7 @@ def test_batching_modes_agree(fcn):
     for a, b in zip(res[1], res[0]):
         assert rel_l2(a, b) < 1e-5
     same = fcn.Solver([wls[0].physics()] * 3, precision=FP32)
+    same.set_sequential_columns(0)
     same.profile(True)
     for i in range(3):
         same.set_field(wls[0].field(), pulse=i)
@@ -771,7 +819,7 @@ def test_physics_variants_match_the_oracle(fcn, name, prec):
     assert rel_l2(ref, other) > 1e-6, name
 
 
-@pytest.mark.parametrize("col_variant", list(range(8)))
+@pytest.mark.parametrize("col_variant", list(range(9)))
 def test_exact_dispersion_in_every_column_variant(fcn, col_variant):
     """Every column kernel applies the exact dispersion factor at its final
     store; FP32 (variants 4-7 are FP32-only paths of the tuner) against the
@@ -780,7 +828,8 @@ def test_exact_dispersion_in_every_column_variant(fcn, col_variant):
     ref, _ = oracle.run(_pb(wl), wl.dz, 3, wl.field())
     s = fcn.Solver([wl.physics(), wl.physics()], precision=FP32)
     s.set_variants(0, col_variant)
-    s.set_pairing(1 if col_variant == 7 else 0)
+    s.set_pairing(1 if col_variant in (7, 8) else 0)
+    s.set_sequential_columns(0)
     for k in range(2):
         s.set_field(wl.field(), pulse=k)
     s.step(wl.dz, 3)
