@@ -305,8 +305,13 @@ int fcn_get_variants(fcn_ctx *ctx, int32_t pulse, int32_t out[2]);
 #define FCN_PROF_COLUMN    3   /* Crank-Nicolson column solve                      */
 #define FCN_PROF_KINDS     4
 
-/* on != 0: later fcn_step calls launch kernels directly (no graphs) with a
- * CUDA event pair around each launch on the context stream; on = 0 stops. */
+/* on = 1: later fcn_step calls launch kernels directly (no graphs) with a
+ * CUDA event pair around each launch on the context stream.
+ * on = 2: later fcn_step calls replay graphs captured with an event record
+ * node before and after every kernel (separate from the untimed graphs), so
+ * the kernels run in the launch structure of an unprofiled replay; each
+ * replay is followed by a synchronisation that reads the events.
+ * on = 0 stops.  FCN_ERR_ARG for other values. */
 int fcn_profile_enable(fcn_ctx *ctx, int32_t on);
 
 /* Total device milliseconds and launch counts per kind (FCN_PROF_KINDS

@@ -306,7 +306,7 @@ struct TableEntry {
 constexpr int kMaxBranches = 8;
 
 struct GraphKey {
-    int kind;        // 0 head, 1 mid x8, 2 mid x1, 3 tail
+    int kind;        // 0 head, 1 mid x8, 2 mid x1, 3 tail; + 4: captured with timing events
     uint64_t dz;
     bool operator<(const GraphKey &o) const { return kind != o.kind ? kind < o.kind : dz < o.dz; }
 };
@@ -337,8 +337,13 @@ struct fcn_ctx {
     std::string err = "no error";
     double *host_red = nullptr;       // pinned [16]
     // kernel timing (fcn_profile_enable): one event pair per launch, by kind
-    bool profiling = false;
-    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof_events;
+    // kernel timing: 0 off, 1 direct launches with an event pair each, 2
+    // graphs captured with an event record node before and after each kernel
+    int profiling = 0;
+    using EvList = std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>>;
+    EvList prof_events;
+    std::map<GraphKey, EvList> graph_events;   // the events of each timed graph
+    EvList *cap_events = nullptr;              // set while a timed graph is captured
     double prof_ms[FCN_PROF_KINDS] = {0};
     int64_t prof_n[FCN_PROF_KINDS] = {0};
     float *mlp = nullptr;             // device FP32 master weights (FCN_MLP_NPARAM)
@@ -403,6 +408,8 @@ size_t coef_offset(int nr, int nt) {
     return (b + 255) / 256 * 256;
 }
 
+void drop_graphs(fcn_ctx *ctx, bool all, uint64_t dz);
+
 // The pivot table of (grid, dz), built on first use.  side = -1 builds it on
 // the launch stream; side = 0 or 1 builds it on a side stream (after all
 // work already queued on the launch stream, which may still read an evicted
@@ -434,18 +441,12 @@ int ensure_table(fcn_ctx *ctx, Pulse &pu, double dz, const cx<T> **out, int side
             if (t->second.stamp < old->second.stamp) old = t;
         const uint64_t odz = old->second.dz;
         bool dropped = false;
-        for (int kind = 0; kind < 4; ++kind) dropped |= ctx->graphs.count(GraphKey{kind, odz}) > 0;
+        for (int kind = 0; kind < 8; ++kind) dropped |= ctx->graphs.count(GraphKey{kind, odz}) > 0;
         dropped |= ctx->batch_args.count(odz) > 0;
         if (dropped) {
             // graphs and argument arrays that refer to the table go with it
             CK(cudaStreamSynchronize(ctx->st), "sync before table eviction");
-            for (int kind = 0; kind < 4; ++kind) {
-                auto g = ctx->graphs.find(GraphKey{kind, odz});
-                if (g != ctx->graphs.end()) {
-                    cudaGraphExecDestroy(g->second);
-                    ctx->graphs.erase(g);
-                }
-            }
+            drop_graphs(ctx, false, odz);
             auto ba = ctx->batch_args.find(odz);
             if (ba != ctx->batch_args.end()) {
                 cudaFree(ba->second.first);
@@ -536,6 +537,20 @@ ColArgs<T> col_args(Pulse &pu, void *field, const cx<T> *table, double dz) {
 template <typename F>
 cudaError_t timed(fcn_ctx *ctx, int kind, cudaStream_t st, F &&launch) {
     if (!ctx->profiling) return launch();
+    if (ctx->profiling == 2) {
+        // inside a capture the two records become event nodes of the graph
+        if (!ctx->cap_events) return launch();
+        cudaEvent_t e0, e1;
+        cudaError_t e = cudaEventCreate(&e0);
+        if (e != cudaSuccess) return e;
+        if ((e = cudaEventCreate(&e1)) != cudaSuccess) { cudaEventDestroy(e0); return e; }
+        ctx->cap_events->push_back({kind, {e0, e1}});
+        // "external" records: event nodes of the graph, recorded at every
+        // replay (a plain record inside a capture only orders the capture)
+        if ((e = cudaEventRecordWithFlags(e0, st, cudaEventRecordExternal)) != cudaSuccess) return e;
+        if ((e = launch()) != cudaSuccess) return e;
+        return cudaEventRecordWithFlags(e1, st, cudaEventRecordExternal);
+    }
     cudaEvent_t e0, e1;
     cudaError_t e = cudaEventCreate(&e0);
     if (e != cudaSuccess) return e;
@@ -559,6 +574,24 @@ void profile_collect(fcn_ctx *ctx) {
         cudaEventDestroy(pe.second.second);
     }
     ctx->prof_events.clear();
+}
+
+// Destroys the captured graphs (all, or those of one dz bit pattern) and the
+// timing events that belong to them.
+void drop_graphs(fcn_ctx *ctx, bool all, uint64_t dz) {
+    for (auto it = ctx->graphs.begin(); it != ctx->graphs.end();) {
+        if (!all && it->first.dz != dz) { ++it; continue; }
+        cudaGraphExecDestroy(it->second);
+        auto ev = ctx->graph_events.find(it->first);
+        if (ev != ctx->graph_events.end()) {
+            for (auto &pe : ev->second) {
+                cudaEventDestroy(pe.second.first);
+                cudaEventDestroy(pe.second.second);
+            }
+            ctx->graph_events.erase(ev);
+        }
+        it = ctx->graphs.erase(it);
+    }
 }
 
 constexpr int OPS_HEAD = OP_NL | OP_FFT;
@@ -826,23 +859,44 @@ cudaError_t launch_block_branched(fcn_ctx *ctx, int kind, double dz, cudaStream_
     return e;
 }
 
+// The timing events made during one capture: destroyed unless the graph
+// is kept (release()).
+struct ContextEvents {
+    fcn_ctx::EvList list;
+    fcn_ctx::EvList release() {
+        fcn_ctx::EvList out;
+        out.swap(list);
+        return out;
+    }
+    ~ContextEvents() {
+        for (auto &pe : list) {
+            cudaEventDestroy(pe.second.first);
+            cudaEventDestroy(pe.second.second);
+        }
+    }
+};
+
 template <typename T>
 int run_block(fcn_ctx *ctx, int kind, double dz, const std::vector<const cx<T> *> &tabs,
               bool use_graph) {
-    if (!use_graph || ctx->profiling) {
+    if (!use_graph || ctx->profiling == 1) {
         CK(launch_block<T>(ctx, kind, dz, ctx->st, tabs), "kernel launch");
         return FCN_OK;
     }
-    GraphKey key{kind, dz_key(dz)};
+    const bool timed_graph = ctx->profiling == 2;
+    GraphKey key{kind + (timed_graph ? 4 : 0), dz_key(dz)};
     auto it = ctx->graphs.find(key);
     if (it == ctx->graphs.end()) {
         // capture on the internal stream (the legacy default stream cannot
         // be captured), then replay on the caller's stream
         cudaGraph_t g = nullptr;
+        ContextEvents evs;
         CK(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
+        if (timed_graph) ctx->cap_events = &evs.list;
         cudaError_t le = (ctx->branches > 1 && !ctx->batched)
                              ? launch_block_branched<T>(ctx, kind, dz, ctx->cap, tabs)
                              : launch_block<T>(ctx, kind, dz, ctx->cap, tabs);
+        ctx->cap_events = nullptr;
         cudaError_t ce = cudaStreamEndCapture(ctx->cap, &g);
         if (le != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_fail(ctx, le, "captured launch"); }
         if (ce != cudaSuccess) return cuda_fail(ctx, ce, "end capture");
@@ -851,8 +905,20 @@ int run_block(fcn_ctx *ctx, int kind, double dz, const std::vector<const cx<T> *
         cudaGraphDestroy(g);
         if (ie != cudaSuccess) return cuda_fail(ctx, ie, "graph instantiate");
         it = ctx->graphs.emplace(key, ex).first;
+        if (timed_graph) ctx->graph_events[key] = evs.release();
     }
     CK(cudaGraphLaunch(it->second, ctx->st), "graph launch");
+    if (timed_graph) {
+        // the graph's event nodes hold this replay's times: read them before
+        // the next replay records them again
+        CK(cudaStreamSynchronize(ctx->st), "timed graph sync");
+        for (auto &pe : ctx->graph_events[key]) {
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, pe.second.first, pe.second.second), "graph event time");
+            ctx->prof_ms[pe.first] += ms;
+            ctx->prof_n[pe.first] += 1;
+        }
+    }
     return FCN_OK;
 }
 
@@ -1512,7 +1578,7 @@ void fcn_destroy(fcn_ctx *ctx) {
     if (!ctx) return;
     if (ctx->st) cudaStreamSynchronize(ctx->st);
     cudaDeviceSynchronize();
-    for (auto &kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
+    drop_graphs(ctx, true, 0);
     profile_collect(ctx);
     for (auto &pu : ctx->pulses) {
         cudaFree(pu.field);
@@ -1752,8 +1818,7 @@ int fcn_set_variants(fcn_ctx *ctx, int32_t row_variant, int32_t col_variant) {
     ctx->pairs = -1;
     for (auto &pu : ctx->pulses) pu.tuned = false;
     ctx->seq_all = -1;
-    for (auto &kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
-    ctx->graphs.clear();
+    drop_graphs(ctx, true, 0);
     return FCN_OK;
 }
 
@@ -1765,8 +1830,7 @@ int fcn_set_batching(fcn_ctx *ctx, int32_t mode) {
         return fail(ctx, FCN_ERR_UNSUPPORTED, "work lists need several FP32 pulses with K = 8 and Nt >= 512");
     const bool want = mode == 1 || (mode == -1 && possible && grids_uneven(ctx) && small_pulses_dominate(ctx));
     if (want != ctx->batched) {
-        for (auto &kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
-        ctx->graphs.clear();
+        drop_graphs(ctx, true, 0);
         ctx->batched = want;
     }
     return FCN_OK;
@@ -1778,8 +1842,7 @@ int fcn_set_pairing(fcn_ctx *ctx, int32_t mode) {
     ctx->pair_mode = mode;
     ctx->pairs = -1;
     ctx->seq_all = -1;
-    for (auto &kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
-    ctx->graphs.clear();
+    drop_graphs(ctx, true, 0);
     return FCN_OK;
 }
 
@@ -1790,8 +1853,7 @@ int fcn_set_sequential_columns(fcn_ctx *ctx, int32_t mode) {
     CK(cudaStreamSynchronize(ctx->st), "sync");
     ctx->seq_mode = mode;
     ctx->seq_all = -1;
-    for (auto &kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
-    ctx->graphs.clear();
+    drop_graphs(ctx, true, 0);
     return FCN_OK;
 }
 
@@ -1808,8 +1870,7 @@ int fcn_set_graph_branches(fcn_ctx *ctx, int32_t n) {
     }
     ctx->branches = n;
     ctx->seq_all = -1;
-    for (auto &kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
-    ctx->graphs.clear();
+    drop_graphs(ctx, true, 0);
     return FCN_OK;
 }
 
@@ -1821,8 +1882,7 @@ int fcn_set_multi_launch(fcn_ctx *ctx, int32_t mode) {
     if (mode != ctx->multi_mode) {
         ctx->multi_mode = mode;
         ctx->seq_all = -1;
-        for (auto &kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
-        ctx->graphs.clear();
+        drop_graphs(ctx, true, 0);
     }
     return FCN_OK;
 }
@@ -1839,9 +1899,10 @@ int fcn_get_variants(fcn_ctx *ctx, int32_t pulse, int32_t out[2]) {
 
 int fcn_profile_enable(fcn_ctx *ctx, int32_t on) {
     if (!ctx) return FCN_ERR_ARG;
+    if (on < 0 || on > 2) return fail(ctx, FCN_ERR_ARG, "profiling mode must be 0, 1 or 2");
     CK(cudaStreamSynchronize(ctx->st), "profile sync");
     profile_collect(ctx);
-    ctx->profiling = on != 0;
+    ctx->profiling = on;
     return FCN_OK;
 }
 

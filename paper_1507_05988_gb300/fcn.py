@@ -331,8 +331,12 @@ class Solver:
         check(fcn_get_variants(self.ctx, pulse, out), self.ctx)
         return out[0], out[1]
 
-    def profile(self, on: bool):
-        check(fcn_profile_enable(self.ctx, 1 if on else 0), self.ctx)
+    def profile(self, on):
+        """False/0: off; True/1: direct launches, an event pair around each;
+        2: graphs captured with event nodes around each kernel (the launch
+        structure and timing of an unprofiled graph replay)."""
+        mode = (1 if on else 0) if isinstance(on, bool) else int(on)
+        check(fcn_profile_enable(self.ctx, mode), self.ctx)
 
     def profile_read(self, reset: bool = True) -> dict:
         ms = (C.c_double * FCN_PROF_KINDS)()

@@ -33,7 +33,8 @@ def main(argv=None) -> int:
     ap.add_argument("--multi", type=int, default=2, help="multi-pulse row launch mode (0, 1, 2)")
     ap.add_argument("--time", type=int, default=0,
                     help="then time this many graph-replayed steps (wall clock around a "
-                         "synchronising call) and as many per-launch event-timed steps")
+                         "synchronising call) and as many steps replayed from graphs with "
+                         "event nodes around every kernel")
     ap.add_argument("--cartesian", action="store_true")
     ap.add_argument("--nxy", type=int, default=255,
                     help="Cartesian nodes per transverse axis (the walls stay at +-5 w0)")
@@ -66,12 +67,13 @@ def main(argv=None) -> int:
         print(f"profile_case: graph replay {1e6 * dt / (a.time * a.pulses):.2f} us per pulse-step "
               f"({a.pulses} pulses, {a.branches} graph branches, "
               f"multi-pulse row launch mode {a.multi})")
-        s.profile(True)
+        s.profile(2)
         s.step(dz, a.time)
         s.diag(0)
         for k, (ms, n) in s.profile_read().items():
             if n:
-                print(f"profile_case: {k} {n} launches, {1e3 * ms / n:.2f} us per launch (events)")
+                print(f"profile_case: {k} {n} launches, {1e3 * ms / n:.2f} us per launch "
+                      "(event nodes in the graphs)")
         s.profile(False)
     print(f"profile_case: config {a.config} {a.precision} steps {a.steps} variants {s.variants(0)} "
           f"energy {d['energy']:.6e}")

@@ -377,6 +377,37 @@ def test_profiling_counts_every_launch(fcn, multi):
     s.close()
 
 
+@pytest.mark.parametrize("seq", [0, 1])
+def test_in_graph_kernel_timing(fcn, seq):
+    """Timing mode 2 replays graphs that carry event nodes around every
+    kernel: it counts every launch of the graph-replayed steps, and the
+    steps it runs are bit-identical to untimed graph replay."""
+    wls = [W.small(64, 512, p_over_pcr=3.0, noise_seed=90 + k) for k in range(2)]
+    out = {}
+    for timed in (False, True):
+        s = fcn.Solver([w.physics() for w in wls], precision=FP32)
+        s.set_pairing(0)
+        s.set_sequential_columns(seq)
+        for k, w in enumerate(wls):
+            s.set_field(w.field(), pulse=k)
+        if timed:
+            s.profile(2)
+        s.step(4e-3, 11)           # head, middle blocks of 8 and 1 x 1, tail
+        if timed:
+            prof = s.profile_read()
+            s.profile(False)
+        out[timed] = [s.get_field(pulse=k) for k in range(2)]
+        s.close()
+    for a, b in zip(out[False], out[True]):
+        assert np.array_equal(a, b)
+    # per pulse: 1 head, 10 middle, 1 tail row stages and 11 column stages;
+    # with the sequential kernel all pulses share each launch
+    per = 1 if seq else 2
+    assert prof["row_head"][1] == per and prof["row_tail"][1] == per
+    assert prof["row_mid"][1] == 10 * per and prof["column"][1] == 11 * per
+    assert all(ms > 0 for ms, n in prof.values())
+
+
 def test_diagnostics_and_profiles_match_oracle(fcn):
     wl = W.small(40, 128, p_over_pcr=3.0, noise_seed=4)
     pb = _pb(wl)
