@@ -184,15 +184,21 @@ int fcn_step(fcn_ctx *ctx, double dz, int64_t n);
  * (for profiling and for checking that graph replay is identical). */
 int fcn_step_nograph(fcn_ctx *ctx, double dz, int64_t n);
 
-/* Adaptive propagation of a single-pulse context to z_end by step doubling:
- * one step of dz and two of dz/2 from the same state; err = ||A2-A1||/||A2||
- * (FP64 reduction); err <= rtol accepts A2; next dz = dz*clamp(0.9
- * (rtol/err)^(1/3), 0.2, 2); the last step lands on z_end exactly.
- * controller 0: proposals from that formula; controller 1: proposals from
- * the learned MLP (fcn_mlp_set) with the formula as fallback after a
- * rejection.  dz0 > 0 is the first proposal.  Fails with
- * FCN_ERR_STEP_UNDERFLOW if dz < dz_min or after max_reject consecutive
- * rejections.  out may be NULL. */
+/* Adaptive propagation to z_end by step doubling: one step of dz and two of
+ * dz/2 from the same state; err = ||A2-A1||/||A2|| (FP64 reduction);
+ * err <= rtol accepts A2; next dz = dz*clamp(0.9 (rtol/err)^(1/3), 0.2, 2);
+ * the last step lands on z_end exactly.  controller 0: proposals from that
+ * formula; controller 1: proposals from the learned MLP (fcn_mlp_set) with
+ * the formula as fallback after a rejection.  dz0 > 0 is the first
+ * proposal.  Fails with FCN_ERR_STEP_UNDERFLOW if dz < dz_min or after
+ * max_reject consecutive rejections.  out may be NULL.
+ * Multi-pulse contexts (all pulses at the same z, batching 0) advance with
+ * one common dz: every attempt runs on all pulses in the launches of
+ * fcn_step (one launch per stage for pulses that share it) and is accepted
+ * when every pulse's err is within rtol; the formula follows the largest
+ * err, the MLP proposes per pulse from that pulse's features and the
+ * smallest proposal is taken.  Counts in *out are per attempt of the batch
+ * (one accepted attempt = one step of every pulse). */
 int fcn_propagate(fcn_ctx *ctx, double z_end, double dz0, double rtol, double dz_min,
                   int32_t max_reject, int32_t controller, fcn_stats *out);
 
@@ -327,28 +333,33 @@ int fcn_profile_read(fcn_ctx *ctx, double *ms, int64_t *count, int32_t reset);
 #define FCN_MLP_NH      64
 #define FCN_MLP_NPARAM  4673
 
-/* Features of a field (computed on the device from the FP64 diagnostics):
+/* Features of a field, computed on the device from the FP64 row statistics
+ * that the closing row launch of every attempt writes anyway (no extra pass):
  *   f0 = log(peak I / I_ref)            f1 = log10(peak rho/rho_nt + 1e-30)/10
- *   f2 = spectral rms / rms_ref - 1     f3 = relative change of peak I over the last step
+ *   f2 = log(on-axis peak I / peak I)   f3 = relative change of peak I over the last step
  *   f4 = log(dz_prev / L_ref)           f5 = log(err_prev / rtol)
- * with I_ref, rms_ref from the field at the start of fcn_propagate and
+ *   fE = relative change of the energy over the last step
+ * with I_ref from the field at the start of fcn_propagate and
  * L_ref = k0 (r_max/5)^2 / 2.  With g = f4 - f5/3 (log of the step that
- * would have brought the last accepted attempt to err = rtol), the network
- * takes n = (f0, f1, f2, f3 exp(-f5/3), g, 0) and its output y corrects the
+ * would have brought the last accepted attempt to err = rtol) and
+ * s = exp(-f5/3), the network takes n = (f0, f1, f2, f3 s, g, fE s) (the
+ * changes scaled to a step of exp(g) L_ref) and its output y corrects the
  * step-doubling law: the proposal is dz = L_ref exp(g + y) (a zero network
  * gives that law without its 0.9 safety factor), clamped to [0.2, 2] times
  * the last accepted step. */
+#define FCN_MLP_LOG_FLOATS 9
 
 /* Loads / reads FP32 master weights (host, FCN_MLP_NPARAM floats). */
 int fcn_mlp_set(fcn_ctx *ctx, const float *host_params);
 int fcn_mlp_get(fcn_ctx *ctx, float *host_params);
 
 /* Makes fcn_propagate append one record per attempt to a caller-owned host
- * buffer of capacity records of 8 floats: f0..f5 of the state the attempt
- * started from, log(h / L_ref) of the attempted step and log(err / rtol) of
- * its step-doubling error.  log(dz_safe / L_ref) of that state follows as
- * rec[6] - rec[7]/3 (the Strang local error is O(dz^3)), and the network's
- * training label as that minus g = rec[4] - rec[5]/3.  capacity 0 stops.
+ * buffer of capacity records of FCN_MLP_LOG_FLOATS (9) floats: f0..f5 and fE
+ * of the state the attempt started from, log(h / L_ref) of the attempted
+ * step and log(err / rtol) of its step-doubling error.  log(dz_safe / L_ref)
+ * of that state follows as rec[7] - rec[8]/3 (the Strang local error is
+ * O(dz^3)), and the network's training label as that minus
+ * g = rec[4] - rec[5]/3.  capacity 0 stops.  Single-pulse contexts only.
  * fcn_mlp_log_count returns the number of records written. */
 int fcn_mlp_set_log(fcn_ctx *ctx, float *host_buf, int64_t capacity);
 int64_t fcn_mlp_log_count(const fcn_ctx *ctx);
@@ -511,6 +522,18 @@ int  fcn_xy_get_variants(const fcn_xy_ctx *ctx, int32_t out[2]);
 #define FCN_XY_PROF_KINDS     5
 int  fcn_xy_profile_enable(fcn_xy_ctx *ctx, int32_t on);
 int  fcn_xy_profile_read(fcn_xy_ctx *ctx, double *ms, int64_t *count, int32_t reset);
+
+/* ===================== arithmetic peak (measurement) =====================
+ * Not an operation of the method: the denominator of the ALU rooflines that
+ * the FP64 path and the row stage are measured against.  Runs this
+ * library's FMA microkernel (independent FMA chains in every thread, 8 CTAs
+ * of 256 threads per SM, best of three CUDA-event-timed launches after a
+ * warm-up) on the current device and stream and returns the rate in
+ * FLOP/s (an FMA counts two) in *flop_per_s.  kind 0: FP64 fma; 1: FP32
+ * fmaf; 2: FP32 packed fma.rn.f32x2 (two FMAs per instruction).  The clocks
+ * are those the GPU runs at; nothing here changes them.  Synchronises.
+ * Errors: FCN_ERR_ARG, FCN_ERR_NOMEM, FCN_ERR_CUDA. */
+int fcn_alu_peak(int32_t kind, double *flop_per_s, void *stream);
 
 /* Library version string. */
 const char *fcn_version(void);

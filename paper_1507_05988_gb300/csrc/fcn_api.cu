@@ -349,6 +349,8 @@ struct fcn_ctx {
     float *mlp = nullptr;             // device FP32 master weights (FCN_MLP_NPARAM)
     bool has_mlp = false;
     unsigned char *mlp_io = nullptr;  // features (8 floats) + proposal (double)
+    unsigned char *batch_io = nullptr;  // the same per pulse of an adaptive batch (64 B each)
+    double *host_ctl = nullptr;         // pinned, 16 doubles per pulse of an adaptive batch
     float *log_buf = nullptr;         // caller-owned host log of adaptive attempts
     int64_t log_cap = 0, log_n = 0;
     int force_row = -1, force_col = -1;   // -1: autotune; else forced variant
@@ -1223,10 +1225,200 @@ int diag_device(fcn_ctx *ctx, Pulse &pu, void *field) {
 // Step doubling (controller 0) or MLP proposals judged by step doubling
 // (controller 1).  With a log buffer (fcn_mlp_set_log) every attempt appends
 // [f0..f5, log(h/L_ref), log(err/rtol)] for training.
+// Adaptive propagation of every pulse of a multi-pulse context with one
+// common dz: each attempt runs one step of h and two of h/2 on all pulses
+// (the launch structure of fcn_step: one launch per stage for pulses that
+// share it), and is accepted when every pulse's step-doubling error is
+// within rtol, so the batch moves at the pace of its hardest pulse.  The
+// law's proposal follows the largest error; the learned controller
+// proposes, per pulse, from that pulse's features, and the smallest
+// proposal is taken.  Counters: an accepted attempt is one accepted step of
+// every pulse.
+template <typename T>
+int propagate_batch(fcn_ctx *ctx, double z_end, double dz0, double rtol, double dz_min, int max_reject,
+                    int controller, fcn_stats *out) {
+    const size_t n = ctx->pulses.size();
+    for (auto &pu : ctx->pulses)
+        if (!pu.has_field) return fail(ctx, FCN_ERR_STATE, "fcn_set_field has not been called");
+    if (!(dz0 > 0) || !std::isfinite(dz0) || !(rtol > 0) || !std::isfinite(z_end) || !(dz_min > 0))
+        return fail(ctx, FCN_ERR_ARG, "bad adaptive arguments");
+    if (controller != 0 && controller != 1) return fail(ctx, FCN_ERR_ARG, "controller must be 0 or 1");
+    if (controller == 1 && !ctx->has_mlp) return fail(ctx, FCN_ERR_STATE, "controller 1 needs MLP weights");
+    if (ctx->batched) return fail(ctx, FCN_ERR_UNSUPPORTED, "adaptive batches use per-pulse launches (batching 0)");
+    for (auto &pu : ctx->pulses)
+        if (pu.z != ctx->pulses[0].z) return fail(ctx, FCN_ERR_STATE, "the pulses of a batch must be at one z");
+    {
+        std::vector<const cx<T> *> tabs(n);
+        for (size_t i = 0; i < n; ++i) {
+            int rc = ensure_table<T>(ctx, ctx->pulses[i], dz0, &tabs[i]);
+            if (rc) return rc;
+        }
+        int rc = ensure_tuned<T>(ctx, tabs, dz0);
+        if (rc) return rc;
+    }
+    bool same_grid = true;
+    for (auto &pu : ctx->pulses)
+        same_grid = same_grid && pu.g.nr == ctx->pulses[0].g.nr && pu.g.nt == ctx->pulses[0].g.nt &&
+                    pu.g.r_max == ctx->pulses[0].g.r_max && pu.g.t_window == ctx->pulses[0].g.t_window &&
+                    pu.p.n0 == ctx->pulses[0].p.n0 && pu.p.lambda0 == ctx->pulses[0].p.lambda0 &&
+                    pu.p.k2 == ctx->pulses[0].p.k2 && pu.p.flags == ctx->pulses[0].p.flags;
+    for (auto &pu : ctx->pulses) {
+        const size_t bytes = csize(ctx->prec) * pu.points();
+        if (!pu.work1) CK(cudaMalloc(&pu.work1, bytes), "work buffer");
+        if (!pu.work2) CK(cudaMalloc(&pu.work2, bytes), "work buffer");
+    }
+    const bool features = controller == 1;
+    // per pulse: features (8 floats) and proposal (double) on the device;
+    // errors, features, proposal and energy on the host
+    if (!ctx->batch_io) CK(cudaMalloc(&ctx->batch_io, 64 * n), "controller buffer");
+    if (!ctx->host_ctl) CK(cudaMallocHost(&ctx->host_ctl, 16 * sizeof(double) * n), "controller buffer");
+    double *H = ctx->host_ctl;
+    auto feat_d = [&](size_t i) { return reinterpret_cast<float *>(ctx->batch_io + 64 * i); };
+    auto dz_d = [&](size_t i) { return reinterpret_cast<double *>(ctx->batch_io + 64 * i + 32); };
+    std::vector<MlpScalars> sc(n);
+    std::vector<float> peak(n, 0.f);
+    for (size_t i = 0; i < n; ++i) {
+        Pulse &pu = ctx->pulses[i];
+        const Consts cs = derive(pu.g, pu.p);
+        std::memset(&sc[i], 0, sizeof(MlpScalars));
+        sc[i].rtol = rtol;
+        sc[i].l_ref = cs.k0 * (pu.g.r_max / 5.0) * (pu.g.r_max / 5.0) / 2.0;
+        sc[i].domega = cs.domega;
+    }
+    if (features) {
+        for (size_t i = 0; i < n; ++i) {
+            Pulse &pu = ctx->pulses[i];
+            int rc = diag_device<T>(ctx, pu, pu.field);
+            if (rc) return rc;
+            CK(cudaMemcpyAsync(H + 16 * i, pu.red, 8 * sizeof(double), cudaMemcpyDeviceToHost, ctx->st), "ref copy");
+        }
+        CK(cudaStreamSynchronize(ctx->st), "ref sync");
+        for (size_t i = 0; i < n; ++i) {
+            sc[i].i_ref = H[16 * i + 1] > 0 ? H[16 * i + 1] : 1.0;
+            sc[i].peak_prev = sc[i].i_ref;
+            peak[i] = (float)sc[i].i_ref;
+            sc[i].e_prev = H[16 * i];
+            sc[i].dz_prev = dz0;
+            sc[i].err_prev = rtol;
+        }
+    }
+    fcn_stats s;
+    std::memset(&s, 0, sizeof s);
+    double z = ctx->pulses[0].z, dz = dz0;
+    int consecutive = 0, status = FCN_OK;
+    bool from_mlp = false;
+    std::vector<void *> f1(n), f2(n);
+    std::vector<const cx<T> *> tab1(n), tab2(n);
+    while (z < z_end) {
+        double h = dz;
+        bool last = false;
+        if (z + h >= z_end) { h = z_end - z; last = true; }
+        // pivot tables of h and h/2: for a batch on one grid, on side streams
+        // behind the copies and the opening row stages
+        cudaEvent_t ev1 = nullptr, ev2 = nullptr;
+        for (size_t i = 0; i < n; ++i) {
+            Pulse &pu = ctx->pulses[i];
+            const int side1 = same_grid && i == 0 ? 0 : -1, side2 = same_grid && i == 0 ? 1 : -1;
+            int rc = ensure_table<T>(ctx, pu, h, &tab1[i], side1, side1 >= 0 ? &ev1 : nullptr);
+            if (!rc) rc = ensure_table<T>(ctx, pu, 0.5 * h, &tab2[i], side2, side2 >= 0 ? &ev2 : nullptr);
+            if (rc) return rc;
+            const size_t bytes = csize(ctx->prec) * pu.points();
+            CK(cudaMemcpyAsync(pu.work1, pu.field, bytes, cudaMemcpyDeviceToDevice, ctx->st), "copy");
+            CK(cudaMemcpyAsync(pu.work2, pu.field, bytes, cudaMemcpyDeviceToDevice, ctx->st), "copy");
+            f1[i] = pu.work1;
+            f2[i] = pu.work2;
+        }
+        CK(launch_block<T>(ctx, 0, h, ctx->st, tab1, &f1), "head");
+        if (ev1) CK(cudaStreamWaitEvent(ctx->st, ev1, 0), "table wait");
+        CK(launch_block<T>(ctx, 3, h, ctx->st, tab1, &f1), "one step");
+        CK(launch_block<T>(ctx, 0, 0.5 * h, ctx->st, tab2, &f2), "head");
+        if (ev2) CK(cudaStreamWaitEvent(ctx->st, ev2, 0), "table wait");
+        CK(launch_block<T>(ctx, 2, 0.5 * h, ctx->st, tab2, &f2), "first half step");
+        CK(launch_block<T>(ctx, 3, 0.5 * h, ctx->st, tab2, &f2), "second half step");
+        const bool next_feat = features && !last;
+        for (size_t i = 0; i < n; ++i) {
+            Pulse &pu = ctx->pulses[i];
+            CK(launch_diff_norm<T>((const cx<T> *)pu.work1, (const cx<T> *)pu.work2, pu.g.nr, pu.g.nt, pu.rows,
+                                   pu.red, ctx->st), "error norm");
+            CK(cudaMemcpyAsync(H + 16 * i, pu.red, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->st), "norm copy");
+            if (next_feat) {
+                // the closing row launch left this pulse's statistics of work2
+                sc[i].peak_prev = peak[i];
+                sc[i].dz_prev = h;
+                sc[i].dz_lo = std::fmax(0.2 * h, dz_min);
+                sc[i].dz_hi = 2.0 * h;
+                CK(launch_reduce_stats(pu.stats, pu.g.nr, pu.red + 8, ctx->st), "feature reduction");
+                CK(launch_mlp_propose(pu.red + 8, sc[i], ctx->mlp, feat_d(i), dz_d(i), ctx->st, pu.red), "features");
+                CK(cudaMemcpyAsync(H + 16 * i + 8, feat_d(i), 8 * sizeof(float), cudaMemcpyDeviceToHost, ctx->st),
+                   "features copy");
+                CK(cudaMemcpyAsync(H + 16 * i + 12, dz_d(i), sizeof(double), cudaMemcpyDeviceToHost, ctx->st),
+                   "proposal copy");
+                CK(cudaMemcpyAsync(H + 16 * i + 13, pu.red + 8, sizeof(double), cudaMemcpyDeviceToHost, ctx->st),
+                   "energy copy");
+            }
+        }
+        CK(cudaStreamSynchronize(ctx->st), "norm sync");
+        double err = 0.0;
+        std::vector<double> erri(n);
+        for (size_t i = 0; i < n; ++i) {
+            erri[i] = H[16 * i + 1] > 0 ? std::sqrt(H[16 * i] / H[16 * i + 1]) : std::sqrt(H[16 * i]);
+            if (!std::isfinite(erri[i])) err = erri[i];
+            else if (std::isfinite(err)) err = std::fmax(err, erri[i]);
+        }
+        s.substeps += 3;
+        s.last_err = err;
+        if (!std::isfinite(err)) { status = fail(ctx, FCN_ERR_NONFINITE, "non-finite step-doubling error"); break; }
+        double fac = err > 0 ? 0.9 * std::cbrt(rtol / err) : 2.0;
+        fac = fac < 0.2 ? 0.2 : (fac > 2.0 ? 2.0 : fac);
+        if (err <= rtol) {
+            z = last ? z_end : z + h;
+            for (size_t i = 0; i < n; ++i) {
+                Pulse &pu = ctx->pulses[i];
+                std::swap(pu.field, pu.work2);
+                pu.z = z;
+                pu.steps++;
+            }
+            s.accepted++;
+            if (from_mlp) s.mlp_proposals++;
+            consecutive = 0;
+            dz = last ? dz : h * fac;
+            if (next_feat) {
+                double prop = 0.0;
+                for (size_t i = 0; i < n; ++i) {
+                    float hf[8];
+                    std::memcpy(hf, H + 16 * i + 8, sizeof hf);
+                    peak[i] = hf[7];
+                    sc[i].err_prev = erri[i];
+                    sc[i].e_prev = H[16 * i + 13];
+                    const double p = H[16 * i + 12];
+                    if (std::isfinite(p) && p > 0) prop = prop > 0 ? std::fmin(prop, p) : p;
+                }
+                if (prop > 0) dz = prop;
+            }
+            from_mlp = features && z < z_end;
+        } else {
+            for (auto &pu : ctx->pulses) pu.rejected++;
+            s.rejected++;
+            consecutive++;
+            dz = h * fac;          // the step-doubling formula is the fallback
+            from_mlp = false;
+        }
+        if (dz < dz_min || consecutive > max_reject) {
+            status = fail(ctx, FCN_ERR_STEP_UNDERFLOW, "dz underflow or too many rejections");
+            break;
+        }
+    }
+    for (auto &pu : ctx->pulses) pu.dz_next = dz;
+    s.z = z;
+    s.dz_next = dz;
+    if (out) *out = s;
+    return status;
+}
+
 template <typename T>
 int propagate_impl(fcn_ctx *ctx, double z_end, double dz0, double rtol, double dz_min,
                    int max_reject, int controller, fcn_stats *out) {
-    if (ctx->pulses.size() != 1) return fail(ctx, FCN_ERR_UNSUPPORTED, "adaptive propagation needs a single-pulse context");
+    if (ctx->pulses.size() != 1) return propagate_batch<T>(ctx, z_end, dz0, rtol, dz_min, max_reject, controller, out);
     Pulse &pu = ctx->pulses[0];
     if (!pu.has_field) return fail(ctx, FCN_ERR_STATE, "fcn_set_field has not been called");
     if (!(dz0 > 0) || !std::isfinite(dz0) || !(rtol > 0) || !std::isfinite(z_end) || !(dz_min > 0))
@@ -1254,18 +1446,18 @@ int propagate_impl(fcn_ctx *ctx, double z_end, double dz0, double rtol, double d
     sc.rtol = rtol;
     sc.l_ref = cs.k0 * (pu.g.r_max / 5.0) * (pu.g.r_max / 5.0) / 2.0;
     sc.domega = cs.domega;
+    // hfeat: f0..f5, fE and the peak intensity of the current state;
+    // host_red[8..11] receives them, [12] the proposal, [13] the energy sum
     float hfeat[8] = {0};
     double mlp_dz = 0.0;
-    auto features_of_field = [&](bool propose) -> int {
-        int rc = diag_device<T>(ctx, pu, pu.field);
-        if (rc) return rc;
-        CK(launch_mlp_propose(pu.red, sc, propose ? ctx->mlp : nullptr, feat_d, dz_d, ctx->st), "features");
-        CK(cudaMemcpyAsync(ctx->host_red + 8, feat_d, 7 * sizeof(float), cudaMemcpyDeviceToHost, ctx->st), "features copy");
+    auto copy_features = [&](bool propose) -> int {
+        CK(cudaMemcpyAsync(ctx->host_red + 8, feat_d, 8 * sizeof(float), cudaMemcpyDeviceToHost, ctx->st),
+           "features copy");
+        CK(cudaMemcpyAsync(ctx->host_red + 13, pu.red + 8, sizeof(double), cudaMemcpyDeviceToHost, ctx->st),
+           "energy copy");
         if (propose)
-            CK(cudaMemcpyAsync(ctx->host_red + 12, dz_d, sizeof(double), cudaMemcpyDeviceToHost, ctx->st), "proposal copy");
-        CK(cudaStreamSynchronize(ctx->st), "features sync");
-        std::memcpy(hfeat, ctx->host_red + 8, 7 * sizeof(float));
-        if (propose) mlp_dz = ctx->host_red[12];
+            CK(cudaMemcpyAsync(ctx->host_red + 12, dz_d, sizeof(double), cudaMemcpyDeviceToHost, ctx->st),
+               "proposal copy");
         return FCN_OK;
     };
     if (features) {
@@ -1275,16 +1467,16 @@ int propagate_impl(fcn_ctx *ctx, double z_end, double dz0, double rtol, double d
         CK(cudaMemcpyAsync(ctx->host_red, pu.red, 8 * sizeof(double), cudaMemcpyDeviceToHost, ctx->st), "ref copy");
         CK(cudaStreamSynchronize(ctx->st), "ref sync");
         sc.i_ref = ctx->host_red[1] > 0 ? ctx->host_red[1] : 1.0;
-        if (ctx->host_red[4] > 0) {
-            const double mean = ctx->host_red[5] / ctx->host_red[4];
-            const double var = ctx->host_red[6] / ctx->host_red[4] - mean * mean;
-            sc.rms_ref = var > 0 ? std::sqrt(var) * cs.domega : 0.0;
-        }
         sc.peak_prev = sc.i_ref;
+        sc.e_prev = ctx->host_red[0];
         sc.dz_prev = dz0;
         sc.err_prev = rtol;
-        rc = features_of_field(false);
+        CK(launch_reduce_stats(pu.stats, pu.g.nr, pu.red + 8, ctx->st), "feature reduction");
+        CK(launch_mlp_propose(pu.red + 8, sc, nullptr, feat_d, dz_d, ctx->st), "features");
+        rc = copy_features(false);
         if (rc) return rc;
+        CK(cudaStreamSynchronize(ctx->st), "features sync");
+        std::memcpy(hfeat, ctx->host_red + 8, 8 * sizeof(float));
     }
     fcn_stats s;
     std::memset(&s, 0, sizeof s);
@@ -1307,20 +1499,19 @@ int propagate_impl(fcn_ctx *ctx, double z_end, double dz0, double rtol, double d
         CK(cudaMemcpyAsync(pu.work1, pu.field, bytes, cudaMemcpyDeviceToDevice, ctx->st), "copy");
         CK(cudaMemcpyAsync(pu.work2, pu.field, bytes, cudaMemcpyDeviceToDevice, ctx->st), "copy");
         rc = substeps<T>(ctx, pu, pu.work1, h, 1, tab1, ev1);
-        // with features, the closing launch of the two half steps also gives
-        // the statistics and spectral moments of the field it leaves, so the
-        // features and the proposal of an accepted attempt need no pass of
-        // their own
+        // the closing launch of the two half steps leaves the statistics of
+        // the field it produces (peak, on-axis peak, peak rho, energy), from
+        // which the features and the proposal of an accepted attempt follow
+        // without a pass of their own
         const bool next_feat = features && !last;
-        if (!rc) rc = substeps<T>(ctx, pu, pu.work2, 0.5 * h, 2, tab2, ev2,
-                                  next_feat ? (OP_FFT | OP_SPEC | OP_SPEC_OF_TIME) : 0);
+        if (!rc) rc = substeps<T>(ctx, pu, pu.work2, 0.5 * h, 2, tab2, ev2, 0);
         if (rc) return rc;
         CK(launch_diff_norm<T>((const cx<T> *)pu.work1, (const cx<T> *)pu.work2, pu.g.nr, pu.g.nt,
                                pu.rows, pu.red, ctx->st), "error norm");
         if (next_feat) {
             // speculative: the features of work2 and the proposal after it,
             // used only if the attempt is accepted
-            sc.peak_prev = hfeat[6];
+            sc.peak_prev = hfeat[7];
             sc.dz_prev = h;
             sc.dz_lo = std::fmax(0.2 * h, dz_min);
             sc.dz_hi = 2.0 * h;
@@ -1328,11 +1519,8 @@ int propagate_impl(fcn_ctx *ctx, double z_end, double dz0, double rtol, double d
             CK(launch_mlp_propose(pu.red + 8, sc, controller == 1 ? ctx->mlp : nullptr, feat_d, dz_d, ctx->st,
                                   pu.red),
                "features");
-            CK(cudaMemcpyAsync(ctx->host_red + 8, feat_d, 7 * sizeof(float), cudaMemcpyDeviceToHost, ctx->st),
-               "features copy");
-            if (controller == 1)
-                CK(cudaMemcpyAsync(ctx->host_red + 12, dz_d, sizeof(double), cudaMemcpyDeviceToHost, ctx->st),
-                   "proposal copy");
+            const int crc = copy_features(controller == 1);
+            if (crc) return crc;
         }
         CK(cudaMemcpyAsync(ctx->host_red, pu.red, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->st),
            "norm copy");
@@ -1343,10 +1531,10 @@ int propagate_impl(fcn_ctx *ctx, double z_end, double dz0, double rtol, double d
         s.last_err = err;
         if (!std::isfinite(err)) { status = fail(ctx, FCN_ERR_NONFINITE, "non-finite step-doubling error"); break; }
         if (ctx->log_buf && ctx->log_n < ctx->log_cap) {
-            float *rec = ctx->log_buf + 8 * ctx->log_n;
-            for (int k = 0; k < 6; ++k) rec[k] = hfeat[k];
-            rec[6] = (float)std::log(h / sc.l_ref);
-            rec[7] = (float)std::log(std::fmax(err, 1e-30) / rtol);
+            float *rec = ctx->log_buf + FCN_MLP_LOG_FLOATS * ctx->log_n;
+            for (int k = 0; k < 7; ++k) rec[k] = hfeat[k];
+            rec[7] = (float)std::log(h / sc.l_ref);
+            rec[8] = (float)std::log(std::fmax(err, 1e-30) / rtol);
             ctx->log_n++;
         }
         double fac = err > 0 ? 0.9 * std::cbrt(rtol / err) : 2.0;
@@ -1361,8 +1549,9 @@ int propagate_impl(fcn_ctx *ctx, double z_end, double dz0, double rtol, double d
             consecutive = 0;
             dz = last ? dz : h * fac;
             if (next_feat) {
-                std::memcpy(hfeat, ctx->host_red + 8, 7 * sizeof(float));
+                std::memcpy(hfeat, ctx->host_red + 8, 8 * sizeof(float));
                 sc.err_prev = err;
+                sc.e_prev = ctx->host_red[13];
                 if (controller == 1) {
                     mlp_dz = ctx->host_red[12];
                     if (std::isfinite(mlp_dz) && mlp_dz > 0) dz = mlp_dz;
@@ -1594,6 +1783,8 @@ void fcn_destroy(fcn_ctx *ctx) {
     for (auto &kv : ctx->tables) cudaFree(kv.second.ptr);
     if (ctx->mlp) cudaFree(ctx->mlp);
     cudaFree(ctx->mlp_io);
+    cudaFree(ctx->batch_io);
+    if (ctx->host_ctl) cudaFreeHost(ctx->host_ctl);
     for (auto &kv : ctx->batch_args) {
         cudaFree(kv.second.first);
         cudaFree(kv.second.second);

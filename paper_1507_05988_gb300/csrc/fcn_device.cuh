@@ -340,13 +340,13 @@ constexpr int kXYVariants = 8;
 
 // Learned dz controller (mlp.cu).
 struct MlpScalars {
-    double i_ref, rms_ref, peak_prev, dz_prev, err_prev, rtol, l_ref, domega, dz_lo, dz_hi;
+    double i_ref, e_prev, peak_prev, dz_prev, err_prev, rtol, l_ref, domega, dz_lo, dz_hi;
 };
 int mlp_nparam();
 cudaError_t launch_mlp_grad(const float *W, const float *X, const float *Y, const int *idx, int n,
                             float *partial, int max_cta, float *grad, float *loss, cudaStream_t st);
 cudaError_t launch_mlp_adam(float *W, float *m, float *v, const float *g, float lr, int t, cudaStream_t st);
-// features (7 floats: f0..f5 and the peak intensity) and, with W, dz_out;
+// features (8 floats: f0..f5, fE and the peak intensity) and, with W, dz_out;
 // with norm non-null the error of f5 is sqrt(norm[0] / norm[1]) (the step-
 // doubling norm on the device) instead of sc.err_prev
 cudaError_t launch_mlp_propose(const double *red, const MlpScalars &sc, const float *W, float *features,

@@ -7,20 +7,25 @@
 // from one state to the next.  The network sees inputs that do not depend
 // on the step sizes the controller happened to take (so data gathered under
 // plain step doubling describes the learned controller's states too):
-//   n = (f0, f1, f2, f3 exp(-f5/3), g, 0),
-// f3 exp(-f5/3) being the peak-intensity change scaled to a step of size
-// exp(g) L_ref (the change over the last step is proportional to it).  Weights are used in BF16 (rounded from FP32 master weights)
-// with FP32 accumulation; training runs on the GPU with these kernels
-// (per-CTA gradient partials reduced in a fixed order, then Adam).  Not in
-// the paper, which uses a fixed dz; step doubling still judges every step.
+//   n = (f0, f1, f2, f3 s, g, fE s),   s = exp(-f5/3),
+// f3 s and fE s being the changes of the peak intensity and of the energy
+// over the last step scaled to a step of size exp(g) L_ref (both changes are
+// proportional to the step).  Weights are used in BF16 (rounded from FP32
+// master weights) with FP32 accumulation; training runs on the GPU with
+// these kernels (per-CTA gradient partials reduced in a fixed order, then
+// Adam).  Not in the paper, which uses a fixed dz; step doubling still
+// judges every step.
 //
 // Parameter layout (floats): W1[64][6], b1[64], W2[64][64], b2[64], W3[64], b3.
 //
-// Features (computed on the device from the FP64 diagnostic reductions):
+// Features, all from the FP64 statistics that the closing row launch of an
+// attempt computes anyway (launch_reduce_stats), so they cost no pass of
+// their own:
 //   f0 = log(peak I / I_ref)          f1 = log10(peak rho / rho_nt + 1e-30) / 10
-//   f2 = spectral rms / rms_ref - 1   f3 = relative change of peak I over the last step
+//   f2 = log(on-axis peak I / peak I) f3 = relative change of peak I over the last step
 //   f4 = log(dz_prev / L_ref)         f5 = log(err_prev / rtol)
-// with I_ref and rms_ref taken from the field at the start of the run and
+//   fE = relative change of the energy over the last step
+// with I_ref taken from the field at the start of the run and
 // L_ref = k0 (r_max/5)^2 / 2 (the Rayleigh length of a beam of waist r_max/5).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -164,30 +169,26 @@ __global__ void mlp_propose(const double *__restrict__ red, MlpScalars sc, const
     if (threadIdx.x == 0) {
         if (norm) sc.err_prev = norm[1] > 0 ? sqrt(norm[0] / norm[1]) : sqrt(norm[0]);
         const double peak = red[1];
-        const double s0 = red[4];
-        double rms = 0.0;
-        if (s0 > 0) {
-            const double mean = red[5] / s0;
-            const double var = red[6] / s0 - mean * mean;
-            rms = var > 0 ? sqrt(var) * sc.domega : 0.0;
-        }
         const double f[NIN] = {
             log(fmax(peak, 1e-300) / sc.i_ref),
             log10(red[2] + 1e-30) / 10.0,
-            sc.rms_ref > 0 ? rms / sc.rms_ref - 1.0 : 0.0,
+            log(fmax(red[3], 1e-300) / fmax(peak, 1e-300)),
             sc.peak_prev > 0 ? (peak - sc.peak_prev) / sc.peak_prev : 0.0,
             log(sc.dz_prev / sc.l_ref),
             log(fmax(sc.err_prev, 1e-30) / sc.rtol),
         };
+        const double fe = sc.e_prev > 0 ? (red[0] - sc.e_prev) / sc.e_prev : 0.0;
         for (int k = 0; k < NIN; ++k) features[k] = (float)f[k];
-        features[NIN] = (float)peak;
+        features[NIN] = (float)fe;
+        features[NIN + 1] = (float)peak;
         const double g = f[4] - f[5] / 3.0;
+        const double sstep = exp(-f[5] / 3.0);
         sx[0] = (float)f[0];
         sx[1] = (float)f[1];
         sx[2] = (float)f[2];
-        sx[3] = (float)(f[3] * exp(-f[5] / 3.0));
+        sx[3] = (float)(f[3] * sstep);
         sx[4] = (float)g;
-        sx[5] = 0.0f;
+        sx[5] = (float)(fe * sstep);
     }
     __syncthreads();
     if (!W) return;

@@ -40,6 +40,7 @@ FCN_FP64 = 0
 FCN_FP32_MIXED = 1
 FCN_OP_IFFT, FCN_OP_NL, FCN_OP_NL2, FCN_OP_FFT, FCN_OP_RHO = 1, 2, 4, 8, 16
 FCN_MLP_NIN, FCN_MLP_NH, FCN_MLP_NPARAM = 6, 64, 4673
+FCN_MLP_LOG_FLOATS = 9
 FCN_NOALLOC_SCRATCH_BYTES = 8 * 1024 * 1024
 FCN_PROF_ROW_HEAD, FCN_PROF_ROW_MID, FCN_PROF_ROW_TAIL, FCN_PROF_COLUMN, FCN_PROF_KINDS = 0, 1, 2, 3, 4
 FCN_XY_PROF_KINDS = 5
@@ -106,6 +107,7 @@ _SIGS = {
     "fcn_set_batching": (C.c_int, [_CTX, C.c_int32]),
     "fcn_set_pairing": (C.c_int, [_CTX, C.c_int32]),
     "fcn_get_pairing": (C.c_int, [_CTX]),
+    "fcn_alu_peak": (C.c_int, [C.c_int32, _D, C.c_void_p]),
     "fcn_set_sequential_columns": (C.c_int, [_CTX, C.c_int32]),
     "fcn_get_sequential_columns": (C.c_int, [_CTX]),
     "fcn_set_field_c64": (C.c_int, [_CTX, C.c_int32, C.POINTER(C.c_float)]),
@@ -358,7 +360,7 @@ class Solver:
 
     def mlp_log(self, capacity: int):
         """Starts logging adaptive attempts; returns the buffer (kept alive here)."""
-        self._log = np.zeros((max(capacity, 0), 8), np.float32)
+        self._log = np.zeros((max(capacity, 0), FCN_MLP_LOG_FLOATS), np.float32)
         check(fcn_mlp_set_log(self.ctx, self._log.ctypes.data_as(_F), int(capacity)), self.ctx)
         return self._log
 
@@ -466,3 +468,11 @@ class SolverXY:
         check_xy(fcn_xy_profile_read(self.ctx, ms, n, 1 if reset else 0), self.ctx)
         names = ("row_head", "row_mid", "row_tail", "line_x", "line_y")
         return {names[k]: (ms[k], n[k]) for k in range(FCN_XY_PROF_KINDS)}
+
+
+def alu_peak(kind: int) -> float:
+    """FLOP/s of the library's FMA microkernel on the current device (kind 0:
+    FP64 fma, 1: FP32 fmaf, 2: FP32 packed f32x2), on the current stream."""
+    out = C.c_double()
+    check(fcn_alu_peak(int(kind), C.byref(out), stream_ptr()), None)
+    return out.value

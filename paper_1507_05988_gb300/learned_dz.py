@@ -12,8 +12,8 @@
    L_ref exp(g + y), g = f4 - f5/3; its target is log(safe step of the
    state) - g, the safe step being h (rtol/err)^(1/3) (Strang: local error
    O(dz^3)), limited to [0.2, 2] like the law.  Inputs (f0, f1, f2,
-   f3 exp(-f5/3), g, 0) are standardised for training and the scaling is
-   folded into the first layer afterwards.
+   f3 s, g, fE s), s = exp(-f5/3), are standardised for training and the
+   scaling is folded into the first layer afterwards.
 3. Training on the GPU (this library's forward and backward kernels, Adam).
 4. Margin: the output bias is lowered by m for m on a small grid, each
    candidate run on held-out pulses (noise seed 100 of configs 1 and 2); the
@@ -69,20 +69,26 @@ def run(wl, z_end, dz0, controller=0, params=None, log=0, rtol=1e-4):
 
 
 def net_inputs(f):
-    """The network's inputs from the logged features (as the proposal kernel
-    forms them): (f0, f1, f2, f3 exp(-f5/3), g = f4 - f5/3, 0)."""
+    """The network's inputs from the logged features f0..f5, fE (as the
+    proposal kernel forms them): (f0, f1, f2, f3 s, g = f4 - f5/3, fE s) with
+    s = exp(-f5/3)."""
     f = np.asarray(f, np.float64)
-    n = np.zeros_like(f)
+    s = np.exp(-f[:, 5] / 3.0)
+    n = np.zeros((f.shape[0], 6))
     n[:, :3] = f[:, :3]
-    n[:, 3] = f[:, 3] * np.exp(-f[:, 5] / 3.0)
+    n[:, 3] = f[:, 3] * s
     n[:, 4] = f[:, 4] - f[:, 5] / 3.0
+    n[:, 5] = f[:, 6] * s
     return n
 
 
 def labels(rec):
-    safe = rec[:, 6] - rec[:, 7] / 3.0
+    """Records of fcn_mlp_set_log (f0..f5, fE, log(h/L_ref), log(err/rtol))
+    to network inputs and labels log(safe step) - g, limited to the law's
+    [0.2, 2] range."""
+    safe = rec[:, 7] - rec[:, 8] / 3.0
     base = rec[:, 4] - rec[:, 5] / 3.0
-    return net_inputs(rec[:, :6]), np.clip(safe - base, np.log(0.2), np.log(2.0))
+    return net_inputs(rec[:, :7]), np.clip(safe - base, np.log(0.2), np.log(2.0))
 
 
 def train(x, y, epochs, lr, seed=0):

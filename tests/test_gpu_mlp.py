@@ -61,10 +61,10 @@ def training_set(rec, margin=0.95):
     to the previous accepted attempt) so the label of y is log(safe step) -
     (f4 - f5/3), with a margin, limited to the [0.2, 2] range of the law."""
     from paper_1507_05988_gb300.learned_dz import net_inputs
-    safe = rec[:, 6] - rec[:, 7] / 3.0
+    safe = rec[:, 7] - rec[:, 8] / 3.0
     base = rec[:, 4] - rec[:, 5] / 3.0
     y = np.clip(safe - base + np.log(margin), np.log(0.2), np.log(2.0))
-    return net_inputs(rec[:, :6]).astype(np.float32), y
+    return net_inputs(rec[:, :7]).astype(np.float32), y
 
 
 def _adaptive(fcn, wl, prec, z_end, dz0, rtol, controller, params=None, log=0):
@@ -87,8 +87,8 @@ def test_learned_dz_controller_end_to_end(fcn):
     from step-doubling runs at noise seeds 1-6, the network (a correction to
     the step-doubling law) trained on the GPU, its margin chosen on seed 7;
     on seed 0 both controllers land on z_end within the tolerance of a
-    fine-step FP64 reference, and the learned one's substeps are compared
-    with plain step doubling."""
+    fine-step FP64 reference, and the learned one needs fewer substeps than
+    plain step doubling."""
     from paper_1507_05988_gb300 import learned_dz as LD
     rtol, z_end, dz0 = 1e-4, 0.3, 2e-3
 
@@ -124,4 +124,6 @@ def test_learned_dz_controller_end_to_end(fcn):
           f"substeps {st0['substeps']}; learned dz (margin {margin}): accepted {st1['accepted']} "
           f"rejected {st1['rejected']} substeps {st1['substeps']} (mlp proposals {st1['mlp_proposals']}); "
           f"substeps saved {100 * gain:.1f} %")
-    assert st1["substeps"] <= 1.05 * st0["substeps"]
+    # the network must gain on the held-out seed: fewer Strang substeps
+    # (accepted and rejected attempts, 3 substeps each) at the same rtol
+    assert st1["substeps"] < st0["substeps"]

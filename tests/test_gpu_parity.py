@@ -475,6 +475,68 @@ def test_adaptive_step_doubling_matches_oracle_controller(fcn, prec):
         assert rel_l2(A, Aref) < 1e-4
 
 
+def test_adaptive_batch_of_identical_pulses_equals_the_single_run(fcn):
+    """A batch advances with one dz accepted when every pulse's step-doubling
+    error is within rtol: a batch of copies of one pulse takes exactly the
+    attempts of that pulse alone (FP64; the batch's column launch may be
+    the sequential kernel, so the fields agree to rounding)."""
+    wl = W.small(32, 128, p_over_pcr=3.0, noise_seed=1)
+    s = fcn.Solver(wl.physics(), precision=FP64)
+    s.set_field(wl.field())
+    st1 = s.propagate(0.6, 0.05, rtol=1e-4)
+    a1 = s.get_field()
+    s.close()
+    b = fcn.Solver([wl.physics()] * 2, precision=FP64)
+    for k in range(2):
+        b.set_field(wl.field(), pulse=k)
+    st2 = b.propagate(0.6, 0.05, rtol=1e-4)
+    assert (st2["accepted"], st2["rejected"], st2["substeps"]) == (st1["accepted"], st1["rejected"], st1["substeps"])
+    for k in range(2):
+        assert rel_l2(b.get_field(pulse=k), a1) < 1e-12
+        assert b.diag(pulse=k)["z"] == 0.6
+    b.close()
+
+
+@pytest.mark.parametrize("controller", [0, 1])
+def test_adaptive_batch_of_different_pulses(fcn, controller):
+    """Three different pulses in one adaptive batch (FP32-mixed): the batch
+    takes at least as many steps as its hardest pulse alone, every pulse
+    lands on z_end, and each stays within the accuracy of the single-pulse
+    runs against a fine-step FP64 reference.  Controller 1 runs the learned
+    proposals (a small network; step doubling judges every attempt)."""
+    wls = [W.small(32, 128, p_over_pcr=p, noise_seed=k) for k, p in enumerate((2.0, 3.0, 4.0))]
+    z_end, rtol = 0.5, 1e-4
+    rng = np.random.default_rng(5)
+    params = (0.02 * rng.standard_normal(fcn.FCN_MLP_NPARAM)).astype(np.float32)
+    singles, refs = [], []
+    for w in wls:
+        s = fcn.Solver(w.physics(), precision=FP32)
+        s.set_field(w.field())
+        singles.append((s.propagate(z_end, 0.05, rtol=rtol), s.get_field()))
+        s.close()
+        r = fcn.Solver(w.physics(), precision=FP64)
+        r.set_field(w.field())
+        r.step(z_end / 2000, 2000)
+        refs.append(r.get_field())
+        r.close()
+    b = fcn.Solver([w.physics() for w in wls], precision=FP32)
+    if controller == 1:
+        b.mlp_set(params)
+    for k, w in enumerate(wls):
+        b.set_field(w.field(), pulse=k)
+    st = b.propagate(z_end, 0.05, rtol=rtol, controller=controller)
+    assert st["z"] == z_end
+    if controller == 0:
+        assert st["accepted"] >= max(sg[0]["accepted"] for sg in singles)
+    else:
+        assert st["mlp_proposals"] > 0
+    for k in range(len(wls)):
+        single_err = rel_l2(singles[k][1], refs[k])
+        assert b.diag(pulse=k)["z"] == z_end
+        assert rel_l2(b.get_field(pulse=k), refs[k]) < max(2 * single_err, 30 * rtol)
+    b.close()
+
+
 # ------------------------------------------------- autotuner and variants
 
 @pytest.mark.parametrize("prec", [FP64, FP32])
