@@ -49,8 +49,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-cfg4", action="store_true")
-    ap.add_argument("--cfg4-steps", type=int, default=20)
+    ap.add_argument("--cfg4-steps", type=int, default=500)
     ap.add_argument("--no-cartesian", action="store_true")
+    ap.add_argument("--no-chosen", action="store_true", help="skip the adaptive chosen-form leg")
+    ap.add_argument("--chosen-z", type=float, default=1.0, help="metres of the chosen-form leg")
     ap.add_argument("--oracle-scaling", action="store_true",
                     help="only run the oracle's thread-scaling table on the paper's grid (CPU)")
     return ap.parse_args()
@@ -279,22 +281,40 @@ def accuracy_leg(fcn, wl, field, dz, make=None, checkpoints=None):
     does, the difference is the problem's conditioning, not the arithmetic.
     make(precision) builds the solver (default: a radial Solver of wl)."""
     import numpy as np
+    per_step = make is None
     if make is None:
         def make(prec):
             return fcn.Solver(wl.physics(), precision=prec)
     rng = np.random.default_rng(12345)
-    pert = field * (1.0 + 6e-8 * rng.uniform(-1.0, 1.0, field.shape))
+    pert = field if per_step else field * (1.0 + 6e-8 * rng.uniform(-1.0, 1.0, field.shape))
     if checkpoints is None:
         checkpoints = [c for c in (100, 200, 300, 400, 500, 750, 1000) if c <= wl.nsteps]
         if wl.nsteps not in checkpoints:
             checkpoints.append(wl.nsteps)
 
-    def run(prec, f0, visit):
+    def run(prec, f0, visit, perturb=False):
+        import torch
         s = make(prec)
         s.set_field(f0)
         done = 0
+        if perturb:
+            # after every step the field is multiplied on the device by
+            # (1 + 6e-8 xi), xi ~ U[-1, 1] drawn per point and step: a
+            # perturbation of FP32 rounding size entering at every step, as
+            # FP32 rounding does
+            gen = torch.Generator(device="cuda")
+            gen.manual_seed(12345)
+            buf = torch.empty(field.shape, dtype=torch.complex128, device="cuda")
         for c in checkpoints:
-            s.step(dz, c - done)
+            if perturb:
+                for _ in range(c - done):
+                    s.step(dz, 1)
+                    s.get_field_device(buf)
+                    xi = torch.rand(field.shape, generator=gen, device="cuda", dtype=torch.float64)
+                    buf.mul_(1.0 + 6e-8 * (2.0 * xi - 1.0))
+                    s.set_field_device(buf)
+            else:
+                s.step(dz, c - done)
             done = c
             visit(c, s.get_field(), s.diag()["energy"])
         s.close()
@@ -302,18 +322,92 @@ def accuracy_leg(fcn, wl, field, dz, make=None, checkpoints=None):
     ref = {}
     run(fcn.FCN_FP64, field, lambda c, a, e: ref.__setitem__(c, (a, e)))
     table = {c: {"steps": c} for c in checkpoints}
-    for name, prec, f0 in (("fp32", fcn.FCN_FP32_MIXED, field), ("fp64_perturbed", fcn.FCN_FP64, pert)):
+    for name, prec, f0, pt in (("fp32", fcn.FCN_FP32_MIXED, field, False),
+                               ("fp64_perturbed", fcn.FCN_FP64, pert, per_step)):
         def visit(c, a, e, name=name):
             table[c][name + "_field_rel_l2"] = rel_l2(a, ref[c][0])
             table[c][name + "_energy_rel"] = abs(e / ref[c][1] - 1)
-        run(prec, f0, visit)
+        run(prec, f0, visit, perturb=pt)
+    for c in checkpoints:
+        ref_d = table[c]["fp64_perturbed_field_rel_l2"]
+        table[c]["fp32_over_reference"] = table[c]["fp32_field_rel_l2"] / ref_d if ref_d > 0 else None
     table = [table[c] for c in checkpoints]
     last = table[-1]
     return {"field_rel_l2": last["fp32_field_rel_l2"], "energy_rel": last["fp32_energy_rel"],
             "run": f"{checkpoints[-1]} steps of dz = {dz} m, FP32-mixed vs FP64 GPU path",
             "checkpoints": table,
-            "conditioning": "fp64_perturbed_*: the FP64 path from the field times (1 + 6e-8 xi), "
-                            "xi ~ U[-1, 1], against the unperturbed FP64 path"}
+            "conditioning": ("fp64_perturbed_*: the FP64 path with its field multiplied by "
+                             "(1 + 6e-8 xi), xi ~ U[-1, 1] per point, after every step, against the "
+                             "unperturbed FP64 path" if per_step else
+                             "fp64_perturbed_*: the FP64 path from the field times (1 + 6e-8 xi), "
+                             "xi ~ U[-1, 1], against the unperturbed FP64 path")}
+
+
+def chosen_form_leg(fcn, W, z_len, pulses=8, rtol=1e-4):
+    """The chosen form against the plain FP64 GPU path at the metric's
+    accuracy: config-2 pulses (noise seeds 0..pulses-1) propagated over
+    z_len metres by step doubling at rtol, in
+      - fp32_batched_plain:   FP32-mixed, all pulses in one adaptive batch
+                              (one dz, one launch per stage), the law's dz;
+      - fp32_batched_learned: the same with the learned dz proposals
+                              (weights trained by learned_dz.py with this
+                              library's kernels; skipped if the file is absent);
+      - fp32_single_plain:    FP32-mixed, pulse 0 alone;
+      - fp64_single_plain:    the plain FP64 GPU path, pulse 0 alone.
+    Throughput counts accepted steps: pulses x Nr x Nt x accepted / wall
+    time (the host loop synchronises every attempt, so wall time is the
+    honest clock); raw counts all Strang substeps.  Pulse 0's final field
+    and energy of every FP32 run are compared with the FP64 run's."""
+    import numpy as np
+    wls = [W.config2(seed=i) for i in range(pulses)]
+    pts = wls[0].points
+    dz0 = 2e-3
+    wpath = os.path.join(ROOT, "paper_1507_05988_gb300", "learned_dz_weights.npy")
+    weights = np.load(wpath) if os.path.exists(wpath) else None
+    fields = [w.field() for w in wls]
+    out = {"workload": f"{pulses} cfg2 pulses 1024x4096 (noise seeds 0..{pulses - 1}), "
+                       f"0 -> {z_len} m, step doubling at rtol {rtol}",
+           "z_m": z_len, "rtol": rtol, "pulses": pulses}
+
+    def run(name, prec, n, controller):
+        s = fcn.Solver([w.physics() for w in wls[:n]] if n > 1 else wls[0].physics(), precision=prec)
+        if controller == 1:
+            s.mlp_set(weights)
+        for i in range(n):
+            s.set_field(fields[i], pulse=i)
+        s.propagate(3 * dz0, dz0, rtol=rtol, controller=controller)   # tuning and first tables
+        for i in range(n):
+            s.set_field(fields[i], pulse=i)
+        t0 = time.perf_counter()
+        st = s.propagate(z_len, dz0, rtol=rtol, controller=controller, max_reject=40)
+        wall = time.perf_counter() - t0
+        a0, e0 = s.get_field(0), s.diag(0)["energy"]
+        s.close()
+        out[name] = {"pulses": n, "wall_s": wall, "accepted": st["accepted"], "rejected": st["rejected"],
+                     "substeps": st["substeps"], "mlp_proposals": st["mlp_proposals"],
+                     "accepted_point_steps_per_s": n * pts * st["accepted"] / wall,
+                     "raw_point_steps_per_s": n * pts * st["substeps"] / wall}
+        return a0, e0
+
+    res = {}
+    res["fp64_single_plain"] = run("fp64_single_plain", fcn.FCN_FP64, 1, 0)
+    res["fp32_single_plain"] = run("fp32_single_plain", fcn.FCN_FP32_MIXED, 1, 0)
+    res["fp32_batched_plain"] = run("fp32_batched_plain", fcn.FCN_FP32_MIXED, pulses, 0)
+    if weights is not None:
+        res["fp32_batched_learned"] = run("fp32_batched_learned", fcn.FCN_FP32_MIXED, pulses, 1)
+    else:
+        out["fp32_batched_learned"] = {"skipped": "no trained weights (learned_dz.py --save)"}
+    a64, e64 = res["fp64_single_plain"]
+    v64 = out["fp64_single_plain"]["accepted_point_steps_per_s"]
+    for name, (a, e) in res.items():
+        if name == "fp64_single_plain":
+            continue
+        out[name]["pulse0_field_rel_l2_vs_fp64"] = rel_l2(a, a64)
+        out[name]["pulse0_energy_rel_vs_fp64"] = abs(e / e64 - 1)
+        out[name]["speedup_over_fp64"] = out[name]["accepted_point_steps_per_s"] / v64
+    best = "fp32_batched_learned" if weights is not None else "fp32_batched_plain"
+    out["chosen"] = best
+    return out
 
 
 def cartesian_leg(fcn, W, pg, world, accuracy=True, cpu=True):
@@ -557,6 +651,12 @@ def run_ours(args):
     v64 = weak_scaling_value(world, B * pts, K64, reduce_max(a.elapsed_time(b), pg, "cuda"))
     s64.close()
 
+    # ---- the chosen form (FP32 + learned dz + batched, adaptive) against the
+    # plain FP64 path at the metric's rtol ----
+    chosen = None
+    if rank == 0 and not args.no_chosen:
+        chosen = chosen_form_leg(fcn, W, args.chosen_z)
+
     # ---- accuracy of the chosen form against the FP64 path, full 1000-step run ----
     acc = None
     if rank == 0 and not args.no_accuracy:
@@ -594,6 +694,7 @@ def run_ours(args):
             "fp64_gpu": {"value": v64, "unit": UNIT, "steps": K64,
                          "speedup_of_chosen_form": value / v64},
             "accuracy_vs_fp64": acc,
+            "chosen_form": chosen,
             "clocks": clk,
             "e2e": e2e,
             "cpu_baseline": cpu,

@@ -218,7 +218,10 @@ int fcn_get_state(fcn_ctx *ctx, int32_t pulse, double state[4]);
 int fcn_set_state(fcn_ctx *ctx, int32_t pulse, const double state[4]);
 
 /* ======================= kernel variants (autotuner) ======================= */
-/* The row stage has 3 occupancy variants (FP32, K = 8) and the column stage 9:
+/* The row stage has 4 variants (FP32, K = 8): 0-2 one CTA per row (group)
+ * with the compiler's register allocation, or 3 or 4 CTAs per SM; 3 a
+ * persistent kernel that prefetches each CTA's next rows into shared memory
+ * by bulk copies (Nt >= 512).  The column stage has 9:
  *   0-3  chunked affine-map scans of the two Thomas sweeps, chunks in
  *        registers (chunk length x CTA size);
  *   4-7  the same with chunks staged in shared memory (cp.async) or fed to
@@ -229,7 +232,7 @@ int fcn_set_state(fcn_ctx *ctx, int32_t pulse, const double state[4]);
  * By default (-1) the first fcn_step of a grid times every variant on a
  * scratch copy of the field and keeps the fastest per (precision, Nr, Nt)
  * for the process; if the environment variable FCN_TUNE_CACHE names a file,
- * choices are read from and appended to it.  row_variant in -1..2 and
+ * choices are read from and appended to it.  row_variant in -1..3 and
  * col_variant in -1..8 force a variant (-1: tune).  Every variant computes
  * the same step up to rounding.  Drops the context's captured graphs.
  * Synchronises. */

@@ -157,6 +157,37 @@ __global__ void cn_table_kernel_f32(TableArgs a, cx<float> *table) {
     }
 }
 
+// Coefficients of row j in the form rhs_j = d x_j + i (sl x_{j-1} + sh x_{j+1}
+// - cd x_j), alpha_j = i sl / piv_j, gamma_j = i sh / piv_j: from the CnCoef
+// rows when the launch has them (context tables), else from s and the ratio
+// tables (stateless operations).
+template <typename T>
+struct RowCo {
+    T sl, sh, d, cd;
+};
+template <typename T>
+__device__ __forceinline__ RowCo<T> row_co(const ColArgs<T> &a, int j, T delta) {
+    RowCo<T> r;
+    const int nr = a.nr;
+    if (a.coef) {
+        CnCoef<T> cf;
+        if (j < nr - 1) {
+            cf = a.coef[FCN_IDX(j, nr, 35)];
+        } else {
+            cf.sl = T(0); cf.sh = T(0); cf.c0 = T(0); cf.d = T(0);
+        }
+        r.sl = cf.sl; r.sh = cf.sh; r.d = cf.d; r.cd = cf.d * (cf.c0 - delta);
+    } else if (j == 0) {
+        r.sl = T(0); r.sh = T(4) * a.s; r.d = T(1); r.cd = T(4) * a.s - delta;
+    } else if (j < nr - 1) {
+        r.sl = a.s * a.lo[FCN_IDX(j, nr, 35)]; r.sh = a.s * a.hi[FCN_IDX(j, nr, 36)];
+        r.d = T(1); r.cd = T(2) * a.s - delta;
+    } else {
+        r.sl = T(0); r.sh = T(0); r.d = T(0); r.cd = T(0);
+    }
+    return r;
+}
+
 // One CTA solves columns [g C, g C + C) of one pulse; blockDim.x >= C P
 // (P = chunks per column), threads beyond C P hold empty chunks.  Every
 // thread of the CTA must call it (barriers inside).
@@ -175,11 +206,7 @@ __device__ __forceinline__ void cn_body(const ColArgs<T> &a, int C, int g, unsig
     const int nq = a.tp;
     const int qq = (q <= nt / 2) ? q : nt - q;
     const T delta = a.dk * T(qq) * T(qq);
-    const T s = a.s;
-    const T g0 = T(4) * s - delta;   // row 0: e = 1 - i g0
-    const T g1 = T(2) * s - delta;   // rows 1..Nr-2
     const int j0 = chunk * L;
-    cx<T> *colp = a.field + q;
 
     cx<T> x[L + 2];
 #pragma unroll
@@ -201,22 +228,11 @@ __device__ __forceinline__ void cn_body(const ColArgs<T> &a, int C, int g, unsig
     for (int k = 0; k < L; ++k) {
         const int j = j0 + k;
         if (j < nr) {
-            cx<T> rhs, alpha;
-            if (j == 0) {
-                const cx<T> w = mk(T(4) * s * x[k + 2].x - g0 * x[k + 1].x,
-                                   T(4) * s * x[k + 2].y - g0 * x[k + 1].y);
-                rhs = mk(x[k + 1].x - w.y, x[k + 1].y + w.x);
-                alpha = czero<T>();
-            } else if (j < nr - 1) {
-                const T sl = s * a.lo[FCN_IDX(j, nr, 35)], sh = s * a.hi[FCN_IDX(j, nr, 36)];
-                const cx<T> w = mk(sl * x[k].x + sh * x[k + 2].x - g1 * x[k + 1].x,
-                                   sl * x[k].y + sh * x[k + 2].y - g1 * x[k + 1].y);
-                rhs = mk(x[k + 1].x - w.y, x[k + 1].y + w.x);
-                alpha = cmul_i(inv[k], sl);
-            } else {
-                rhs = czero<T>();
-                alpha = czero<T>();
-            }
+            const RowCo<T> c = row_co(a, j, delta);
+            const cx<T> w = mk(c.sl * x[k].x + c.sh * x[k + 2].x - c.cd * x[k + 1].x,
+                               c.sl * x[k].y + c.sh * x[k + 2].y - c.cd * x[k + 1].y);
+            const cx<T> rhs = mk(c.d * x[k + 1].x - w.y, c.d * x[k + 1].y + w.x);
+            const cx<T> alpha = cmul_i(inv[k], c.sl);
             y[k] = cmul(rhs, inv[k]);
             PB = cmul(alpha, PB) + y[k];
             PA = cmul(alpha, PA);
@@ -231,7 +247,7 @@ __device__ __forceinline__ void cn_body(const ColArgs<T> &a, int C, int g, unsig
         for (int k = 0; k < L; ++k) {
             const int j = j0 + k;
             if (j < nr) {
-                const cx<T> alpha = (j >= 1 && j < nr - 1) ? cmul_i(inv[k], s * a.lo[j]) : czero<T>();
+                const cx<T> alpha = cmul_i(inv[k], row_co(a, j, delta).sl);
                 y[k] = cmul(alpha, yp) + y[k];
                 yp = y[k];
             }
@@ -243,8 +259,7 @@ __device__ __forceinline__ void cn_body(const ColArgs<T> &a, int C, int g, unsig
     for (int k = L - 1; k >= 0; --k) {
         const int j = j0 + k;
         if (j < nr) {
-            const cx<T> gamma = (j == 0) ? cmul_i(inv[k], T(4) * s)
-                              : (j < nr - 1) ? cmul_i(inv[k], s * a.hi[j]) : czero<T>();
+            const cx<T> gamma = cmul_i(inv[k], row_co(a, j, delta).sh);
             QB = cmul(gamma, QB) + y[k];
             QA = cmul(gamma, QA);
         }
@@ -257,8 +272,7 @@ __device__ __forceinline__ void cn_body(const ColArgs<T> &a, int C, int g, unsig
         for (int k = L - 1; k >= 0; --k) {
             const int j = j0 + k;
             if (j < nr) {
-                const cx<T> gamma = (j == 0) ? cmul_i(inv[k], T(4) * s)
-                                  : (j < nr - 1) ? cmul_i(inv[k], s * a.hi[j]) : czero<T>();
+                const cx<T> gamma = cmul_i(inv[k], row_co(a, j, delta).sh);
                 xn = cmul(gamma, xn) + y[k];
                 a.field[FCN_IDX((size_t)j * nt + q, (size_t)nr * nt, 37)] = disp_apply(xn, ph);
             }
@@ -530,12 +544,12 @@ __global__ void cn_coef_kernel(TableArgs a, CnCoef<T> *coef) {
     if (j >= a.nr) return;
     const T s = T(a.s);
     CnCoef<T> c;
-    if (j == 0) {
-        c.sl = T(0); c.sh = T(4) * s; c.c0 = T(4) * s; c.d = T(1);
-    } else if (j < a.nr - 1) {
-        c.sl = s * T(a.lo[j]); c.sh = s * T(a.hi[j]); c.c0 = T(2) * s; c.d = T(1);
-    } else {
+    if (j >= a.nr - 1) {
         c.sl = T(0); c.sh = T(0); c.c0 = T(0); c.d = T(0);
+    } else if (j == 0) {
+        c.sl = T(0); c.sh = T(4) * s; c.c0 = T(4) * s; c.d = T(1);
+    } else {
+        c.sl = s * T(a.lo[j]); c.sh = s * T(a.hi[j]); c.c0 = T(2) * s; c.d = T(1);
     }
     coef[j] = c;
 }

@@ -242,6 +242,10 @@ cn_seq_kernel(const __grid_constant__ SeqParams<T> p) {
                 x0[k] = xp;
             }
         }
+        // stage s is consumed: refill it now, so that issuing the copies
+        // overlaps the recurrences below
+        __syncwarp();
+        if (lane == 0 && issued < nb && issued == t + S) issue(issued++);
 #pragma unroll
         for (int r = 0; r < R; ++r) {
 #pragma unroll
@@ -250,9 +254,6 @@ cn_seq_kernel(const __grid_constant__ SeqParams<T> p) {
                 if (r < rows) col[k][(size_t)(jb + r) * nt] = y[k];
             }
         }
-        __syncwarp();
-        if (lane == 0 && issued < nb && issued == t + S) issue(issued++);
-        __syncwarp();
     }
     // y must reach the async proxy before the backward boxes read it back
     asm volatile("fence.proxy.async.global;" ::: "memory");
@@ -273,23 +274,26 @@ cn_seq_kernel(const __grid_constant__ SeqParams<T> p) {
         const CnCoef<T> *Cf = stage_c(s);
         const int jb = R * block_of(t);
         const int rows = min(R, nr - jb);
-        cx<T> ga[R];
+        cx<T> ga[R], yv[NP][R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) ga[r] = cmul_i(I[r * 34 + il], Cf[r].sh);
+        for (int r = 0; r < R; ++r) {
+            ga[r] = cmul_i(I[r * 34 + il], Cf[r].sh);
+#pragma unroll
+            for (int k = 0; k < NP; ++k) yv[k][r] = stage_x(s, k)[r * 32 + lane];
+        }
+        __syncwarp();
+        if (lane == 0 && issued < ntask && issued == t + S) issue(issued++);
 #pragma unroll
         for (int r = R - 1; r >= 0; --r) {
 #pragma unroll
             for (int k = 0; k < NP; ++k) {
-                const cx<T> xv = cmul(ga[r], xn[k]) + stage_x(s, k)[r * 32 + lane];
+                const cx<T> xv = cmul(ga[r], xn[k]) + yv[k][r];
                 if (r < rows) {                        // rows past nr keep x = 0
                     xn[k] = xv;
                     col[k][(size_t)(jb + r) * nt] = disp_apply(xv, ph);
                 }
             }
         }
-        __syncwarp();
-        if (lane == 0 && issued < ntask && issued == t + S) issue(issued++);
-        __syncwarp();
     }
 }
 

@@ -486,9 +486,9 @@ int ensure_table(fcn_ctx *ctx, Pulse &pu, double dz, const cx<T> **out, int side
         CK(cudaEventRecord(ctx->tbefore[side], ctx->st), "table event");
         CK(cudaStreamWaitEvent(bs, ctx->tbefore[side], 0), "table wait");
     }
+    CnCoef<T> *coef = (CnCoef<T> *)((char *)d + coef_offset<T>(pu.g.nr, pu.g.nt));
+    CK(launch_cn_coef<T>(ta, coef, bs), "row coefficient kernel");
     CK(launch_cn_table<T>(ta, (cx<T> *)d, bs), "pivot table kernel");
-    CK(launch_cn_coef<T>(ta, (CnCoef<T> *)((char *)d + coef_offset<T>(pu.g.nr, pu.g.nt)), bs),
-       "row coefficient kernel");
     if (side >= 0) {
         CK(cudaEventRecord(ctx->tready[side], bs), "table event");
         if (ready) *ready = ctx->tready[side];
@@ -511,6 +511,7 @@ RowArgs<T> row_args(Pulse &pu, void *field, int ops, double dz) {
     a.ops = ops;
     a.variant = pu.row_var;
     a.nl = nl_coef<T>(pu.g, pu.p, 0.5 * dz);
+    a.err = pu.err;
     return a;
 }
 
@@ -1852,11 +1853,15 @@ int fcn_set_field_device(fcn_ctx *ctx, int32_t pulse, const void *dev) {
 
 // FCN_ERR_CUDA when a kernel of this pulse recorded that a bounded wait gave
 // up (the field is then not valid); synchronises the context stream.
+// (a launch over several pulses records in the first pulse's flag)
 static int check_wait_flag(fcn_ctx *ctx, const Pulse &pu) {
-    int h = 0;
-    CK(cudaMemcpyAsync(&h, pu.err, sizeof(int), cudaMemcpyDeviceToHost, ctx->st), "error flag");
+    int h[2] = {0, 0};
+    CK(cudaMemcpyAsync(&h[0], pu.err, sizeof(int), cudaMemcpyDeviceToHost, ctx->st), "error flag");
+    CK(cudaMemcpyAsync(&h[1], ctx->pulses[0].err, sizeof(int), cudaMemcpyDeviceToHost, ctx->st), "error flag");
     CK(cudaStreamSynchronize(ctx->st), "sync");
-    if (h) return fail(ctx, FCN_ERR_CUDA, "column stage: a bounded wait for a TMA copy gave up");
+    if (h[0] || h[1])
+        return fail(ctx, FCN_ERR_CUDA, (h[0] | h[1]) & 1 ? "column stage: a bounded wait for a TMA copy gave up"
+                                                          : "row stage: a bounded wait for a row copy gave up");
     return FCN_OK;
 }
 

@@ -197,8 +197,11 @@ struct RowArgs {
     int nr;
     int nt;
     int ops;
-    int variant;          // occupancy variant (0..2), chosen by the autotuner
+    int variant;          // 0..2: occupancy variants; 3: persistent, next rows
+                          // prefetched by bulk copies (FP32, K = 8, Nt >= 512);
+                          // chosen by the autotuner
     NLCoef<T> nl;
+    int *err = nullptr;   // set nonzero by a kernel whose bounded wait gave up
 };
 
 // One launch of the row stage over up to kRowMulti pulses that share the
@@ -214,7 +217,7 @@ struct RowMultiArgs {
 };
 
 // Per-row coefficients of the Crank-Nicolson system (Eqs. (Ma)-(Mb)) for one
-// dz, in the form the staged column kernel uses: with delta_q = dk q^2,
+// dz, in the form the column kernels use: with delta_q = dk q^2,
 //   explicit side  w_j = sl x_{j-1} + sh x_{j+1} - d (c0 - delta_q) x_j,
 //                  rhs_j = d x_j + i w_j,
 //   sweep factors  alpha_j = i sl / piv_j,  gamma_j = i sh / piv_j.
@@ -269,7 +272,7 @@ template <typename T>
 cudaError_t prepare_rows(int nt);
 template <typename T>
 cudaError_t launch_cn(const ColArgs<T> &a, cudaStream_t st);
-constexpr int kRowVariants = 3;
+constexpr int kRowVariants = 4;
 constexpr int kColVariants = 9;
 constexpr int kColStagedFirst = 4;      // variants >= this need ColArgs::coef
 constexpr int kColSeq = 8;              // the sequential TMA-fed column kernel (col_seq.cu)

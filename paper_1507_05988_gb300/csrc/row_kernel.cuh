@@ -841,9 +841,18 @@ struct KahanF {
 // One CTA of TH threads processes rows [row_base, row_base + TH/TPR) of one
 // pulse: TH = RowCfg<NT>::THREADS in the per-Nt kernels, 512 in the batched
 // work-list kernel.  Every thread of the CTA must call it (barriers inside).
-template <typename T, int NT, int KT, int TH>
+struct NoHook {
+    __device__ __forceinline__ void operator()() const {}
+};
+
+// One row stage of RPC rows.  PF: the input rows were staged in shared memory
+// (xs: RPC rows of NT values in natural order, row_base's first) and are read
+// from there; hook() runs once every thread has finished reading them (the
+// prefetch of the next rows may then overwrite xs).
+template <typename T, int NT, int KT, int TH, bool PF = false, typename Hook = NoHook>
 __device__ __forceinline__ void row_body(const RowArgs<T> &a, int row_base, int ops,
-                                         unsigned char *smem_raw) {
+                                         unsigned char *smem_raw, const cx<T> *xs = nullptr,
+                                         Hook hook = Hook()) {
     using C = RowCfg<NT>;
     constexpr int E = C::E;
     constexpr int RPC = TH / C::TPR;
@@ -880,21 +889,25 @@ __device__ __forceinline__ void row_body(const RowArgs<T> &a, int row_base, int 
         constexpr int PL = C::NPASS - 1;
         constexpr int RL = PassCfg<NT, PL>::R;
         constexpr int NSL = PassCfg<NT, PL>::NS;
+        const cx<T> *src = PF ? xs + rloc * NT : g;
 #pragma unroll
         for (int i = 0; i < E / RL; ++i) {
             const int j = t + C::TPR * i;
 #pragma unroll
             for (int r = 0; r < RL; ++r)
-                v[i * RL + r] = valid ? g[FCN_IDX(j + r * NSL, NT, 4)] : mk(T(0), T(0));
+                v[i * RL + r] = valid ? src[FCN_IDX(j + r * NSL, NT, 4)] : mk(T(0), T(0));
         }
         InvDispatch<T, NT, PL, (PL < 0)>::run(v, S, t, a.tw, a.nl.inv_nt);
+        hook();
     } else {
+        const cx<T> *src = PF ? xs + rloc * NT : g;
 #pragma unroll
         for (int i = 0; i < E; ++i) {
             const int idx = t + C::TPR * i;
-            S[FCN_IDX(pidx(tpos<NT>(idx), NT), C::PADN, 5)] = valid ? g[FCN_IDX(idx, NT, 6)] : mk(T(0), T(0));
+            S[FCN_IDX(pidx(tpos<NT>(idx), NT), C::PADN, 5)] = valid ? src[FCN_IDX(idx, NT, 6)] : mk(T(0), T(0));
         }
         __syncthreads();
+        hook();
     }
 
     // the time-domain stage runs whenever the row passes through tau space
@@ -1074,6 +1087,90 @@ row_kernel_multi(const __grid_constant__ RowMultiArgs<T> m) {
     row_body<T, NT, KT, RowCfg<NT>::THREADS>(a, blockIdx.x * RowCfg<NT>::RPC, a.ops, smem_raw);
 }
 
+// Persistent row stage with the next rows prefetched: each CTA walks the
+// units (RPC consecutive rows of one pulse) u = blockIdx.x, + gridDim.x, ...
+// of the launch's pulses; while it transforms and steps one unit, one bulk
+// copy (cp.async.bulk, completion on an mbarrier) brings the next unit's
+// rows from HBM into a staging buffer, so no thread waits on a global load
+// when a unit starts.  The wait on the mbarrier is bounded (~1 s): after it
+// the CTA records an error code, waits (bounded) for its copy in flight and
+// returns.
+constexpr long long kRowWaitCycles = 1ll << 31;
+
+__device__ __forceinline__ bool row_mbar_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok = 0;
+    const long long t0 = clock64();
+    for (;;) {
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (clock64() - t0 > kRowWaitCycles) return false;
+    }
+}
+
+// Byte offset of the staging buffer: after the rows, the FP64 scratch and
+// (launches with rho or statistics) the u rows, 128-byte aligned.
+template <typename T, int NT>
+__host__ __device__ constexpr size_t pf_stage_offset(bool with_u) {
+    using C = RowCfg<NT>;
+    return ((sizeof(cx<T>) + (with_u ? sizeof(T) : 0)) * C::RPC * C::PADN + sizeof(double) * kRowScratch +
+            127) / 128 * 128;
+}
+
+template <typename T, int NT, int KT, int MB>
+__global__ void __launch_bounds__(RowCfg<NT>::THREADS, MB)
+row_kernel_pf(const __grid_constant__ RowMultiArgs<T> m, int npulse, int *err) {
+    using C = RowCfg<NT>;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    pdl_enter();
+    const RowArgs<T> &a0 = m.a;
+    const int upp = (a0.nr + C::RPC - 1) / C::RPC;      // units per pulse
+    const int units = upp * npulse;
+    if ((int)blockIdx.x >= units) return;
+    const bool with_u = (a0.ops & (OP_RHO | OP_STATS)) != 0;
+    cx<T> *xs = reinterpret_cast<cx<T> *>(smem_raw + pf_stage_offset<T, NT>(with_u));
+    const uint32_t bar = (uint32_t)__cvta_generic_to_shared(xs + C::RPC * NT);
+    auto issue = [&](int u) {                           // thread 0 only
+        const int pulse = u / upp, row0 = (u - pulse * upp) * C::RPC;
+        const int rows = min(C::RPC, a0.nr - row0);
+        const uint32_t bytes = (uint32_t)(rows * NT * sizeof(cx<T>));
+        const cx<T> *src = m.field[pulse] + (size_t)row0 * NT;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+            ::"r"((uint32_t)__cvta_generic_to_shared(xs)), "l"(src), "r"(bytes), "r"(bar)
+            : "memory");
+    };
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        issue(blockIdx.x);
+    }
+    __syncthreads();
+    uint32_t parity = 0;
+    for (int u = blockIdx.x; u < units; u += gridDim.x, parity ^= 1u) {
+        if (!row_mbar_wait(bar, parity)) {
+            if (threadIdx.x == 0 && err) atomicExch(err, 2);
+            row_mbar_wait(bar, parity);                 // the copy in flight, bounded
+            return;
+        }
+        const int pulse = u / upp, row0 = (u - pulse * upp) * C::RPC;
+        RowArgs<T> a = a0;
+        a.field = m.field[pulse];
+        a.rho = m.rho[pulse];
+        a.stats = m.stats[pulse];
+        const int next = u + gridDim.x;
+        row_body<T, NT, KT, C::THREADS, true>(a, row0, a.ops, smem_raw, xs, [&] {
+            if (threadIdx.x == 0 && next < units) issue(next);
+        });
+        __syncthreads();                                // S and the scratch are reused
+    }
+}
+
 // Batched work list: each item (pulse, first row) covers 512 / (Nt/16) rows of
 // one pulse; pulses may have different Nr and Nt (Nt = 512 ... 8192).  A
 // persistent grid pulls items from a global counter, largest rows first.
@@ -1142,6 +1239,18 @@ cudaError_t set_smem_attr() {
     return e;
 }
 
+// The prefetching persistent variant (3): FP32, K = 8, Nt >= 512; 3 CTAs of
+// 256 threads per SM (the staging buffer leaves no room for a fourth), or
+// 1 CTA of 512 threads for Nt = 8192.
+template <int NT>
+constexpr int mb_pf() { return RowCfg<NT>::THREADS >= 512 ? 1 : 3; }
+template <typename T, int NT>
+constexpr bool has_pf() { return sizeof(T) == 4 && NT >= 512; }
+template <typename T, int NT>
+size_t pf_smem_bytes(bool with_u) {
+    return pf_stage_offset<T, NT>(with_u) + sizeof(cx<T>) * RowCfg<NT>::RPC * NT + 16;
+}
+
 template <typename T, int NT>
 cudaError_t prepare_nt() {
     cudaError_t e = set_smem_attr<T, NT, 0, 1>();
@@ -1150,7 +1259,41 @@ cudaError_t prepare_nt() {
         if (e == cudaSuccess) e = set_smem_attr<T, NT, 8, mb_of<NT>(1)>();
         if (e == cudaSuccess) e = set_smem_attr<T, NT, 8, mb_of<NT>(2)>();
     }
+    if constexpr (has_pf<T, NT>()) {
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(row_kernel_pf<T, NT, 8, mb_pf<NT>()>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pf_smem_bytes<T, NT>(true));
+    }
     return e;
+}
+
+// Launch of the prefetching variant over npulse pulses: one CTA per SM slot
+// (occupancy queried once), each walking units of RPC rows.
+template <typename T, int NT>
+cudaError_t launch_nt_pf(const RowMultiArgs<T> &m, int npulse, cudaStream_t st) {
+    using C = RowCfg<NT>;
+    if constexpr (!has_pf<T, NT>()) {
+        return cudaErrorInvalidConfiguration;
+    } else {
+        const RowArgs<T> &a = m.a;
+        const bool with_u = (a.ops & (OP_RHO | OP_STATS)) != 0;
+        const size_t smem = pf_smem_bytes<T, NT>(with_u);
+        const int units = (a.nr + C::RPC - 1) / C::RPC * npulse;
+        if (units <= 0) return cudaSuccess;
+        auto k = row_kernel_pf<T, NT, 8, mb_pf<NT>()>;
+        static int slots[2] = {0, 0};
+        int &sl = slots[with_u ? 1 : 0];
+        if (!sl) {
+            int dev = 0, sms = 0, occ = 0;
+            cudaError_t e = cudaGetDevice(&dev);
+            if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, C::THREADS, smem);
+            if (e != cudaSuccess) return e;
+            sl = sms * (occ > 0 ? occ : 1);
+        }
+        const int grid = units < sl ? units : sl;
+        return launch_k(k, dim3(grid), dim3(C::THREADS), smem, st, m, npulse, a.err);
+    }
 }
 
 template <typename T, int NT>
@@ -1161,6 +1304,8 @@ cudaError_t launch_nt_multi(const RowMultiArgs<T> &m, int npulse, cudaStream_t s
     const dim3 grid((a.nr + C::RPC - 1) / C::RPC, npulse);
     if (grid.x == 0 || npulse <= 0) return cudaSuccess;
     if (npulse > kRowMulti) return cudaErrorInvalidValue;
+    if constexpr (has_pf<T, NT>())
+        if (a.variant == 3 && a.nl.K == 8) return launch_nt_pf<T, NT>(m, npulse, st);
     void (*k)(const RowMultiArgs<T>) = row_kernel_multi<T, NT, 8, 1>;
     if (a.nl.K != 8) {
         k = row_kernel_multi<T, NT, 0, 1>;
@@ -1177,6 +1322,18 @@ cudaError_t launch_nt(const RowArgs<T> &a, cudaStream_t st) {
     const size_t smem = smem_bytes<T, NT>((a.ops & (OP_RHO | OP_STATS)) != 0);
     const int grid = (a.nr + C::RPC - 1) / C::RPC;
     if (grid == 0) return cudaSuccess;
+    if constexpr (has_pf<T, NT>()) {
+        if (a.variant == 3 && a.nl.K == 8) {
+            RowMultiArgs<T> m;
+            m.a = a;
+            for (int c = 0; c < kRowMulti; ++c) {
+                m.field[c] = a.field;
+                m.rho[c] = a.rho;
+                m.stats[c] = a.stats;
+            }
+            return launch_nt_pf<T, NT>(m, 1, st);
+        }
+    }
     // K = 8 (the photon number of 800 nm in air) gets unrolled powers
     void (*k)(RowArgs<T>) = row_kernel<T, NT, 8, 1>;
     if (a.nl.K != 8) {

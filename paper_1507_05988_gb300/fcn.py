@@ -260,6 +260,16 @@ class Solver:
         assert a.shape == self._shape(pulse)
         check(fcn_set_field_c64(self.ctx, pulse, a.ctypes.data_as(_F)), self.ctx)
 
+    def set_field_device(self, t, pulse: int = 0):
+        """From a contiguous CUDA tensor in the working precision
+        (complex128 for FCN_FP64, complex64 for FCN_FP32_MIXED)."""
+        check(fcn_set_field_device(self.ctx, pulse, tensor_ptr(t)), self.ctx)
+
+    def get_field_device(self, t, pulse: int = 0):
+        """Into a contiguous CUDA tensor in the working precision."""
+        check(fcn_get_field_device(self.ctx, pulse, tensor_ptr(t)), self.ctx)
+        return t
+
     def get_field_c64(self, pulse: int = 0, out: np.ndarray | None = None) -> np.ndarray:
         out = np.empty(self._shape(pulse), np.complex64) if out is None else out
         check(fcn_get_field_c64(self.ctx, pulse, out.ctypes.data_as(_F)), self.ctx)

@@ -1,7 +1,7 @@
 """Trains the learned dz controller and compares it with plain step doubling.
 
-    python -m paper_1507_05988_gb300.learned_dz --seeds 1-8 --z-train 2,50,5 \
-        --z-test 1000 --json out.json
+    python -m paper_1507_05988_gb300.learned_dz --seeds 1-32 --z-train 2,0.5,5 \
+        --z-val 2,2 --z-test 20 --json out.json --save learned_dz_weights.npy
 
 1. Data: adaptive runs (plain step doubling, rtol 1e-4, FP32-mixed) of the
    three seeded pulses of configs 1-3 (1 % amplitude noise, seeds as given),
@@ -128,6 +128,8 @@ def main(argv=None) -> int:
     ap.add_argument("--lr", type=float, default=2e-3)
     ap.add_argument("--margins", default="0,0.05,0.1,0.15,0.2")
     ap.add_argument("--json", default="")
+    ap.add_argument("--save", default="", help="write the trained weights (with the chosen "
+                                                "margin) to this .npy file")
     a = ap.parse_args(argv)
     zt = [float(v) for v in a.z_train.split(",")]
     zv = [float(v) for v in a.z_val.split(",")]
@@ -160,6 +162,8 @@ def main(argv=None) -> int:
     m_best = min(scores, key=scores.get)
     out["validation_substeps"] = {"plain": plain_val, "learned_by_margin": scores, "margin": m_best}
     print(f"learned_dz: validation substeps plain {plain_val}, learned {scores}", flush=True)
+    if a.save:
+        np.save(a.save, with_margin(params, m_best))
 
     wl = W.config5(seed=0)
     A0, s0, _ = run(wl, a.z_test, 2e-3)

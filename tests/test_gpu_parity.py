@@ -540,7 +540,7 @@ def test_adaptive_batch_of_different_pulses(fcn, controller):
 # ------------------------------------------------- autotuner and variants
 
 @pytest.mark.parametrize("prec", [FP64, FP32])
-@pytest.mark.parametrize("row_v", [0, 1, 2])
+@pytest.mark.parametrize("row_v", [0, 1, 2, 3])
 @pytest.mark.parametrize("col_v", [0, 1, 2, 3, 4, 5, 6, 7, 8])
 def test_every_kernel_variant_matches_oracle(fcn, prec, row_v, col_v):
     """Every variant the autotuner can pick computes the same step."""
@@ -557,7 +557,7 @@ def test_every_kernel_variant_matches_oracle(fcn, prec, row_v, col_v):
     assert rel_l2(A, Aref) < (1e-10 if prec == FP64 else 1e-5)
 
 
-@pytest.mark.parametrize("row_v", [0, 1, 2])
+@pytest.mark.parametrize("row_v", [0, 1, 2, 3])
 def test_row_occupancy_variants_at_nt_256(fcn, row_v):
     """Nt = 256 rows (config 1, the Cartesian grid) have their own FP32
     occupancy variants (3 and 4 CTAs per SM)."""
@@ -687,19 +687,21 @@ def test_graph_branches_are_bit_identical(fcn, pairing):
         assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("row_v", [0, 3])
 @pytest.mark.parametrize("graph", [True, False])
-def test_multi_pulse_row_launch_is_bit_identical(fcn, graph):
+def test_multi_pulse_row_launch_is_bit_identical(fcn, graph, row_v):
     """The row stage of pulses sharing grid and coefficients as one launch
-    (blockIdx.y = pulse) computes exactly what one launch per pulse does;
-    a pulse with other physics (a different power) is split off into its
-    own launch and stays exact too."""
+    (blockIdx.y = pulse, or the persistent prefetching kernel walking the
+    rows of all of them: row variant 3) computes exactly what one launch per
+    pulse does; a pulse with other physics (a different power) is split off
+    into its own launch and stays exact too."""
     wls = [W.small(72, 512, p_over_pcr=4.0, noise_seed=50 + k).with_(n2j=(W.N2, W.N4, 0, 0))
            for k in range(4)]
     wls.insert(2, W.small(72, 512, p_over_pcr=4.0, noise_seed=60).with_(n2j=(W.N2, 0, 0, 0)))
     out = {}
     for multi in (0, 1, 2):
         s = fcn.Solver([w.physics() for w in wls], precision=FP32)
-        s.set_variants(0, 7)
+        s.set_variants(row_v, 7)
         s.set_pairing(1)
         s.set_sequential_columns(0)
         s.set_multi_launch(multi)
@@ -774,7 +776,7 @@ def test_autotuner_picks_a_valid_variant_and_stays_correct(fcn):
     s.set_field(wl.field())
     s.step(4e-3, 3)
     rv, cv = s.variants()
-    assert 0 <= rv < 3 and 0 <= cv < 9
+    assert 0 <= rv < 4 and 0 <= cv < 9
     A = s.get_field()
     s.close()
     Aref, _ = oracle.run(pb, 4e-3, 3, wl.field())
