@@ -501,7 +501,8 @@ def run_ours(args):
     solver.step(dz, args.warmup)
     torch.cuda.synchronize()
     variants = {"row": solver.variants(0)[0], "column": solver.variants(0)[1],
-                "paired_columns": solver.pairing()}
+                "paired_columns": solver.pairing(),
+                "sequential_columns_all_pulses": solver.sequential_columns()}
 
     def barrier():
         if pg:
@@ -562,7 +563,8 @@ def run_ours(args):
     if os.path.exists(tpath):
         with open(tpath) as f:
             tj = json.load(f)
-        if dom_name == "column" and variants["paired_columns"]:
+        if dom_name == "column" and variants["paired_columns"] == 1 and \
+                variants["sequential_columns_all_pulses"] != 1:
             t = tj.get("column_pair")
             traffic = t * units / 2 if t else None
         else:
@@ -650,6 +652,18 @@ def run_ours(args):
     torch.cuda.synchronize()
     v64 = weak_scaling_value(world, B * pts, K64, reduce_max(a.elapsed_time(b), pg, "cuda"))
     s64.close()
+    # the FP64 path is bound by FP64 arithmetic: flops per point-step from the
+    # ncu instruction counts of its row and column kernels (2 DFMA + DADD +
+    # DMUL: 346 + 96 per point, profiles/fp64_kernels_cfg2.md) against the
+    # FP64 FMA rate measured here by the library's microkernel
+    fp64_flops_per_point_step = 442.0
+    fp64_peak = fcn.alu_peak(0)
+    fp64_roof = {"bound": "alu", "achieved": fp64_flops_per_point_step * v64 / world / 1e12,
+                 "peak": fp64_peak / 1e12, "unit": "TFLOP/s",
+                 "frac": fp64_flops_per_point_step * v64 / world / fp64_peak,
+                 "flops_per_point_step": fp64_flops_per_point_step,
+                 "peak_source": "fcn_alu_peak(0): this library's FP64 FMA microkernel, measured in this run",
+                 "fp32_fma_peak_tflops": fcn.alu_peak(1) / 1e12}
 
     # ---- the chosen form (FP32 + learned dz + batched, adaptive) against the
     # plain FP64 path at the metric's rtol ----
@@ -692,7 +706,7 @@ def run_ours(args):
             "batched_cfg4": cfg4,
             "cartesian_3d1": cart,
             "fp64_gpu": {"value": v64, "unit": UNIT, "steps": K64,
-                         "speedup_of_chosen_form": value / v64},
+                         "speedup_of_fp32_mixed": value / v64, "roofline": fp64_roof},
             "accuracy_vs_fp64": acc,
             "chosen_form": chosen,
             "clocks": clk,

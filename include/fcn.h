@@ -189,7 +189,8 @@ int fcn_step_nograph(fcn_ctx *ctx, double dz, int64_t n);
  * err <= rtol accepts A2; next dz = dz*clamp(0.9 (rtol/err)^(1/3), 0.2, 2);
  * the last step lands on z_end exactly.  controller 0: proposals from that
  * formula; controller 1: proposals from the learned MLP (fcn_mlp_set) with
- * the formula as fallback after a rejection.  dz0 > 0 is the first
+ * the formula as fallback after a rejection (and for the next 16 accepted
+ * steps after a rejected MLP proposal).  dz0 > 0 is the first
  * proposal.  Fails with FCN_ERR_STEP_UNDERFLOW if dz < dz_min or after
  * max_reject consecutive rejections.  out may be NULL.
  * Multi-pulse contexts (all pulses at the same z, batching 0) advance with

@@ -1223,6 +1223,11 @@ int diag_device(fcn_ctx *ctx, Pulse &pu, void *field) {
     return FCN_OK;
 }
 
+// After an MLP proposal is rejected, the next kMlpCooldown accepted steps
+// take the step-doubling law's proposal: a state where the network
+// overreaches does not turn into a run of rejected attempts.
+constexpr int kMlpCooldown = 16;
+
 // Step doubling (controller 0) or MLP proposals judged by step doubling
 // (controller 1).  With a log buffer (fcn_mlp_set_log) every attempt appends
 // [f0..f5, log(h/L_ref), log(err/rtol)] for training.
@@ -1306,7 +1311,7 @@ int propagate_batch(fcn_ctx *ctx, double z_end, double dz0, double rtol, double 
     fcn_stats s;
     std::memset(&s, 0, sizeof s);
     double z = ctx->pulses[0].z, dz = dz0;
-    int consecutive = 0, status = FCN_OK;
+    int consecutive = 0, cooldown = 0, status = FCN_OK;
     bool from_mlp = false;
     std::vector<void *> f1(n), f2(n);
     std::vector<const cx<T> *> tab1(n), tab2(n);
@@ -1383,6 +1388,7 @@ int propagate_batch(fcn_ctx *ctx, double z_end, double dz0, double rtol, double 
             if (from_mlp) s.mlp_proposals++;
             consecutive = 0;
             dz = last ? dz : h * fac;
+            bool proposed = false;
             if (next_feat) {
                 double prop = 0.0;
                 for (size_t i = 0; i < n; ++i) {
@@ -1394,14 +1400,20 @@ int propagate_batch(fcn_ctx *ctx, double z_end, double dz0, double rtol, double 
                     const double p = H[16 * i + 12];
                     if (std::isfinite(p) && p > 0) prop = prop > 0 ? std::fmin(prop, p) : p;
                 }
-                if (prop > 0) dz = prop;
+                if (cooldown > 0) {
+                    --cooldown;
+                } else if (prop > 0) {
+                    dz = prop;
+                    proposed = true;
+                }
             }
-            from_mlp = features && z < z_end;
+            from_mlp = proposed && z < z_end;
         } else {
             for (auto &pu : ctx->pulses) pu.rejected++;
             s.rejected++;
             consecutive++;
             dz = h * fac;          // the step-doubling formula is the fallback
+            if (from_mlp) cooldown = kMlpCooldown;
             from_mlp = false;
         }
         if (dz < dz_min || consecutive > max_reject) {
@@ -1482,7 +1494,7 @@ int propagate_impl(fcn_ctx *ctx, double z_end, double dz0, double rtol, double d
     fcn_stats s;
     std::memset(&s, 0, sizeof s);
     double dz = dz0;
-    int consecutive = 0;
+    int consecutive = 0, cooldown = 0;
     int status = FCN_OK;
     bool from_mlp = false;
     while (pu.z < z_end) {
@@ -1549,21 +1561,28 @@ int propagate_impl(fcn_ctx *ctx, double z_end, double dz0, double rtol, double d
             if (from_mlp) s.mlp_proposals++;
             consecutive = 0;
             dz = last ? dz : h * fac;
+            bool proposed = false;
             if (next_feat) {
                 std::memcpy(hfeat, ctx->host_red + 8, 8 * sizeof(float));
                 sc.err_prev = err;
                 sc.e_prev = ctx->host_red[13];
                 if (controller == 1) {
                     mlp_dz = ctx->host_red[12];
-                    if (std::isfinite(mlp_dz) && mlp_dz > 0) dz = mlp_dz;
+                    if (cooldown > 0) {
+                        --cooldown;
+                    } else if (std::isfinite(mlp_dz) && mlp_dz > 0) {
+                        dz = mlp_dz;
+                        proposed = true;
+                    }
                 }
             }
-            from_mlp = controller == 1 && features && pu.z < z_end;
+            from_mlp = proposed && pu.z < z_end;
         } else {
             pu.rejected++;
             s.rejected++;
             consecutive++;
             dz = h * fac;          // the step-doubling formula is the fallback
+            if (from_mlp) cooldown = kMlpCooldown;
             from_mlp = false;
         }
         if (dz < dz_min || consecutive > max_reject) {

@@ -118,6 +118,28 @@ def with_margin(params, m):
     return q
 
 
+def test_one(params, z_test):
+    wl = W.config5(seed=0)
+    A0, s0, _ = run(wl, z_test, 2e-3)
+    A1, s1, _ = run(wl, z_test, 2e-3, controller=1, params=params)
+    diff = float(np.linalg.norm(A1 - A0) / np.linalg.norm(A0))
+    keys = ("accepted", "rejected", "substeps", "mlp_proposals", "wall_s")
+    return {"workload": f"config-5 pulse (config-2 grid 1024x4096, noise seed 0), "
+                        f"0 -> {z_test} m, rtol 1e-4, FP32-mixed",
+            "plain": {k: s0[k] for k in keys if k != "mlp_proposals"},
+            "learned": {k: s1[k] for k in keys},
+            "final_field_rel_l2_learned_vs_plain": diff}
+
+
+def test_only(params, z_test, path) -> int:
+    out = {"test": test_one(params, z_test)}
+    print(json.dumps(out["test"]), flush=True)
+    if path:
+        with open(path, "w") as f:
+            json.dump(out, f, indent=1)
+    return 0
+
+
 def main(argv=None) -> int:
     ap = argparse.ArgumentParser()
     ap.add_argument("--seeds", default="1-8")
@@ -130,7 +152,10 @@ def main(argv=None) -> int:
     ap.add_argument("--json", default="")
     ap.add_argument("--save", default="", help="write the trained weights (with the chosen "
                                                 "margin) to this .npy file")
+    ap.add_argument("--load", default="", help="skip data and training: test these weights")
     a = ap.parse_args(argv)
+    if a.load:
+        return test_only(np.load(a.load), a.z_test, a.json)
     zt = [float(v) for v in a.z_train.split(",")]
     zv = [float(v) for v in a.z_val.split(",")]
     out = {"seeds": a.seeds, "z_train_m": zt, "z_val_m": zv, "z_test_m": a.z_test}
@@ -165,16 +190,7 @@ def main(argv=None) -> int:
     if a.save:
         np.save(a.save, with_margin(params, m_best))
 
-    wl = W.config5(seed=0)
-    A0, s0, _ = run(wl, a.z_test, 2e-3)
-    A1, s1, _ = run(wl, a.z_test, 2e-3, controller=1, params=with_margin(params, m_best))
-    diff = float(np.linalg.norm(A1 - A0) / np.linalg.norm(A0))
-    keys = ("accepted", "rejected", "substeps", "mlp_proposals", "wall_s")
-    out["test"] = {"workload": f"config-5 pulse (config-2 grid 1024x4096, noise seed 0), "
-                               f"0 -> {a.z_test} m, rtol 1e-4, FP32-mixed",
-                   "plain": {k: s0[k] for k in keys if k != "mlp_proposals"},
-                   "learned": {k: s1[k] for k in keys},
-                   "final_field_rel_l2_learned_vs_plain": diff}
+    out["test"] = test_one(with_margin(params, m_best), a.z_test)
     print(json.dumps(out["test"]), flush=True)
     if a.json:
         with open(a.json, "w") as f:
