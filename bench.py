@@ -273,44 +273,42 @@ def oracle_thread_scaling(steps=3):
     return 0
 
 
+PERTURB_DEVICE = "cuda"      # where the conditioning reference's perturbation is drawn
+
+
 def accuracy_leg(fcn, wl, field, dz, make=None, checkpoints=None):
     """FP32-mixed against the FP64 GPU path over the full fixed-step run, at
-    checkpoints; beside it the same FP64 path started from the field times
-    (1 + 6e-8 xi), xi uniform in [-1, 1] (a perturbation of FP32 rounding
-    size): where that run drifts as far from the unperturbed one as FP32
-    does, the difference is the problem's conditioning, not the arithmetic.
-    make(precision) builds the solver (default: a radial Solver of wl)."""
-    import numpy as np
-    per_step = make is None
+    checkpoints; beside it the same FP64 path with its field multiplied by
+    (1 + 6e-8 xi), xi uniform in [-1, 1] per point, after every step (a
+    perturbation of FP32 rounding size entering at every step, the way FP32
+    rounding does): where that run drifts as far from the unperturbed one as
+    FP32 does, the difference is the problem's conditioning, not the
+    arithmetic.  make(precision) builds the solver (default: a radial Solver
+    of wl); both solver kinds take the perturbation through their device
+    field entry points."""
     if make is None:
         def make(prec):
             return fcn.Solver(wl.physics(), precision=prec)
-    rng = np.random.default_rng(12345)
-    pert = field if per_step else field * (1.0 + 6e-8 * rng.uniform(-1.0, 1.0, field.shape))
     if checkpoints is None:
         checkpoints = [c for c in (100, 200, 300, 400, 500, 750, 1000) if c <= wl.nsteps]
         if wl.nsteps not in checkpoints:
             checkpoints.append(wl.nsteps)
 
-    def run(prec, f0, visit, perturb=False):
+    def run(prec, visit, perturb=False):
         import torch
         s = make(prec)
-        s.set_field(f0)
+        s.set_field(field)
         done = 0
         if perturb:
-            # after every step the field is multiplied on the device by
-            # (1 + 6e-8 xi), xi ~ U[-1, 1] drawn per point and step: a
-            # perturbation of FP32 rounding size entering at every step, as
-            # FP32 rounding does
-            gen = torch.Generator(device="cuda")
+            gen = torch.Generator(device=PERTURB_DEVICE)
             gen.manual_seed(12345)
-            buf = torch.empty(field.shape, dtype=torch.complex128, device="cuda")
+            buf = torch.empty(field.shape, dtype=torch.complex128, device=PERTURB_DEVICE)
         for c in checkpoints:
             if perturb:
                 for _ in range(c - done):
                     s.step(dz, 1)
                     s.get_field_device(buf)
-                    xi = torch.rand(field.shape, generator=gen, device="cuda", dtype=torch.float64)
+                    xi = torch.rand(field.shape, generator=gen, device=PERTURB_DEVICE, dtype=torch.float64)
                     buf.mul_(1.0 + 6e-8 * (2.0 * xi - 1.0))
                     s.set_field_device(buf)
             else:
@@ -320,14 +318,13 @@ def accuracy_leg(fcn, wl, field, dz, make=None, checkpoints=None):
         s.close()
 
     ref = {}
-    run(fcn.FCN_FP64, field, lambda c, a, e: ref.__setitem__(c, (a, e)))
+    run(fcn.FCN_FP64, lambda c, a, e: ref.__setitem__(c, (a, e)))
     table = {c: {"steps": c} for c in checkpoints}
-    for name, prec, f0, pt in (("fp32", fcn.FCN_FP32_MIXED, field, False),
-                               ("fp64_perturbed", fcn.FCN_FP64, pert, per_step)):
+    for name, prec, pt in (("fp32", fcn.FCN_FP32_MIXED, False), ("fp64_perturbed", fcn.FCN_FP64, True)):
         def visit(c, a, e, name=name):
             table[c][name + "_field_rel_l2"] = rel_l2(a, ref[c][0])
             table[c][name + "_energy_rel"] = abs(e / ref[c][1] - 1)
-        run(prec, f0, visit, perturb=pt)
+        run(prec, visit, perturb=pt)
     for c in checkpoints:
         ref_d = table[c]["fp64_perturbed_field_rel_l2"]
         table[c]["fp32_over_reference"] = table[c]["fp32_field_rel_l2"] / ref_d if ref_d > 0 else None
@@ -338,9 +335,32 @@ def accuracy_leg(fcn, wl, field, dz, make=None, checkpoints=None):
             "checkpoints": table,
             "conditioning": ("fp64_perturbed_*: the FP64 path with its field multiplied by "
                              "(1 + 6e-8 xi), xi ~ U[-1, 1] per point, after every step, against the "
-                             "unperturbed FP64 path" if per_step else
-                             "fp64_perturbed_*: the FP64 path from the field times (1 + 6e-8 xi), "
-                             "xi ~ U[-1, 1], against the unperturbed FP64 path")}
+                             "unperturbed FP64 path")}
+
+
+def energy_drift_leg(fcn, W, steps=300):
+    """Energy change per step of the loss-free parts of the step, where the
+    exact discrete step conserves the energy: the config-2 pulse (1024 x
+    4096, dz = 2 mm) with diffraction + dispersion only, and with the Kerr
+    terms (n2, n4: pure phases) added, over `steps` steps in FP32-mixed and
+    in FP64.  (E_n / E_0 - 1) / n; FP32 rounding that perturbs the discrete
+    operator the same way at every step shows here as a steady drift."""
+    wl = W.config2(seed=0)
+    f = wl.field()
+    out = {"workload": f"cfg2 pulse {wl.nr}x{wl.nt}, {steps} steps of {wl.dz} m"}
+    for tag, flags in (("linear", fcn.FCN_DIFFRACTION | fcn.FCN_DISPERSION),
+                       ("linear_kerr", fcn.FCN_DIFFRACTION | fcn.FCN_DISPERSION | fcn.FCN_KERR)):
+        phys = dict(wl.physics(), flags=flags)
+        row = {}
+        for prec, name in ((fcn.FCN_FP32_MIXED, "fp32"), (fcn.FCN_FP64, "fp64")):
+            s = fcn.Solver(phys, precision=prec)
+            s.set_field(f)
+            e0 = s.diag()["energy"]
+            s.step(wl.dz, steps)
+            row[name] = (s.diag()["energy"] / e0 - 1.0) / steps
+            s.close()
+        out[tag] = row
+    return out
 
 
 def chosen_form_leg(fcn, W, z_len, pulses=8, rtol=1e-4):
@@ -675,6 +695,7 @@ def run_ours(args):
     acc = None
     if rank == 0 and not args.no_accuracy:
         acc = accuracy_leg(fcn, wl0, fields[0], dz)
+        acc["loss_free_energy_drift_per_step"] = energy_drift_leg(fcn, W)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -497,6 +497,12 @@ int  fcn_xy_set_field(fcn_xy_ctx *ctx, const double *host);
 int  fcn_xy_get_field(fcn_xy_ctx *ctx, double *host);
 int  fcn_xy_set_field_c64(fcn_xy_ctx *ctx, const float *host);
 int  fcn_xy_get_field_c64(fcn_xy_ctx *ctx, float *host);
+/* The same from / into a caller-owned device buffer in the working
+ * precision (complex128 in FCN_FP64, complex64 in FCN_FP32_MIXED; Nx*Ny*Nt
+ * values): device-to-device copies on the context stream, no
+ * synchronisation.  Setting resets z, the step count and rho. */
+int  fcn_xy_set_field_device(fcn_xy_ctx *ctx, const void *dev_field);
+int  fcn_xy_get_field_device(fcn_xy_ctx *ctx, void *dev_out);
 /* rho [m^-3] of the last nonlinear half step, Nx*Ny*Nt doubles. */
 int  fcn_xy_get_rho(fcn_xy_ctx *ctx, double *host);
 /* n Strang steps of length dz (n >= 0, dz > 0 finite); blocks of eight

@@ -161,22 +161,16 @@ __global__ void cn_table_kernel_f32(TableArgs a, cx<float> *table) {
 // - cd x_j), alpha_j = i sl / piv_j, gamma_j = i sh / piv_j: from the CnCoef
 // rows when the launch has them (context tables), else from s and the ratio
 // tables (stateless operations).
+// With CnCoef rows the FP32 explicit side is two-float (see CnCoef); the
+// stateless path forms single-rounded coefficients from s and the tables.
 template <typename T>
-struct RowCo {
-    T sl, sh, d, cd;
-};
-template <typename T>
-__device__ __forceinline__ RowCo<T> row_co(const ColArgs<T> &a, int j, T delta) {
-    RowCo<T> r;
+__device__ __forceinline__ ExRow<T> row_co(const ColArgs<T> &a, int j, T delta, const CdCol<T> &cdc) {
+    ExRow<T> r;
+    r.sll = r.shl = r.cdl = T(0);
     const int nr = a.nr;
     if (a.coef) {
-        CnCoef<T> cf;
-        if (j < nr - 1) {
-            cf = a.coef[FCN_IDX(j, nr, 35)];
-        } else {
-            cf.sl = T(0); cf.sh = T(0); cf.c0 = T(0); cf.d = T(0);
-        }
-        r.sl = cf.sl; r.sh = cf.sh; r.d = cf.d; r.cd = cf.d * (cf.c0 - delta);
+        const CnCoef<T> cf = j < nr - 1 ? a.coef[FCN_IDX(j, nr, 35)] : CnCoef<T>{};
+        r = ex_row(cf, j == 0, cdc);
     } else if (j == 0) {
         r.sl = T(0); r.sh = T(4) * a.s; r.d = T(1); r.cd = T(4) * a.s - delta;
     } else if (j < nr - 1) {
@@ -206,6 +200,7 @@ __device__ __forceinline__ void cn_body(const ColArgs<T> &a, int C, int g, unsig
     const int nq = a.tp;
     const int qq = (q <= nt / 2) ? q : nt - q;
     const T delta = a.dk * T(qq) * T(qq);
+    const CdCol<T> cdc = cd_col<T>(a.s64, a.dk64, qq);
     const int j0 = chunk * L;
 
     cx<T> x[L + 2];
@@ -228,10 +223,8 @@ __device__ __forceinline__ void cn_body(const ColArgs<T> &a, int C, int g, unsig
     for (int k = 0; k < L; ++k) {
         const int j = j0 + k;
         if (j < nr) {
-            const RowCo<T> c = row_co(a, j, delta);
-            const cx<T> w = mk(c.sl * x[k].x + c.sh * x[k + 2].x - c.cd * x[k + 1].x,
-                               c.sl * x[k].y + c.sh * x[k + 2].y - c.cd * x[k + 1].y);
-            const cx<T> rhs = mk(c.d * x[k + 1].x - w.y, c.d * x[k + 1].y + w.x);
+            const ExRow<T> c = row_co(a, j, delta, cdc);
+            const cx<T> rhs = ex_rhs(c, x[k], x[k + 1], x[k + 2]);
             const cx<T> alpha = cmul_i(inv[k], c.sl);
             y[k] = cmul(rhs, inv[k]);
             PB = cmul(alpha, PB) + y[k];
@@ -247,7 +240,7 @@ __device__ __forceinline__ void cn_body(const ColArgs<T> &a, int C, int g, unsig
         for (int k = 0; k < L; ++k) {
             const int j = j0 + k;
             if (j < nr) {
-                const cx<T> alpha = cmul_i(inv[k], row_co(a, j, delta).sl);
+                const cx<T> alpha = cmul_i(inv[k], row_co(a, j, delta, cdc).sl);
                 y[k] = cmul(alpha, yp) + y[k];
                 yp = y[k];
             }
@@ -259,7 +252,7 @@ __device__ __forceinline__ void cn_body(const ColArgs<T> &a, int C, int g, unsig
     for (int k = L - 1; k >= 0; --k) {
         const int j = j0 + k;
         if (j < nr) {
-            const cx<T> gamma = cmul_i(inv[k], row_co(a, j, delta).sh);
+            const cx<T> gamma = cmul_i(inv[k], row_co(a, j, delta, cdc).sh);
             QB = cmul(gamma, QB) + y[k];
             QA = cmul(gamma, QA);
         }
@@ -272,7 +265,7 @@ __device__ __forceinline__ void cn_body(const ColArgs<T> &a, int C, int g, unsig
         for (int k = L - 1; k >= 0; --k) {
             const int j = j0 + k;
             if (j < nr) {
-                const cx<T> gamma = cmul_i(inv[k], row_co(a, j, delta).sh);
+                const cx<T> gamma = cmul_i(inv[k], row_co(a, j, delta, cdc).sh);
                 xn = cmul(gamma, xn) + y[k];
                 a.field[FCN_IDX((size_t)j * nt + q, (size_t)nr * nt, 37)] = disp_apply(xn, ph);
             }
@@ -363,7 +356,7 @@ constexpr size_t kCnStagedSmemMax = 227 * 1024;
 // hoists the loads of the unrolled loop), alpha_j and gamma_j go to the
 // thread's shared-memory slots.  EDGE: the chunk touches row -1 or row nr.
 template <typename T, int L, bool EDGE, int NTC>
-__device__ __forceinline__ void cn_f1_reg(const ColArgs<T> &a, int q, int qq, int j0, T delta, cx<T> *At,
+__device__ __forceinline__ void cn_f1_reg(const ColArgs<T> &a, int q, int qq, int j0, const CdCol<T> &cdc, cx<T> *At,
                                           cx<T> *Gt, int BD, cx<T> (&y)[L], cx<T> &PA, cx<T> &PB) {
     // NTC: Nt as a compile-time constant (row strides become immediates), 0: a.nt
     const int nt = NTC ? NTC : a.nt, nr = a.nr, nq = a.tp;
@@ -384,12 +377,9 @@ __device__ __forceinline__ void cn_f1_reg(const ColArgs<T> &a, int q, int qq, in
         if (!EDGE || j < nr - 1) {
             cf = a.coef[FCN_IDX(j, nr, 53)];
         } else {
-            cf.sl = T(0); cf.sh = T(0); cf.c0 = T(0); cf.d = T(0);
+            cf = CnCoef<T>{};
         }
-        const T cd = cf.d * (cf.c0 - delta);
-        const T wx = cf.sl * xm.x + cf.sh * xp.x - cd * x0.x;
-        const T wy = cf.sl * xm.y + cf.sh * xp.y - cd * x0.y;
-        const cx<T> rhs = mk(cf.d * x0.x - wy, cf.d * x0.y + wx);
+        const cx<T> rhs = ex_rhs(ex_row(cf, j == 0, cdc), xm, x0, xp);
         const cx<T> beta = cmul(rhs, inv);
         const cx<T> al = cmul_i(inv, cf.sl);
         At[k * BD] = al;
@@ -421,7 +411,7 @@ __device__ __forceinline__ void cn_staged_body(const ColArgs<T> &a, int C, int g
     const int nt = NTC ? NTC : a.nt, nr = a.nr;
     const int nq = a.tp;
     const int qq = (q <= nt / 2) ? q : nt - q;
-    const T delta = a.dk * T(qq) * T(qq);
+    const CdCol<T> cdc = cd_col<T>(a.s64, a.dk64, qq);
     const int j0 = chunk * L;
 
     cx<T> y[L];
@@ -430,9 +420,9 @@ __device__ __forceinline__ void cn_staged_body(const ColArgs<T> &a, int C, int g
     cx<T> *At = REG ? Xt : Xt + BD;
     if constexpr (REG) {
         if (j0 >= 1 && j0 + L < nr)
-            cn_f1_reg<T, L, false, NTC>(a, q, qq, j0, delta, At, Gt, BD, y, PA, PB);
+            cn_f1_reg<T, L, false, NTC>(a, q, qq, j0, cdc, At, Gt, BD, y, PA, PB);
         else
-            cn_f1_reg<T, L, true, NTC>(a, q, qq, j0, delta, At, Gt, BD, y, PA, PB);
+            cn_f1_reg<T, L, true, NTC>(a, q, qq, j0, cdc, At, Gt, BD, y, PA, PB);
     } else {
     if (j0 >= 1 && j0 + L < nr) {
         // interior chunk: every row j0-1 .. j0+L exists
@@ -472,12 +462,9 @@ __device__ __forceinline__ void cn_staged_body(const ColArgs<T> &a, int C, int g
         if (j < nr - 1) {
             cf = a.coef[FCN_IDX(j, nr, 46)];
         } else {
-            cf.sl = T(0); cf.sh = T(0); cf.c0 = T(0); cf.d = T(0);
+            cf = CnCoef<T>{};
         }
-        const T cd = cf.d * (cf.c0 - delta);
-        const T wx = cf.sl * xm.x + cf.sh * xp.x - cd * x0.x;
-        const T wy = cf.sl * xm.y + cf.sh * xp.y - cd * x0.y;
-        const cx<T> rhs = mk(cf.d * x0.x - wy, cf.d * x0.y + wx);
+        const cx<T> rhs = ex_rhs(ex_row(cf, j == 0, cdc), xm, x0, xp);
         const cx<T> beta = cmul(rhs, inv);
         const cx<T> al = cmul_i(inv, cf.sl);
         Xt[(k + 1) * BD] = al;                  // x_j (slot k+1) is no longer read
@@ -542,14 +529,18 @@ template <typename T>
 __global__ void cn_coef_kernel(TableArgs a, CnCoef<T> *coef) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= a.nr) return;
-    const T s = T(a.s);
-    CnCoef<T> c;
-    if (j >= a.nr - 1) {
-        c.sl = T(0); c.sh = T(0); c.c0 = T(0); c.d = T(0);
-    } else if (j == 0) {
-        c.sl = T(0); c.sh = T(4) * s; c.c0 = T(4) * s; c.d = T(1);
-    } else {
-        c.sl = s * T(a.lo[j]); c.sh = s * T(a.hi[j]); c.c0 = T(2) * s; c.d = T(1);
+    CnCoef<T> c = CnCoef<T>{};
+    if (j < a.nr - 1) {
+        // sl, sh from their FP64 values, rounded once; the lo parts hold the
+        // rounding errors (zero in FP64)
+        const double vl = j == 0 ? 0.0 : a.s * a.lo[j];
+        const double vh = j == 0 ? 4.0 * a.s : a.s * a.hi[j];
+        c.sl = T(vl);
+        c.sh = T(vh);
+        c.sll = T(vl - double(c.sl));
+        c.shl = T(vh - double(c.sh));
+        c.c0 = T((j == 0 ? 4.0 : 2.0) * a.s);
+        c.d = T(1);
     }
     coef[j] = c;
 }
@@ -602,7 +593,7 @@ cudaError_t launch_cn_l(const ColArgs<T> &a, int target, cudaStream_t st) {
 
 template <typename T, int L, bool EDGE, int NTC>
 __device__ __forceinline__ void cn_f1_pair(const ColArgs<T> &a, const cx<T> *f2, int q, int qq, int j0,
-                                           T delta, cx<T> *At, cx<T> *Gt, int BD, cx<T> (&y1)[L],
+                                           const CdCol<T> &cdc, cx<T> *At, cx<T> *Gt, int BD, cx<T> (&y1)[L],
                                            cx<T> (&y2)[L], cx<T> &PA, cx<T> &PB1, cx<T> &PB2) {
     const int nt = NTC ? NTC : a.nt, nr = a.nr, nq = a.tp;
     const cx<T> *fx = a.field + q;
@@ -624,23 +615,19 @@ __device__ __forceinline__ void cn_f1_pair(const ColArgs<T> &a, const cx<T> *f2,
         if (!EDGE || j < nr - 1) {
             cf = a.coef[FCN_IDX(j, nr, 62)];
         } else {
-            cf.sl = T(0); cf.sh = T(0); cf.c0 = T(0); cf.d = T(0);
+            cf = CnCoef<T>{};
         }
-        const T cd = cf.d * (cf.c0 - delta);
+        const ExRow<T> e = ex_row(cf, j == 0, cdc);
         const cx<T> al = cmul_i(inv, cf.sl);
         At[k * BD] = al;
         Gt[k * BD] = cmul_i(inv, cf.sh);
         {
-            const T wx = cf.sl * xm1.x + cf.sh * xp1.x - cd * x01.x;
-            const T wy = cf.sl * xm1.y + cf.sh * xp1.y - cd * x01.y;
-            const cx<T> beta = cmul(mk(cf.d * x01.x - wy, cf.d * x01.y + wx), inv);
+            const cx<T> beta = cmul(ex_rhs(e, xm1, x01, xp1), inv);
             PB1 = cmul(al, PB1) + beta;
             y1[k] = beta;
         }
         {
-            const T wx = cf.sl * xm2.x + cf.sh * xp2.x - cd * x02.x;
-            const T wy = cf.sl * xm2.y + cf.sh * xp2.y - cd * x02.y;
-            const cx<T> beta = cmul(mk(cf.d * x02.x - wy, cf.d * x02.y + wx), inv);
+            const cx<T> beta = cmul(ex_rhs(e, xm2, x02, xp2), inv);
             PB2 = cmul(al, PB2) + beta;
             y2[k] = beta;
         }
@@ -667,15 +654,15 @@ __device__ __forceinline__ void cn_pair_body(const ColArgs<T> &a, cx<T> *field2,
     const int q = g * C + col;
     const int nt = NTC ? NTC : a.nt, nr = a.nr;
     const int qq = (q <= nt / 2) ? q : nt - q;
-    const T delta = a.dk * T(qq) * T(qq);
+    const CdCol<T> cdc = cd_col<T>(a.s64, a.dk64, qq);
     const int j0 = chunk * L;
 
     cx<T> y1[L], y2[L];
     cx<T> PA = mk(T(1), T(0)), PB[2] = {czero<T>(), czero<T>()};
     if (j0 >= 1 && j0 + L < nr)
-        cn_f1_pair<T, L, false, NTC>(a, field2, q, qq, j0, delta, At, Gt, BD, y1, y2, PA, PB[0], PB[1]);
+        cn_f1_pair<T, L, false, NTC>(a, field2, q, qq, j0, cdc, At, Gt, BD, y1, y2, PA, PB[0], PB[1]);
     else
-        cn_f1_pair<T, L, true, NTC>(a, field2, q, qq, j0, delta, At, Gt, BD, y1, y2, PA, PB[0], PB[1]);
+        cn_f1_pair<T, L, true, NTC>(a, field2, q, qq, j0, cdc, At, Gt, BD, y1, y2, PA, PB[0], PB[1]);
     {
         cx<T> yp[2];
         chunk_scan_n<T, false, 2>(PA, PB, C, col, smA, smB, smC, yp);

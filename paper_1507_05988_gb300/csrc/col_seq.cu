@@ -51,7 +51,7 @@ struct SeqParams {
     cx<T> *field[kSeqMaxPulses];
     const CnCoef<T> *coef;             // [nr]
     int nr, nt, ngroups;
-    T dk;                              // delta_q = dk q^2
+    double s64, dk64;                  // s and dk: c0 - delta_q = {4, 2} s - dk q^2
     double disp;                       // exact dispersion factor coefficient, 0: none
     int *err;                          // set to 1 when a wait gives up (may be null)
 };
@@ -148,7 +148,7 @@ cn_seq_kernel(const __grid_constant__ SeqParams<T> p) {
     const int qq = mirror ? nt - q : q;
     const int tx = mirror ? nt - q0 - 32 : q0;          // first pivot column of the box
     const int il = mirror ? 32 - lane : lane;           // this lane's pivot column in the box
-    const T delta = p.dk * T(qq) * T(qq);
+    const CdCol<T> cdc = cd_col<T>(p.s64, p.dk64, qq);
     const CUtensorMap *tmap = &p.tmap;
     cx<T> *col[NP];
 #pragma unroll
@@ -230,14 +230,12 @@ cn_seq_kernel(const __grid_constant__ SeqParams<T> p) {
         for (int r = 0; r < R; ++r) {
             const cx<T> inv = I[r * 34 + il];
             const CnCoef<T> cf = Cf[r];
-            const T cd = cf.d * (cf.c0 - delta);
+            const ExRow<T> e = ex_row(cf, jb + r == 0, cdc);
             al[r] = cmul_i(inv, cf.sl);
 #pragma unroll
             for (int k = 0; k < NP; ++k) {
                 const cx<T> xp = (r + 1 < R) ? stage_x(s, k)[(r + 1) * 32 + lane] : xnext[k];
-                const T wx = cf.sl * xm[k].x + cf.sh * xp.x - cd * x0[k].x;
-                const T wy = cf.sl * xm[k].y + cf.sh * xp.y - cd * x0[k].y;
-                be[k][r] = cmul(mk(cf.d * x0[k].x - wy, cf.d * x0[k].y + wx), inv);
+                be[k][r] = cmul(ex_rhs(e, xm[k], x0[k], xp), inv);
                 xm[k] = x0[k];
                 x0[k] = xp;
             }
@@ -358,7 +356,8 @@ cudaError_t launch_seq_shape(const ColArgs<T> &a, cx<T> *const *fields, int npul
     p.nr = a.nr;
     p.nt = a.nt;
     p.ngroups = a.nt / 32;
-    p.dk = a.dk;
+    p.s64 = a.s64;
+    p.dk64 = a.dk64;
     p.disp = a.disp;
     p.err = a.err;
     const size_t smem = (size_t)W * Ring::kBytes;

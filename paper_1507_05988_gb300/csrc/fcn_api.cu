@@ -348,8 +348,9 @@ struct fcn_ctx {
     int64_t prof_n[FCN_PROF_KINDS] = {0};
     float *mlp = nullptr;             // device FP32 master weights (FCN_MLP_NPARAM)
     bool has_mlp = false;
-    unsigned char *mlp_io = nullptr;  // features (8 floats) + proposal (double)
+    unsigned char *mlp_io = nullptr;  // controller output: 8 doubles
     unsigned char *batch_io = nullptr;  // the same per pulse of an adaptive batch (64 B each)
+    size_t batch_cap = 0;               // pulses batch_io and host_ctl hold
     double *host_ctl = nullptr;         // pinned, 16 doubles per pulse of an adaptive batch
     float *log_buf = nullptr;         // caller-owned host log of adaptive attempts
     int64_t log_cap = 0, log_n = 0;
@@ -529,6 +530,8 @@ ColArgs<T> col_args(Pulse &pu, void *field, const cx<T> *table, double dz) {
     cn_coefs(pu.g, pu.p, dz, &s, &dk, &disp);
     a.s = T(s);
     a.dk = T(dk);
+    a.s64 = s;
+    a.dk64 = dk;
     a.disp = disp;
     a.variant = pu.col_var;
     a.tp = table_pitch(pu.g.nt);
@@ -1274,13 +1277,20 @@ int propagate_batch(fcn_ctx *ctx, double z_end, double dz0, double rtol, double 
         if (!pu.work2) CK(cudaMalloc(&pu.work2, bytes), "work buffer");
     }
     const bool features = controller == 1;
-    // per pulse: features (8 floats) and proposal (double) on the device;
-    // errors, features, proposal and energy on the host
-    if (!ctx->batch_io) CK(cudaMalloc(&ctx->batch_io, 64 * n), "controller buffer");
-    if (!ctx->host_ctl) CK(cudaMallocHost(&ctx->host_ctl, 16 * sizeof(double) * n), "controller buffer");
+    // per pulse: the controller kernel's output (8 doubles) on the device;
+    // norms, features, proposal and energy on the host.  Regrown when pulses
+    // were added since the last batch.
+    if (ctx->batch_cap < n) {
+        cudaFree(ctx->batch_io);
+        if (ctx->host_ctl) cudaFreeHost(ctx->host_ctl);
+        ctx->batch_io = nullptr;
+        ctx->host_ctl = nullptr;
+        ctx->batch_cap = 0;
+        CK(cudaMalloc(&ctx->batch_io, 64 * n), "controller buffer");
+        CK(cudaMallocHost(&ctx->host_ctl, 16 * sizeof(double) * n), "controller buffer");
+        ctx->batch_cap = n;
+    }
     double *H = ctx->host_ctl;
-    auto feat_d = [&](size_t i) { return reinterpret_cast<float *>(ctx->batch_io + 64 * i); };
-    auto dz_d = [&](size_t i) { return reinterpret_cast<double *>(ctx->batch_io + 64 * i + 32); };
     std::vector<MlpScalars> sc(n);
     std::vector<float> peak(n, 0.f);
     for (size_t i = 0; i < n; ++i) {
@@ -1344,23 +1354,29 @@ int propagate_batch(fcn_ctx *ctx, double z_end, double dz0, double rtol, double 
         const bool next_feat = features && !last;
         for (size_t i = 0; i < n; ++i) {
             Pulse &pu = ctx->pulses[i];
-            CK(launch_diff_norm<T>((const cx<T> *)pu.work1, (const cx<T> *)pu.work2, pu.g.nr, pu.g.nt, pu.rows,
-                                   pu.red, ctx->st), "error norm");
-            CK(cudaMemcpyAsync(H + 16 * i, pu.red, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->st), "norm copy");
             if (next_feat) {
-                // the closing row launch left this pulse's statistics of work2
+                // the closing row launch left this pulse's statistics of work2:
+                // norm, features, proposal and energy in one kernel (behind
+                // the per-row norm partials) and one copy; the network runs
+                // only when its proposal can be taken (no cooldown)
                 sc[i].peak_prev = peak[i];
                 sc[i].dz_prev = h;
                 sc[i].dz_lo = std::fmax(0.2 * h, dz_min);
                 sc[i].dz_hi = 2.0 * h;
-                CK(launch_reduce_stats(pu.stats, pu.g.nr, pu.red + 8, ctx->st), "feature reduction");
-                CK(launch_mlp_propose(pu.red + 8, sc[i], ctx->mlp, feat_d(i), dz_d(i), ctx->st, pu.red), "features");
-                CK(cudaMemcpyAsync(H + 16 * i + 8, feat_d(i), 8 * sizeof(float), cudaMemcpyDeviceToHost, ctx->st),
-                   "features copy");
-                CK(cudaMemcpyAsync(H + 16 * i + 12, dz_d(i), sizeof(double), cudaMemcpyDeviceToHost, ctx->st),
-                   "proposal copy");
-                CK(cudaMemcpyAsync(H + 16 * i + 13, pu.red + 8, sizeof(double), cudaMemcpyDeviceToHost, ctx->st),
-                   "energy copy");
+                double *ctl = reinterpret_cast<double *>(ctx->batch_io + 64 * i);
+                CK(launch_diff_rows<T>((const cx<T> *)pu.work1, (const cx<T> *)pu.work2, pu.g.nr, pu.g.nt,
+                                       pu.rows, ctx->st),
+                   "error norm");
+                CK(launch_mlp_step_control(pu.stats, pu.g.nr, pu.rows, sc[i], cooldown == 0 ? ctx->mlp : nullptr,
+                                           ctl, ctx->st),
+                   "controller");
+                CK(cudaMemcpyAsync(H + 16 * i, ctl, 8 * sizeof(double), cudaMemcpyDeviceToHost, ctx->st),
+                   "controller copy");
+            } else {
+                CK(launch_diff_norm<T>((const cx<T> *)pu.work1, (const cx<T> *)pu.work2, pu.g.nr, pu.g.nt,
+                                       pu.rows, pu.red, ctx->st), "error norm");
+                CK(cudaMemcpyAsync(H + 16 * i, pu.red, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->st),
+                   "norm copy");
             }
         }
         CK(cudaStreamSynchronize(ctx->st), "norm sync");
@@ -1393,11 +1409,11 @@ int propagate_batch(fcn_ctx *ctx, double z_end, double dz0, double rtol, double 
                 double prop = 0.0;
                 for (size_t i = 0; i < n; ++i) {
                     float hf[8];
-                    std::memcpy(hf, H + 16 * i + 8, sizeof hf);
+                    std::memcpy(hf, H + 16 * i + 2, sizeof hf);
                     peak[i] = hf[7];
                     sc[i].err_prev = erri[i];
-                    sc[i].e_prev = H[16 * i + 13];
-                    const double p = H[16 * i + 12];
+                    sc[i].e_prev = H[16 * i + 7];
+                    const double p = H[16 * i + 6];
                     if (std::isfinite(p) && p > 0) prop = prop > 0 ? std::fmin(prop, p) : p;
                 }
                 if (cooldown > 0) {
@@ -1451,28 +1467,18 @@ int propagate_impl(fcn_ctx *ctx, double z_end, double dz0, double rtol, double d
     if (!pu.work2) CK(cudaMalloc(&pu.work2, bytes), "work buffer");
     const bool features = controller == 1 || ctx->log_buf != nullptr;
     if (features && !ctx->mlp_io) CK(cudaMalloc(&ctx->mlp_io, 64), "controller buffer");
-    float *feat_d = reinterpret_cast<float *>(ctx->mlp_io);
-    double *dz_d = reinterpret_cast<double *>(ctx->mlp_io + 32);
     const Consts cs = derive(pu.g, pu.p);
     MlpScalars sc;
     std::memset(&sc, 0, sizeof sc);
     sc.rtol = rtol;
     sc.l_ref = cs.k0 * (pu.g.r_max / 5.0) * (pu.g.r_max / 5.0) / 2.0;
     sc.domega = cs.domega;
-    // hfeat: f0..f5, fE and the peak intensity of the current state;
-    // host_red[8..11] receives them, [12] the proposal, [13] the energy sum
+    // hfeat: f0..f5, fE and the peak intensity of the current state.  The
+    // controller kernel leaves [norm0, norm1, hfeat (4 doubles), proposal,
+    // energy sum] in ctl_d, which comes back in one copy into host_red[0..7]
     float hfeat[8] = {0};
     double mlp_dz = 0.0;
-    auto copy_features = [&](bool propose) -> int {
-        CK(cudaMemcpyAsync(ctx->host_red + 8, feat_d, 8 * sizeof(float), cudaMemcpyDeviceToHost, ctx->st),
-           "features copy");
-        CK(cudaMemcpyAsync(ctx->host_red + 13, pu.red + 8, sizeof(double), cudaMemcpyDeviceToHost, ctx->st),
-           "energy copy");
-        if (propose)
-            CK(cudaMemcpyAsync(ctx->host_red + 12, dz_d, sizeof(double), cudaMemcpyDeviceToHost, ctx->st),
-               "proposal copy");
-        return FCN_OK;
-    };
+    double *ctl_d = reinterpret_cast<double *>(ctx->mlp_io);
     if (features) {
         // references from the field at the start of the run
         int rc = diag_device<T>(ctx, pu, pu.field);
@@ -1484,12 +1490,11 @@ int propagate_impl(fcn_ctx *ctx, double z_end, double dz0, double rtol, double d
         sc.e_prev = ctx->host_red[0];
         sc.dz_prev = dz0;
         sc.err_prev = rtol;
-        CK(launch_reduce_stats(pu.stats, pu.g.nr, pu.red + 8, ctx->st), "feature reduction");
-        CK(launch_mlp_propose(pu.red + 8, sc, nullptr, feat_d, dz_d, ctx->st), "features");
-        rc = copy_features(false);
-        if (rc) return rc;
+        CK(launch_mlp_step_control(pu.stats, pu.g.nr, nullptr, sc, nullptr, ctl_d, ctx->st), "features");
+        CK(cudaMemcpyAsync(ctx->host_red, ctl_d, 8 * sizeof(double), cudaMemcpyDeviceToHost, ctx->st),
+           "features copy");
         CK(cudaStreamSynchronize(ctx->st), "features sync");
-        std::memcpy(hfeat, ctx->host_red + 8, 8 * sizeof(float));
+        std::memcpy(hfeat, ctx->host_red + 2, 8 * sizeof(float));
     }
     fcn_stats s;
     std::memset(&s, 0, sizeof s);
@@ -1519,24 +1524,29 @@ int propagate_impl(fcn_ctx *ctx, double z_end, double dz0, double rtol, double d
         const bool next_feat = features && !last;
         if (!rc) rc = substeps<T>(ctx, pu, pu.work2, 0.5 * h, 2, tab2, ev2, 0);
         if (rc) return rc;
-        CK(launch_diff_norm<T>((const cx<T> *)pu.work1, (const cx<T> *)pu.work2, pu.g.nr, pu.g.nt,
-                               pu.rows, pu.red, ctx->st), "error norm");
         if (next_feat) {
-            // speculative: the features of work2 and the proposal after it,
-            // used only if the attempt is accepted
+            // the norm, the features of work2 and (speculative, used only
+            // if the attempt is accepted) the proposal after it: one kernel
+            // behind the per-row norm partials, one copy.  The network runs
+            // only when its proposal can be taken (no cooldown).
             sc.peak_prev = hfeat[7];
             sc.dz_prev = h;
             sc.dz_lo = std::fmax(0.2 * h, dz_min);
             sc.dz_hi = 2.0 * h;
-            CK(launch_reduce_stats(pu.stats, pu.g.nr, pu.red + 8, ctx->st), "feature reduction");
-            CK(launch_mlp_propose(pu.red + 8, sc, controller == 1 ? ctx->mlp : nullptr, feat_d, dz_d, ctx->st,
-                                  pu.red),
-               "features");
-            const int crc = copy_features(controller == 1);
-            if (crc) return crc;
+            CK(launch_diff_rows<T>((const cx<T> *)pu.work1, (const cx<T> *)pu.work2, pu.g.nr, pu.g.nt, pu.rows,
+                                   ctx->st),
+               "error norm");
+            CK(launch_mlp_step_control(pu.stats, pu.g.nr, pu.rows, sc,
+                                       controller == 1 && cooldown == 0 ? ctx->mlp : nullptr, ctl_d, ctx->st),
+               "controller");
+            CK(cudaMemcpyAsync(ctx->host_red, ctl_d, 8 * sizeof(double), cudaMemcpyDeviceToHost, ctx->st),
+               "controller copy");
+        } else {
+            CK(launch_diff_norm<T>((const cx<T> *)pu.work1, (const cx<T> *)pu.work2, pu.g.nr, pu.g.nt,
+                                   pu.rows, pu.red, ctx->st), "error norm");
+            CK(cudaMemcpyAsync(ctx->host_red, pu.red, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->st),
+               "norm copy");
         }
-        CK(cudaMemcpyAsync(ctx->host_red, pu.red, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->st),
-           "norm copy");
         CK(cudaStreamSynchronize(ctx->st), "norm sync");
         const double err = ctx->host_red[1] > 0 ? std::sqrt(ctx->host_red[0] / ctx->host_red[1])
                                                 : std::sqrt(ctx->host_red[0]);
@@ -1563,11 +1573,11 @@ int propagate_impl(fcn_ctx *ctx, double z_end, double dz0, double rtol, double d
             dz = last ? dz : h * fac;
             bool proposed = false;
             if (next_feat) {
-                std::memcpy(hfeat, ctx->host_red + 8, 8 * sizeof(float));
+                std::memcpy(hfeat, ctx->host_red + 2, 8 * sizeof(float));
                 sc.err_prev = err;
-                sc.e_prev = ctx->host_red[13];
+                sc.e_prev = ctx->host_red[7];
                 if (controller == 1) {
-                    mlp_dz = ctx->host_red[12];
+                    mlp_dz = ctx->host_red[6];
                     if (cooldown > 0) {
                         --cooldown;
                     } else if (std::isfinite(mlp_dz) && mlp_dz > 0) {

@@ -224,10 +224,82 @@ struct RowMultiArgs {
 // Row 0 (symmetry axis): sl = 0, sh = c0 = 4s, d = 1; rows 1..Nr-2:
 // sl = s lo_j, sh = s hi_j, c0 = 2s, d = 1; the boundary row Nr-1 and the
 // padding rows of a ragged last chunk are all zero (A = 0 there).
+//
+// In FP32 the explicit side takes every coefficient as a two-float pair
+// (hi + lo, lo = the FP32 rounding error of the FP64 value): rounded once,
+// sl, sh and c0 - delta_q would perturb the discrete operator itself by
+// ~6e-8 the same way at every z-step, an error that adds up coherently
+// over a run (it was the largest systematic FP32 error of a step).  sll and
+// shl hold the lo parts of sl and sh; the pair of c0 - delta_q is formed per
+// column from the FP64 s and dk (CdCol).  The sweep factors keep sl and sh.
 template <typename T>
-struct alignas(4 * sizeof(T)) CnCoef {
+struct alignas(8 * sizeof(T)) CnCoef {
     T sl, sh, c0, d;
+    T sll, shl, pad0, pad1;
 };
+
+// c0 - delta_q of one column as two-float pairs, for the axis row (c0 = 4s)
+// and the interior rows (c0 = 2s); in FP64 the lo parts are zero.
+template <typename T>
+struct CdCol {
+    T ah, al, ih, il;
+};
+template <typename T>
+__device__ __forceinline__ CdCol<T> cd_col(double s, double dk, int qq) {
+    const double dl = dk * double(qq) * double(qq);
+    const double a = 4.0 * s - dl, i = 2.0 * s - dl;
+    CdCol<T> c;
+    c.ah = T(a);
+    c.ih = T(i);
+    c.al = T(a - double(c.ah));
+    c.il = T(i - double(c.ih));
+    return c;
+}
+
+// The explicit side of one row: sl, sh, cd = d (c0 - delta_q) and their lo
+// parts (all zero in FP64 and for rows without a CnCoef row).
+template <typename T>
+struct ExRow {
+    T sl, sh, cd, d, sll, shl, cdl;
+};
+template <typename T>
+__device__ __forceinline__ ExRow<T> ex_row(const CnCoef<T> &cf, bool axis, const CdCol<T> &c) {
+    ExRow<T> e;
+    e.sl = cf.sl;
+    e.sh = cf.sh;
+    e.d = cf.d;
+    e.cd = cf.d * (axis ? c.ah : c.ih);
+    if constexpr (sizeof(T) == 4) {
+        e.sll = cf.sll;
+        e.shl = cf.shl;
+        e.cdl = cf.d * (axis ? c.al : c.il);
+    } else {
+        e.sll = e.shl = e.cdl = T(0);
+    }
+    return e;
+}
+// w = sl xm + sh xp - cd x0 for one real component; in FP32 the lo-part
+// products go first, then the hi parts accumulate onto them through FMAs.
+template <typename T>
+__device__ __forceinline__ T ex_w(const ExRow<T> &e, T xm, T xp, T x0) {
+    if constexpr (sizeof(T) == 4) {
+        float t = e.sll * xm;
+        t = fmaf(e.shl, xp, t);
+        t = fmaf(-e.cdl, x0, t);
+        t = fmaf(e.sl, xm, t);
+        t = fmaf(e.sh, xp, t);
+        return fmaf(-e.cd, x0, t);
+    } else {
+        return e.sl * xm + e.sh * xp - e.cd * x0;
+    }
+}
+// rhs_j = d x0 + i w for one pulse
+template <typename T>
+__device__ __forceinline__ cx<T> ex_rhs(const ExRow<T> &e, cx<T> xm, cx<T> x0, cx<T> xp) {
+    const T wx = ex_w(e, xm.x, xp.x, x0.x);
+    const T wy = ex_w(e, xm.y, xp.y, x0.y);
+    return mk(e.d * x0.x - wy, e.d * x0.y + wx);
+}
 
 template <typename T>
 struct ColArgs {
@@ -239,6 +311,7 @@ struct ColArgs {
     int nr, nt;
     T s;                     // dz / (4 k0 dr^2), 0 without diffraction
     T dk;                    // k'' dz/4 domega^2, 0 without dispersion: delta_q = dk q^2
+    double s64 = 0.0, dk64 = 0.0;   // the same in FP64 (the coef variants' c0 - delta_q)
     double disp = 0.0;       // FCN_EXACT_DISPERSION: dk goes here instead, and the
                              // stage multiplies column q by exp(2 i disp q^2)
     int variant;             // 0..3: register chunks, long/short x CTA 256/512;
@@ -328,6 +401,7 @@ struct XYLine {
     long long total;         // elements of the field buffer
     T s;                     // dz / (4 k0 h^2), 0 without diffraction
     T dk;                    // delta_q = dk q^2 (0 in a line without dispersion)
+    double s64, dk64;        // s and dk in FP64 (two-float explicit side in FP32)
     double disp;             // exact dispersion factor exp(2 i disp q^2), 0: none
     // chunk length L (long: 16 nodes in FP32, 8 in FP64; short: half),
     // lines per thread NP and CTA size: 0 long/1/512, 1 short/1/512,
@@ -349,11 +423,14 @@ int mlp_nparam();
 cudaError_t launch_mlp_grad(const float *W, const float *X, const float *Y, const int *idx, int n,
                             float *partial, int max_cta, float *grad, float *loss, cudaStream_t st);
 cudaError_t launch_mlp_adam(float *W, float *m, float *v, const float *g, float lr, int t, cudaStream_t st);
-// features (8 floats: f0..f5, fE and the peak intensity) and, with W, dz_out;
-// with norm non-null the error of f5 is sqrt(norm[0] / norm[1]) (the step-
-// doubling norm on the device) instead of sc.err_prev
-cudaError_t launch_mlp_propose(const double *red, const MlpScalars &sc, const float *W, float *features,
-                               double *dz_out, cudaStream_t st, const double *norm = nullptr);
+// One attempt's controller outputs in one launch of 256 threads: the
+// step-doubling norm from the per-row partials diff_rows (summed as
+// launch_diff_norm does; null: no norm), the reduction of the per-row
+// statistics (nr rows of NSTAT), the features and, with W, the proposal;
+// out (8 doubles): [norm0, norm1, 8 feature floats in 4 doubles (f0..f5,
+// fE, peak), dz, energy sum]
+cudaError_t launch_mlp_step_control(const double *stats, int nr, const double *diff_rows, const MlpScalars &sc,
+                                    const float *W, double *out, cudaStream_t st);
 
 // reductions and conversions
 template <typename T>
@@ -370,6 +447,41 @@ cudaError_t launch_reduce_stats(const double *stats, int nr, double *out, cudaSt
 cudaError_t launch_reduce_stats_flat(const double *stats, int nrows, int axis_row, double *out,
                                      cudaStream_t st);
 // Per-row sums of |a-b|^2 and |b|^2 (FP64) then the final reduction into out[0..1].
+// Radial weight of row m in the energy sums (1/8 at the axis, m beyond).
+__device__ __forceinline__ double radial_weight(int m) { return m == 0 ? 0.125 : double(m); }
+
+// Block-wide FP64 sum / maximum with a fixed shuffle and shared-memory tree
+// (bit-identical from run to run); result in thread 0; every thread of the
+// block calls it; sh holds 32 doubles.
+__device__ __forceinline__ double block_sum(double x, double *sh) {
+    for (int d = 16; d >= 1; d >>= 1) x += __shfl_down_sync(0xffffffffu, x, d);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) sh[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        x = (l < (int)(blockDim.x >> 5)) ? sh[l] : 0.0;
+        for (int d = 16; d >= 1; d >>= 1) x += __shfl_down_sync(0xffffffffu, x, d);
+    }
+    return x;
+}
+__device__ __forceinline__ double block_max(double x, double *sh) {
+    for (int d = 16; d >= 1; d >>= 1) x = fmax(x, __shfl_down_sync(0xffffffffu, x, d));
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) sh[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        x = (l < (int)(blockDim.x >> 5)) ? sh[l] : 0.0;
+        for (int d = 16; d >= 1; d >>= 1) x = fmax(x, __shfl_down_sync(0xffffffffu, x, d));
+    }
+    return x;
+}
+
+// Per-row partials of the step-doubling norm: rows[2m] = sum_p |a - b|^2,
+// rows[2m+1] = sum_p |b|^2 (the first kernel of launch_diff_norm).
+template <typename T>
+cudaError_t launch_diff_rows(const cx<T> *a, const cx<T> *b, int nr, int nt, double *rows, cudaStream_t st);
 template <typename T>
 cudaError_t launch_diff_norm(const cx<T> *a, const cx<T> *b, int nr, int nt, double *rows,
                              double *out, cudaStream_t st);

@@ -9,34 +9,6 @@ namespace {
 
 constexpr int RT = 256;   // threads of the reduction CTAs
 
-__device__ __forceinline__ double radial_weight(int m) { return m == 0 ? 0.125 : double(m); }
-
-// Block-wide sum with a fixed shuffle/shared tree; result in thread 0.
-__device__ __forceinline__ double block_sum(double x, double *sh) {
-    for (int d = 16; d >= 1; d >>= 1) x += __shfl_down_sync(0xffffffffu, x, d);
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    __syncthreads();
-    if (l == 0) sh[w] = x;
-    __syncthreads();
-    if (w == 0) {
-        x = (l < (int)(blockDim.x >> 5)) ? sh[l] : 0.0;
-        for (int d = 16; d >= 1; d >>= 1) x += __shfl_down_sync(0xffffffffu, x, d);
-    }
-    return x;
-}
-
-__device__ __forceinline__ double block_max(double x, double *sh) {
-    for (int d = 16; d >= 1; d >>= 1) x = fmax(x, __shfl_down_sync(0xffffffffu, x, d));
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    __syncthreads();
-    if (l == 0) sh[w] = x;
-    __syncthreads();
-    if (w == 0) {
-        x = (l < (int)(blockDim.x >> 5)) ? sh[l] : 0.0;
-        for (int d = 16; d >= 1; d >>= 1) x = fmax(x, __shfl_down_sync(0xffffffffu, x, d));
-    }
-    return x;
-}
 
 template <typename T>
 __global__ void widen_kernel(const cx<T> *src, double *dst, int64_t n) {
@@ -190,6 +162,11 @@ cudaError_t launch_reduce_stats_flat(const double *stats, int nrows, int axis_ro
     return cudaGetLastError();
 }
 template <typename T>
+cudaError_t launch_diff_rows(const cx<T> *a, const cx<T> *b, int nr, int nt, double *rows, cudaStream_t st) {
+    diff_rows_kernel<T><<<nr, RT, 0, st>>>(a, b, nt, rows);
+    return cudaGetLastError();
+}
+template <typename T>
 cudaError_t launch_diff_norm(const cx<T> *a, const cx<T> *b, int nr, int nt, double *rows,
                              double *out, cudaStream_t st) {
     diff_rows_kernel<T><<<nr, RT, 0, st>>>(a, b, nt, rows);
@@ -208,6 +185,8 @@ cudaError_t launch_profiles(const cx<T> *f, int nr, int nt, double *power, doubl
     template cudaError_t launch_widen<T>(const cx<T> *, double *, int64_t, cudaStream_t);  \
     template cudaError_t launch_narrow<T>(const double *, cx<T> *, int64_t, cudaStream_t); \
     template cudaError_t launch_widen_real<T>(const T *, double *, int64_t, cudaStream_t); \
+    template cudaError_t launch_diff_rows<T>(const cx<T> *, const cx<T> *, int, int, double *, \
+                                             cudaStream_t);                                \
     template cudaError_t launch_diff_norm<T>(const cx<T> *, const cx<T> *, int, int, double *, \
                                              double *, cudaStream_t);                      \
     template cudaError_t launch_profiles<T>(const cx<T> *, int, int, double *, double *,   \

@@ -149,6 +149,8 @@ XYLine<T> line_args(fcn_xy_ctx *ctx, void *field, int axis, double dz) {
     }
     a.s = T(s);
     a.dk = T(dk);
+    a.s64 = s;
+    a.dk64 = dk;
     a.disp = disp;
     a.variant = ctx->line_var;
     return a;
@@ -542,6 +544,20 @@ int fcn_xy_get_field_c64(fcn_xy_ctx *ctx, float *host) {
         CK(cudaMemcpyAsync(host, ctx->stage, 8 * np, cudaMemcpyDeviceToHost, ctx->st), "D2H field");
     }
     CK(cudaStreamSynchronize(ctx->st), "sync");
+    return FCN_OK;
+}
+
+int fcn_xy_set_field_device(fcn_xy_ctx *ctx, const void *dev) {
+    if (!ctx || !dev) return fail(ctx, FCN_ERR_ARG, "null context or buffer");
+    const size_t bytes = (ctx->prec == FCN_FP64 ? 16 : 8) * (size_t)ctx->points();
+    CK(cudaMemcpyAsync(ctx->field, dev, bytes, cudaMemcpyDeviceToDevice, ctx->st), "D2D field");
+    return reset_state(ctx);
+}
+
+int fcn_xy_get_field_device(fcn_xy_ctx *ctx, void *dev) {
+    if (!ctx || !dev) return fail(ctx, FCN_ERR_ARG, "null context or buffer");
+    const size_t bytes = (ctx->prec == FCN_FP64 ? 16 : 8) * (size_t)ctx->points();
+    CK(cudaMemcpyAsync(dev, ctx->field, bytes, cudaMemcpyDeviceToDevice, ctx->st), "D2D field");
     return FCN_OK;
 }
 

@@ -71,8 +71,15 @@ xy_line_kernel(XYLine<T> a, int C) {
     const int q = c & (nt - 1);
     const int nq = nt / 2 + 1;
     const int qq = (q <= nt / 2) ? q : nt - q;
+    // interior: e = 1 - i g1, g1 = 2s - delta_q; the explicit side takes s
+    // and g1 as two-float pairs in FP32 (lo = rounding error of the FP64
+    // value), as the radial stage does, so that the rounding of the
+    // coefficients does not perturb the discrete operator the same way at
+    // every step; the sweep factors use s
     const T s = a.s;
-    const T g1 = T(2) * s - a.dk * T(qq) * T(qq);   // interior: e = 1 - i g1
+    const double g1d = 2.0 * a.s64 - a.dk64 * double(qq) * double(qq);
+    const T g1 = T(g1d);
+    const T sl = T(a.s64 - double(s)), g1l = T(g1d - double(g1));
     const int j0 = chunk * L;
     cx<T> *line[NP];
     bool on[NP];
@@ -113,8 +120,14 @@ xy_line_kernel(XYLine<T> a, int C) {
             const cx<T> alpha = cmul_i(inv[k], s);
 #pragma unroll
             for (int i = 0; i < NP; ++i) {
-                const cx<T> w = mk(s * (x[i][k].x + x[i][k + 2].x) - g1 * x[i][k + 1].x,
-                                   s * (x[i][k].y + x[i][k + 2].y) - g1 * x[i][k + 1].y);
+                const cx<T> sum = x[i][k] + x[i][k + 2];
+                cx<T> w;
+                if constexpr (sizeof(T) == 4) {
+                    w.x = fmaf(-g1, x[i][k + 1].x, fmaf(s, sum.x, fmaf(-g1l, x[i][k + 1].x, sl * sum.x)));
+                    w.y = fmaf(-g1, x[i][k + 1].y, fmaf(s, sum.y, fmaf(-g1l, x[i][k + 1].y, sl * sum.y)));
+                } else {
+                    w = mk(s * sum.x - g1 * x[i][k + 1].x, s * sum.y - g1 * x[i][k + 1].y);
+                }
                 const cx<T> rhs = mk(x[i][k + 1].x - w.y, x[i][k + 1].y + w.x);
                 y[i][k] = cmul(rhs, inv[k]);
                 PB[i] = cmul(alpha, PB[i]) + y[i][k];

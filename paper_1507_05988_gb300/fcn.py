@@ -137,6 +137,8 @@ _SIGS = {
     "fcn_xy_get_field": (C.c_int, [_CTX, _D]),
     "fcn_xy_set_field_c64": (C.c_int, [_CTX, _F]),
     "fcn_xy_get_field_c64": (C.c_int, [_CTX, _F]),
+    "fcn_xy_set_field_device": (C.c_int, [_CTX, _P]),
+    "fcn_xy_get_field_device": (C.c_int, [_CTX, _P]),
     "fcn_xy_get_rho": (C.c_int, [_CTX, _D]),
     "fcn_xy_step": (C.c_int, [_CTX, C.c_double, C.c_int64]),
     "fcn_xy_step_nograph": (C.c_int, [_CTX, C.c_double, C.c_int64]),
@@ -446,6 +448,15 @@ class SolverXY:
         out = np.empty(self.shape, np.complex64) if out is None else out
         check_xy(fcn_xy_get_field_c64(self.ctx, out.ctypes.data_as(_F)), self.ctx)
         return out
+
+    def set_field_device(self, t):
+        """From a contiguous CUDA tensor in the working precision."""
+        check_xy(fcn_xy_set_field_device(self.ctx, tensor_ptr(t)), self.ctx)
+
+    def get_field_device(self, t):
+        """Into a contiguous CUDA tensor in the working precision."""
+        check_xy(fcn_xy_get_field_device(self.ctx, tensor_ptr(t)), self.ctx)
+        return t
 
     def get_rho(self) -> np.ndarray:
         out = np.empty(self.shape, np.float64)

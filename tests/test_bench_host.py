@@ -40,6 +40,13 @@ class _Solver:
     def get_field(self):
         return self.a
 
+    def get_field_device(self, t):
+        t.copy_(torch.from_numpy(np.asarray(self.a, np.complex128)))
+        return t
+
+    def set_field_device(self, t):
+        self.a = t.numpy().copy()
+
     def diag(self):
         return {"energy": float(np.sum(np.abs(self.a) ** 2))}
 
@@ -61,6 +68,7 @@ class _Solver:
 def fake_cuda(monkeypatch):
     monkeypatch.setattr(torch.cuda, "Event", _Event)
     monkeypatch.setattr(torch.cuda, "synchronize", lambda: None)
+    monkeypatch.setattr(bench, "PERTURB_DEVICE", "cpu")
 
 
 def test_cartesian_leg_reports_throughput_kernels_roofline_accuracy(fake_cuda):
@@ -82,7 +90,13 @@ def test_cartesian_leg_reports_throughput_kernels_roofline_accuracy(fake_cuda):
     assert [c["steps"] for c in acc["checkpoints"]] == [25, 50, 100, 150, 200]
     # the stand-in's FP32 drift after 200 steps
     assert acc["field_rel_l2"] == pytest.approx((1 + 1e-7) ** 200 - 1, rel=1e-6)
-    assert acc["checkpoints"][0]["fp64_perturbed_field_rel_l2"] < 1e-7
+    # the reference is perturbed by 6e-8 xi after every step: a random walk
+    # of ~6e-8 / sqrt(3) per step
+    c0, c4 = acc["checkpoints"][0], acc["checkpoints"][4]
+    assert 1e-8 < c0["fp64_perturbed_field_rel_l2"] < 6e-8 * 25 ** 0.5
+    assert c4["fp64_perturbed_field_rel_l2"] > c0["fp64_perturbed_field_rel_l2"]
+    assert c4["fp32_over_reference"] == pytest.approx(
+        c4["fp32_field_rel_l2"] / c4["fp64_perturbed_field_rel_l2"])
 
 
 def test_weak_scaling_counts_every_rank():
