@@ -266,11 +266,13 @@ int fcn_get_pairing(const fcn_ctx *ctx);
  * warp and two pulses per thread, rows streamed through shared memory by
  * TMA, all pulses in one launch; the row stage then runs as one launch over
  * all pulses per z-step as in fcn_set_multi_launch mode 1.
- * mode 1 on, 0 off, -1 (default) decided on the first step by timing one
- * such launch against the per-group launches of the tuned column variant
- * (on scratch copies).  Graph branches > 1 turn it off.  Drops the captured
- * graphs.  fcn_get_sequential_columns returns the decision: 1, 0, or -1
- * before the first step. */
+ * mode 1 on, 0 off, -1 (default) decided on the first step by timing such
+ * launches (each ring shape: rows per stage against warps per SM) against
+ * the per-group launches of the tuned column variant (on scratch copies),
+ * keeping the fastest; 2, 3, 4: on with ring shape 0, 1, 2 (1: shape 0).
+ * Graph branches > 1 turn it off.  Drops the captured graphs.
+ * fcn_get_sequential_columns returns the decision: 1, 0, or -1 before the
+ * first step.  Other modes: FCN_ERR_ARG. */
 int fcn_set_sequential_columns(fcn_ctx *ctx, int32_t mode);
 int fcn_get_sequential_columns(const fcn_ctx *ctx);
 

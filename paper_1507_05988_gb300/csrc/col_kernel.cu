@@ -141,6 +141,13 @@ __global__ void cn_table_kernel_f32(TableArgs a, cx<float> *table) {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= nq) return;
     const double delta = a.dk * double(q) * double(q);
+    if (a.cc) {
+        const cx<double> lim = piv_limit(a.s, a.dk, q);
+        const CdCol<float> c = cd_col<float>(a.s, a.dk, q);
+        const float hx = float(lim.x), hy = float(lim.y);
+        a.cc[q].lim = make_float4(hx, hy, float(lim.x - double(hx)), float(lim.y - double(hy)));
+        a.cc[q].cd = make_float4(c.ah, c.al, c.ih, c.il);
+    }
     const f2 by0 = to_f2(4.0 * a.s - delta), by1 = to_f2(2.0 * a.s - delta);
     f2 ix = {0.f, 0.f}, iy = {0.f, 0.f};
     const f2 one = {1.f, 0.f};
@@ -153,7 +160,16 @@ __global__ void cn_table_kernel_f32(TableArgs a, cx<float> *table) {
         ix = df_mul(wx, rn);
         iy = df_mul(wy, rn);
         iy = {-iy.h, -iy.l};
-        table[FCN_IDX((size_t)j * tp + q, (size_t)a.nr * tp, 30)] = mk(ix.h + ix.l, iy.h + iy.l);
+        cx<float> e;
+        if (a.pivlim) {
+            // relative to the column's limit (piv_limit), in FP64 from the
+            // double-float value
+            const cx<double> lim = piv_limit(a.s, a.dk, q);
+            e = mk(float((double(ix.h) + double(ix.l)) - lim.x), float((double(iy.h) + double(iy.l)) - lim.y));
+        } else {
+            e = mk(ix.h + ix.l, iy.h + iy.l);
+        }
+        table[FCN_IDX((size_t)j * tp + q, (size_t)a.nr * tp, 30)] = e;
     }
 }
 
@@ -200,7 +216,9 @@ __device__ __forceinline__ void cn_body(const ColArgs<T> &a, int C, int g, unsig
     const int nq = a.tp;
     const int qq = (q <= nt / 2) ? q : nt - q;
     const T delta = a.dk * T(qq) * T(qq);
-    const CdCol<T> cdc = cd_col<T>(a.s64, a.dk64, qq);
+    CdCol<T> cdc;
+    PivLim<T> plim;
+    col_consts<T>(a.cc, a.pivlim, a.s64, a.dk64, qq, &cdc, &plim);
     const int j0 = chunk * L;
 
     cx<T> x[L + 2];
@@ -209,11 +227,13 @@ __device__ __forceinline__ void cn_body(const ColArgs<T> &a, int C, int g, unsig
         const int j = j0 - 1 + k;
         x[k] = (j >= 0 && j < nr) ? a.field[FCN_IDX((size_t)j * nt + q, (size_t)nr * nt, 33)] : czero<T>();
     }
-    cx<T> inv[L];
+    cx<T> inv[L];       // table entries (rhs / pivot by piv_apply)
+    cx<T> ivf[L];       // 1/pivot rounded, for the sweep factors
 #pragma unroll
     for (int k = 0; k < L; ++k) {
         const int j = j0 + k;
         inv[k] = (j < nr) ? ldg_cx(&a.invden[FCN_IDX((size_t)j * nq + qq, (size_t)nr * nq, 34)]) : czero<T>();
+        ivf[k] = (j < nr) ? piv_full(inv[k], plim) : czero<T>();
     }
 
     // forward sweep, pass 1: beta_j and the chunk map y_end = PA y_in + PB
@@ -225,8 +245,8 @@ __device__ __forceinline__ void cn_body(const ColArgs<T> &a, int C, int g, unsig
         if (j < nr) {
             const ExRow<T> c = row_co(a, j, delta, cdc);
             const cx<T> rhs = ex_rhs(c, x[k], x[k + 1], x[k + 2]);
-            const cx<T> alpha = cmul_i(inv[k], c.sl);
-            y[k] = cmul(rhs, inv[k]);
+            const cx<T> alpha = cmul_i(ivf[k], c.sl);
+            y[k] = piv_apply(rhs, inv[k], plim);
             PB = cmul(alpha, PB) + y[k];
             PA = cmul(alpha, PA);
         } else {
@@ -240,7 +260,7 @@ __device__ __forceinline__ void cn_body(const ColArgs<T> &a, int C, int g, unsig
         for (int k = 0; k < L; ++k) {
             const int j = j0 + k;
             if (j < nr) {
-                const cx<T> alpha = cmul_i(inv[k], row_co(a, j, delta, cdc).sl);
+                const cx<T> alpha = cmul_i(ivf[k], row_co(a, j, delta, cdc).sl);
                 y[k] = cmul(alpha, yp) + y[k];
                 yp = y[k];
             }
@@ -252,7 +272,7 @@ __device__ __forceinline__ void cn_body(const ColArgs<T> &a, int C, int g, unsig
     for (int k = L - 1; k >= 0; --k) {
         const int j = j0 + k;
         if (j < nr) {
-            const cx<T> gamma = cmul_i(inv[k], row_co(a, j, delta, cdc).sh);
+            const cx<T> gamma = cmul_i(ivf[k], row_co(a, j, delta, cdc).sh);
             QB = cmul(gamma, QB) + y[k];
             QA = cmul(gamma, QA);
         }
@@ -265,7 +285,7 @@ __device__ __forceinline__ void cn_body(const ColArgs<T> &a, int C, int g, unsig
         for (int k = L - 1; k >= 0; --k) {
             const int j = j0 + k;
             if (j < nr) {
-                const cx<T> gamma = cmul_i(inv[k], row_co(a, j, delta, cdc).sh);
+                const cx<T> gamma = cmul_i(ivf[k], row_co(a, j, delta, cdc).sh);
                 xn = cmul(gamma, xn) + y[k];
                 a.field[FCN_IDX((size_t)j * nt + q, (size_t)nr * nt, 37)] = disp_apply(xn, ph);
             }
@@ -356,7 +376,8 @@ constexpr size_t kCnStagedSmemMax = 227 * 1024;
 // hoists the loads of the unrolled loop), alpha_j and gamma_j go to the
 // thread's shared-memory slots.  EDGE: the chunk touches row -1 or row nr.
 template <typename T, int L, bool EDGE, int NTC>
-__device__ __forceinline__ void cn_f1_reg(const ColArgs<T> &a, int q, int qq, int j0, const CdCol<T> &cdc, cx<T> *At,
+__device__ __forceinline__ void cn_f1_reg(const ColArgs<T> &a, int q, int qq, int j0, const CdCol<T> &cdc,
+                                          const PivLim<T> &plim, cx<T> *At,
                                           cx<T> *Gt, int BD, cx<T> (&y)[L], cx<T> &PA, cx<T> &PB) {
     // NTC: Nt as a compile-time constant (row strides become immediates), 0: a.nt
     const int nt = NTC ? NTC : a.nt, nr = a.nr, nq = a.tp;
@@ -380,10 +401,11 @@ __device__ __forceinline__ void cn_f1_reg(const ColArgs<T> &a, int q, int qq, in
             cf = CnCoef<T>{};
         }
         const cx<T> rhs = ex_rhs(ex_row(cf, j == 0, cdc), xm, x0, xp);
-        const cx<T> beta = cmul(rhs, inv);
-        const cx<T> al = cmul_i(inv, cf.sl);
+        const cx<T> beta = piv_apply(rhs, inv, plim);
+        const cx<T> ivf = piv_full(inv, plim);
+        const cx<T> al = cmul_i(ivf, cf.sl);
         At[k * BD] = al;
-        Gt[k * BD] = cmul_i(inv, cf.sh);
+        Gt[k * BD] = cmul_i(ivf, cf.sh);
         PB = cmul(al, PB) + beta;
         PA = cmul(al, PA);
         y[k] = beta;
@@ -411,7 +433,9 @@ __device__ __forceinline__ void cn_staged_body(const ColArgs<T> &a, int C, int g
     const int nt = NTC ? NTC : a.nt, nr = a.nr;
     const int nq = a.tp;
     const int qq = (q <= nt / 2) ? q : nt - q;
-    const CdCol<T> cdc = cd_col<T>(a.s64, a.dk64, qq);
+    CdCol<T> cdc;
+    PivLim<T> plim;
+    col_consts<T>(a.cc, a.pivlim, a.s64, a.dk64, qq, &cdc, &plim);
     const int j0 = chunk * L;
 
     cx<T> y[L];
@@ -420,9 +444,9 @@ __device__ __forceinline__ void cn_staged_body(const ColArgs<T> &a, int C, int g
     cx<T> *At = REG ? Xt : Xt + BD;
     if constexpr (REG) {
         if (j0 >= 1 && j0 + L < nr)
-            cn_f1_reg<T, L, false, NTC>(a, q, qq, j0, cdc, At, Gt, BD, y, PA, PB);
+            cn_f1_reg<T, L, false, NTC>(a, q, qq, j0, cdc, plim, At, Gt, BD, y, PA, PB);
         else
-            cn_f1_reg<T, L, true, NTC>(a, q, qq, j0, cdc, At, Gt, BD, y, PA, PB);
+            cn_f1_reg<T, L, true, NTC>(a, q, qq, j0, cdc, plim, At, Gt, BD, y, PA, PB);
     } else {
     if (j0 >= 1 && j0 + L < nr) {
         // interior chunk: every row j0-1 .. j0+L exists
@@ -465,10 +489,11 @@ __device__ __forceinline__ void cn_staged_body(const ColArgs<T> &a, int C, int g
             cf = CnCoef<T>{};
         }
         const cx<T> rhs = ex_rhs(ex_row(cf, j == 0, cdc), xm, x0, xp);
-        const cx<T> beta = cmul(rhs, inv);
-        const cx<T> al = cmul_i(inv, cf.sl);
+        const cx<T> beta = piv_apply(rhs, inv, plim);
+        const cx<T> ivf = piv_full(inv, plim);
+        const cx<T> al = cmul_i(ivf, cf.sl);
         Xt[(k + 1) * BD] = al;                  // x_j (slot k+1) is no longer read
-        Gt[k * BD] = cmul_i(inv, cf.sh);
+        Gt[k * BD] = cmul_i(ivf, cf.sh);
         PB = cmul(al, PB) + beta;
         PA = cmul(al, PA);
         y[k] = beta;
@@ -593,7 +618,8 @@ cudaError_t launch_cn_l(const ColArgs<T> &a, int target, cudaStream_t st) {
 
 template <typename T, int L, bool EDGE, int NTC>
 __device__ __forceinline__ void cn_f1_pair(const ColArgs<T> &a, const cx<T> *f2, int q, int qq, int j0,
-                                           const CdCol<T> &cdc, cx<T> *At, cx<T> *Gt, int BD, cx<T> (&y1)[L],
+                                           const CdCol<T> &cdc, const PivLim<T> &plim, cx<T> *At, cx<T> *Gt,
+                                           int BD, cx<T> (&y1)[L],
                                            cx<T> (&y2)[L], cx<T> &PA, cx<T> &PB1, cx<T> &PB2) {
     const int nt = NTC ? NTC : a.nt, nr = a.nr, nq = a.tp;
     const cx<T> *fx = a.field + q;
@@ -618,16 +644,17 @@ __device__ __forceinline__ void cn_f1_pair(const ColArgs<T> &a, const cx<T> *f2,
             cf = CnCoef<T>{};
         }
         const ExRow<T> e = ex_row(cf, j == 0, cdc);
-        const cx<T> al = cmul_i(inv, cf.sl);
+        const cx<T> ivf = piv_full(inv, plim);
+        const cx<T> al = cmul_i(ivf, cf.sl);
         At[k * BD] = al;
-        Gt[k * BD] = cmul_i(inv, cf.sh);
+        Gt[k * BD] = cmul_i(ivf, cf.sh);
         {
-            const cx<T> beta = cmul(ex_rhs(e, xm1, x01, xp1), inv);
+            const cx<T> beta = piv_apply(ex_rhs(e, xm1, x01, xp1), inv, plim);
             PB1 = cmul(al, PB1) + beta;
             y1[k] = beta;
         }
         {
-            const cx<T> beta = cmul(ex_rhs(e, xm2, x02, xp2), inv);
+            const cx<T> beta = piv_apply(ex_rhs(e, xm2, x02, xp2), inv, plim);
             PB2 = cmul(al, PB2) + beta;
             y2[k] = beta;
         }
@@ -654,15 +681,17 @@ __device__ __forceinline__ void cn_pair_body(const ColArgs<T> &a, cx<T> *field2,
     const int q = g * C + col;
     const int nt = NTC ? NTC : a.nt, nr = a.nr;
     const int qq = (q <= nt / 2) ? q : nt - q;
-    const CdCol<T> cdc = cd_col<T>(a.s64, a.dk64, qq);
+    CdCol<T> cdc;
+    PivLim<T> plim;
+    col_consts<T>(a.cc, a.pivlim, a.s64, a.dk64, qq, &cdc, &plim);
     const int j0 = chunk * L;
 
     cx<T> y1[L], y2[L];
     cx<T> PA = mk(T(1), T(0)), PB[2] = {czero<T>(), czero<T>()};
     if (j0 >= 1 && j0 + L < nr)
-        cn_f1_pair<T, L, false, NTC>(a, field2, q, qq, j0, cdc, At, Gt, BD, y1, y2, PA, PB[0], PB[1]);
+        cn_f1_pair<T, L, false, NTC>(a, field2, q, qq, j0, cdc, plim, At, Gt, BD, y1, y2, PA, PB[0], PB[1]);
     else
-        cn_f1_pair<T, L, true, NTC>(a, field2, q, qq, j0, cdc, At, Gt, BD, y1, y2, PA, PB[0], PB[1]);
+        cn_f1_pair<T, L, true, NTC>(a, field2, q, qq, j0, cdc, plim, At, Gt, BD, y1, y2, PA, PB[0], PB[1]);
     {
         cx<T> yp[2];
         chunk_scan_n<T, false, 2>(PA, PB, C, col, smA, smB, smC, yp);

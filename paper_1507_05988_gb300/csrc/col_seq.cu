@@ -52,6 +52,8 @@ struct SeqParams {
     const CnCoef<T> *coef;             // [nr]
     int nr, nt, ngroups;
     double s64, dk64;                  // s and dk: c0 - delta_q = {4, 2} s - dk q^2
+    int pivlim;                        // table entries relative to 1/p_inf (ColArgs::pivlim)
+    const ColConst *cc;                // per-column constants (FP32 contexts) or null
     double disp;                       // exact dispersion factor coefficient, 0: none
     int *err;                          // set to 1 when a wait gives up (may be null)
 };
@@ -148,7 +150,9 @@ cn_seq_kernel(const __grid_constant__ SeqParams<T> p) {
     const int qq = mirror ? nt - q : q;
     const int tx = mirror ? nt - q0 - 32 : q0;          // first pivot column of the box
     const int il = mirror ? 32 - lane : lane;           // this lane's pivot column in the box
-    const CdCol<T> cdc = cd_col<T>(p.s64, p.dk64, qq);
+    CdCol<T> cdc;
+    PivLim<T> plim;
+    col_consts<T>(p.cc, p.pivlim, p.s64, p.dk64, qq, &cdc, &plim);
     const CUtensorMap *tmap = &p.tmap;
     cx<T> *col[NP];
 #pragma unroll
@@ -231,11 +235,11 @@ cn_seq_kernel(const __grid_constant__ SeqParams<T> p) {
             const cx<T> inv = I[r * 34 + il];
             const CnCoef<T> cf = Cf[r];
             const ExRow<T> e = ex_row(cf, jb + r == 0, cdc);
-            al[r] = cmul_i(inv, cf.sl);
+            al[r] = cmul_i(piv_full(inv, plim), cf.sl);
 #pragma unroll
             for (int k = 0; k < NP; ++k) {
                 const cx<T> xp = (r + 1 < R) ? stage_x(s, k)[(r + 1) * 32 + lane] : xnext[k];
-                be[k][r] = cmul(ex_rhs(e, xm[k], x0[k], xp), inv);
+                be[k][r] = piv_apply(ex_rhs(e, xm[k], x0[k], xp), inv, plim);
                 xm[k] = x0[k];
                 x0[k] = xp;
             }
@@ -275,7 +279,7 @@ cn_seq_kernel(const __grid_constant__ SeqParams<T> p) {
         cx<T> ga[R], yv[NP][R];
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            ga[r] = cmul_i(I[r * 34 + il], Cf[r].sh);
+            ga[r] = cmul_i(piv_full(I[r * 34 + il], plim), Cf[r].sh);
 #pragma unroll
             for (int k = 0; k < NP; ++k) yv[k][r] = stage_x(s, k)[r * 32 + lane];
         }
@@ -358,6 +362,8 @@ cudaError_t launch_seq_shape(const ColArgs<T> &a, cx<T> *const *fields, int npul
     p.ngroups = a.nt / 32;
     p.s64 = a.s64;
     p.dk64 = a.dk64;
+    p.pivlim = a.pivlim;
+    p.cc = a.cc;
     p.disp = a.disp;
     p.err = a.err;
     const size_t smem = (size_t)W * Ring::kBytes;
@@ -373,15 +379,29 @@ cudaError_t launch_seq_shape(const ColArgs<T> &a, cx<T> *const *fields, int npul
 }
 
 template <typename T>
-cudaError_t launch_cn_seq(const ColArgs<T> &a, cx<T> *const *fields, int npulse, cudaStream_t st) {
+cudaError_t launch_cn_seq(const ColArgs<T> &a, cx<T> *const *fields, int npulse, cudaStream_t st, int shape) {
     if (npulse < 1 || npulse > kSeqMaxPulses || !cn_seq_supported(a)) return cudaErrorInvalidConfiguration;
-    // two pulses per thread when their count is even (measured on 8 pulses
+    // Two pulses per thread when their count is even (measured on 8 pulses
     // of 1024 x 4096: 172 us per launch against 230 us with one pulse per
-    // thread and 190 us with four); rings of 4 stages of 16 rows (FP32) or
-    // 8 rows (FP64); CTAs of two warps, or of four with one pulse per thread
+    // thread and 190 us with four).  Each warp runs its columns' sweeps
+    // with few other warps beside it (the rings take the shared memory), so
+    // the ring shape trades rows in flight per warp against warps per SM;
+    // the autotuner times the shapes (kSeqShapes):
+    //   FP32: 0: 4 stages x 16 rows, 2 warps per CTA (4 warps per SM),
+    //         1: 4 x 8 rows, 4 warps (8 per SM), 2: 4 x 4 rows, 4 warps (16 per SM);
+    //   FP64: 0: 4 x 8 rows, 2 warps, 1: 4 x 4 rows, 4 warps, 2: 4 x 2 rows, 4 warps.
+    // Odd pulse counts: one pulse per thread, 4 x 16 rows and 4 warps (FP32),
+    // 4 x 8 rows and 2 warps (FP64).
     if (npulse % 2 == 0) {
-        if constexpr (sizeof(T) == 4) return launch_seq_shape<T, 16, 4, 2, 2>(a, fields, npulse, st);
-        else return launch_seq_shape<T, 8, 4, 2, 2>(a, fields, npulse, st);
+        if constexpr (sizeof(T) == 4) {
+            if (shape == 1) return launch_seq_shape<T, 8, 4, 4, 2>(a, fields, npulse, st);
+            if (shape == 2) return launch_seq_shape<T, 4, 4, 4, 2>(a, fields, npulse, st);
+            return launch_seq_shape<T, 16, 4, 2, 2>(a, fields, npulse, st);
+        } else {
+            if (shape == 1) return launch_seq_shape<T, 4, 4, 4, 2>(a, fields, npulse, st);
+            if (shape == 2) return launch_seq_shape<T, 2, 4, 4, 2>(a, fields, npulse, st);
+            return launch_seq_shape<T, 8, 4, 2, 2>(a, fields, npulse, st);
+        }
     }
     if constexpr (sizeof(T) == 4) return launch_seq_shape<T, 16, 4, 4, 1>(a, fields, npulse, st);
     else return launch_seq_shape<T, 8, 4, 2, 1>(a, fields, npulse, st);
@@ -389,7 +409,7 @@ cudaError_t launch_cn_seq(const ColArgs<T> &a, cx<T> *const *fields, int npulse,
 
 template bool cn_seq_supported<float>(const ColArgs<float> &);
 template bool cn_seq_supported<double>(const ColArgs<double> &);
-template cudaError_t launch_cn_seq<float>(const ColArgs<float> &, cx<float> *const *, int, cudaStream_t);
-template cudaError_t launch_cn_seq<double>(const ColArgs<double> &, cx<double> *const *, int, cudaStream_t);
+template cudaError_t launch_cn_seq<float>(const ColArgs<float> &, cx<float> *const *, int, cudaStream_t, int);
+template cudaError_t launch_cn_seq<double>(const ColArgs<double> &, cx<double> *const *, int, cudaStream_t, int);
 
 }  // namespace fcn

@@ -360,8 +360,9 @@ struct fcn_ctx {
     int pair_mode = -1, pairs = -1;
     // the sequential column kernel over all pulses in one launch (equal
     // grids, one pivot table): mode -1 decide by timing, 0 off, 1 on;
-    // seq_all is the decision (-1 before the first step)
-    int seq_mode = -1, seq_all = -1;
+    // seq_all is the decision (-1 before the first step), seq_shape the
+    // ring shape the tuner chose for it
+    int seq_mode = -1, seq_all = -1, seq_shape = 0;
     // batched work lists (FP32, K = 8, several pulses): one launch per stage
     bool batched = false;
     int2 *row_items = nullptr;
@@ -410,6 +411,17 @@ size_t coef_offset(int nr, int nt) {
     const size_t b = sizeof(cx<T>) * (size_t)nr * (size_t)table_pitch(nt);
     return (b + 255) / 256 * 256;
 }
+// then, in FP32, the per-column constants (ColConst, table_pitch entries)
+template <typename T>
+size_t cc_offset(int nr, int nt) {
+    const size_t b = coef_offset<T>(nr, nt) + sizeof(CnCoef<T>) * (size_t)nr;
+    return (b + 255) / 256 * 256;
+}
+template <typename T>
+size_t table_bytes(int nr, int nt) {
+    return sizeof(T) == 4 ? cc_offset<T>(nr, nt) + sizeof(ColConst) * (size_t)table_pitch(nt)
+                          : coef_offset<T>(nr, nt) + sizeof(CnCoef<T>) * (size_t)nr;
+}
 
 void drop_graphs(fcn_ctx *ctx, bool all, uint64_t dz);
 
@@ -435,7 +447,7 @@ int ensure_table(fcn_ctx *ctx, Pulse &pu, double dz, const cx<T> **out, int side
         *out = (const cx<T> *)it->second.ptr;
         return FCN_OK;
     }
-    const size_t need = coef_offset<T>(pu.g.nr, pu.g.nt) + sizeof(CnCoef<T>) * pu.g.nr;
+    const size_t need = table_bytes<T>(pu.g.nr, pu.g.nt);
     void *d = nullptr;
     const size_t cap = 2 * ctx->pulses.size() + 8;
     if (ctx->tables.size() >= cap) {
@@ -476,6 +488,8 @@ int ensure_table(fcn_ctx *ctx, Pulse &pu, double dz, const cx<T> **out, int side
     ta.lo = pu.lo64;
     ta.hi = pu.hi64;
     ta.tp = table_pitch(pu.g.nt);
+    ta.pivlim = ctx->prec == FCN_FP32_MIXED ? 1 : 0;
+    if (sizeof(T) == 4) ta.cc = (ColConst *)((char *)d + cc_offset<T>(pu.g.nr, pu.g.nt));
     cudaStream_t bs = ctx->st;
     if (side >= 0) {
         if (!ctx->tside[side]) {
@@ -536,6 +550,8 @@ ColArgs<T> col_args(Pulse &pu, void *field, const cx<T> *table, double dz) {
     a.variant = pu.col_var;
     a.tp = table_pitch(pu.g.nt);
     a.err = pu.err;
+    a.pivlim = sizeof(T) == 4 ? 1 : 0;   // FP32 context tables hold deltas (ensure_table)
+    if (sizeof(T) == 4) a.cc = (const ColConst *)((const char *)table + cc_offset<T>(pu.g.nr, pu.g.nt));
     return a;
 }
 
@@ -831,7 +847,8 @@ cudaError_t launch_block(fcn_ctx *ctx, int kind, double dz, cudaStream_t st,
             std::vector<cx<T> *> f(n);
             for (size_t i = 0; i < n; ++i) f[i] = (cx<T> *)(fields ? (*fields)[i] : ctx->pulses[i].field);
             e = timed(ctx, FCN_PROF_COLUMN, st, [&] {
-                return launch_cn_seq<T>(col_args<T>(ctx->pulses[0], f[0], tabs[0], dz), f.data(), (int)n, st);
+                return launch_cn_seq<T>(col_args<T>(ctx->pulses[0], f[0], tabs[0], dz), f.data(), (int)n, st,
+                                        ctx->seq_shape);
             });
         } else {
             for (size_t i = 0; i < n && e == cudaSuccess; i += m) e = launch_group<T>(ctx, -1, dz, st, tabs, fields, i, &m);
@@ -1108,11 +1125,19 @@ int ensure_tuned(fcn_ctx *ctx, const std::vector<const cx<T> *> &tabs, double dz
                 CK(cudaMemcpyAsync(f[i], ctx->pulses[i].field, bytes, cudaMemcpyDeviceToDevice, ctx->st),
                    "sequential-column copy");
             }
-            float t_all = 0.f, t_groups = 0.f;
-            int rc = time_launches(ctx, [&] {
-                return launch_cn_seq<T>(col_args<T>(p0, f[0], tabs[0], dz), fc.data(), (int)n, ctx->st);
-            }, &t_all);
-            if (rc) return rc;
+            float t_all = 1e30f, t_groups = 0.f;
+            int rc = 0;
+            for (int shape = 0; shape < kSeqShapes; ++shape) {
+                float t = 0.f;
+                rc = time_launches(ctx, [&] {
+                    return launch_cn_seq<T>(col_args<T>(p0, f[0], tabs[0], dz), fc.data(), (int)n, ctx->st, shape);
+                }, &t);
+                if (rc) return rc;
+                if (t < t_all) {
+                    t_all = t;
+                    ctx->seq_shape = shape;
+                }
+            }
             rc = time_launches(ctx, [&] {
                 cudaError_t e = cudaSuccess;
                 size_t m = 1;
@@ -2074,9 +2099,10 @@ int fcn_set_pairing(fcn_ctx *ctx, int32_t mode) {
 int fcn_get_pairing(const fcn_ctx *ctx) { return ctx ? ctx->pairs : FCN_ERR_ARG; }
 
 int fcn_set_sequential_columns(fcn_ctx *ctx, int32_t mode) {
-    if (!ctx || mode < -1 || mode > 1) return FCN_ERR_ARG;
+    if (!ctx || mode < -1 || mode > 1 + kSeqShapes) return FCN_ERR_ARG;
     CK(cudaStreamSynchronize(ctx->st), "sync");
-    ctx->seq_mode = mode;
+    ctx->seq_mode = mode > 1 ? 1 : mode;
+    ctx->seq_shape = mode > 1 ? mode - 2 : 0;
     ctx->seq_all = -1;
     drop_graphs(ctx, true, 0);
     return FCN_OK;

@@ -301,6 +301,15 @@ __device__ __forceinline__ cx<T> ex_rhs(const ExRow<T> &e, cx<T> xm, cx<T> x0, c
     return mk(e.d * x0.x - wy, e.d * x0.y + wx);
 }
 
+// Per-column constants of an FP32 context table, one per |q| (written by
+// the table kernel, so that the column kernels' threads do no FP64 work of
+// their own): lim = 1/p_inf(q) as a two-float pair (x, y hi; z, w lo), cd =
+// c0 - delta_q as two-float pairs for the axis row (x hi, y lo) and the
+// interior rows (z hi, w lo).
+struct ColConst {
+    float4 lim, cd;
+};
+
 template <typename T>
 struct ColArgs {
     cx<T> *field;            // [nr][nt], frequency domain, in place
@@ -321,6 +330,9 @@ struct ColArgs {
                              // (4..8 need coef)
     int tp = 0;              // row pitch of invden in complex values (>= nt/2 + 1)
     int *err = nullptr;      // set nonzero by a kernel whose bounded wait gave up
+    int pivlim = 0;          // 1 (FP32 context tables): invden holds 1/pivot_j - 1/p_inf(q)
+                             // (see piv_limit), applied with the limit as a two-float pair
+    const ColConst *cc = nullptr;   // FP32 context tables: per-column constants (|q|)
 };
 
 struct TableArgs {
@@ -328,7 +340,110 @@ struct TableArgs {
     double s, dk;
     const double *lo, *hi;   // FP64 copies of the ratio tables
     int tp = 0;              // row pitch of the table in complex values (0: nt/2 + 1)
+    int pivlim = 0;          // FP32: store 1/pivot_j - 1/p_inf(q) (ColArgs::pivlim)
+    ColConst *cc = nullptr;  // FP32: per-column constants (tp entries), or none
 };
+
+// 1/p_inf(q), the limit of 1/pivot_j for large j in column q: with lo_j,
+// hi_j -> 1 the pivot recurrence piv_j = b + s^2 lo_j hi_{j-1} / piv_{j-1}
+// (b = 1 + i (2s - delta_q)) tends to the fixed point p of p = b + s^2 / p,
+// p = (b + sqrt(b^2 + 4 s^2)) / 2 (the root of larger modulus; the
+// principal square root, Re b = 1 > 0).  Where the coefficients hardly
+// change with j (small s, large j) the pivots settle to this value within a
+// few rows, and their FP32 roundings then repeat from row to row: rounded
+// once, they made the discrete step non-unitary coherently (an FP32
+// emulation on the 1350 x 1024 grid of the 1.1 km run: +2.9e-8 energy per
+// step, -1.4e-10 with the pivots applied exactly).  FP32 context tables
+// therefore hold 1/pivot_j - 1/p_inf, small wherever the pivots have
+// settled, and the column kernels add the limit back as a two-float pair.
+__host__ __device__ inline cx<double> piv_limit(double s, double dk, int qq) {
+    const double g = 2.0 * s - dk * double(qq) * double(qq);
+    // z = b^2 + 4 s^2 with b = 1 + i g
+    const double zx = 1.0 - g * g + 4.0 * s * s, zy = 2.0 * g;
+    const double r = hypot(zx, zy);
+    const double u = sqrt(0.5 * (r + fabs(zx)));
+    double sx, sy;
+    if (zx >= 0.0) {
+        sx = u;
+        sy = u > 0.0 ? 0.5 * zy / u : 0.0;
+    } else {
+        sx = u > 0.0 ? 0.5 * fabs(zy) / u : 0.0;
+        sy = copysign(u, zy);
+    }
+    const double px = 0.5 * (1.0 + sx), py = 0.5 * (g + sy);
+    const double m = px * px + py * py;
+    cx<double> inv;
+    inv.x = px / m;
+    inv.y = -py / m;
+    return inv;
+}
+
+// The limit as the column kernels use it: off (plain 1/pivot tables, and
+// always in FP64), or on with 1/p_inf = h + l two-float.
+template <typename T>
+struct PivLim {
+    cx<T> h, l;
+    bool on;
+};
+template <typename T>
+__device__ __forceinline__ PivLim<T> piv_lim(int pivlim, double s, double dk, int qq) {
+    PivLim<T> L;
+    L.on = false;
+    L.h = L.l = mk(T(0), T(0));
+    if constexpr (sizeof(T) == 4) {
+        if (pivlim) {
+            const cx<double> v = piv_limit(s, dk, qq);
+            L.on = true;
+            L.h = mk(float(v.x), float(v.y));
+            L.l = mk(float(v.x - double(L.h.x)), float(v.y - double(L.h.y)));
+        }
+    }
+    return L;
+}
+// 1/pivot_j from a table entry (rounded to T; for the sweep factors).  In
+// FP32 branch-free: without the limit h = l = 0 and the sums are exact, so
+// the straight-line sweeps keep no data-dependent branch.
+template <typename T>
+__device__ __forceinline__ cx<T> piv_full(cx<T> v, const PivLim<T> &L) {
+    if constexpr (sizeof(T) == 4) return mk(L.h.x + (v.x + L.l.x), L.h.y + (v.y + L.l.y));
+    else return v;
+}
+// The explicit side's c0 - delta_q pairs and the pivot limit of column |q|:
+// from the table's per-column constants when there are (FP32 contexts),
+// else formed here (FP64; stateless FP32 launches, which have no limit).
+template <typename T>
+__device__ __forceinline__ void col_consts(const ColConst *cc, int pivlim, double s, double dk, int qq,
+                                           CdCol<T> *cd, PivLim<T> *L) {
+    if constexpr (sizeof(T) == 4) {
+        if (cc) {
+            const float4 lim = __ldg(&cc[qq].lim), c = __ldg(&cc[qq].cd);
+            cd->ah = c.x;
+            cd->al = c.y;
+            cd->ih = c.z;
+            cd->il = c.w;
+            L->on = pivlim != 0;
+            L->h = L->on ? mk(lim.x, lim.y) : mk(0.f, 0.f);
+            L->l = L->on ? mk(lim.z, lim.w) : mk(0.f, 0.f);
+            return;
+        }
+    }
+    *cd = cd_col<T>(s, dk, qq);
+    *L = piv_lim<T>(pivlim, s, dk, qq);
+}
+
+// rhs / pivot_j: with the limit on, rhs (h + (v + l)), the small part first
+// (FP32: branch-free as piv_full; without the limit the result is rhs v
+// exactly as the plain product computes it)
+template <typename T>
+__device__ __forceinline__ cx<T> piv_apply(cx<T> rhs, cx<T> v, const PivLim<T> &L) {
+    if constexpr (sizeof(T) == 4) {
+        const cx<T> lo = mk(v.x + L.l.x, v.y + L.l.y);
+        const cx<T> t = cmul(rhs, lo);
+        return mk(fmaf(rhs.x, L.h.x, fmaf(-rhs.y, L.h.y, t.x)), fmaf(rhs.x, L.h.y, fmaf(rhs.y, L.h.x, t.y)));
+    } else {
+        return cmul(rhs, v);
+    }
+}
 
 // Row pitch (complex values) of the pivot tables a context builds: nt/2 + 1
 // rounded up to even, so that every row starts on 16 bytes (a TMA row stride).
@@ -353,7 +468,8 @@ constexpr int kColSeq = 8;              // the sequential TMA-fed column kernel 
 // coefficients and the pivot table (fields[k], blockIdx.y = k);
 // cudaErrorInvalidConfiguration when cn_seq_supported(a) is false.
 template <typename T>
-cudaError_t launch_cn_seq(const ColArgs<T> &a, cx<T> *const *fields, int npulse, cudaStream_t st);
+cudaError_t launch_cn_seq(const ColArgs<T> &a, cx<T> *const *fields, int npulse, cudaStream_t st, int shape = 0);
+constexpr int kSeqShapes = 3;   // ring shapes of the all-pulse sequential launch (launch_cn_seq)
 template <typename T>
 bool cn_seq_supported(const ColArgs<T> &a);
 template <typename T>

@@ -199,8 +199,9 @@ int ensure_tables(fcn_xy_ctx *ctx, double dz) {
     }
     const int nq = ctx->g.nt / 2 + 1;
     if (!ctx->tab_x) {
-        CK(cudaMalloc(&ctx->tab_x, sizeof(cx<T>) * (size_t)ctx->g.nx * nq), "x pivot table");
-        CK(cudaMalloc(&ctx->tab_y, sizeof(cx<T>) * (size_t)ctx->g.ny * nq), "y pivot table");
+        const size_t per = sizeof(cx<T>) * (sizeof(T) == 4 ? 2 : 1);   // FP32: two-float entries
+        CK(cudaMalloc(&ctx->tab_x, per * (size_t)ctx->g.nx * nq), "x pivot table");
+        CK(cudaMalloc(&ctx->tab_y, per * (size_t)ctx->g.ny * nq), "y pivot table");
     }
     double s, dk, disp;
     line_coefs(ctx, dz, dx_of(ctx), &s, &dk, &disp);

@@ -19,7 +19,9 @@
 // precision), and the two sweeps run as the chunked parallel scan of affine
 // maps that the radial column stage uses (colscan::chunk_scan_n): a thread
 // owns L consecutive nodes of one line (or of NP lines of the same
-// frequency bin, which share the pivots) in registers.  The lines of one
+// frequency bin, which share the pivots) in registers.  In FP32 the
+// pivots, the sweep factors and the explicit side's coefficients are
+// two-float pairs (see xy_table_kernel).  The lines of one
 // launch are addressed as b * bstride + j * pitch + c (see XYLine), so the x
 // lines (stride ny*nt) and the y lines (stride nt) use the same kernel, with
 // C adjacent frequency columns per CTA for whole-sector row accesses.
@@ -32,7 +34,14 @@ using namespace colscan;
 
 // One thread per |q| = 0..nt/2: piv_0 = 1 (wall), piv_1 = b,
 // piv_j = b - a c / piv_{j-1} = b + s^2 / piv_{j-1} (2 <= j <= n-2),
-// piv_{n-1} = 1 (wall); the table holds 1/piv_j, row j at j * (nt/2+1).
+// piv_{n-1} = 1 (wall); the table holds 1/piv_j, row j at j * (nt/2+1):
+// in FP64 one complex double per entry, in FP32 a two-float pair (hi, lo;
+// xy_table_entries complex floats per entry).  On a line the coefficients do
+// not depend on j, so the pivots settle to one value within a few nodes and
+// their FP32 roundings are the same at almost every node: rounded once they
+// made the discrete factor non-unitary coherently along the line, which
+// showed as an energy drift of -2e-8 per line factor and step (an FP32
+// emulation of one line; -3e-10 with the pivots and sweep factors two-float).
 template <typename T>
 __global__ void xy_table_kernel(int n, int nt, double s, double dk, cx<T> *table) {
     const int nq = nt / 2 + 1;
@@ -47,7 +56,62 @@ __global__ void xy_table_kernel(int n, int nt, double s, double dk, cx<T> *table
         else if (j == 1) piv = b;
         else piv = b + mk(s * s * inv.x, s * s * inv.y);
         inv = crecip(piv);
-        table[FCN_IDX((size_t)j * nq + q, (size_t)n * nq, 70)] = mk(T(inv.x), T(inv.y));
+        const size_t e = FCN_IDX((size_t)j * nq + q, (size_t)n * nq, 70);
+        if constexpr (sizeof(T) == 4) {
+            const float hx = float(inv.x), hy = float(inv.y);
+            reinterpret_cast<float4 *>(table)[e] =
+                make_float4(hx, hy, float(inv.x - double(hx)), float(inv.y - double(hy)));
+        } else {
+            table[e] = mk(T(inv.x), T(inv.y));
+        }
+    }
+}
+
+// Two-float pivots and sweep factors of the FP32 line sweeps (FP64: the lo
+// parts are zero and drop out at compile time).
+template <typename T>
+struct Piv2 {
+    cx<T> h, l;
+};
+template <typename T>
+__device__ __forceinline__ Piv2<T> load_piv(const cx<T> *tab, size_t e) {
+    Piv2<T> p;
+    if constexpr (sizeof(T) == 4) {
+        const float4 w = __ldg(reinterpret_cast<const float4 *>(tab) + e);
+        p.h = mk(w.x, w.y);
+        p.l = mk(w.z, w.w);
+    } else {
+        p.h = ldg_cx(tab + e);
+        p.l = czero<T>();
+    }
+    return p;
+}
+// alpha = i s / piv as a two-float pair from s = sh + sl and 1/piv = h + l:
+// hi the rounded product i sh h, lo its rounding error (exact by FMA) plus
+// i (sh l + sl h).
+template <typename T>
+__device__ __forceinline__ Piv2<T> sweep_factor(const Piv2<T> &v, T sh, T sl) {
+    Piv2<T> a;
+    if constexpr (sizeof(T) == 4) {
+        const float hx = -sh * v.h.y, hy = sh * v.h.x;
+        const float ex = fmaf(-sh, v.h.y, -hx), ey = fmaf(sh, v.h.x, -hy);
+        a.h = mk(hx, hy);
+        a.l = mk(fmaf(-sh, v.l.y, fmaf(-sl, v.h.y, ex)), fmaf(sh, v.l.x, fmaf(sl, v.h.x, ey)));
+    } else {
+        a.h = cmul_i(v.h, sh);
+        a.l = czero<T>();
+    }
+    return a;
+}
+// a x + b with a two-float: the lo product first, then the hi one fused.
+template <typename T>
+__device__ __forceinline__ cx<T> cmadd2(const Piv2<T> &a, cx<T> x, cx<T> b) {
+    if constexpr (sizeof(T) == 4) {
+        const float tx = fmaf(a.l.x, x.x, fmaf(-a.l.y, x.y, b.x));
+        const float ty = fmaf(a.l.x, x.y, fmaf(a.l.y, x.x, b.y));
+        return mk(fmaf(a.h.x, x.x, fmaf(-a.h.y, x.y, tx)), fmaf(a.h.x, x.y, fmaf(a.h.y, x.x, ty)));
+    } else {
+        return cmul(a.h, x) + b;
     }
 }
 
@@ -71,11 +135,11 @@ xy_line_kernel(XYLine<T> a, int C) {
     const int q = c & (nt - 1);
     const int nq = nt / 2 + 1;
     const int qq = (q <= nt / 2) ? q : nt - q;
-    // interior: e = 1 - i g1, g1 = 2s - delta_q; the explicit side takes s
-    // and g1 as two-float pairs in FP32 (lo = rounding error of the FP64
-    // value), as the radial stage does, so that the rounding of the
-    // coefficients does not perturb the discrete operator the same way at
-    // every step; the sweep factors use s
+    // interior: e = 1 - i g1, g1 = 2s - delta_q; in FP32 s and g1 are
+    // two-float pairs (lo = rounding error of the FP64 value), on the
+    // explicit side as in the radial stage and in the sweep factors with the
+    // two-float pivots, so that the rounding of the coefficients does not
+    // perturb the discrete operator the same way at every step
     const T s = a.s;
     const double g1d = 2.0 * a.s64 - a.dk64 * double(qq) * double(qq);
     const T g1 = T(g1d);
@@ -100,11 +164,15 @@ xy_line_kernel(XYLine<T> a, int C) {
                           ? a.field[FCN_IDX(line[i] - a.field + (size_t)j * a.pitch, a.total, 71)]
                           : czero<T>();
         }
-    cx<T> inv[L];
+    Piv2<T> inv[L];
 #pragma unroll
     for (int k = 0; k < L; ++k) {
         const int j = j0 + k;
-        inv[k] = (j < n) ? ldg_cx(&a.invden[FCN_IDX((size_t)j * nq + qq, (size_t)n * nq, 72)]) : czero<T>();
+        if (j < n) {
+            inv[k] = load_piv(a.invden, FCN_IDX((size_t)j * nq + qq, (size_t)n * nq, 72));
+        } else {
+            inv[k].h = inv[k].l = czero<T>();
+        }
     }
 
     // forward sweep, pass 1: y_j = alpha_j y_{j-1} + beta_j per node, and the
@@ -117,7 +185,7 @@ xy_line_kernel(XYLine<T> a, int C) {
     for (int k = 0; k < L; ++k) {
         const int j = j0 + k;
         if (j >= 1 && j < n - 1) {
-            const cx<T> alpha = cmul_i(inv[k], s);
+            const Piv2<T> alpha = sweep_factor(inv[k], s, sl);
 #pragma unroll
             for (int i = 0; i < NP; ++i) {
                 const cx<T> sum = x[i][k] + x[i][k + 2];
@@ -129,10 +197,10 @@ xy_line_kernel(XYLine<T> a, int C) {
                     w = mk(s * sum.x - g1 * x[i][k + 1].x, s * sum.y - g1 * x[i][k + 1].y);
                 }
                 const cx<T> rhs = mk(x[i][k + 1].x - w.y, x[i][k + 1].y + w.x);
-                y[i][k] = cmul(rhs, inv[k]);
-                PB[i] = cmul(alpha, PB[i]) + y[i][k];
+                y[i][k] = cmadd2(inv[k], rhs, czero<T>());
+                PB[i] = cmadd2(alpha, PB[i], y[i][k]);
             }
-            PA = cmul(alpha, PA);
+            PA = cmadd2(alpha, PA, czero<T>());
         } else {
             // walls: y = 0 and the map sends everything to 0; nodes past the
             // end of the line: identity
@@ -152,11 +220,11 @@ xy_line_kernel(XYLine<T> a, int C) {
         for (int k = 0; k < L; ++k) {
             const int j = j0 + k;
             const bool inner = j >= 1 && j < n - 1;
-            const cx<T> alpha = cmul_i(inv[k], s);
+            const Piv2<T> alpha = sweep_factor(inv[k], s, sl);
 #pragma unroll
             for (int i = 0; i < NP; ++i) {
                 if (inner) {
-                    y[i][k] = cmul(alpha, yp[i]) + y[i][k];
+                    y[i][k] = cmadd2(alpha, yp[i], y[i][k]);
                     yp[i] = y[i][k];
                 } else if (j < n) {
                     yp[i] = czero<T>();
@@ -173,10 +241,12 @@ xy_line_kernel(XYLine<T> a, int C) {
     for (int k = L - 1; k >= 0; --k) {
         const int j = j0 + k;
         if (j < n) {
-            const cx<T> gamma = (j >= 1 && j < n - 1) ? cmul_i(inv[k], s) : czero<T>();
+            Piv2<T> gamma;
+            if (j >= 1 && j < n - 1) gamma = sweep_factor(inv[k], s, sl);
+            else gamma.h = gamma.l = czero<T>();
 #pragma unroll
-            for (int i = 0; i < NP; ++i) QB[i] = cmul(gamma, QB[i]) + y[i][k];
-            QA = cmul(gamma, QA);
+            for (int i = 0; i < NP; ++i) QB[i] = cmadd2(gamma, QB[i], y[i][k]);
+            QA = cmadd2(gamma, QA, czero<T>());
         }
     }
     // backward sweep, pass 2 and store
@@ -188,10 +258,12 @@ xy_line_kernel(XYLine<T> a, int C) {
         for (int k = L - 1; k >= 0; --k) {
             const int j = j0 + k;
             if (j < n) {
-                const cx<T> gamma = (j >= 1 && j < n - 1) ? cmul_i(inv[k], s) : czero<T>();
+                Piv2<T> gamma;
+                if (j >= 1 && j < n - 1) gamma = sweep_factor(inv[k], s, sl);
+                else gamma.h = gamma.l = czero<T>();
 #pragma unroll
                 for (int i = 0; i < NP; ++i) {
-                    xn[i] = cmul(gamma, xn[i]) + y[i][k];
+                    xn[i] = cmadd2(gamma, xn[i], y[i][k]);
                     if (on[i])
                         a.field[FCN_IDX(line[i] - a.field + (size_t)j * a.pitch, a.total, 73)] =
                             disp_apply(xn[i], ph);

@@ -32,7 +32,8 @@ def main(argv=None) -> int:
     ap.add_argument("--branches", type=int, default=1, help="graph branches (pulse groups run concurrently)")
     ap.add_argument("--multi", type=int, default=2, help="multi-pulse row launch mode (0, 1, 2)")
     ap.add_argument("--seq", type=int, default=-1,
-                    help="sequential column kernel over all pulses: 1 on, 0 off, -1 decided by timing")
+                    help="sequential column kernel over all pulses: 1 on, 0 off, -1 decided by "
+                         "timing, 2..4 on with ring shape 0..2")
     ap.add_argument("--time", type=int, default=0,
                     help="then time this many graph-replayed steps (wall clock around a "
                          "synchronising call) and as many steps replayed from graphs with "
@@ -56,7 +57,7 @@ def main(argv=None) -> int:
     s.set_multi_launch(a.multi)
     if a.pulses > 1:
         s.set_sequential_columns(a.seq)
-        if a.seq == 1:
+        if a.seq >= 1:
             s.set_pairing(0)      # no pairing decision: the column launches are the step's own
     dz = wls[0].dz if wls[0].nsteps else 2e-3
     s.step(dz, a.steps, graph=a.graph)
