@@ -219,10 +219,13 @@ int fcn_get_state(fcn_ctx *ctx, int32_t pulse, double state[4]);
 int fcn_set_state(fcn_ctx *ctx, int32_t pulse, const double state[4]);
 
 /* ======================= kernel variants (autotuner) ======================= */
-/* The row stage has 4 variants (FP32, K = 8): 0-2 one CTA per row (group)
+/* The row stage has 6 variants (FP32, K = 8): 0-2 one CTA per row (group)
  * with the compiler's register allocation, or 3 or 4 CTAs per SM; 3 a
  * persistent kernel that prefetches each CTA's next rows into shared memory
- * by bulk copies (Nt >= 512).  The column stage has 9:
+ * by bulk copies (Nt >= 512); 4, 5 the occupancy of 1, 2 with the other FFT
+ * decomposition: radix-8 passes before the final radix-16 one (Nt = 4096:
+ * 4 8 8 16) instead of radix-16 passes after one radix 2/4/8 pass (16 16 16)
+ * (Nt >= 256; smaller rows run variant 0).  The column stage has 9:
  *   0-3  chunked affine-map scans of the two Thomas sweeps, chunks in
  *        registers (chunk length x CTA size);
  *   4-7  the same with chunks staged in shared memory (cp.async) or fed to
@@ -233,7 +236,7 @@ int fcn_set_state(fcn_ctx *ctx, int32_t pulse, const double state[4]);
  * By default (-1) the first fcn_step of a grid times every variant on a
  * scratch copy of the field and keeps the fastest per (precision, Nr, Nt)
  * for the process; if the environment variable FCN_TUNE_CACHE names a file,
- * choices are read from and appended to it.  row_variant in -1..3 and
+ * choices are read from and appended to it.  row_variant in -1..5 and
  * col_variant in -1..8 force a variant (-1: tune).  Every variant computes
  * the same step up to rounding.  Drops the context's captured graphs.
  * Synchronises. */
@@ -517,7 +520,8 @@ int  fcn_xy_step_nograph(fcn_xy_ctx *ctx, double dz, int64_t n);
 /* FP64 diagnostics of the current field (synchronises the stream).
  * Returns FCN_ERR_NONFINITE if the field holds NaN or Inf. */
 int  fcn_xy_get_diag(fcn_xy_ctx *ctx, fcn_diag *out);
-/* Forces the row-stage variant (0..2) and the line variant (0..7: the chunk
+/* Forces the row-stage variant (0..5, as fcn_set_variants; 3 runs as 0
+ * here) and the line variant (0..7: the chunk
  * of nodes a thread owns, 16 or 8 in FP32 and 8 or 4 in FP64, one or two
  * lines per thread, CTAs of up to 512 or 256 threads); -1 returns to
  * timing.  Every variant computes the same step (up to rounding order). */

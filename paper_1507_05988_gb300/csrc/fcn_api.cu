@@ -128,17 +128,19 @@ void cn_coefs(const fcn_grid &g, const fcn_params &p, double dz, double *s, doub
 
 // ---- process-wide constant tables (twiddles, radial ratios) ----
 struct ConstTables {
-    std::map<std::pair<int, int>, void *> tw;      // (prec, nt) -> cx<T>[nt]
+    std::map<std::pair<int, int>, void *> tw;      // (prec, nt with FFT plan tag) -> twiddle blocks
     std::map<std::pair<int, int>, void *> lohi;    // (prec, nr) -> T[2*nr]
     std::map<int, double *> lohi64;                // nr -> double[2*nr]
 };
 ConstTables g_tables;
 
+// ntp: Nt with the FFT plan in its high bits (fft_tag)
 template <typename T>
-cudaError_t get_twiddles(int nt, const cx<T> **out) {
+cudaError_t get_twiddles(int ntp, const cx<T> **out) {
     const int prec = sizeof(T) == 8 ? FCN_FP64 : FCN_FP32_MIXED;
+    const int nt = fft_nt(ntp);
     std::lock_guard<std::mutex> lk(g_mu);
-    auto key = std::make_pair(prec, nt);
+    auto key = std::make_pair(prec, ntp);
     auto it = g_tables.tw.find(key);
     if (it != g_tables.tw.end()) { *out = (const cx<T> *)it->second; return cudaSuccess; }
     // W^m = exp(-2 pi i m / nt); FP32 entries as two-float pairs (hi, lo):
@@ -159,14 +161,14 @@ cudaError_t get_twiddles(int nt, const cx<T> **out) {
         }
     }
     // per-pass blocks (layout in fcn_device.cuh: tw_offset)
-    const size_t n = std::max(1, tw_size(nt));
+    const size_t n = std::max(1, tw_size(ntp));
     std::vector<cx<T>> h(n * PER, mk(T(0), T(0)));
-    for (int p = 1; p < fft_npass(nt); ++p) {
-        const int R = fft_radix(nt, p), NS = fft_ns(nt, p), stride = nt / (NS * R);
+    for (int p = 1; p < fft_npass(ntp); ++p) {
+        const int R = fft_radix(ntp, p), NS = fft_ns(ntp, p), stride = nt / (NS * R);
         for (int r = 1; r < R; ++r)
             for (int k = 0; k < NS; ++k)
                 for (int u = 0; u < PER; ++u)
-                    h[((size_t)tw_offset(nt, p) + (r - 1) * NS + k) * PER + u] =
+                    h[((size_t)tw_offset(ntp, p) + (r - 1) * NS + k) * PER + u] =
                         w[(size_t)(r * k * stride) * PER + u];
     }
     void *d = nullptr;
@@ -239,8 +241,8 @@ NLCoef<T> nl(const fcn_grid &g, const fcn_params &p, double h) {
 template NLCoef<float> nl<float>(const fcn_grid &, const fcn_params &, double);
 template NLCoef<double> nl<double>(const fcn_grid &, const fcn_params &, double);
 template <typename T>
-cudaError_t twiddles(int nt, const cx<T> **out) {
-    return get_twiddles<T>(nt, out);
+cudaError_t twiddles(int ntp, const cx<T> **out) {
+    return get_twiddles<T>(ntp, out);
 }
 template cudaError_t twiddles<float>(int, const cx<float> **);
 template cudaError_t twiddles<double>(int, const cx<double> **);
@@ -275,6 +277,7 @@ struct Pulse {
     double *stage = nullptr;   // double staging [2*nr*nt] for host transfers
     int *err = nullptr;        // [1] set by a kernel whose bounded wait gave up
     const void *tw = nullptr;
+    const void *tw1 = nullptr;   // twiddles of FFT plan 1 (FP32, Nt >= 256), or null
     const void *lo = nullptr, *hi = nullptr;
     const double *lo64 = nullptr, *hi64 = nullptr;
     double z = 0.0, dz_next = 0.0;
@@ -519,6 +522,7 @@ RowArgs<T> row_args(Pulse &pu, void *field, int ops, double dz) {
     RowArgs<T> a;
     a.field = (cx<T> *)field;
     a.tw = (const cx<T> *)pu.tw;
+    a.tw1 = (const cx<T> *)pu.tw1;
     a.rho = (T *)pu.rho;
     a.stats = pu.stats;
     a.nr = pu.g.nr;
@@ -1775,14 +1779,15 @@ int create_impl(int n, const fcn_grid *grids, const fcn_params *params, int prec
                 return bail(FCN_ERR_CUDA);
             }
         } else {
-            const cx<float> *tw;
+            const cx<float> *tw, *tw1 = nullptr;
             const float *lo, *hi;
             if ((e = get_twiddles<float>(pu.g.nt, &tw)) != cudaSuccess ||
+                (pu.g.nt >= 256 && (e = get_twiddles<float>(fft_tag(pu.g.nt, 1), &tw1)) != cudaSuccess) ||
                 (e = get_lohi<float>(pu.g.nr, &lo, &hi, &pu.lo64, &pu.hi64)) != cudaSuccess) {
                 cuda_fail(ctx, e, "constant tables");
                 return bail(FCN_ERR_CUDA);
             }
-            pu.tw = tw; pu.lo = lo; pu.hi = hi;
+            pu.tw = tw; pu.tw1 = tw1; pu.lo = lo; pu.hi = hi;
             if ((e = prepare_rows<float>(pu.g.nt)) != cudaSuccess || (e = prepare_cn<float>()) != cudaSuccess) {
                 cuda_fail(ctx, e, "row kernel attributes");
                 return bail(FCN_ERR_CUDA);

@@ -147,25 +147,48 @@ struct NLCoef {
     unsigned flags;
 };
 
-// Pass structure of the row stage's in-place FFT of Nt points (one radix
-// 2/4/8 pass first for the factor left over by radix 16, then radix-16
-// passes; Nt < 16: one pass of radix Nt) and the layout of its twiddle
-// table: for every pass p >= 1 (radix R_p, Ns_p = product of the earlier
-// radices) one block of (R_p - 1) Ns_p factors, entry (r - 1) Ns_p + k =
-// W^(r k Nt / (Ns_p R_p)), W = exp(-2 pi i / Nt), r = 1..R_p-1,
+// Pass structure of the row stage's in-place FFT of Nt points and the layout
+// of its twiddle table.  Two decompositions (plans), chosen per grid by the
+// autotuner through the row variant; the last pass is radix 16 in both (a
+// thread's 16 consecutive samples then sit at one position stride):
+//   plan 0: one radix 2/4/8 pass first for the factor left over by radix 16,
+//           then radix-16 passes (Nt = 4096: 16 16 16);
+//   plan 1 (Nt >= 256): radix-8 passes, one radix 2/4 pass first for the
+//           factor left over, then the radix-16 pass (Nt = 4096: 4 8 8 16).
+// Nt < 16: one pass of radix Nt.  A kernel's Nt template argument carries
+// the plan in its high bits (fft_tag); fft_nt / fft_plan decode it.
+// Twiddle table: for every pass p >= 1 (radix R_p, Ns_p = product of the
+// earlier radices) one block of (R_p - 1) Ns_p factors, entry (r - 1) Ns_p +
+// k = W^(r k Nt / (Ns_p R_p)), W = exp(-2 pi i / Nt), r = 1..R_p-1,
 // k = 0..Ns_p-1: the threads of a warp (consecutive k) read consecutive
 // entries.  An FP32 entry is a two-float pair (hi, lo) of complex floats,
 // 16 bytes; an FP64 entry one complex double.
+constexpr int kFftPlanShift = 20;
+__host__ __device__ constexpr int fft_tag(int nt, int plan) { return nt | (plan << kFftPlanShift); }
+__host__ __device__ constexpr int fft_nt(int ntp) { return ntp & ((1 << kFftPlanShift) - 1); }
+__host__ __device__ constexpr int fft_plan(int ntp) { return ntp >> kFftPlanShift; }
 __host__ __device__ constexpr int fft_log2(int n) { return n <= 1 ? 0 : 1 + fft_log2(n / 2); }
 __host__ __device__ constexpr int fft_n16(int nt) { return nt >= 16 ? fft_log2(nt) / 4 : 0; }
 __host__ __device__ constexpr int fft_rem(int nt) { return nt >= 16 ? (1 << (fft_log2(nt) % 4)) : nt; }
-__host__ __device__ constexpr int fft_npass(int nt) { return fft_n16(nt) + (fft_rem(nt) > 1 ? 1 : 0); }
-__host__ __device__ constexpr int fft_radix(int nt, int p) {
-    return nt < 16 ? nt : ((fft_rem(nt) > 1 && p == 0) ? fft_rem(nt) : 16);
+// plan 1: m = log2(Nt/16) radix-2 factors before the radix-16 pass, as
+// radix-8 passes and a radix 2^(m mod 3) pass first
+__host__ __device__ constexpr int fft_m8(int nt) { return fft_log2(nt) - 4; }
+__host__ __device__ constexpr bool fft_plan1(int ntp) { return fft_plan(ntp) == 1 && fft_nt(ntp) >= 256; }
+__host__ __device__ constexpr int fft_npass(int ntp) {
+    return fft_plan1(ntp) ? (fft_m8(fft_nt(ntp)) % 3 ? 1 : 0) + fft_m8(fft_nt(ntp)) / 3 + 1
+                          : fft_n16(fft_nt(ntp)) + (fft_rem(fft_nt(ntp)) > 1 ? 1 : 0);
 }
-__host__ __device__ constexpr int fft_ns(int nt, int p) {
-    return nt < 16 ? 1
-                   : (fft_rem(nt) > 1 ? (p == 0 ? 1 : fft_rem(nt) << (4 * (p - 1))) : (1 << (4 * p)));
+__host__ __device__ constexpr int fft_radix(int ntp, int p) {
+    return fft_nt(ntp) < 16 ? fft_nt(ntp)
+         : fft_plan1(ntp)
+             ? (p == fft_npass(ntp) - 1 ? 16
+                : ((fft_m8(fft_nt(ntp)) % 3 && p == 0) ? (1 << (fft_m8(fft_nt(ntp)) % 3)) : 8))
+             : ((fft_rem(fft_nt(ntp)) > 1 && p == 0) ? fft_rem(fft_nt(ntp)) : 16);
+}
+__host__ __device__ constexpr int fft_ns(int ntp, int p) {
+    int ns = 1;
+    for (int q = 0; q < p; ++q) ns *= fft_radix(ntp, q);
+    return ns;
 }
 __host__ __device__ constexpr int tw_offset(int nt, int p) {
     int o = 0;
@@ -191,7 +214,7 @@ enum : int {
 template <typename T>
 struct RowArgs {
     cx<T> *field;         // [nr][nt]
-    const cx<T> *tw;      // forward twiddles W_nt^m = exp(-2 pi i m / nt), m < nt
+    const cx<T> *tw;      // twiddle table of FFT plan 0 (layout: tw_offset)
     T *rho;               // [nr][nt] or null
     double *stats;        // [nr][NSTAT] or null
     int nr;
@@ -199,9 +222,12 @@ struct RowArgs {
     int ops;
     int variant;          // 0..2: occupancy variants; 3: persistent, next rows
                           // prefetched by bulk copies (FP32, K = 8, Nt >= 512);
+                          // 4, 5: FFT plan 1 (radix-8 passes) with the
+                          // occupancy of variants 1, 2 (FP32, K = 8, Nt >= 256);
                           // chosen by the autotuner
     NLCoef<T> nl;
     int *err = nullptr;   // set nonzero by a kernel whose bounded wait gave up
+    const cx<T> *tw1 = nullptr;   // twiddle table of FFT plan 1 (variants 4, 5)
 };
 
 // One launch of the row stage over up to kRowMulti pulses that share the
@@ -460,7 +486,7 @@ template <typename T>
 cudaError_t prepare_rows(int nt);
 template <typename T>
 cudaError_t launch_cn(const ColArgs<T> &a, cudaStream_t st);
-constexpr int kRowVariants = 4;
+constexpr int kRowVariants = 6;
 constexpr int kColVariants = 9;
 constexpr int kColStagedFirst = 4;      // variants >= this need ColArgs::coef
 constexpr int kColSeq = 8;              // the sequential TMA-fed column kernel (col_seq.cu)

@@ -18,7 +18,7 @@ template <typename T>
 NLCoef<T> nl(const fcn_grid &g, const fcn_params &p, double h);
 // Process-wide twiddle table of the row stage's FFT of nt points.
 template <typename T>
-cudaError_t twiddles(int nt, const cx<T> **out);
+cudaError_t twiddles(int ntp, const cx<T> **out);   // ntp: Nt with the FFT plan tag (fft_tag)
 // k0 = 2 pi n0/lambda0, dtau = T/Nt, domega = 2 pi/(Nt dtau).
 void consts(const fcn_grid &g, const fcn_params &p, double *k0, double *dtau, double *domega);
 // s = dz/(4 k0 dr^2) and dk (delta_q = dk q^2) of the Crank-Nicolson system;

@@ -46,23 +46,24 @@ constexpr int ilog2(int n) { return n <= 1 ? 0 : 1 + ilog2(n / 2); }
 // reductions (rows per CTA x warps per row x values <= 64)
 constexpr int kRowScratch = 64;
 
+// NT is the row length with the FFT plan in its high bits (fft_tag); N is
+// the length itself.
 template <int NT>
 struct RowCfg {
-    static constexpr int E = NT < 16 ? NT : 16;             // values per thread
-    static constexpr int TPR = NT / E;                      // threads per row
+    static constexpr int N = fft_nt(NT);                    // points per row
+    static constexpr int PLAN = fft_plan(NT);               // FFT decomposition
+    static constexpr int E = N < 16 ? N : 16;               // values per thread
+    static constexpr int TPR = N / E;                       // threads per row
     static constexpr int THREADS = TPR >= 256 ? TPR : 256;  // CTA size
     static constexpr int RPC = THREADS / TPR;               // rows per CTA
-    static constexpr int PADN = NT >= 16 ? NT + NT / 16 : NT;
-    static constexpr int LOG = ilog2(NT);
-    static constexpr int N16 = NT >= 16 ? LOG / 4 : 0;      // radix-16 passes
-    static constexpr int REM = NT >= 16 ? (1 << (LOG % 4)) : NT;  // last radix (1: none)
-    static constexpr int NPASS = N16 + (REM > 1 ? 1 : 0);
+    static constexpr int PADN = N >= 16 ? N + N / 16 : N;
+    static constexpr int NPASS = fft_npass(NT);
     static constexpr int WARPS_PER_ROW = TPR > 32 ? TPR / 32 : 1;
+    static_assert(fft_radix(NT, NPASS - 1) == E, "the last pass has the radix of a thread's samples");
 };
 
-// Pass P of the transform: radix R (the radix 2/4/8 pass first when Nt is
-// not a power of 16, then radix-16 passes) and Ns, the product of the
-// radices of the earlier passes.
+// Pass P of the transform: radix R (fft_radix: the plan's sequence, its last
+// pass radix 16) and Ns, the product of the radices of the earlier passes.
 template <int NT, int P>
 struct PassCfg {
     static constexpr int R = fft_radix(NT, P);
@@ -318,7 +319,7 @@ __device__ __forceinline__ void pass_load(cx<T> (&v)[RowCfg<NT>::E], const cx<T>
         const int j = t + C::TPR * i;
         const int base = (j / NS) * NS * R + (j & (NS - 1));
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[i * R + r] = S[FCN_IDX(pidx(base + r * NS, NT), C::PADN, 1)];
+        for (int r = 0; r < R; ++r) v[i * R + r] = S[FCN_IDX(pidx(base + r * NS, fft_nt(NT)), C::PADN, 1)];
     }
 }
 
@@ -333,7 +334,7 @@ __device__ __forceinline__ void pass_store(const cx<T> (&v)[RowCfg<NT>::E], cx<T
         const int j = t + C::TPR * i;
         const int base = (j / NS) * NS * R + (j & (NS - 1));
 #pragma unroll
-        for (int r = 0; r < R; ++r) S[FCN_IDX(pidx(base + r * NS, NT), C::PADN, 2)] = v[i * R + r];
+        for (int r = 0; r < R; ++r) S[FCN_IDX(pidx(base + r * NS, fft_nt(NT)), C::PADN, 2)] = v[i * R + r];
     }
 }
 
@@ -404,8 +405,8 @@ struct FwdDispatch<T, NT, P, true> {
 // are one base plus compile-time offsets.
 template <int NT, int NSL>
 __device__ __forceinline__ int own_idx(int q0, int p0, int e) {
-    if constexpr (NT >= 16 && NSL % 16 == 0) return q0 + e * (NSL + NSL / 16);
-    else return pidx(p0 + e * NSL, NT);
+    if constexpr (fft_nt(NT) >= 16 && NSL % 16 == 0) return q0 + e * (NSL + NSL / 16);
+    else return pidx(p0 + e * NSL, fft_nt(NT));
 }
 
 // Position in S of time sample tau.  The forward transform takes its input
@@ -683,13 +684,13 @@ __device__ __forceinline__ void nl_half_smem(cx<T> *S, T *U, int t, const NLCoef
     static_assert(PassCfg<NT, C::NPASS - 1>::R == E, "a thread's samples differ in the last digit only");
     // the thread's samples tau = E t + e sit at p0 + e NSL (tpos)
     const int p0 = tpos<NT>(E * t);
-    const int q0 = pidx(p0, NT);
+    const int q0 = pidx(p0, fft_nt(NT));
     const bool last_thread = (t == C::TPR - 1);
     // |A|^2 of the thread's points and of the next thread's first point
     T cn[E + 1];
 #pragma unroll
     for (int e = 0; e < E; ++e) cn[e] = cnorm(S[FCN_IDX((own_idx<NT, NSL>(q0, p0, e)), C::PADN, 8)]);
-    cn[E] = last_thread ? T(0) : cnorm(S[FCN_IDX(pidx(tpos<NT>(E * (t + 1)), NT), C::PADN, 8)]);
+    cn[E] = last_thread ? T(0) : cnorm(S[FCN_IDX(pidx(tpos<NT>(E * (t + 1)), fft_nt(NT)), C::PADN, 8)]);
     T cmax = T(0);
 #pragma unroll
     for (int e = 0; e < E; ++e) cmax = fmax(cmax, cn[e]);
@@ -856,7 +857,7 @@ struct NoHook {
 };
 
 // One row stage of RPC rows.  PF: the input rows were staged in shared memory
-// (xs: RPC rows of NT values in natural order, row_base's first) and are read
+// (xs: RPC rows of Nt values in natural order, row_base's first) and are read
 // from there; hook() runs once every thread has finished reading them (the
 // prefetch of the next rows may then overwrite xs).
 template <typename T, int NT, int KT, int TH, bool PF = false, typename Hook = NoHook>
@@ -890,7 +891,7 @@ __device__ __forceinline__ void row_body(const RowArgs<T> &a, int row_base, int 
     const bool valid = row < a.nr;
     cx<T> *S = S_all + rloc * C::PADN;
     T *U = U_all + rloc * C::PADN;
-    cx<T> *g = a.field + (size_t)(valid ? row : 0) * NT;
+    cx<T> *g = a.field + (size_t)(valid ? row : 0) * C::N;
 
     cx<T> v[E];
     if (ops & OP_IFFT) {
@@ -899,22 +900,22 @@ __device__ __forceinline__ void row_body(const RowArgs<T> &a, int row_base, int 
         constexpr int PL = C::NPASS - 1;
         constexpr int RL = PassCfg<NT, PL>::R;
         constexpr int NSL = PassCfg<NT, PL>::NS;
-        const cx<T> *src = PF ? xs + rloc * NT : g;
+        const cx<T> *src = PF ? xs + rloc * C::N : g;
 #pragma unroll
         for (int i = 0; i < E / RL; ++i) {
             const int j = t + C::TPR * i;
 #pragma unroll
             for (int r = 0; r < RL; ++r)
-                v[i * RL + r] = valid ? src[FCN_IDX(j + r * NSL, NT, 4)] : mk(T(0), T(0));
+                v[i * RL + r] = valid ? src[FCN_IDX(j + r * NSL, fft_nt(NT), 4)] : mk(T(0), T(0));
         }
-        InvDispatch<T, NT, PL, (PL < 0)>::run(v, S, t, a.tw, a.nl.inv_nt);
+        InvDispatch<T, NT, PL, (PL < 0)>::run(v, S, t, C::PLAN ? a.tw1 : a.tw, a.nl.inv_nt);
         hook();
     } else {
-        const cx<T> *src = PF ? xs + rloc * NT : g;
+        const cx<T> *src = PF ? xs + rloc * C::N : g;
 #pragma unroll
         for (int i = 0; i < E; ++i) {
             const int idx = t + C::TPR * i;
-            S[FCN_IDX(pidx(tpos<NT>(idx), NT), C::PADN, 5)] = valid ? src[FCN_IDX(idx, NT, 6)] : mk(T(0), T(0));
+            S[FCN_IDX(pidx(tpos<NT>(idx), fft_nt(NT)), C::PADN, 5)] = valid ? src[FCN_IDX(idx, fft_nt(NT), 6)] : mk(T(0), T(0));
         }
         __syncthreads();
         hook();
@@ -947,7 +948,7 @@ __device__ __forceinline__ void row_body(const RowArgs<T> &a, int row_base, int 
                     float mxf = 0.f, muf = 0.f, badf = 0.f;
 #pragma unroll 4
                     for (int e = 0; e < E; ++e) {
-                        const int ip = own_idx<NT, PassCfg<NT, C::NPASS - 1>::NS>(pidx(tpos<NT>(E * t), NT),
+                        const int ip = own_idx<NT, PassCfg<NT, C::NPASS - 1>::NS>(pidx(tpos<NT>(E * t), fft_nt(NT)),
                                                                                   tpos<NT>(E * t), e);
                         const cx<T> x = S[FCN_IDX(ip, C::PADN, 29)];
                         const float i2 = fmaf(x.x, x.x, x.y * x.y);
@@ -963,7 +964,7 @@ __device__ __forceinline__ void row_body(const RowArgs<T> &a, int row_base, int 
                 } else {
 #pragma unroll 4
                     for (int e = 0; e < E; ++e) {
-                        const int ip = own_idx<NT, PassCfg<NT, C::NPASS - 1>::NS>(pidx(tpos<NT>(E * t), NT),
+                        const int ip = own_idx<NT, PassCfg<NT, C::NPASS - 1>::NS>(pidx(tpos<NT>(E * t), fft_nt(NT)),
                                                                                   tpos<NT>(E * t), e);
                         const cx<T> x = S[FCN_IDX(ip, C::PADN, 29)];
                         const double i2 = double(x.x) * double(x.x) + double(x.y) * double(x.y);
@@ -988,12 +989,12 @@ __device__ __forceinline__ void row_body(const RowArgs<T> &a, int row_base, int 
             __syncthreads();
             if ((ops & OP_RHO) && valid && a.rho) {
                 // consecutive threads write consecutive tau points
-                T *rr = a.rho + (size_t)row * NT;
+                T *rr = a.rho + (size_t)row * C::N;
 #pragma unroll
                 for (int i = 0; i < E; ++i) {
                     const int idx = t + C::TPR * i;
-                    rr[FCN_IDX(idx, NT, 12)] =
-                        have_u ? U[FCN_IDX(pidx(tpos<NT>(idx), NT), C::PADN, 30)] * a.nl.rho_nt : T(0);
+                    rr[FCN_IDX(idx, fft_nt(NT), 12)] =
+                        have_u ? U[FCN_IDX(pidx(tpos<NT>(idx), fft_nt(NT)), C::PADN, 30)] * a.nl.rho_nt : T(0);
                 }
             }
         }
@@ -1001,7 +1002,7 @@ __device__ __forceinline__ void row_body(const RowArgs<T> &a, int row_base, int 
 #pragma unroll
             for (int i = 0; i < E; ++i) {
                 const int idx = t + C::TPR * i;
-                g[FCN_IDX(idx, NT, 10)] = S[FCN_IDX(pidx(tpos<NT>(idx), NT), C::PADN, 11)];
+                g[FCN_IDX(idx, fft_nt(NT), 10)] = S[FCN_IDX(pidx(tpos<NT>(idx), fft_nt(NT)), C::PADN, 11)];
             }
         }
         // the in-place transform below overwrites S: every thread's store first
@@ -1009,7 +1010,7 @@ __device__ __forceinline__ void row_body(const RowArgs<T> &a, int row_base, int 
     }
 
     if (ops & OP_FFT) {
-        FwdDispatch<T, NT, 0, (C::NPASS <= 0)>::run(v, S, t, a.tw);
+        FwdDispatch<T, NT, 0, (C::NPASS <= 0)>::run(v, S, t, C::PLAN ? a.tw1 : a.tw);
         // last-pass outputs: index j + r*NS, j = t + TPR*i
         constexpr int PL = C::NPASS - 1;
         constexpr int R = PassCfg<NT, PL>::R;
@@ -1020,7 +1021,7 @@ __device__ __forceinline__ void row_body(const RowArgs<T> &a, int row_base, int 
             for (int i = 0; i < NB; ++i) {
                 const int j = t + C::TPR * i;
 #pragma unroll
-                for (int r = 0; r < R; ++r) g[FCN_IDX(j + r * NS, NT, 13)] = v[i * R + r];
+                for (int r = 0; r < R; ++r) g[FCN_IDX(j + r * NS, fft_nt(NT), 13)] = v[i * R + r];
             }
         }
         if ((ops & OP_SPEC) && a.stats) {
@@ -1034,7 +1035,7 @@ __device__ __forceinline__ void row_body(const RowArgs<T> &a, int row_base, int 
 #pragma unroll
                     for (int r = 0; r < R; ++r) {
                         const int q = j + r * NS;
-                        const float w = float(q < NT / 2 ? q : q - NT);
+                        const float w = float(q < C::N / 2 ? q : q - C::N);
                         const cx<T> x = v[i * R + r];
                         const float p2 = fmaf(x.x, x.x, x.y * x.y);
                         k0.add(p2);
@@ -1052,7 +1053,7 @@ __device__ __forceinline__ void row_body(const RowArgs<T> &a, int row_base, int 
 #pragma unroll
                     for (int r = 0; r < R; ++r) {
                         const int q = j + r * NS;
-                        const double w = double(q < NT / 2 ? q : q - NT);
+                        const double w = double(q < C::N / 2 ? q : q - C::N);
                         const cx<T> x = v[i * R + r];
                         const double p2 = double(x.x) * double(x.x) + double(x.y) * double(x.y);
                         m3[0] += p2;
@@ -1143,12 +1144,12 @@ row_kernel_pf(const __grid_constant__ RowMultiArgs<T> m, int npulse, int *err) {
     if ((int)blockIdx.x >= units) return;
     const bool with_u = (a0.ops & (OP_RHO | OP_STATS)) != 0;
     cx<T> *xs = reinterpret_cast<cx<T> *>(smem_raw + pf_stage_offset<T, NT>(with_u));
-    const uint32_t bar = (uint32_t)__cvta_generic_to_shared(xs + C::RPC * NT);
+    const uint32_t bar = (uint32_t)__cvta_generic_to_shared(xs + C::RPC * C::N);
     auto issue = [&](int u) {                           // thread 0 only
         const int pulse = u / upp, row0 = (u - pulse * upp) * C::RPC;
         const int rows = min(C::RPC, a0.nr - row0);
-        const uint32_t bytes = (uint32_t)(rows * NT * sizeof(cx<T>));
-        const cx<T> *src = m.field[pulse] + (size_t)row0 * NT;
+        const uint32_t bytes = (uint32_t)(rows * C::N * sizeof(cx<T>));
+        const cx<T> *src = m.field[pulse] + (size_t)row0 * C::N;
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
         asm volatile(
             "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
@@ -1255,19 +1256,22 @@ cudaError_t set_smem_attr() {
 template <int NT>
 constexpr int mb_pf() { return RowCfg<NT>::THREADS >= 512 ? 1 : 3; }
 template <typename T, int NT>
-constexpr bool has_pf() { return sizeof(T) == 4 && NT >= 512; }
+constexpr bool has_pf() { return sizeof(T) == 4 && fft_nt(NT) >= 512 && fft_plan(NT) == 0; }
 template <typename T, int NT>
 size_t pf_smem_bytes(bool with_u) {
-    return pf_stage_offset<T, NT>(with_u) + sizeof(cx<T>) * RowCfg<NT>::RPC * NT + 16;
+    return pf_stage_offset<T, NT>(with_u) + sizeof(cx<T>) * RowCfg<NT>::RPC * RowCfg<NT>::N + 16;
 }
 
 template <typename T, int NT>
 cudaError_t prepare_nt() {
     cudaError_t e = set_smem_attr<T, NT, 0, 1>();
     if (e == cudaSuccess) e = set_smem_attr<T, NT, 8, 1>();
-    if constexpr (sizeof(T) == 4 && NT >= 256) {
+    if constexpr (sizeof(T) == 4 && fft_nt(NT) >= 256) {
+        constexpr int NT1 = fft_tag(NT, 1);
         if (e == cudaSuccess) e = set_smem_attr<T, NT, 8, mb_of<NT>(1)>();
         if (e == cudaSuccess) e = set_smem_attr<T, NT, 8, mb_of<NT>(2)>();
+        if (e == cudaSuccess) e = set_smem_attr<T, NT1, 8, mb_of<NT1>(1)>();
+        if (e == cudaSuccess) e = set_smem_attr<T, NT1, 8, mb_of<NT1>(2)>();
     }
     if constexpr (has_pf<T, NT>()) {
         if (e == cudaSuccess)
@@ -1319,9 +1323,12 @@ cudaError_t launch_nt_multi(const RowMultiArgs<T> &m, int npulse, cudaStream_t s
     void (*k)(const RowMultiArgs<T>) = row_kernel_multi<T, NT, 8, 1>;
     if (a.nl.K != 8) {
         k = row_kernel_multi<T, NT, 0, 1>;
-    } else if constexpr (sizeof(T) == 4 && NT >= 256) {
+    } else if constexpr (sizeof(T) == 4 && fft_nt(NT) >= 256) {
+        constexpr int NT1 = fft_tag(NT, 1);
         if (a.variant == 1) k = row_kernel_multi<T, NT, 8, mb_of<NT>(1)>;
         else if (a.variant == 2) k = row_kernel_multi<T, NT, 8, mb_of<NT>(2)>;
+        else if (a.variant == 4 && a.tw1) k = row_kernel_multi<T, NT1, 8, mb_of<NT1>(1)>;
+        else if (a.variant == 5 && a.tw1) k = row_kernel_multi<T, NT1, 8, mb_of<NT1>(2)>;
     }
     return launch_k(k, grid, dim3(C::THREADS), smem, st, m);
 }
@@ -1348,9 +1355,12 @@ cudaError_t launch_nt(const RowArgs<T> &a, cudaStream_t st) {
     void (*k)(RowArgs<T>) = row_kernel<T, NT, 8, 1>;
     if (a.nl.K != 8) {
         k = row_kernel<T, NT, 0, 1>;
-    } else if constexpr (sizeof(T) == 4 && NT >= 256) {
+    } else if constexpr (sizeof(T) == 4 && fft_nt(NT) >= 256) {
+        constexpr int NT1 = fft_tag(NT, 1);
         if (a.variant == 1) k = row_kernel<T, NT, 8, mb_of<NT>(1)>;
         else if (a.variant == 2) k = row_kernel<T, NT, 8, mb_of<NT>(2)>;
+        else if (a.variant == 4 && a.tw1) k = row_kernel<T, NT1, 8, mb_of<NT1>(1)>;
+        else if (a.variant == 5 && a.tw1) k = row_kernel<T, NT1, 8, mb_of<NT1>(2)>;
     }
     return launch_k(k, dim3(grid), dim3(C::THREADS), smem, st, a);
 }

@@ -37,6 +37,7 @@ struct fcn_xy_ctx {
     double *red = nullptr;          // [16]
     double *host_red = nullptr;     // pinned [16]
     const void *tw = nullptr;
+    const void *tw1 = nullptr;   // twiddles of FFT plan 1 (FP32, Nt >= 256), or null
     // pivot tables of the current dz: x lines (no dispersion), y lines
     uint64_t tab_dz = 0;
     void *tab_x = nullptr, *tab_y = nullptr;
@@ -110,6 +111,7 @@ RowArgs<T> row_args(fcn_xy_ctx *ctx, void *field, int ops, double dz) {
     RowArgs<T> a;
     a.field = (cx<T> *)field;
     a.tw = (const cx<T> *)ctx->tw;
+    a.tw1 = (const cx<T> *)ctx->tw1;
     a.rho = (T *)ctx->rho;
     a.stats = ctx->stats;
     a.nr = (int)ctx->rows();
@@ -449,9 +451,11 @@ int fcn_xy_create(const fcn_grid_xy *grid, const fcn_params *params, int32_t pre
             ctx->tw = tw;
             if (e == cudaSuccess) e = prepare_rows<double>(grid->nt);
         } else {
-            const cx<float> *tw;
+            const cx<float> *tw, *tw1 = nullptr;
             e = hostx::twiddles<float>(grid->nt, &tw);
+            if (e == cudaSuccess && grid->nt >= 256) e = hostx::twiddles<float>(fft_tag(grid->nt, 1), &tw1);
             ctx->tw = tw;
+            ctx->tw1 = tw1;
             if (e == cudaSuccess) e = prepare_rows<float>(grid->nt);
         }
     }

@@ -542,7 +542,7 @@ def test_adaptive_batch_of_different_pulses(fcn, controller):
 # ------------------------------------------------- autotuner and variants
 
 @pytest.mark.parametrize("prec", [FP64, FP32])
-@pytest.mark.parametrize("row_v", [0, 1, 2, 3])
+@pytest.mark.parametrize("row_v", [0, 1, 2, 3, 4, 5])
 @pytest.mark.parametrize("col_v", [0, 1, 2, 3, 4, 5, 6, 7, 8])
 def test_every_kernel_variant_matches_oracle(fcn, prec, row_v, col_v):
     """Every variant the autotuner can pick computes the same step."""
@@ -559,10 +559,11 @@ def test_every_kernel_variant_matches_oracle(fcn, prec, row_v, col_v):
     assert rel_l2(A, Aref) < (1e-10 if prec == FP64 else 1e-5)
 
 
-@pytest.mark.parametrize("row_v", [0, 1, 2, 3])
+@pytest.mark.parametrize("row_v", [0, 1, 2, 3, 4, 5])
 def test_row_occupancy_variants_at_nt_256(fcn, row_v):
     """Nt = 256 rows (config 1, the Cartesian grid) have their own FP32
-    occupancy variants (3 and 4 CTAs per SM)."""
+    occupancy variants (3 and 4 CTAs per SM) and the radix-8 FFT plan
+    (2 8 16 instead of 16 16)."""
     wl = W.small(70, 256, p_over_pcr=4.0, noise_seed=8)
     s = fcn.Solver(wl.physics(), precision=FP32)
     s.set_variants(row_v, 0)
@@ -572,6 +573,29 @@ def test_row_occupancy_variants_at_nt_256(fcn, row_v):
     s.close()
     Aref, _ = oracle.run(_pb(wl), 1e-2, 6, wl.field())
     assert rel_l2(A, Aref) < 1e-5
+
+
+@pytest.mark.parametrize("nt", [256, 512, 1024, 2048, 4096, 8192])
+@pytest.mark.parametrize("row_v", [4, 5])
+def test_radix8_fft_plan_every_nt(fcn, nt, row_v):
+    """Row variants 4 and 5 run the other FFT decomposition (radix-8 passes
+    before the last radix-16 pass: 2 8 16 at Nt = 256, 4 8 16, 8 8 16,
+    2 8 8 16, 4 8 8 16, 8 8 8 16 at 8192) in the fused row stage, with its
+    own twiddle table: against the oracle over whole steps, and within FP32
+    rounding of the radix-16 plan (variant 1 or 2, same occupancy)."""
+    wl = W.small(24, nt, p_over_pcr=4.0, noise_seed=12).with_(n2j=(W.N2, W.N4, 0, 0))
+    out = {}
+    for v in (row_v, row_v - 3):
+        s = fcn.Solver(wl.physics(), precision=FP32)
+        s.set_variants(v, 0)
+        s.set_field(wl.field())
+        s.step(5e-3, 5)
+        assert s.variants() == (v, 0)
+        out[v] = s.get_field()
+        s.close()
+    Aref, _ = oracle.run(_pb(wl), 5e-3, 5, wl.field())
+    assert rel_l2(out[row_v], Aref) < 1e-5
+    assert rel_l2(out[row_v], out[row_v - 3]) < 1e-5
 
 
 @pytest.mark.parametrize("prec", [FP64, FP32])
