@@ -141,14 +141,21 @@ __global__ void cn_table_kernel_f32(TableArgs a, cx<float> *table) {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= nq) return;
     const double delta = a.dk * double(q) * double(q);
+    const cx<double> lim = (a.cc || a.pivlim) ? piv_limit(a.s, a.dk, q) : cx<double>{0.0, 0.0};
     if (a.cc) {
-        const cx<double> lim = piv_limit(a.s, a.dk, q);
         const CdCol<float> c = cd_col<float>(a.s, a.dk, q);
         const float hx = float(lim.x), hy = float(lim.y);
         a.cc[q].lim = make_float4(hx, hy, float(lim.x - double(hx)), float(lim.y - double(hy)));
         a.cc[q].cd = make_float4(c.ah, c.al, c.ih, c.il);
     }
     const f2 by0 = to_f2(4.0 * a.s - delta), by1 = to_f2(2.0 * a.s - delta);
+    // the column's pivot limit as double-float pairs (FP64 once per thread:
+    // the loop below stays in FP32 arithmetic)
+    f2 lx = {0.f, 0.f}, ly = {0.f, 0.f};
+    if (a.pivlim) {
+        lx = to_f2(lim.x);
+        ly = to_f2(lim.y);
+    }
     f2 ix = {0.f, 0.f}, iy = {0.f, 0.f};
     const f2 one = {1.f, 0.f};
     for (int j = 0; j < a.nr; ++j) {
@@ -160,15 +167,10 @@ __global__ void cn_table_kernel_f32(TableArgs a, cx<float> *table) {
         ix = df_mul(wx, rn);
         iy = df_mul(wy, rn);
         iy = {-iy.h, -iy.l};
-        cx<float> e;
-        if (a.pivlim) {
-            // relative to the column's limit (piv_limit), in FP64 from the
-            // double-float value
-            const cx<double> lim = piv_limit(a.s, a.dk, q);
-            e = mk(float((double(ix.h) + double(ix.l)) - lim.x), float((double(iy.h) + double(iy.l)) - lim.y));
-        } else {
-            e = mk(ix.h + ix.l, iy.h + iy.l);
-        }
+        // relative to the column's limit (piv_limit): the hi parts differ
+        // exactly where the pivot has settled (Sterbenz), then the lo parts
+        const cx<float> e = a.pivlim ? mk((ix.h - lx.h) + (ix.l - lx.l), (iy.h - ly.h) + (iy.l - ly.l))
+                                     : mk(ix.h + ix.l, iy.h + iy.l);
         table[FCN_IDX((size_t)j * tp + q, (size_t)a.nr * tp, 30)] = e;
     }
 }

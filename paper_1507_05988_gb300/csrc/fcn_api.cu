@@ -726,7 +726,7 @@ bool same_row_launch(const RowArgs<T> &a, const RowArgs<T> &b) {
 template <typename T>
 cudaError_t launch_group(fcn_ctx *ctx, int kind, double dz, cudaStream_t st,
                          const std::vector<const cx<T> *> &tabs, const std::vector<void *> *fields,
-                         size_t i, size_t *m_out) {
+                         size_t i, size_t *m_out, const std::vector<void *> *srcs = nullptr) {
     cudaError_t e = cudaSuccess;
     {
         // pulses i and i+1 share the column launch when pairing is on and
@@ -737,7 +737,9 @@ cudaError_t launch_group(fcn_ctx *ctx, int kind, double dz, cudaStream_t st,
         auto rows1 = [&](size_t k, int ops, int pk) {
             Pulse &pu = ctx->pulses[k];
             void *f = fields ? (*fields)[k] : pu.field;
-            return timed(ctx, pk, st, [&] { return launch_rows<T>(row_args<T>(pu, f, ops, dz), pu.g.nt, st); });
+            RowArgs<T> a = row_args<T>(pu, f, ops, dz);
+            if (srcs && kind == 0) a.in = (const cx<T> *)(*srcs)[k];
+            return timed(ctx, pk, st, [&] { return launch_rows<T>(a, pu.g.nt, st); });
         };
         // the row stage of the group's pulses (one two-pulse launch when the
         // pair's launches differ only in their buffers and mode 2 is set)
@@ -794,7 +796,7 @@ cudaError_t launch_group(fcn_ctx *ctx, int kind, double dz, cudaStream_t st,
 // most kRowMulti per launch).
 template <typename T>
 cudaError_t launch_rows_all(fcn_ctx *ctx, int ops, int pk, double dz, cudaStream_t st,
-                            const std::vector<void *> *fields) {
+                            const std::vector<void *> *fields, const std::vector<void *> *srcs = nullptr) {
     const size_t n = ctx->pulses.size();
     cudaError_t e = cudaSuccess;
     for (size_t i = 0; i < n && e == cudaSuccess;) {
@@ -810,12 +812,15 @@ cudaError_t launch_rows_all(fcn_ctx *ctx, int ops, int pk, double dz, cudaStream
             m.field[cnt] = ak.field;
             m.rho[cnt] = ak.rho;
             m.stats[cnt] = ak.stats;
+            m.in[cnt] = srcs ? (const cx<T> *)(*srcs)[k] : nullptr;
             ++cnt;
         }
+        m.a.in = m.in[0];
         for (int c = cnt; c < kRowMulti; ++c) {
             m.field[c] = nullptr;
             m.rho[c] = nullptr;
             m.stats[c] = nullptr;
+            m.in[c] = nullptr;
         }
         e = timed(ctx, pk, st, [&] {
             return cnt == 1 ? launch_rows<T>(m.a, p0.g.nt, st) : launch_rows_multi<T>(m, cnt, p0.g.nt, st);
@@ -826,23 +831,27 @@ cudaError_t launch_rows_all(fcn_ctx *ctx, int ops, int pk, double dz, cudaStream
 }
 
 template <typename T>
+// srcs (kind 0 only): the head reads pulse k's rows from srcs[k] and writes
+// them to its field (fields[k]): out of place, no copy of the start field.
 cudaError_t launch_block(fcn_ctx *ctx, int kind, double dz, cudaStream_t st,
                          const std::vector<const cx<T> *> &tabs,
-                         const std::vector<void *> *fields = nullptr) {
+                         const std::vector<void *> *fields = nullptr,
+                         const std::vector<void *> *srcs = nullptr) {
     if (ctx->batched && !fields) return launch_block_batched<T>(ctx, kind, dz, st, tabs);
     cudaError_t e = cudaSuccess;
     const size_t n = ctx->pulses.size();
     size_t m = 1;
     const bool seq_all = ctx->seq_all == 1 && n >= 2;
     if ((ctx->multi_mode != 1 && !seq_all) || n == 1) {
-        for (size_t i = 0; i < n && e == cudaSuccess; i += m) e = launch_group<T>(ctx, kind, dz, st, tabs, fields, i, &m);
+        for (size_t i = 0; i < n && e == cudaSuccess; i += m)
+            e = launch_group<T>(ctx, kind, dz, st, tabs, fields, i, &m, srcs);
         return e;
     }
     // multi-pulse row launches (mode 1, and always with the sequential
     // column kernel over all pulses): per z-step the column stage of every
     // pulse group, then the row stage of all pulses (each pulse still runs
     // head, (column, row) per step and tail in order)
-    if (kind == 0) return launch_rows_all<T>(ctx, OPS_HEAD, FCN_PROF_ROW_HEAD, dz, st, fields);
+    if (kind == 0) return launch_rows_all<T>(ctx, OPS_HEAD, FCN_PROF_ROW_HEAD, dz, st, fields, srcs);
     const int reps = kind == 1 ? 8 : 1;
     // with the sequential column kernel chosen, all pulses (same grid and
     // pivot table) take one column launch together
@@ -1194,7 +1203,7 @@ int step_impl(fcn_ctx *ctx, double dz, int64_t n, bool use_graph) {
 // One Strang step of length h (or two of h/2) on a work buffer, direct launches.
 template <typename T>
 int substeps(fcn_ctx *ctx, Pulse &pu, void *f, double h, int count, const cx<T> *tab = nullptr,
-             cudaEvent_t table_ready = nullptr, int tail_extra = 0) {
+             cudaEvent_t table_ready = nullptr, int tail_extra = 0, const void *src = nullptr) {
     if (!tab) {
         int rc = ensure_table<T>(ctx, pu, h, &tab);
         if (rc) return rc;
@@ -1204,7 +1213,13 @@ int substeps(fcn_ctx *ctx, Pulse &pu, void *f, double h, int count, const cx<T> 
         int rc = ensure_tuned<T>(ctx, tabs, h);
         if (rc) return rc;
     }
-    CK(launch_rows<T>(row_args<T>(pu, f, OPS_HEAD, h), pu.g.nt, ctx->st), "head");
+    {
+        // src: the head reads its rows there and writes them to f (out of
+        // place: the field an attempt starts from needs no copy)
+        RowArgs<T> a = row_args<T>(pu, f, OPS_HEAD, h);
+        a.in = (const cx<T> *)src;
+        CK(launch_rows<T>(a, pu.g.nt, ctx->st), "head");
+    }
     // the opening row stage does not read the table: a table built on a side
     // stream has until here
     if (table_ready) CK(cudaStreamWaitEvent(ctx->st, table_ready, 0), "table wait");
@@ -1306,9 +1321,9 @@ int propagate_batch(fcn_ctx *ctx, double z_end, double dz0, double rtol, double 
         if (!pu.work2) CK(cudaMalloc(&pu.work2, bytes), "work buffer");
     }
     const bool features = controller == 1;
-    // per pulse: the controller kernel's output (8 doubles) on the device;
-    // norms, features, proposal and energy on the host.  Regrown when pulses
-    // were added since the last batch.
+    // per pulse: the controller kernel's output (8 doubles) on the device and
+    // its copy on the host (norms, features, proposal, energy).  Regrown
+    // when pulses were added since the last batch.
     if (ctx->batch_cap < n) {
         cudaFree(ctx->batch_io);
         if (ctx->host_ctl) cudaFreeHost(ctx->host_ctl);
@@ -1335,14 +1350,14 @@ int propagate_batch(fcn_ctx *ctx, double z_end, double dz0, double rtol, double 
             Pulse &pu = ctx->pulses[i];
             int rc = diag_device<T>(ctx, pu, pu.field);
             if (rc) return rc;
-            CK(cudaMemcpyAsync(H + 16 * i, pu.red, 8 * sizeof(double), cudaMemcpyDeviceToHost, ctx->st), "ref copy");
+            CK(cudaMemcpyAsync(H + 8 * i, pu.red, 8 * sizeof(double), cudaMemcpyDeviceToHost, ctx->st), "ref copy");
         }
         CK(cudaStreamSynchronize(ctx->st), "ref sync");
         for (size_t i = 0; i < n; ++i) {
-            sc[i].i_ref = H[16 * i + 1] > 0 ? H[16 * i + 1] : 1.0;
+            sc[i].i_ref = H[8 * i + 1] > 0 ? H[8 * i + 1] : 1.0;
             sc[i].peak_prev = sc[i].i_ref;
             peak[i] = (float)sc[i].i_ref;
-            sc[i].e_prev = H[16 * i];
+            sc[i].e_prev = H[8 * i];
             sc[i].dz_prev = dz0;
             sc[i].err_prev = rtol;
         }
@@ -1352,7 +1367,7 @@ int propagate_batch(fcn_ctx *ctx, double z_end, double dz0, double rtol, double 
     double z = ctx->pulses[0].z, dz = dz0;
     int consecutive = 0, cooldown = 0, status = FCN_OK;
     bool from_mlp = false;
-    std::vector<void *> f1(n), f2(n);
+    std::vector<void *> f0(n), f1(n), f2(n);
     std::vector<const cx<T> *> tab1(n), tab2(n);
     while (z < z_end) {
         double h = dz;
@@ -1367,21 +1382,52 @@ int propagate_batch(fcn_ctx *ctx, double z_end, double dz0, double rtol, double 
             int rc = ensure_table<T>(ctx, pu, h, &tab1[i], side1, side1 >= 0 ? &ev1 : nullptr);
             if (!rc) rc = ensure_table<T>(ctx, pu, 0.5 * h, &tab2[i], side2, side2 >= 0 ? &ev2 : nullptr);
             if (rc) return rc;
-            const size_t bytes = csize(ctx->prec) * pu.points();
-            CK(cudaMemcpyAsync(pu.work1, pu.field, bytes, cudaMemcpyDeviceToDevice, ctx->st), "copy");
-            CK(cudaMemcpyAsync(pu.work2, pu.field, bytes, cudaMemcpyDeviceToDevice, ctx->st), "copy");
             f1[i] = pu.work1;
             f2[i] = pu.work2;
+            f0[i] = pu.field;
         }
-        CK(launch_block<T>(ctx, 0, h, ctx->st, tab1, &f1), "head");
+        // the heads read the start field and write the work buffers
+        CK(launch_block<T>(ctx, 0, h, ctx->st, tab1, &f1, &f0), "head");
         if (ev1) CK(cudaStreamWaitEvent(ctx->st, ev1, 0), "table wait");
         CK(launch_block<T>(ctx, 3, h, ctx->st, tab1, &f1), "one step");
-        CK(launch_block<T>(ctx, 0, 0.5 * h, ctx->st, tab2, &f2), "head");
+        CK(launch_block<T>(ctx, 0, 0.5 * h, ctx->st, tab2, &f2, &f0), "head");
         if (ev2) CK(cudaStreamWaitEvent(ctx->st, ev2, 0), "table wait");
         CK(launch_block<T>(ctx, 2, 0.5 * h, ctx->st, tab2, &f2), "first half step");
         CK(launch_block<T>(ctx, 3, 0.5 * h, ctx->st, tab2, &f2), "second half step");
         const bool next_feat = features && !last;
-        for (size_t i = 0; i < n; ++i) {
+        if (same_grid && n <= (size_t)kCtlMulti) {
+            // every pulse's norm partials in one launch, then norm, features
+            // and (no cooldown) the proposals in one launch, one copy
+            DiffMulti<T> dm;
+            CtlMulti cm;
+            std::memset(&dm, 0, sizeof dm);
+            std::memset(&cm, 0, sizeof cm);
+            dm.nr = cm.nr = ctx->pulses[0].g.nr;
+            dm.nt = ctx->pulses[0].g.nt;
+            dm.n = cm.n = (int)n;
+            cm.out = reinterpret_cast<double *>(ctx->batch_io);
+            for (size_t i = 0; i < n; ++i) {
+                Pulse &pu = ctx->pulses[i];
+                dm.a[i] = (const cx<T> *)pu.work1;
+                dm.c[i] = (const cx<T> *)pu.work2;
+                dm.rows[i] = pu.rows;
+                cm.stats[i] = pu.stats;
+                cm.rows[i] = pu.rows;
+                if (next_feat) {
+                    sc[i].peak_prev = peak[i];
+                    sc[i].dz_prev = h;
+                    sc[i].dz_lo = std::fmax(0.2 * h, dz_min);
+                    sc[i].dz_hi = 2.0 * h;
+                }
+                cm.sc[i] = sc[i];
+            }
+            CK(launch_diff_rows_multi<T>(dm, ctx->st), "error norm");
+            CK(launch_mlp_step_control_multi(cm, next_feat && cooldown == 0 ? ctx->mlp : nullptr, ctx->st),
+               "controller");
+            CK(cudaMemcpyAsync(H, ctx->batch_io, 8 * sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->st),
+               "controller copy");
+        }
+        for (size_t i = 0; i < n && !(same_grid && n <= (size_t)kCtlMulti); ++i) {
             Pulse &pu = ctx->pulses[i];
             if (next_feat) {
                 // the closing row launch left this pulse's statistics of work2:
@@ -1399,12 +1445,12 @@ int propagate_batch(fcn_ctx *ctx, double z_end, double dz0, double rtol, double 
                 CK(launch_mlp_step_control(pu.stats, pu.g.nr, pu.rows, sc[i], cooldown == 0 ? ctx->mlp : nullptr,
                                            ctl, ctx->st),
                    "controller");
-                CK(cudaMemcpyAsync(H + 16 * i, ctl, 8 * sizeof(double), cudaMemcpyDeviceToHost, ctx->st),
+                CK(cudaMemcpyAsync(H + 8 * i, ctl, 8 * sizeof(double), cudaMemcpyDeviceToHost, ctx->st),
                    "controller copy");
             } else {
                 CK(launch_diff_norm<T>((const cx<T> *)pu.work1, (const cx<T> *)pu.work2, pu.g.nr, pu.g.nt,
                                        pu.rows, pu.red, ctx->st), "error norm");
-                CK(cudaMemcpyAsync(H + 16 * i, pu.red, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->st),
+                CK(cudaMemcpyAsync(H + 8 * i, pu.red, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->st),
                    "norm copy");
             }
         }
@@ -1412,7 +1458,7 @@ int propagate_batch(fcn_ctx *ctx, double z_end, double dz0, double rtol, double 
         double err = 0.0;
         std::vector<double> erri(n);
         for (size_t i = 0; i < n; ++i) {
-            erri[i] = H[16 * i + 1] > 0 ? std::sqrt(H[16 * i] / H[16 * i + 1]) : std::sqrt(H[16 * i]);
+            erri[i] = H[8 * i + 1] > 0 ? std::sqrt(H[8 * i] / H[8 * i + 1]) : std::sqrt(H[8 * i]);
             if (!std::isfinite(erri[i])) err = erri[i];
             else if (std::isfinite(err)) err = std::fmax(err, erri[i]);
         }
@@ -1438,11 +1484,11 @@ int propagate_batch(fcn_ctx *ctx, double z_end, double dz0, double rtol, double 
                 double prop = 0.0;
                 for (size_t i = 0; i < n; ++i) {
                     float hf[8];
-                    std::memcpy(hf, H + 16 * i + 2, sizeof hf);
+                    std::memcpy(hf, H + 8 * i + 2, sizeof hf);
                     peak[i] = hf[7];
                     sc[i].err_prev = erri[i];
-                    sc[i].e_prev = H[16 * i + 7];
-                    const double p = H[16 * i + 6];
+                    sc[i].e_prev = H[8 * i + 7];
+                    const double p = H[8 * i + 6];
                     if (std::isfinite(p) && p > 0) prop = prop > 0 ? std::fmin(prop, p) : p;
                 }
                 if (cooldown > 0) {
@@ -1543,15 +1589,14 @@ int propagate_impl(fcn_ctx *ctx, double z_end, double dz0, double rtol, double d
         int rc = ensure_table<T>(ctx, pu, h, &tab1, 0, &ev1);
         if (!rc) rc = ensure_table<T>(ctx, pu, 0.5 * h, &tab2, 1, &ev2);
         if (rc) return rc;
-        CK(cudaMemcpyAsync(pu.work1, pu.field, bytes, cudaMemcpyDeviceToDevice, ctx->st), "copy");
-        CK(cudaMemcpyAsync(pu.work2, pu.field, bytes, cudaMemcpyDeviceToDevice, ctx->st), "copy");
-        rc = substeps<T>(ctx, pu, pu.work1, h, 1, tab1, ev1);
+        // the heads read the start field and write the work buffers (no copies)
+        rc = substeps<T>(ctx, pu, pu.work1, h, 1, tab1, ev1, 0, pu.field);
         // the closing launch of the two half steps leaves the statistics of
         // the field it produces (peak, on-axis peak, peak rho, energy), from
         // which the features and the proposal of an accepted attempt follow
         // without a pass of their own
         const bool next_feat = features && !last;
-        if (!rc) rc = substeps<T>(ctx, pu, pu.work2, 0.5 * h, 2, tab2, ev2, 0);
+        if (!rc) rc = substeps<T>(ctx, pu, pu.work2, 0.5 * h, 2, tab2, ev2, 0, pu.field);
         if (rc) return rc;
         if (next_feat) {
             // the norm, the features of work2 and (speculative, used only

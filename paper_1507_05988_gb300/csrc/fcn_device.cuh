@@ -228,6 +228,8 @@ struct RowArgs {
     NLCoef<T> nl;
     int *err = nullptr;   // set nonzero by a kernel whose bounded wait gave up
     const cx<T> *tw1 = nullptr;   // twiddle table of FFT plan 1 (variants 4, 5)
+    const cx<T> *in = nullptr;    // rows read from here instead of field (output
+                                  // still to field; may not alias it), or null
 };
 
 // One launch of the row stage over up to kRowMulti pulses that share the
@@ -240,6 +242,7 @@ struct RowMultiArgs {
     cx<T> *field[kRowMulti];
     T *rho[kRowMulti];
     double *stats[kRowMulti];
+    const cx<T> *in[kRowMulti] = {};   // per pulse as RowArgs::in (null: field)
 };
 
 // Per-row coefficients of the Crank-Nicolson system (Eqs. (Ma)-(Mb)) for one
@@ -573,6 +576,29 @@ cudaError_t launch_mlp_adam(float *W, float *m, float *v, const float *g, float 
 // fE, peak), dz, energy sum]
 cudaError_t launch_mlp_step_control(const double *stats, int nr, const double *diff_rows, const MlpScalars &sc,
                                     const float *W, double *out, cudaStream_t st);
+// The same for up to kCtlMulti pulses on one grid in one launch (a CTA per
+// pulse): pulse b reads stats[b], rows[b] (null: no norm), sc[b] and writes
+// out + 8 b.
+constexpr int kCtlMulti = 8;
+struct CtlMulti {
+    const double *stats[kCtlMulti];
+    const double *rows[kCtlMulti];
+    MlpScalars sc[kCtlMulti];
+    double *out;
+    int nr, n;
+};
+cudaError_t launch_mlp_step_control_multi(const CtlMulti &p, const float *W, cudaStream_t st);
+// Per-row norm partials of up to kCtlMulti pulses on one grid in one launch
+// (grid nr x n): pulse b compares a[b] with c[b] into rows[b].
+template <typename T>
+struct DiffMulti {
+    const cx<T> *a[kCtlMulti];
+    const cx<T> *c[kCtlMulti];
+    double *rows[kCtlMulti];
+    int nr, nt, n;
+};
+template <typename T>
+cudaError_t launch_diff_rows_multi(const DiffMulti<T> &p, cudaStream_t st);
 
 // reductions and conversions
 template <typename T>

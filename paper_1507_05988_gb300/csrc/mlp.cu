@@ -462,9 +462,8 @@ __global__ void mlp_adam(float *W, float *m, float *v, const float *__restrict__
 // out[0..1] = norm (0 without diff_rows); out[2..5] = the 8 feature floats
 // (f0..f5, fE, peak); out[6] = proposal (0 without W); out[7] = energy sum.
 constexpr int CT = 256;
-__global__ void __launch_bounds__(CT)
-mlp_step_control(const double *__restrict__ st, int nr, const double *__restrict__ diff_rows, MlpScalars sc,
-                 const float *__restrict__ W, double *out) {
+__device__ __forceinline__ void step_control(const double *__restrict__ st, int nr, const double *__restrict__ diff_rows,
+                                             MlpScalars sc, const float *__restrict__ W, double *out) {
     __shared__ float sw[NP];
     __shared__ float sx[NIN], h1[NH], h2[NH], r[2];
     __shared__ double sh[32];
@@ -536,6 +535,18 @@ mlp_step_control(const double *__restrict__ st, int nr, const double *__restrict
     }
 }
 
+__global__ void __launch_bounds__(CT)
+mlp_step_control(const double *__restrict__ st, int nr, const double *__restrict__ diff_rows, MlpScalars sc,
+                 const float *__restrict__ W, double *out) {
+    step_control(st, nr, diff_rows, sc, W, out);
+}
+
+// The same for the pulses of an adaptive batch on one grid, a CTA per pulse.
+__global__ void __launch_bounds__(CT) mlp_step_control_multi(const __grid_constant__ CtlMulti p, const float *W) {
+    const int b = blockIdx.x;
+    step_control(p.stats[b], p.nr, p.rows[b], p.sc[b], W, p.out + 8 * b);
+}
+
 }  // namespace
 
 int mlp_nparam() { return NP; }
@@ -543,6 +554,12 @@ int mlp_nparam() { return NP; }
 cudaError_t launch_mlp_step_control(const double *stats, int nr, const double *diff_rows, const MlpScalars &sc,
                                     const float *W, double *out, cudaStream_t st) {
     mlp_step_control<<<1, CT, 0, st>>>(stats, nr, diff_rows, sc, W, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_step_control_multi(const CtlMulti &p, const float *W, cudaStream_t st) {
+    if (p.n < 1 || p.n > kCtlMulti) return cudaErrorInvalidValue;
+    mlp_step_control_multi<<<p.n, CT, 0, st>>>(p, W);
     return cudaGetLastError();
 }
 

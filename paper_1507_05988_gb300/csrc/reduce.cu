@@ -90,6 +90,25 @@ __global__ void diff_rows_kernel(const cx<T> *a, const cx<T> *b, int nt, double 
     if (threadIdx.x == 0) rows[2 * m + 1] = b2;
 }
 
+template <typename T>
+__global__ void diff_rows_multi_kernel(const __grid_constant__ DiffMulti<T> p) {
+    __shared__ double sh[32];
+    const int m = blockIdx.x, b = blockIdx.y;
+    const cx<T> *ra = p.a[b] + (size_t)m * p.nt;
+    const cx<T> *rb = p.c[b] + (size_t)m * p.nt;
+    double d2 = 0.0, b2 = 0.0;
+    for (int q = threadIdx.x; q < p.nt; q += blockDim.x) {
+        const cx<T> x = ra[q], y = rb[q];
+        const double dx = double(x.x) - double(y.x), dy = double(x.y) - double(y.y);
+        d2 += dx * dx + dy * dy;
+        b2 += double(y.x) * double(y.x) + double(y.y) * double(y.y);
+    }
+    d2 = block_sum(d2, sh);
+    if (threadIdx.x == 0) p.rows[b][2 * m] = d2;
+    b2 = block_sum(b2, sh);
+    if (threadIdx.x == 0) p.rows[b][2 * m + 1] = b2;
+}
+
 __global__ void diff_final_kernel(const double *rows, int nr, double *out) {
     __shared__ double sh[32];
     double d2 = 0.0, b2 = 0.0;
@@ -167,6 +186,12 @@ cudaError_t launch_diff_rows(const cx<T> *a, const cx<T> *b, int nr, int nt, dou
     return cudaGetLastError();
 }
 template <typename T>
+cudaError_t launch_diff_rows_multi(const DiffMulti<T> &p, cudaStream_t st) {
+    if (p.n < 1 || p.n > kCtlMulti || p.nr < 1) return cudaErrorInvalidValue;
+    diff_rows_multi_kernel<T><<<dim3(p.nr, p.n), RT, 0, st>>>(p);
+    return cudaGetLastError();
+}
+template <typename T>
 cudaError_t launch_diff_norm(const cx<T> *a, const cx<T> *b, int nr, int nt, double *rows,
                              double *out, cudaStream_t st) {
     diff_rows_kernel<T><<<nr, RT, 0, st>>>(a, b, nt, rows);
@@ -187,6 +212,7 @@ cudaError_t launch_profiles(const cx<T> *f, int nr, int nt, double *power, doubl
     template cudaError_t launch_widen_real<T>(const T *, double *, int64_t, cudaStream_t); \
     template cudaError_t launch_diff_rows<T>(const cx<T> *, const cx<T> *, int, int, double *, \
                                              cudaStream_t);                                \
+    template cudaError_t launch_diff_rows_multi<T>(const DiffMulti<T> &, cudaStream_t);        \
     template cudaError_t launch_diff_norm<T>(const cx<T> *, const cx<T> *, int, int, double *, \
                                              double *, cudaStream_t);                      \
     template cudaError_t launch_profiles<T>(const cx<T> *, int, int, double *, double *,   \

@@ -892,6 +892,8 @@ __device__ __forceinline__ void row_body(const RowArgs<T> &a, int row_base, int 
     cx<T> *S = S_all + rloc * C::PADN;
     T *U = U_all + rloc * C::PADN;
     cx<T> *g = a.field + (size_t)(valid ? row : 0) * C::N;
+    // the row's input: the field itself, or a separate source (out of place)
+    const cx<T> *gin = a.in ? a.in + (size_t)(valid ? row : 0) * C::N : g;
 
     cx<T> v[E];
     if (ops & OP_IFFT) {
@@ -900,7 +902,7 @@ __device__ __forceinline__ void row_body(const RowArgs<T> &a, int row_base, int 
         constexpr int PL = C::NPASS - 1;
         constexpr int RL = PassCfg<NT, PL>::R;
         constexpr int NSL = PassCfg<NT, PL>::NS;
-        const cx<T> *src = PF ? xs + rloc * C::N : g;
+        const cx<T> *src = PF ? xs + rloc * C::N : gin;
 #pragma unroll
         for (int i = 0; i < E / RL; ++i) {
             const int j = t + C::TPR * i;
@@ -911,7 +913,7 @@ __device__ __forceinline__ void row_body(const RowArgs<T> &a, int row_base, int 
         InvDispatch<T, NT, PL, (PL < 0)>::run(v, S, t, C::PLAN ? a.tw1 : a.tw, a.nl.inv_nt);
         hook();
     } else {
-        const cx<T> *src = PF ? xs + rloc * C::N : g;
+        const cx<T> *src = PF ? xs + rloc * C::N : gin;
 #pragma unroll
         for (int i = 0; i < E; ++i) {
             const int idx = t + C::TPR * i;
@@ -1095,6 +1097,7 @@ row_kernel_multi(const __grid_constant__ RowMultiArgs<T> m) {
     a.field = m.field[blockIdx.y];
     a.rho = m.rho[blockIdx.y];
     a.stats = m.stats[blockIdx.y];
+    a.in = m.in[blockIdx.y];
     row_body<T, NT, KT, RowCfg<NT>::THREADS>(a, blockIdx.x * RowCfg<NT>::RPC, a.ops, smem_raw);
 }
 
@@ -1149,7 +1152,7 @@ row_kernel_pf(const __grid_constant__ RowMultiArgs<T> m, int npulse, int *err) {
         const int pulse = u / upp, row0 = (u - pulse * upp) * C::RPC;
         const int rows = min(C::RPC, a0.nr - row0);
         const uint32_t bytes = (uint32_t)(rows * C::N * sizeof(cx<T>));
-        const cx<T> *src = m.field[pulse] + (size_t)row0 * C::N;
+        const cx<T> *src = (m.in[pulse] ? m.in[pulse] : m.field[pulse]) + (size_t)row0 * C::N;
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
         asm volatile(
             "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
@@ -1347,6 +1350,7 @@ cudaError_t launch_nt(const RowArgs<T> &a, cudaStream_t st) {
                 m.field[c] = a.field;
                 m.rho[c] = a.rho;
                 m.stats[c] = a.stats;
+                m.in[c] = a.in;
             }
             return launch_nt_pf<T, NT>(m, 1, st);
         }
