@@ -32,6 +32,8 @@
 // pivot rows from L2.
 #include "col_scan.cuh"
 
+#include <mutex>
+
 namespace fcn {
 namespace {
 
@@ -172,6 +174,139 @@ __global__ void cn_table_kernel_f32(TableArgs a, cx<float> *table) {
         const cx<float> e = a.pivlim ? mk((ix.h - lx.h) + (ix.l - lx.l), (iy.h - ly.h) + (iy.l - ly.l))
                                      : mk(ix.h + ix.l, iy.h + iy.l);
         table[FCN_IDX((size_t)j * tp + q, (size_t)a.nr * tp, 30)] = e;
+    }
+}
+
+// The same table with the rows split into kTabChunks chunks, so that a
+// column's recurrence no longer runs down all Nr rows in one thread.  The
+// step 1/piv_j = 1/(b_j + kappa_j / piv_{j-1}) is a Moebius map of
+// z = 1/piv_{j-1}: z -> (0 z + 1)/(kappa_j z + b_j), i.e. the matrix
+// F_j = [[0, 1], [kappa_j, b_j]] acting on (num, den), z = num/den.
+//   1. warp c composes its chunk's matrices, G_c = F_{j1-1} ... F_{j0}
+//      (double-float complex entries, rescaled by powers of two now and
+//      then: z is a ratio, so the common scale is free);
+//   2. warp 0 walks the chunks from (num, den) = (0, 1) (1/piv_{-1} = 0),
+//      giving each chunk the z that enters it;
+//   3. warp c runs the recurrence of cn_table_kernel_f32 over its rows from
+//      that z and stores the table.
+// The entering z comes from the matrix products instead of the recurrence
+// itself, so the two kernels agree to double-float precision (~1e-14), not
+// bit for bit.  Lane = frequency bin (32 per CTA).
+constexpr int kTabChunks = 16;
+struct c2 {
+    f2 re, im;
+};
+__device__ __forceinline__ f2 df_neg(f2 a) { return {-a.h, -a.l}; }
+__device__ __forceinline__ f2 df_scale(f2 a, float p2) { return {a.h * p2, a.l * p2}; }   // p2 a power of 2
+__device__ __forceinline__ c2 c2_add(c2 a, c2 b) { return {df_add(a.re, b.re), df_add(a.im, b.im)}; }
+__device__ __forceinline__ c2 c2_real(f2 k, c2 a) { return {df_mul(k, a.re), df_mul(k, a.im)}; }
+// (1 + i by) a
+__device__ __forceinline__ c2 c2_b(f2 by, c2 a) {
+    return {df_add(a.re, df_neg(df_mul(by, a.im))), df_add(a.im, df_mul(by, a.re))};
+}
+__device__ __forceinline__ c2 c2_mul(c2 a, c2 b) {
+    return {df_add(df_mul(a.re, b.re), df_neg(df_mul(a.im, b.im))), df_add(df_mul(a.re, b.im), df_mul(a.im, b.re))};
+}
+__device__ __forceinline__ c2 c2_scale(c2 a, float p2) { return {df_scale(a.re, p2), df_scale(a.im, p2)}; }
+__device__ __forceinline__ int c2_exp(c2 a) {
+    int e = 0;
+    frexpf(fmaxf(fabsf(a.re.h), fabsf(a.im.h)), &e);
+    return e;
+}
+// rescales the entries by a common power of two so that the largest is O(1)
+__device__ __forceinline__ void c2_norm(c2 *v, int n) {
+    int e = -1000;
+    for (int k = 0; k < n; ++k)
+        if (v[k].re.h != 0.f || v[k].im.h != 0.f) e = max(e, c2_exp(v[k]));
+    if (e == -1000 || e == 0) return;
+    const float p2 = ldexpf(1.f, -e);
+    for (int k = 0; k < n; ++k) v[k] = c2_scale(v[k], p2);
+}
+
+__global__ void __launch_bounds__(32 * kTabChunks) cn_table_kernel_f32_chunked(TableArgs a, cx<float> *table) {
+    extern __shared__ double sh_tab[];
+    f2 *kap = reinterpret_cast<f2 *>(sh_tab);                         // [nr]
+    c2 *G = reinterpret_cast<c2 *>(kap + a.nr);                      // [kTabChunks][32][4]
+    c2 *Z = G + kTabChunks * 32 * 4;                                 // [kTabChunks][32]
+    const double s2 = a.s * a.s;
+    for (int j = threadIdx.x; j < a.nr; j += blockDim.x) {
+        double k = 0.0;
+        if (j == 1) k = s2 * a.lo[FCN_IDX(1, a.nr, 31)] * 4.0;
+        else if (j >= 2 && j < a.nr - 1) k = s2 * a.lo[FCN_IDX(j, a.nr, 31)] * a.hi[FCN_IDX(j - 1, a.nr, 32)];
+        kap[j] = to_f2(k);
+    }
+    const int lane = threadIdx.x & 31, c = threadIdx.x >> 5;
+    const int nq = a.nt / 2 + 1;
+    const int tp = a.tp ? a.tp : nq;
+    const int q = blockIdx.x * 32 + lane;
+    const bool on = q < nq;
+    const int qc = on ? q : nq - 1;             // lanes past the last bin compute bin nq-1, store nothing
+    const double delta = a.dk * double(qc) * double(qc);
+    const cx<double> lim = (a.cc || a.pivlim) ? piv_limit(a.s, a.dk, qc) : cx<double>{0.0, 0.0};
+    if (a.cc && on && c == 0) {
+        const CdCol<float> cd = cd_col<float>(a.s, a.dk, q);
+        const float hx = float(lim.x), hy = float(lim.y);
+        a.cc[q].lim = make_float4(hx, hy, float(lim.x - double(hx)), float(lim.y - double(hy)));
+        a.cc[q].cd = make_float4(cd.ah, cd.al, cd.ih, cd.il);
+    }
+    const f2 by0 = to_f2(4.0 * a.s - delta), by1 = to_f2(2.0 * a.s - delta);
+    const f2 zero = {0.f, 0.f}, one = {1.f, 0.f};
+    const int L = (a.nr + kTabChunks - 1) / kTabChunks;
+    const int j0 = min(a.nr, c * L), j1 = min(a.nr, j0 + L);
+    auto by_of = [&](int j) { return (j == 0) ? by0 : ((j < a.nr - 1) ? by1 : zero); };
+    __syncthreads();
+    {
+        // 1. this chunk's matrix
+        c2 g[4] = {{one, zero}, {zero, zero}, {zero, zero}, {one, zero}};   // g00 g01 g10 g11
+        for (int j = j0; j < j1; ++j) {
+            const f2 kp = kap[j], by = by_of(j);
+            const c2 n10 = c2_add(c2_real(kp, g[0]), c2_b(by, g[2]));
+            const c2 n11 = c2_add(c2_real(kp, g[1]), c2_b(by, g[3]));
+            g[0] = g[2];
+            g[1] = g[3];
+            g[2] = n10;
+            g[3] = n11;
+            if (((j - j0) & 7) == 7) c2_norm(g, 4);
+        }
+        c2_norm(g, 4);
+        for (int k = 0; k < 4; ++k) G[(c * 32 + lane) * 4 + k] = g[k];
+    }
+    __syncthreads();
+    if (c == 0) {
+        // 2. the z entering every chunk
+        c2 v[2] = {{zero, zero}, {one, zero}};                                // (num, den)
+        for (int k = 0; k < kTabChunks; ++k) {
+            const c2 n = v[0], d = v[1];
+            const f2 rn = df_recip(df_add(df_mul(d.re, d.re), df_mul(d.im, d.im)));
+            const c2 z = c2_mul(n, c2{d.re, df_neg(d.im)});
+            Z[k * 32 + lane] = c2{df_mul(z.re, rn), df_mul(z.im, rn)};
+            const c2 *gk = G + (k * 32 + lane) * 4;
+            v[0] = c2_add(c2_mul(gk[0], n), c2_mul(gk[1], d));
+            v[1] = c2_add(c2_mul(gk[2], n), c2_mul(gk[3], d));
+            c2_norm(v, 2);
+        }
+    }
+    __syncthreads();
+    // 3. the rows of this chunk
+    f2 lx = zero, ly = zero;
+    if (a.pivlim) {
+        lx = to_f2(lim.x);
+        ly = to_f2(lim.y);
+    }
+    const c2 z = Z[c * 32 + lane];
+    f2 ix = z.re, iy = z.im;
+    for (int j = j0; j < j1; ++j) {
+        const f2 kp = kap[j];
+        const f2 by = by_of(j);
+        const f2 wx = df_add(df_mul(kp, ix), one);
+        const f2 wy = df_add(df_mul(kp, iy), by);
+        const f2 rn = df_recip(df_add(df_mul(wx, wx), df_mul(wy, wy)));
+        ix = df_mul(wx, rn);
+        iy = df_mul(wy, rn);
+        iy = {-iy.h, -iy.l};
+        const cx<float> e = a.pivlim ? mk((ix.h - lx.h) + (ix.l - lx.l), (iy.h - ly.h) + (iy.l - ly.l))
+                                     : mk(ix.h + ix.l, iy.h + iy.l);
+        if (on) table[FCN_IDX((size_t)j * tp + q, (size_t)a.nr * tp, 30)] = e;
     }
 }
 
@@ -895,9 +1030,24 @@ template <typename T>
 cudaError_t launch_cn_table(const TableArgs &a, cx<T> *table, cudaStream_t st) {
     const int nq = a.nt / 2 + 1;
     const int threads = 32;   // spread the latency-bound recurrences over many SMs
-    if constexpr (sizeof(T) == 4)
-        cn_table_kernel_f32<<<(nq + threads - 1) / threads, threads, sizeof(double) * a.nr, st>>>(a, table);
-    else
+    if constexpr (sizeof(T) == 4) {
+        if (a.nr >= 128) {
+            // rows in chunks (cn_table_kernel_f32_chunked): the serial
+            // recurrence down a tall column is the cost of a table
+            const size_t smem = sizeof(f2) * a.nr + sizeof(c2) * kTabChunks * 32 * 5;
+            static std::once_flag once;
+            static cudaError_t attr = cudaSuccess;
+            std::call_once(once, [] {
+                attr = cudaFuncSetAttribute(cn_table_kernel_f32_chunked, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)(sizeof(f2) * 4096 + sizeof(c2) * kTabChunks * 32 * 5));
+            });
+            if (attr != cudaSuccess) return attr;
+            if (a.nr > 4096) return cudaErrorInvalidValue;
+            cn_table_kernel_f32_chunked<<<(nq + 31) / 32, 32 * kTabChunks, smem, st>>>(a, table);
+        } else {
+            cn_table_kernel_f32<<<(nq + threads - 1) / threads, threads, sizeof(double) * a.nr, st>>>(a, table);
+        }
+    } else
         cn_table_kernel<T><<<(nq + threads - 1) / threads, threads, sizeof(double) * 2 * a.nr, st>>>(a, table);
     return cudaGetLastError();
 }

@@ -165,6 +165,39 @@ def test_crank_nicolson_columns(fcn, prec, nr, nt, flags):
     assert np.all(out[-1] == 0)
 
 
+@pytest.mark.parametrize("nr", [100, 130, 1000, 2048])
+def test_fp32_pivot_table_is_the_fp64_table_rounded_once(fcn, nr):
+    """The FP32 pivot table (double-float recurrence; from Nr = 128 on, the
+    rows in chunks whose entering values come from products of the
+    recurrence's Moebius matrices) holds 1/pivot_j of the FP64 Thomas
+    factorisation rounded once to float: every entry within one rounding of
+    the oracle's FP64 value."""
+    nt = 64
+    wl = W.small(nr, nt).with_(k2=2e-27)
+    pb = _pb(wl)
+    dz = 2e-2
+    g, p = _gp(fcn, wl)
+    ent = fcn.fcn_cn_table_entries(C.byref(g))
+    table = torch.zeros(ent, dtype=torch.complex64, device="cuda")
+    assert fcn.fcn_op_cn_table(C.byref(g), C.byref(p), FP32, dz, fcn.tensor_ptr(table), fcn.stream_ptr()) == 0
+    torch.cuda.synchronize()
+    tab = table.cpu().numpy().reshape(nr, nt // 2 + 1).astype(np.complex128)
+    worst = 0.0
+    for q in range(nt // 2 + 1):
+        a, b, c, _, _, _ = oracle.cn_coeffs(pb, dz, q)
+        inv = np.empty(nr, np.complex128)
+        cp = 0.0
+        for j in range(nr):
+            den = b[j] - (a[j] * cp if j > 0 else 0.0)
+            inv[j] = 1.0 / den
+            cp = c[j] * inv[j]
+        err = np.abs(tab[:, q] - inv) / np.abs(inv)
+        worst = max(worst, float(err.max()))
+    # one rounding per component: half an ulp, or a whole one where the
+    # double-float value and the FP64 one fall on either side of a midpoint
+    assert worst < 2.0 ** -23
+
+
 # ------------------------------------------------------------- full steps
 
 def _run_gpu(fcn, wl, prec, dz, n, graph=True):
