@@ -407,22 +407,20 @@ __host__ __device__ inline cx<double> piv_limit(double s, double dk, int qq) {
     return inv;
 }
 
-// The limit as the column kernels use it: off (plain 1/pivot tables, and
-// always in FP64), or on with 1/p_inf = h + l two-float.
+// The limit as the column kernels use it: 1/p_inf = h + l two-float, or
+// h = l = 0 for plain 1/pivot tables (stateless FP32 launches; FP64 always),
+// with which piv_full and piv_apply reduce to the plain forms exactly.
 template <typename T>
 struct PivLim {
     cx<T> h, l;
-    bool on;
 };
 template <typename T>
 __device__ __forceinline__ PivLim<T> piv_lim(int pivlim, double s, double dk, int qq) {
     PivLim<T> L;
-    L.on = false;
     L.h = L.l = mk(T(0), T(0));
     if constexpr (sizeof(T) == 4) {
         if (pivlim) {
             const cx<double> v = piv_limit(s, dk, qq);
-            L.on = true;
             L.h = mk(float(v.x), float(v.y));
             L.l = mk(float(v.x - double(L.h.x)), float(v.y - double(L.h.y)));
         }
@@ -450,9 +448,8 @@ __device__ __forceinline__ void col_consts(const ColConst *cc, int pivlim, doubl
             cd->al = c.y;
             cd->ih = c.z;
             cd->il = c.w;
-            L->on = pivlim != 0;
-            L->h = L->on ? mk(lim.x, lim.y) : mk(0.f, 0.f);
-            L->l = L->on ? mk(lim.z, lim.w) : mk(0.f, 0.f);
+            L->h = pivlim ? mk(lim.x, lim.y) : mk(0.f, 0.f);
+            L->l = pivlim ? mk(lim.z, lim.w) : mk(0.f, 0.f);
             return;
         }
     }

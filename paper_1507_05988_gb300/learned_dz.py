@@ -118,22 +118,30 @@ def with_margin(params, m):
     return q
 
 
-def test_one(params, z_test):
-    wl = W.config5(seed=0)
+def test_one(params, z_test, seed=0):
+    wl = W.config5(seed=seed)
     A0, s0, _ = run(wl, z_test, 2e-3)
     A1, s1, _ = run(wl, z_test, 2e-3, controller=1, params=params)
     diff = float(np.linalg.norm(A1 - A0) / np.linalg.norm(A0))
     keys = ("accepted", "rejected", "substeps", "mlp_proposals", "wall_s")
-    return {"workload": f"config-5 pulse (config-2 grid 1024x4096, noise seed 0), "
+    return {"workload": f"config-5 pulse (config-2 grid 1024x4096, noise seed {seed}), "
                         f"0 -> {z_test} m, rtol 1e-4, FP32-mixed",
             "plain": {k: s0[k] for k in keys if k != "mlp_proposals"},
             "learned": {k: s1[k] for k in keys},
             "final_field_rel_l2_learned_vs_plain": diff}
 
 
-def test_only(params, z_test, path) -> int:
-    out = {"test": test_one(params, z_test)}
-    print(json.dumps(out["test"]), flush=True)
+def test_only(params, z_test, path, seeds=(0,)) -> int:
+    """The test pulse at each noise seed (seed 0: config 5 itself; seeds
+    above 100 are held out from training and validation)."""
+    tests = [test_one(params, z_test, sd) for sd in seeds]
+    for t in tests:
+        print(json.dumps(t), flush=True)
+    out = {"test": tests[0] if len(tests) == 1 else tests}
+    if len(tests) > 1:
+        tot = {c: {k: sum(t[c][k] for t in tests) for k in ("substeps", "wall_s")} for c in ("plain", "learned")}
+        out["total"] = tot
+        print(json.dumps({"total": tot}), flush=True)
     if path:
         with open(path, "w") as f:
             json.dump(out, f, indent=1)
@@ -153,9 +161,10 @@ def main(argv=None) -> int:
     ap.add_argument("--save", default="", help="write the trained weights (with the chosen "
                                                 "margin) to this .npy file")
     ap.add_argument("--load", default="", help="skip data and training: test these weights")
+    ap.add_argument("--test-seeds", default="0", help="noise seeds of the test pulse (with --load)")
     a = ap.parse_args(argv)
     if a.load:
-        return test_only(np.load(a.load), a.z_test, a.json)
+        return test_only(np.load(a.load), a.z_test, a.json, _ranges(a.test_seeds))
     zt = [float(v) for v in a.z_train.split(",")]
     zv = [float(v) for v in a.z_val.split(",")]
     out = {"seeds": a.seeds, "z_train_m": zt, "z_val_m": zv, "z_test_m": a.z_test}
