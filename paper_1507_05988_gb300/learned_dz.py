@@ -1,7 +1,11 @@
 """Trains the learned dz controller and compares it with plain step doubling.
 
-    python -m paper_1507_05988_gb300.learned_dz --seeds 1-32 --z-train 2,0.5,5 \
-        --z-val 2,2 --z-test 20 --json out.json --save learned_dz_weights.npy
+    python -m paper_1507_05988_gb300.learned_dz --seeds 1-8 --z-train 2,5,5 \
+        --z-val 2,5 --margins 0,0.05,0.1,0.15,0.2,0.3 --z-test 20 \
+        --json out.json --save learned_dz_weights.npy
+
+(the command that wrote the shipped weights: config 2 runs to 5 m, past the
+collapse, so the data holds filamented states as well as the focusing ones)
 
 1. Data: adaptive runs (plain step doubling, rtol 1e-4, FP32-mixed) of the
    three seeded pulses of configs 1-3 (1 % amplitude noise, seeds as given),
@@ -18,7 +22,8 @@
 4. Margin: the output bias is lowered by m for m on a small grid, each
    candidate run on held-out pulses (noise seed 100 of configs 1 and 2); the
    one with the fewest substeps is kept.
-5. Test: the config-2 pulse (noise seed 0) over z_test m, plain step doubling
+5. Test: the config-5 pulse on the config-2 grid (noise seed 0, or the
+   --test-seeds given with --load) over z_test m, plain step doubling
    against the learned controller: accepted and rejected steps, substeps,
    wall time, and the difference of their final fields.
 """
@@ -151,12 +156,12 @@ def test_only(params, z_test, path, seeds=(0,)) -> int:
 def main(argv=None) -> int:
     ap = argparse.ArgumentParser()
     ap.add_argument("--seeds", default="1-8")
-    ap.add_argument("--z-train", default="2,50,5", help="config 1, 2, 3 training distances [m]")
-    ap.add_argument("--z-val", default="2,20")
-    ap.add_argument("--z-test", type=float, default=1000.0)
+    ap.add_argument("--z-train", default="2,5,5", help="config 1, 2, 3 training distances [m]")
+    ap.add_argument("--z-val", default="2,5")
+    ap.add_argument("--z-test", type=float, default=20.0)
     ap.add_argument("--epochs", type=int, default=300)
     ap.add_argument("--lr", type=float, default=2e-3)
-    ap.add_argument("--margins", default="0,0.05,0.1,0.15,0.2")
+    ap.add_argument("--margins", default="0,0.05,0.1,0.15,0.2,0.3")
     ap.add_argument("--json", default="")
     ap.add_argument("--save", default="", help="write the trained weights (with the chosen "
                                                 "margin) to this .npy file")
