@@ -70,7 +70,7 @@ struct PassCfg {
     static constexpr int NS = fft_ns(NT, P);
 };
 
-__device__ __forceinline__ int pidx(int i, int nt) { return nt >= 16 ? i + (i >> 4) : i; }
+__host__ __device__ __forceinline__ int pidx(int i, int nt) { return nt >= 16 ? i + (i >> 4) : i; }
 
 // cos(2 pi m / 16)
 __host__ __device__ constexpr double cos16(int m) {
@@ -404,7 +404,7 @@ struct FwdDispatch<T, NT, P, true> {
 // NSL is a multiple of 16 the padding is linear in e, so that the indices
 // are one base plus compile-time offsets.
 template <int NT, int NSL>
-__device__ __forceinline__ int own_idx(int q0, int p0, int e) {
+__host__ __device__ __forceinline__ int own_idx(int q0, int p0, int e) {
     if constexpr (fft_nt(NT) >= 16 && NSL % 16 == 0) return q0 + e * (NSL + NSL / 16);
     else return pidx(p0 + e * NSL, fft_nt(NT));
 }
@@ -416,7 +416,7 @@ __device__ __forceinline__ int own_idx(int q0, int p0, int e) {
 // radix E, a thread's E consecutive samples tau = E t + e sit at
 // tpos(E t) + e NS_last.
 template <int NT>
-__device__ __forceinline__ int tpos(int tau) {
+__host__ __device__ __forceinline__ int tpos(int tau) {
     int p = 0;
 #pragma unroll
     for (int s = RowCfg<NT>::NPASS - 1; s >= 0; --s) {
@@ -424,6 +424,70 @@ __device__ __forceinline__ int tpos(int tau) {
         tau /= fft_radix(NT, s);
     }
     return p;
+}
+
+// Time-domain rows between HBM (natural order) and S (digit-reversed
+// positions, tpos).  Consecutive tau sit NS_last apart in S, which for the
+// usual sizes is one bank (4096 points: 272 values apart): lanes moving
+// consecutive tau would meet a 32-way bank conflict on every access of S.
+// Instead, per instruction, lanes 2b and 2b+1 move the two 16-byte halves of
+// one 32-byte sector of line b of a group of 16 consecutive 128-byte lines:
+// whole sectors to and from HBM, and the 16 lines' values sit in different
+// banks of S (their positions differ in the higher digits).  A thread moves
+// its E values as E / CPC 16-byte chunks.  Needs whole warps per row and
+// whole groups of 16 lines; otherwise the per-value coalesced loop is used.
+template <typename T, int NT>
+struct RowIo {
+    static constexpr int N = fft_nt(NT);
+    static constexpr int CPC = 16 / (int)sizeof(cx<T>);   // values per 16-byte chunk
+    static constexpr int LW = 128 / (int)sizeof(cx<T>);   // values per 128-byte line
+    static constexpr int UNITS = RowCfg<NT>::E / CPC;      // chunks per thread
+    static constexpr int NSL = PassCfg<NT, RowCfg<NT>::NPASS - 1>::NS;
+    static constexpr bool OK = RowCfg<NT>::E == 16 && RowCfg<NT>::TPR % 32 == 0 &&
+                               (N * (int)sizeof(cx<T>)) % 2048 == 0 && UNITS % 4 == 0;
+};
+
+// The row at p can move in 16-byte chunks (complex<double> is 16-byte aligned
+// by its type; a float row needs a 16-byte aligned start).
+template <typename T, int NT>
+__device__ __forceinline__ bool row_io_chunks(const cx<T> *p) {
+    if constexpr (!RowIo<T, NT>::OK) return false;
+    else return sizeof(T) == 8 || (reinterpret_cast<uintptr_t>(p) & 15) == 0;
+}
+
+template <typename T>
+__device__ __forceinline__ void ld_chunk(const cx<T> *p, cx<T> *v) {
+    if constexpr (sizeof(T) == 4) {
+        const float4 q = *reinterpret_cast<const float4 *>(p);
+        v[0] = mk(q.x, q.y);
+        v[1] = mk(q.z, q.w);
+    } else {
+        v[0] = *p;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void st_chunk(cx<T> *p, const cx<T> *v) {
+    if constexpr (sizeof(T) == 4) *reinterpret_cast<float4 *>(p) = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+    else *p = v[0];
+}
+
+// Visits the thread's chunks: f(tau, q0, p0) with tau the chunk's first time
+// sample and (q0, p0) the padded and unpadded S positions of tau rounded down
+// to a multiple of 16 (own_idx then places tau & 15 and the next values).
+template <typename T, int NT, typename F>
+__host__ __device__ __forceinline__ void row_chunks(int t, F f) {
+    using IO = RowIo<T, NT>;
+    const int lane = t & 31, w = t >> 5;
+#pragma unroll
+    for (int gi = 0; gi < IO::UNITS / 4; ++gi) {
+        const int line = 16 * (w * (IO::UNITS / 4) + gi) + (lane >> 1);
+        const int tl = line * IO::LW;
+        const int p0 = tpos<NT>(tl & ~15);
+        const int q0 = pidx(p0, IO::N);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) f(tl + (2 * j + (lane & 1)) * IO::CPC, q0, p0);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -914,10 +978,26 @@ __device__ __forceinline__ void row_body(const RowArgs<T> &a, int row_base, int 
         hook();
     } else {
         const cx<T> *src = PF ? xs + rloc * C::N : gin;
+        if (!PF && row_io_chunks<T, NT>(src)) {
+            using IO = RowIo<T, NT>;
+            row_chunks<T, NT>(t, [&](int tau, int cq0, int cp0) {
+                cx<T> cv[IO::CPC];
+                if (valid) {
+                    ld_chunk<T>(src + FCN_IDX(tau, IO::N - IO::CPC + 1, 6), cv);
+                } else {
 #pragma unroll
-        for (int i = 0; i < E; ++i) {
-            const int idx = t + C::TPR * i;
-            S[FCN_IDX(pidx(tpos<NT>(idx), fft_nt(NT)), C::PADN, 5)] = valid ? src[FCN_IDX(idx, fft_nt(NT), 6)] : mk(T(0), T(0));
+                    for (int m = 0; m < IO::CPC; ++m) cv[m] = mk(T(0), T(0));
+                }
+#pragma unroll
+                for (int m = 0; m < IO::CPC; ++m)
+                    S[FCN_IDX((own_idx<NT, IO::NSL>(cq0, cp0, (tau & 15) + m)), C::PADN, 5)] = cv[m];
+            });
+        } else {
+#pragma unroll
+            for (int i = 0; i < E; ++i) {
+                const int idx = t + C::TPR * i;
+                S[FCN_IDX(pidx(tpos<NT>(idx), fft_nt(NT)), C::PADN, 5)] = valid ? src[FCN_IDX(idx, fft_nt(NT), 6)] : mk(T(0), T(0));
+            }
         }
         __syncthreads();
         hook();
@@ -1001,10 +1081,21 @@ __device__ __forceinline__ void row_body(const RowArgs<T> &a, int row_base, int 
             }
         }
         if ((!(ops & OP_FFT) || (ops & OP_SPEC_OF_TIME)) && !(ops & OP_NOSTORE) && valid) {
+            if (row_io_chunks<T, NT>(g)) {
+                using IO = RowIo<T, NT>;
+                row_chunks<T, NT>(t, [&](int tau, int cq0, int cp0) {
+                    cx<T> cv[IO::CPC];
 #pragma unroll
-            for (int i = 0; i < E; ++i) {
-                const int idx = t + C::TPR * i;
-                g[FCN_IDX(idx, fft_nt(NT), 10)] = S[FCN_IDX(pidx(tpos<NT>(idx), fft_nt(NT)), C::PADN, 11)];
+                    for (int m = 0; m < IO::CPC; ++m)
+                        cv[m] = S[FCN_IDX((own_idx<NT, IO::NSL>(cq0, cp0, (tau & 15) + m)), C::PADN, 11)];
+                    st_chunk<T>(g + FCN_IDX(tau, IO::N - IO::CPC + 1, 10), cv);
+                });
+            } else {
+#pragma unroll
+                for (int i = 0; i < E; ++i) {
+                    const int idx = t + C::TPR * i;
+                    g[FCN_IDX(idx, fft_nt(NT), 10)] = S[FCN_IDX(pidx(tpos<NT>(idx), fft_nt(NT)), C::PADN, 11)];
+                }
             }
         }
         // the in-place transform below overwrites S: every thread's store first

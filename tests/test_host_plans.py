@@ -81,3 +81,36 @@ def test_pivot_limit_is_the_attracting_fixed_point(dump):
         for _ in range(4000):
             piv = b + s * s / piv
         assert abs(1 / piv - inv) <= 1e-9 * abs(inv) or s > 10
+
+
+def test_chunked_row_io_is_a_permutation_and_cuts_bank_conflicts():
+    """The head and tail row launches move time-domain rows between HBM and
+    the digit-reversed shared-memory layout in 16-byte chunks (RowIo,
+    row_chunks): every value of the row once, at its digit-reversed
+    position, whole 32-byte sectors per warp instruction, and no more
+    shared-memory wavefronts than the per-value loop: for the 4096-point
+    float rows 2 instead of 16."""
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not available")
+    d = tempfile.mkdtemp()
+    exe = os.path.join(d, "row_io")
+    subprocess.run([nvcc, "-std=c++17", "-x", "cu", "-diag-suppress", "20013,1886",
+                    os.path.join(ROOT, "tests", "row_io.cu"), "-o", exe], check=True, capture_output=True)
+    out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout
+    shutil.rmtree(d, ignore_errors=True)
+    rows = {}
+    for line in out.splitlines():
+        f = line.split()
+        if f[0] != "io" or f[-1] == "skip":
+            continue
+        rows[(f[1], int(f[2]), int(f[3]))] = dict(zip(f[4::2], map(int, f[5::2])))
+    # float rows from 512 points, double rows from 512 points (whole warps, whole line groups)
+    assert len(rows) == 2 * 2 * 5
+    for (prec, nt, plan), r in rows.items():
+        assert r["bad"] == 0, (prec, nt, plan)
+        assert r["sectors"] == 16                       # 16 full 32-byte sectors per instruction
+        assert r["wf_new"] <= r["wf_old"], (prec, nt, plan)
+    assert rows[("f32", 4096, 0)]["wf_new"] == 2 and rows[("f32", 4096, 0)]["wf_old"] == 16
+    assert rows[("f32", 1024, 0)]["wf_new"] == 2
+    assert rows[("f64", 4096, 0)]["wf_new"] == 4        # 512 bytes: the minimum
