@@ -623,9 +623,13 @@ void drop_graphs(fcn_ctx *ctx, bool all, uint64_t dz) {
 constexpr int OPS_HEAD = OP_NL | OP_FFT;
 constexpr int OPS_MID = OP_IFFT | OP_NL | OP_NL2 | OP_FFT;
 constexpr int OPS_TAIL = OP_IFFT | OP_NL | OP_RHO | OP_STATS;
+// The closing launch of a state that is never kept (the one-step result of a
+// step-doubling attempt, which only enters the error norm): no rho output and
+// no statistics, so no u rows in shared memory either.
+constexpr int OPS_TAIL_BARE = OP_IFFT | OP_NL;
 
 // Launches `kind` for every pulse on stream st: 0 head, 1 eight (col, mid)
-// pairs, 2 one (col, mid) pair, 3 (col, tail).
+// pairs, 2 one (col, mid) pair, 3 (col, tail), 5 (col, bare tail).
 // Device argument arrays of the batched kernels for this dz (built once).
 template <typename T>
 cudaError_t batch_args(fcn_ctx *ctx, double dz, const std::vector<const cx<T> *> &tabs,
@@ -689,7 +693,7 @@ cudaError_t launch_block_batched(fcn_ctx *ctx, int kind, double dz, cudaStream_t
             }
         } else {
             e = col();
-            if (e == cudaSuccess) e = rows(OPS_TAIL, FCN_PROF_ROW_TAIL);
+            if (e == cudaSuccess) e = rows(kind == 5 ? OPS_TAIL_BARE : OPS_TAIL, FCN_PROF_ROW_TAIL);
         }
         return e;
     }
@@ -785,7 +789,7 @@ cudaError_t launch_group(fcn_ctx *ctx, int kind, double dz, cudaStream_t st,
             }
         } else {
             e = col();
-            if (e == cudaSuccess) e = rows_group(OPS_TAIL, FCN_PROF_ROW_TAIL);
+            if (e == cudaSuccess) e = rows_group(kind == 5 ? OPS_TAIL_BARE : OPS_TAIL, FCN_PROF_ROW_TAIL);
         }
     }
     return e;
@@ -867,7 +871,8 @@ cudaError_t launch_block(fcn_ctx *ctx, int kind, double dz, cudaStream_t st,
             for (size_t i = 0; i < n && e == cudaSuccess; i += m) e = launch_group<T>(ctx, -1, dz, st, tabs, fields, i, &m);
         }
         if (e == cudaSuccess)
-            e = kind == 3 ? launch_rows_all<T>(ctx, OPS_TAIL, FCN_PROF_ROW_TAIL, dz, st, fields)
+            e = kind == 3 || kind == 5
+                    ? launch_rows_all<T>(ctx, kind == 5 ? OPS_TAIL_BARE : OPS_TAIL, FCN_PROF_ROW_TAIL, dz, st, fields)
                           : launch_rows_all<T>(ctx, OPS_MID, FCN_PROF_ROW_MID, dz, st, fields);
     }
     return e;
@@ -1203,7 +1208,7 @@ int step_impl(fcn_ctx *ctx, double dz, int64_t n, bool use_graph) {
 // One Strang step of length h (or two of h/2) on a work buffer, direct launches.
 template <typename T>
 int substeps(fcn_ctx *ctx, Pulse &pu, void *f, double h, int count, const cx<T> *tab = nullptr,
-             cudaEvent_t table_ready = nullptr, int tail_extra = 0, const void *src = nullptr) {
+             cudaEvent_t table_ready = nullptr, int tail_ops = OPS_TAIL, const void *src = nullptr) {
     if (!tab) {
         int rc = ensure_table<T>(ctx, pu, h, &tab);
         if (rc) return rc;
@@ -1225,7 +1230,7 @@ int substeps(fcn_ctx *ctx, Pulse &pu, void *f, double h, int count, const cx<T> 
     if (table_ready) CK(cudaStreamWaitEvent(ctx->st, table_ready, 0), "table wait");
     for (int i = 0; i < count; ++i) {
         CK(launch_cn<T>(col_args<T>(pu, f, tab, h), ctx->st), "column");
-        const int ops = (i + 1 < count) ? OPS_MID : (OPS_TAIL | tail_extra);
+        const int ops = (i + 1 < count) ? OPS_MID : tail_ops;
         CK(launch_rows<T>(row_args<T>(pu, f, ops, h), pu.g.nt, ctx->st), "row");
     }
     return FCN_OK;
@@ -1389,7 +1394,7 @@ int propagate_batch(fcn_ctx *ctx, double z_end, double dz0, double rtol, double 
         // the heads read the start field and write the work buffers
         CK(launch_block<T>(ctx, 0, h, ctx->st, tab1, &f1, &f0), "head");
         if (ev1) CK(cudaStreamWaitEvent(ctx->st, ev1, 0), "table wait");
-        CK(launch_block<T>(ctx, 3, h, ctx->st, tab1, &f1), "one step");
+        CK(launch_block<T>(ctx, 5, h, ctx->st, tab1, &f1), "one step");
         CK(launch_block<T>(ctx, 0, 0.5 * h, ctx->st, tab2, &f2, &f0), "head");
         if (ev2) CK(cudaStreamWaitEvent(ctx->st, ev2, 0), "table wait");
         CK(launch_block<T>(ctx, 2, 0.5 * h, ctx->st, tab2, &f2), "first half step");
@@ -1590,13 +1595,14 @@ int propagate_impl(fcn_ctx *ctx, double z_end, double dz0, double rtol, double d
         if (!rc) rc = ensure_table<T>(ctx, pu, 0.5 * h, &tab2, 1, &ev2);
         if (rc) return rc;
         // the heads read the start field and write the work buffers (no copies)
-        rc = substeps<T>(ctx, pu, pu.work1, h, 1, tab1, ev1, 0, pu.field);
+        // (the one-step result only enters the error norm: a bare tail)
+        rc = substeps<T>(ctx, pu, pu.work1, h, 1, tab1, ev1, OPS_TAIL_BARE, pu.field);
         // the closing launch of the two half steps leaves the statistics of
         // the field it produces (peak, on-axis peak, peak rho, energy), from
         // which the features and the proposal of an accepted attempt follow
         // without a pass of their own
         const bool next_feat = features && !last;
-        if (!rc) rc = substeps<T>(ctx, pu, pu.work2, 0.5 * h, 2, tab2, ev2, 0, pu.field);
+        if (!rc) rc = substeps<T>(ctx, pu, pu.work2, 0.5 * h, 2, tab2, ev2, OPS_TAIL, pu.field);
         if (rc) return rc;
         if (next_feat) {
             // the norm, the features of work2 and (speculative, used only
