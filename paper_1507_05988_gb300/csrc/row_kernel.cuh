@@ -490,6 +490,41 @@ __host__ __device__ __forceinline__ void row_chunks(int t, F f) {
     }
 }
 
+// The same sector-wise order for a row of reals (the rho output from the u
+// rows): 16-byte chunks of RC reals, 128-byte lines of 8 RC reals.  Used with
+// FFT plan 0, where it cuts the wavefronts at every Nt (4096 float points:
+// 2 instead of 8); with plan 1 it would not at every Nt, and the per-value
+// loop stays.
+template <typename T, int NT>
+struct RowIoReal {
+    static constexpr int N = fft_nt(NT);
+    static constexpr int RC = 16 / (int)sizeof(T);        // reals per 16-byte chunk
+    static constexpr int LW = 128 / (int)sizeof(T);       // reals per 128-byte line
+    static constexpr int UNITS = RowCfg<NT>::E / RC;       // chunks per thread
+    static constexpr bool OK = fft_plan(NT) == 0 && RowCfg<NT>::E == 16 && RowCfg<NT>::TPR % 32 == 0 &&
+                               (N * (int)sizeof(T)) % 2048 == 0 && UNITS % 4 == 0;
+};
+
+template <typename T, int NT>
+__device__ __forceinline__ bool row_io_real_chunks(const T *p) {
+    if constexpr (!RowIoReal<T, NT>::OK) return false;
+    else return (reinterpret_cast<uintptr_t>(p) & 15) == 0;
+}
+
+// Visits the thread's chunks of a real row: f(tau), tau the chunk's first
+// time sample (a chunk never crosses a multiple of 16).
+template <typename T, int NT, typename F>
+__host__ __device__ __forceinline__ void row_real_chunks(int t, F f) {
+    using IO = RowIoReal<T, NT>;
+    const int lane = t & 31, w = t >> 5;
+#pragma unroll
+    for (int gi = 0; gi < IO::UNITS / 4; ++gi) {
+        const int line = 16 * (w * (IO::UNITS / 4) + gi) + (lane >> 1);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) f(line * IO::LW + (2 * j + (lane & 1)) * IO::RC);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Nonlinear half step
 // ---------------------------------------------------------------------------
@@ -1070,13 +1105,32 @@ __device__ __forceinline__ void row_body(const RowArgs<T> &a, int row_base, int 
             }
             __syncthreads();
             if ((ops & OP_RHO) && valid && a.rho) {
-                // consecutive threads write consecutive tau points
                 T *rr = a.rho + (size_t)row * C::N;
+                if (row_io_real_chunks<T, NT>(rr)) {
+                    // 16-byte chunks in the sector-wise order of the field rows
+                    using IO = RowIoReal<T, NT>;
+                    constexpr int NSL = PassCfg<NT, C::NPASS - 1>::NS;
+                    row_real_chunks<T, NT>(t, [&](int tau) {
+                        const int cp0 = tpos<NT>(tau & ~15);
+                        const int cq0 = pidx(cp0, fft_nt(NT));
+                        T w[IO::RC];
 #pragma unroll
-                for (int i = 0; i < E; ++i) {
-                    const int idx = t + C::TPR * i;
-                    rr[FCN_IDX(idx, fft_nt(NT), 12)] =
-                        have_u ? U[FCN_IDX(pidx(tpos<NT>(idx), fft_nt(NT)), C::PADN, 30)] * a.nl.rho_nt : T(0);
+                        for (int m = 0; m < IO::RC; ++m)
+                            w[m] = have_u ? U[FCN_IDX((own_idx<NT, NSL>(cq0, cp0, (tau & 15) + m)), C::PADN, 30)] *
+                                                a.nl.rho_nt
+                                          : T(0);
+                        T *dst = rr + FCN_IDX(tau, IO::N - IO::RC + 1, 12);
+                        if constexpr (sizeof(T) == 4) *reinterpret_cast<float4 *>(dst) = make_float4(w[0], w[1], w[2], w[3]);
+                        else *reinterpret_cast<double2 *>(dst) = make_double2(w[0], w[1]);
+                    });
+                } else {
+                    // consecutive threads write consecutive tau points
+#pragma unroll
+                    for (int i = 0; i < E; ++i) {
+                        const int idx = t + C::TPR * i;
+                        rr[FCN_IDX(idx, fft_nt(NT), 12)] =
+                            have_u ? U[FCN_IDX(pidx(tpos<NT>(idx), fft_nt(NT)), C::PADN, 30)] * a.nl.rho_nt : T(0);
+                    }
                 }
             }
         }

@@ -89,7 +89,8 @@ def test_chunked_row_io_is_a_permutation_and_cuts_bank_conflicts():
     row_chunks): every value of the row once, at its digit-reversed
     position, whole 32-byte sectors per warp instruction, and no more
     shared-memory wavefronts than the per-value loop: for the 4096-point
-    float rows 2 instead of 16."""
+    float rows 2 instead of 16.  The same for the rho output's rows of
+    reals (FFT plan 0)."""
     nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
     if not os.path.exists(nvcc):
         pytest.skip("nvcc not available")
@@ -99,12 +100,12 @@ def test_chunked_row_io_is_a_permutation_and_cuts_bank_conflicts():
                     os.path.join(ROOT, "tests", "row_io.cu"), "-o", exe], check=True, capture_output=True)
     out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout
     shutil.rmtree(d, ignore_errors=True)
-    rows = {}
+    rows, reals = {}, {}
     for line in out.splitlines():
         f = line.split()
-        if f[0] != "io" or f[-1] == "skip":
+        if f[0] not in ("io", "rio") or f[-1] == "skip":
             continue
-        rows[(f[1], int(f[2]), int(f[3]))] = dict(zip(f[4::2], map(int, f[5::2])))
+        (rows if f[0] == "io" else reals)[(f[1], int(f[2]), int(f[3]))] = dict(zip(f[4::2], map(int, f[5::2])))
     # float rows from 512 points, double rows from 512 points (whole warps, whole line groups)
     assert len(rows) == 2 * 2 * 5
     for (prec, nt, plan), r in rows.items():
@@ -114,3 +115,9 @@ def test_chunked_row_io_is_a_permutation_and_cuts_bank_conflicts():
     assert rows[("f32", 4096, 0)]["wf_new"] == 2 and rows[("f32", 4096, 0)]["wf_old"] == 16
     assert rows[("f32", 1024, 0)]["wf_new"] == 2
     assert rows[("f64", 4096, 0)]["wf_new"] == 4        # 512 bytes: the minimum
+    # the rho output's chunks of reals (FFT plan 0, from 512 points)
+    assert len(reals) == 2 * 5
+    for key, r in reals.items():
+        assert key[2] == 0 and r["bad"] == 0, key
+        assert r["wf_new"] <= r["wf_old"], key
+    assert reals[("f32", 4096, 0)]["wf_new"] == 2 and reals[("f32", 4096, 0)]["wf_old"] == 8
