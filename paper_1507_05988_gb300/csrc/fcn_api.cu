@@ -730,7 +730,8 @@ bool same_row_launch(const RowArgs<T> &a, const RowArgs<T> &b) {
 template <typename T>
 cudaError_t launch_group(fcn_ctx *ctx, int kind, double dz, cudaStream_t st,
                          const std::vector<const cx<T> *> &tabs, const std::vector<void *> *fields,
-                         size_t i, size_t *m_out, const std::vector<void *> *srcs = nullptr) {
+                         size_t i, size_t *m_out, const std::vector<void *> *srcs = nullptr,
+                         const std::vector<void *> *cmps = nullptr) {
     cudaError_t e = cudaSuccess;
     {
         // pulses i and i+1 share the column launch when pairing is on and
@@ -743,6 +744,10 @@ cudaError_t launch_group(fcn_ctx *ctx, int kind, double dz, cudaStream_t st,
             void *f = fields ? (*fields)[k] : pu.field;
             RowArgs<T> a = row_args<T>(pu, f, ops, dz);
             if (srcs && kind == 0) a.in = (const cx<T> *)(*srcs)[k];
+            if (ops & OP_DIFF) {
+                a.cmp = (const cx<T> *)(*cmps)[k];
+                a.diff = pu.rows;
+            }
             return timed(ctx, pk, st, [&] { return launch_rows<T>(a, pu.g.nt, st); });
         };
         // the row stage of the group's pulses (one two-pulse launch when the
@@ -761,6 +766,12 @@ cudaError_t launch_group(fcn_ctx *ctx, int kind, double dz, cudaStream_t st,
                     }
                     ma.field[0] = ma.a.field; ma.rho[0] = ma.a.rho; ma.stats[0] = ma.a.stats;
                     ma.field[1] = a1.field; ma.rho[1] = a1.rho; ma.stats[1] = a1.stats;
+                    if (ops & OP_DIFF) {
+                        ma.cmp[0] = (const cx<T> *)(*cmps)[i];
+                        ma.cmp[1] = (const cx<T> *)(*cmps)[i + 1];
+                        ma.diff[0] = p0.rows;
+                        ma.diff[1] = p1.rows;
+                    }
                     return timed(ctx, pk, st, [&] { return launch_rows_multi<T>(ma, 2, p0.g.nt, st); });
                 }
             }
@@ -789,7 +800,8 @@ cudaError_t launch_group(fcn_ctx *ctx, int kind, double dz, cudaStream_t st,
             }
         } else {
             e = col();
-            if (e == cudaSuccess) e = rows_group(kind == 5 ? OPS_TAIL_BARE : OPS_TAIL, FCN_PROF_ROW_TAIL);
+            const int tops = (kind == 5 ? OPS_TAIL_BARE : OPS_TAIL) | (cmps ? OP_DIFF : 0);
+            if (e == cudaSuccess) e = rows_group(tops, FCN_PROF_ROW_TAIL);
         }
     }
     return e;
@@ -800,7 +812,8 @@ cudaError_t launch_group(fcn_ctx *ctx, int kind, double dz, cudaStream_t st,
 // most kRowMulti per launch).
 template <typename T>
 cudaError_t launch_rows_all(fcn_ctx *ctx, int ops, int pk, double dz, cudaStream_t st,
-                            const std::vector<void *> *fields, const std::vector<void *> *srcs = nullptr) {
+                            const std::vector<void *> *fields, const std::vector<void *> *srcs = nullptr,
+                            const std::vector<void *> *cmps = nullptr) {
     const size_t n = ctx->pulses.size();
     cudaError_t e = cudaSuccess;
     for (size_t i = 0; i < n && e == cudaSuccess;) {
@@ -817,14 +830,20 @@ cudaError_t launch_rows_all(fcn_ctx *ctx, int ops, int pk, double dz, cudaStream
             m.rho[cnt] = ak.rho;
             m.stats[cnt] = ak.stats;
             m.in[cnt] = srcs ? (const cx<T> *)(*srcs)[k] : nullptr;
+            m.cmp[cnt] = cmps ? (const cx<T> *)(*cmps)[k] : nullptr;
+            m.diff[cnt] = cmps ? pk_.rows : nullptr;
             ++cnt;
         }
         m.a.in = m.in[0];
+        m.a.cmp = m.cmp[0];
+        m.a.diff = m.diff[0];
         for (int c = cnt; c < kRowMulti; ++c) {
             m.field[c] = nullptr;
             m.rho[c] = nullptr;
             m.stats[c] = nullptr;
             m.in[c] = nullptr;
+            m.cmp[c] = nullptr;
+            m.diff[c] = nullptr;
         }
         e = timed(ctx, pk, st, [&] {
             return cnt == 1 ? launch_rows<T>(m.a, p0.g.nt, st) : launch_rows_multi<T>(m, cnt, p0.g.nt, st);
@@ -837,18 +856,22 @@ cudaError_t launch_rows_all(fcn_ctx *ctx, int ops, int pk, double dz, cudaStream
 template <typename T>
 // srcs (kind 0 only): the head reads pulse k's rows from srcs[k] and writes
 // them to its field (fields[k]): out of place, no copy of the start field.
+// cmps (kind 3 only): the tail also leaves the step-doubling norm's per-row
+// sums of its output against cmps[k] in pulse k's rows buffer (OP_DIFF).
 cudaError_t launch_block(fcn_ctx *ctx, int kind, double dz, cudaStream_t st,
                          const std::vector<const cx<T> *> &tabs,
                          const std::vector<void *> *fields = nullptr,
-                         const std::vector<void *> *srcs = nullptr) {
+                         const std::vector<void *> *srcs = nullptr,
+                         const std::vector<void *> *cmps = nullptr) {
     if (ctx->batched && !fields) return launch_block_batched<T>(ctx, kind, dz, st, tabs);
+    if (kind != 3) cmps = nullptr;
     cudaError_t e = cudaSuccess;
     const size_t n = ctx->pulses.size();
     size_t m = 1;
     const bool seq_all = ctx->seq_all == 1 && n >= 2;
     if ((ctx->multi_mode != 1 && !seq_all) || n == 1) {
         for (size_t i = 0; i < n && e == cudaSuccess; i += m)
-            e = launch_group<T>(ctx, kind, dz, st, tabs, fields, i, &m, srcs);
+            e = launch_group<T>(ctx, kind, dz, st, tabs, fields, i, &m, srcs, cmps);
         return e;
     }
     // multi-pulse row launches (mode 1, and always with the sequential
@@ -872,7 +895,8 @@ cudaError_t launch_block(fcn_ctx *ctx, int kind, double dz, cudaStream_t st,
         }
         if (e == cudaSuccess)
             e = kind == 3 || kind == 5
-                    ? launch_rows_all<T>(ctx, kind == 5 ? OPS_TAIL_BARE : OPS_TAIL, FCN_PROF_ROW_TAIL, dz, st, fields)
+                    ? launch_rows_all<T>(ctx, (kind == 5 ? OPS_TAIL_BARE : OPS_TAIL) | (cmps ? OP_DIFF : 0),
+                                         FCN_PROF_ROW_TAIL, dz, st, fields, nullptr, cmps)
                           : launch_rows_all<T>(ctx, OPS_MID, FCN_PROF_ROW_MID, dz, st, fields);
     }
     return e;
@@ -1208,7 +1232,8 @@ int step_impl(fcn_ctx *ctx, double dz, int64_t n, bool use_graph) {
 // One Strang step of length h (or two of h/2) on a work buffer, direct launches.
 template <typename T>
 int substeps(fcn_ctx *ctx, Pulse &pu, void *f, double h, int count, const cx<T> *tab = nullptr,
-             cudaEvent_t table_ready = nullptr, int tail_ops = OPS_TAIL, const void *src = nullptr) {
+             cudaEvent_t table_ready = nullptr, int tail_ops = OPS_TAIL, const void *src = nullptr,
+             const void *cmp = nullptr) {
     if (!tab) {
         int rc = ensure_table<T>(ctx, pu, h, &tab);
         if (rc) return rc;
@@ -1231,7 +1256,14 @@ int substeps(fcn_ctx *ctx, Pulse &pu, void *f, double h, int count, const cx<T> 
     for (int i = 0; i < count; ++i) {
         CK(launch_cn<T>(col_args<T>(pu, f, tab, h), ctx->st), "column");
         const int ops = (i + 1 < count) ? OPS_MID : tail_ops;
-        CK(launch_rows<T>(row_args<T>(pu, f, ops, h), pu.g.nt, ctx->st), "row");
+        RowArgs<T> a = row_args<T>(pu, f, ops, h);
+        if (cmp && i + 1 == count) {
+            // the closing launch also leaves the per-row norm sums against cmp
+            a.ops |= OP_DIFF;
+            a.cmp = (const cx<T> *)cmp;
+            a.diff = pu.rows;
+        }
+        CK(launch_rows<T>(a, pu.g.nt, ctx->st), "row");
     }
     return FCN_OK;
 }
@@ -1398,24 +1430,20 @@ int propagate_batch(fcn_ctx *ctx, double z_end, double dz0, double rtol, double 
         CK(launch_block<T>(ctx, 0, 0.5 * h, ctx->st, tab2, &f2, &f0), "head");
         if (ev2) CK(cudaStreamWaitEvent(ctx->st, ev2, 0), "table wait");
         CK(launch_block<T>(ctx, 2, 0.5 * h, ctx->st, tab2, &f2), "first half step");
-        CK(launch_block<T>(ctx, 3, 0.5 * h, ctx->st, tab2, &f2), "second half step");
+        // the closing launch also leaves each pulse's per-row norm sums of
+        // work2 against work1 (OP_DIFF): no pass of its own over both fields
+        CK(launch_block<T>(ctx, 3, 0.5 * h, ctx->st, tab2, &f2, nullptr, &f1), "second half step");
         const bool next_feat = features && !last;
         if (same_grid && n <= (size_t)kCtlMulti) {
-            // every pulse's norm partials in one launch, then norm, features
-            // and (no cooldown) the proposals in one launch, one copy
-            DiffMulti<T> dm;
+            // every pulse's norm, features and (no cooldown) proposals in one
+            // launch, one copy
             CtlMulti cm;
-            std::memset(&dm, 0, sizeof dm);
             std::memset(&cm, 0, sizeof cm);
-            dm.nr = cm.nr = ctx->pulses[0].g.nr;
-            dm.nt = ctx->pulses[0].g.nt;
-            dm.n = cm.n = (int)n;
+            cm.nr = ctx->pulses[0].g.nr;
+            cm.n = (int)n;
             cm.out = reinterpret_cast<double *>(ctx->batch_io);
             for (size_t i = 0; i < n; ++i) {
                 Pulse &pu = ctx->pulses[i];
-                dm.a[i] = (const cx<T> *)pu.work1;
-                dm.c[i] = (const cx<T> *)pu.work2;
-                dm.rows[i] = pu.rows;
                 cm.stats[i] = pu.stats;
                 cm.rows[i] = pu.rows;
                 if (next_feat) {
@@ -1426,7 +1454,6 @@ int propagate_batch(fcn_ctx *ctx, double z_end, double dz0, double rtol, double 
                 }
                 cm.sc[i] = sc[i];
             }
-            CK(launch_diff_rows_multi<T>(dm, ctx->st), "error norm");
             CK(launch_mlp_step_control_multi(cm, next_feat && cooldown == 0 ? ctx->mlp : nullptr, ctx->st),
                "controller");
             CK(cudaMemcpyAsync(H, ctx->batch_io, 8 * sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->st),
@@ -1435,26 +1462,22 @@ int propagate_batch(fcn_ctx *ctx, double z_end, double dz0, double rtol, double 
         for (size_t i = 0; i < n && !(same_grid && n <= (size_t)kCtlMulti); ++i) {
             Pulse &pu = ctx->pulses[i];
             if (next_feat) {
-                // the closing row launch left this pulse's statistics of work2:
-                // norm, features, proposal and energy in one kernel (behind
-                // the per-row norm partials) and one copy; the network runs
-                // only when its proposal can be taken (no cooldown)
+                // the closing row launch left this pulse's statistics of work2
+                // and its per-row norm sums: norm, features, proposal and
+                // energy in one kernel and one copy; the network runs only
+                // when its proposal can be taken (no cooldown)
                 sc[i].peak_prev = peak[i];
                 sc[i].dz_prev = h;
                 sc[i].dz_lo = std::fmax(0.2 * h, dz_min);
                 sc[i].dz_hi = 2.0 * h;
                 double *ctl = reinterpret_cast<double *>(ctx->batch_io + 64 * i);
-                CK(launch_diff_rows<T>((const cx<T> *)pu.work1, (const cx<T> *)pu.work2, pu.g.nr, pu.g.nt,
-                                       pu.rows, ctx->st),
-                   "error norm");
                 CK(launch_mlp_step_control(pu.stats, pu.g.nr, pu.rows, sc[i], cooldown == 0 ? ctx->mlp : nullptr,
                                            ctl, ctx->st),
                    "controller");
                 CK(cudaMemcpyAsync(H + 8 * i, ctl, 8 * sizeof(double), cudaMemcpyDeviceToHost, ctx->st),
                    "controller copy");
             } else {
-                CK(launch_diff_norm<T>((const cx<T> *)pu.work1, (const cx<T> *)pu.work2, pu.g.nr, pu.g.nt,
-                                       pu.rows, pu.red, ctx->st), "error norm");
+                CK(launch_diff_final(pu.rows, pu.g.nr, pu.red, ctx->st), "error norm");
                 CK(cudaMemcpyAsync(H + 8 * i, pu.red, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->st),
                    "norm copy");
             }
@@ -1602,28 +1625,25 @@ int propagate_impl(fcn_ctx *ctx, double z_end, double dz0, double rtol, double d
         // which the features and the proposal of an accepted attempt follow
         // without a pass of their own
         const bool next_feat = features && !last;
-        if (!rc) rc = substeps<T>(ctx, pu, pu.work2, 0.5 * h, 2, tab2, ev2, OPS_TAIL, pu.field);
+        if (!rc) rc = substeps<T>(ctx, pu, pu.work2, 0.5 * h, 2, tab2, ev2, OPS_TAIL, pu.field, pu.work1);
         if (rc) return rc;
         if (next_feat) {
             // the norm, the features of work2 and (speculative, used only
             // if the attempt is accepted) the proposal after it: one kernel
-            // behind the per-row norm partials, one copy.  The network runs
-            // only when its proposal can be taken (no cooldown).
+            // over the per-row norm sums the closing launch left, one copy.
+            // The network runs only when its proposal can be taken (no
+            // cooldown).
             sc.peak_prev = hfeat[7];
             sc.dz_prev = h;
             sc.dz_lo = std::fmax(0.2 * h, dz_min);
             sc.dz_hi = 2.0 * h;
-            CK(launch_diff_rows<T>((const cx<T> *)pu.work1, (const cx<T> *)pu.work2, pu.g.nr, pu.g.nt, pu.rows,
-                                   ctx->st),
-               "error norm");
             CK(launch_mlp_step_control(pu.stats, pu.g.nr, pu.rows, sc,
                                        controller == 1 && cooldown == 0 ? ctx->mlp : nullptr, ctl_d, ctx->st),
                "controller");
             CK(cudaMemcpyAsync(ctx->host_red, ctl_d, 8 * sizeof(double), cudaMemcpyDeviceToHost, ctx->st),
                "controller copy");
         } else {
-            CK(launch_diff_norm<T>((const cx<T> *)pu.work1, (const cx<T> *)pu.work2, pu.g.nr, pu.g.nt,
-                                   pu.rows, pu.red, ctx->st), "error norm");
+            CK(launch_diff_final(pu.rows, pu.g.nr, pu.red, ctx->st), "error norm");
             CK(cudaMemcpyAsync(ctx->host_red, pu.red, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->st),
                "norm copy");
         }

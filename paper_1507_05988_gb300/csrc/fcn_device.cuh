@@ -116,7 +116,11 @@ enum : int {
     OP_NOSTORE = 128, // do not write the field back (diagnostics only)
     // with OP_FFT | OP_SPEC: store the time-domain row as without OP_FFT and
     // transform it only for the spectral moments (the spectrum is not stored)
-    OP_SPEC_OF_TIME = 256
+    OP_SPEC_OF_TIME = 256,
+    // with the time-domain store: the step-doubling norm's per-row sums
+    // against RowArgs::cmp into RowArgs::diff (diff[2m] = sum |cmp - A|^2,
+    // diff[2m+1] = sum |A|^2 over row m of the stored field A)
+    OP_DIFF = 512
 };
 
 // Coefficients of one nonlinear half step in scaled intensity units
@@ -230,6 +234,8 @@ struct RowArgs {
     const cx<T> *tw1 = nullptr;   // twiddle table of FFT plan 1 (variants 4, 5)
     const cx<T> *in = nullptr;    // rows read from here instead of field (output
                                   // still to field; may not alias it), or null
+    const cx<T> *cmp = nullptr;   // OP_DIFF: the field compared against, [nr][nt]
+    double *diff = nullptr;       // OP_DIFF: per-row sums, [nr][2]
 };
 
 // One launch of the row stage over up to kRowMulti pulses that share the
@@ -243,6 +249,8 @@ struct RowMultiArgs {
     T *rho[kRowMulti];
     double *stats[kRowMulti];
     const cx<T> *in[kRowMulti] = {};   // per pulse as RowArgs::in (null: field)
+    const cx<T> *cmp[kRowMulti] = {};  // per pulse as RowArgs::cmp
+    double *diff[kRowMulti] = {};      // per pulse as RowArgs::diff
 };
 
 // Per-row coefficients of the Crank-Nicolson system (Eqs. (Ma)-(Mb)) for one
@@ -650,6 +658,9 @@ cudaError_t launch_diff_rows(const cx<T> *a, const cx<T> *b, int nr, int nt, dou
 template <typename T>
 cudaError_t launch_diff_norm(const cx<T> *a, const cx<T> *b, int nr, int nt, double *rows,
                              double *out, cudaStream_t st);
+// The second kernel of launch_diff_norm alone: out[0] = sum_m rows[2m],
+// out[1] = sum_m rows[2m+1] (per-row sums left by a row launch with OP_DIFF).
+cudaError_t launch_diff_final(const double *rows, int nr, double *out, cudaStream_t st);
 // Power P(tau_p) (unscaled: sum_m W_m |A|^2) and fluence rows (sum_p |A|^2), FP64.
 template <typename T>
 cudaError_t launch_profiles(const cx<T> *f, int nr, int nt, double *power, double *rowsum,

@@ -215,6 +215,10 @@ cudaError_t launch_diff_norm(const cx<T> *a, const cx<T> *b, int nr, int nt, dou
     diff_final_kernel<<<1, RT, 0, st>>>(rows, nr, out);
     return cudaGetLastError();
 }
+cudaError_t launch_diff_final(const double *rows, int nr, double *out, cudaStream_t st) {
+    diff_final_kernel<<<1, RT, 0, st>>>(rows, nr, out);
+    return cudaGetLastError();
+}
 template <typename T>
 cudaError_t launch_profiles(const cx<T> *f, int nr, int nt, double *power, double *rowsum,
                             cudaStream_t st) {

@@ -955,14 +955,67 @@ struct NoHook {
     __device__ __forceinline__ void operator()() const {}
 };
 
+// The time-domain store of a row (when `store`) and the step-doubling norm's
+// sums of the stored row A against cmp (diff[2 row] = sum |cmp - A|^2,
+// diff[2 row + 1] = sum |A|^2; per-thread sums in the working precision over
+// the thread's few points, FP64 from the row sum on).  Called by every
+// thread of the CTA (row_reduce has block barriers).
+template <typename T, int NT>
+__device__ __forceinline__ void row_store_diff(cx<T> *g, const cx<T> *S, const cx<T> *cmp, double *diff, int nr,
+                                               int row, int t, bool valid, bool store, double *scr, int rloc) {
+    using C = RowCfg<NT>;
+    constexpr int E = C::E;
+    T d2 = T(0), b2 = T(0);
+    const cx<T> *gc = cmp ? cmp + (size_t)(valid ? row : 0) * C::N : nullptr;
+    auto acc = [&](cx<T> x, cx<T> y) {             // x: stored value, y: compared value
+        const T dx = y.x - x.x, dy = y.y - x.y;
+        d2 = fma(dx, dx, fma(dy, dy, d2));
+        b2 = fma(x.x, x.x, fma(x.y, x.y, b2));
+    };
+    if (store && valid) {
+        if (row_io_chunks<T, NT>(g) && (!gc || row_io_chunks<T, NT>(gc))) {
+            using IO = RowIo<T, NT>;
+            row_chunks<T, NT>(t, [&](int tau, int cq0, int cp0) {
+                cx<T> cv[IO::CPC];
+#pragma unroll
+                for (int m = 0; m < IO::CPC; ++m)
+                    cv[m] = S[FCN_IDX((own_idx<NT, IO::NSL>(cq0, cp0, (tau & 15) + m)), C::PADN, 11)];
+                st_chunk<T>(g + FCN_IDX(tau, IO::N - IO::CPC + 1, 10), cv);
+                if (gc) {
+                    cx<T> yv[IO::CPC];
+                    ld_chunk<T>(gc + FCN_IDX(tau, IO::N - IO::CPC + 1, 32), yv);
+#pragma unroll
+                    for (int m = 0; m < IO::CPC; ++m) acc(cv[m], yv[m]);
+                }
+            });
+        } else {
+#pragma unroll
+            for (int i = 0; i < E; ++i) {
+                const int idx = t + C::TPR * i;
+                const cx<T> x = S[FCN_IDX(pidx(tpos<NT>(idx), fft_nt(NT)), C::PADN, 11)];
+                g[FCN_IDX(idx, fft_nt(NT), 10)] = x;
+                if (gc) acc(x, gc[FCN_IDX(idx, fft_nt(NT), 32)]);
+            }
+        }
+    }
+    double v2[2] = {double(d2), double(b2)};
+    const bool sk[2] = {false, false};
+    row_reduce<NT, 2>(v2, sk, t, scr, rloc);
+    if (t == 0 && valid && diff) {
+        diff[FCN_IDX((size_t)2 * row, (size_t)2 * nr, 33)] = v2[0];
+        diff[FCN_IDX((size_t)2 * row + 1, (size_t)2 * nr, 34)] = v2[1];
+    }
+    __syncthreads();                               // the scratch is reused
+}
+
 // One row stage of RPC rows.  PF: the input rows were staged in shared memory
 // (xs: RPC rows of Nt values in natural order, row_base's first) and are read
 // from there; hook() runs once every thread has finished reading them (the
 // prefetch of the next rows may then overwrite xs).
-template <typename T, int NT, int KT, int TH, bool PF = false, typename Hook = NoHook>
+template <typename T, int NT, int KT, int TH, bool PF = false, typename Hook = NoHook, bool DIFFK = false>
 __device__ __forceinline__ void row_body(const RowArgs<T> &a, int row_base, int ops,
                                          unsigned char *smem_raw, const cx<T> *xs = nullptr,
-                                         Hook hook = Hook()) {
+                                         Hook hook = Hook(), const RowMultiArgs<T> *mp = nullptr) {
     using C = RowCfg<NT>;
     constexpr int E = C::E;
     constexpr int RPC = TH / C::TPR;
@@ -1134,7 +1187,14 @@ __device__ __forceinline__ void row_body(const RowArgs<T> &a, int row_base, int 
                 }
             }
         }
-        if ((!(ops & OP_FFT) || (ops & OP_SPEC_OF_TIME)) && !(ops & OP_NOSTORE) && valid) {
+        if constexpr (DIFFK) {
+            // the kernels of launches with OP_DIFF: the store and the norm sums
+            // (a multi-pulse launch's per-pulse pointers from its parameters)
+            const bool store = (!(ops & OP_FFT) || (ops & OP_SPEC_OF_TIME)) && !(ops & OP_NOSTORE);
+            const cx<T> *cmp = mp ? mp->cmp[blockIdx.y] : a.cmp;
+            double *diff = mp ? mp->diff[blockIdx.y] : a.diff;
+            row_store_diff<T, NT>(g, S, cmp, diff, a.nr, row, t, valid, store, scr, rloc);
+        } else if ((!(ops & OP_FFT) || (ops & OP_SPEC_OF_TIME)) && !(ops & OP_NOSTORE) && valid) {
             if (row_io_chunks<T, NT>(g)) {
                 using IO = RowIo<T, NT>;
                 row_chunks<T, NT>(t, [&](int tau, int cq0, int cp0) {
@@ -1221,19 +1281,27 @@ __device__ __forceinline__ void row_body(const RowArgs<T> &a, int row_base, int 
     }
 }
 
-template <typename T, int NT, int KT, int MB>
+// DIFFK: the kernels for launches with OP_DIFF (the closing launch of a
+// step-doubling attempt); the others are compiled without that code, so
+// that it does not weigh on the register allocation of the launch that runs
+// at almost every z-step.
+template <typename T, int NT, int KT, int MB, bool DIFFK = false>
 __global__ void __launch_bounds__(RowCfg<NT>::THREADS, MB)
 row_kernel(RowArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     pdl_enter();
-    row_body<T, NT, KT, RowCfg<NT>::THREADS>(a, blockIdx.x * RowCfg<NT>::RPC, a.ops, smem_raw);
+    if constexpr (DIFFK)
+        row_body<T, NT, KT, RowCfg<NT>::THREADS, false, NoHook, true>(a, blockIdx.x * RowCfg<NT>::RPC, a.ops,
+                                                                       smem_raw);
+    else
+        row_body<T, NT, KT, RowCfg<NT>::THREADS>(a, blockIdx.x * RowCfg<NT>::RPC, a.ops, smem_raw);
 }
 
 // Several pulses of one grid and one set of coefficients in one launch:
 // blockIdx.y selects the pulse (its field, rho and statistics pointers; all
 // else is shared).  One launch over all pulses fills the waves that a launch
 // per pulse leaves part-empty.
-template <typename T, int NT, int KT, int MB>
+template <typename T, int NT, int KT, int MB, bool DIFFK = false>
 __global__ void __launch_bounds__(RowCfg<NT>::THREADS, MB)
 row_kernel_multi(const __grid_constant__ RowMultiArgs<T> m) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1243,7 +1311,11 @@ row_kernel_multi(const __grid_constant__ RowMultiArgs<T> m) {
     a.rho = m.rho[blockIdx.y];
     a.stats = m.stats[blockIdx.y];
     a.in = m.in[blockIdx.y];
-    row_body<T, NT, KT, RowCfg<NT>::THREADS>(a, blockIdx.x * RowCfg<NT>::RPC, a.ops, smem_raw);
+    if constexpr (DIFFK)
+        row_body<T, NT, KT, RowCfg<NT>::THREADS, false, NoHook, true>(a, blockIdx.x * RowCfg<NT>::RPC, a.ops,
+                                                                       smem_raw, nullptr, NoHook(), &m);
+    else
+        row_body<T, NT, KT, RowCfg<NT>::THREADS>(a, blockIdx.x * RowCfg<NT>::RPC, a.ops, smem_raw);
 }
 
 // Persistent row stage with the next rows prefetched: each CTA walks the
@@ -1390,11 +1462,14 @@ constexpr int mb_of(int v) {
 
 template <typename T, int NT, int KT, int MB>
 cudaError_t set_smem_attr() {
-    cudaError_t e = cudaFuncSetAttribute(row_kernel<T, NT, KT, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem_bytes<T, NT>());
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(row_kernel_multi<T, NT, KT, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem_bytes<T, NT>());
+    cudaError_t e = cudaSuccess;
+    for (int d = 0; d < 2 && e == cudaSuccess; ++d) {
+        e = cudaFuncSetAttribute(d ? row_kernel<T, NT, KT, MB, true> : row_kernel<T, NT, KT, MB, false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<T, NT>());
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(d ? row_kernel_multi<T, NT, KT, MB, true> : row_kernel_multi<T, NT, KT, MB, false>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<T, NT>());
+    }
     return e;
 }
 
@@ -1458,6 +1533,36 @@ cudaError_t launch_nt_pf(const RowMultiArgs<T> &m, int npulse, cudaStream_t st) 
     }
 }
 
+// The kernel of the launch's variant (K = 8: unrolled powers; other K: the
+// generic kernel), compiled with the norm sums (DIFFK) or without.
+template <typename T, int NT, bool DIFFK>
+auto multi_kernel_for(const RowArgs<T> &a) -> void (*)(const RowMultiArgs<T>) {
+    if (a.nl.K != 8) return row_kernel_multi<T, NT, 0, 1, DIFFK>;
+    void (*k)(const RowMultiArgs<T>) = row_kernel_multi<T, NT, 8, 1, DIFFK>;
+    if constexpr (sizeof(T) == 4 && fft_nt(NT) >= 256) {
+        constexpr int NT1 = fft_tag(NT, 1);
+        if (a.variant == 1) k = row_kernel_multi<T, NT, 8, mb_of<NT>(1), DIFFK>;
+        else if (a.variant == 2) k = row_kernel_multi<T, NT, 8, mb_of<NT>(2), DIFFK>;
+        else if (a.variant == 4 && a.tw1) k = row_kernel_multi<T, NT1, 8, mb_of<NT1>(1), DIFFK>;
+        else if (a.variant == 5 && a.tw1) k = row_kernel_multi<T, NT1, 8, mb_of<NT1>(2), DIFFK>;
+    }
+    return k;
+}
+
+template <typename T, int NT, bool DIFFK>
+auto kernel_for(const RowArgs<T> &a) -> void (*)(RowArgs<T>) {
+    if (a.nl.K != 8) return row_kernel<T, NT, 0, 1, DIFFK>;
+    void (*k)(RowArgs<T>) = row_kernel<T, NT, 8, 1, DIFFK>;
+    if constexpr (sizeof(T) == 4 && fft_nt(NT) >= 256) {
+        constexpr int NT1 = fft_tag(NT, 1);
+        if (a.variant == 1) k = row_kernel<T, NT, 8, mb_of<NT>(1), DIFFK>;
+        else if (a.variant == 2) k = row_kernel<T, NT, 8, mb_of<NT>(2), DIFFK>;
+        else if (a.variant == 4 && a.tw1) k = row_kernel<T, NT1, 8, mb_of<NT1>(1), DIFFK>;
+        else if (a.variant == 5 && a.tw1) k = row_kernel<T, NT1, 8, mb_of<NT1>(2), DIFFK>;
+    }
+    return k;
+}
+
 template <typename T, int NT>
 cudaError_t launch_nt_multi(const RowMultiArgs<T> &m, int npulse, cudaStream_t st) {
     using C = RowCfg<NT>;
@@ -1466,18 +1571,10 @@ cudaError_t launch_nt_multi(const RowMultiArgs<T> &m, int npulse, cudaStream_t s
     const dim3 grid((a.nr + C::RPC - 1) / C::RPC, npulse);
     if (grid.x == 0 || npulse <= 0) return cudaSuccess;
     if (npulse > kRowMulti) return cudaErrorInvalidValue;
+    const bool dk = (a.ops & OP_DIFF) != 0;
     if constexpr (has_pf<T, NT>())
-        if (a.variant == 3 && a.nl.K == 8) return launch_nt_pf<T, NT>(m, npulse, st);
-    void (*k)(const RowMultiArgs<T>) = row_kernel_multi<T, NT, 8, 1>;
-    if (a.nl.K != 8) {
-        k = row_kernel_multi<T, NT, 0, 1>;
-    } else if constexpr (sizeof(T) == 4 && fft_nt(NT) >= 256) {
-        constexpr int NT1 = fft_tag(NT, 1);
-        if (a.variant == 1) k = row_kernel_multi<T, NT, 8, mb_of<NT>(1)>;
-        else if (a.variant == 2) k = row_kernel_multi<T, NT, 8, mb_of<NT>(2)>;
-        else if (a.variant == 4 && a.tw1) k = row_kernel_multi<T, NT1, 8, mb_of<NT1>(1)>;
-        else if (a.variant == 5 && a.tw1) k = row_kernel_multi<T, NT1, 8, mb_of<NT1>(2)>;
-    }
+        if (a.variant == 3 && a.nl.K == 8 && !dk) return launch_nt_pf<T, NT>(m, npulse, st);
+    void (*k)(const RowMultiArgs<T>) = dk ? multi_kernel_for<T, NT, true>(a) : multi_kernel_for<T, NT, false>(a);
     return launch_k(k, grid, dim3(C::THREADS), smem, st, m);
 }
 
@@ -1487,8 +1584,9 @@ cudaError_t launch_nt(const RowArgs<T> &a, cudaStream_t st) {
     const size_t smem = smem_bytes<T, NT>((a.ops & (OP_RHO | OP_STATS)) != 0);
     const int grid = (a.nr + C::RPC - 1) / C::RPC;
     if (grid == 0) return cudaSuccess;
+    const bool dk = (a.ops & OP_DIFF) != 0;
     if constexpr (has_pf<T, NT>()) {
-        if (a.variant == 3 && a.nl.K == 8) {
+        if (a.variant == 3 && a.nl.K == 8 && !dk) {
             RowMultiArgs<T> m;
             m.a = a;
             for (int c = 0; c < kRowMulti; ++c) {
@@ -1501,16 +1599,7 @@ cudaError_t launch_nt(const RowArgs<T> &a, cudaStream_t st) {
         }
     }
     // K = 8 (the photon number of 800 nm in air) gets unrolled powers
-    void (*k)(RowArgs<T>) = row_kernel<T, NT, 8, 1>;
-    if (a.nl.K != 8) {
-        k = row_kernel<T, NT, 0, 1>;
-    } else if constexpr (sizeof(T) == 4 && fft_nt(NT) >= 256) {
-        constexpr int NT1 = fft_tag(NT, 1);
-        if (a.variant == 1) k = row_kernel<T, NT, 8, mb_of<NT>(1)>;
-        else if (a.variant == 2) k = row_kernel<T, NT, 8, mb_of<NT>(2)>;
-        else if (a.variant == 4 && a.tw1) k = row_kernel<T, NT1, 8, mb_of<NT1>(1)>;
-        else if (a.variant == 5 && a.tw1) k = row_kernel<T, NT1, 8, mb_of<NT1>(2)>;
-    }
+    void (*k)(RowArgs<T>) = dk ? kernel_for<T, NT, true>(a) : kernel_for<T, NT, false>(a);
     return launch_k(k, dim3(grid), dim3(C::THREADS), smem, st, a);
 }
 
