@@ -574,8 +574,9 @@ cudaError_t launch_mlp_grad(const float *W, const float *X, const float *Y, cons
                             float *partial, int max_cta, float *grad, float *loss, cudaStream_t st);
 cudaError_t launch_mlp_adam(float *W, float *m, float *v, const float *g, float lr, int t, cudaStream_t st);
 // One attempt's controller outputs in one launch of 256 threads: the
-// step-doubling norm from the per-row partials diff_rows (summed as
-// launch_diff_norm does; null: no norm), the reduction of the per-row
+// step-doubling norm from the per-row sums diff_rows that a row launch with
+// OP_DIFF leaves (summed as launch_diff_final does; null: no norm), the
+// reduction of the per-row
 // statistics (nr rows of NSTAT), the features and, with W, the proposal;
 // out (8 doubles): [norm0, norm1, 8 feature floats in 4 doubles (f0..f5,
 // fE, peak), dz, energy sum]
@@ -593,17 +594,6 @@ struct CtlMulti {
     int nr, n;
 };
 cudaError_t launch_mlp_step_control_multi(const CtlMulti &p, const float *W, cudaStream_t st);
-// Per-row norm partials of up to kCtlMulti pulses on one grid in one launch
-// (grid nr x n): pulse b compares a[b] with c[b] into rows[b].
-template <typename T>
-struct DiffMulti {
-    const cx<T> *a[kCtlMulti];
-    const cx<T> *c[kCtlMulti];
-    double *rows[kCtlMulti];
-    int nr, nt, n;
-};
-template <typename T>
-cudaError_t launch_diff_rows_multi(const DiffMulti<T> &p, cudaStream_t st);
 
 // reductions and conversions
 template <typename T>
@@ -651,15 +641,9 @@ __device__ __forceinline__ double block_max(double x, double *sh) {
     return x;
 }
 
-// Per-row partials of the step-doubling norm: rows[2m] = sum_p |a - b|^2,
-// rows[2m+1] = sum_p |b|^2 (the first kernel of launch_diff_norm).
-template <typename T>
-cudaError_t launch_diff_rows(const cx<T> *a, const cx<T> *b, int nr, int nt, double *rows, cudaStream_t st);
-template <typename T>
-cudaError_t launch_diff_norm(const cx<T> *a, const cx<T> *b, int nr, int nt, double *rows,
-                             double *out, cudaStream_t st);
-// The second kernel of launch_diff_norm alone: out[0] = sum_m rows[2m],
-// out[1] = sum_m rows[2m+1] (per-row sums left by a row launch with OP_DIFF).
+// The step-doubling norm from the per-row sums a row launch with OP_DIFF
+// leaves (rows[2m] = sum_p |cmp - A|^2, rows[2m+1] = sum_p |A|^2):
+// out[0] = sum_m rows[2m], out[1] = sum_m rows[2m+1], FP64, one fixed tree.
 cudaError_t launch_diff_final(const double *rows, int nr, double *out, cudaStream_t st);
 // Power P(tau_p) (unscaled: sum_m W_m |A|^2) and fluence rows (sum_p |A|^2), FP64.
 template <typename T>

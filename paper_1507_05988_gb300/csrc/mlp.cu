@@ -454,7 +454,8 @@ __global__ void mlp_adam(float *W, float *m, float *v, const float *__restrict__
 
 // The controller's work after an attempt, in one launch of CT threads with
 // one contiguous output (one copy to the host): the step-doubling norm from
-// the per-row partials (summed as launch_diff_norm sums them), the
+// the per-row sums a row launch with OP_DIFF leaves (summed as
+// launch_diff_final sums them), the
 // reduction of the per-row statistics (as launch_reduce_stats: the same
 // tree, so the same energy), the features, and with W non-null the MLP's
 // proposal dz = L_ref exp(f4 - f5/3 + y), clamped to [dz_lo, dz_hi].  With

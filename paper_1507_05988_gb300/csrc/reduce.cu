@@ -70,62 +70,6 @@ __global__ void reduce_stats_kernel(const double *st, int nr, int axis_row, doub
     if (threadIdx.x == 0) out[7] = bad;
 }
 
-// Per-thread partial sums of one row of the step-doubling norm: sum_p
-// |a-b|^2 and sum_p |b|^2 over the thread's points.  FP32 fields: in FP32
-// over the thread's few points (the norm decides against rtol, where 1e-7
-// relative is far below what matters), FP64 from the block sum on; FP64
-// fields in FP64.  The FP32 form keeps the FP64 units (a small fraction of
-// the FP32 ones on this GPU) out of a pass over two whole fields.
-template <typename T>
-__device__ __forceinline__ void diff_partials(const cx<T> *ra, const cx<T> *rb, int nt, double *d2o, double *b2o) {
-    if constexpr (sizeof(T) == 4) {
-        float d2 = 0.f, b2 = 0.f;
-        for (int p = threadIdx.x; p < nt; p += blockDim.x) {
-            const cx<T> x = ra[p], y = rb[p];
-            const float dx = x.x - y.x, dy = x.y - y.y;
-            d2 = fmaf(dx, dx, fmaf(dy, dy, d2));
-            b2 = fmaf(y.x, y.x, fmaf(y.y, y.y, b2));
-        }
-        *d2o = double(d2);
-        *b2o = double(b2);
-    } else {
-        double d2 = 0.0, b2 = 0.0;
-        for (int p = threadIdx.x; p < nt; p += blockDim.x) {
-            const cx<T> x = ra[p], y = rb[p];
-            const double dx = double(x.x) - double(y.x), dy = double(x.y) - double(y.y);
-            d2 += dx * dx + dy * dy;
-            b2 += double(y.x) * double(y.x) + double(y.y) * double(y.y);
-        }
-        *d2o = d2;
-        *b2o = b2;
-    }
-}
-
-// rows[2m] = sum_p |a-b|^2, rows[2m+1] = sum_p |b|^2 for row m
-template <typename T>
-__global__ void diff_rows_kernel(const cx<T> *a, const cx<T> *b, int nt, double *rows) {
-    __shared__ double sh[32];
-    const int m = blockIdx.x;
-    double d2, b2;
-    diff_partials<T>(a + (size_t)m * nt, b + (size_t)m * nt, nt, &d2, &b2);
-    d2 = block_sum(d2, sh);
-    if (threadIdx.x == 0) rows[2 * m] = d2;
-    b2 = block_sum(b2, sh);
-    if (threadIdx.x == 0) rows[2 * m + 1] = b2;
-}
-
-template <typename T>
-__global__ void diff_rows_multi_kernel(const __grid_constant__ DiffMulti<T> p) {
-    __shared__ double sh[32];
-    const int m = blockIdx.x, b = blockIdx.y;
-    double d2, b2;
-    diff_partials<T>(p.a[b] + (size_t)m * p.nt, p.c[b] + (size_t)m * p.nt, p.nt, &d2, &b2);
-    d2 = block_sum(d2, sh);
-    if (threadIdx.x == 0) p.rows[b][2 * m] = d2;
-    b2 = block_sum(b2, sh);
-    if (threadIdx.x == 0) p.rows[b][2 * m + 1] = b2;
-}
-
 __global__ void diff_final_kernel(const double *rows, int nr, double *out) {
     __shared__ double sh[32];
     double d2 = 0.0, b2 = 0.0;
@@ -197,24 +141,6 @@ cudaError_t launch_reduce_stats_flat(const double *stats, int nrows, int axis_ro
     reduce_stats_kernel<true><<<1, 1024, 0, st>>>(stats, nrows, axis_row, out);
     return cudaGetLastError();
 }
-template <typename T>
-cudaError_t launch_diff_rows(const cx<T> *a, const cx<T> *b, int nr, int nt, double *rows, cudaStream_t st) {
-    diff_rows_kernel<T><<<nr, RT, 0, st>>>(a, b, nt, rows);
-    return cudaGetLastError();
-}
-template <typename T>
-cudaError_t launch_diff_rows_multi(const DiffMulti<T> &p, cudaStream_t st) {
-    if (p.n < 1 || p.n > kCtlMulti || p.nr < 1) return cudaErrorInvalidValue;
-    diff_rows_multi_kernel<T><<<dim3(p.nr, p.n), RT, 0, st>>>(p);
-    return cudaGetLastError();
-}
-template <typename T>
-cudaError_t launch_diff_norm(const cx<T> *a, const cx<T> *b, int nr, int nt, double *rows,
-                             double *out, cudaStream_t st) {
-    diff_rows_kernel<T><<<nr, RT, 0, st>>>(a, b, nt, rows);
-    diff_final_kernel<<<1, RT, 0, st>>>(rows, nr, out);
-    return cudaGetLastError();
-}
 cudaError_t launch_diff_final(const double *rows, int nr, double *out, cudaStream_t st) {
     diff_final_kernel<<<1, RT, 0, st>>>(rows, nr, out);
     return cudaGetLastError();
@@ -231,11 +157,6 @@ cudaError_t launch_profiles(const cx<T> *f, int nr, int nt, double *power, doubl
     template cudaError_t launch_widen<T>(const cx<T> *, double *, int64_t, cudaStream_t);  \
     template cudaError_t launch_narrow<T>(const double *, cx<T> *, int64_t, cudaStream_t); \
     template cudaError_t launch_widen_real<T>(const T *, double *, int64_t, cudaStream_t); \
-    template cudaError_t launch_diff_rows<T>(const cx<T> *, const cx<T> *, int, int, double *, \
-                                             cudaStream_t);                                \
-    template cudaError_t launch_diff_rows_multi<T>(const DiffMulti<T> &, cudaStream_t);        \
-    template cudaError_t launch_diff_norm<T>(const cx<T> *, const cx<T> *, int, int, double *, \
-                                             double *, cudaStream_t);                      \
     template cudaError_t launch_profiles<T>(const cx<T> *, int, int, double *, double *,   \
                                             cudaStream_t);
 FCN_INST(float)
