@@ -691,8 +691,9 @@ void orc_diag_compute(const orc_problem *pb, const double *Ad, const double *rho
         for (size_t i = 0; i < (size_t)nr * nt; ++i)
             if (rho[i] > out->peak_rho) out->peak_rho = rho[i];
     }
-    /* spectral rms width */
+    /* spectral rms width (no memory: NaN) */
     double *row = (double *)malloc(sizeof(double) * 2 * (size_t)nt);
+    if (!row) { out->spectral_rms = NAN; return; }
     double s0 = 0.0, s1 = 0.0, s2 = 0.0;
     for (int m = 0; m < nr; ++m) {
         memcpy(row, A + (size_t)m * nt, sizeof(double) * 2 * (size_t)nt);
@@ -906,6 +907,11 @@ void orc_xy_diag(const orc_problem *pb, const orc_xy_grid *g, const double *Ad, 
     memset(out, 0, sizeof(*out));
     double esum = 0.0, s0 = 0.0, s1 = 0.0, s2 = 0.0;
     double *row = (double *)malloc(sizeof(double) * 2 * (size_t)nt);
+    if (!row) {                      /* no memory: every diagnostic NaN */
+        out->energy = out->peak_intensity = out->onaxis_peak = out->peak_rho = out->spectral_rms = NAN;
+        out->nonfinite = 1;
+        return;
+    }
     for (size_t m = 0; m < rows; ++m) {
         for (int p = 0; p < nt; ++p) {
             cplx v = A[m * nt + p];
@@ -970,6 +976,11 @@ int orc_propagate_adaptive(const orc_problem *pb, double *A, double *rho,
     double *a2 = (double *)malloc(sizeof(double) * n2);
     double *r2 = (double *)malloc(sizeof(double) * n1);
     memset(res, 0, sizeof(*res));
+    if (!a1 || !a2 || !r2) {
+        free(a1); free(a2); free(r2);
+        res->status = -3;
+        return -3;
+    }
     double z = z0, dz = dz0;
     int consecutive = 0;
     int status = 0;
@@ -1035,6 +1046,7 @@ int orc_mlp_forward(int batch, int nin, int nh, const double *pr,
     mlp_offsets(nin, nh, o);
     double *h1 = (double *)malloc(sizeof(double) * (size_t)nh);
     double *h2 = (double *)malloc(sizeof(double) * (size_t)nh);
+    if (!h1 || !h2) { free(h1); free(h2); return -3; }
     for (int b = 0; b < batch; ++b) {
         const double *xb = x + (size_t)b * nin;
         for (int i = 0; i < nh; ++i) {
@@ -1070,6 +1082,7 @@ int orc_mlp_loss_grad(int batch, int nin, int nh, const double *pr,
     double *h2 = (double *)malloc(sizeof(double) * (size_t)nh);
     double *g1 = (double *)malloc(sizeof(double) * (size_t)nh);
     double *g2 = (double *)malloc(sizeof(double) * (size_t)nh);
+    if (!h1 || !h2 || !g1 || !g2) { free(h1); free(h2); free(g1); free(g2); return -3; }
     double total = 0.0;
     for (int b = 0; b < batch; ++b) {
         const double *xb = x + (size_t)b * nin;

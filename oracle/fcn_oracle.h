@@ -79,7 +79,8 @@ typedef struct {
     long   accepted;
     long   rejected;
     double last_err;
-    int    status;        /* 0 ok, -1 dz underflow / too many rejections   */
+    int    status;        /* 0 ok, -1 dz underflow / too many rejections, */
+                          /* -3 no memory                                   */
 } orc_adaptive_result;
 
 /* Derived constants. */
