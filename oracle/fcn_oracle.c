@@ -447,7 +447,7 @@ struct orc_pool {
     orc_member *mem;
     pthread_barrier_t go, done;
     orc_gate gate;
-    orc_range_fn fn;         /* the task of the current round */
+    orc_range_fn fn;         /* the current parallel-for body */
     void *ctx;
     long items;
     int quit;
